@@ -1,0 +1,217 @@
+/*
+ * kkm.h -- C ABI of a GB300 (sm_103a) library for approximate mini-batch
+ * kernel k-means (Ferrarotti, Decherchi & Rocchia, "Distributed kernel
+ * k-means for large scale clustering", arXiv 1710.03013).
+ *
+ * Conventions shared by every call
+ *   - Matrices are row-major float32.  A "sample" is one row of length d.  For
+ *     the molecular-dynamics kernel (KKM_RMSD) a row holds one frame as
+ *     [n_atoms][3] coordinates, so d == 3 * n_atoms.
+ *   - Input pointers may point to device memory (e.g. a CUDA tensor) or to
+ *     host memory; the library detects which with cudaPointerGetAttributes and
+ *     copies host inputs to the device itself.  Output pointers follow the
+ *     same rule unless the comment says "host".
+ *   - The caller owns every buffer it passes and keeps it valid until the call
+ *     returns.  Calls run in stream order on the given stream (NULL = the
+ *     legacy default stream) and are synchronous: results are complete when
+ *     the call returns.
+ *   - No call aborts, traps or throws.  Errors are returned as kkm_status; a
+ *     readable message for the calling thread is in kkm_last_error().  Invalid
+ *     arguments give KKM_EINVAL and write nothing.
+ *   - Work is deterministic: the same inputs, seed and options give
+ *     bit-identical results.
+ */
+#ifndef KKM_H
+#define KKM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kkm_status {
+  KKM_OK = 0,
+  KKM_EINVAL = 1,    /* invalid argument (sizes, NaN/Inf inputs, bad kernel) */
+  KKM_ENOMEM = 2,    /* device allocation failed                            */
+  KKM_EBUDGET = 3,   /* refused by a memory budget                          */
+  KKM_ECUDA = 4,     /* a CUDA runtime call failed                          */
+  KKM_ETIMEOUT = 5,  /* a bounded device wait gave up                       */
+  KKM_EINTERNAL = 6  /* internal inconsistency                              */
+} kkm_status;
+
+/* Kernel functions (Section 2 replaces feature-space products by a Mercer
+ * kernel K; the paper uses a Gaussian kernel and, for MD frames, asks for
+ * roto-translational invariance without writing the kernel down):
+ *   KKM_RBF    K(x,y) = exp(-||x-y||^2 / (2 sigma^2))
+ *   KKM_RMSD   K(x,y) = exp(-rmsd(x,y)^2 / (2 sigma^2)), rmsd after optimal
+ *              proper superposition of the mean-centred frames (QCP root)
+ *   KKM_LINEAR K(x,y) = x . y  (kernel k-means then equals Lloyd k-means)   */
+typedef enum kkm_kernel_kind { KKM_RBF = 0, KKM_RMSD = 1, KKM_LINEAR = 2 } kkm_kernel_kind;
+
+/* Arithmetic of the kernel-block evaluation.  KKM_FP32 is the plain path. */
+typedef enum kkm_precision { KKM_FP32 = 0, KKM_BF16 = 1, KKM_FP8 = 2 } kkm_precision;
+
+/* Mini-batch fetching (Section 3.1): stride X^i = {x_(i+jB)}; block = B
+ * contiguous pieces, the first N mod B one sample longer.                   */
+typedef enum kkm_sampling { KKM_STRIDE = 0, KKM_BLOCK = 1 } kkm_sampling;
+
+/* Prototypes used by kkm_assign / kkm_cost: the sparse landmark centroids
+ * of the last mini-batch (Eq. 14-17) or the global medoids (Eq. 2 against
+ * the output M of Algorithm 1).                                             */
+typedef enum kkm_assign_mode { KKM_ASSIGN_SUPPORTS = 0, KKM_ASSIGN_MEDOIDS = 1 } kkm_assign_mode;
+
+typedef struct kkm_kernel {
+  int32_t kind;     /* kkm_kernel_kind                                         */
+  float sigma;      /* Gaussian width; <= 0 asks kkm_fit for the median rule   */
+  int32_t n_atoms;  /* KKM_RMSD only: atoms per frame (d == 3 * n_atoms)       */
+} kkm_kernel;
+
+typedef struct kkm_options {
+  int32_t precision;            /* kkm_precision (default KKM_FP32)             */
+  int32_t sampling;             /* kkm_sampling (default KKM_STRIDE)            */
+  int32_t early_stop;           /* 1: stop an inner loop when no label changes */
+  int32_t reserved;             /* must be 0                                    */
+  const int64_t* init_medoids;  /* host [C] global sample indices replacing
+                                   kernel k-means++, or NULL                    */
+  void* stream;                 /* cudaStream_t or NULL                         */
+} kkm_options;
+
+/* A fitted model.  It owns device copies of everything it keeps (medoid and
+ * landmark coordinates, landmark labels, compactness g_hat); nothing aliases
+ * the caller's data.                                                        */
+typedef struct kkm_model kkm_model;
+
+/* Fills *opt with the defaults listed above (early_stop = 1). */
+void kkm_options_default(kkm_options* opt);
+
+/*
+ * kkm_fit -- Algorithm 1 with the landmark approximation of Section 3.2.
+ *   X        [N][d] float32 samples (device or host).
+ *   C        number of clusters, 1 <= C <= 256 and C <= every mini-batch size.
+ *   B        number of mini-batches, 1 <= B <= N.
+ *   s        landmark fraction of Eq. 18, 0 < s <= 1; per mini-batch
+ *            |L| = clamp(ceil(s N_i - 1e-9), 1, N_i), computed in double.
+ *   k        kernel; sigma <= 0 selects the median pairwise distance of up to
+ *            2048 samples drawn with the seed (not allowed for KKM_LINEAR).
+ *   iters    cap on inner iterations per mini-batch (>= 0).
+ *   seed     seeds SplitMix64; its draws seed k-means++, the bandwidth sample
+ *            and one landmark draw per mini-batch, in that order.
+ *   opt      options or NULL for the defaults.
+ *   labels_out [N] int32 (device or host, nullable): each sample's final
+ *            label in its own mini-batch.
+ *   model_out  receives a new model (free with kkm_model_free), nullable.
+ * Per mini-batch it evaluates the block K(X^i, L) once (Alg. 1 line 3),
+ * initialises labels from the global medoids (Eq. 8, k-means++ on the first
+ * mini-batch), iterates Eq. 15-17, then computes the mini-batch medoids
+ * (Eq. 10) and merges them into the global ones (Eq. 11-13).
+ * Errors: KKM_EINVAL for bad sizes, s outside (0,1], d != 3 n_atoms, C larger
+ * than a mini-batch, non-finite X or out-of-range init_medoids.
+ */
+kkm_status kkm_fit(const float* X, int64_t N, int64_t d, int32_t C, int32_t B,
+                   double s, const kkm_kernel* k, int32_t iters, uint64_t seed,
+                   const kkm_options* opt, int32_t* labels_out,
+                   kkm_model** model_out);
+
+/*
+ * kkm_assign -- label new samples against a fitted model: Eq. 15 with the
+ * model's landmark supports (mode KKM_ASSIGN_SUPPORTS) or Eq. 2 against its
+ * medoids (KKM_ASSIGN_MEDOIDS).  Ties go to the lowest cluster index.
+ *   Xnew [M][d] float32, labels_out [M] int32, dist_out [M] float32 squared
+ *   feature-space distance to the chosen prototype (nullable).  M may be 0.
+ */
+kkm_status kkm_assign(const kkm_model* m, const float* Xnew, int64_t M,
+                      int32_t mode, int32_t* labels_out, float* dist_out,
+                      void* stream);
+
+/* kkm_cost -- Eq. 1 for samples X against the model's prototypes:
+ * *omega_out (host) = sum_i min_j ||phi(x_i) - w_j||^2, accumulated in FP64. */
+kkm_status kkm_cost(const kkm_model* m, const float* X, int64_t N, int32_t mode,
+                    double* omega_out, void* stream);
+
+/* Model accessors.  All outputs are host memory unless stated. */
+kkm_status kkm_model_info(const kkm_model* m, int32_t* C, int64_t* d,
+                          int32_t* n_support, float* sigma);
+/* idx_out [C] global sample indices of the medoids; counts_out [C] the
+ * cumulative member counts |w_j| of Eq. 13 (nullable); coords_out [C][d]
+ * medoid coordinates (device or host, nullable). */
+kkm_status kkm_model_medoids(const kkm_model* m, int64_t* idx_out,
+                             int64_t* counts_out, float* coords_out);
+/* Final supports of the last mini-batch: landmark labels [n_support],
+ * g_hat [C] (Eq. 16) and landmark counts n_j [C]; each nullable. */
+kkm_status kkm_model_supports(const kkm_model* m, int32_t* labels_out,
+                              double* ghat_out, int32_t* n_out);
+/* Inner-loop trace over all mini-batches: Omega (Eq. 9) and the number of
+ * changed labels of each executed iteration, up to cap entries; *n_out gets
+ * the total number of entries. */
+kkm_status kkm_model_trace(const kkm_model* m, double* omega, int32_t* changed,
+                           int32_t cap, int32_t* n_out);
+void kkm_model_free(kkm_model* m);
+
+/* kkm_kernel_matrix -- out[a][b] = K(A_a, B_b) for A [nA][d], B [nB][d]
+ * (the kernel-block evaluation of Alg. 1 line 3 as a standalone call).
+ * out is [nA][nB] float32, device or host.  sigma must be > 0. */
+kkm_status kkm_kernel_matrix(const float* A, int64_t nA, const float* Bm,
+                             int64_t nB, int64_t d, const kkm_kernel* k,
+                             float* out, void* stream);
+
+/* kkm_median_bandwidth -- the bandwidth rule kkm_fit applies when sigma <= 0:
+ * the lower median of the pairwise distances (Euclidean, or RMSD for
+ * KKM_RMSD) among min(N, 2048) samples drawn by the bandwidth stream of
+ * `seed`.  *sigma_out is host memory. */
+kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d,
+                                const kkm_kernel* k, uint64_t seed,
+                                float* sigma_out);
+
+/*
+ * kkm_debug_step -- one inner iteration (Eq. 15-17) on one mini-batch with
+ * the labels given (teacher forcing), for step-by-step checks.
+ *   Xb [Ni][d] mini-batch samples; L [nL] sorted local landmark indices
+ *   (host); u_in [Ni] labels (host).  Outputs (host, each nullable):
+ *   u_out [Ni], fhat_out [Ni][C] (Eq. 17; NaN where n_j = 0),
+ *   margin_out [Ni] (second-best minus best distance), ghat_out [C]
+ *   (Eq. 16; NaN where n_j = 0), n_out [C], *omega_out, *changed_out.
+ */
+kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d,
+                          const int32_t* L, int32_t nL, const kkm_kernel* k,
+                          int32_t C, const int32_t* u_in, int32_t* u_out,
+                          float* fhat_out, float* margin_out, double* ghat_out,
+                          int32_t* n_out, double* omega_out,
+                          int32_t* changed_out, void* stream);
+
+/* kkm_debug_kmeanspp -- the kernel k-means++ picks kkm_fit makes on its first
+ * mini-batch X0 [N0][d] for `seed`: picks_out [C] local indices (host). */
+kkm_status kkm_debug_kmeanspp(const float* X0, int64_t N0, int64_t d,
+                              const kkm_kernel* k, int32_t C, uint64_t seed,
+                              int64_t* picks_out, void* stream);
+
+/* kkm_minibatch_plan -- host-only (no GPU needed): the mini-batch geometry
+ * and landmark draw kkm_fit uses for mini-batch `batch` of N samples.
+ * Mini-batch `batch` holds the global samples start + l*step, l < *n_out
+ * (Section 3.1 sampling); L_out (nullable, capacity *n_out) receives its
+ * sorted local landmark indices (Eq. 14, |L| from Eq. 18) and *nl_out their
+ * number.  All pointers are host memory. */
+kkm_status kkm_minibatch_plan(int64_t N, int32_t B, int32_t sampling, double s,
+                              uint64_t seed, int32_t batch, int64_t* start_out,
+                              int64_t* step_out, int64_t* n_out, int32_t* L_out,
+                              int64_t* nl_out);
+
+const char* kkm_status_string(kkm_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char* kkm_last_error(void);
+
+/* Per-kernel device timing.  When enabled, every library kernel launch is
+ * bracketed by CUDA events on its stream; kkm_prof_read returns the number of
+ * launches and the summed device milliseconds of the named kernel since the
+ * last reset (0 launches if unknown).  kkm_prof_names writes a
+ * comma-separated list of the names seen into buf. */
+void kkm_prof_enable(int32_t on);
+void kkm_prof_reset(void);
+int32_t kkm_prof_read(const char* name, int64_t* launches, double* ms);
+int32_t kkm_prof_names(char* buf, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KKM_H */

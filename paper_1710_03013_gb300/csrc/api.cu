@@ -1,0 +1,1237 @@
+// C-ABI entry points and host orchestration of Algorithm 1.
+//
+// The host side only validates arguments, draws the random numbers of the
+// method (SplitMix64, Steele, Lea & Flood 2014: landmark sets, k-means++
+// draws, the bandwidth sample), allocates stream-ordered device memory and
+// enqueues kernels.  Every step of the clustering itself runs on the device;
+// one mini-batch needs no host synchronisation between its kernels (early stop
+// is a device flag that makes the remaining launches return at once).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
+#include <mutex>
+#include <type_traits>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+// ======================================================================
+// Opaque model
+// ======================================================================
+struct kkm_model {
+  int C = 0;
+  int64_t d = 0;
+  int kind = 0;
+  float sigma = 1.0f;
+  int n_atoms = 0;
+  int dp = 0;  // prepared row length (padded)
+  int nL = 0;
+  int device = 0;
+  float* sup = nullptr;        // [nL][dp] prepared landmark rows
+  float* sup_aux = nullptr;    // [nL] squared norms (RBF/linear) or G (RMSD)
+  int64_t* sup_ids = nullptr;  // [nL] global sample ids of the landmarks
+  int32_t* sup_labels = nullptr;
+  int32_t* L_ident = nullptr;  // [nL] 0..nL-1
+  int32_t* perm = nullptr;
+  int32_t* seg_off = nullptr;
+  int32_t* n_j = nullptr;
+  int32_t* unit_j = nullptr;
+  int32_t* unit_kb = nullptr;
+  int32_t* unit_ke = nullptr;
+  int32_t* seg_unit = nullptr;
+  int32_t* n_units = nullptr;
+  double* ghat = nullptr;      // [C]
+  float* med = nullptr;        // [C][dp]
+  float* med_aux = nullptr;    // [C]
+  std::vector<int64_t> medoids, W;
+  std::vector<double> omega;
+  std::vector<int32_t> changed;
+  std::vector<int32_t> sup_labels_h;
+  std::vector<double> ghat_h;
+  std::vector<int32_t> n_h;
+  std::vector<float> med_coords_h;  // [C][d]
+  ~kkm_model() {
+    void* ps[] = {sup, sup_aux, sup_ids, sup_labels, L_ident, perm, seg_off, n_j, unit_j,
+                  unit_kb, unit_ke, seg_unit, n_units, ghat, med, med_aux};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+  }
+};
+
+namespace kkm {
+
+// ======================================================================
+// Errors
+// ======================================================================
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+kkm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  cudaGetLastError();
+  set_error(std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+            ") in " + what + " at " + file + ":" + std::to_string(line));
+  return e == cudaErrorMemoryAllocation ? KKM_ENOMEM : KKM_ECUDA;
+}
+static kkm_status invalid(const std::string& msg) {
+  set_error(msg);
+  return KKM_EINVAL;
+}
+
+// ======================================================================
+// Profiling (per-kernel CUDA-event timing)
+// ======================================================================
+struct ProfEntry {
+  int64_t launches = 0;
+  double ms = 0.0;
+};
+struct Pending {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::unordered_map<std::string, ProfEntry> g_prof;
+static std::vector<Pending> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  Pending p{name, take_event(), take_event()};
+  cudaEventRecord(p.a, s);
+  g_pending.push_back(p);
+  slot = (int)g_pending.size() - 1;
+}
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(g_pending[slot].b, stream);
+}
+void prof_collect() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& p : g_pending) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& e = g_prof[p.name];
+      e.launches += 1;
+      e.ms += ms;
+    }
+    cudaGetLastError();
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+#define KKM_RUN(name, st, call)                 \
+  do {                                          \
+    ::kkm::ProfScope _ps(name, st);             \
+    KKM_CK(call);                               \
+  } while (0)
+
+// ======================================================================
+// Random numbers: SplitMix64 from its published definition
+// ======================================================================
+struct SplitMix64 {
+  uint64_t state;
+  explicit SplitMix64(uint64_t s) : state(s) {}
+  uint64_t next() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double u01() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// First k entries of a partial Fisher-Yates shuffle of [0, n).
+static std::vector<int64_t> partial_shuffle(int64_t n, int64_t k, SplitMix64& rng) {
+  std::vector<int64_t> idx((size_t)n);
+  for (int64_t a = 0; a < n; ++a) idx[(size_t)a] = a;
+  for (int64_t a = 0; a < k; ++a) {
+    const int64_t r = a + (int64_t)floor(rng.u01() * (double)(n - a));
+    std::swap(idx[(size_t)a], idx[(size_t)r]);
+  }
+  idx.resize((size_t)k);
+  return idx;
+}
+
+// Eq. 18 solved for |L|.
+static int64_t n_landmarks(int64_t Ni, double s) {
+  int64_t nl = (int64_t)ceil(s * (double)Ni - 1e-9);
+  return std::min<int64_t>(std::max<int64_t>(nl, 1), Ni);
+}
+
+// ======================================================================
+// Device memory helpers
+// ======================================================================
+static void setup_pool_once(int dev) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
+struct Workspace {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Workspace(cudaStream_t s) : st(s) {}
+  ~Workspace() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <typename T>
+  kkm_status alloc(T** p, int64_t n) {
+    void* q = nullptr;
+    const size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+    KKM_CK(cudaMallocAsync(&q, bytes, st));
+    ptrs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return KKM_OK;
+  }
+};
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller input: the pointer itself if it is device memory,
+// otherwise a workspace copy.
+template <typename T>
+static kkm_status device_input(Workspace& ws, const T* p, int64_t n, const T** out) {
+  if (n <= 0 || is_device_ptr(p)) {
+    *out = p;
+    return KKM_OK;
+  }
+  T* d = nullptr;
+  KKM_TRY(ws.alloc(&d, n));
+  KKM_CK(cudaMemcpyAsync(d, p, (size_t)n * sizeof(T), cudaMemcpyHostToDevice, ws.st));
+  *out = d;
+  return KKM_OK;
+}
+
+// ======================================================================
+// Small kernels of the host orchestration
+// ======================================================================
+__global__ void iota64_kernel(int64_t* out, int64_t start, int64_t step, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = start + i * step;
+}
+__global__ void gather_i64_kernel(const int64_t* in, const int32_t* idx, int64_t n, int64_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = idx[i] >= 0 ? in[idx[i]] : -1;
+}
+__global__ void gather_i32_kernel(const int32_t* in, const int32_t* idx, int64_t n, int32_t* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[idx[i]];
+}
+__global__ void clamp_idx_kernel(const int32_t* in, int n, int32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i] >= 0 ? in[i] : 0;
+}
+
+static unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, ceil_div(n, t)); }
+
+// ======================================================================
+// Kernel-function dispatch (RBF / linear via the Gram product, MD via RMSD)
+// ======================================================================
+struct KernelSpec {
+  int kind;       // kkm_kernel_kind
+  float sigma;
+  int n_atoms;
+  int64_t d;
+  int dp;         // prepared row length
+  int ap;         // padded atoms (RMSD)
+  float neg_scale() const { return (float)(-1.4426950408889634 / (2.0 * (double)sigma * (double)sigma)); }
+  bool gaussian() const { return kind != KKM_LINEAR; }
+};
+
+static kkm_status make_spec(const kkm_kernel* k, int64_t d, KernelSpec* sp) {
+  if (!k) return invalid("kernel is NULL");
+  sp->kind = k->kind;
+  sp->sigma = k->sigma;
+  sp->n_atoms = k->n_atoms;
+  sp->d = d;
+  if (d < 1) return invalid("d must be >= 1");
+  if (k->kind == KKM_RBF || k->kind == KKM_LINEAR) {
+    sp->dp = (int)round_up(d, 8);
+    sp->ap = 0;
+  } else if (k->kind == KKM_RMSD) {
+    if (k->n_atoms < 1 || (int64_t)3 * k->n_atoms != d)
+      return invalid("KKM_RMSD needs n_atoms >= 1 and d == 3 * n_atoms");
+    sp->ap = (int)round_up(k->n_atoms, 8);
+    sp->dp = 3 * sp->ap;
+  } else {
+    return invalid("unknown kernel kind");
+  }
+  if (sp->dp > (1 << 20)) return invalid("d too large");
+  return KKM_OK;
+}
+
+// Prepared rows start + l*step of X (device) -> out [n][dp], aux [n].
+static kkm_status prep_rows(const KernelSpec& sp, const float* X, int64_t start, int64_t step,
+                            int64_t n, float* out, float* aux, cudaStream_t st) {
+  if (sp.kind == KKM_RMSD)
+    KKM_RUN("rmsd_prep", st, launch_rmsd_prep_rows(X, sp.n_atoms, start, step, n, out, sp.ap, aux, st));
+  else
+    KKM_RUN("gather_rows", st, launch_gather_rows(X, sp.d, start, step, n, out, sp.dp, aux, st));
+  return KKM_OK;
+}
+static kkm_status prep_ids(const KernelSpec& sp, const float* X, const int64_t* ids, int64_t n,
+                           float* out, float* aux, cudaStream_t st) {
+  if (sp.kind == KKM_RMSD)
+    KKM_RUN("rmsd_prep", st, launch_rmsd_prep_idx64(X, sp.n_atoms, ids, n, out, sp.ap, aux, st));
+  else
+    KKM_RUN("gather_rows", st, launch_gather_idx64(X, sp.d, ids, n, out, sp.dp, aux, st));
+  return KKM_OK;
+}
+// Copies of already prepared rows (the row's sum of squares is its aux value
+// for both layouts: squared norm, or G of a centred frame).
+static kkm_status copy_prepared(const KernelSpec& sp, const float* Xp, const int32_t* idx, int64_t n,
+                                float* out, float* aux, cudaStream_t st) {
+  KKM_RUN("gather_rows", st, launch_gather_idx32(Xp, sp.dp, idx, n, out, sp.dp, aux, st));
+  return KKM_OK;
+}
+// out[a*ldo + b] = K(A_a, B_b).  dist != 0 gives distances instead.
+static kkm_status kernel_block(const KernelSpec& sp, const float* A, const float* auxA,
+                               const int64_t* idA, int64_t nA, const float* Bm, const float* auxB,
+                               const int64_t* idB, int64_t nB, float* out, int64_t ldo,
+                               cudaStream_t st, bool dist = false) {
+  if (sp.kind == KKM_RMSD) {
+    KKM_RUN("rmsd_gram", st,
+            launch_rmsd_gram(dist ? DK_DIST : DK_RBF, A, nA, Bm, nB, sp.ap, sp.n_atoms, auxA, auxB, idA,
+                             idB, sp.neg_scale(), out, ldo, st));
+  } else {
+    const int dk = dist ? DK_DIST : (sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF);
+    KKM_RUN("gram", st,
+            launch_gram(dk, A, nA, Bm, nB, sp.dp, auxA, auxB, idA, idB, sp.neg_scale(), out, ldo, st));
+  }
+  return KKM_OK;
+}
+
+// ======================================================================
+// Bandwidth rule
+// ======================================================================
+static kkm_status median_bandwidth_dev(const KernelSpec& sp, const float* X, int64_t N, uint64_t bw_seed,
+                                       Workspace& ws, float* sigma_out) {
+  const int64_t M = std::min<int64_t>(N, 2048);
+  if (M < 2) {
+    *sigma_out = 1.0f;
+    return KKM_OK;
+  }
+  SplitMix64 bw(bw_seed);
+  std::vector<int64_t> pick = partial_shuffle(N, M, bw);
+  cudaStream_t st = ws.st;
+  int64_t* ids;
+  float *P, *aux, *D, *out;
+  uint32_t* scratch;
+  const int64_t ld = round_up(M, 4);
+  KKM_TRY(ws.alloc(&ids, M));
+  KKM_TRY(ws.alloc(&P, M * sp.dp));
+  KKM_TRY(ws.alloc(&aux, M));
+  KKM_TRY(ws.alloc(&D, M * ld));
+  KKM_TRY(ws.alloc(&out, 1));
+  KKM_TRY(ws.alloc(&scratch, 1024));
+  KKM_CK(cudaMemcpyAsync(ids, pick.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
+  KKM_TRY(prep_ids(sp, X, ids, M, P, aux, st));
+  KKM_TRY(kernel_block(sp, P, aux, ids, M, P, aux, ids, M, D, ld, st, /*dist=*/true));
+  const int64_t pairs = M * (M - 1) / 2;
+  KKM_RUN("median_select", st, launch_select_upper(D, (int)M, ld, (pairs - 1) / 2, scratch, out, st));
+  float sig = 0.0f;
+  KKM_CK(cudaMemcpyAsync(&sig, out, 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  if (!(sig > 0.0f) || !isfinite(sig)) sig = 1.0f;
+  *sigma_out = sig;
+  return KKM_OK;
+}
+
+// ======================================================================
+// Per-problem device state of the inner loop
+// ======================================================================
+struct LoopBuffers {
+  Supports S{};
+  IterState I{};
+  int32_t* n_copy = nullptr;  // [C]
+  int max_units = 0;
+};
+
+static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int trace_cap, LoopBuffers* lb) {
+  Supports& S = lb->S;
+  IterState& I = lb->I;
+  const int mu = max_units_for(nLmax, C);
+  lb->max_units = mu;
+  S.C = C;
+  S.max_units = mu;
+  KKM_TRY(ws.alloc(&S.perm, nLmax));
+  KKM_TRY(ws.alloc(&S.seg_off, C + 1));
+  KKM_TRY(ws.alloc(&S.n_j, C));
+  KKM_TRY(ws.alloc(&S.unit_j, mu));
+  KKM_TRY(ws.alloc(&S.unit_kb, mu));
+  KKM_TRY(ws.alloc(&S.unit_ke, mu));
+  KKM_TRY(ws.alloc(&S.seg_unit, C + 1));
+  KKM_TRY(ws.alloc(&S.n_units, 1));
+  KKM_TRY(ws.alloc(&S.col_label, ldk));
+  KKM_TRY(ws.alloc(&lb->n_copy, C));
+  I.n_strips = (int)ceil_div(ldk, kStripCols);
+  I.assign_grid = (int)std::min<int64_t>(ceil_div(ldk, 256), 152 * 4);
+  KKM_TRY(ws.alloc(&I.partial, (int64_t)mu * ldk));
+  KKM_TRY(ws.alloc(&I.gpart, (int64_t)mu * I.n_strips));
+  KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.ticket, 1));
+  KKM_TRY(ws.alloc(&I.done, 1));
+  KKM_TRY(ws.alloc(&I.trace_omega, std::max(trace_cap, 1)));
+  KKM_TRY(ws.alloc(&I.trace_changed, std::max(trace_cap, 1)));
+  KKM_TRY(ws.alloc(&I.trace_count, 1));
+  KKM_CK(cudaMemsetAsync(I.ticket, 0, 4, ws.st));
+  KKM_CK(cudaMemsetAsync(I.done, 0, 4, ws.st));
+  KKM_CK(cudaMemsetAsync(I.trace_count, 0, 4, ws.st));
+  return KKM_OK;
+}
+
+// Kernel k-means++ on prepared rows Xi (picks[0] already on the device).
+static kkm_status kmeanspp_dev(const KernelSpec& sp, const float* Xi, const float* aux_i, int Ni, int C,
+                               const float* kself, float* rowbuf, float* rowaux, float* kcol,
+                               int64_t ldk, double* D2, int32_t* picks, const double* draws_d,
+                               cudaStream_t st) {
+  for (int r = 1; r < C; ++r) {
+    KKM_TRY(copy_prepared(sp, Xi, picks + (r - 1), 1, rowbuf, rowaux, st));
+    KKM_TRY(kernel_block(sp, rowbuf, rowaux, nullptr, 1, Xi, aux_i, nullptr, Ni, kcol, ldk, st));
+    KKM_RUN("kpp_round", st, launch_kpp_round(kcol, Ni, kself, D2, picks, draws_d, r, st));
+  }
+  return KKM_OK;
+}
+
+struct BatchGeom {
+  int64_t start, step, Ni;
+};
+
+static std::vector<BatchGeom> batch_geometry(int64_t N, int B, int sampling) {
+  std::vector<BatchGeom> g;
+  if (sampling == KKM_STRIDE) {
+    for (int i = 0; i < B; ++i) g.push_back({i, B, (N - i + B - 1) / B});
+  } else {
+    const int64_t base = N / B, extra = N % B;
+    int64_t start = 0;
+    for (int i = 0; i < B; ++i) {
+      const int64_t n = base + (i < extra ? 1 : 0);
+      g.push_back({start, 1, n});
+      start += n;
+    }
+  }
+  return g;
+}
+
+// ======================================================================
+// kkm_fit
+// ======================================================================
+static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, int32_t B, double s,
+                           const kkm_kernel* k, int32_t iters, uint64_t seed, const kkm_options* opt_in,
+                           int32_t* labels_out, kkm_model** model_out) {
+  kkm_options opt;
+  kkm_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  if (!X_in) return invalid("X is NULL");
+  if (N < 1 || N > INT32_MAX) return invalid("N must be in [1, 2^31)");
+  if (C < 1 || C > kMaxC) return invalid("C must be in [1, 256]");
+  if (B < 1 || B > N) return invalid("B must be in [1, N]");
+  if (!(s > 0.0 && s <= 1.0)) return invalid("s must be in (0, 1]");
+  if (iters < 0) return invalid("iters must be >= 0");
+  if (opt.reserved != 0) return invalid("options.reserved must be 0");
+  if (opt.sampling != KKM_STRIDE && opt.sampling != KKM_BLOCK) return invalid("unknown sampling");
+  if (opt.precision != KKM_FP32) return invalid("only KKM_FP32 is available in this build");
+  KernelSpec sp;
+  KKM_TRY(make_spec(k, d, &sp));
+  if (sp.kind != KKM_LINEAR && !isfinite(sp.sigma)) return invalid("sigma must be finite");
+  const std::vector<BatchGeom> geo = batch_geometry(N, B, opt.sampling);
+  int64_t Nmax = 0, Nmin = INT64_MAX, nLmax = 0;
+  for (auto& g : geo) {
+    Nmax = std::max(Nmax, g.Ni);
+    Nmin = std::min(Nmin, g.Ni);
+    nLmax = std::max(nLmax, n_landmarks(g.Ni, s));
+  }
+  if (C > Nmin) return invalid("C exceeds the size of a mini-batch");
+  std::vector<int64_t> init;
+  if (opt.init_medoids) {
+    init.assign(opt.init_medoids, opt.init_medoids + C);
+    for (int64_t v : init)
+      if (v < 0 || v >= N) return invalid("init_medoids out of range");
+  }
+
+  cudaStream_t st = (cudaStream_t)opt.stream;
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  setup_pool_once(dev);
+  Workspace ws(st);
+
+  // ---- inputs on the device, validated
+  const float* X = nullptr;
+  KKM_TRY(device_input(ws, X_in, N * d, &X));
+  {
+    int* flag;
+    KKM_TRY(ws.alloc(&flag, 1));
+    KKM_CK(cudaMemsetAsync(flag, 0, 4, st));
+    KKM_RUN("check_finite", st, launch_check_finite(X, N * d, flag, st));
+    int bad = 0;
+    KKM_CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    if (bad) return invalid("X holds NaN or Inf");
+  }
+
+  // ---- random numbers (Section 3.1, 3.2): k-means++, bandwidth, landmarks
+  SplitMix64 master(seed);
+  SplitMix64 kpp(master.next());
+  const uint64_t bw_seed = master.next();
+  std::vector<SplitMix64> lm;
+  for (int i = 0; i < B; ++i) lm.emplace_back(master.next());
+  std::vector<int64_t> L_off(B + 1, 0);
+  std::vector<int32_t> L_all;
+  for (int i = 0; i < B; ++i) {
+    const int64_t Ni = geo[i].Ni, nl = n_landmarks(Ni, s);
+    if (nl == Ni) {
+      for (int64_t a = 0; a < Ni; ++a) L_all.push_back((int32_t)a);
+    } else {
+      std::vector<int64_t> p = partial_shuffle(Ni, nl, lm[i]);
+      std::sort(p.begin(), p.end());
+      for (int64_t v : p) L_all.push_back((int32_t)v);
+    }
+    L_off[i + 1] = (int64_t)L_all.size();
+  }
+  const bool do_kpp = init.empty();
+  std::vector<double> draws(C, 0.0);
+  std::vector<int32_t> pick0(1, 0);
+  if (do_kpp) {
+    for (int r = 0; r < C; ++r) draws[r] = kpp.u01();
+    pick0[0] = (int32_t)floor(draws[0] * (double)geo[0].Ni);
+  }
+
+  // ---- bandwidth
+  if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
+    float sig = 1.0f;
+    KKM_TRY(median_bandwidth_dev(sp, X, N, bw_seed, ws, &sig));
+    sp.sigma = sig;
+  }
+
+  // ---- workspace
+  const int64_t ldk = round_up(Nmax, 32);
+  const int trace_cap = B * iters;
+  float *Xi, *aux_i, *XL, *auxL, *KT, *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol;
+  int64_t *gid, *gidL, *Mg, *W, *idMI;
+  int32_t *u, *Ld_all, *mi, *mi_safe, *cnt, *picks, *labels_dev = nullptr;
+  unsigned long long* keys;
+  double *ghat, *D2 = nullptr, *draws_d = nullptr;
+  KKM_TRY(ws.alloc(&Xi, Nmax * sp.dp));
+  KKM_TRY(ws.alloc(&aux_i, Nmax));
+  KKM_TRY(ws.alloc(&gid, Nmax));
+  KKM_TRY(ws.alloc(&XL, nLmax * sp.dp));
+  KKM_TRY(ws.alloc(&auxL, nLmax));
+  KKM_TRY(ws.alloc(&gidL, nLmax));
+  KKM_TRY(ws.alloc(&KT, nLmax * ldk));
+  KKM_TRY(ws.alloc(&Kt, (int64_t)C * ldk));
+  KKM_TRY(ws.alloc(&Kmi, (int64_t)C * ldk));
+  KKM_TRY(ws.alloc(&MX, (int64_t)C * sp.dp));
+  KKM_TRY(ws.alloc(&auxM, C));
+  KKM_TRY(ws.alloc(&MIX, (int64_t)C * sp.dp));
+  KKM_TRY(ws.alloc(&auxMI, C));
+  KKM_TRY(ws.alloc(&idMI, C));
+  KKM_TRY(ws.alloc(&Mg, C));
+  KKM_TRY(ws.alloc(&W, C));
+  KKM_TRY(ws.alloc(&u, Nmax));
+  KKM_TRY(ws.alloc(&Ld_all, (int64_t)L_all.size()));
+  KKM_TRY(ws.alloc(&mi, C));
+  KKM_TRY(ws.alloc(&mi_safe, C));
+  KKM_TRY(ws.alloc(&cnt, C));
+  KKM_TRY(ws.alloc(&keys, C));
+  KKM_TRY(ws.alloc(&ghat, C));
+  KKM_TRY(ws.alloc(&picks, C));
+  KKM_TRY(ws.alloc(&rowbuf, sp.dp));
+  KKM_TRY(ws.alloc(&rowaux, 1));
+  KKM_TRY(ws.alloc(&kcol, ldk));
+  LoopBuffers lb;
+  KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
+  Supports& S = lb.S;
+  IterState& I = lb.I;
+  if (do_kpp) {
+    KKM_TRY(ws.alloc(&D2, geo[0].Ni));
+    KKM_TRY(ws.alloc(&draws_d, C));
+    KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
+    KKM_CK(cudaMemcpyAsync(picks, pick0.data(), 4, cudaMemcpyHostToDevice, st));
+  } else {
+    KKM_CK(cudaMemcpyAsync(Mg, init.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
+  }
+  KKM_CK(cudaMemcpyAsync(Ld_all, L_all.data(), L_all.size() * 4, cudaMemcpyHostToDevice, st));
+  KKM_CK(cudaMemsetAsync(W, 0, (size_t)C * 8, st));
+  const bool labels_on_host = labels_out && !is_device_ptr(labels_out);
+  if (labels_out) {
+    if (labels_on_host)
+      KKM_TRY(ws.alloc(&labels_dev, N));
+    else
+      labels_dev = labels_out;
+  }
+  const float* kself = sp.kind == KKM_LINEAR ? aux_i : nullptr;
+  const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+
+  // ---- Algorithm 1
+  for (int i = 0; i < B; ++i) {
+    const BatchGeom& g = geo[i];
+    const int Ni = (int)g.Ni;
+    const int nL = (int)(L_off[i + 1] - L_off[i]);
+    const int32_t* Ld = Ld_all + L_off[i];
+    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, Xi, aux_i, st));             // fetch X^i
+    iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni);
+    KKM_LAUNCH_CK();
+    KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
+    gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL);
+    KKM_LAUNCH_CK();
+    KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st));  // Alg. 1 line 3
+
+    if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
+      KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, st));
+      KKM_RUN("local_to_global", st, launch_local_to_global(picks, C, g.start, g.step, Mg, st));
+    }
+    // Eq. 8: auxiliary block K~ = K(M, X^i) and nearest-medoid labels
+    KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, st));
+    KKM_TRY(kernel_block(sp, MX, auxM, Mg, C, Xi, aux_i, gid, Ni, Kt, ldk, st));
+    KKM_RUN("nearest", st, launch_nearest(Kt, ldk, Ni, C, kself, kmm, u, nullptr, st));
+
+    // supports of the initial labels
+    S.L = Ld;
+    S.nL = nL;
+    KKM_RUN("fill", st, launch_fill_i32(S.col_label, -1, ldk, st));
+    KKM_RUN("build_supports", st, launch_build_supports(S, u, st));
+    KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
+    for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
+      KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
+      KKM_RUN("assign", st,
+              launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
+                            /*rebuild=*/1, st));
+    }
+    // Eq. 10: f_hat of the final labels and the mini-batch medoids
+    IterState Ifin = I;
+    Ifin.done = nullptr;
+    KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, Ifin, st));
+    KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
+    KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, st));
+    KKM_RUN("medoid_keys", st, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, st));
+    KKM_RUN("medoid_pick", st, launch_medoid_pick(keys, cnt, S.n_j, C, mi, st));
+    // Eq. 12: K(X^i, m^i) and the convex merge
+    clamp_idx_kernel<<<blocks_for(C), 256, 0, st>>>(mi, C, mi_safe);
+    KKM_LAUNCH_CK();
+    KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, st));
+    gather_i64_kernel<<<blocks_for(C), 256, 0, st>>>(gid, mi, C, idMI);
+    KKM_LAUNCH_CK();
+    KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, st));
+    KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
+    KKM_RUN("merge_keys", st, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, st));
+    KKM_RUN("merge_apply", st, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, st));
+    if (labels_dev)
+      KKM_RUN("scatter_labels", st, launch_scatter_labels(u, Ni, g.start, g.step, labels_dev, st));
+    if (i == B - 1 && model_out) {
+      // keep the final supports of the last mini-batch
+      kkm_model* m = new kkm_model();
+      m->C = C;
+      m->d = d;
+      m->kind = sp.kind;
+      m->sigma = sp.sigma;
+      m->n_atoms = sp.n_atoms;
+      m->dp = sp.dp;
+      m->nL = nL;
+      m->device = dev;
+      std::unique_ptr<kkm_model> guard(m);
+      const int mu = lb.max_units;
+      auto A = [&](auto** p, int64_t n) -> kkm_status {
+        using T = std::remove_reference_t<decltype(**p)>;
+        void* q = nullptr;
+        KKM_CK(cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
+        *p = reinterpret_cast<T*>(q);
+        return KKM_OK;
+      };
+      KKM_TRY(A(&m->sup, (int64_t)nL * sp.dp));
+      KKM_TRY(A(&m->sup_aux, nL));
+      KKM_TRY(A(&m->sup_ids, nL));
+      KKM_TRY(A(&m->sup_labels, nL));
+      KKM_TRY(A(&m->L_ident, nL));
+      KKM_TRY(A(&m->perm, nL));
+      KKM_TRY(A(&m->seg_off, C + 1));
+      KKM_TRY(A(&m->n_j, C));
+      KKM_TRY(A(&m->unit_j, mu));
+      KKM_TRY(A(&m->unit_kb, mu));
+      KKM_TRY(A(&m->unit_ke, mu));
+      KKM_TRY(A(&m->seg_unit, C + 1));
+      KKM_TRY(A(&m->n_units, 1));
+      KKM_TRY(A(&m->ghat, C));
+      KKM_TRY(A(&m->med, (int64_t)C * sp.dp));
+      KKM_TRY(A(&m->med_aux, C));
+      auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
+        KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+        return KKM_OK;
+      };
+      KKM_TRY(cp(m->sup, XL, (size_t)nL * sp.dp * 4));
+      KKM_TRY(cp(m->sup_aux, auxL, (size_t)nL * 4));
+      KKM_TRY(cp(m->sup_ids, gidL, (size_t)nL * 8));
+      KKM_TRY(cp(m->perm, S.perm, (size_t)nL * 4));
+      KKM_TRY(cp(m->seg_off, S.seg_off, (size_t)(C + 1) * 4));
+      KKM_TRY(cp(m->n_j, S.n_j, (size_t)C * 4));
+      KKM_TRY(cp(m->unit_j, S.unit_j, (size_t)mu * 4));
+      KKM_TRY(cp(m->unit_kb, S.unit_kb, (size_t)mu * 4));
+      KKM_TRY(cp(m->unit_ke, S.unit_ke, (size_t)mu * 4));
+      KKM_TRY(cp(m->seg_unit, S.seg_unit, (size_t)(C + 1) * 4));
+      KKM_TRY(cp(m->n_units, S.n_units, 4));
+      KKM_TRY(cp(m->ghat, ghat, (size_t)C * 8));
+      gather_i32_kernel<<<blocks_for(nL), 256, 0, st>>>(u, Ld, nL, m->sup_labels);
+      KKM_LAUNCH_CK();
+      {
+        std::vector<int32_t> ident(nL);
+        for (int q = 0; q < nL; ++q) ident[q] = q;
+        KKM_CK(cudaMemcpyAsync(m->L_ident, ident.data(), (size_t)nL * 4, cudaMemcpyHostToDevice, st));
+        KKM_CK(cudaStreamSynchronize(st));
+      }
+      *model_out = guard.release();
+    }
+  }
+
+  // ---- results
+  if (model_out && *model_out) {
+    kkm_model* m = *model_out;
+    KKM_TRY(prep_ids(sp, X, Mg, C, m->med, m->med_aux, st));
+    m->medoids.resize(C);
+    m->W.resize(C);
+    int32_t tc = 0;
+    KKM_CK(cudaMemcpyAsync(m->medoids.data(), Mg, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(m->W.data(), W, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(&tc, I.trace_count, 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    m->omega.resize(tc);
+    m->changed.resize(tc);
+    if (tc > 0) {
+      KKM_CK(cudaMemcpyAsync(m->omega.data(), I.trace_omega, (size_t)tc * 8, cudaMemcpyDeviceToHost, st));
+      KKM_CK(cudaMemcpyAsync(m->changed.data(), I.trace_changed, (size_t)tc * 4, cudaMemcpyDeviceToHost, st));
+    }
+    m->sup_labels_h.resize(m->nL);
+    m->ghat_h.resize(C);
+    m->n_h.resize(C);
+    KKM_CK(cudaMemcpyAsync(m->sup_labels_h.data(), m->sup_labels, (size_t)m->nL * 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(m->ghat_h.data(), m->ghat, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(m->n_h.data(), m->n_j, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
+    m->med_coords_h.resize((size_t)C * d);
+  }
+  if (labels_on_host)
+    KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  if (model_out && *model_out) {
+    kkm_model* m = *model_out;
+    // medoid coordinates in the caller's layout
+    for (int j = 0; j < C; ++j)
+      KKM_CK(cudaMemcpy(m->med_coords_h.data() + (size_t)j * d, X + m->medoids[j] * d, (size_t)d * 4,
+                        cudaMemcpyDeviceToHost));
+  }
+  prof_collect();
+  return KKM_OK;
+}
+
+}  // namespace kkm
+
+namespace kkm {
+
+// ======================================================================
+// kkm_assign / kkm_cost
+// ======================================================================
+static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t M, int32_t mode,
+                              int32_t* labels_out, float* dist_out, double* omega_out,
+                              cudaStream_t st) {
+  if (!m) return invalid("model is NULL");
+  if (M < 0 || M > INT32_MAX) return invalid("M must be in [0, 2^31)");
+  if (mode != KKM_ASSIGN_SUPPORTS && mode != KKM_ASSIGN_MEDOIDS) return invalid("unknown assign mode");
+  if (M == 0) {
+    if (omega_out) *omega_out = 0.0;
+    return KKM_OK;
+  }
+  if (!Xnew_in) return invalid("X is NULL");
+  kkm_kernel kk{m->kind, m->sigma, m->n_atoms};
+  KernelSpec sp;
+  KKM_TRY(make_spec(&kk, m->d, &sp));
+  const int64_t d = m->d;
+  const int C = m->C;
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  setup_pool_once(dev);
+  Workspace ws(st);
+  const float* X = nullptr;
+  KKM_TRY(device_input(ws, Xnew_in, M * d, &X));
+  {
+    int* flag;
+    KKM_TRY(ws.alloc(&flag, 1));
+    KKM_CK(cudaMemsetAsync(flag, 0, 4, st));
+    KKM_RUN("check_finite", st, launch_check_finite(X, M * d, flag, st));
+    int bad = 0;
+    KKM_CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    if (bad) return invalid("X holds NaN or Inf");
+  }
+  int32_t* lab = nullptr;
+  float* dist = nullptr;
+  const bool lab_host = labels_out && !is_device_ptr(labels_out);
+  const bool dist_host = dist_out && !is_device_ptr(dist_out);
+  if (!labels_out || lab_host) KKM_TRY(ws.alloc(&lab, M)); else lab = labels_out;
+  if (!dist_out || dist_host) KKM_TRY(ws.alloc(&dist, M)); else dist = dist_out;
+
+  const int rows_ref = mode == KKM_ASSIGN_SUPPORTS ? m->nL : C;
+  const int64_t budget_floats = (int64_t)1 << 27;  // 512 MB of kernel values per chunk
+  const int64_t chunk = std::max<int64_t>(1024, std::min<int64_t>(M, budget_floats / std::max(rows_ref, 1)));
+  const int64_t ldm = round_up(std::min(chunk, M), 32);
+  float *Xc, *auxc, *Kb;
+  KKM_TRY(ws.alloc(&Xc, ldm * sp.dp));
+  KKM_TRY(ws.alloc(&auxc, ldm));
+  KKM_TRY(ws.alloc(&Kb, (int64_t)rows_ref * ldm));
+  const float* kself = sp.kind == KKM_LINEAR ? auxc : nullptr;
+  LoopBuffers lb;
+  if (mode == KKM_ASSIGN_SUPPORTS) {
+    KKM_TRY(alloc_loop(ws, m->nL, C, ldm, 1, &lb));
+    Supports& S = lb.S;
+    S.L = m->L_ident;
+    S.nL = m->nL;
+    S.perm = m->perm;
+    S.seg_off = m->seg_off;
+    S.n_j = m->n_j;
+    S.unit_j = m->unit_j;
+    S.unit_kb = m->unit_kb;
+    S.unit_ke = m->unit_ke;
+    S.seg_unit = m->seg_unit;
+    S.n_units = m->n_units;
+    S.col_label = nullptr;
+    lb.I.ghat_in = m->ghat;
+    lb.I.done = nullptr;
+  }
+  for (int64_t c0 = 0; c0 < M; c0 += chunk) {
+    const int n = (int)std::min<int64_t>(chunk, M - c0);
+    KKM_TRY(prep_rows(sp, X, c0, 1, n, Xc, auxc, st));
+    if (mode == KKM_ASSIGN_SUPPORTS) {
+      KKM_TRY(kernel_block(sp, m->sup, m->sup_aux, nullptr, m->nL, Xc, auxc, nullptr, n, Kb, ldm, st));
+      KKM_RUN("fhat_partial", st, launch_fhat_partial(Kb, ldm, n, lb.S, lb.I, st));
+      KKM_RUN("assign", st,
+              launch_assign(ldm, n, lb.S, lb.I, kself, lab + c0, nullptr, dist + c0, nullptr, nullptr, 0,
+                            /*rebuild=*/0, st));
+    } else {
+      KKM_TRY(kernel_block(sp, m->med, m->med_aux, nullptr, C, Xc, auxc, nullptr, n, Kb, ldm, st));
+      KKM_RUN("nearest", st,
+              launch_nearest(Kb, ldm, n, C, kself, sp.kind == KKM_LINEAR ? m->med_aux : nullptr, lab + c0,
+                             dist + c0, st));
+    }
+  }
+  double* omega_d = nullptr;
+  if (omega_out) {
+    double* part;
+    KKM_TRY(ws.alloc(&part, 256));
+    KKM_TRY(ws.alloc(&omega_d, 1));
+    KKM_RUN("sum", st, launch_sum_f32_to_f64(dist, M, part, 256, omega_d, st));
+    KKM_CK(cudaMemcpyAsync(omega_out, omega_d, 8, cudaMemcpyDeviceToHost, st));
+  }
+  if (lab_host) KKM_CK(cudaMemcpyAsync(labels_out, lab, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
+  if (dist_host) KKM_CK(cudaMemcpyAsync(dist_out, dist, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  prof_collect();
+  return KKM_OK;
+}
+
+// ======================================================================
+// kkm_kernel_matrix
+// ======================================================================
+static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float* B_in, int64_t nB, int64_t d,
+                                     const kkm_kernel* k, float* out, cudaStream_t st) {
+  KernelSpec sp;
+  KKM_TRY(make_spec(k, d, &sp));
+  if (nA < 0 || nB < 0 || nA > INT32_MAX || nB > INT32_MAX) return invalid("bad sizes");
+  if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
+  if (nA == 0 || nB == 0) return KKM_OK;
+  if (!A_in || !B_in || !out) return invalid("NULL pointer");
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  setup_pool_once(dev);
+  Workspace ws(st);
+  const float *A, *Bm;
+  KKM_TRY(device_input(ws, A_in, nA * d, &A));
+  KKM_TRY(device_input(ws, B_in, nB * d, &Bm));
+  float *Ap, *Bp, *aA, *aB, *o;
+  KKM_TRY(ws.alloc(&Ap, nA * sp.dp));
+  KKM_TRY(ws.alloc(&Bp, nB * sp.dp));
+  KKM_TRY(ws.alloc(&aA, nA));
+  KKM_TRY(ws.alloc(&aB, nB));
+  const bool host_out = !is_device_ptr(out);
+  if (host_out) KKM_TRY(ws.alloc(&o, nA * nB)); else o = out;
+  KKM_TRY(prep_rows(sp, A, 0, 1, nA, Ap, aA, st));
+  KKM_TRY(prep_rows(sp, Bm, 0, 1, nB, Bp, aB, st));
+  KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
+  if (host_out) KKM_CK(cudaMemcpyAsync(out, o, (size_t)nA * nB * 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  prof_collect();
+  return KKM_OK;
+}
+
+// ======================================================================
+// kkm_debug_step (teacher-forced inner iteration)
+// ======================================================================
+static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, const int32_t* L, int32_t nL,
+                                  const kkm_kernel* k, int32_t C, const int32_t* u_in, int32_t* u_out,
+                                  float* fhat_out, float* margin_out, double* ghat_out, int32_t* n_out,
+                                  double* omega_out, int32_t* changed_out, cudaStream_t st) {
+  KernelSpec sp;
+  KKM_TRY(make_spec(k, d, &sp));
+  if (Ni < 1 || Ni > INT32_MAX) return invalid("Ni must be >= 1");
+  if (C < 1 || C > kMaxC) return invalid("C must be in [1, 256]");
+  if (nL < 1 || nL > Ni || !L || !u_in || !Xb_in) return invalid("bad landmarks or NULL pointer");
+  if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
+  for (int q = 0; q < nL; ++q)
+    if (L[q] < 0 || L[q] >= Ni || (q > 0 && L[q] <= L[q - 1])) return invalid("L must be sorted, in [0, Ni)");
+  for (int64_t q = 0; q < Ni; ++q)
+    if (u_in[q] < 0 || u_in[q] >= C) return invalid("labels must be in [0, C)");
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  setup_pool_once(dev);
+  Workspace ws(st);
+  const float* X;
+  KKM_TRY(device_input(ws, Xb_in, Ni * d, &X));
+  const int64_t ldk = round_up(Ni, 32);
+  float *Xi, *aux, *XL, *auxL, *KT, *fh, *mg;
+  int64_t *gid, *gidL;
+  int32_t *Ld, *u;
+  double* gh;
+  KKM_TRY(ws.alloc(&Xi, Ni * sp.dp));
+  KKM_TRY(ws.alloc(&aux, Ni));
+  KKM_TRY(ws.alloc(&gid, Ni));
+  KKM_TRY(ws.alloc(&XL, (int64_t)nL * sp.dp));
+  KKM_TRY(ws.alloc(&auxL, nL));
+  KKM_TRY(ws.alloc(&gidL, nL));
+  KKM_TRY(ws.alloc(&KT, (int64_t)nL * ldk));
+  KKM_TRY(ws.alloc(&Ld, nL));
+  KKM_TRY(ws.alloc(&u, Ni));
+  KKM_TRY(ws.alloc(&fh, Ni * C));
+  KKM_TRY(ws.alloc(&mg, Ni));
+  KKM_TRY(ws.alloc(&gh, C));
+  KKM_CK(cudaMemcpyAsync(Ld, L, (size_t)nL * 4, cudaMemcpyHostToDevice, st));
+  KKM_CK(cudaMemcpyAsync(u, u_in, (size_t)Ni * 4, cudaMemcpyHostToDevice, st));
+  KKM_TRY(prep_rows(sp, X, 0, 1, Ni, Xi, aux, st));
+  iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, 0, 1, Ni);
+  KKM_LAUNCH_CK();
+  KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));
+  gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL);
+  KKM_LAUNCH_CK();
+  KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux, gid, Ni, KT, ldk, st));
+  LoopBuffers lb;
+  KKM_TRY(alloc_loop(ws, nL, C, ldk, 1, &lb));
+  lb.S.L = Ld;
+  lb.S.nL = nL;
+  KKM_RUN("fill", st, launch_fill_i32(lb.S.col_label, -1, ldk, st));
+  KKM_RUN("build_supports", st, launch_build_supports(lb.S, u, st));
+  KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
+  const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
+  KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
+  KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st));
+  if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
+  if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));
+  if (margin_out) KKM_CK(cudaMemcpyAsync(margin_out, mg, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
+  if (ghat_out) KKM_CK(cudaMemcpyAsync(ghat_out, gh, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+  if (n_out) KKM_CK(cudaMemcpyAsync(n_out, lb.n_copy, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
+  if (omega_out) KKM_CK(cudaMemcpyAsync(omega_out, lb.I.trace_omega, 8, cudaMemcpyDeviceToHost, st));
+  if (changed_out) KKM_CK(cudaMemcpyAsync(changed_out, lb.I.trace_changed, 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  prof_collect();
+  return KKM_OK;
+}
+
+static kkm_status debug_kmeanspp_impl(const float* X0_in, int64_t N0, int64_t d, const kkm_kernel* k, int32_t C,
+                                      uint64_t seed, int64_t* picks_out, cudaStream_t st) {
+  KernelSpec sp;
+  KKM_TRY(make_spec(k, d, &sp));
+  if (N0 < 1 || N0 > INT32_MAX || C < 1 || C > N0 || C > kMaxC || !X0_in || !picks_out)
+    return invalid("bad sizes or NULL pointer");
+  if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
+  SplitMix64 master(seed);
+  SplitMix64 kpp(master.next());
+  std::vector<double> draws(C);
+  for (int r = 0; r < C; ++r) draws[r] = kpp.u01();
+  const int32_t p0 = (int32_t)floor(draws[0] * (double)N0);
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  setup_pool_once(dev);
+  Workspace ws(st);
+  const float* X;
+  KKM_TRY(device_input(ws, X0_in, N0 * d, &X));
+  const int64_t ldk = round_up(N0, 32);
+  float *Xi, *aux, *rowbuf, *rowaux, *kcol;
+  double *D2, *draws_d;
+  int32_t* picks;
+  KKM_TRY(ws.alloc(&Xi, N0 * sp.dp));
+  KKM_TRY(ws.alloc(&aux, N0));
+  KKM_TRY(ws.alloc(&rowbuf, sp.dp));
+  KKM_TRY(ws.alloc(&rowaux, 1));
+  KKM_TRY(ws.alloc(&kcol, ldk));
+  KKM_TRY(ws.alloc(&D2, N0));
+  KKM_TRY(ws.alloc(&draws_d, C));
+  KKM_TRY(ws.alloc(&picks, C));
+  KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
+  KKM_CK(cudaMemcpyAsync(picks, &p0, 4, cudaMemcpyHostToDevice, st));
+  KKM_TRY(prep_rows(sp, X, 0, 1, N0, Xi, aux, st));
+  KKM_TRY(kmeanspp_dev(sp, Xi, aux, (int)N0, C, sp.kind == KKM_LINEAR ? aux : nullptr, rowbuf, rowaux, kcol,
+                       ldk, D2, picks, draws_d, st));
+  std::vector<int32_t> ph(C);
+  KKM_CK(cudaMemcpyAsync(ph.data(), picks, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < C; ++r) picks_out[r] = ph[r];
+  prof_collect();
+  return KKM_OK;
+}
+
+template <typename F>
+static kkm_status guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return KKM_ENOMEM;
+  } catch (...) {
+    set_error("internal exception");
+    return KKM_EINTERNAL;
+  }
+}
+
+}  // namespace kkm
+
+// ======================================================================
+// extern "C"
+// ======================================================================
+using namespace kkm;
+
+extern "C" {
+
+void kkm_options_default(kkm_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->precision = KKM_FP32;
+  opt->sampling = KKM_STRIDE;
+  opt->early_stop = 1;
+}
+
+kkm_status kkm_fit(const float* X, int64_t N, int64_t d, int32_t C, int32_t B, double s, const kkm_kernel* k,
+                   int32_t iters, uint64_t seed, const kkm_options* opt, int32_t* labels_out,
+                   kkm_model** model_out) {
+  set_error("");
+  if (model_out) *model_out = nullptr;
+  kkm_status r = guarded([&] { return fit_impl(X, N, d, C, B, s, k, iters, seed, opt, labels_out, model_out); });
+  if (r != KKM_OK && model_out && *model_out) {
+    delete *model_out;
+    *model_out = nullptr;
+  }
+  return r;
+}
+
+kkm_status kkm_assign(const kkm_model* m, const float* Xnew, int64_t M, int32_t mode, int32_t* labels_out,
+                      float* dist_out, void* stream) {
+  set_error("");
+  if (!labels_out) return invalid("labels_out is NULL");
+  return guarded([&] { return assign_impl(m, Xnew, M, mode, labels_out, dist_out, nullptr, (cudaStream_t)stream); });
+}
+
+kkm_status kkm_cost(const kkm_model* m, const float* X, int64_t N, int32_t mode, double* omega_out, void* stream) {
+  set_error("");
+  if (!omega_out) return invalid("omega_out is NULL");
+  return guarded([&] { return assign_impl(m, X, N, mode, nullptr, nullptr, omega_out, (cudaStream_t)stream); });
+}
+
+kkm_status kkm_model_info(const kkm_model* m, int32_t* C, int64_t* d, int32_t* n_support, float* sigma) {
+  if (!m) return invalid("model is NULL");
+  if (C) *C = m->C;
+  if (d) *d = m->d;
+  if (n_support) *n_support = m->nL;
+  if (sigma) *sigma = m->sigma;
+  return KKM_OK;
+}
+
+kkm_status kkm_model_medoids(const kkm_model* m, int64_t* idx_out, int64_t* counts_out, float* coords_out) {
+  if (!m) return invalid("model is NULL");
+  if (idx_out) memcpy(idx_out, m->medoids.data(), m->medoids.size() * 8);
+  if (counts_out) memcpy(counts_out, m->W.data(), m->W.size() * 8);
+  if (coords_out) {
+    cudaError_t e = cudaMemcpy(coords_out, m->med_coords_h.data(), m->med_coords_h.size() * 4, cudaMemcpyDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);
+  }
+  return KKM_OK;
+}
+
+kkm_status kkm_model_supports(const kkm_model* m, int32_t* labels_out, double* ghat_out, int32_t* n_out) {
+  if (!m) return invalid("model is NULL");
+  if (labels_out) memcpy(labels_out, m->sup_labels_h.data(), m->sup_labels_h.size() * 4);
+  if (ghat_out) memcpy(ghat_out, m->ghat_h.data(), m->ghat_h.size() * 8);
+  if (n_out) memcpy(n_out, m->n_h.data(), m->n_h.size() * 4);
+  return KKM_OK;
+}
+
+kkm_status kkm_model_trace(const kkm_model* m, double* omega, int32_t* changed, int32_t cap, int32_t* n_out) {
+  if (!m) return invalid("model is NULL");
+  const int32_t n = (int32_t)m->omega.size();
+  if (n_out) *n_out = n;
+  const int32_t c = std::min(n, std::max(cap, 0));
+  if (omega) memcpy(omega, m->omega.data(), (size_t)c * 8);
+  if (changed) memcpy(changed, m->changed.data(), (size_t)c * 4);
+  return KKM_OK;
+}
+
+void kkm_model_free(kkm_model* m) { delete m; }
+
+kkm_status kkm_kernel_matrix(const float* A, int64_t nA, const float* Bm, int64_t nB, int64_t d, const kkm_kernel* k,
+                             float* out, void* stream) {
+  set_error("");
+  return guarded([&] { return kernel_matrix_impl(A, nA, Bm, nB, d, k, out, (cudaStream_t)stream); });
+}
+
+kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d, const kkm_kernel* k, uint64_t seed,
+                                float* sigma_out) {
+  set_error("");
+  return guarded([&]() -> kkm_status {
+    KernelSpec sp;
+    KKM_TRY(make_spec(k, d, &sp));
+    if (N < 1 || N > INT32_MAX || !X || !sigma_out) return invalid("bad sizes or NULL pointer");
+    SplitMix64 master(seed);
+    master.next();
+    const uint64_t bw_seed = master.next();
+    int dev = 0;
+    KKM_CK(cudaGetDevice(&dev));
+    setup_pool_once(dev);
+    Workspace ws(nullptr);
+    const float* Xd;
+    KKM_TRY(device_input(ws, X, N * d, &Xd));
+    KKM_TRY(median_bandwidth_dev(sp, Xd, N, bw_seed, ws, sigma_out));
+    prof_collect();
+    return KKM_OK;
+  });
+}
+
+kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d, const int32_t* L, int32_t nL, const kkm_kernel* k,
+                          int32_t C, const int32_t* u_in, int32_t* u_out, float* fhat_out, float* margin_out,
+                          double* ghat_out, int32_t* n_out, double* omega_out, int32_t* changed_out,
+                          void* stream) {
+  set_error("");
+  return guarded([&] {
+    return debug_step_impl(Xb, Ni, d, L, nL, k, C, u_in, u_out, fhat_out, margin_out, ghat_out, n_out, omega_out,
+                           changed_out, (cudaStream_t)stream);
+  });
+}
+
+kkm_status kkm_debug_kmeanspp(const float* X0, int64_t N0, int64_t d, const kkm_kernel* k, int32_t C, uint64_t seed,
+                              int64_t* picks_out, void* stream) {
+  set_error("");
+  return guarded([&] { return debug_kmeanspp_impl(X0, N0, d, k, C, seed, picks_out, (cudaStream_t)stream); });
+}
+
+kkm_status kkm_minibatch_plan(int64_t N, int32_t B, int32_t sampling, double s, uint64_t seed, int32_t batch,
+                              int64_t* start_out, int64_t* step_out, int64_t* n_out, int32_t* L_out,
+                              int64_t* nl_out) {
+  set_error("");
+  return guarded([&]() -> kkm_status {
+    if (N < 1 || B < 1 || B > N || batch < 0 || batch >= B) return invalid("bad N, B or batch");
+    if (sampling != KKM_STRIDE && sampling != KKM_BLOCK) return invalid("unknown sampling");
+    if (!(s > 0.0 && s <= 1.0)) return invalid("s must be in (0, 1]");
+    const std::vector<BatchGeom> geo = batch_geometry(N, B, sampling);
+    const BatchGeom& g = geo[batch];
+    if (start_out) *start_out = g.start;
+    if (step_out) *step_out = g.step;
+    if (n_out) *n_out = g.Ni;
+    SplitMix64 master(seed);
+    master.next();
+    master.next();
+    uint64_t lm_seed = 0;
+    for (int i = 0; i <= batch; ++i) lm_seed = master.next();
+    SplitMix64 lm(lm_seed);
+    const int64_t nl = n_landmarks(g.Ni, s);
+    if (nl_out) *nl_out = nl;
+    if (L_out) {
+      if (nl == g.Ni) {
+        for (int64_t a = 0; a < nl; ++a) L_out[a] = (int32_t)a;
+      } else {
+        std::vector<int64_t> p = partial_shuffle(g.Ni, nl, lm);
+        std::sort(p.begin(), p.end());
+        for (int64_t a = 0; a < nl; ++a) L_out[a] = (int32_t)p[(size_t)a];
+      }
+    }
+    return KKM_OK;
+  });
+}
+
+const char* kkm_status_string(kkm_status s) {
+  switch (s) {
+    case KKM_OK: return "KKM_OK";
+    case KKM_EINVAL: return "KKM_EINVAL";
+    case KKM_ENOMEM: return "KKM_ENOMEM";
+    case KKM_EBUDGET: return "KKM_EBUDGET";
+    case KKM_ECUDA: return "KKM_ECUDA";
+    case KKM_ETIMEOUT: return "KKM_ETIMEOUT";
+    case KKM_EINTERNAL: return "KKM_EINTERNAL";
+  }
+  return "KKM_UNKNOWN";
+}
+
+const char* kkm_last_error(void) { return g_last_error.c_str(); }
+
+void kkm_prof_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+}
+void kkm_prof_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.clear();
+}
+int32_t kkm_prof_read(const char* name, int64_t* launches, double* ms) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto it = g_prof.find(name ? name : "");
+  if (it == g_prof.end()) {
+    if (launches) *launches = 0;
+    if (ms) *ms = 0.0;
+    return 0;
+  }
+  if (launches) *launches = it->second.launches;
+  if (ms) *ms = it->second.ms;
+  return 1;
+}
+int32_t kkm_prof_names(char* buf, int32_t cap) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  std::string all;
+  for (auto& kv : g_prof) {
+    if (!all.empty()) all += ",";
+    all += kv.first;
+  }
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>(all.size(), (size_t)cap - 1);
+    memcpy(buf, all.data(), n);
+    buf[n] = 0;
+  }
+  return (int32_t)all.size();
+}
+
+}  // extern "C"

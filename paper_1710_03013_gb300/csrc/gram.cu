@@ -1,0 +1,277 @@
+// Kernel-block evaluation for feature vectors (Alg. 1 line 3, Section 3.2):
+// out[a][b] = kappa(A_a, B_b) with kappa the Gaussian RBF, the linear kernel
+// or the plain Euclidean distance (for the bandwidth rule).
+//
+// The contraction A.B^T runs as an FP32 FFMA register-tiled product (128x128
+// CTA tile, 8x8 outputs per thread, double-buffered shared memory) and the
+// epilogue forms ||a||^2 + ||b||^2 - 2 a.b, clamps it at 0 and applies the
+// exponential.  Squared norms are accumulated in FP64 once per row by the
+// gather kernels.  A "skinny" kernel covers <= 32 reference rows (medoid
+// columns, k-means++ columns) with one warp per sample row.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace kkm {
+
+// ------------------------------------------------------------------ gathers
+__global__ void gather_rows_kernel(const float* __restrict__ X, int64_t d, int64_t start,
+                                   int64_t step, int64_t n, float* __restrict__ out, int dp,
+                                   float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float* src = X + (start + row * step) * d;
+  float* dst = out + row * (int64_t)dp;
+  double acc = 0.0;
+  for (int c = lane; c < dp; c += 32) {
+    float v = c < d ? src[c] : 0.0f;
+    dst[c] = v;
+    acc += (double)v * (double)v;
+  }
+  acc = warp_sum_f64(acc);
+  if (normsq && lane == 0) normsq[row] = (float)acc;
+}
+
+template <typename IDX>
+__global__ void gather_idx_kernel(const float* __restrict__ X, int64_t ld_in, int64_t d,
+                                  const IDX* __restrict__ idx, int64_t n, float* __restrict__ out,
+                                  int dp, float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const int64_t g = (int64_t)idx[row];
+  const float* src = X + g * ld_in;
+  float* dst = out + row * (int64_t)dp;
+  double acc = 0.0;
+  for (int c = lane; c < dp; c += 32) {
+    float v = c < d ? src[c] : 0.0f;
+    dst[c] = v;
+    acc += (double)v * (double)v;
+  }
+  acc = warp_sum_f64(acc);
+  if (normsq && lane == 0) normsq[row] = (float)acc;
+}
+
+cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step, int64_t n,
+                               float* out, int dp, float* normsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  gather_rows_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, start, step, n, out, dp, normsq);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_idx64(const float* X, int64_t d, const int64_t* idx, int64_t n,
+                                float* out, int dp, float* normsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  gather_idx_kernel<int64_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, d, idx, n, out, dp, normsq);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_idx32(const float* Xp, int dp_in, const int32_t* idx, int64_t n,
+                                float* out, int dp, float* normsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  gather_idx_kernel<int32_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(Xp, dp_in, dp_in, idx, n, out, dp,
+                                                                    normsq);
+  return cudaGetLastError();
+}
+
+__global__ void check_finite_kernel(const float* __restrict__ X, int64_t n, int* flag) {
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(X[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int grid = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+  check_finite_kernel<<<grid, 256, 0, st>>>(X, n, flag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- epilogue
+template <int KIND>
+__device__ __forceinline__ float gram_epilogue(float dot, float na, float nb, bool same,
+                                               float neg_scale) {
+  if (KIND == DK_LINEAR) return dot;
+  float d2 = fmaxf(na + nb - 2.0f * dot, 0.0f);
+  if (KIND == DK_DIST) return same ? 0.0f : sqrtf(d2);
+  return same ? 1.0f : exp2f(d2 * neg_scale);
+}
+
+// ------------------------------------------------------- tiled FP32 product
+constexpr int TB_M = 128, TB_N = 128, TB_K = 8;
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 2)
+gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
+                  int dp, const float* __restrict__ normA, const float* __restrict__ normB,
+                  const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
+                  float neg_scale, float* __restrict__ out, int64_t ldo, int vec_ok) {
+  __shared__ __align__(16) float As[2][TB_K][TB_M];
+  __shared__ __align__(16) float Bs[2][TB_K][TB_N];
+  const int tid = threadIdx.x;
+  const int a0 = blockIdx.y * TB_M, b0 = blockIdx.x * TB_N;
+  const int lr = tid >> 1, lk = (tid & 1) << 2;
+  // Rows past the end re-read the last valid row; their outputs are dropped.
+  const float* pa = A + (int64_t)min(a0 + lr, nA - 1) * dp + lk;
+  const float* pb = Bm + (int64_t)min(b0 + lr, nB - 1) * dp + lk;
+  float4 ga = __ldg(reinterpret_cast<const float4*>(pa));
+  float4 gb = __ldg(reinterpret_cast<const float4*>(pb));
+  As[0][lk + 0][lr] = ga.x; As[0][lk + 1][lr] = ga.y; As[0][lk + 2][lr] = ga.z; As[0][lk + 3][lr] = ga.w;
+  Bs[0][lk + 0][lr] = gb.x; Bs[0][lk + 1][lr] = gb.y; Bs[0][lk + 2][lr] = gb.z; Bs[0][lk + 3][lr] = gb.w;
+  __syncthreads();
+
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+  const int nk = dp / TB_K;
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) {
+      ga = __ldg(reinterpret_cast<const float4*>(pa + (kt + 1) * TB_K));
+      gb = __ldg(reinterpret_cast<const float4*>(pb + (kt + 1) * TB_K));
+    }
+#pragma unroll
+    for (int k = 0; k < TB_K; ++k) {
+      const float4 al = *reinterpret_cast<const float4*>(&As[cur][k][ty * 4]);
+      const float4 ah = *reinterpret_cast<const float4*>(&As[cur][k][64 + ty * 4]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bs[cur][k][tx * 4]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bs[cur][k][64 + tx * 4]);
+      const float a[8] = {al.x, al.y, al.z, al.w, ah.x, ah.y, ah.z, ah.w};
+      const float b[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (kt + 1 < nk) {
+      const int nx = cur ^ 1;
+      As[nx][lk + 0][lr] = ga.x; As[nx][lk + 1][lr] = ga.y; As[nx][lk + 2][lr] = ga.z; As[nx][lk + 3][lr] = ga.w;
+      Bs[nx][lk + 0][lr] = gb.x; Bs[nx][lk + 1][lr] = gb.y; Bs[nx][lk + 2][lr] = gb.z; Bs[nx][lk + 3][lr] = gb.w;
+    }
+    __syncthreads();
+  }
+
+  // Epilogue: rows a0 + {ty*4+i, 64+ty*4+i}, columns b0 + {tx*4+j, 64+tx*4+j}.
+  float nb[8];
+  int64_t ib[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int b = b0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+    nb[j] = (KIND != DK_LINEAR && b < nB) ? normB[b] : 0.0f;
+    ib[j] = (idB && b < nB) ? idB[b] : -1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int a = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (a >= nA) continue;
+    const float na = KIND != DK_LINEAR ? normA[a] : 0.0f;
+    const int64_t ia = idA ? idA[a] : -2;
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = gram_epilogue<KIND>(acc[i][j], na, nb[j], ia == ib[j], neg_scale);
+    float* orow = out + (int64_t)a * ldo;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int b = b0 + h * 64 + tx * 4;
+      if (vec_ok && b + 3 < nB) {
+        *reinterpret_cast<float4*>(orow + b) = make_float4(v[h * 4], v[h * 4 + 1], v[h * 4 + 2], v[h * 4 + 3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (b + q < nB) orow[b + q] = v[h * 4 + q];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------ skinny (<= 32 reference rows)
+template <int KIND, int NA>
+__global__ void __launch_bounds__(256)
+gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
+                   int dp, const float* __restrict__ normA, const float* __restrict__ normB,
+                   const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
+                   float neg_scale, float* __restrict__ out, int64_t ldo) {
+  extern __shared__ float4 As4[];  // [nA][dp/4]
+  const int dq = dp >> 2;
+  const float4* A4 = reinterpret_cast<const float4*>(A);
+  for (int e = threadIdx.x; e < nA * dq; e += blockDim.x) As4[e] = A4[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= nB) return;
+  float acc[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
+  const float4* pb = reinterpret_cast<const float4*>(Bm + (int64_t)b * dp);
+  for (int q = lane; q < dq; q += 32) {
+    const float4 x = __ldg(pb + q);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      if (a < nA) {
+        const float4 y = As4[a * dq + q];
+        acc[a] = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc[a]))));
+      }
+    }
+  }
+  float mine = 0.0f;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    const float t = warp_sum_f32(acc[a]);
+    if (lane == a) mine = t;
+  }
+  if (lane < nA) {
+    const float na = KIND != DK_LINEAR ? normA[lane] : 0.0f;
+    const float nbv = KIND != DK_LINEAR ? normB[b] : 0.0f;
+    const bool same = idA && idB && idA[lane] == idB[b];
+    out[(int64_t)lane * ldo + b] = gram_epilogue<KIND>(mine, na, nbv, same, neg_scale);
+  }
+}
+
+template <int KIND>
+static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, int64_t nB, int dp,
+                                 const float* normA, const float* normB, const int64_t* idA,
+                                 const int64_t* idB, float neg_scale, float* out, int64_t ldo,
+                                 cudaStream_t st) {
+  const size_t skinny_smem = (size_t)nA * dp * sizeof(float);
+  if (nA <= 32 && skinny_smem <= 96 * 1024) {
+    const int grid = (int)ceil_div(nB, 8);
+    cudaError_t e;
+#define KKM_SKINNY(NAV)                                                                 \
+  e = cudaFuncSetAttribute(gram_skinny_kernel<KIND, NAV>,                               \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);     \
+  if (e != cudaSuccess) return e;                                                       \
+  gram_skinny_kernel<KIND, NAV><<<grid, 256, skinny_smem, st>>>(                        \
+      A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB, neg_scale, out, ldo);
+    if (nA <= 1) { KKM_SKINNY(1) }
+    else if (nA <= 4) { KKM_SKINNY(4) }
+    else if (nA <= 16) { KKM_SKINNY(16) }
+    else { KKM_SKINNY(32) }
+#undef KKM_SKINNY
+    return cudaGetLastError();
+  }
+  dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  gram_tiled_kernel<KIND><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
+                                                neg_scale, out, ldo, vec_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB, int dp,
+                        const float* normA, const float* normB, const int64_t* idA,
+                        const int64_t* idB, float neg_scale, float* out, int64_t ldo,
+                        cudaStream_t st) {
+  if (nA <= 0 || nB <= 0) return cudaSuccess;
+  switch (kind) {
+    case DK_RBF:
+      return gram_dispatch<DK_RBF>(A, nA, Bm, nB, dp, normA, normB, idA, idB, neg_scale, out, ldo, st);
+    case DK_LINEAR:
+      return gram_dispatch<DK_LINEAR>(A, nA, Bm, nB, dp, normA, normB, idA, idB, neg_scale, out, ldo, st);
+    default:
+      return gram_dispatch<DK_DIST>(A, nA, Bm, nB, dp, normA, normB, idA, idB, neg_scale, out, ldo, st);
+  }
+}
+
+}  // namespace kkm

@@ -1,0 +1,179 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kkm.h"
+
+namespace kkm {
+
+// ---------------------------------------------------------------- errors ---
+void set_error(const std::string& msg);
+kkm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define KKM_CK(expr)                                                        \
+  do {                                                                      \
+    cudaError_t _e = (expr);                                                \
+    if (_e != cudaSuccess) return ::kkm::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define KKM_TRY(expr)                      \
+  do {                                     \
+    kkm_status _s = (expr);                \
+    if (_s != KKM_OK) return _s;           \
+  } while (0)
+
+// ------------------------------------------------------------- profiling ---
+// Brackets one kernel launch with events when profiling is on.
+struct ProfScope {
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+  int slot;
+  cudaStream_t stream;
+};
+void prof_collect();  // after a stream sync: fold finished events into totals
+
+// Launch check after every kernel launch.
+#define KKM_LAUNCH_CK() KKM_CK(cudaGetLastError())
+
+// --------------------------------------------------------------- layouts ---
+constexpr int kUnitRows = 64;     // landmark rows per f_hat streaming unit
+constexpr int kStripCols = 512;   // sample columns per streaming CTA (128 x float4)
+constexpr int kMaxC = 256;     // clusters per problem (one scan slot per thread of a 256-thread CTA)
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Kernel-function codes used on the device.
+enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2 };
+
+// --------------------------------------------------------- kernel launchers
+// (all asynchronous on `st`; they return a CUDA error code of the launch)
+
+// Rows of X chosen as start + l*step (l < n) copied to out [n][dp], zero-padded,
+// with FP64-accumulated squared norms (normsq nullable).
+cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step,
+                               int64_t n, float* out, int dp, float* normsq, cudaStream_t st);
+// Rows X[idx[l]] (device indices, int64 or int32) copied like above.
+cudaError_t launch_gather_idx64(const float* X, int64_t d, const int64_t* idx, int64_t n,
+                                float* out, int dp, float* normsq, cudaStream_t st);
+cudaError_t launch_gather_idx32(const float* Xp, int dp_in, const int32_t* idx, int64_t n,
+                                float* out, int dp, float* normsq, cudaStream_t st);
+// Sets *flag = 1 if any of the n floats is NaN or Inf.
+cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream_t st);
+
+// out[a*ldo + b] = kappa(A_a, B_b) for a < nA, b < nB (A [nA][dp], B [nB][dp]).
+// kind: DK_RBF (neg_scale = -log2(e)/(2 sigma^2)), DK_LINEAR, DK_DIST (sqrt of
+// squared distance).  idA/idB (nullable) are sample ids: equal ids give K = 1
+// exactly for RBF and 0 for DIST.
+cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB,
+                        int dp, const float* normA, const float* normB, const int64_t* idA,
+                        const int64_t* idB, float neg_scale, float* out, int64_t ldo,
+                        cudaStream_t st);
+
+// ---- MD kernel (RMSD) -----------------------------------------------------
+// Frames [n][n_atoms][3] (rows start + l*step of X) -> centred SoA [n][3][ap]
+// (ap = padded atom count) with G = sum |x_a|^2 in gsq.
+cudaError_t launch_rmsd_prep_rows(const float* X, int n_atoms, int64_t start, int64_t step,
+                                  int64_t n, float* out, int ap, float* gsq, cudaStream_t st);
+cudaError_t launch_rmsd_prep_idx64(const float* X, int n_atoms, const int64_t* idx, int64_t n,
+                                   float* out, int ap, float* gsq, cudaStream_t st);
+// kind DK_RBF: out = exp(-rmsd^2/(2 sigma^2)) via neg_scale; DK_DIST: rmsd.
+cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB,
+                             int ap, int n_atoms, const float* gA, const float* gB,
+                             const int64_t* idA, const int64_t* idB, float neg_scale,
+                             float* out, int64_t ldo, cudaStream_t st);
+
+// ---- inner iteration ---------------------------------------------------------
+struct Supports {
+  // landmark structure of one mini-batch, all device memory
+  const int32_t* L;      // [nL] local positions of landmarks (sorted)
+  int nL;
+  int C;
+  int32_t* perm;         // [nL] landmark ordinals k sorted by label (stable)
+  int32_t* seg_off;      // [C+1]
+  int32_t* n_j;          // [C]
+  int32_t* unit_j;       // [max_units]
+  int32_t* unit_kb;      // [max_units]
+  int32_t* unit_ke;      // [max_units]
+  int32_t* seg_unit;     // [C+1] first unit of each segment
+  int32_t* n_units;      // [1]
+  int32_t* col_label;    // [ldk] label of the landmark in column i, else -1;
+                         // NULL: no g_hat numerators are needed
+  int max_units;
+};
+inline int max_units_for(int nL, int C) { return (int)(ceil_div(nL, kUnitRows) + C); }
+
+struct IterState {
+  float* partial;        // [max_units][ldk]
+  double* gpart;         // [max_units][n_strips]
+  double* omega_part;    // [assign grid]
+  int32_t* changed_part; // [assign grid]
+  uint32_t* ticket;      // [1], zero between launches
+  int32_t* done;         // [1] early-stop flag (device)
+  double* trace_omega;   // [trace cap]
+  int32_t* trace_changed;// [trace cap]
+  int32_t* trace_count;  // [1]
+  const double* ghat_in = nullptr;  // g_hat given (assign against a model), else from gpart
+  int assign_grid;
+  int n_strips;
+};
+
+// Builds perm/seg/units/col_label from u (one CTA).
+cudaError_t launch_build_supports(const Supports& S, const int32_t* u, cudaStream_t st);
+// Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
+cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
+                                const IterState& I, cudaStream_t st);
+// g_hat, f_hat, distances, argmin, margin, Omega; updates u in place.  With
+// rebuild != 0 the last CTA also writes the trace entry, the early-stop flag
+// and rebuilds the supports for the next iteration.
+cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                          const float* kself, int32_t* u, float* margin, float* dmin,
+                          float* fhat_out, double* ghat_out, int early_stop, int rebuild,
+                          cudaStream_t st);
+
+// ---- mini-batch boundary -----------------------------------------------------
+// Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).
+cudaError_t launch_nearest(const float* Kt, int64_t ldk, int Ni, int C, const float* kself,
+                           const float* kmm, int32_t* u, float* dmin, cudaStream_t st);
+// Eq. 10 keys and member counts c_j (keys/c must be reset by the caller).
+cudaError_t launch_medoid_keys(int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                               const float* kself, const int32_t* u, unsigned long long* keys,
+                               int32_t* c, double* ghat_out, cudaStream_t st);
+// mi[j] = local index of the Eq. 10 medoid, or -1 when empty.
+cudaError_t launch_medoid_pick(const unsigned long long* keys, const int32_t* c,
+                               const int32_t* n_j, int C, int32_t* mi, cudaStream_t st);
+// Eq. 12 keys.
+cudaError_t launch_merge_keys(const float* Kt, const float* Kmi, int64_t ldk, int Ni, int C,
+                              const float* kself, const int32_t* mi, const int32_t* c,
+                              const int64_t* W, unsigned long long* keys, cudaStream_t st);
+// Applies the merge: M[j] = start + l*step for non-empty j, W += c.
+cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi,
+                               const int32_t* c, int C, int64_t start, int64_t step,
+                               int64_t* M, int64_t* W, cudaStream_t st);
+// labels_out[start + l*step] = u[l]
+cudaError_t launch_scatter_labels(const int32_t* u, int Ni, int64_t start, int64_t step,
+                                  int32_t* labels_out, cudaStream_t st);
+cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, int n, cudaStream_t st);
+cudaError_t launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
+cudaError_t launch_fill_f32(float* p, float v, int64_t n, cudaStream_t st);
+// kernel k-means++ round r (1..C-1): D2 update with column Kc and the next pick.
+cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2,
+                             int32_t* picks, const double* draws, int r, cudaStream_t st);
+// picks (local) -> global ids start + p*step
+cudaError_t launch_local_to_global(const int32_t* picks, int C, int64_t start, int64_t step,
+                                   int64_t* M, cudaStream_t st);
+// sum of n doubles in a fixed order into *out (device)
+cudaError_t launch_sum_f32_to_f64(const float* v, int64_t n, double* part, int parts,
+                                  double* out, cudaStream_t st);
+
+// ---- bandwidth ----------------------------------------------------------------
+// k-th smallest (0-based) of the upper-triangle entries of D [M][ld] (j > i),
+// written to *out (device); scratch >= 4 KB.
+cudaError_t launch_select_upper(const float* D, int M, int64_t ld, int64_t k, uint32_t* scratch,
+                                float* out, cudaStream_t st);
+
+}  // namespace kkm

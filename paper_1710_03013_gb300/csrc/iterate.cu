@@ -1,0 +1,621 @@
+// Inner iteration of the approximate mini-batch kernel k-means (Eq. 15-17)
+// and the mini-batch boundary steps (Eq. 8, 10, 12, kernel k-means++).
+//
+// Layout.  The kernel block of mini-batch i is stored transposed,
+// KT[k][l] = K(x_{L_k}, x_l) for landmark ordinal k < |L| and sample l < N_i,
+// with a row pitch ldk that is a multiple of 32 floats.  Landmarks are kept
+// sorted by label in `perm` (a stable counting sort), so the support S_j of
+// cluster j is the contiguous segment perm[seg_off[j] .. seg_off[j+1]).  The
+// segment is cut into units of at most kUnitRows landmark rows.
+//
+// One iteration is two launches:
+//   fhat_partial  streams KT once (the HBM-bound step): every CTA sums the
+//                 rows of one unit over a 512-column strip with float4 loads
+//                 and writes the partial numerators of f_hat (Eq. 17), plus
+//                 the part of the g_hat numerator (Eq. 16) that falls on
+//                 landmark columns of the same cluster;
+//   assign        adds the partials of each segment in a fixed order, forms
+//                 d_ij = K_ii - 2 f_hat_ij + g_hat_j, takes the argmin (lowest
+//                 j on ties), the margin and the FP64 cost partials, and
+//                 updates the labels in place.  Its last CTA to finish (atomic
+//                 ticket, no waiting) sums the cost in a fixed order, records
+//                 the trace, raises the early-stop flag and rebuilds the
+//                 supports for the next iteration from the new landmark labels.
+// Every sum has a fixed order, so results are bit-reproducible.
+#include <math.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace kkm {
+
+constexpr int kSupThreads = 256;  // build_supports block size (8 warps)
+constexpr int kAssignThreads = 256;
+constexpr int kStreamThreads = kStripCols / 4;
+
+// Exclusive scan of one int per thread over a 256-thread block.
+__device__ __forceinline__ int block_excl_scan_256(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < 8 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < 8) sh[lane] = s;
+  }
+  __syncthreads();
+  const int off = w > 0 ? sh[w - 1] : 0;
+  *total = sh[7];
+  __syncthreads();
+  return off + x - v;
+}
+
+// Rebuilds the support structure of the landmarks from the labels u.  Runs
+// on one whole CTA of kSupThreads threads.  u is read through L2 (it was
+// written by other CTAs of the same launch).
+__device__ void build_supports_block(const Supports& S, const int32_t* u) {
+  __shared__ int cnt[kMaxC];
+  __shared__ int base[kMaxC];
+  __shared__ int wcnt[8 * kMaxC];
+  __shared__ int scan_sh[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int C = S.C, nL = S.nL;
+  for (int j = tid; j < C; j += kSupThreads) cnt[j] = 0;
+  __syncthreads();
+  for (int k = tid; k < nL; k += kSupThreads) {
+    const int l = S.L[k];
+    const int lab = __ldcg(u + l);
+    S.col_label[l] = lab;
+    atomicAdd(&cnt[lab], 1);
+  }
+  __syncthreads();
+  // segment offsets and unit counts (C <= 256: one entry per thread)
+  const int cj = tid < C ? cnt[tid] : 0;
+  int total;
+  const int off = block_excl_scan_256(cj, scan_sh, &total);
+  const int nu = (cj + kUnitRows - 1) / kUnitRows;
+  const int uoff = block_excl_scan_256(nu, scan_sh, &total);
+  if (tid < C) {
+    base[tid] = off;
+    S.seg_off[tid] = off;
+    S.n_j[tid] = cj;
+    S.seg_unit[tid] = uoff;
+    for (int r = 0; r < nu; ++r) {
+      const int un = uoff + r;
+      S.unit_j[un] = tid;
+      S.unit_kb[un] = off + r * kUnitRows;
+      S.unit_ke[un] = min(off + (r + 1) * kUnitRows, off + cj);
+    }
+  }
+  if (tid == 0) {
+    S.seg_off[C] = nL;
+    S.seg_unit[C] = total;
+    *S.n_units = total;
+  }
+  __syncthreads();
+  // stable scatter: chunk by chunk in landmark order
+  for (int start = 0; start < nL; start += kSupThreads) {
+    const int k = start + tid;
+    const int lab = k < nL ? __ldcg(u + S.L[k]) : -1;
+    const unsigned peers = __match_any_sync(kFull, lab);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    for (int e = tid; e < 8 * C; e += kSupThreads) wcnt[e] = 0;
+    __syncthreads();
+    if (lab >= 0 && rank == 0) wcnt[w * C + lab] = __popc(peers);
+    __syncthreads();
+    for (int j = tid; j < C; j += kSupThreads) {
+      int run = base[j];
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) {
+        const int t = wcnt[ww * C + j];
+        wcnt[ww * C + j] = run;
+        run += t;
+      }
+      base[j] = run;
+    }
+    __syncthreads();
+    if (lab >= 0) S.perm[wcnt[w * C + lab] + rank] = k;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSupThreads) build_supports_kernel(Supports S, const int32_t* u) {
+  build_supports_block(S, u);
+}
+
+cudaError_t launch_build_supports(const Supports& S, const int32_t* u, cudaStream_t st) {
+  build_supports_kernel<<<1, kSupThreads, 0, st>>>(S, u);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- f_hat streaming
+__global__ void __launch_bounds__(kStreamThreads)
+fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports S,
+                    float* __restrict__ partial, double* __restrict__ gpart, int n_strips,
+                    const int32_t* __restrict__ skip) {
+  __shared__ double red[kStreamThreads / 32];
+  if (skip && *skip) return;
+  const int unit = blockIdx.y;
+  if (unit >= *S.n_units) return;
+  const int j = S.unit_j[unit], kb = S.unit_kb[unit], ke = S.unit_ke[unit];
+  const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * 4;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (col < Ni) {
+    const float* base = KT + col;
+    int k = kb;
+    for (; k + 8 <= ke; k += 8) {
+      int p[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] = __ldg(S.perm + k + q);
+      float4 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)p[q] * ldk));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
+      }
+    }
+    for (; k < ke; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(base + (int64_t)__ldg(S.perm + k) * ldk));
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    *reinterpret_cast<float4*>(partial + (int64_t)unit * ldk + col) = acc;
+  }
+  // g_hat numerator: landmark columns of the same cluster
+  if (!S.col_label) return;
+  double g = 0.0;
+  if (col < Ni) {
+    const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (col + q < Ni && __ldg(S.col_label + col + q) == j) g += (double)a4[q];
+  }
+  g = block_sum(g, red);
+  if (threadIdx.x == 0) gpart[(int64_t)unit * n_strips + blockIdx.x] = g;
+}
+
+cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
+                                const IterState& I, cudaStream_t st) {
+  dim3 grid((unsigned)I.n_strips, (unsigned)S.max_units);
+  fhat_partial_kernel<<<grid, kStreamThreads, 0, st>>>(KT, ldk, Ni, S, I.partial, I.gpart, I.n_strips,
+                                                       I.done);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ assign
+// Loads n_j, the unit ranges and g_hat (Eq. 16) into shared memory.
+struct AssignShared {
+  double gh[kMaxC];
+  float ghf[kMaxC];
+  int nj[kMaxC];
+  int su[kMaxC + 1];
+};
+
+__device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
+                                                   const double* __restrict__ gpart, int n_strips,
+                                                   const double* __restrict__ ghat_in) {
+  const int C = S.C;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    sh.nj[j] = S.n_j[j];
+    sh.su[j] = S.seg_unit[j];
+  }
+  if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
+  __syncthreads();
+  if (ghat_in) {
+    for (int j = threadIdx.x; j < C; j += blockDim.x) {
+      sh.gh[j] = ghat_in[j];
+      sh.ghf[j] = (float)ghat_in[j];
+    }
+    __syncthreads();
+    return;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = w; j < C; j += nw) {
+    const int64_t e0 = (int64_t)sh.su[j] * n_strips, e1 = (int64_t)sh.su[j + 1] * n_strips;
+    double s = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) s += gpart[e];
+    s = warp_sum_f64(s);
+    if (lane == 0) {
+      const double n = (double)sh.nj[j];
+      const double g = sh.nj[j] > 0 ? s / (n * n) : __longlong_as_double(0x7ff8000000000000LL);
+      sh.gh[j] = g;
+      sh.ghf[j] = (float)g;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __restrict__ partial,
+                                         int64_t ldk, int i, int j) {
+  float f = 0.0f;
+  for (int un = sh.su[j]; un < sh.su[j + 1]; ++un) f += partial[(int64_t)un * ldk + i];
+  return f / (float)sh.nj[j];
+}
+
+__global__ void __launch_bounds__(kAssignThreads)
+assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
+              int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
+              float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
+              int rebuild) {
+  __shared__ AssignShared sh;
+  __shared__ double red_d[kAssignThreads / 32];
+  __shared__ int red_i[kAssignThreads / 32];
+  __shared__ int is_last;
+  if (I.done && *I.done) return;
+  const int C = S.C;
+  load_cluster_stats(sh, S, I.gpart, I.n_strips, I.ghat_in);
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
+
+  double om = 0.0;
+  int ch = 0;
+  const float inf = __int_as_float(0x7f800000);
+  for (int i = blockIdx.x * kAssignThreads + threadIdx.x; i < Ni; i += gridDim.x * kAssignThreads) {
+    const float ks = kself ? kself[i] : 1.0f;
+    float best = inf, second = inf;
+    int bj = 0;
+    for (int j = 0; j < C; ++j) {
+      if (sh.nj[j] == 0) {
+        if (fhat_out) fhat_out[(int64_t)i * C + j] = __int_as_float(0x7fc00000);
+        continue;
+      }
+      const float fh = fhat_of(sh, I.partial, ldk, i, j);
+      if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
+      const float dj = ks - 2.0f * fh + sh.ghf[j];
+      if (dj < best) {
+        second = best;
+        best = dj;
+        bj = j;
+      } else if (dj < second) {
+        second = dj;
+      }
+    }
+    const int old = u[i];
+    u[i] = bj;
+    ch += (old != bj);
+    if (margin) margin[i] = second - best;
+    if (dmin) dmin[i] = best;
+    om += (double)best;
+  }
+  om = block_sum(om, red_d);
+  ch = block_sum(ch, red_i);
+  if (threadIdx.x == 0) {
+    I.omega_part[blockIdx.x] = om;
+    I.changed_part[blockIdx.x] = ch;
+  }
+  if (!rebuild) return;
+  // last CTA to finish: trace, early-stop flag, supports of the next iteration
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double o = 0.0;
+  int c = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kAssignThreads) {
+    o += __ldcg(I.omega_part + b);
+    c += __ldcg(I.changed_part + b);
+  }
+  o = block_sum(o, red_d);
+  c = block_sum(c, red_i);
+  if (threadIdx.x == 0) {
+    const int t = *I.trace_count;
+    I.trace_omega[t] = o;
+    I.trace_changed[t] = c;
+    *I.trace_count = t + 1;
+    if (early_stop && c == 0) *I.done = 1;
+    *I.ticket = 0u;
+  }
+  __syncthreads();
+  build_supports_block(S, u);
+}
+
+cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                          const float* kself, int32_t* u, float* margin, float* dmin,
+                          float* fhat_out, double* ghat_out, int early_stop, int rebuild,
+                          cudaStream_t st) {
+  assign_kernel<<<I.assign_grid, kAssignThreads, 0, st>>>(ldk, Ni, S, I, kself, u, margin, dmin,
+                                                         fhat_out, ghat_out, early_stop, rebuild);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------- Eq. 8 nearest medoid
+__global__ void nearest_kernel(const float* __restrict__ Kt, int64_t ldk, int Ni, int C,
+                               const float* __restrict__ kself, const float* __restrict__ kmm,
+                               int32_t* __restrict__ u, float* __restrict__ dmin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ni) return;
+  const float ks = kself ? kself[i] : 1.0f;
+  float best = __int_as_float(0x7f800000);
+  int bj = 0;
+  for (int j = 0; j < C; ++j) {
+    const float dj = ks - 2.0f * Kt[(int64_t)j * ldk + i] + (kmm ? kmm[j] : 1.0f);
+    if (dj < best) {
+      best = dj;
+      bj = j;
+    }
+  }
+  u[i] = bj;
+  if (dmin) dmin[i] = best;
+}
+
+cudaError_t launch_nearest(const float* Kt, int64_t ldk, int Ni, int C, const float* kself,
+                           const float* kmm, int32_t* u, float* dmin, cudaStream_t st) {
+  if (Ni <= 0) return cudaSuccess;
+  nearest_kernel<<<(unsigned)ceil_div(Ni, 256), 256, 0, st>>>(Kt, ldk, Ni, C, kself, kmm, u, dmin);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------- Eq. 10 medoid keys
+__global__ void __launch_bounds__(kAssignThreads)
+medoid_keys_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
+                   const int32_t* __restrict__ u, unsigned long long* __restrict__ keys,
+                   int32_t* __restrict__ c, double* __restrict__ ghat_out) {
+  __shared__ AssignShared sh;
+  __shared__ unsigned long long bkey[kMaxC];
+  __shared__ int bcnt[kMaxC];
+  const int C = S.C;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    bkey[j] = ~0ull;
+    bcnt[j] = 0;
+  }
+  load_cluster_stats(sh, S, I.gpart, I.n_strips, I.ghat_in);
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
+  for (int i = blockIdx.x * kAssignThreads + threadIdx.x; i < Ni; i += gridDim.x * kAssignThreads) {
+    const float ks = kself ? kself[i] : 1.0f;
+    atomicAdd(&bcnt[u[i]], 1);
+    for (int j = 0; j < C; ++j) {
+      if (sh.nj[j] == 0) continue;
+      const float v = ks - 2.0f * fhat_of(sh, I.partial, ldk, i, j);
+      atomicMin(&bkey[j], pack_key(v, (uint32_t)i));
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    if (bkey[j] != ~0ull) atomicMin(keys + j, bkey[j]);
+    if (bcnt[j]) atomicAdd(c + j, bcnt[j]);
+  }
+}
+
+cudaError_t launch_medoid_keys(int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                               const float* kself, const int32_t* u, unsigned long long* keys,
+                               int32_t* c, double* ghat_out, cudaStream_t st) {
+  medoid_keys_kernel<<<I.assign_grid, kAssignThreads, 0, st>>>(ldk, Ni, S, I, kself, u, keys, c,
+                                                              ghat_out);
+  return cudaGetLastError();
+}
+
+__global__ void medoid_pick_kernel(const unsigned long long* __restrict__ keys,
+                                   const int32_t* __restrict__ c, const int32_t* __restrict__ n_j,
+                                   int C, int32_t* __restrict__ mi) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= C) return;
+  mi[j] = (c[j] > 0 && n_j[j] > 0 && keys[j] != ~0ull) ? (int32_t)(keys[j] & 0xffffffffull) : -1;
+}
+
+cudaError_t launch_medoid_pick(const unsigned long long* keys, const int32_t* c,
+                               const int32_t* n_j, int C, int32_t* mi, cudaStream_t st) {
+  medoid_pick_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, c, n_j, C, mi);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- Eq. 12 merge
+__global__ void __launch_bounds__(256)
+merge_keys_kernel(const float* __restrict__ Kt, const float* __restrict__ Kmi, int64_t ldk, int Ni,
+                  int C, const float* __restrict__ kself, const int32_t* __restrict__ mi,
+                  const int32_t* __restrict__ c, const int64_t* __restrict__ W,
+                  unsigned long long* __restrict__ keys) {
+  __shared__ unsigned long long bkey[kMaxC];
+  __shared__ float alpha[kMaxC];
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    bkey[j] = ~0ull;
+    alpha[j] = mi[j] >= 0 ? (float)((double)c[j] / ((double)c[j] + (double)W[j])) : 0.0f;
+  }
+  __syncthreads();
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Ni; l += gridDim.x * blockDim.x) {
+    const float ks = kself ? kself[l] : 1.0f;
+    for (int j = 0; j < C; ++j) {
+      if (mi[j] < 0) continue;
+      const float a = alpha[j];
+      const float v = ks - 2.0f * (1.0f - a) * Kt[(int64_t)j * ldk + l] - 2.0f * a * Kmi[(int64_t)j * ldk + l];
+      atomicMin(&bkey[j], pack_key(v, (uint32_t)l));
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < C; j += blockDim.x)
+    if (bkey[j] != ~0ull) atomicMin(keys + j, bkey[j]);
+}
+
+cudaError_t launch_merge_keys(const float* Kt, const float* Kmi, int64_t ldk, int Ni, int C,
+                              const float* kself, const int32_t* mi, const int32_t* c,
+                              const int64_t* W, unsigned long long* keys, cudaStream_t st) {
+  const int grid = (int)std::min<int64_t>(ceil_div(Ni, 256), 152 * 4);
+  merge_keys_kernel<<<grid, 256, 0, st>>>(Kt, Kmi, ldk, Ni, C, kself, mi, c, W, keys);
+  return cudaGetLastError();
+}
+
+__global__ void merge_apply_kernel(const unsigned long long* __restrict__ keys,
+                                   const int32_t* __restrict__ mi, const int32_t* __restrict__ c,
+                                   int C, int64_t start, int64_t step, int64_t* __restrict__ M,
+                                   int64_t* __restrict__ W) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= C || mi[j] < 0) return;
+  const int64_t l = (int64_t)(keys[j] & 0xffffffffull);
+  M[j] = start + l * step;
+  W[j] += c[j];
+}
+
+cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi, const int32_t* c,
+                               int C, int64_t start, int64_t step, int64_t* M, int64_t* W,
+                               cudaStream_t st) {
+  merge_apply_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, mi, c, C, start, step, M, W);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- small utils
+__global__ void scatter_labels_kernel(const int32_t* __restrict__ u, int Ni, int64_t start,
+                                      int64_t step, int32_t* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < Ni) out[start + (int64_t)l * step] = u[l];
+}
+cudaError_t launch_scatter_labels(const int32_t* u, int Ni, int64_t start, int64_t step,
+                                  int32_t* labels_out, cudaStream_t st) {
+  if (Ni <= 0) return cudaSuccess;
+  scatter_labels_kernel<<<(unsigned)ceil_div(Ni, 256), 256, 0, st>>>(u, Ni, start, step, labels_out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void fill_kernel(T* p, T v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  fill_kernel<unsigned long long><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(p, v, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  fill_kernel<int32_t><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(p, v, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill_f32(float* p, float v, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  fill_kernel<float><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, st>>>(p, v, n);
+  return cudaGetLastError();
+}
+
+__global__ void local_to_global_kernel(const int32_t* __restrict__ picks, int C, int64_t start,
+                                       int64_t step, int64_t* __restrict__ M) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < C) M[j] = start + (int64_t)picks[j] * step;
+}
+cudaError_t launch_local_to_global(const int32_t* picks, int C, int64_t start, int64_t step,
+                                   int64_t* M, cudaStream_t st) {
+  local_to_global_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(picks, C, start, step, M);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- k-means++ round
+// One CTA: D2 <- min(D2, max(0, K_ll - 2K(x_l, m) + K_mm)) with the column of
+// the previous pick, an FP64 exclusive scan in index order, then the first
+// index whose running sum exceeds u01 * total (lowest unchosen index when the
+// total is 0).
+constexpr int kKppThreads = 1024;
+__global__ void __launch_bounds__(kKppThreads)
+kpp_round_kernel(const float* __restrict__ Kc, int N0, const float* __restrict__ kself,
+                 double* __restrict__ D2, int32_t* __restrict__ picks,
+                 const double* __restrict__ draws, int r) {
+  __shared__ double wsum[kKppThreads / 32];
+  __shared__ double total_sh;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int m = picks[r - 1];
+  const double km = kself ? (double)kself[m] : 1.0;
+  const int per = (N0 + kKppThreads - 1) / kKppThreads;
+  const int lo = min(N0, tid * per), hi = min(N0, lo + per);
+  double loc = 0.0;
+  for (int l = lo; l < hi; ++l) {
+    const double ks = kself ? (double)kself[l] : 1.0;
+    double v = ks - 2.0 * (double)Kc[l] + km;
+    v = v > 0.0 ? v : 0.0;
+    const double dv = (r == 1) ? v : fmin(D2[l], v);
+    D2[l] = dv;
+    loc += dv;
+  }
+  // exclusive block scan of loc
+  double x = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  if (tid == 0) picks[r] = -1;
+  __syncthreads();
+  if (w == 0) {
+    double s = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s;
+    if (lane == 31) total_sh = s;
+  }
+  __syncthreads();
+  const double excl = (w > 0 ? wsum[w - 1] : 0.0) + x - loc;
+  const double total = total_sh;
+  if (total > 0.0) {
+    const double target = draws[r] * total;
+    double run = excl;
+    for (int l = lo; l < hi; ++l) {
+      const double nxt = run + D2[l];
+      if (run <= target && nxt > target) picks[r] = l;
+      run = nxt;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && picks[r] < 0) {
+    if (total > 0.0) {  // rounding put the target at the very end
+      int l = N0 - 1;
+      while (l > 0 && !(D2[l] > 0.0)) --l;
+      picks[r] = l;
+    } else {
+      for (int l = 0; l < N0; ++l) {
+        bool taken = false;
+        for (int q = 0; q < r; ++q) taken |= (picks[q] == l);
+        if (!taken) {
+          picks[r] = l;
+          break;
+        }
+      }
+    }
+  }
+}
+
+cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2,
+                             int32_t* picks, const double* draws, int r, cudaStream_t st) {
+  kpp_round_kernel<<<1, kKppThreads, 0, st>>>(Kc, N0, kself, D2, picks, draws, r);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------- fixed-order sums
+__global__ void sum_partial_kernel(const float* __restrict__ v, int64_t n, double* __restrict__ part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)v[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+__global__ void sum_final_kernel(const double* __restrict__ part, int parts, double* __restrict__ out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < parts; b += blockDim.x) s += part[b];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+cudaError_t launch_sum_f32_to_f64(const float* v, int64_t n, double* part, int parts, double* out,
+                                  cudaStream_t st) {
+  sum_partial_kernel<<<parts, 256, 0, st>>>(v, n, part);
+  sum_final_kernel<<<1, 256, 0, st>>>(part, parts, out);
+  return cudaGetLastError();
+}
+
+}  // namespace kkm

@@ -1,0 +1,412 @@
+// MD kernel: K(x, y) = exp(-rmsd^2 / (2 sigma^2)) with rmsd the minimum RMSD
+// of two frames after optimal proper superposition.  The paper asks for a
+// roto-translation invariant similarity for MD frames without writing one
+// down; the minimum RMSD is the standard choice.
+//
+// Frames are prepared once as centred structure-of-arrays rows [3][ap]
+// (x, y, z planes of ap = n_atoms rounded up to 8, zero padded) with their
+// squared radius G = sum |x_a|^2.
+//
+// rmsd_gram computes a CTA tile of 32 reference frames x 64 sample frames, 8
+// pairs per thread, in two passes over the atoms:
+//   pass 1  the 3x3 correlation H = sum_a x_a y_a^T of each pair (FP32 FFMA,
+//           72 accumulators per thread, double-buffered shared-memory tiles of
+//           8 atoms);  then per pair the QCP root: the largest eigenvalue of
+//           Horn's 4x4 quaternion matrix as the largest root of its
+//           characteristic polynomial lambda^4 + c2 lambda^2 + c1 lambda + c0
+//           (c2 = -2 |S|_F^2, c1 = -8 det S, c0 = det N; Theobald 2005), found
+//           by Newton's method from the upper bound (G_x + G_y)/2, and the
+//           rotation from the quaternion eigenvector (a cofactor row of
+//           N - lambda I).
+//   pass 2  for pairs whose kernel value is not negligible, the residual
+//           sum_a |R x_a - y_a|^2 evaluated directly at that rotation.
+// Why two passes: rmsd^2 = (G_x + G_y - 2 lambda)/n cancels catastrophically
+// (G ~ 1e5 A^2 against n rmsd^2 ~ 1e2 for similar frames), so FP32 rounding of
+// H and G alone moves K by ~1e-4.  The direct residual has no cancellation,
+// and since the residual is stationary at the optimal rotation, the rotation's
+// own FP32 error enters only at second order.  No FP64 is needed.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace kkm {
+
+// ------------------------------------------------------------------ prep
+__global__ void rmsd_prep_kernel(const float* __restrict__ X, int n_atoms, int64_t start, int64_t step,
+                                 const int64_t* __restrict__ idx, int64_t n, float* __restrict__ out,
+                                 int ap, float* __restrict__ gsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const int64_t g = idx ? idx[row] : start + row * step;
+  const float* src = X + g * 3 * (int64_t)n_atoms;
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int a = lane; a < n_atoms; a += 32) {
+    sx += src[3 * a];
+    sy += src[3 * a + 1];
+    sz += src[3 * a + 2];
+  }
+  sx = warp_sum_f64(sx) / n_atoms;
+  sy = warp_sum_f64(sy) / n_atoms;
+  sz = warp_sum_f64(sz) / n_atoms;
+  float* dst = out + row * 3 * (int64_t)ap;
+  double gg = 0.0;
+  for (int a = lane; a < ap; a += 32) {
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (a < n_atoms) {
+      cx = (float)((double)src[3 * a] - sx);
+      cy = (float)((double)src[3 * a + 1] - sy);
+      cz = (float)((double)src[3 * a + 2] - sz);
+    }
+    dst[a] = cx;
+    dst[ap + a] = cy;
+    dst[2 * ap + a] = cz;
+    gg += (double)cx * cx + (double)cy * cy + (double)cz * cz;
+  }
+  gg = warp_sum_f64(gg);
+  if (lane == 0) gsq[row] = (float)gg;
+}
+
+cudaError_t launch_rmsd_prep_rows(const float* X, int n_atoms, int64_t start, int64_t step, int64_t n,
+                                  float* out, int ap, float* gsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  rmsd_prep_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, n_atoms, start, step, nullptr, n, out, ap, gsq);
+  return cudaGetLastError();
+}
+cudaError_t launch_rmsd_prep_idx64(const float* X, int n_atoms, const int64_t* idx, int64_t n, float* out,
+                                   int ap, float* gsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  rmsd_prep_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, n_atoms, 0, 0, idx, n, out, ap, gsq);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- QCP
+__device__ __forceinline__ float det3(float a, float b, float c, float d, float e, float f, float g,
+                                      float h, float i) {
+  return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// Minor of the symmetric 4x4 matrix m with row r and column c removed.
+__device__ __forceinline__ float minor4(const float m[4][4], int r, int c) {
+  int rr[3], cc[3];
+  int k = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q != r) rr[k++] = q;
+  k = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (q != c) cc[k++] = q;
+  return det3(m[rr[0]][cc[0]], m[rr[0]][cc[1]], m[rr[0]][cc[2]], m[rr[1]][cc[0]], m[rr[1]][cc[1]],
+              m[rr[1]][cc[2]], m[rr[2]][cc[0]], m[rr[2]][cc[1]], m[rr[2]][cc[2]]);
+}
+
+// Cofactor row r of m (the r-th column of its adjugate).
+template <int R>
+__device__ __forceinline__ void cofactor_row(const float m[4][4], float v[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = (((R + c) & 1) ? -1.f : 1.f) * minor4(m, R, c);
+}
+
+// H = sum_a x_a y_a^T (row-major 3x3) of centred frames x (reference) and y
+// (sample) with squared radii Gx, Gy.  Returns the estimate G_x + G_y -
+// 2 lambda_max (>= 0) and the rotation R (row-major) with R x ~ y.
+__device__ __forceinline__ float qcp_rotation(const float H[9], float Gx, float Gy, float R[9]) {
+  const float E0 = 0.5f * (Gx + Gy);
+  R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
+  R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
+  R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
+  if (!(E0 > 0.f)) return 0.f;
+  const float inv = 1.0f / E0;
+  const float Sxx = H[0] * inv, Sxy = H[1] * inv, Sxz = H[2] * inv;
+  const float Syx = H[3] * inv, Syy = H[4] * inv, Syz = H[5] * inv;
+  const float Szx = H[6] * inv, Szy = H[7] * inv, Szz = H[8] * inv;
+  float m[4][4];
+  m[0][0] = Sxx + Syy + Szz;
+  m[0][1] = Syz - Szy;
+  m[0][2] = Szx - Sxz;
+  m[0][3] = Sxy - Syx;
+  m[1][1] = Sxx - Syy - Szz;
+  m[1][2] = Sxy + Syx;
+  m[1][3] = Szx + Sxz;
+  m[2][2] = -Sxx + Syy - Szz;
+  m[2][3] = Syz + Szy;
+  m[3][3] = -Sxx - Syy + Szz;
+  m[1][0] = m[0][1]; m[2][0] = m[0][2]; m[3][0] = m[0][3];
+  m[2][1] = m[1][2]; m[3][1] = m[1][3]; m[3][2] = m[2][3];
+  const float c2 = -2.0f * (Sxx * Sxx + Sxy * Sxy + Sxz * Sxz + Syx * Syx + Syy * Syy + Syz * Syz +
+                            Szx * Szx + Szy * Szy + Szz * Szz);
+  const float c1 = -8.0f * det3(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz);
+  // det N by expansion in complementary 2x2 minors of rows (0,1) and (2,3)
+  const float s0 = m[0][0] * m[1][1] - m[1][0] * m[0][1], s1 = m[0][0] * m[1][2] - m[1][0] * m[0][2];
+  const float s2 = m[0][0] * m[1][3] - m[1][0] * m[0][3], s3 = m[0][1] * m[1][2] - m[1][1] * m[0][2];
+  const float s4 = m[0][1] * m[1][3] - m[1][1] * m[0][3], s5 = m[0][2] * m[1][3] - m[1][2] * m[0][3];
+  const float t5 = m[2][2] * m[3][3] - m[3][2] * m[2][3], t4 = m[2][1] * m[3][3] - m[3][1] * m[2][3];
+  const float t3 = m[2][1] * m[3][2] - m[3][1] * m[2][2], t2 = m[2][0] * m[3][3] - m[3][0] * m[2][3];
+  const float t1 = m[2][0] * m[3][2] - m[3][0] * m[2][2], t0 = m[2][0] * m[3][1] - m[3][0] * m[2][1];
+  const float c0 = s0 * t5 - s1 * t4 + s2 * t3 + s3 * t2 - s4 * t1 + s5 * t0;
+  // Newton from the upper bound 1 (= (Gx+Gy)/2 after scaling)
+  float lam = 1.0f;
+  for (int it = 0; it < 60; ++it) {
+    const float l2 = lam * lam;
+    const float P = ((l2 + c2) * lam + c1) * lam + c0;
+    const float dP = (4.0f * l2 + 2.0f * c2) * lam + c1;
+    if (!(dP != 0.0f)) break;
+    const float dl = P / dP;
+    lam -= dl;
+    if (fabsf(dl) <= 1e-7f * fabsf(lam)) break;
+  }
+  // eigenvector: the cofactor row of N - lambda I with the largest diagonal cofactor
+  float a[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[r][c] = m[r][c] - (r == c ? lam : 0.0f);
+  const float d0 = fabsf(minor4(a, 0, 0)), d1 = fabsf(minor4(a, 1, 1));
+  const float d2 = fabsf(minor4(a, 2, 2)), d3 = fabsf(minor4(a, 3, 3));
+  float v[4];
+  if (d0 >= d1 && d0 >= d2 && d0 >= d3) cofactor_row<0>(a, v);
+  else if (d1 >= d2 && d1 >= d3) cofactor_row<1>(a, v);
+  else if (d2 >= d3) cofactor_row<2>(a, v);
+  else cofactor_row<3>(a, v);
+  const float nv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (nv > 0.0f && isfinite(nv)) {
+    const float s = rsqrtf(nv);
+    const float w = v[0] * s, x = v[1] * s, y = v[2] * s, z = v[3] * s;
+    R[0] = w * w + x * x - y * y - z * z;
+    R[1] = 2.f * (x * y - w * z);
+    R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);
+    R[4] = w * w - x * x + y * y - z * z;
+    R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);
+    R[7] = 2.f * (y * z + w * x);
+    R[8] = w * w - x * x - y * y + z * z;
+  }
+  return fmaxf((Gx + Gy) * (1.0f - lam), 0.0f);
+}
+
+// --------------------------------------------------------------- pair tile
+constexpr int RT_A = 32, RT_B = 64, RT_K = 8;
+
+struct RmsdTiles {
+  float As[2][RT_K][3][RT_A];
+  float Bs[2][RT_K][3][RT_B];
+};
+
+// Prefetch of one atom stage into registers: A 192 float4, B 384 float4.
+struct RmsdPrefetch {
+  float4 a, b0, b1;
+};
+
+__device__ __forceinline__ void rmsd_fetch(const float* __restrict__ A, int nA, const float* __restrict__ Bm,
+                                           int nB, int ap, int a0, int b0, int k0, RmsdPrefetch& p) {
+  const int tid = threadIdx.x;
+  if (tid < 192) {
+    const int f = tid & 31, rest = tid >> 5, c = rest >> 1, h = rest & 1;
+    p.a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)min(a0 + f, nA - 1) * 3 * ap + c * ap + k0 + h * 4));
+  }
+  {
+    const int e = tid;
+    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
+    p.b0 = __ldg(reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + f, nB - 1) * 3 * ap + c * ap + k0 + h * 4));
+  }
+  if (tid < 128) {
+    const int e = tid + 256;
+    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
+    p.b1 = __ldg(reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + f, nB - 1) * 3 * ap + c * ap + k0 + h * 4));
+  }
+}
+
+__device__ __forceinline__ void rmsd_store(RmsdTiles& t, int buf, const RmsdPrefetch& p) {
+  const int tid = threadIdx.x;
+  if (tid < 192) {
+    const int f = tid & 31, rest = tid >> 5, c = rest >> 1, h = rest & 1;
+    t.As[buf][h * 4 + 0][c][f] = p.a.x;
+    t.As[buf][h * 4 + 1][c][f] = p.a.y;
+    t.As[buf][h * 4 + 2][c][f] = p.a.z;
+    t.As[buf][h * 4 + 3][c][f] = p.a.w;
+  }
+  {
+    const int e = tid;
+    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
+    t.Bs[buf][h * 4 + 0][c][f] = p.b0.x;
+    t.Bs[buf][h * 4 + 1][c][f] = p.b0.y;
+    t.Bs[buf][h * 4 + 2][c][f] = p.b0.z;
+    t.Bs[buf][h * 4 + 3][c][f] = p.b0.w;
+  }
+  if (tid < 128) {
+    const int e = tid + 256;
+    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
+    t.Bs[buf][h * 4 + 0][c][f] = p.b1.x;
+    t.Bs[buf][h * 4 + 1][c][f] = p.b1.y;
+    t.Bs[buf][h * 4 + 2][c][f] = p.b1.z;
+    t.Bs[buf][h * 4 + 3][c][f] = p.b1.w;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 2)
+rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB, int ap,
+                 int n_atoms, const float* __restrict__ gA, const float* __restrict__ gB,
+                 const int64_t* __restrict__ idA, const int64_t* __restrict__ idB, float neg_scale,
+                 float* __restrict__ out, int64_t ldo, int vec_ok) {
+  __shared__ __align__(16) RmsdTiles t;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int a0 = blockIdx.y * RT_A, b0 = blockIdx.x * RT_B;
+  const int nk = ap / RT_K;
+
+  // ---- pass 1: correlation matrices
+  float h[2][4][9];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[r][q][e] = 0.f;
+  RmsdPrefetch pf;
+  rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+  rmsd_store(t, 0, pf);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+#pragma unroll
+    for (int k = 0; k < RT_K; ++k) {
+      float2 av[3];
+      float4 bv[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        av[c] = *reinterpret_cast<const float2*>(&t.As[cur][k][c][ty * 2]);
+        bv[c] = *reinterpret_cast<const float4*>(&t.Bs[cur][k][c][tx * 4]);
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float x[3] = {r ? av[0].y : av[0].x, r ? av[1].y : av[1].x, r ? av[2].y : av[2].x};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float y[3] = {q == 0 ? bv[0].x : q == 1 ? bv[0].y : q == 2 ? bv[0].z : bv[0].w,
+                              q == 0 ? bv[1].x : q == 1 ? bv[1].y : q == 2 ? bv[1].z : bv[1].w,
+                              q == 0 ? bv[2].x : q == 1 ? bv[2].y : q == 2 ? bv[2].z : bv[2].w};
+#pragma unroll
+          for (int c1 = 0; c1 < 3; ++c1)
+#pragma unroll
+            for (int c2 = 0; c2 < 3; ++c2) h[r][q][c1 * 3 + c2] = fmaf(x[c1], y[c2], h[r][q][c1 * 3 + c2]);
+        }
+      }
+    }
+    if (kt + 1 < nk) rmsd_store(t, cur ^ 1, pf);
+    __syncthreads();
+  }
+
+  // ---- QCP estimates and rotations (h is overwritten by R)
+  float r2[2][4];
+  unsigned need = 0u;
+  const float inv_n = 1.0f / (float)n_atoms;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int a = min(a0 + ty * 2 + r, nA - 1);
+    const float ga = gA[a];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int b = min(b0 + tx * 4 + q, nB - 1);
+      float Rm[9];
+      const float est = qcp_rotation(h[r][q], ga, gB[b], Rm) * inv_n;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) h[r][q][e] = Rm[e];
+      r2[r][q] = est;
+      const bool refine = (KIND == DK_DIST) || (exp2f(est * neg_scale) > 1e-4f);
+      if (refine) need |= 1u << (r * 4 + q);
+    }
+  }
+
+  // ---- pass 2: direct residuals at the QCP rotation
+  if (__syncthreads_or(need != 0u)) {
+    float res[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) res[r][q] = 0.f;
+    rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+    rmsd_store(t, 0, pf);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+      const int cur = kt & 1;
+      if (kt + 1 < nk) rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+#pragma unroll
+      for (int k = 0; k < RT_K; ++k) {
+        float2 av[3];
+        float4 bv[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          av[c] = *reinterpret_cast<const float2*>(&t.As[cur][k][c][ty * 2]);
+          bv[c] = *reinterpret_cast<const float4*>(&t.Bs[cur][k][c][tx * 4]);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const float x0 = r ? av[0].y : av[0].x, x1 = r ? av[1].y : av[1].x, x2 = r ? av[2].y : av[2].x;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float y0 = q == 0 ? bv[0].x : q == 1 ? bv[0].y : q == 2 ? bv[0].z : bv[0].w;
+            const float y1 = q == 0 ? bv[1].x : q == 1 ? bv[1].y : q == 2 ? bv[1].z : bv[1].w;
+            const float y2 = q == 0 ? bv[2].x : q == 1 ? bv[2].y : q == 2 ? bv[2].z : bv[2].w;
+            const float* Rm = h[r][q];
+            const float e0 = fmaf(Rm[0], x0, fmaf(Rm[1], x1, fmaf(Rm[2], x2, -y0)));
+            const float e1 = fmaf(Rm[3], x0, fmaf(Rm[4], x1, fmaf(Rm[5], x2, -y1)));
+            const float e2 = fmaf(Rm[6], x0, fmaf(Rm[7], x1, fmaf(Rm[8], x2, -y2)));
+            res[r][q] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, res[r][q])));
+          }
+        }
+      }
+      if (kt + 1 < nk) rmsd_store(t, cur ^ 1, pf);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (need & (1u << (r * 4 + q))) r2[r][q] = res[r][q] * inv_n;
+  }
+
+  // ---- epilogue
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int a = a0 + ty * 2 + r;
+    if (a >= nA) continue;
+    const int64_t ia = idA ? idA[a] : -2;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int b = b0 + tx * 4 + q;
+      const bool same = idB && b < nB && idB[b] == ia;
+      const float rr = fmaxf(r2[r][q], 0.0f);
+      if (KIND == DK_DIST) v[q] = same ? 0.0f : sqrtf(rr);
+      else v[q] = same ? 1.0f : exp2f(rr * neg_scale);
+    }
+    float* orow = out + (int64_t)a * ldo;
+    const int b = b0 + tx * 4;
+    if (vec_ok && b + 3 < nB) {
+      *reinterpret_cast<float4*>(orow + b) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (b + q < nB) orow[b + q] = v[q];
+    }
+  }
+}
+
+cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB, int ap,
+                             int n_atoms, const float* gA, const float* gB, const int64_t* idA,
+                             const int64_t* idB, float neg_scale, float* out, int64_t ldo, cudaStream_t st) {
+  if (nA <= 0 || nB <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(nB, RT_B), (unsigned)ceil_div(nA, RT_A));
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  if (kind == DK_DIST)
+    rmsd_gram_kernel<DK_DIST><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, idB,
+                                                    neg_scale, out, ldo, vec_ok);
+  else
+    rmsd_gram_kernel<DK_RBF><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, idB,
+                                                   neg_scale, out, ldo, vec_ok);
+  return cudaGetLastError();
+}
+
+}  // namespace kkm

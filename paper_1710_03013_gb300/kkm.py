@@ -1,0 +1,356 @@
+"""Python binding of the C ABI in include/kkm.h (argument marshalling only).
+
+Every computation runs in ``libkkm.so``; this module converts tensors and
+arrays to pointers, calls the C function of the same name and raises
+``KKMError`` on a non-OK status.  Inputs may be CUDA tensors (device pointers)
+or host arrays (numpy / CPU tensors); device work runs on the current torch
+stream of the input's device.  There is no fallback: a missing library is an
+error.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkkm.so")
+
+KKM_RBF, KKM_RMSD, KKM_LINEAR = 0, 1, 2
+KKM_FP32, KKM_BF16, KKM_FP8 = 0, 1, 2
+KKM_STRIDE, KKM_BLOCK = 0, 1
+KKM_ASSIGN_SUPPORTS, KKM_ASSIGN_MEDOIDS = 0, 1
+KIND = {"rbf": KKM_RBF, "rmsd": KKM_RMSD, "linear": KKM_LINEAR}
+SAMPLING = {"stride": KKM_STRIDE, "block": KKM_BLOCK}
+MODE = {"supports": KKM_ASSIGN_SUPPORTS, "medoids": KKM_ASSIGN_MEDOIDS}
+STATUS_EINVAL = 1
+
+
+class KKMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class kkm_kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("sigma", ctypes.c_float), ("n_atoms", ctypes.c_int32)]
+
+
+class kkm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("sampling", ctypes.c_int32),
+                ("early_stop", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("init_medoids", ctypes.POINTER(ctypes.c_int64)), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32, _I64, _U64, _F32, _F64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                ctypes.c_float, ctypes.c_double)
+
+_SIGNATURES = {
+    "kkm_options_default": (None, [ctypes.POINTER(kkm_options)]),
+    "kkm_fit": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
+                       ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P)]),
+    "kkm_assign": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "kkm_cost": (_I32, [_P, _P, _I64, _I32, ctypes.POINTER(_F64), _P]),
+    "kkm_model_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
+                              ctypes.POINTER(_F32)]),
+    "kkm_model_medoids": (_I32, [_P, _P, _P, _P]),
+    "kkm_model_supports": (_I32, [_P, _P, _P, _P]),
+    "kkm_model_trace": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
+    "kkm_model_free": (None, [_P]),
+    "kkm_kernel_matrix": (_I32, [_P, _I64, _P, _I64, _I64, ctypes.POINTER(kkm_kernel), _P, _P]),
+    "kkm_median_bandwidth": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _U64,
+                                    ctypes.POINTER(_F32)]),
+    "kkm_debug_step": (_I32, [_P, _I64, _I64, _P, _I32, ctypes.POINTER(kkm_kernel), _I32, _P, _P, _P,
+                              _P, _P, _P, ctypes.POINTER(_F64), ctypes.POINTER(_I32), _P]),
+    "kkm_debug_kmeanspp": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _U64, _P, _P]),
+    "kkm_minibatch_plan": (_I32, [_I64, _I32, _I32, _F64, _U64, _I32, ctypes.POINTER(_I64),
+                                  ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P, ctypes.POINTER(_I64)]),
+    "kkm_status_string": (ctypes.c_char_p, [_I32]),
+    "kkm_last_error": (ctypes.c_char_p, []),
+    "kkm_prof_enable": (None, [_I32]),
+    "kkm_prof_reset": (None, []),
+    "kkm_prof_read": (_I32, [ctypes.c_char_p, ctypes.POINTER(_I64), ctypes.POINTER(_F64)]),
+    "kkm_prof_names": (_I32, [ctypes.c_char_p, _I32]),
+}
+
+
+def load():
+    """Loads libkkm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1710_03013_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(s):
+    return load().kkm_status_string(s).decode()
+
+
+def last_error():
+    return load().kkm_last_error().decode()
+
+
+def _check(status):
+    if status != 0:
+        raise KKMError(status, last_error())
+
+
+# ------------------------------------------------------------ marshalling
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _as_input(x, dtype):
+    """(pointer, keep-alive object) of a C-contiguous input of `dtype`."""
+    if hasattr(x, "data_ptr"):
+        torch = _torch()
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        t = x.to(tdt).contiguous()
+        return ctypes.c_void_p(t.data_ptr()), t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _stream_of(x):
+    if _is_cuda(x):
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _out_like(x, n, dtype):
+    """Output buffer on the same side as x: CUDA tensor or numpy array."""
+    if _is_cuda(x):
+        torch = _torch()
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        t = torch.empty(n, dtype=tdt, device=x.device)
+        return ctypes.c_void_p(t.data_ptr()), t
+    a = np.empty(n, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _kernel(kind, sigma, n_atoms):
+    k = KIND[kind] if isinstance(kind, str) else int(kind)
+    return kkm_kernel(k, float(sigma), int(n_atoms))
+
+
+# ----------------------------------------------------------------- model
+class Model:
+    """A fitted model (owns the C handle)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.kkm_model_free(self._h)
+            self._h = None
+
+    def info(self):
+        C, d, nL, sig = _I32(), _I64(), _I32(), _F32()
+        _check(load().kkm_model_info(self._h, ctypes.byref(C), ctypes.byref(d), ctypes.byref(nL),
+                                     ctypes.byref(sig)))
+        return {"C": C.value, "d": d.value, "n_support": nL.value, "sigma": sig.value}
+
+    def medoids(self):
+        inf = self.info()
+        idx = np.empty(inf["C"], np.int64)
+        cnt = np.empty(inf["C"], np.int64)
+        coords = np.empty((inf["C"], inf["d"]), np.float32)
+        _check(load().kkm_model_medoids(self._h, idx.ctypes.data, cnt.ctypes.data, coords.ctypes.data))
+        return idx, cnt, coords
+
+    def supports(self):
+        inf = self.info()
+        lab = np.empty(inf["n_support"], np.int32)
+        gh = np.empty(inf["C"], np.float64)
+        n = np.empty(inf["C"], np.int32)
+        _check(load().kkm_model_supports(self._h, lab.ctypes.data, gh.ctypes.data, n.ctypes.data))
+        return lab, gh, n
+
+    def trace(self):
+        n = _I32()
+        _check(load().kkm_model_trace(self._h, None, None, 0, ctypes.byref(n)))
+        om = np.empty(n.value, np.float64)
+        ch = np.empty(n.value, np.int32)
+        _check(load().kkm_model_trace(self._h, om.ctypes.data, ch.ctypes.data, n.value, ctypes.byref(n)))
+        return om, ch
+
+
+# ------------------------------------------------------------- functions
+def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
+            precision=KKM_FP32, sampling="stride", early_stop=True, init_medoids=None,
+            labels=True, stream=None):
+    """kkm_fit of the C ABI.  Returns (labels or None, Model)."""
+    lib = load()
+    N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
+    xp, keep = _as_input(X, np.float32)
+    k = _kernel(kind, sigma, n_atoms)
+    opt = kkm_options()
+    lib.kkm_options_default(ctypes.byref(opt))
+    opt.precision = int(precision)
+    opt.sampling = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    opt.early_stop = 1 if early_stop else 0
+    init_arr = None
+    if init_medoids is not None:
+        init_arr = np.ascontiguousarray(init_medoids, dtype=np.int64)
+        opt.init_medoids = init_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    opt.stream = stream if stream is not None else _stream_of(X)
+    lab_p, lab = _out_like(X, N, np.int32) if labels else (None, None)
+    h = ctypes.c_void_p()
+    _check(lib.kkm_fit(xp, N, d, int(C), int(B), float(s), ctypes.byref(k), int(iters),
+                       int(seed) & ((1 << 64) - 1), ctypes.byref(opt), lab_p, ctypes.byref(h)))
+    del keep, init_arr
+    return lab, Model(h)
+
+
+def kkm_assign(model, Xnew, mode="supports", stream=None):
+    """kkm_assign of the C ABI.  Returns (labels, squared distances)."""
+    lib = load()
+    M = int(Xnew.shape[0])
+    xp, keep = _as_input(Xnew, np.float32)
+    lab_p, lab = _out_like(Xnew, M, np.int32)
+    dist_p, dist = _out_like(Xnew, M, np.float32)
+    st = stream if stream is not None else _stream_of(Xnew)
+    _check(lib.kkm_assign(model.handle, xp, M, MODE[mode] if isinstance(mode, str) else int(mode),
+                          lab_p, dist_p, st))
+    del keep
+    return lab, dist
+
+
+def kkm_cost(model, X, mode="supports", stream=None):
+    """kkm_cost of the C ABI (Eq. 1, FP64)."""
+    lib = load()
+    N = int(X.shape[0])
+    xp, keep = _as_input(X, np.float32)
+    out = _F64()
+    st = stream if stream is not None else _stream_of(X)
+    _check(lib.kkm_cost(model.handle, xp, N, MODE[mode] if isinstance(mode, str) else int(mode),
+                        ctypes.byref(out), st))
+    del keep
+    return out.value
+
+
+def kkm_kernel_matrix(A, B, kind="rbf", sigma=1.0, n_atoms=0, stream=None):
+    """kkm_kernel_matrix of the C ABI: K(A, B) as [len(A)][len(B)] float32."""
+    lib = load()
+    nA, nB = int(A.shape[0]), int(B.shape[0])
+    d = int(np.prod(A.shape[1:]))
+    ap, ka = _as_input(A, np.float32)
+    bp, kb = _as_input(B, np.float32)
+    if _is_cuda(A):
+        torch = _torch()
+        out = torch.empty((nA, nB), dtype=torch.float32, device=A.device)
+        op = ctypes.c_void_p(out.data_ptr())
+    else:
+        out = np.empty((nA, nB), np.float32)
+        op = ctypes.c_void_p(out.ctypes.data)
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(A)
+    _check(lib.kkm_kernel_matrix(ap, nA, bp, nB, d, ctypes.byref(k), op, st))
+    del ka, kb
+    return out
+
+
+def kkm_median_bandwidth(X, kind="rbf", n_atoms=0, seed=0):
+    lib = load()
+    N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
+    xp, keep = _as_input(X, np.float32)
+    k = _kernel(kind, 0.0, n_atoms)
+    out = _F32()
+    _check(lib.kkm_median_bandwidth(xp, N, d, ctypes.byref(k), int(seed) & ((1 << 64) - 1),
+                                    ctypes.byref(out)))
+    del keep
+    return out.value
+
+
+def kkm_debug_step(Xb, L, u, C, kind="rbf", sigma=1.0, n_atoms=0, stream=None):
+    """kkm_debug_step of the C ABI: one teacher-forced inner iteration."""
+    lib = load()
+    Ni, d = int(Xb.shape[0]), int(np.prod(Xb.shape[1:]))
+    xp, keep = _as_input(Xb, np.float32)
+    L = np.ascontiguousarray(L, np.int32)
+    u = np.ascontiguousarray(u, np.int32)
+    out = {"u": np.empty(Ni, np.int32), "fhat": np.empty((Ni, C), np.float32),
+           "margin": np.empty(Ni, np.float32), "ghat": np.empty(C, np.float64),
+           "n": np.empty(C, np.int32)}
+    om, ch = _F64(), _I32()
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(Xb)
+    _check(lib.kkm_debug_step(xp, Ni, d, L.ctypes.data, len(L), ctypes.byref(k), int(C), u.ctypes.data,
+                              out["u"].ctypes.data, out["fhat"].ctypes.data, out["margin"].ctypes.data,
+                              out["ghat"].ctypes.data, out["n"].ctypes.data, ctypes.byref(om),
+                              ctypes.byref(ch), st))
+    out["omega"] = om.value
+    out["changed"] = ch.value
+    del keep
+    return out
+
+
+def kkm_debug_kmeanspp(X0, C, seed, kind="rbf", sigma=1.0, n_atoms=0, stream=None):
+    lib = load()
+    N0, d = int(X0.shape[0]), int(np.prod(X0.shape[1:]))
+    xp, keep = _as_input(X0, np.float32)
+    picks = np.empty(C, np.int64)
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(X0)
+    _check(lib.kkm_debug_kmeanspp(xp, N0, d, ctypes.byref(k), int(C), int(seed) & ((1 << 64) - 1),
+                                  picks.ctypes.data, st))
+    del keep
+    return picks
+
+
+def kkm_minibatch_plan(N, B, s, seed, batch, sampling="stride"):
+    """Host-only: (global indices of mini-batch `batch`, its sorted landmarks)."""
+    lib = load()
+    smp = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    start, step, n, nl = _I64(), _I64(), _I64(), _I64()
+    args = (int(N), int(B), smp, float(s), int(seed) & ((1 << 64) - 1), int(batch))
+    _check(lib.kkm_minibatch_plan(*args, ctypes.byref(start), ctypes.byref(step), ctypes.byref(n), None,
+                                  ctypes.byref(nl)))
+    L = np.empty(nl.value, np.int32)
+    _check(lib.kkm_minibatch_plan(*args, ctypes.byref(start), ctypes.byref(step), ctypes.byref(n),
+                                  L.ctypes.data, ctypes.byref(nl)))
+    gidx = start.value + step.value * np.arange(n.value, dtype=np.int64)
+    return gidx, L
+
+
+# ------------------------------------------------------------- profiling
+def prof_enable(on=True):
+    load().kkm_prof_enable(1 if on else 0)
+
+
+def prof_reset():
+    load().kkm_prof_reset()
+
+
+def prof_read(name):
+    n, ms = _I64(), _F64()
+    load().kkm_prof_read(name.encode(), ctypes.byref(n), ctypes.byref(ms))
+    return n.value, ms.value
+
+
+def prof_names():
+    lib = load()
+    size = lib.kkm_prof_names(None, 0)
+    buf = ctypes.create_string_buffer(size + 1)
+    lib.kkm_prof_names(buf, size + 1)
+    return [s for s in buf.value.decode().split(",") if s]

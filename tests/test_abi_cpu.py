@@ -1,0 +1,71 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol the
+header declares, and its host-only planning (mini-batch geometry and the
+SplitMix64 landmark draw, Section 3.1 and Eq. 14/18) equals the oracle's."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import kkm_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def kkm():
+    from paper_1710_03013_gb300 import build
+    build.build()
+    from paper_1710_03013_gb300 import kkm as mod
+    mod.load()
+    return mod
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "kkm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kkm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for want in ["kkm_fit", "kkm_assign", "kkm_cost", "kkm_model_free", "kkm_kernel_matrix",
+                 "kkm_debug_step", "kkm_status_string", "kkm_last_error"]:
+        assert want in names
+
+
+def test_library_exports_every_header_symbol(kkm):
+    lib = kkm.load()
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_header_symbol(kkm):
+    assert set(header_functions()) <= set(kkm._SIGNATURES)
+
+
+def test_status_strings(kkm):
+    assert kkm.status_string(0) == "KKM_OK"
+    assert kkm.status_string(1) == "KKM_EINVAL"
+
+
+@pytest.mark.parametrize("sampling", ["stride", "block"])
+@pytest.mark.parametrize("N,B,s,seed", [(60000, 4, 0.2, 7), (3001, 3, 0.3, 1), (17, 5, 1.0, 2),
+                                         (1000, 7, 0.01, 3), (500000, 20, 0.05, 11)])
+def test_minibatch_plan_matches_oracle(kkm, sampling, N, B, s, seed):
+    batches = O.minibatch_indices(N, B, sampling)
+    _, _, lm = O.rng_streams(seed, B)
+    for i in range(B):
+        gidx, L = kkm.kkm_minibatch_plan(N, B, s, seed, i, sampling)
+        assert np.array_equal(gidx, batches[i])
+        want = O.landmark_indices(len(batches[i]), s, lm[i])
+        assert np.array_equal(L, want)
+
+
+def test_minibatch_plan_rejects_bad_arguments(kkm):
+    for args in [(10, 0, 0.5, 1, 0), (10, 11, 0.5, 1, 0), (10, 2, 0.0, 1, 0), (10, 2, 1.5, 1, 0),
+                 (10, 2, 0.5, 1, 2)]:
+        with pytest.raises(kkm.KKMError) as e:
+            kkm.kkm_minibatch_plan(*args)
+        assert e.value.status == kkm.STATUS_EINVAL

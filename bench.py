@@ -1,0 +1,343 @@
+"""Benchmark of the approximate mini-batch kernel k-means fit on one GB300.
+
+Workload (the MNIST-shaped feature-vector run): N = 60,000 samples x d = 784
+values in [0, 1] quantised to k/255 (10 sparse Gaussian-mixture classes), RBF
+kernel with the median-distance bandwidth computed inside the fit, C = 10,
+B = 4 stride mini-batches, s = 0.2 (|L| = 3,000 landmarks per mini-batch of
+15,000), 30 inner iterations per mini-batch with early stop off (so every
+step does exactly 120 iterations), kernel k-means++ seeding, FP32.
+
+One step = one kkm_fit call over the whole data set.  Reported:
+  value      kernel evaluations per second of the whole fit, device-timed
+             with X resident in HBM (CUDA events on the fit's stream);
+  e2e        the same metric through the C ABI with host buffers (X in
+             pinned host memory, labels back to host), copies inside the timed
+             region;
+  roofline   for the kernel with the largest share of device time, its
+             algorithmic work per launch over its event-timed launch duration;
+  cpu_baseline  the FP64 oracle on a bounded sample of the same workload.
+Inputs are larger than L2 (X 188 MB, the kernel block 180 MB), so no L2 flush
+is needed between steps.
+
+--impl reference times the oracle (the plain FP64 CPU restatement of the
+method) on a bounded sample of the same workload per step.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="mnist-shaped 60000x784 RBF, C=10, B=4, s=0.2, 30 iters", N=60000, d=784, C=10,
+                B=4, s=0.2, iters=30, seed=1710)
+METRIC = "kernel evals/s & iters/s vs plain FP32 path at matched labels; p50/p99 latency"
+UNIT = "kernel evals/s"
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FFMA lanes x 2 flops x max SM clock
+CPU_SAMPLE_ROWS = 12000
+REF_SAMPLE_ROWS = 6000
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def n_landmarks(Ni, s):
+    import math
+    return int(min(max(math.ceil(s * Ni - 1e-9), 1), Ni))
+
+
+def fit_evals(N, B, C, s):
+    """Kernel evaluations of one fit (Alg. 1): per mini-batch the block
+    N_i x |L|, the auxiliary block N_i x C (Eq. 8) and the merge column block
+    N_i x C (Eq. 12); plus (C-1) k-means++ columns over the first mini-batch."""
+    total = 0
+    for i in range(B):
+        Ni = (N - i + B - 1) // B
+        total += Ni * n_landmarks(Ni, s) + 2 * Ni * C
+    total += (C - 1) * ((N + B - 1) // B)
+    return total
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1710_03013_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
+    None when the kernel's source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        data = json.load(f)
+    ent = data.get(kernel_name)
+    if not ent:
+        return None
+    try:
+        if source_hash(ent["sources"]) != ent["source_hash"]:
+            return None
+    except OSError:
+        return None
+    return ent["bytes_per_launch"]
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(X, rows, cfg):
+    """The oracle's whole fit on the first `rows` samples (same d, C, B, s,
+    iters).  Returns (kernel evals, seconds)."""
+    from oracle import kkm_oracle as O
+    Xs = X[:rows].astype(np.float64)
+    t0 = time.perf_counter()
+    O.fit(Xs, cfg["C"], cfg["B"], cfg["s"], O.Kernel(O.KIND_RBF, 0.0), cfg["iters"], cfg["seed"],
+          early_stop=False)
+    dt = time.perf_counter() - t0
+    return fit_evals(rows, cfg["B"], cfg["C"], cfg["s"]), dt
+
+
+def run_reference(args, cfg, X):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, evals = [], 0
+    for k in range(args.warmup + args.steps):
+        ev, dt = oracle_sample(X, REF_SAMPLE_ROWS, cfg)
+        if k >= args.warmup:
+            times.append(dt)
+            evals = ev
+    tot = sum(times)
+    value = evals * len(times) / tot
+    sample = (f"oracle fit of the first {REF_SAMPLE_ROWS} samples (same d, C, B, s, iters; "
+              f"{evals} kernel evals per step)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": cfg["name"], "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, cfg, X):
+    import torch
+    import torch.distributed as dist
+    from paper_1710_03013_gb300 import kkm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    C, B, s, iters, seed = cfg["C"], cfg["B"], cfg["s"], cfg["iters"], cfg["seed"]
+
+    def step():
+        return kkm.kkm_fit(Xd, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False)
+
+    for _ in range(args.warmup):
+        lab, model = step()
+    torch.cuda.synchronize()
+    kkm.prof_reset()
+    kkm.prof_enable(True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            lab, model = step()
+        ev1.record(stream)
+        barrier()
+    kkm.prof_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = {n: kkm.prof_read(n) for n in kkm.prof_names()}
+    launches = sum(v[0] for v in prof.values())
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    evals = fit_evals(cfg["N"], B, C, s)
+    value = world * evals / (ms / 1e3)
+    om, _ = model.trace()
+
+    # ---- end to end through the C ABI with host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    e2e_ms = []
+    for k in range(max(2, min(5, args.steps)) + 1):
+        barrier()
+        t0 = time.perf_counter()
+        lab_h, _ = kkm.kkm_fit(Xh, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False,
+                               stream=ctypes_stream(stream))
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_ms.append(1e3 * (t1 - t0))
+    e2e = float(np.median(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    Ni = (cfg["N"] + B - 1) // B
+    nL = n_landmarks(Ni, s)
+    roof = None
+    if dom == "gram_block":
+        n, tms = prof[dom]
+        flops = sum(2.0 * ((cfg["N"] - i + B - 1) // B) * n_landmarks((cfg["N"] - i + B - 1) // B, s)
+                    * cfg["d"] for i in range(B)) / B
+        ach = flops / (tms / n / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / PEAK_FP32_TFLOPS, "traffic": ncu_traffic("gram_block"),
+                "kernel": "gram_block", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "work_per_launch": f"2*N_i*|L|*d = {flops:.4g} flop"}
+    elif dom == "fhat_partial":
+        n, tms = prof[dom]
+        by = 4.0 * Ni * nL
+        ach = by / (tms / n / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic("fhat_partial"),
+                "kernel": "fhat_partial", "peak_source": peak_kind,
+                "work_per_launch": f"4*N_i*|L| = {by:.4g} B (one read of the kernel block)"}
+
+    # ---- CPU baseline: the oracle on a bounded sample
+    ev, dt = oracle_sample(X, CPU_SAMPLE_ROWS, cfg)
+    cpu = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"oracle fit of the first {CPU_SAMPLE_ROWS} samples (same d, C, B, s, iters), "
+                     f"{ev} kernel evals in {dt:.1f} s"}
+
+    it_ms = sum(prof.get(k, (0, 0.0))[1] for k in ("fhat_partial", "assign")) / args.steps
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "N": cfg["N"], "d": cfg["d"], "C": C, "B": B, "s": s,
+                   "iters_per_minibatch": iters, "precision": "fp32", "bandwidth": "median rule inside the fit",
+                   "l2": "inputs larger than L2 (X 188 MB, kernel block 180 MB); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "iters_per_s": world * B * iters / (ms / 1e3),
+        "inner_iter_ms": it_ms / (B * iters),
+        "evals_per_step": evals,
+        "e2e": {"value": world * evals / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(4 * cfg["N"])},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "final_omega": float(om[-1]) if len(om) else None,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def ctypes_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    from synth import mnist_like
+    cfg = dict(WORKLOAD)
+    X, _ = mnist_like(cfg["N"], cfg["d"])
+    if args.impl == "reference":
+        run_reference(args, cfg, X)
+    else:
+        from paper_1710_03013_gb300 import build as _b
+        _b.build()
+        run_ours(args, cfg, X)
+
+
+if __name__ == "__main__":
+    main()

@@ -324,14 +324,14 @@ static kkm_status copy_prepared(const KernelSpec& sp, const float* Xp, const int
 static kkm_status kernel_block(const KernelSpec& sp, const float* A, const float* auxA,
                                const int64_t* idA, int64_t nA, const float* Bm, const float* auxB,
                                const int64_t* idB, int64_t nB, float* out, int64_t ldo,
-                               cudaStream_t st, bool dist = false) {
+                               cudaStream_t st, bool dist = false, bool block = false) {
   if (sp.kind == KKM_RMSD) {
-    KKM_RUN("rmsd_gram", st,
+    KKM_RUN(block ? "rmsd_block" : "rmsd_gram", st,
             launch_rmsd_gram(dist ? DK_DIST : DK_RBF, A, nA, Bm, nB, sp.ap, sp.n_atoms, auxA, auxB, idA,
                              idB, sp.neg_scale(), out, ldo, st));
   } else {
     const int dk = dist ? DK_DIST : (sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF);
-    KKM_RUN("gram", st,
+    KKM_RUN(block ? "gram_block" : "gram", st,
             launch_gram(dk, A, nA, Bm, nB, sp.dp, auxA, auxB, idA, idB, sp.neg_scale(), out, ldo, st));
   }
   return KKM_OK;
@@ -611,7 +611,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
     gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL);
     KKM_LAUNCH_CK();
-    KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st));  // Alg. 1 line 3
+    KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));  // Alg. 1 line 3
 
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
       KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, st));

@@ -22,7 +22,9 @@ def rel_margin(d):
     if d.shape[1] < 2:
         return np.full(d.shape[0], np.inf)
     part = np.partition(d, 1, axis=1)
-    return (part[:, 1] - part[:, 0]) / np.maximum(np.abs(part[:, 1]), 1e-12)
+    with np.errstate(invalid="ignore"):
+        rel = (part[:, 1] - part[:, 0]) / np.maximum(np.abs(part[:, 1]), 1e-12)
+    return np.where(np.isinf(part[:, 1]), np.inf, rel)
 
 
 def clear_rows(d):

@@ -399,9 +399,11 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&S.seg_unit, C + 1));
   KKM_TRY(ws.alloc(&S.n_units, 1));
   KKM_TRY(ws.alloc(&S.col_label, ldk));
+  KKM_TRY(ws.alloc(&S.col_ord, ldk));
+  KKM_TRY(ws.alloc(&S.lab, nLmax));
   KKM_TRY(ws.alloc(&lb->n_copy, C));
   I.n_strips = (int)ceil_div(ldk, kStripCols);
-  I.assign_grid = (int)std::min<int64_t>(ceil_div(ldk, 256), 152 * 4);
+  I.assign_grid = (int)ceil_div(ldk, 128);
   KKM_TRY(ws.alloc(&I.partial, (int64_t)mu * ldk));
   KKM_TRY(ws.alloc(&I.gpart, (int64_t)mu * I.n_strips));
   KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
@@ -418,14 +420,17 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
 }
 
 // Kernel k-means++ on prepared rows Xi (picks[0] already on the device).
+// D2 needs 2*Ni + ceil(Ni/256) doubles (D^2, block prefixes, block totals).
 static kkm_status kmeanspp_dev(const KernelSpec& sp, const float* Xi, const float* aux_i, int Ni, int C,
                                const float* kself, float* rowbuf, float* rowaux, float* kcol,
                                int64_t ldk, double* D2, int32_t* picks, const double* draws_d,
                                cudaStream_t st) {
+  double* P = D2 + Ni;
+  double* bsum = P + Ni;
   for (int r = 1; r < C; ++r) {
     KKM_TRY(copy_prepared(sp, Xi, picks + (r - 1), 1, rowbuf, rowaux, st));
     KKM_TRY(kernel_block(sp, rowbuf, rowaux, nullptr, 1, Xi, aux_i, nullptr, Ni, kcol, ldk, st));
-    KKM_RUN("kpp_round", st, launch_kpp_round(kcol, Ni, kself, D2, picks, draws_d, r, st));
+    KKM_RUN("kpp_round", st, launch_kpp_round(kcol, Ni, kself, D2, P, bsum, picks, draws_d, r, st));
   }
   return KKM_OK;
 }
@@ -580,7 +585,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   Supports& S = lb.S;
   IterState& I = lb.I;
   if (do_kpp) {
-    KKM_TRY(ws.alloc(&D2, geo[0].Ni));
+    KKM_TRY(ws.alloc(&D2, 2 * geo[0].Ni + ceil_div(geo[0].Ni, 256)));
     KKM_TRY(ws.alloc(&draws_d, C));
     KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
     KKM_CK(cudaMemcpyAsync(picks, pick0.data(), 4, cudaMemcpyHostToDevice, st));
@@ -606,11 +611,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const int nL = (int)(L_off[i + 1] - L_off[i]);
     const int32_t* Ld = Ld_all + L_off[i];
     KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, Xi, aux_i, st));             // fetch X^i
-    iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni);
-    KKM_LAUNCH_CK();
+    KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
-    gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL);
-    KKM_LAUNCH_CK();
+    KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
     KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));  // Alg. 1 line 3
 
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
@@ -626,13 +629,16 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     S.L = Ld;
     S.nL = nL;
     KKM_RUN("fill", st, launch_fill_i32(S.col_label, -1, ldk, st));
-    KKM_RUN("build_supports", st, launch_build_supports(S, u, st));
+    KKM_RUN("fill", st, launch_fill_i32(S.col_ord, -1, ldk, st));
+    KKM_RUN("landmark_maps", st, launch_landmark_maps(S, u, st));
+    KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, st));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
-                            /*rebuild=*/1, st));
+                            /*trace=*/1, st));
+      KKM_RUN("build_supports", st, launch_build_supports(S, I.done, st));
     }
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
@@ -643,11 +649,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("medoid_keys", st, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, st));
     KKM_RUN("medoid_pick", st, launch_medoid_pick(keys, cnt, S.n_j, C, mi, st));
     // Eq. 12: K(X^i, m^i) and the convex merge
-    clamp_idx_kernel<<<blocks_for(C), 256, 0, st>>>(mi, C, mi_safe);
-    KKM_LAUNCH_CK();
+    KKM_RUN("clamp_idx", st, (clamp_idx_kernel<<<blocks_for(C), 256, 0, st>>>(mi, C, mi_safe), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, st));
-    gather_i64_kernel<<<blocks_for(C), 256, 0, st>>>(gid, mi, C, idMI);
-    KKM_LAUNCH_CK();
+    KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(C), 256, 0, st>>>(gid, mi, C, idMI), cudaGetLastError()));
     KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, st));
     KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
     KKM_RUN("merge_keys", st, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, st));
@@ -706,8 +710,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(cp(m->seg_unit, S.seg_unit, (size_t)(C + 1) * 4));
       KKM_TRY(cp(m->n_units, S.n_units, 4));
       KKM_TRY(cp(m->ghat, ghat, (size_t)C * 8));
-      gather_i32_kernel<<<blocks_for(nL), 256, 0, st>>>(u, Ld, nL, m->sup_labels);
-      KKM_LAUNCH_CK();
+      KKM_RUN("gather_labels", st, (gather_i32_kernel<<<blocks_for(nL), 256, 0, st>>>(u, Ld, nL, m->sup_labels), cudaGetLastError()));
       {
         std::vector<int32_t> ident(nL);
         for (int q = 0; q < nL; ++q) ident[q] = q;
@@ -827,6 +830,8 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
     S.seg_unit = m->seg_unit;
     S.n_units = m->n_units;
     S.col_label = nullptr;
+    S.col_ord = nullptr;
+    S.lab = nullptr;
     lb.I.ghat_in = m->ghat;
     lb.I.done = nullptr;
   }
@@ -938,18 +943,18 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_CK(cudaMemcpyAsync(Ld, L, (size_t)nL * 4, cudaMemcpyHostToDevice, st));
   KKM_CK(cudaMemcpyAsync(u, u_in, (size_t)Ni * 4, cudaMemcpyHostToDevice, st));
   KKM_TRY(prep_rows(sp, X, 0, 1, Ni, Xi, aux, st));
-  iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, 0, 1, Ni);
-  KKM_LAUNCH_CK();
+  KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, 0, 1, Ni), cudaGetLastError()));
   KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));
-  gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL);
-  KKM_LAUNCH_CK();
+  KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
   KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux, gid, Ni, KT, ldk, st));
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, nL, C, ldk, 1, &lb));
   lb.S.L = Ld;
   lb.S.nL = nL;
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_label, -1, ldk, st));
-  KKM_RUN("build_supports", st, launch_build_supports(lb.S, u, st));
+  KKM_RUN("fill", st, launch_fill_i32(lb.S.col_ord, -1, ldk, st));
+  KKM_RUN("landmark_maps", st, launch_landmark_maps(lb.S, u, st));
+  KKM_RUN("build_supports", st, launch_build_supports(lb.S, nullptr, st));
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
   const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
   KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
@@ -993,7 +998,7 @@ static kkm_status debug_kmeanspp_impl(const float* X0_in, int64_t N0, int64_t d,
   KKM_TRY(ws.alloc(&rowbuf, sp.dp));
   KKM_TRY(ws.alloc(&rowaux, 1));
   KKM_TRY(ws.alloc(&kcol, ldk));
-  KKM_TRY(ws.alloc(&D2, N0));
+  KKM_TRY(ws.alloc(&D2, 2 * N0 + ceil_div(N0, 256)));
   KKM_TRY(ws.alloc(&draws_d, C));
   KKM_TRY(ws.alloc(&picks, C));
   KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));

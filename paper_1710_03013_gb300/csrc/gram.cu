@@ -8,6 +8,8 @@
 // exponential.  Squared norms are accumulated in FP64 once per row by the
 // gather kernels.  A "skinny" kernel covers <= 32 reference rows (medoid
 // columns, k-means++ columns) with one warp per sample row.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -27,6 +29,25 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int64_t d, int64
     float v = c < d ? src[c] : 0.0f;
     dst[c] = v;
     acc += (double)v * (double)v;
+  }
+  acc = warp_sum_f64(acc);
+  if (normsq && lane == 0) normsq[row] = (float)acc;
+}
+
+// Same with 16-byte vectors (d a multiple of 4 and X 16-byte aligned).
+__global__ void gather_rows4_kernel(const float4* __restrict__ X, int64_t d4, int64_t start,
+                                    int64_t step, int64_t n, float4* __restrict__ out, int dp4,
+                                    float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float4* src = X + (start + row * step) * d4;
+  float4* dst = out + row * (int64_t)dp4;
+  double acc = 0.0;
+  for (int c = lane; c < dp4; c += 32) {
+    const float4 v = c < d4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    dst[c] = v;
+    acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
   }
   acc = warp_sum_f64(acc);
   if (normsq && lane == 0) normsq[row] = (float)acc;
@@ -55,7 +76,14 @@ __global__ void gather_idx_kernel(const float* __restrict__ X, int64_t ld_in, in
 cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step, int64_t n,
                                float* out, int dp, float* normsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  gather_rows_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, start, step, n, out, dp, normsq);
+  if (d % 4 == 0 && dp % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    gather_rows4_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(
+        reinterpret_cast<const float4*>(X), d / 4, start, step, n, reinterpret_cast<float4*>(out), dp / 4,
+        normsq);
+  } else {
+    gather_rows_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, start, step, n, out, dp, normsq);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_gather_idx64(const float* X, int64_t d, const int64_t* idx, int64_t n,
@@ -200,8 +228,8 @@ gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict_
   for (int e = threadIdx.x; e < nA * dq; e += blockDim.x) As4[e] = A4[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= nB) return;
+  for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nB;
+       b += gridDim.x * (blockDim.x >> 5)) {
   float acc[NA];
 #pragma unroll
   for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
@@ -228,6 +256,7 @@ gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict_
     const bool same = idA && idB && idA[lane] == idB[b];
     out[(int64_t)lane * ldo + b] = gram_epilogue<KIND>(mine, na, nbv, same, neg_scale);
   }
+  }
 }
 
 template <int KIND>
@@ -237,7 +266,7 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
                                  cudaStream_t st) {
   const size_t skinny_smem = (size_t)nA * dp * sizeof(float);
   if (nA <= 32 && skinny_smem <= 96 * 1024) {
-    const int grid = (int)ceil_div(nB, 8);
+    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8), 152 * 8);
     cudaError_t e;
 #define KKM_SKINNY(NAV)                                                                 \
   e = cudaFuncSetAttribute(gram_skinny_kernel<KIND, NAV>,                               \

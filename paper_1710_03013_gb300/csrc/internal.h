@@ -103,6 +103,8 @@ struct Supports {
   int32_t* n_units;      // [1]
   int32_t* col_label;    // [ldk] label of the landmark in column i, else -1;
                          // NULL: no g_hat numerators are needed
+  int32_t* col_ord;      // [ldk] landmark ordinal of column i, else -1 (NULL: none)
+  int32_t* lab;          // [nL] landmark labels, written by assign
   int max_units;
 };
 inline int max_units_for(int nL, int C) { return (int)(ceil_div(nL, kUnitRows) + C); }
@@ -122,17 +124,20 @@ struct IterState {
   int n_strips;
 };
 
-// Builds perm/seg/units/col_label from u (one CTA).
-cudaError_t launch_build_supports(const Supports& S, const int32_t* u, cudaStream_t st);
+// Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA);
+// skipped when *skip != 0.
+cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, cudaStream_t st);
+// col_ord[L[k]] = k (col_ord pre-filled with -1) and lab[k] = u[L[k]].
+cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st);
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st);
 // g_hat, f_hat, distances, argmin, margin, Omega; updates u in place.  With
-// rebuild != 0 the last CTA also writes the trace entry, the early-stop flag
-// and rebuilds the supports for the next iteration.
+// trace != 0 the last CTA also writes the trace entry and the early-stop flag.
+// Uses ceil(Ni/128) CTAs (omega_part/changed_part need that many slots).
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,
-                          float* fhat_out, double* ghat_out, int early_stop, int rebuild,
+                          float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st);
 
 // ---- mini-batch boundary -----------------------------------------------------
@@ -161,8 +166,9 @@ cudaError_t launch_fill_u64(unsigned long long* p, unsigned long long v, int n, 
 cudaError_t launch_fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
 cudaError_t launch_fill_f32(float* p, float v, int64_t n, cudaStream_t st);
 // kernel k-means++ round r (1..C-1): D2 update with column Kc and the next pick.
-cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2,
-                             int32_t* picks, const double* draws, int r, cudaStream_t st);
+// P [N0] and bsum [ceil(N0/256)] are scratch.
+cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2, double* P,
+                             double* bsum, int32_t* picks, const double* draws, int r, cudaStream_t st);
 // picks (local) -> global ids start + p*step
 cudaError_t launch_local_to_global(const int32_t* picks, int C, int64_t start, int64_t step,
                                    int64_t* M, cudaStream_t st);

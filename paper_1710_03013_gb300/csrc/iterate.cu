@@ -8,7 +8,7 @@
 // cluster j is the contiguous segment perm[seg_off[j] .. seg_off[j+1]).  The
 // segment is cut into units of at most kUnitRows landmark rows.
 //
-// One iteration is two launches:
+// One iteration is three launches:
 //   fhat_partial  streams KT once (the HBM-bound step): every CTA sums the
 //                 rows of one unit over a 512-column strip with float4 loads
 //                 and writes the partial numerators of f_hat (Eq. 17), plus
@@ -19,8 +19,9 @@
 //                 j on ties), the margin and the FP64 cost partials, and
 //                 updates the labels in place.  Its last CTA to finish (atomic
 //                 ticket, no waiting) sums the cost in a fixed order, records
-//                 the trace, raises the early-stop flag and rebuilds the
-//                 supports for the next iteration from the new landmark labels.
+//                 the trace and raises the early-stop flag;
+//   build_supports  one 1024-thread CTA re-sorts the landmarks by their new
+//                 labels for the next iteration.
 // Every sum has a fixed order, so results are bit-reproducible.
 #include <math.h>
 
@@ -29,13 +30,15 @@
 
 namespace kkm {
 
-constexpr int kSupThreads = 256;  // build_supports block size (8 warps)
-constexpr int kAssignThreads = 256;
+constexpr int kSortThreads = 1024;  // build_supports: one CTA of 32 warps
+constexpr int kAssignThreads = 128;
 constexpr int kStreamThreads = kStripCols / 4;
 
-// Exclusive scan of one int per thread over a 256-thread block.
-__device__ __forceinline__ int block_excl_scan_256(int v, int* sh, int* total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Exclusive scan of one int per thread over the whole CTA (blockDim a
+// multiple of 32, at most 1024).  `sh` needs 32 slots.  Returns the
+// exclusive prefix; *total gets the CTA total.
+__device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -46,46 +49,55 @@ __device__ __forceinline__ int block_excl_scan_256(int v, int* sh, int* total) {
   if (lane == 31) sh[w] = x;
   __syncthreads();
   if (w == 0) {
-    int s = lane < 8 ? sh[lane] : 0;
+    int s = lane < nw ? sh[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(kFull, s, o);
       if (lane >= o) s += y;
     }
-    if (lane < 8) sh[lane] = s;
+    sh[lane] = s;
   }
   __syncthreads();
   const int off = w > 0 ? sh[w - 1] : 0;
-  *total = sh[7];
+  *total = sh[nw - 1];
   __syncthreads();
   return off + x - v;
 }
 
-// Rebuilds the support structure of the landmarks from the labels u.  Runs
-// on one whole CTA of kSupThreads threads.  u is read through L2 (it was
-// written by other CTAs of the same launch).
-__device__ void build_supports_block(const Supports& S, const int32_t* u) {
+// Rebuilds the support structure of the landmarks from the labels u: a
+// stable counting sort of the landmark ordinals by label (n_j, segment and
+// unit tables, perm) and the label of every landmark column.  One CTA of
+// kSortThreads threads; returns at once when the early-stop flag is set.
+__global__ void __launch_bounds__(kSortThreads)
+build_supports_kernel(Supports S, const int32_t* __restrict__ skip) {
   __shared__ int cnt[kMaxC];
   __shared__ int base[kMaxC];
-  __shared__ int wcnt[8 * kMaxC];
-  __shared__ int scan_sh[8];
+  __shared__ int wtab[32 * kMaxC];
+  __shared__ int scan_sh[32];
+  if (skip && *skip) return;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int C = S.C, nL = S.nL;
-  for (int j = tid; j < C; j += kSupThreads) cnt[j] = 0;
+  for (int j = tid; j < C; j += kSortThreads) cnt[j] = 0;
   __syncthreads();
-  for (int k = tid; k < nL; k += kSupThreads) {
-    const int l = S.L[k];
-    const int lab = __ldcg(u + l);
-    S.col_label[l] = lab;
-    atomicAdd(&cnt[lab], 1);
+  // pass 1: counts (one shared atomic per distinct label and warp)
+  for (int start = 0; start < nL; start += kSortThreads) {
+    const int k = start + tid;
+    int lab = -1;
+    if (k < nL) {
+      lab = S.lab[k];
+      S.col_label[S.L[k]] = lab;
+    }
+    const unsigned peers = __match_any_sync(kFull, lab);
+    if (lab >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[lab], __popc(peers));
   }
   __syncthreads();
-  // segment offsets and unit counts (C <= 256: one entry per thread)
+  // segment offsets and units (C <= 256 <= blockDim: one entry per thread)
   const int cj = tid < C ? cnt[tid] : 0;
   int total;
-  const int off = block_excl_scan_256(cj, scan_sh, &total);
+  const int off = block_excl_scan(cj, scan_sh, &total);
   const int nu = (cj + kUnitRows - 1) / kUnitRows;
-  const int uoff = block_excl_scan_256(nu, scan_sh, &total);
+  int nunits;
+  const int uoff = block_excl_scan(nu, scan_sh, &nunits);
   if (tid < C) {
     base[tid] = off;
     S.seg_off[tid] = off;
@@ -100,42 +112,56 @@ __device__ void build_supports_block(const Supports& S, const int32_t* u) {
   }
   if (tid == 0) {
     S.seg_off[C] = nL;
-    S.seg_unit[C] = total;
-    *S.n_units = total;
+    S.seg_unit[C] = nunits;
+    *S.n_units = nunits;
   }
   __syncthreads();
-  // stable scatter: chunk by chunk in landmark order
-  for (int start = 0; start < nL; start += kSupThreads) {
+  // pass 2: stable scatter, 1024 landmarks at a time in landmark order
+  for (int start = 0; start < nL; start += kSortThreads) {
     const int k = start + tid;
-    const int lab = k < nL ? __ldcg(u + S.L[k]) : -1;
+    const int lab = k < nL ? S.lab[k] : -1;
     const unsigned peers = __match_any_sync(kFull, lab);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    for (int e = tid; e < 8 * C; e += kSupThreads) wcnt[e] = 0;
+    for (int e = tid; e < 32 * C; e += kSortThreads) wtab[e] = 0;
     __syncthreads();
-    if (lab >= 0 && rank == 0) wcnt[w * C + lab] = __popc(peers);
+    if (lab >= 0 && rank == 0) wtab[w * C + lab] = __popc(peers);
     __syncthreads();
-    for (int j = tid; j < C; j += kSupThreads) {
-      int run = base[j];
+    // per label, an exclusive scan over the 32 warps (one warp per label)
+    for (int j = w; j < C; j += 32) {
+      const int v = wtab[lane * C + j];
+      int x = v;
 #pragma unroll
-      for (int ww = 0; ww < 8; ++ww) {
-        const int t = wcnt[ww * C + j];
-        wcnt[ww * C + j] = run;
-        run += t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
       }
-      base[j] = run;
+      const int b = base[j];
+      wtab[lane * C + j] = b + x - v;
+      __syncwarp();
+      if (lane == 31) base[j] = b + x;
     }
     __syncthreads();
-    if (lab >= 0) S.perm[wcnt[w * C + lab] + rank] = k;
+    if (lab >= 0) S.perm[wtab[w * C + lab] + rank] = k;
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(kSupThreads) build_supports_kernel(Supports S, const int32_t* u) {
-  build_supports_block(S, u);
+cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, cudaStream_t st) {
+  build_supports_kernel<<<1, kSortThreads, 0, st>>>(S, skip);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_build_supports(const Supports& S, const int32_t* u, cudaStream_t st) {
-  build_supports_kernel<<<1, kSupThreads, 0, st>>>(S, u);
+__global__ void landmark_maps_kernel(Supports S, const int32_t* __restrict__ u) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= S.nL) return;
+  const int l = S.L[k];
+  S.col_ord[l] = k;
+  S.lab[k] = u[l];
+}
+
+cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st) {
+  if (S.nL <= 0) return cudaSuccess;
+  landmark_maps_kernel<<<(unsigned)ceil_div(S.nL, 256), 256, 0, st>>>(S, u);
   return cudaGetLastError();
 }
 
@@ -145,29 +171,33 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
                     float* __restrict__ partial, double* __restrict__ gpart, int n_strips,
                     const int32_t* __restrict__ skip) {
   __shared__ double red[kStreamThreads / 32];
+  __shared__ int rows[kUnitRows];
   if (skip && *skip) return;
   const int unit = blockIdx.y;
-  if (unit >= *S.n_units) return;
+  // unit tables are allocated for max_units entries, so these loads stay in
+  // bounds even for the units this launch does not use
+  const int nu = *S.n_units;
   const int j = S.unit_j[unit], kb = S.unit_kb[unit], ke = S.unit_ke[unit];
+  if (unit >= nu) return;
+  const int nrow = ke - kb;
+  for (int t = threadIdx.x; t < nrow; t += kStreamThreads) rows[t] = S.perm[kb + t];
+  __syncthreads();
   const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * 4;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (col < Ni) {
     const float* base = KT + col;
-    int k = kb;
-    for (; k + 8 <= ke; k += 8) {
-      int p[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) p[q] = __ldg(S.perm + k + q);
+    int k = 0;
+    for (; k + 8 <= nrow; k += 8) {
       float4 v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)p[q] * ldk));
+      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k + q] * ldk));
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
       }
     }
-    for (; k < ke; ++k) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(base + (int64_t)__ldg(S.perm + k) * ldk));
+    for (; k < nrow; ++k) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k] * ldk));
       acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
     *reinterpret_cast<float4*>(partial + (int64_t)unit * ldk + col) = acc;
@@ -236,10 +266,24 @@ __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Suppo
   __syncthreads();
 }
 
+__device__ __forceinline__ float partial_at(const float* __restrict__ partial, int64_t ldk, int un, int i) {
+  return partial[(int64_t)un * ldk + i];
+}
+
 __device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __restrict__ partial,
                                          int64_t ldk, int i, int j) {
   float f = 0.0f;
-  for (int un = sh.su[j]; un < sh.su[j + 1]; ++un) f += partial[(int64_t)un * ldk + i];
+  int un = sh.su[j];
+  const int e = sh.su[j + 1];
+  for (; un + 4 <= e; un += 4) {
+    const float v0 = partial[(int64_t)un * ldk + i], v1 = partial[(int64_t)(un + 1) * ldk + i];
+    const float v2 = partial[(int64_t)(un + 2) * ldk + i], v3 = partial[(int64_t)(un + 3) * ldk + i];
+    f += v0;
+    f += v1;
+    f += v2;
+    f += v3;
+  }
+  for (; un < e; ++un) f += partial[(int64_t)un * ldk + i];
   return f / (float)sh.nj[j];
 }
 
@@ -247,7 +291,7 @@ __global__ void __launch_bounds__(kAssignThreads)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
-              int rebuild) {
+              int trace) {
   __shared__ AssignShared sh;
   __shared__ double red_d[kAssignThreads / 32];
   __shared__ int red_i[kAssignThreads / 32];
@@ -261,16 +305,21 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   double om = 0.0;
   int ch = 0;
   const float inf = __int_as_float(0x7f800000);
-  for (int i = blockIdx.x * kAssignThreads + threadIdx.x; i < Ni; i += gridDim.x * kAssignThreads) {
+  const int i = blockIdx.x * kAssignThreads + threadIdx.x;
+  if (i < Ni) {
     const float ks = kself ? kself[i] : 1.0f;
     float best = inf, second = inf;
     int bj = 0;
-    for (int j = 0; j < C; ++j) {
-      if (sh.nj[j] == 0) {
+    // Clusters with n_j = 0 own no unit; d = +inf for them (never chosen).
+    auto skip_empty = [&](int j) {
+      while (j < C && sh.nj[j] == 0) {
         if (fhat_out) fhat_out[(int64_t)i * C + j] = __int_as_float(0x7fc00000);
-        continue;
+        ++j;
       }
-      const float fh = fhat_of(sh, I.partial, ldk, i, j);
+      return j;
+    };
+    auto finish = [&](int j, float f) {
+      const float fh = f / (float)sh.nj[j];
       if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
       const float dj = ks - 2.0f * fh + sh.ghf[j];
       if (dj < best) {
@@ -280,13 +329,38 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       } else if (dj < second) {
         second = dj;
       }
+    };
+    // The units of cluster j are su[j] .. su[j+1]-1, in cluster order; their
+    // partial sums are added in unit order (the same order for every row).
+    const int U = sh.su[C];
+    int j = skip_empty(0);
+    float f = 0.0f;
+    for (int u0 = 0; u0 < U; u0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = (u0 + q < U) ? partial_at(I.partial, ldk, u0 + q, i) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (u0 + q < U) {
+          f += v[q];
+          if (u0 + q + 1 == sh.su[j + 1]) {
+            finish(j, f);
+            f = 0.0f;
+            j = skip_empty(j + 1);
+          }
+        }
+      }
     }
     const int old = u[i];
     u[i] = bj;
-    ch += (old != bj);
+    if (S.col_ord) {
+      const int k = S.col_ord[i];
+      if (k >= 0) S.lab[k] = bj;
+    }
+    ch = (old != bj);
     if (margin) margin[i] = second - best;
     if (dmin) dmin[i] = best;
-    om += (double)best;
+    om = (double)best;
   }
   om = block_sum(om, red_d);
   ch = block_sum(ch, red_i);
@@ -294,8 +368,10 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     I.omega_part[blockIdx.x] = om;
     I.changed_part[blockIdx.x] = ch;
   }
-  if (!rebuild) return;
-  // last CTA to finish: trace, early-stop flag, supports of the next iteration
+  if (!trace) return;
+  // The last CTA to finish (atomic ticket, no waiting) closes the iteration:
+  // Omega and the number of changed labels in a fixed order, the trace entry
+  // and the early-stop flag.
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
@@ -318,16 +394,15 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     if (early_stop && c == 0) *I.done = 1;
     *I.ticket = 0u;
   }
-  __syncthreads();
-  build_supports_block(S, u);
 }
 
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,
-                          float* fhat_out, double* ghat_out, int early_stop, int rebuild,
+                          float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st) {
-  assign_kernel<<<I.assign_grid, kAssignThreads, 0, st>>>(ldk, Ni, S, I, kself, u, margin, dmin,
-                                                         fhat_out, ghat_out, early_stop, rebuild);
+  if (Ni <= 0) return cudaSuccess;
+  assign_kernel<<<(unsigned)ceil_div(Ni, kAssignThreads), kAssignThreads, 0, st>>>(
+      ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace);
   return cudaGetLastError();
 }
 
@@ -512,61 +587,84 @@ cudaError_t launch_local_to_global(const int32_t* picks, int C, int64_t start, i
 }
 
 // --------------------------------------------------------- k-means++ round
-// One CTA: D2 <- min(D2, max(0, K_ll - 2K(x_l, m) + K_mm)) with the column of
-// the previous pick, an FP64 exclusive scan in index order, then the first
-// index whose running sum exceeds u01 * total (lowest unchosen index when the
-// total is 0).
-constexpr int kKppThreads = 1024;
+// Round r (1..C-1) of kernel k-means++:
+//   kpp_update  D2 <- min(D2, max(0, K_ll - 2K(x_l, m) + K_mm)) with the
+//               kernel column of the previous pick, and an FP64 inclusive
+//               prefix of D2 inside each 256-row block plus the block totals;
+//   kpp_pick    one CTA scans the block totals, takes target = u01 * total
+//               and finds the first index whose running sum exceeds it (the
+//               lowest unchosen index when the total is 0).
+constexpr int kKppThreads = 256;
+
 __global__ void __launch_bounds__(kKppThreads)
-kpp_round_kernel(const float* __restrict__ Kc, int N0, const float* __restrict__ kself,
-                 double* __restrict__ D2, int32_t* __restrict__ picks,
-                 const double* __restrict__ draws, int r) {
+kpp_update_kernel(const float* __restrict__ Kc, int N0, const float* __restrict__ kself,
+                  double* __restrict__ D2, double* __restrict__ P, double* __restrict__ bsum,
+                  const int32_t* __restrict__ picks, int r) {
   __shared__ double wsum[kKppThreads / 32];
-  __shared__ double total_sh;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int l = blockIdx.x * kKppThreads + tid;
   const int m = picks[r - 1];
   const double km = kself ? (double)kself[m] : 1.0;
-  const int per = (N0 + kKppThreads - 1) / kKppThreads;
-  const int lo = min(N0, tid * per), hi = min(N0, lo + per);
-  double loc = 0.0;
-  for (int l = lo; l < hi; ++l) {
+  double dv = 0.0;
+  if (l < N0) {
     const double ks = kself ? (double)kself[l] : 1.0;
     double v = ks - 2.0 * (double)Kc[l] + km;
     v = v > 0.0 ? v : 0.0;
-    const double dv = (r == 1) ? v : fmin(D2[l], v);
+    dv = (r == 1) ? v : fmin(D2[l], v);
     D2[l] = dv;
-    loc += dv;
   }
-  // exclusive block scan of loc
-  double x = loc;
+  double x = dv;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double y = __shfl_up_sync(kFull, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) wsum[w] = x;
-  if (tid == 0) picks[r] = -1;
   __syncthreads();
-  if (w == 0) {
-    double s = wsum[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(kFull, s, o);
-      if (lane >= o) s += y;
+  double off = 0.0;
+  for (int q = 0; q < w; ++q) off += wsum[q];
+  if (l < N0) P[l] = off + x;
+  if (tid == kKppThreads - 1) bsum[blockIdx.x] = off + x;
+}
+
+__global__ void __launch_bounds__(kKppThreads)
+kpp_pick_kernel(const double* __restrict__ D2, const double* __restrict__ P,
+                const double* __restrict__ bsum, int nb, int N0, int32_t* __restrict__ picks,
+                const double* __restrict__ draws, int r) {
+  __shared__ double base_sh, total_sh;
+  __shared__ int blk;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    // running sum over the block totals, in block order
+    double run = 0.0;
+    for (int b = 0; b < nb; ++b) run += bsum[b];
+    total_sh = run;
+    blk = -1;
+    picks[r] = -1;
+    if (run > 0.0) {
+      const double target = draws[r] * run;
+      double acc = 0.0;
+      for (int b = 0; b < nb; ++b) {
+        if (acc <= target && acc + bsum[b] > target) {
+          blk = b;
+          base_sh = acc;
+          break;
+        }
+        acc += bsum[b];
+      }
     }
-    wsum[lane] = s;
-    if (lane == 31) total_sh = s;
   }
   __syncthreads();
-  const double excl = (w > 0 ? wsum[w - 1] : 0.0) + x - loc;
   const double total = total_sh;
-  if (total > 0.0) {
+  if (total > 0.0 && blk >= 0) {
+    // interval [base + P[l-1], base + P[l]) of element l; neighbours share endpoints exactly
     const double target = draws[r] * total;
-    double run = excl;
-    for (int l = lo; l < hi; ++l) {
-      const double nxt = run + D2[l];
-      if (run <= target && nxt > target) picks[r] = l;
-      run = nxt;
+    const double base = base_sh;
+    const int l = blk * kKppThreads + tid;
+    if (l < N0) {
+      const double hi = base + P[l];
+      const double lo = base + (tid > 0 ? P[l - 1] : 0.0);
+      if (lo <= target && hi > target) picks[r] = l;
     }
   }
   __syncthreads();
@@ -588,9 +686,11 @@ kpp_round_kernel(const float* __restrict__ Kc, int N0, const float* __restrict__
   }
 }
 
-cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2,
-                             int32_t* picks, const double* draws, int r, cudaStream_t st) {
-  kpp_round_kernel<<<1, kKppThreads, 0, st>>>(Kc, N0, kself, D2, picks, draws, r);
+cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2, double* P,
+                             double* bsum, int32_t* picks, const double* draws, int r, cudaStream_t st) {
+  const int nb = (int)ceil_div(N0, kKppThreads);
+  kpp_update_kernel<<<nb, kKppThreads, 0, st>>>(Kc, N0, kself, D2, P, bsum, picks, r);
+  kpp_pick_kernel<<<1, kKppThreads, 0, st>>>(D2, P, bsum, nb, N0, picks, draws, r);
   return cudaGetLastError();
 }
 

@@ -200,11 +200,13 @@ const char* kkm_status_string(kkm_status s);
 /* Message of the last failed call on this thread ("" if none). */
 const char* kkm_last_error(void);
 
-/* Per-kernel device timing.  When enabled, every library kernel launch is
- * bracketed by CUDA events on its stream; kkm_prof_read returns the number of
- * launches and the summed device milliseconds of the named kernel since the
- * last reset (0 launches if unknown).  kkm_prof_names writes a
- * comma-separated list of the names seen into buf. */
+/* Per-kernel device timing.  kkm_prof_enable(1): every library kernel launch
+ * is counted and bracketed by CUDA events on its stream; (2): every launch is
+ * counted, only the kernel-block and streaming kernels ("gram_block",
+ * "rmsd_block", "fhat_partial") are bracketed; (0): off.  kkm_prof_read
+ * returns the number of launches and the summed device milliseconds of the
+ * named kernel since the last reset (0 launches if unknown).  kkm_prof_names
+ * writes a comma-separated list of the names seen into buf. */
 void kkm_prof_enable(int32_t on);
 void kkm_prof_reset(void);
 int32_t kkm_prof_read(const char* name, int64_t* launches, double* ms);

@@ -94,7 +94,11 @@ struct Pending {
   cudaEvent_t a, b;
 };
 static std::mutex g_prof_mu;
-static bool g_prof_on = false;
+static int g_prof_on = 0;  // 0 off, 1 time every launch, 2 count all, time the heavy kernels
+
+static bool heavy_kernel(const char* name) {
+  return !strcmp(name, "gram_block") || !strcmp(name, "rmsd_block") || !strcmp(name, "fhat_partial");
+}
 static std::unordered_map<std::string, ProfEntry> g_prof;
 static std::vector<Pending> g_pending;
 static std::vector<cudaEvent_t> g_event_pool;
@@ -113,6 +117,10 @@ static cudaEvent_t take_event() {
 ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_prof_on == 2 && !heavy_kernel(name)) {
+    g_prof[name].launches += 1;
+    return;
+  }
   Pending p{name, take_event(), take_event()};
   cudaEventRecord(p.a, s);
   g_pending.push_back(p);
@@ -403,11 +411,13 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&S.lab, nLmax));
   KKM_TRY(ws.alloc(&lb->n_copy, C));
   I.n_strips = (int)ceil_div(ldk, kStripCols);
-  I.assign_grid = (int)ceil_div(ldk, 128);
+  I.assign_grid = (int)ceil_div(ldk, 32);
   KKM_TRY(ws.alloc(&I.partial, (int64_t)mu * ldk));
   KKM_TRY(ws.alloc(&I.gpart, (int64_t)mu * I.n_strips));
   KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.lm_changed, 1));
   KKM_TRY(ws.alloc(&I.ticket, 1));
   KKM_TRY(ws.alloc(&I.done, 1));
   KKM_TRY(ws.alloc(&I.trace_omega, std::max(trace_cap, 1)));
@@ -631,14 +641,14 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("fill", st, launch_fill_i32(S.col_label, -1, ldk, st));
     KKM_RUN("fill", st, launch_fill_i32(S.col_ord, -1, ldk, st));
     KKM_RUN("landmark_maps", st, launch_landmark_maps(S, u, st));
-    KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, st));
+    KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, nullptr, st));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
                             /*trace=*/1, st));
-      KKM_RUN("build_supports", st, launch_build_supports(S, I.done, st));
+      KKM_RUN("build_supports", st, launch_build_supports(S, I.done, I.lm_changed, st));
     }
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
@@ -954,7 +964,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_label, -1, ldk, st));
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_ord, -1, ldk, st));
   KKM_RUN("landmark_maps", st, launch_landmark_maps(lb.S, u, st));
-  KKM_RUN("build_supports", st, launch_build_supports(lb.S, nullptr, st));
+  KKM_RUN("build_supports", st, launch_build_supports(lb.S, nullptr, nullptr, st));
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
   const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
   KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
@@ -1206,7 +1216,7 @@ const char* kkm_last_error(void) { return g_last_error.c_str(); }
 
 void kkm_prof_enable(int32_t on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  g_prof_on = on != 0;
+  g_prof_on = (on == 1 || on == 2) ? on : 0;
 }
 void kkm_prof_reset(void) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -120,21 +120,25 @@ struct IterState {
   int32_t* trace_changed;// [trace cap]
   int32_t* trace_count;  // [1]
   const double* ghat_in = nullptr;  // g_hat given (assign against a model), else from gpart
+  int32_t* lm_part = nullptr;       // [assign grid] landmark label changes per CTA
+  int32_t* lm_changed = nullptr;    // [1] landmark labels changed by the last assign
   int assign_grid;
   int n_strips;
 };
 
 // Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA);
-// skipped when *skip != 0.
-cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, cudaStream_t st);
+// skipped when *skip != 0 or when *lm_changed == 0 (then nothing changed).
+cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
+                                  cudaStream_t st);
 // col_ord[L[k]] = k (col_ord pre-filled with -1) and lab[k] = u[L[k]].
 cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st);
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st);
-// g_hat, f_hat, distances, argmin, margin, Omega; updates u in place.  With
-// trace != 0 the last CTA also writes the trace entry and the early-stop flag.
-// Uses ceil(Ni/128) CTAs (omega_part/changed_part need that many slots).
+// f_hat, distances, argmin, margin, Omega; updates u in place.  With
+// trace != 0 the last CTA also writes the trace entry, the early-stop flag and
+// the count of changed landmark labels.  Uses ceil(Ni/32) CTAs
+// (omega_part/changed_part/lm_part need that many slots).
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,
                           float* fhat_out, double* ghat_out, int early_stop, int trace,

@@ -25,13 +25,16 @@
 // Every sum has a fixed order, so results are bit-reproducible.
 #include <math.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "internal.h"
 
 namespace kkm {
 
 constexpr int kSortThreads = 1024;  // build_supports: one CTA of 32 warps
-constexpr int kAssignThreads = 128;
+constexpr int kLabRegs = 8;         // landmark labels held in registers per thread
+constexpr int kAssignThreads = 256;
 constexpr int kStreamThreads = kStripCols / 4;
 
 // Exclusive scan of one int per thread over the whole CTA (blockDim a
@@ -69,24 +72,35 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
 // unit tables, perm) and the label of every landmark column.  One CTA of
 // kSortThreads threads; returns at once when the early-stop flag is set.
 __global__ void __launch_bounds__(kSortThreads)
-build_supports_kernel(Supports S, const int32_t* __restrict__ skip) {
+build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
+                      const int32_t* __restrict__ lm_changed) {
   __shared__ int cnt[kMaxC];
   __shared__ int base[kMaxC];
   __shared__ int wtab[32 * kMaxC];
   __shared__ int scan_sh[32];
   if (skip && *skip) return;
+  if (lm_changed && *lm_changed == 0) return;  // same landmark labels: same supports
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int C = S.C, nL = S.nL;
   for (int j = tid; j < C; j += kSortThreads) cnt[j] = 0;
   __syncthreads();
+  // all landmark labels of this thread, loaded at once (kLabRegs per thread;
+  // larger landmark sets reload from global memory in pass 2)
+  int labr[kLabRegs];
+#pragma unroll
+  for (int q = 0; q < kLabRegs; ++q) {
+    const int k = q * kSortThreads + tid;
+    labr[q] = k < nL ? S.lab[k] : -1;
+  }
   // pass 1: counts (one shared atomic per distinct label and warp)
-  for (int start = 0; start < nL; start += kSortThreads) {
+  for (int start = 0, q = 0; start < nL; start += kSortThreads, ++q) {
     const int k = start + tid;
     int lab = -1;
-    if (k < nL) {
-      lab = S.lab[k];
-      S.col_label[S.L[k]] = lab;
-    }
+#pragma unroll
+    for (int qq = 0; qq < kLabRegs; ++qq)
+      if (qq == q) lab = labr[qq];
+    if (q >= kLabRegs) lab = k < nL ? S.lab[k] : -1;
+    if (k < nL) S.col_label[S.L[k]] = lab;
     const unsigned peers = __match_any_sync(kFull, lab);
     if (lab >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[lab], __popc(peers));
   }
@@ -117,9 +131,13 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip) {
   }
   __syncthreads();
   // pass 2: stable scatter, 1024 landmarks at a time in landmark order
-  for (int start = 0; start < nL; start += kSortThreads) {
+  for (int start = 0, q = 0; start < nL; start += kSortThreads, ++q) {
     const int k = start + tid;
-    const int lab = k < nL ? S.lab[k] : -1;
+    int lab = -1;
+#pragma unroll
+    for (int qq = 0; qq < kLabRegs; ++qq)
+      if (qq == q) lab = labr[qq];
+    if (q >= kLabRegs) lab = k < nL ? S.lab[k] : -1;
     const unsigned peers = __match_any_sync(kFull, lab);
     const int rank = __popc(peers & ((1u << lane) - 1u));
     for (int e = tid; e < 32 * C; e += kSortThreads) wtab[e] = 0;
@@ -146,8 +164,9 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip) {
   }
 }
 
-cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, cudaStream_t st) {
-  build_supports_kernel<<<1, kSortThreads, 0, st>>>(S, skip);
+cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
+                                  cudaStream_t st) {
+  build_supports_kernel<<<1, kSortThreads, 0, st>>>(S, skip, lm_changed);
   return cudaGetLastError();
 }
 
@@ -187,10 +206,21 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
   if (col < Ni) {
     const float* base = KT + col;
     int k = 0;
-    for (; k + 8 <= nrow; k += 8) {
+    if (nrow >= 8) {
+      // the loads of the next 8 rows are in flight while the current 8 are added
       float4 v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k + q] * ldk));
+      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[q] * ldk));
+      for (k = 8; k + 8 <= nrow; k += 8) {
+        float4 w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k + q] * ldk));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
+          v[q] = w[q];
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
@@ -232,33 +262,40 @@ struct AssignShared {
   int su[kMaxC + 1];
 };
 
+// n_j, unit ranges and g_hat into shared memory.  g_hat_j is given (assign
+// against a model) or reduced here from the per-(unit, strip) numerators:
+// one warp per cluster, all loads of a lane issued before they are added, in
+// a fixed order.
 __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
-                                                   const double* __restrict__ gpart, int n_strips,
-                                                   const double* __restrict__ ghat_in) {
+                                                   const IterState& I) {
   const int C = S.C;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     sh.nj[j] = S.n_j[j];
     sh.su[j] = S.seg_unit[j];
+    if (I.ghat_in) {
+      sh.gh[j] = I.ghat_in[j];
+      sh.ghf[j] = (float)I.ghat_in[j];
+    }
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
   __syncthreads();
-  if (ghat_in) {
-    for (int j = threadIdx.x; j < C; j += blockDim.x) {
-      sh.gh[j] = ghat_in[j];
-      sh.ghf[j] = (float)ghat_in[j];
-    }
-    __syncthreads();
-    return;
-  }
+  if (I.ghat_in) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ns = I.n_strips;
   for (int j = w; j < C; j += nw) {
-    const int64_t e0 = (int64_t)sh.su[j] * n_strips, e1 = (int64_t)sh.su[j + 1] * n_strips;
-    double s = 0.0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) s += gpart[e];
-    s = warp_sum_f64(s);
+    const int64_t e0 = (int64_t)sh.su[j] * ns, e1 = (int64_t)sh.su[j + 1] * ns;
+    double sacc = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (e + 32 * q < e1) ? I.gpart[e + 32 * q] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sacc += v[q];
+    }
+    sacc = warp_sum_f64(sacc);
     if (lane == 0) {
       const double n = (double)sh.nj[j];
-      const double g = sh.nj[j] > 0 ? s / (n * n) : __longlong_as_double(0x7ff8000000000000LL);
+      const double g = sh.nj[j] > 0 ? sacc / (n * n) : __longlong_as_double(0x7ff8000000000000LL);
       sh.gh[j] = g;
       sh.ghf[j] = (float)g;
     }
@@ -287,41 +324,63 @@ __device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __
   return f / (float)sh.nj[j];
 }
 
-__global__ void __launch_bounds__(kAssignThreads)
+// One CTA per 32 rows: warp w forms d_ij for the clusters j = w, w + nw, ...
+// of its 32 rows (lane = row), each lane adding only the partials of its own
+// cluster (coalesced across the warp); warp 0 then takes the argmin over the
+// clusters from shared memory.
+constexpr int kAssignRows = 32;
+
+__global__ void __launch_bounds__(1024)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
               int trace) {
   __shared__ AssignShared sh;
-  __shared__ double red_d[kAssignThreads / 32];
-  __shared__ int red_i[kAssignThreads / 32];
+  __shared__ float dsh[kMaxC][kAssignRows];
+  __shared__ double red_d[32];
+  __shared__ int red_i[32], red_l[32];
   __shared__ int is_last;
   if (I.done && *I.done) return;
   const int C = S.C;
-  load_cluster_stats(sh, S, I.gpart, I.n_strips, I.ghat_in);
+  load_cluster_stats(sh, S, I);
   if (blockIdx.x == 0 && ghat_out)
     for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
-
-  double om = 0.0;
-  int ch = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int i = blockIdx.x * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
-  const int i = blockIdx.x * kAssignThreads + threadIdx.x;
+  const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
+  for (int j = w; j < C; j += nw) {
+    float dj = inf;
+    if (i < Ni) {
+      if (sh.nj[j] > 0) {
+        const int e = sh.su[j + 1];
+        float f = 0.0f;
+        for (int un = sh.su[j]; un < e; un += 8) {
+          float v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = (un + q < e) ? partial_at(I.partial, ldk, un + q, i) : 0.0f;
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (un + q < e) f += v[q];
+        }
+        const float fh = f / (float)sh.nj[j];
+        if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
+        dj = ks - 2.0f * fh + sh.ghf[j];
+      } else if (fhat_out) {
+        fhat_out[(int64_t)i * C + j] = __int_as_float(0x7fc00000);
+      }
+    }
+    dsh[j][lane] = dj;
+  }
+  __syncthreads();
+  if (w != 0) return;
+  double om = 0.0;
+  int ch = 0, lmc = 0;
   if (i < Ni) {
-    const float ks = kself ? kself[i] : 1.0f;
     float best = inf, second = inf;
     int bj = 0;
-    // Clusters with n_j = 0 own no unit; d = +inf for them (never chosen).
-    auto skip_empty = [&](int j) {
-      while (j < C && sh.nj[j] == 0) {
-        if (fhat_out) fhat_out[(int64_t)i * C + j] = __int_as_float(0x7fc00000);
-        ++j;
-      }
-      return j;
-    };
-    auto finish = [&](int j, float f) {
-      const float fh = f / (float)sh.nj[j];
-      if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
-      const float dj = ks - 2.0f * fh + sh.ghf[j];
+    for (int j = 0; j < C; ++j) {  // lowest j on ties
+      const float dj = dsh[j][lane];
       if (dj < best) {
         second = best;
         best = dj;
@@ -329,69 +388,56 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       } else if (dj < second) {
         second = dj;
       }
-    };
-    // The units of cluster j are su[j] .. su[j+1]-1, in cluster order; their
-    // partial sums are added in unit order (the same order for every row).
-    const int U = sh.su[C];
-    int j = skip_empty(0);
-    float f = 0.0f;
-    for (int u0 = 0; u0 < U; u0 += 16) {
-      float v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = (u0 + q < U) ? partial_at(I.partial, ldk, u0 + q, i) : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (u0 + q < U) {
-          f += v[q];
-          if (u0 + q + 1 == sh.su[j + 1]) {
-            finish(j, f);
-            f = 0.0f;
-            j = skip_empty(j + 1);
-          }
-        }
-      }
     }
     const int old = u[i];
     u[i] = bj;
+    ch = (old != bj);
     if (S.col_ord) {
       const int k = S.col_ord[i];
-      if (k >= 0) S.lab[k] = bj;
+      if (k >= 0) {
+        S.lab[k] = bj;
+        lmc = ch;
+      }
     }
-    ch = (old != bj);
     if (margin) margin[i] = second - best;
     if (dmin) dmin[i] = best;
     om = (double)best;
   }
-  om = block_sum(om, red_d);
-  ch = block_sum(ch, red_i);
-  if (threadIdx.x == 0) {
+  om = warp_sum_f64(om);
+  ch = warp_sum_i32(ch);
+  lmc = warp_sum_i32(lmc);
+  if (lane == 0) {
     I.omega_part[blockIdx.x] = om;
     I.changed_part[blockIdx.x] = ch;
+    if (I.lm_part) I.lm_part[blockIdx.x] = lmc;
   }
   if (!trace) return;
   // The last CTA to finish (atomic ticket, no waiting) closes the iteration:
-  // Omega and the number of changed labels in a fixed order, the trace entry
-  // and the early-stop flag.
+  // Omega and the counts in a fixed order, the trace entry, the early-stop
+  // flag and the landmark-change count read by build_supports.
   __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
+  __syncwarp();
+  if (lane == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  __syncwarp();
   if (!is_last) return;
   __threadfence();
   double o = 0.0;
-  int c = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += kAssignThreads) {
+  int c = 0, lm = 0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) {
     o += __ldcg(I.omega_part + b);
     c += __ldcg(I.changed_part + b);
+    if (I.lm_part) lm += __ldcg(I.lm_part + b);
   }
-  o = block_sum(o, red_d);
-  c = block_sum(c, red_i);
-  if (threadIdx.x == 0) {
+  o = warp_sum_f64(o);
+  c = warp_sum_i32(c);
+  lm = warp_sum_i32(lm);
+  if (lane == 0) {
     const int t = *I.trace_count;
     I.trace_omega[t] = o;
     I.trace_changed[t] = c;
     *I.trace_count = t + 1;
     if (early_stop && c == 0) *I.done = 1;
+    if (I.lm_changed) *I.lm_changed = lm;
     *I.ticket = 0u;
   }
 }
@@ -401,7 +447,8 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st) {
   if (Ni <= 0) return cudaSuccess;
-  assign_kernel<<<(unsigned)ceil_div(Ni, kAssignThreads), kAssignThreads, 0, st>>>(
+  const int threads = 32 * std::min(S.C, 32);
+  assign_kernel<<<(unsigned)ceil_div(Ni, kAssignRows), threads, 0, st>>>(
       ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace);
   return cudaGetLastError();
 }
@@ -446,7 +493,7 @@ medoid_keys_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __
     bkey[j] = ~0ull;
     bcnt[j] = 0;
   }
-  load_cluster_stats(sh, S, I.gpart, I.n_strips, I.ghat_in);
+  load_cluster_stats(sh, S, I);
   if (blockIdx.x == 0 && ghat_out)
     for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   for (int i = blockIdx.x * kAssignThreads + threadIdx.x; i < Ni; i += gridDim.x * kAssignThreads) {

@@ -335,7 +335,8 @@ def kkm_minibatch_plan(N, B, s, seed, batch, sampling="stride"):
 
 # ------------------------------------------------------------- profiling
 def prof_enable(on=True):
-    load().kkm_prof_enable(1 if on else 0)
+    """True/1: time every launch; 2: count every launch, time the heavy kernels."""
+    load().kkm_prof_enable(int(on) if not isinstance(on, bool) else (1 if on else 0))
 
 
 def prof_reset():

@@ -49,7 +49,11 @@ typedef enum kkm_status {
  *   KKM_LINEAR K(x,y) = x . y  (kernel k-means then equals Lloyd k-means)   */
 typedef enum kkm_kernel_kind { KKM_RBF = 0, KKM_RMSD = 1, KKM_LINEAR = 2 } kkm_kernel_kind;
 
-/* Arithmetic of the kernel-block evaluation.  KKM_FP32 is the plain path. */
+/* Arithmetic of the kernel-block evaluation K(X^i, L).  KKM_FP32 is the
+ * plain FFMA path.  KKM_BF16 (RBF and linear kernels) runs the Gram product
+ * on the tensor cores from BF16-rounded rows with FP32 accumulation; the
+ * C-column blocks (Eq. 8, 12, k-means++) and all sums stay FP32/FP64.
+ * KKM_FP8 is reserved. */
 typedef enum kkm_precision { KKM_FP32 = 0, KKM_BF16 = 1, KKM_FP8 = 2 } kkm_precision;
 
 /* Mini-batch fetching (Section 3.1): stride X^i = {x_(i+jB)}; block = B
@@ -150,10 +154,13 @@ void kkm_model_free(kkm_model* m);
 
 /* kkm_kernel_matrix -- out[a][b] = K(A_a, B_b) for A [nA][d], B [nB][d]
  * (the kernel-block evaluation of Alg. 1 line 3 as a standalone call).
- * out is [nA][nB] float32, device or host.  sigma must be > 0. */
+ * out is [nA][nB] float32, device or host.  sigma must be > 0.
+ * precision KKM_BF16 (RBF and linear kernels) evaluates the product on the
+ * tensor cores from BF16-rounded rows with FP32 accumulation; the result is
+ * then the kernel of the rounded rows. */
 kkm_status kkm_kernel_matrix(const float* A, int64_t nA, const float* Bm,
                              int64_t nB, int64_t d, const kkm_kernel* k,
-                             float* out, void* stream);
+                             int32_t precision, float* out, void* stream);
 
 /* kkm_median_bandwidth -- the bandwidth rule kkm_fit applies when sigma <= 0:
  * the lower median of the pairwise distances (Euclidean, or RMSD for

@@ -272,6 +272,7 @@ static unsigned blocks_for(int64_t n, int t = 256) { return (unsigned)std::max<i
 // Kernel-function dispatch (RBF / linear via the Gram product, MD via RMSD)
 // ======================================================================
 struct KernelSpec {
+  int precision = KKM_FP32;
   int kind;       // kkm_kernel_kind
   float sigma;
   int n_atoms;
@@ -342,6 +343,33 @@ static kkm_status kernel_block(const KernelSpec& sp, const float* A, const float
     KKM_RUN(block ? "gram_block" : "gram", st,
             launch_gram(dk, A, nA, Bm, nB, sp.dp, auxA, auxB, idA, idB, sp.neg_scale(), out, ldo, st));
   }
+  return KKM_OK;
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+    cudaGetLastError();
+  }
+  return n;
+}
+
+// The kernel block on the tensor cores: P (reference rows) and Q (sample
+// rows) are prepared FP32 rows; their BF16 copies and rounded norms go to the
+// given scratch.  out[n*ldo + m] = K(P_n, Q_m).
+static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const int64_t* idP, int64_t nP,
+                                    const float* Q, const int64_t* idQ, int64_t nQ, float* out, int64_t ldo,
+                                    __nv_bfloat16* Pb, float* nPb, __nv_bfloat16* Qb, float* nQb, int* err,
+                                    cudaStream_t st) {
+  KKM_RUN("to_bf16", st, launch_to_bf16(P, nP, sp.dp, Pb, nPb, st));
+  KKM_RUN("to_bf16", st, launch_to_bf16(Q, nQ, sp.dp, Qb, nQb, st));
+  const int dk = (int)sp.d;
+  KKM_RUN("gram_block", st,
+          launch_gram_tc(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Pb, nP, Qb, nQ, dk, sp.dp, nPb, nQb, idP, idQ,
+                         sp.neg_scale(), out, ldo, err, sm_count(), st));
   return KKM_OK;
 }
 
@@ -482,9 +510,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   if (iters < 0) return invalid("iters must be >= 0");
   if (opt.reserved != 0) return invalid("options.reserved must be 0");
   if (opt.sampling != KKM_STRIDE && opt.sampling != KKM_BLOCK) return invalid("unknown sampling");
-  if (opt.precision != KKM_FP32) return invalid("only KKM_FP32 is available in this build");
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
+  if (opt.precision != KKM_FP32 && opt.precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
+  if (opt.precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  sp.precision = opt.precision;
   if (sp.kind != KKM_LINEAR && !isfinite(sp.sigma)) return invalid("sigma must be finite");
   const std::vector<BatchGeom> geo = batch_geometry(N, B, opt.sampling);
   int64_t Nmax = 0, Nmin = INT64_MAX, nLmax = 0;
@@ -590,6 +620,17 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(ws.alloc(&rowbuf, sp.dp));
   KKM_TRY(ws.alloc(&rowaux, 1));
   KKM_TRY(ws.alloc(&kcol, ldk));
+  __nv_bfloat16 *Xib = nullptr, *XLb = nullptr;
+  float *nXib = nullptr, *nXLb = nullptr;
+  int* tc_err = nullptr;
+  if (sp.precision == KKM_BF16) {
+    KKM_TRY(ws.alloc(&Xib, Nmax * sp.dp));
+    KKM_TRY(ws.alloc(&XLb, nLmax * sp.dp));
+    KKM_TRY(ws.alloc(&nXib, Nmax));
+    KKM_TRY(ws.alloc(&nXLb, nLmax));
+    KKM_TRY(ws.alloc(&tc_err, 1));
+    KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
+  }
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
   Supports& S = lb.S;
@@ -624,7 +665,10 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
     KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
-    KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));  // Alg. 1 line 3
+    if (sp.precision == KKM_BF16)                                                // Alg. 1 line 3
+      KKM_TRY(kernel_block_bf16(sp, XL, gidL, nL, Xi, gid, Ni, KT, ldk, XLb, nXLb, Xib, nXib, tc_err, st));
+    else
+      KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));
 
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
       KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, st));
@@ -758,7 +802,13 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   }
   if (labels_on_host)
     KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+  int tc_err_h = 0;
+  if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
+  if (tc_err_h) {
+    set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
+    return KKM_ETIMEOUT;
+  }
   if (model_out && *model_out) {
     kkm_model* m = *model_out;
     // medoid coordinates in the caller's layout
@@ -880,9 +930,12 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
 // kkm_kernel_matrix
 // ======================================================================
 static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float* B_in, int64_t nB, int64_t d,
-                                     const kkm_kernel* k, float* out, cudaStream_t st) {
+                                     const kkm_kernel* k, int32_t precision, float* out, cudaStream_t st) {
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
+  if (precision != KKM_FP32 && precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
+  if (precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  sp.precision = precision;
   if (nA < 0 || nB < 0 || nA > INT32_MAX || nB > INT32_MAX) return invalid("bad sizes");
   if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
   if (nA == 0 || nB == 0) return KKM_OK;
@@ -903,10 +956,29 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
   if (host_out) KKM_TRY(ws.alloc(&o, nA * nB)); else o = out;
   KKM_TRY(prep_rows(sp, A, 0, 1, nA, Ap, aA, st));
   KKM_TRY(prep_rows(sp, Bm, 0, 1, nB, Bp, aB, st));
-  KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
+  int tc_err_h = 0;
+  if (precision == KKM_BF16) {
+    __nv_bfloat16 *Ab, *Bb;
+    float *nAb, *nBb;
+    int* err;
+    KKM_TRY(ws.alloc(&Ab, nA * sp.dp));
+    KKM_TRY(ws.alloc(&Bb, nB * sp.dp));
+    KKM_TRY(ws.alloc(&nAb, nA));
+    KKM_TRY(ws.alloc(&nBb, nB));
+    KKM_TRY(ws.alloc(&err, 1));
+    KKM_CK(cudaMemsetAsync(err, 0, 4, st));
+    KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nullptr, nB, o, nB, Ab, nAb, Bb, nBb, err, st));
+    KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
+  } else {
+    KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
+  }
   if (host_out) KKM_CK(cudaMemcpyAsync(out, o, (size_t)nA * nB * 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
   prof_collect();
+  if (tc_err_h) {
+    set_error("tensor-core kernel block: a bounded pipeline wait gave up");
+    return KKM_ETIMEOUT;
+  }
   return KKM_OK;
 }
 
@@ -1121,9 +1193,9 @@ kkm_status kkm_model_trace(const kkm_model* m, double* omega, int32_t* changed, 
 void kkm_model_free(kkm_model* m) { delete m; }
 
 kkm_status kkm_kernel_matrix(const float* A, int64_t nA, const float* Bm, int64_t nB, int64_t d, const kkm_kernel* k,
-                             float* out, void* stream) {
+                             int32_t precision, float* out, void* stream) {
   set_error("");
-  return guarded([&] { return kernel_matrix_impl(A, nA, Bm, nB, d, k, out, (cudaStream_t)stream); });
+  return guarded([&] { return kernel_matrix_impl(A, nA, Bm, nB, d, k, precision, out, (cudaStream_t)stream); });
 }
 
 kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d, const kkm_kernel* k, uint64_t seed,

@@ -1,0 +1,406 @@
+// Kernel-block evaluation on the 5th-generation tensor cores (tcgen05) in
+// BF16 with FP32 accumulation (the precision option KKM_BF16).
+//
+//   out[n][m] = kappa(P_n, Q_m),  kappa = exp(-max(0, |p|^2 + |q|^2 - 2 p.q) / (2 sigma^2))
+//
+// with P the reference rows (landmarks) and Q the sample rows, both BF16 and
+// K-major in HBM.  The product Q P^T runs as tcgen05.mma kind::f16 (M = 128
+// sample rows, N = 256 reference rows, K = 16 per instruction) from
+// shared-memory tiles that TMA fills with the 128-byte swizzle, into an FP32
+// accumulator in tensor memory.  The epilogue reads the accumulator with
+// tcgen05.ld (thread = sample row, so every column is a coalesced 128-byte
+// store of the transposed block) and applies the norms and the exponential.
+//
+// The squared norms passed in are those of the BF16-rounded rows, so
+// |p|^2 + |q|^2 - 2 p.q is the squared distance of the rounded vectors up to
+// FP32 accumulation: its error scales with |p - q|, not with the norms, and
+// near-duplicate pairs do not cancel catastrophically.
+//
+// Structure: persistent CTAs (one per SM), 6 warps:
+//   warp 0      TMA producer (one elected lane), 4-stage ring of 48 KB stages
+//   warp 1      TMEM owner (allocates all 512 columns) and MMA issuer
+//   warps 2..5  epilogue, one TMEM lane quarter each
+// Two accumulators of 256 columns let the epilogue of one tile overlap the
+// MMAs of the next.  Every mbarrier wait is bounded: on timeout the kernel
+// records an error code, stops issuing work, and still frees its tensor
+// memory before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace kkm {
+
+constexpr int TC_M = 128;          // sample rows per tile (UMMA M)
+constexpr int TC_N = 256;          // reference rows per tile (UMMA N)
+constexpr int TC_K = 64;           // K elements per stage (one 128-byte swizzle row)
+constexpr int TC_STAGES = 4;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2;   // 16 KB
+constexpr int TC_B_BYTES = TC_N * TC_K * 2;   // 32 KB
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_THREADS = 192;
+constexpr int TC_TMEM_COLS = 512;
+constexpr uint32_t TC_SPIN_LIMIT = 1u << 24;  // bounded mbarrier waits
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 2048;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < TC_SPIN_LIMIT; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 1023u) == 1023u && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile of 128-byte rows with
+// the 128-byte swizzle (8-row atoms, 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address
+  d |= (uint64_t)1 << 16;                          // leading-dimension byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride between 8-row atoms
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = TC_N, M = TC_M.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+struct TcShared {
+  uint64_t full[TC_STAGES];
+  uint64_t empty[TC_STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint32_t tmem_base;
+  int abort_flag;
+  float nP[4][TC_N];        // reference norms of the current tile, per epilogue warp
+  long long idP[4][TC_N];   // reference ids of the current tile
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
+               int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
+               const int64_t* __restrict__ idQ, const int64_t* __restrict__ idP, float neg_scale,
+               float* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // stages must start on a 1024-byte boundary (swizzle atom)
+  uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ TcShared sh;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles_m = (nQ + TC_M - 1) / TC_M, tiles_n = (nP + TC_N - 1) / TC_N;
+  const int n_tiles = tiles_m * tiles_n;
+  const int nk = (dk + TC_K - 1) / TC_K;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.tfull[b], 1);
+      mbar_init(&sh.tempty[b], 4);
+    }
+    sh.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(&sh.tmem_base, TC_TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        const int tm = t % tiles_m, tn = t / tiles_m;
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&sh.empty[s], ph ^ 1u, &sh.abort_flag)) {
+            ok = false;
+            break;
+          }
+          uint8_t* a = stages + (size_t)s * TC_STAGE_BYTES;
+          uint8_t* b = a + TC_A_BYTES;
+          mbar_expect_tx(&sh.full[s], TC_STAGE_BYTES);
+          tma_load_2d(&mapQ, &sh.full[s], a, kb * TC_K, tm * TC_M);
+          tma_load_2d(&mapP, &sh.full[s], b, kb * TC_K, tn * TC_N);
+          if (++s == TC_STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        atomicExch(err, 1);
+        sh.abort_flag = 1;
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      int lt = 0;
+      const uint32_t idesc = tc_idesc();
+      for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
+        const int buf = lt & 1;
+        const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
+        if (!mbar_wait(&sh.tempty[buf], tph ^ 1u, &sh.abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)(buf * TC_N);
+        for (int kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(&sh.full[s], ph, &sh.abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(stages + (size_t)s * TC_STAGE_BYTES);
+          const uint32_t b = a + TC_A_BYTES;
+#pragma unroll
+          for (int k = 0; k < TC_K / 16; ++k)
+            umma_bf16(d_tmem, sw128_desc(a + k * 32), sw128_desc(b + k * 32), idesc, (kb | k) != 0);
+          umma_commit(&sh.empty[s]);
+          if (++s == TC_STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (ok) umma_commit(&sh.tfull[buf]);
+      }
+      if (!ok) {
+        atomicExch(err, 2);
+        sh.abort_flag = 1;
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5)
+    const int q = warp & 3;             // TMEM lane quarter of this warp
+    const int ew = warp - 2;            // epilogue warp index 0..3
+    int lt = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      const int tm = t % tiles_m, tn = t / tiles_m;
+      const int buf = lt & 1;
+      const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
+      // reference norms and ids of this tile (each warp keeps its own copy)
+      for (int c = lane; c < TC_N; c += 32) {
+        const int n = tn * TC_N + c;
+        sh.nP[ew][c] = n < nP ? normP[n] : 0.0f;
+        sh.idP[ew][c] = (idP && n < nP) ? (long long)idP[n] : -1ll;
+      }
+      __syncwarp();
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(&sh.tfull[buf], tph, &sh.abort_flag);
+      ok = __shfl_sync(kFull, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(err, 3);
+          sh.abort_flag = 1;
+        }
+        break;
+      }
+      tc_fence_after();
+      const int m = tm * TC_M + q * 32 + lane;
+      const bool mvalid = m < nQ;
+      const float nq = mvalid ? normQ[m] : 0.0f;
+      const long long iq = (idQ && mvalid) ? (long long)idQ[m] : -2ll;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TC_N; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tbase + (uint32_t)c0, r);
+        if (mvalid) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int n = tn * TC_N + c0 + c;
+            if (n < nP) {
+              const float dot = __uint_as_float(r[c]);
+              const float d2 = fmaxf(nq + sh.nP[ew][c0 + c] - 2.0f * dot, 0.0f);
+              const bool same = sh.idP[ew][c0 + c] == iq;
+              float v;
+              if (KIND == DK_DIST) v = same ? 0.0f : sqrtf(d2);
+              else if (KIND == DK_LINEAR) v = dot;
+              else v = same ? 1.0f : exp2f(d2 * neg_scale);
+              out[(int64_t)n * ldo + m] = v;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.tempty[buf]);
+    }
+  }
+  // teardown: every role is done issuing; the TMEM owner frees tensor memory
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TC_TMEM_COLS);
+  }
+}
+
+// ------------------------------------------------------------ host side
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][ld] (ld elements per row, ld*2 a
+// multiple of 16 bytes), box = box_rows x TC_K, 128-byte swizzle, zero fill.
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
+                           int dk, int ldb, const float* normP, const float* normQ, const int64_t* idP,
+                           const int64_t* idQ, float neg_scale, float* out, int64_t ldo, int* err,
+                           int n_sms, cudaStream_t st) {
+  if (nP <= 0 || nQ <= 0) return cudaSuccess;
+  if ((ldb * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15))
+    return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap mq, mp;
+  if (!make_map(&mq, Q, nQ, dk, ldb, TC_M) || !make_map(&mp, P, nP, dk, ldb, TC_N)) return cudaErrorInvalidValue;
+  const int64_t tiles = ceil_div(nQ, TC_M) * ceil_div(nP, TC_N);
+  const int grid = (int)std::min<int64_t>(tiles, std::max(n_sms, 1));
+  cudaError_t e;
+#define KKM_TC_LAUNCH(K)                                                                             \
+  e = cudaFuncSetAttribute(gram_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
+  if (e != cudaSuccess) return e;                                                                    \
+  gram_tc_kernel<K><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, (int)nQ, (int)nP, dk, normQ, normP, idQ, idP, \
+                                                       neg_scale, out, ldo, err);
+  if (kind == DK_DIST) {
+    KKM_TC_LAUNCH(DK_DIST)
+  } else if (kind == DK_LINEAR) {
+    KKM_TC_LAUNCH(DK_LINEAR)
+  } else {
+    KKM_TC_LAUNCH(DK_RBF)
+  }
+#undef KKM_TC_LAUNCH
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ FP32 rows -> BF16 rows
+// dst[r][c] = bf16(src[r][c]) for c < dp, and the squared norm of the rounded
+// row (FP64 accumulation) in normsq.
+__global__ void to_bf16_kernel(const float* __restrict__ src, int64_t n, int dp, __nv_bfloat16* __restrict__ dst,
+                               float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float* s = src + row * dp;
+  __nv_bfloat16* d = dst + row * dp;
+  double acc = 0.0;
+  for (int c = lane; c < dp; c += 32) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(s[c]);
+    d[c] = b;
+    const double v = (double)__bfloat162float(b);
+    acc += v * v;
+  }
+  acc = warp_sum_f64(acc);
+  if (normsq && lane == 0) normsq[row] = (float)acc;
+}
+
+cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  to_bf16_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(src, n, dp, dst, normsq);
+  return cudaGetLastError();
+}
+
+}  // namespace kkm

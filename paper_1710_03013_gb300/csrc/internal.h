@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -73,6 +74,18 @@ cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, i
                         int dp, const float* normA, const float* normB, const int64_t* idA,
                         const int64_t* idB, float neg_scale, float* out, int64_t ldo,
                         cudaStream_t st);
+
+// ---- tensor-core (tcgen05) BF16 kernel block ----------------------------
+// out[n*ldo + m] = kappa(P_n, Q_m) for BF16 rows P [nP][ldb], Q [nQ][ldb]
+// (dk valid columns), with the squared norms of the BF16 rows.  *err gets a
+// nonzero code if a bounded wait gave up.
+cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
+                           int dk, int ldb, const float* normP, const float* normQ, const int64_t* idP,
+                           const int64_t* idQ, float neg_scale, float* out, int64_t ldo, int* err,
+                           int n_sms, cudaStream_t st);
+// BF16 copy of FP32 rows [n][dp] with the squared norms of the rounded rows.
+cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq,
+                           cudaStream_t st);
 
 // ---- MD kernel (RMSD) -----------------------------------------------------
 // Frames [n][n_atoms][3] (rows start + l*step of X) -> centred SoA [n][3][ap]

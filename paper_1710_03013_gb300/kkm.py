@@ -59,7 +59,7 @@ _SIGNATURES = {
     "kkm_model_supports": (_I32, [_P, _P, _P, _P]),
     "kkm_model_trace": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "kkm_model_free": (None, [_P]),
-    "kkm_kernel_matrix": (_I32, [_P, _I64, _P, _I64, _I64, ctypes.POINTER(kkm_kernel), _P, _P]),
+    "kkm_kernel_matrix": (_I32, [_P, _I64, _P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _P, _P]),
     "kkm_median_bandwidth": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _U64,
                                     ctypes.POINTER(_F32)]),
     "kkm_debug_step": (_I32, [_P, _I64, _I64, _P, _I32, ctypes.POINTER(kkm_kernel), _I32, _P, _P, _P,
@@ -249,7 +249,7 @@ def kkm_cost(model, X, mode="supports", stream=None):
     return out.value
 
 
-def kkm_kernel_matrix(A, B, kind="rbf", sigma=1.0, n_atoms=0, stream=None):
+def kkm_kernel_matrix(A, B, kind="rbf", sigma=1.0, n_atoms=0, precision=KKM_FP32, stream=None):
     """kkm_kernel_matrix of the C ABI: K(A, B) as [len(A)][len(B)] float32."""
     lib = load()
     nA, nB = int(A.shape[0]), int(B.shape[0])
@@ -265,7 +265,7 @@ def kkm_kernel_matrix(A, B, kind="rbf", sigma=1.0, n_atoms=0, stream=None):
         op = ctypes.c_void_p(out.ctypes.data)
     k = _kernel(kind, sigma, n_atoms)
     st = stream if stream is not None else _stream_of(A)
-    _check(lib.kkm_kernel_matrix(ap, nA, bp, nB, d, ctypes.byref(k), op, st))
+    _check(lib.kkm_kernel_matrix(ap, nA, bp, nB, d, ctypes.byref(k), int(precision), op, st))
     del ka, kb
     return out
 

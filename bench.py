@@ -203,11 +203,14 @@ def run_ours(args, cfg, X):
     stream = torch.cuda.current_stream(dev)
     C, B, s, iters, seed = cfg["C"], cfg["B"], cfg["s"], cfg["iters"], cfg["seed"]
 
-    def step():
-        return kkm.kkm_fit(Xd, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False)
+    BF16, FP32 = kkm.KKM_BF16, kkm.KKM_FP32
+
+    def step(prec=BF16):
+        return kkm.kkm_fit(Xd, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False, precision=prec)
 
     for _ in range(args.warmup):
-        lab, model = step()
+        lab, model = step(BF16)
+        lab32, model32 = step(FP32)
     torch.cuda.synchronize()
 
     def barrier():
@@ -215,24 +218,34 @@ def run_ours(args, cfg, X):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # timed region 1: the headline value (no per-kernel instrumentation)
+    def timed(prec, n):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(n):
+            out = step(prec)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / n, out
+
+    # timed region 1: the headline value (tensor-core BF16 kernel block, no instrumentation)
     with ClockSampler(local) as clk:
-        barrier()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            lab, model = step()
-        ev1.record(stream)
-        barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    # timed region 2: the same steps; every library launch is counted and the
-    # kernel-block and streaming kernels are bracketed by CUDA events on their
-    # stream (their durations feed the roofline)
+        ms, (lab, model) = timed(BF16, args.steps)
+    # the plain FP32 path on the same workload, for comparison
+    ms32, (lab32, model32) = timed(FP32, args.steps)
+    agree = float((lab == lab32).float().mean().item())
+    om16, _ = model.trace()
+    om32, _ = model32.trace()
+    omega_rel = float(np.max(np.abs(om16 - om32) / np.abs(om32))) if len(om32) else None
+    # timed region 2: the same BF16 steps; every library launch is counted and
+    # the kernel-block and streaming kernels are bracketed by CUDA events on
+    # their stream (their durations feed the roofline)
     kkm.prof_reset()
     kkm.prof_enable(2)
     barrier()
     for _ in range(args.steps):
-        lab, model = step()
+        lab, model = step(BF16)
     barrier()
     kkm.prof_enable(False)
     prof = {n: kkm.prof_read(n) for n in kkm.prof_names()}
@@ -240,14 +253,14 @@ def run_ours(args, cfg, X):
     # one more step with every launch timed, for the per-kernel breakdown
     kkm.prof_reset()
     kkm.prof_enable(1)
-    lab, model = step()
+    lab, model = step(BF16)
     torch.cuda.synchronize()
     kkm.prof_enable(False)
     breakdown = {n: kkm.prof_read(n)[1] for n in kkm.prof_names()}
     if world > 1:
-        t = torch.tensor([ms], device=dev)
+        t = torch.tensor([ms, ms32], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, ms32 = float(t[0].item()), float(t[1].item())
 
     evals = fit_evals(cfg["N"], B, C, s)
     value = world * evals / (ms / 1e3)
@@ -260,7 +273,7 @@ def run_ours(args, cfg, X):
         barrier()
         t0 = time.perf_counter()
         lab_h, _ = kkm.kkm_fit(Xh, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False,
-                               stream=ctypes_stream(stream))
+                               precision=BF16, stream=ctypes_stream(stream))
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append(1e3 * (t1 - t0))
@@ -286,9 +299,10 @@ def run_ours(args, cfg, X):
         flops = sum(2.0 * ((cfg["N"] - i + B - 1) // B) * n_landmarks((cfg["N"] - i + B - 1) // B, s)
                     * cfg["d"] for i in range(B)) / B
         ach = flops / (tms / n / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / PEAK_FP32_TFLOPS, "traffic": ncu_traffic("gram_block"),
-                "kernel": "gram_block", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                "traffic": ncu_traffic("gram_block"), "kernel": "gram_block (tcgen05 BF16)",
+                "peak_source": peak_kind + " bf16 sustained",
                 "work_per_launch": f"2*N_i*|L|*d = {flops:.4g} flop"}
     elif dom == "fhat_partial":
         n, tms = prof[dom]
@@ -309,12 +323,16 @@ def run_ours(args, cfg, X):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16 products, f32 accumulation and sums, f64 cost",
+        "data": "synthetic",
         "config": {"workload": cfg["name"], "N": cfg["N"], "d": cfg["d"], "C": C, "B": B, "s": s,
-                   "iters_per_minibatch": iters, "precision": "fp32", "bandwidth": "median rule inside the fit",
+                   "iters_per_minibatch": iters, "precision": "bf16 tensor-core kernel block, FP32 near-tie re-score", "bandwidth": "median rule inside the fit",
                    "l2": "inputs larger than L2 (X 188 MB, kernel block 180 MB); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "iters_per_s": world * B * iters / (ms / 1e3),
+        "fp32_path": {"value": world * evals / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+                      "iters_per_s": world * B * iters / (ms32 / 1e3)},
+        "matched_labels": {"fraction_equal_to_fp32_path": agree, "omega_max_rel_diff": omega_rel},
         "inner_iter_ms": it_ms / (B * iters),
         "evals_per_step": evals,
         "e2e": {"value": world * evals / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e,

@@ -360,18 +360,38 @@ static int sm_count() {
 // The kernel block on the tensor cores: P (reference rows) and Q (sample
 // rows) are prepared FP32 rows; their BF16 copies and rounded norms go to the
 // given scratch.  out[n*ldo + m] = K(P_n, Q_m).
-static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const int64_t* idP, int64_t nP,
-                                    const float* Q, const int64_t* idQ, int64_t nQ, float* out, int64_t ldo,
-                                    __nv_bfloat16* Pb, float* nPb, __nv_bfloat16* Qb, float* nQb, int* err,
-                                    cudaStream_t st) {
+// L (nullable): local sample positions of the reference rows; their diagonal
+// entries are then set to exactly 1 (Gaussian kernels).
+static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const int32_t* L, int64_t nP,
+                                    const float* Q, int64_t nQ, float* out, int64_t ldo, __nv_bfloat16* Pb,
+                                    float* nPb, __nv_bfloat16* Qb, float* nQb, int* err, cudaStream_t st) {
   KKM_RUN("to_bf16", st, launch_to_bf16(P, nP, sp.dp, Pb, nPb, st));
   KKM_RUN("to_bf16", st, launch_to_bf16(Q, nQ, sp.dp, Qb, nQb, st));
   const int dk = (int)sp.d;
   KKM_RUN("gram_block", st,
-          launch_gram_tc(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Pb, nP, Qb, nQ, dk, sp.dp, nPb, nQb, idP, idQ,
+          launch_gram_tc(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Pb, nP, Qb, nQ, dk, sp.dp, nPb, nQb,
                          sp.neg_scale(), out, ldo, err, sm_count(), st));
+  if (L && sp.kind != KKM_LINEAR) KKM_RUN("set_diag", st, launch_set_diag(out, ldo, L, (int)nP, st));
   return KKM_OK;
 }
+
+int l2_keep_rows(int64_t ldk, int rows, double share) {
+  static int l2 = -1;
+  if (l2 < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+    cudaGetLastError();
+  }
+  const double row_bytes = (double)ldk * 4.0;
+  return (int)std::min<double>(rows, std::floor(share * (double)l2 / row_bytes));
+}
+
+// Rows whose low-precision margin d2 - d1 is below this fraction of
+// max(|d2|, K_ii + g_hat) are re-scored with exact FP32 kernel values.
+constexpr float kRescoreMargin = 1e-3f;
+// Share of L2 given to kernel-block rows that stay resident through the inner loop.
+constexpr double kL2KeepShare = 0.70;
 
 // ======================================================================
 // Bandwidth rule
@@ -446,6 +466,14 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_changed, 1));
+  KKM_TRY(ws.alloc(&I.flag_rows, (int64_t)I.assign_grid * 32));
+  KKM_TRY(ws.alloc(&I.flag_old, (int64_t)I.assign_grid * 32));
+  KKM_TRY(ws.alloc(&I.flag_d, (int64_t)I.assign_grid * 32));
+  KKM_TRY(ws.alloc(&I.flag_cnt, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.nflag, 1));
+  KKM_TRY(ws.alloc(&I.ticket_sink, 1));
+  KKM_CK(cudaMemsetAsync(I.nflag, 0, 4, ws.st));
+  KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.ticket, 1));
   KKM_TRY(ws.alloc(&I.done, 1));
   KKM_TRY(ws.alloc(&I.trace_omega, std::max(trace_cap, 1)));
@@ -666,9 +694,18 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
     KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
     if (sp.precision == KKM_BF16)                                                // Alg. 1 line 3
-      KKM_TRY(kernel_block_bf16(sp, XL, gidL, nL, Xi, gid, Ni, KT, ldk, XLb, nXLb, Xib, nXib, tc_err, st));
+      KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, KT, ldk, XLb, nXLb, Xib, nXib, tc_err, st));
     else
       KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));
+    // L2 hygiene for the inner loop: the BF16 copies are not read again
+    // (dropped), the FP32 rows only by the few boundary steps (evict first),
+    // so the block rows kept with evict_last own the cache.
+    if (Xib) {
+      KKM_RUN("l2_hygiene", st, launch_l2_discard(Xib, (int64_t)Ni * sp.dp * 2, st));
+      KKM_RUN("l2_hygiene", st, launch_l2_discard(XLb, (int64_t)nL * sp.dp * 2, st));
+    }
+    KKM_RUN("l2_hygiene", st, launch_l2_demote(Xi, (int64_t)Ni * sp.dp * 4, I.ticket_sink, st));
+    KKM_RUN("l2_hygiene", st, launch_l2_demote(XL, (int64_t)nL * sp.dp * 4, I.ticket_sink, st));
 
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
       KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, st));
@@ -687,17 +724,27 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("landmark_maps", st, launch_landmark_maps(S, u, st));
     KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, nullptr, st));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
+    const bool rescore = sp.precision != KKM_FP32;
+    I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare);
+    I.flag_tau = rescore ? kRescoreMargin : 0.0f;
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
+      KKM_RUN("ghat_reduce", st, launch_ghat_reduce(S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
                             /*trace=*/1, st));
+      if (rescore)
+        KKM_RUN("rescore", st,
+                launch_rescore(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Ni, sp.dp, Xi, aux_i, XL, auxL,
+                               sp.neg_scale(), S, I, kself, u, opt.early_stop, st));
       KKM_RUN("build_supports", st, launch_build_supports(S, I.done, I.lm_changed, st));
     }
+    I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
     Ifin.done = nullptr;
     KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, Ifin, st));
+    KKM_RUN("ghat_reduce", st, launch_ghat_reduce(S, Ifin, st));
     KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
     KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, st));
     KKM_RUN("medoid_keys", st, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, st));
@@ -967,7 +1014,7 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
     KKM_TRY(ws.alloc(&nBb, nB));
     KKM_TRY(ws.alloc(&err, 1));
     KKM_CK(cudaMemsetAsync(err, 0, 4, st));
-    KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nullptr, nB, o, nB, Ab, nAb, Bb, nBb, err, st));
+    KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nB, o, nB, Ab, nAb, Bb, nBb, err, st));
     KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
   } else {
     KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
@@ -1040,6 +1087,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
   const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
   KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
+  KKM_RUN("ghat_reduce", st, launch_ghat_reduce(lb.S, lb.I, st));
   KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));

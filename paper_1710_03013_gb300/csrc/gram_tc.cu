@@ -16,10 +16,11 @@
 // FP32 accumulation: its error scales with |p - q|, not with the norms, and
 // near-duplicate pairs do not cancel catastrophically.
 //
-// Structure: persistent CTAs (one per SM), 6 warps:
+// Structure: persistent CTAs (one per SM), 10 warps:
 //   warp 0      TMA producer (one elected lane), 4-stage ring of 48 KB stages
 //   warp 1      TMEM owner (allocates all 512 columns) and MMA issuer
-//   warps 2..5  epilogue, one TMEM lane quarter each
+//   warps 2..9  epilogue: warp w reads TMEM lane quarter w % 4 (the lanes a
+//               warp may access) and half (w - 2) / 4 of the 256 columns
 // Two accumulators of 256 columns let the epilogue of one tile overlap the
 // MMAs of the next.  Every mbarrier wait is bounded: on timeout the kernel
 // records an error code, stops issuing work, and still frees its tensor
@@ -42,7 +43,7 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_A_BYTES = TC_M * TC_K * 2;   // 16 KB
 constexpr int TC_B_BYTES = TC_N * TC_K * 2;   // 32 KB
 constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;   // 2 + 8 warps
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 24;  // bounded mbarrier waits
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 2048;
@@ -116,6 +117,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 2^x with the hardware approximation (ex2.approx, ~2 ulp); its error is far
+// below the BF16 rounding of the inputs.
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Shared-memory matrix descriptor: K-major operand tile of 128-byte rows with
 // the 128-byte swizzle (8-row atoms, 1024 bytes apart).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -141,21 +150,20 @@ struct TcShared {
   uint64_t tempty[2];
   uint32_t tmem_base;
   int abort_flag;
-  float nP[4][TC_N];        // reference norms of the current tile, per epilogue warp
-  long long idP[4][TC_N];   // reference ids of the current tile
+  float nP[8][TC_N / 2];    // reference norms of the current tile, per epilogue warp
 };
 
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
                int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
-               const int64_t* __restrict__ idQ, const int64_t* __restrict__ idP, float neg_scale,
-               float* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+               float neg_scale, float* __restrict__ out, int64_t ldo, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // stages must start on a 1024-byte boundary (swizzle atom)
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ TcShared sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  static_assert(TC_THREADS == 320, "two control warps and eight epilogue warps");
   const int tiles_m = (nQ + TC_M - 1) / TC_M, tiles_n = (nP + TC_N - 1) / TC_N;
   const int n_tiles = tiles_m * tiles_n;
   const int nk = (dk + TC_K - 1) / TC_K;
@@ -167,7 +175,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.tfull[b], 1);
-      mbar_init(&sh.tempty[b], 4);
+      mbar_init(&sh.tempty[b], 8);
     }
     sh.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -252,19 +260,19 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5)
+    // ---------------- epilogue (warps 2..9)
     const int q = warp & 3;             // TMEM lane quarter of this warp
-    const int ew = warp - 2;            // epilogue warp index 0..3
+    const int ew = warp - 2;            // epilogue warp index 0..7
+    const int half = ew >> 2;           // column half 0..1
     int lt = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       const int tm = t % tiles_m, tn = t / tiles_m;
       const int buf = lt & 1;
       const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
-      // reference norms and ids of this tile (each warp keeps its own copy)
-      for (int c = lane; c < TC_N; c += 32) {
-        const int n = tn * TC_N + c;
+      const int n0 = tn * TC_N + half * (TC_N / 2);   // first reference row of this warp
+      for (int c = lane; c < TC_N / 2; c += 32) {
+        const int n = n0 + c;
         sh.nP[ew][c] = n < nP ? normP[n] : 0.0f;
-        sh.idP[ew][c] = (idP && n < nP) ? (long long)idP[n] : -1ll;
       }
       __syncwarp();
       bool ok = true;
@@ -281,25 +289,43 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       const int m = tm * TC_M + q * 32 + lane;
       const bool mvalid = m < nQ;
       const float nq = mvalid ? normQ[m] : 0.0f;
-      const long long iq = (idQ && mvalid) ? (long long)idQ[m] : -2ll;
-      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + half * (TC_N / 2));
+      const int ncols = min(TC_N / 2, nP - n0);  // valid reference rows of this warp (may be <= 0)
+      float* orow = out + (int64_t)n0 * ldo + m;
 #pragma unroll 1
-      for (int c0 = 0; c0 < TC_N; c0 += 32) {
+      for (int c0 = 0; c0 < TC_N / 2; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tbase + (uint32_t)c0, r);
         if (mvalid) {
+          if (c0 + 32 <= ncols) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int n = tn * TC_N + c0 + c;
-            if (n < nP) {
+            for (int c = 0; c < 32; ++c) {
               const float dot = __uint_as_float(r[c]);
-              const float d2 = fmaxf(nq + sh.nP[ew][c0 + c] - 2.0f * dot, 0.0f);
-              const bool same = sh.idP[ew][c0 + c] == iq;
               float v;
-              if (KIND == DK_DIST) v = same ? 0.0f : sqrtf(d2);
-              else if (KIND == DK_LINEAR) v = dot;
-              else v = same ? 1.0f : exp2f(d2 * neg_scale);
-              out[(int64_t)n * ldo + m] = v;
+              if (KIND == DK_LINEAR) {
+                v = dot;
+              } else {
+                const float d2 = fmaxf(fmaf(-2.0f, dot, nq + sh.nP[ew][c0 + c]), 0.0f);
+                if (KIND == DK_DIST) v = sqrtf(d2);
+                else v = fast_exp2(d2 * neg_scale);
+              }
+              orow[(int64_t)(c0 + c) * ldo] = v;
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              if (c0 + c < ncols) {
+                const float dot = __uint_as_float(r[c]);
+                float v;
+                if (KIND == DK_LINEAR) {
+                  v = dot;
+                } else {
+                  const float d2 = fmaxf(fmaf(-2.0f, dot, nq + sh.nP[ew][c0 + c]), 0.0f);
+                  if (KIND == DK_DIST) v = sqrtf(d2);
+                  else v = fast_exp2(d2 * neg_scale);
+                }
+                orow[(int64_t)(c0 + c) * ldo] = v;
+              }
             }
           }
         }
@@ -349,9 +375,8 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t c
 }
 
 cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
-                           int dk, int ldb, const float* normP, const float* normQ, const int64_t* idP,
-                           const int64_t* idQ, float neg_scale, float* out, int64_t ldo, int* err,
-                           int n_sms, cudaStream_t st) {
+                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, float* out,
+                           int64_t ldo, int* err, int n_sms, cudaStream_t st) {
   if (nP <= 0 || nQ <= 0) return cudaSuccess;
   if ((ldb * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15))
     return cudaErrorInvalidValue;
@@ -363,8 +388,8 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
 #define KKM_TC_LAUNCH(K)                                                                             \
   e = cudaFuncSetAttribute(gram_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
   if (e != cudaSuccess) return e;                                                                    \
-  gram_tc_kernel<K><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, (int)nQ, (int)nP, dk, normQ, normP, idQ, idP, \
-                                                       neg_scale, out, ldo, err);
+  gram_tc_kernel<K><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, (int)nQ, (int)nP, dk, normQ, normP, neg_scale, \
+                                                       out, ldo, err);
   if (kind == DK_DIST) {
     KKM_TC_LAUNCH(DK_DIST)
   } else if (kind == DK_LINEAR) {
@@ -373,6 +398,17 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
     KKM_TC_LAUNCH(DK_RBF)
   }
 #undef KKM_TC_LAUNCH
+  return cudaGetLastError();
+}
+
+// K = 1 on the diagonal of the block: out[k][L[k]] for landmark ordinals k.
+__global__ void set_diag_kernel(float* __restrict__ out, int64_t ldo, const int32_t* __restrict__ L, int nL) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nL) out[(int64_t)k * ldo + L[k]] = 1.0f;
+}
+cudaError_t launch_set_diag(float* out, int64_t ldo, const int32_t* L, int nL, cudaStream_t st) {
+  if (nL <= 0) return cudaSuccess;
+  set_diag_kernel<<<(unsigned)ceil_div(nL, 256), 256, 0, st>>>(out, ldo, L, nL);
   return cudaGetLastError();
 }
 

@@ -80,9 +80,10 @@ cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, i
 // (dk valid columns), with the squared norms of the BF16 rows.  *err gets a
 // nonzero code if a bounded wait gave up.
 cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
-                           int dk, int ldb, const float* normP, const float* normQ, const int64_t* idP,
-                           const int64_t* idQ, float neg_scale, float* out, int64_t ldo, int* err,
-                           int n_sms, cudaStream_t st);
+                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, float* out,
+                           int64_t ldo, int* err, int n_sms, cudaStream_t st);
+// out[k*ldo + L[k]] = 1 (the exact diagonal of a Gaussian kernel block).
+cudaError_t launch_set_diag(float* out, int64_t ldo, const int32_t* L, int nL, cudaStream_t st);
 // BF16 copy of FP32 rows [n][dp] with the squared norms of the rounded rows.
 cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq,
                            cudaStream_t st);
@@ -135,10 +136,29 @@ struct IterState {
   const double* ghat_in = nullptr;  // g_hat given (assign against a model), else from gpart
   int32_t* lm_part = nullptr;       // [assign grid] landmark label changes per CTA
   int32_t* lm_changed = nullptr;    // [1] landmark labels changed by the last assign
+  // near-tie re-score (low-precision kernel blocks): rows whose relative
+  // margin is below flag_tau are listed per assign CTA (32 slots each)
+  float flag_tau = 0.0f;
+  int32_t* flag_rows = nullptr;     // [assign grid * 32]
+  int32_t* flag_old = nullptr;      // label before the assign
+  float* flag_d = nullptr;          // low-precision distance of the chosen cluster
+  int32_t* flag_cnt = nullptr;      // [assign grid]
+  int32_t* nflag = nullptr;         // [1] flagged rows of the last assign (zero otherwise)
+  int32_t* ticket_sink = nullptr;   // [1] write target that keeps L2-demotion loads alive
+  double* ghat_cur = nullptr;       // [C] g_hat of the current supports (ghat_reduce)
+  int keep_rows = 0;                // block rows kept in L2 across iterations (evict_last)
   int assign_grid;
   int n_strips;
 };
+// Rows of a [rows][ldk] float block that fit in the given share of L2.
+int l2_keep_rows(int64_t ldk, int rows, double share);
 
+// g_hat of the current supports into I.ghat_cur (one CTA).
+cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st);
+// L2 hygiene: re-read a range with the evict_first policy / drop a range
+// whose contents are not needed again.
+cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st);
+cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st);
 // Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA);
 // skipped when *skip != 0 or when *lm_changed == 0 (then nothing changed).
 cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
@@ -156,6 +176,13 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           const float* kself, int32_t* u, float* margin, float* dmin,
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st);
+
+// FP32 re-score of the rows flagged by assign (exact kernel values over the
+// supports from FP32 rows), then the iteration's closing step (trace, flags).
+// kind DK_RBF or DK_LINEAR.  Uses the assign grid.
+cudaError_t launch_rescore(int kind, int Ni, int dp, const float* Xi, const float* nXi, const float* XL,
+                           const float* nXL, float neg_scale, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, int early_stop, cudaStream_t st);
 
 // ---- mini-batch boundary -----------------------------------------------------
 // Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).

@@ -185,10 +185,19 @@ cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream
 }
 
 // --------------------------------------------------------- f_hat streaming
+// 16-byte load with an L2 eviction-priority policy (createpolicy).
+__device__ __forceinline__ float4 ld_policy(const float* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+
 __global__ void __launch_bounds__(kStreamThreads)
 fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports S,
                     float* __restrict__ partial, double* __restrict__ gpart, int n_strips,
-                    const int32_t* __restrict__ skip) {
+                    const int32_t* __restrict__ skip, int keep_rows) {
   __shared__ double red[kStreamThreads / 32];
   __shared__ int rows[kUnitRows];
   if (skip && *skip) return;
@@ -201,34 +210,30 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
   const int nrow = ke - kb;
   for (int t = threadIdx.x; t < nrow; t += kStreamThreads) rows[t] = S.perm[kb + t];
   __syncthreads();
+  // Rows of the block with ordinal < keep_rows stay in L2 across iterations
+  // (evict_last); the rest stream through (evict_first).
+  uint64_t keep, stream;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
   const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * 4;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
   if (col < Ni) {
     const float* base = KT + col;
-    int k = 0;
-    if (nrow >= 8) {
-      // the loads of the next 8 rows are in flight while the current 8 are added
+    for (int k = 0; k < nrow; k += 8) {
       float4 v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[q] * ldk));
-      for (k = 8; k + 8 <= nrow; k += 8) {
-        float4 w[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) w[q] = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k + q] * ldk));
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
-          v[q] = w[q];
+      for (int q = 0; q < 8; ++q) {
+        if (k + q < nrow) {
+          const int r = rows[k + q];
+          v[q] = ld_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream);
+        } else {
+          v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
       }
-    }
-    for (; k < nrow; ++k) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(base + (int64_t)rows[k] * ldk));
-      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
     *reinterpret_cast<float4*>(partial + (int64_t)unit * ldk + col) = acc;
   }
@@ -249,7 +254,80 @@ cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supp
                                 const IterState& I, cudaStream_t st) {
   dim3 grid((unsigned)I.n_strips, (unsigned)S.max_units);
   fhat_partial_kernel<<<grid, kStreamThreads, 0, st>>>(KT, ldk, Ni, S, I.partial, I.gpart, I.n_strips,
-                                                       I.done);
+                                                       I.done, I.keep_rows);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- g_hat reduce
+// g_hat_j = (sum of the per-(unit, strip) numerators of cluster j) / n_j^2,
+// once per iteration by one CTA (one warp per cluster, FP64, fixed order).
+__global__ void __launch_bounds__(1024)
+ghat_reduce_kernel(Supports S, const double* __restrict__ gpart, int n_strips, double* __restrict__ ghat,
+                   const int32_t* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = w; j < S.C; j += nw) {
+    const int64_t e0 = (int64_t)S.seg_unit[j] * n_strips, e1 = (int64_t)S.seg_unit[j + 1] * n_strips;
+    double acc = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (e + 32 * q < e1) ? gpart[e + 32 * q] : 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += v[q];
+    }
+    acc = warp_sum_f64(acc);
+    if (lane == 0) {
+      const int n = S.n_j[j];
+      ghat[j] = n > 0 ? acc / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
+    }
+  }
+}
+
+cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st) {
+  const int threads = 32 * std::min(std::max(S.C, 1), 32);
+  ghat_reduce_kernel<<<1, threads, 0, st>>>(S, I.gpart, I.n_strips, I.ghat_cur, I.done);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- L2 priorities
+// Lines of [p, p + bytes) are re-read with the evict_first policy so that
+// they leave L2 before anything else (16-byte accesses, p 16-byte aligned).
+__global__ void l2_demote_kernel(const float4* __restrict__ p, int64_t n16, int* __restrict__ sink) {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  float acc = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p + i), "l"(pol));
+    acc += v.x;
+  }
+  if (acc == 1.2345e-30f) *sink = 1;  // keeps the loads; practically never taken
+}
+// Lines fully inside [p, p + bytes) are dropped from L2 without write-back:
+// only for buffers whose contents are not needed again.
+__global__ void l2_discard_kernel(char* p, int64_t lines) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lines; i += (int64_t)gridDim.x * blockDim.x)
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p + i * 128) : "memory");
+}
+
+cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st) {
+  const int64_t n16 = bytes / 16;
+  if (n16 <= 0) return cudaSuccess;
+  l2_demote_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n16, 256), 152 * 8), 256, 0, st>>>(
+      reinterpret_cast<const float4*>(p), n16, sink);
+  return cudaGetLastError();
+}
+cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st) {
+  // whole 128-byte lines inside the range only
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t b = (a + 127) & ~uintptr_t(127);
+  const int64_t lines = (int64_t)(a + bytes - b) / 128;
+  if (lines <= 0) return cudaSuccess;
+  l2_discard_kernel<<<(unsigned)std::min<int64_t>(ceil_div(lines, 256), 152 * 8), 256, 0, st>>>(
+      reinterpret_cast<char*>(b), lines);
   return cudaGetLastError();
 }
 
@@ -266,40 +344,19 @@ struct AssignShared {
 // against a model) or reduced here from the per-(unit, strip) numerators:
 // one warp per cluster, all loads of a lane issued before they are added, in
 // a fixed order.
+// n_j, unit ranges and g_hat into shared memory (g_hat given for an assign
+// against a model, else computed by ghat_reduce for this iteration).
 __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
                                                    const IterState& I) {
   const int C = S.C;
+  const double* g = I.ghat_in ? I.ghat_in : I.ghat_cur;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     sh.nj[j] = S.n_j[j];
     sh.su[j] = S.seg_unit[j];
-    if (I.ghat_in) {
-      sh.gh[j] = I.ghat_in[j];
-      sh.ghf[j] = (float)I.ghat_in[j];
-    }
+    sh.gh[j] = g[j];
+    sh.ghf[j] = (float)g[j];
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
-  __syncthreads();
-  if (I.ghat_in) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int ns = I.n_strips;
-  for (int j = w; j < C; j += nw) {
-    const int64_t e0 = (int64_t)sh.su[j] * ns, e1 = (int64_t)sh.su[j + 1] * ns;
-    double sacc = 0.0;
-    for (int64_t e = e0 + lane; e < e1; e += 32 * 8) {
-      double v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (e + 32 * q < e1) ? I.gpart[e + 32 * q] : 0.0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) sacc += v[q];
-    }
-    sacc = warp_sum_f64(sacc);
-    if (lane == 0) {
-      const double n = (double)sh.nj[j];
-      const double g = sh.nj[j] > 0 ? sacc / (n * n) : __longlong_as_double(0x7ff8000000000000LL);
-      sh.gh[j] = g;
-      sh.ghf[j] = (float)g;
-    }
-  }
   __syncthreads();
 }
 
@@ -343,8 +400,10 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   if (I.done && *I.done) return;
   const int C = S.C;
   load_cluster_stats(sh, S, I);
-  if (blockIdx.x == 0 && ghat_out)
-    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
+  if (blockIdx.x == 0) {
+    if (ghat_out)
+      for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i = blockIdx.x * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
@@ -376,6 +435,9 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   if (w != 0) return;
   double om = 0.0;
   int ch = 0, lmc = 0;
+  bool flagged = false;
+  int old_lab = 0;
+  float best_d = 0.0f;
   if (i < Ni) {
     float best = inf, second = inf;
     int bj = 0;
@@ -402,6 +464,26 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     if (margin) margin[i] = second - best;
     if (dmin) dmin[i] = best;
     om = (double)best;
+    old_lab = old;
+    best_d = best;
+    // near tie on the scale of the terms of d (K_ii + g_hat ~ 1): the
+    // low-precision error of d is absolute, so the criterion is too
+    if (I.flag_tau > 0.0f && second < inf)
+      flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + sh.ghf[bj]);
+  }
+  if (I.flag_tau > 0.0f) {
+    // rows to re-score, in lane order within this CTA
+    const unsigned fm = __ballot_sync(kFull, flagged);
+    if (flagged) {
+      const int e = blockIdx.x * kAssignRows + __popc(fm & ((1u << lane) - 1u));
+      I.flag_rows[e] = i;
+      I.flag_old[e] = old_lab;
+      I.flag_d[e] = best_d;
+    }
+    if (lane == 0) {
+      I.flag_cnt[blockIdx.x] = __popc(fm);
+      if (fm) atomicAdd(I.nflag, __popc(fm));
+    }
   }
   om = warp_sum_f64(om);
   ch = warp_sum_i32(ch);
@@ -423,10 +505,23 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   __threadfence();
   double o = 0.0;
   int c = 0, lm = 0;
-  for (int b = lane; b < (int)gridDim.x; b += 32) {
-    o += __ldcg(I.omega_part + b);
-    c += __ldcg(I.changed_part + b);
-    if (I.lm_part) lm += __ldcg(I.lm_part + b);
+  const int G = (int)gridDim.x;
+  for (int b0 = lane; b0 < G; b0 += 32 * 8) {
+    double ov[8];
+    int cv[8], lv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = b0 + 32 * q;
+      ov[q] = b < G ? __ldcg(I.omega_part + b) : 0.0;
+      cv[q] = b < G ? __ldcg(I.changed_part + b) : 0;
+      lv[q] = (b < G && I.lm_part) ? __ldcg(I.lm_part + b) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      o += ov[q];
+      c += cv[q];
+      lm += lv[q];
+    }
   }
   o = warp_sum_f64(o);
   c = warp_sum_i32(c);
@@ -436,7 +531,9 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     I.trace_omega[t] = o;
     I.trace_changed[t] = c;
     *I.trace_count = t + 1;
-    if (early_stop && c == 0) *I.done = 1;
+    // rows awaiting the re-score may still change: the re-score decides then
+    const bool pending = I.nflag && __ldcg(I.nflag) > 0;
+    if (early_stop && c == 0 && !pending) *I.done = 1;
     if (I.lm_changed) *I.lm_changed = lm;
     *I.ticket = 0u;
   }
@@ -450,6 +547,161 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
   const int threads = 32 * std::min(S.C, 32);
   assign_kernel<<<(unsigned)ceil_div(Ni, kAssignRows), threads, 0, st>>>(
       ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- near-tie re-score
+// One CTA per assign CTA.  For each row the assign flagged (low-precision
+// margin below flag_tau), every cluster's distance is recomputed from exact
+// FP32 kernel values K(x_i, x_l) over its support (dot products of the FP32
+// rows, the same norm expansion and exponential as the FP32 block), in a
+// fixed order: warp w takes the landmarks w, w+8, ... of each segment, then
+// the warp sums are added in warp order.  The CTA then corrects its own
+// Omega / change partials; its last CTA to finish re-closes the iteration
+// (corrects the trace entry assign wrote).  With no flagged row it returns
+// at once.
+constexpr int kRescoreThreads = 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(kRescoreThreads)
+rescore_kernel(int Ni, int dp, const float* __restrict__ Xi, const float* __restrict__ nXi,
+               const float* __restrict__ XL, const float* __restrict__ nXL, float neg_scale, Supports S,
+               IterState I, const float* __restrict__ kself, int32_t* __restrict__ u, int early_stop) {
+  extern __shared__ float xs[];   // [dp]
+  __shared__ float wsum[kRescoreThreads / 32];
+  __shared__ float dsh[kMaxC];
+  __shared__ double red_d[32];
+  __shared__ int red_i[32];
+  __shared__ int is_last;
+  if (I.done && *I.done) return;
+  if (*I.nflag == 0) return;  // nothing to re-score: assign closed the iteration
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int b = blockIdx.x;
+  const int nflag = I.flag_cnt[b];
+  const int C = S.C;
+  double om_adj = 0.0;
+  int ch_adj = 0, lm_adj = 0;
+  for (int sl = 0; sl < nflag; ++sl) {
+    const int e = b * kAssignRows + sl;
+    const int i = I.flag_rows[e];
+    const float* xi = Xi + (int64_t)i * dp;
+    for (int c = tid; c < dp; c += kRescoreThreads) xs[c] = xi[c];
+    __syncthreads();
+    const float ni = nXi[i];
+    const float ks = kself ? kself[i] : 1.0f;
+    for (int j = 0; j < C; ++j) {
+      const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
+      float acc = 0.0f;
+      for (int kk = k0 + w; kk < k1; kk += kRescoreThreads / 32) {
+        const int k = S.perm[kk];
+        const float* xl = XL + (int64_t)k * dp;
+        float dot = 0.0f;
+        for (int c = lane; c < dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
+        dot = warp_sum_f32(dot);
+        float kv;
+        if (KIND == DK_LINEAR) kv = dot;
+        else kv = (S.L[k] == i) ? 1.0f : exp2f(fmaxf(ni + nXL[k] - 2.0f * dot, 0.0f) * neg_scale);
+        acc += kv;
+      }
+      if (lane == 0) wsum[w] = acc;
+      __syncthreads();
+      if (tid == 0) {
+        float f = 0.0f;
+        for (int q = 0; q < kRescoreThreads / 32; ++q) f += wsum[q];
+        const int n = k1 - k0;
+        dsh[j] = n > 0 ? ks - 2.0f * (f / (float)n) + (float)I.ghat_cur[j] : __int_as_float(0x7f800000);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      float best = __int_as_float(0x7f800000);
+      int bj = 0;
+      for (int j = 0; j < C; ++j)
+        if (dsh[j] < best) {
+          best = dsh[j];
+          bj = j;
+        }
+      const int old = I.flag_old[e];
+      const int lowp = u[i];
+      om_adj += (double)best - (double)I.flag_d[e];
+      ch_adj += (int)(bj != old) - (int)(lowp != old);
+      u[i] = bj;
+      if (S.col_ord) {
+        const int k = S.col_ord[i];
+        if (k >= 0) {
+          S.lab[k] = bj;
+          lm_adj += (int)(bj != old) - (int)(lowp != old);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && nflag > 0) {
+    I.omega_part[b] += om_adj;
+    I.changed_part[b] += ch_adj;
+    I.lm_part[b] += lm_adj;
+  }
+  // the last CTA closes the iteration (as assign does without re-scoring)
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double o = 0.0;
+  int c = 0, lm = 0;
+  const int G = (int)gridDim.x;
+  for (int q0 = tid; q0 < G; q0 += kRescoreThreads * 4) {
+    double ov[4];
+    int cv[4], lv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int b = q0 + kRescoreThreads * q;
+      ov[q] = b < G ? __ldcg(I.omega_part + b) : 0.0;
+      cv[q] = b < G ? __ldcg(I.changed_part + b) : 0;
+      lv[q] = b < G ? __ldcg(I.lm_part + b) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      o += ov[q];
+      c += cv[q];
+      lm += lv[q];
+    }
+  }
+  o = block_sum(o, red_d);
+  c = block_sum(c, red_i);
+  lm = block_sum(lm, red_i);
+  if (tid == 0) {
+    const int t = *I.trace_count - 1;  // the entry assign wrote, corrected
+    I.trace_omega[t] = o;
+    I.trace_changed[t] = c;
+    if (early_stop && c == 0) *I.done = 1;
+    if (I.lm_changed) *I.lm_changed = lm;
+    *I.nflag = 0;
+    *I.ticket = 0u;
+  }
+}
+
+cudaError_t launch_rescore(int kind, int Ni, int dp, const float* Xi, const float* nXi, const float* XL,
+                           const float* nXL, float neg_scale, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, int early_stop, cudaStream_t st) {
+  if (Ni <= 0) return cudaSuccess;
+  const int grid = (int)ceil_div(Ni, kAssignRows);
+  const size_t smem = (size_t)dp * sizeof(float);
+  if (smem > 48 * 1024) {
+    cudaError_t e = kind == DK_LINEAR
+                        ? cudaFuncSetAttribute(rescore_kernel<DK_LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)
+                        : cudaFuncSetAttribute(rescore_kernel<DK_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (kind == DK_LINEAR)
+    rescore_kernel<DK_LINEAR><<<grid, kRescoreThreads, smem, st>>>(Ni, dp, Xi, nXi, XL, nXL, neg_scale, S, I, kself,
+                                                                  u, early_stop);
+  else
+    rescore_kernel<DK_RBF><<<grid, kRescoreThreads, smem, st>>>(Ni, dp, Xi, nXi, XL, nXL, neg_scale, S, I, kself, u,
+                                                               early_stop);
   return cudaGetLastError();
 }
 

@@ -203,6 +203,30 @@ kkm_status kkm_minibatch_plan(int64_t N, int32_t B, int32_t sampling, double s,
                               int64_t* step_out, int64_t* n_out, int32_t* L_out,
                               int64_t* nl_out);
 
+/* kkm_assign_noalloc -- kkm_assign for callers that cannot allocate device
+ * memory: a request path where cudaMalloc could synchronise the device and
+ * stall other work, or a process whose device memory belongs to another
+ * framework's pool.  The paper has no counterpart; this is a library service.
+ *   Same results as kkm_assign (labels, squared distances) for one chunk of
+ *   at most KKM_NOALLOC_MAX_ROWS query rows, for models with at most
+ *   KKM_NOALLOC_MAX_REF reference rows (landmark supports in mode
+ *   KKM_ASSIGN_SUPPORTS, medoids in mode KKM_ASSIGN_MEDOIDS) and a prepared
+ *   row length of at most KKM_NOALLOC_MAX_ROWLEN floats (d rounded up to 8;
+ *   for KKM_RMSD 3 * n_atoms rounded up to 24).  Larger sizes give KKM_EINVAL.
+ *   Xnew, labels_out and dist_out (nullable) must be device memory.
+ * It allocates nothing: its working memory is one fixed scratch array of
+ * about 21 MB that every GPU loading this library keeps until exit.  The
+ * first call on each device looks up that array's device address (and may
+ * load the library's device code); make it before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps (several streams or
+ * threads at once) race; calls in order on one stream are safe. */
+#define KKM_NOALLOC_MAX_ROWS 1024
+#define KKM_NOALLOC_MAX_REF 4096
+#define KKM_NOALLOC_MAX_ROWLEN 1024
+kkm_status kkm_assign_noalloc(const kkm_model* m, const float* Xnew, int64_t M,
+                              int32_t mode, int32_t* labels_out,
+                              float* dist_out, void* stream);
+
 const char* kkm_status_string(kkm_status s);
 /* Message of the last failed call on this thread ("" if none). */
 const char* kkm_last_error(void);

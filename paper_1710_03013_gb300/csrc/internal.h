@@ -6,8 +6,51 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/kkm.h"
+
+// The model behind the opaque kkm_model handle: device copies of what
+// kkm_assign / kkm_cost need, plus host copies of the reported results.
+struct kkm_model {
+  int C = 0;
+  int64_t d = 0;
+  int kind = 0;
+  float sigma = 1.0f;
+  int n_atoms = 0;
+  int dp = 0;  // prepared row length (padded)
+  int nL = 0;
+  int device = 0;
+  float* sup = nullptr;        // [nL][dp] prepared landmark rows
+  float* sup_aux = nullptr;    // [nL] squared norms (RBF/linear) or G (RMSD)
+  int64_t* sup_ids = nullptr;  // [nL] global sample ids of the landmarks
+  int32_t* sup_labels = nullptr;
+  int32_t* L_ident = nullptr;  // [nL] 0..nL-1
+  int32_t* perm = nullptr;
+  int32_t* seg_off = nullptr;
+  int32_t* n_j = nullptr;
+  int32_t* unit_j = nullptr;
+  int32_t* unit_kb = nullptr;
+  int32_t* unit_ke = nullptr;
+  int32_t* seg_unit = nullptr;
+  int32_t* n_units = nullptr;
+  double* ghat = nullptr;      // [C]
+  float* med = nullptr;        // [C][dp]
+  float* med_aux = nullptr;    // [C]
+  std::vector<int64_t> medoids, W;
+  std::vector<double> omega;
+  std::vector<int32_t> changed;
+  std::vector<int32_t> sup_labels_h;
+  std::vector<double> ghat_h;
+  std::vector<int32_t> n_h;
+  std::vector<float> med_coords_h;  // [C][d]
+  ~kkm_model() {
+    void* ps[] = {sup, sup_aux, sup_ids, sup_labels, L_ident, perm, seg_off, n_j, unit_j,
+                  unit_kb, unit_ke, seg_unit, n_units, ghat, med, med_aux};
+    for (void* p : ps)
+      if (p) cudaFree(p);
+  }
+};
 
 namespace kkm {
 

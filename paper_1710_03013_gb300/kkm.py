@@ -67,6 +67,7 @@ _SIGNATURES = {
     "kkm_debug_kmeanspp": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _U64, _P, _P]),
     "kkm_minibatch_plan": (_I32, [_I64, _I32, _I32, _F64, _U64, _I32, ctypes.POINTER(_I64),
                                   ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P, ctypes.POINTER(_I64)]),
+    "kkm_assign_noalloc": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "kkm_status_string": (ctypes.c_char_p, [_I32]),
     "kkm_last_error": (ctypes.c_char_p, []),
     "kkm_prof_enable": (None, [_I32]),
@@ -234,6 +235,20 @@ def kkm_assign(model, Xnew, mode="supports", stream=None):
                           lab_p, dist_p, st))
     del keep
     return lab, dist
+
+
+def kkm_assign_noalloc(model, Xnew, labels_out, dist_out=None, mode="supports", stream=None):
+    """kkm_assign_noalloc of the C ABI: labels (and squared distances) of at
+    most KKM_NOALLOC_MAX_ROWS new samples written into the caller's CUDA
+    tensors; neither this function nor the library allocates."""
+    lib = load()
+    M = int(Xnew.shape[0])
+    st = stream if stream is not None else _stream_of(Xnew)
+    _check(lib.kkm_assign_noalloc(model.handle, ctypes.c_void_p(Xnew.data_ptr()), M,
+                                  MODE[mode] if isinstance(mode, str) else int(mode),
+                                  ctypes.c_void_p(labels_out.data_ptr()),
+                                  ctypes.c_void_p(dist_out.data_ptr()) if dist_out is not None else None,
+                                  st))
 
 
 def kkm_cost(model, X, mode="supports", stream=None):

@@ -425,13 +425,7 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_changed, 1));
-  KKM_TRY(ws.alloc(&I.flag_rows, (int64_t)I.assign_grid * 32));
-  KKM_TRY(ws.alloc(&I.flag_old, (int64_t)I.assign_grid * 32));
-  KKM_TRY(ws.alloc(&I.flag_d, (int64_t)I.assign_grid * 32));
-  KKM_TRY(ws.alloc(&I.flag_cnt, I.assign_grid));
-  KKM_TRY(ws.alloc(&I.nflag, 1));
   KKM_TRY(ws.alloc(&I.ticket_sink, 1));
-  KKM_CK(cudaMemsetAsync(I.nflag, 0, 4, ws.st));
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.ticket, 1));
   KKM_TRY(ws.alloc(&I.done, 1));
@@ -686,16 +680,22 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const bool rescore = sp.precision != KKM_FP32;
     I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare);
     I.flag_tau = rescore ? kRescoreMargin : 0.0f;
+    RescoreArgs R;
+    if (rescore) {
+      R.kind = sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF;
+      R.dp = sp.dp;
+      R.Xi = Xi;
+      R.nXi = aux_i;
+      R.XL = XL;
+      R.nXL = auxL;
+      R.neg_scale = sp.neg_scale();
+    }
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
       KKM_RUN("ghat_reduce", st, launch_ghat_reduce(S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
-                            /*trace=*/1, st));
-      if (rescore)
-        KKM_RUN("rescore", st,
-                launch_rescore(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Ni, sp.dp, Xi, aux_i, XL, auxL,
-                               sp.neg_scale(), S, I, kself, u, opt.early_stop, st));
+                            /*trace=*/1, st, R));
       KKM_RUN("build_supports", st, launch_build_supports(S, I.done, I.lm_changed, st));
     }
     I.flag_tau = 0.0f;

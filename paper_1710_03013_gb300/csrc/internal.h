@@ -179,14 +179,9 @@ struct IterState {
   const double* ghat_in = nullptr;  // g_hat given (assign against a model), else from gpart
   int32_t* lm_part = nullptr;       // [assign grid] landmark label changes per CTA
   int32_t* lm_changed = nullptr;    // [1] landmark labels changed by the last assign
-  // near-tie re-score (low-precision kernel blocks): rows whose relative
-  // margin is below flag_tau are listed per assign CTA (32 slots each)
+  // near-tie re-score (low-precision kernel blocks): rows whose margin is
+  // below flag_tau * max(|d2|, K_ii + g_hat) are re-scored in FP32 by assign
   float flag_tau = 0.0f;
-  int32_t* flag_rows = nullptr;     // [assign grid * 32]
-  int32_t* flag_old = nullptr;      // label before the assign
-  float* flag_d = nullptr;          // low-precision distance of the chosen cluster
-  int32_t* flag_cnt = nullptr;      // [assign grid]
-  int32_t* nflag = nullptr;         // [1] flagged rows of the last assign (zero otherwise)
   int32_t* ticket_sink = nullptr;   // [1] write target that keeps L2-demotion loads alive
   double* ghat_cur = nullptr;       // [C] g_hat of the current supports (ghat_reduce)
   int keep_rows = 0;                // block rows kept in L2 across iterations (evict_last)
@@ -211,6 +206,18 @@ cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st);
+// FP32 rows for the near-tie re-score of a low-precision kernel block
+// (Xi == NULL: no re-score).
+struct RescoreArgs {
+  int kind = DK_RBF;           // DK_RBF or DK_LINEAR
+  int dp = 0;
+  const float* Xi = nullptr;   // [Ni][dp] sample rows
+  const float* nXi = nullptr;  // squared norms
+  const float* XL = nullptr;   // [nL][dp] landmark rows (by ordinal)
+  const float* nXL = nullptr;
+  float neg_scale = 0.0f;
+};
+
 // f_hat, distances, argmin, margin, Omega; updates u in place.  With
 // trace != 0 the last CTA also writes the trace entry, the early-stop flag and
 // the count of changed landmark labels.  Uses ceil(Ni/32) CTAs
@@ -218,14 +225,7 @@ cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supp
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
-                          cudaStream_t st);
-
-// FP32 re-score of the rows flagged by assign (exact kernel values over the
-// supports from FP32 rows), then the iteration's closing step (trace, flags).
-// kind DK_RBF or DK_LINEAR.  Uses the assign grid.
-cudaError_t launch_rescore(int kind, int Ni, int dp, const float* Xi, const float* nXi, const float* XL,
-                           const float* nXL, float neg_scale, const Supports& S, const IterState& I,
-                           const float* kself, int32_t* u, int early_stop, cudaStream_t st);
+                          cudaStream_t st, const RescoreArgs& R = RescoreArgs());
 
 // ---- mini-batch boundary -----------------------------------------------------
 // Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).

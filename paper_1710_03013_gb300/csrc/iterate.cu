@@ -32,6 +32,28 @@
 
 namespace kkm {
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor finishes;
+// it waits here before touching anything the predecessor wrote.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int kSortThreads = 1024;  // build_supports: one CTA of 32 warps
 constexpr int kLabRegs = 8;         // landmark labels held in registers per thread
 constexpr int kAssignThreads = 256;
@@ -78,6 +100,8 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
   __shared__ int base[kMaxC];
   __shared__ int wtab[32 * kMaxC];
   __shared__ int scan_sh[32];
+  griddep_wait();
+  griddep_launch();
   if (skip && *skip) return;
   if (lm_changed && *lm_changed == 0) return;  // same landmark labels: same supports
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -166,8 +190,7 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
 
 cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
                                   cudaStream_t st) {
-  build_supports_kernel<<<1, kSortThreads, 0, st>>>(S, skip, lm_changed);
-  return cudaGetLastError();
+  return launch_pdl(build_supports_kernel, dim3(1), dim3(kSortThreads), 0, st, S, skip, lm_changed);
 }
 
 __global__ void landmark_maps_kernel(Supports S, const int32_t* __restrict__ u) {
@@ -200,6 +223,8 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
                     const int32_t* __restrict__ skip, int keep_rows) {
   __shared__ double red[kStreamThreads / 32];
   __shared__ int rows[kUnitRows];
+  griddep_wait();
+  griddep_launch();
   if (skip && *skip) return;
   const int unit = blockIdx.y;
   // unit tables are allocated for max_units entries, so these loads stay in
@@ -253,9 +278,8 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st) {
   dim3 grid((unsigned)I.n_strips, (unsigned)S.max_units);
-  fhat_partial_kernel<<<grid, kStreamThreads, 0, st>>>(KT, ldk, Ni, S, I.partial, I.gpart, I.n_strips,
-                                                       I.done, I.keep_rows);
-  return cudaGetLastError();
+  return launch_pdl(fhat_partial_kernel, grid, dim3(kStreamThreads), 0, st, KT, ldk, Ni, S, I.partial, I.gpart,
+                    I.n_strips, (const int32_t*)I.done, I.keep_rows);
 }
 
 // ----------------------------------------------------------- g_hat reduce
@@ -264,6 +288,8 @@ cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supp
 __global__ void __launch_bounds__(1024)
 ghat_reduce_kernel(Supports S, const double* __restrict__ gpart, int n_strips, double* __restrict__ ghat,
                    const int32_t* __restrict__ skip) {
+  griddep_wait();
+  griddep_launch();
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = w; j < S.C; j += nw) {
@@ -286,8 +312,8 @@ ghat_reduce_kernel(Supports S, const double* __restrict__ gpart, int n_strips, d
 
 cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st) {
   const int threads = 32 * std::min(std::max(S.C, 1), 32);
-  ghat_reduce_kernel<<<1, threads, 0, st>>>(S, I.gpart, I.n_strips, I.ghat_cur, I.done);
-  return cudaGetLastError();
+  return launch_pdl(ghat_reduce_kernel, dim3(1), dim3(threads), 0, st, S, (const double*)I.gpart, I.n_strips,
+                    I.ghat_cur, (const int32_t*)I.done);
 }
 
 // ----------------------------------------------------------- L2 priorities
@@ -385,25 +411,35 @@ __device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __
 // of its 32 rows (lane = row), each lane adding only the partials of its own
 // cluster (coalesced across the warp); warp 0 then takes the argmin over the
 // clusters from shared memory.
+//
+// Near-tie re-score (low-precision kernel blocks, R.Xi != NULL): rows whose
+// margin d2 - d1 is below flag_tau * max(|d2|, K_ii + g_hat) get every
+// cluster's distance recomputed by the whole CTA from exact FP32 kernel
+// values over the supports (dot products of the FP32 rows, the same norm
+// expansion and exponential as the FP32 block; warp w takes landmarks
+// w, w + nw, ... of each segment, warp sums added in warp order).
 constexpr int kAssignRows = 32;
 
 __global__ void __launch_bounds__(1024)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
-              int trace) {
+              int trace, RescoreArgs R) {
+  extern __shared__ float xs[];  // [R.dp] while re-scoring a row
   __shared__ AssignShared sh;
   __shared__ float dsh[kMaxC][kAssignRows];
-  __shared__ double red_d[32];
-  __shared__ int red_i[32], red_l[32];
+  __shared__ float rbest[kAssignRows], rsecond[kAssignRows];
+  __shared__ int rlab[kAssignRows];
+  __shared__ float wsum[32];
+  __shared__ unsigned flag_mask;
   __shared__ int is_last;
+  griddep_wait();
+  griddep_launch();
   if (I.done && *I.done) return;
   const int C = S.C;
   load_cluster_stats(sh, S, I);
-  if (blockIdx.x == 0) {
-    if (ghat_out)
-      for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
-  }
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i = blockIdx.x * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
@@ -432,25 +468,84 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     dsh[j][lane] = dj;
   }
   __syncthreads();
+  if (w == 0) {
+    float best = inf, second = inf;
+    int bj = 0;
+    bool flagged = false;
+    if (i < Ni) {
+      for (int j = 0; j < C; ++j) {  // lowest j on ties
+        const float dj = dsh[j][lane];
+        if (dj < best) {
+          second = best;
+          best = dj;
+          bj = j;
+        } else if (dj < second) {
+          second = dj;
+        }
+      }
+      // near tie on the scale of the terms of d (K_ii + g_hat ~ 1): the
+      // low-precision error of d is absolute, so the criterion is too
+      if (R.Xi && I.flag_tau > 0.0f && second < inf)
+        flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + sh.ghf[bj]);
+    }
+    rbest[lane] = best;
+    rsecond[lane] = second;
+    rlab[lane] = bj;
+    const unsigned fm = __ballot_sync(kFull, flagged);
+    if (lane == 0) flag_mask = fm;
+  }
+  __syncthreads();
+  for (unsigned fm = flag_mask; fm; fm &= fm - 1) {  // the same sequence in every thread
+    const int r = __ffs(fm) - 1;
+    const int ir = blockIdx.x * kAssignRows + r;
+    const float* xi = R.Xi + (int64_t)ir * R.dp;
+    for (int c = threadIdx.x; c < R.dp; c += blockDim.x) xs[c] = xi[c];
+    __syncthreads();
+    const float ni = R.nXi[ir];
+    const float ksr = kself ? kself[ir] : 1.0f;
+    for (int j = 0; j < C; ++j) {
+      const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
+      float acc = 0.0f;
+      for (int kk = k0 + w; kk < k1; kk += nw) {
+        const int k = S.perm[kk];
+        const float* xl = R.XL + (int64_t)k * R.dp;
+        float dot = 0.0f;
+        for (int c = lane; c < R.dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
+        dot = warp_sum_f32(dot);
+        float kv;
+        if (R.kind == DK_LINEAR) kv = dot;
+        else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+        acc += kv;
+      }
+      if (lane == 0) wsum[w] = acc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float f = 0.0f;
+        for (int q = 0; q < nw; ++q) f += wsum[q];
+        const int n = k1 - k0;
+        dsh[j][r] = n > 0 ? ksr - 2.0f * (f / (float)n) + sh.ghf[j] : inf;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      float best = inf;
+      int bj = 0;
+      for (int j = 0; j < C; ++j)
+        if (dsh[j][r] < best) {
+          best = dsh[j][r];
+          bj = j;
+        }
+      rbest[r] = best;
+      rlab[r] = bj;
+    }
+    __syncthreads();
+  }
   if (w != 0) return;
   double om = 0.0;
   int ch = 0, lmc = 0;
-  bool flagged = false;
-  int old_lab = 0;
-  float best_d = 0.0f;
   if (i < Ni) {
-    float best = inf, second = inf;
-    int bj = 0;
-    for (int j = 0; j < C; ++j) {  // lowest j on ties
-      const float dj = dsh[j][lane];
-      if (dj < best) {
-        second = best;
-        best = dj;
-        bj = j;
-      } else if (dj < second) {
-        second = dj;
-      }
-    }
+    const int bj = rlab[lane];
+    const float best = rbest[lane];
     const int old = u[i];
     u[i] = bj;
     ch = (old != bj);
@@ -461,29 +556,9 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
         lmc = ch;
       }
     }
-    if (margin) margin[i] = second - best;
+    if (margin) margin[i] = rsecond[lane] - best;
     if (dmin) dmin[i] = best;
     om = (double)best;
-    old_lab = old;
-    best_d = best;
-    // near tie on the scale of the terms of d (K_ii + g_hat ~ 1): the
-    // low-precision error of d is absolute, so the criterion is too
-    if (I.flag_tau > 0.0f && second < inf)
-      flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + sh.ghf[bj]);
-  }
-  if (I.flag_tau > 0.0f) {
-    // rows to re-score, in lane order within this CTA
-    const unsigned fm = __ballot_sync(kFull, flagged);
-    if (flagged) {
-      const int e = blockIdx.x * kAssignRows + __popc(fm & ((1u << lane) - 1u));
-      I.flag_rows[e] = i;
-      I.flag_old[e] = old_lab;
-      I.flag_d[e] = best_d;
-    }
-    if (lane == 0) {
-      I.flag_cnt[blockIdx.x] = __popc(fm);
-      if (fm) atomicAdd(I.nflag, __popc(fm));
-    }
   }
   om = warp_sum_f64(om);
   ch = warp_sum_i32(ch);
@@ -531,9 +606,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     I.trace_omega[t] = o;
     I.trace_changed[t] = c;
     *I.trace_count = t + 1;
-    // rows awaiting the re-score may still change: the re-score decides then
-    const bool pending = I.nflag && __ldcg(I.nflag) > 0;
-    if (early_stop && c == 0 && !pending) *I.done = 1;
+    if (early_stop && c == 0) *I.done = 1;
     if (I.lm_changed) *I.lm_changed = lm;
     *I.ticket = 0u;
   }
@@ -542,167 +615,16 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
-                          cudaStream_t st) {
+                          cudaStream_t st, const RescoreArgs& R) {
   if (Ni <= 0) return cudaSuccess;
   const int threads = 32 * std::min(S.C, 32);
-  assign_kernel<<<(unsigned)ceil_div(Ni, kAssignRows), threads, 0, st>>>(
-      ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace);
-  return cudaGetLastError();
-}
-
-// ------------------------------------------------------- near-tie re-score
-// One CTA per assign CTA.  For each row the assign flagged (low-precision
-// margin below flag_tau), every cluster's distance is recomputed from exact
-// FP32 kernel values K(x_i, x_l) over its support (dot products of the FP32
-// rows, the same norm expansion and exponential as the FP32 block), in a
-// fixed order: warp w takes the landmarks w, w+8, ... of each segment, then
-// the warp sums are added in warp order.  The CTA then corrects its own
-// Omega / change partials; its last CTA to finish re-closes the iteration
-// (corrects the trace entry assign wrote).  With no flagged row it returns
-// at once.
-constexpr int kRescoreThreads = 256;
-
-template <int KIND>
-__global__ void __launch_bounds__(kRescoreThreads)
-rescore_kernel(int Ni, int dp, const float* __restrict__ Xi, const float* __restrict__ nXi,
-               const float* __restrict__ XL, const float* __restrict__ nXL, float neg_scale, Supports S,
-               IterState I, const float* __restrict__ kself, int32_t* __restrict__ u, int early_stop) {
-  extern __shared__ float xs[];   // [dp]
-  __shared__ float wsum[kRescoreThreads / 32];
-  __shared__ float dsh[kMaxC];
-  __shared__ double red_d[32];
-  __shared__ int red_i[32];
-  __shared__ int is_last;
-  if (I.done && *I.done) return;
-  if (*I.nflag == 0) return;  // nothing to re-score: assign closed the iteration
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int b = blockIdx.x;
-  const int nflag = I.flag_cnt[b];
-  const int C = S.C;
-  double om_adj = 0.0;
-  int ch_adj = 0, lm_adj = 0;
-  for (int sl = 0; sl < nflag; ++sl) {
-    const int e = b * kAssignRows + sl;
-    const int i = I.flag_rows[e];
-    const float* xi = Xi + (int64_t)i * dp;
-    for (int c = tid; c < dp; c += kRescoreThreads) xs[c] = xi[c];
-    __syncthreads();
-    const float ni = nXi[i];
-    const float ks = kself ? kself[i] : 1.0f;
-    for (int j = 0; j < C; ++j) {
-      const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
-      float acc = 0.0f;
-      for (int kk = k0 + w; kk < k1; kk += kRescoreThreads / 32) {
-        const int k = S.perm[kk];
-        const float* xl = XL + (int64_t)k * dp;
-        float dot = 0.0f;
-        for (int c = lane; c < dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
-        dot = warp_sum_f32(dot);
-        float kv;
-        if (KIND == DK_LINEAR) kv = dot;
-        else kv = (S.L[k] == i) ? 1.0f : exp2f(fmaxf(ni + nXL[k] - 2.0f * dot, 0.0f) * neg_scale);
-        acc += kv;
-      }
-      if (lane == 0) wsum[w] = acc;
-      __syncthreads();
-      if (tid == 0) {
-        float f = 0.0f;
-        for (int q = 0; q < kRescoreThreads / 32; ++q) f += wsum[q];
-        const int n = k1 - k0;
-        dsh[j] = n > 0 ? ks - 2.0f * (f / (float)n) + (float)I.ghat_cur[j] : __int_as_float(0x7f800000);
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      float best = __int_as_float(0x7f800000);
-      int bj = 0;
-      for (int j = 0; j < C; ++j)
-        if (dsh[j] < best) {
-          best = dsh[j];
-          bj = j;
-        }
-      const int old = I.flag_old[e];
-      const int lowp = u[i];
-      om_adj += (double)best - (double)I.flag_d[e];
-      ch_adj += (int)(bj != old) - (int)(lowp != old);
-      u[i] = bj;
-      if (S.col_ord) {
-        const int k = S.col_ord[i];
-        if (k >= 0) {
-          S.lab[k] = bj;
-          lm_adj += (int)(bj != old) - (int)(lowp != old);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && nflag > 0) {
-    I.omega_part[b] += om_adj;
-    I.changed_part[b] += ch_adj;
-    I.lm_part[b] += lm_adj;
-  }
-  // the last CTA closes the iteration (as assign does without re-scoring)
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  double o = 0.0;
-  int c = 0, lm = 0;
-  const int G = (int)gridDim.x;
-  for (int q0 = tid; q0 < G; q0 += kRescoreThreads * 4) {
-    double ov[4];
-    int cv[4], lv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int b = q0 + kRescoreThreads * q;
-      ov[q] = b < G ? __ldcg(I.omega_part + b) : 0.0;
-      cv[q] = b < G ? __ldcg(I.changed_part + b) : 0;
-      lv[q] = b < G ? __ldcg(I.lm_part + b) : 0;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      o += ov[q];
-      c += cv[q];
-      lm += lv[q];
-    }
-  }
-  o = block_sum(o, red_d);
-  c = block_sum(c, red_i);
-  lm = block_sum(lm, red_i);
-  if (tid == 0) {
-    const int t = *I.trace_count - 1;  // the entry assign wrote, corrected
-    I.trace_omega[t] = o;
-    I.trace_changed[t] = c;
-    if (early_stop && c == 0) *I.done = 1;
-    if (I.lm_changed) *I.lm_changed = lm;
-    *I.nflag = 0;
-    *I.ticket = 0u;
-  }
-}
-
-cudaError_t launch_rescore(int kind, int Ni, int dp, const float* Xi, const float* nXi, const float* XL,
-                           const float* nXL, float neg_scale, const Supports& S, const IterState& I,
-                           const float* kself, int32_t* u, int early_stop, cudaStream_t st) {
-  if (Ni <= 0) return cudaSuccess;
-  const int grid = (int)ceil_div(Ni, kAssignRows);
-  const size_t smem = (size_t)dp * sizeof(float);
-  if (smem > 48 * 1024) {
-    cudaError_t e = kind == DK_LINEAR
-                        ? cudaFuncSetAttribute(rescore_kernel<DK_LINEAR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem)
-                        : cudaFuncSetAttribute(rescore_kernel<DK_RBF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
+  const size_t smem = R.Xi ? (size_t)R.dp * sizeof(float) : 0;
+  if (smem > 8 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  if (kind == DK_LINEAR)
-    rescore_kernel<DK_LINEAR><<<grid, kRescoreThreads, smem, st>>>(Ni, dp, Xi, nXi, XL, nXL, neg_scale, S, I, kself,
-                                                                  u, early_stop);
-  else
-    rescore_kernel<DK_RBF><<<grid, kRescoreThreads, smem, st>>>(Ni, dp, Xi, nXi, XL, nXL, neg_scale, S, I, kself, u,
-                                                               early_stop);
-  return cudaGetLastError();
+  return launch_pdl(assign_kernel, dim3((unsigned)ceil_div(Ni, kAssignRows)), dim3(threads), smem, st, ldk, Ni, S,
+                    I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
 }
 
 // ----------------------------------------------------- Eq. 8 nearest medoid

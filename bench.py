@@ -37,13 +37,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="mnist-shaped 60000x784 RBF, C=10, B=4, s=0.2, 30 iters", N=60000, d=784, C=10,
-                B=4, s=0.2, iters=30, seed=1710)
+WORKLOADS = {
+    # the benchmark line: MNIST-shaped feature vectors, RBF, tensor-core block
+    "mnist": dict(name="mnist-shaped 60000x784 RBF, C=10, B=4, s=0.2, 30 iters", N=60000, d=784, C=10,
+                  B=4, s=0.2, iters=30, seed=1710, kind="rbf", sigma=0.0, n_atoms=0,
+                  precisions=("bf16", "fp32")),
+    # secondary: MD-shaped trajectory, RMSD kernel (FP32 FFMA)
+    "md": dict(name="md-shaped 500000 frames x 300 atoms RMSD, sigma=1.5, C=8, B=20, s=0.05, 25 iters",
+               N=500000, d=900, C=8, B=20, s=0.05, iters=25, seed=1710, kind="rmsd", sigma=1.5, n_atoms=300,
+               precisions=("fp32",)),
+}
+WORKLOAD = WORKLOADS["mnist"]
 METRIC = "kernel evals/s & iters/s vs plain FP32 path at matched labels; p50/p99 latency"
 UNIT = "kernel evals/s"
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FFMA lanes x 2 flops x max SM clock
-CPU_SAMPLE_ROWS = 10000
-REF_SAMPLE_ROWS = 3000
+CPU_SAMPLE_ROWS = {"mnist": 10000, "md": 20000}
+REF_SAMPLE_ROWS = {"mnist": 3000, "md": 8000}
 
 
 def log(*a):
@@ -155,10 +164,11 @@ def oracle_sample(X, rows, cfg):
     """The oracle's whole fit on the first `rows` samples (same d, C, B, s,
     iters).  Returns (kernel evals, seconds)."""
     from oracle import kkm_oracle as O
-    Xs = X[:rows].astype(np.float64)
+    Xs = X[:rows].reshape(rows, -1).astype(np.float64)
+    kind = O.KIND_RMSD if cfg["kind"] == "rmsd" else O.KIND_RBF
     t0 = time.perf_counter()
-    O.fit(Xs, cfg["C"], cfg["B"], cfg["s"], O.Kernel(O.KIND_RBF, 0.0), cfg["iters"], cfg["seed"],
-          early_stop=False)
+    O.fit(Xs, cfg["C"], cfg["B"], cfg["s"], O.Kernel(kind, cfg["sigma"], cfg["n_atoms"]), cfg["iters"],
+          cfg["seed"], early_stop=False)
     dt = time.perf_counter() - t0
     return fit_evals(rows, cfg["B"], cfg["C"], cfg["s"]), dt
 
@@ -169,13 +179,13 @@ def run_reference(args, cfg, X):
         return
     times, evals = [], 0
     for k in range(args.warmup + args.steps):
-        ev, dt = oracle_sample(X, REF_SAMPLE_ROWS, cfg)
+        ev, dt = oracle_sample(X, REF_SAMPLE_ROWS[cfg["key"]], cfg)
         if k >= args.warmup:
             times.append(dt)
             evals = ev
     tot = sum(times)
     value = evals * len(times) / tot
-    sample = (f"oracle fit of the first {REF_SAMPLE_ROWS} samples (same d, C, B, s, iters; "
+    sample = (f"oracle fit of the first {REF_SAMPLE_ROWS[cfg['key']]} samples (same d, C, B, s, iters; "
               f"{evals} kernel evals per step)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
@@ -203,14 +213,18 @@ def run_ours(args, cfg, X):
     stream = torch.cuda.current_stream(dev)
     C, B, s, iters, seed = cfg["C"], cfg["B"], cfg["s"], cfg["iters"], cfg["seed"]
 
-    BF16, FP32 = kkm.KKM_BF16, kkm.KKM_FP32
+    PREC = {"bf16": kkm.KKM_BF16, "fp32": kkm.KKM_FP32}
+    HEAD = PREC[cfg["precisions"][0]]
+    CMP = PREC[cfg["precisions"][1]] if len(cfg["precisions"]) > 1 else None
+    kind, sig, atoms = cfg["kind"], cfg["sigma"], cfg["n_atoms"]
 
-    def step(prec=BF16):
-        return kkm.kkm_fit(Xd, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False, precision=prec)
+    def step(prec=HEAD):
+        return kkm.kkm_fit(Xd, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False, precision=prec)
 
     for _ in range(args.warmup):
-        lab, model = step(BF16)
-        lab32, model32 = step(FP32)
+        lab, model = step(HEAD)
+        if CMP is not None:
+            step(CMP)
     torch.cuda.synchronize()
 
     def barrier():
@@ -229,15 +243,17 @@ def run_ours(args, cfg, X):
         barrier()
         return e0.elapsed_time(e1) / n, out
 
-    # timed region 1: the headline value (tensor-core BF16 kernel block, no instrumentation)
+    # timed region 1: the headline value (no instrumentation)
     with ClockSampler(local) as clk:
-        ms, (lab, model) = timed(BF16, args.steps)
-    # the plain FP32 path on the same workload, for comparison
-    ms32, (lab32, model32) = timed(FP32, args.steps)
-    agree = float((lab == lab32).float().mean().item())
-    om16, _ = model.trace()
-    om32, _ = model32.trace()
-    omega_rel = float(np.max(np.abs(om16 - om32) / np.abs(om32))) if len(om32) else None
+        ms, (lab, model) = timed(HEAD, args.steps)
+    ms32, agree, omega_rel = None, None, None
+    if CMP is not None:
+        # the plain FP32 path on the same workload, for comparison
+        ms32, (lab32, model32) = timed(CMP, args.steps)
+        agree = float((lab == lab32).float().mean().item())
+        om16, _ = model.trace()
+        om32, _ = model32.trace()
+        omega_rel = float(np.max(np.abs(om16 - om32) / np.abs(om32))) if len(om32) else None
     # timed region 2: the same BF16 steps; every library launch is counted and
     # the kernel-block and streaming kernels are bracketed by CUDA events on
     # their stream (their durations feed the roofline)
@@ -245,7 +261,7 @@ def run_ours(args, cfg, X):
     kkm.prof_enable(2)
     barrier()
     for _ in range(args.steps):
-        lab, model = step(BF16)
+        lab, model = step(HEAD)
     barrier()
     kkm.prof_enable(False)
     prof = {n: kkm.prof_read(n) for n in kkm.prof_names()}
@@ -253,14 +269,14 @@ def run_ours(args, cfg, X):
     # one more step with every launch timed, for the per-kernel breakdown
     kkm.prof_reset()
     kkm.prof_enable(1)
-    lab, model = step(BF16)
+    lab, model = step(HEAD)
     torch.cuda.synchronize()
     kkm.prof_enable(False)
     breakdown = {n: kkm.prof_read(n)[1] for n in kkm.prof_names()}
     if world > 1:
-        t = torch.tensor([ms, ms32], device=dev)
+        t = torch.tensor([ms, ms32 or 0.0], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms32 = float(t[0].item()), float(t[1].item())
+        ms, ms32 = float(t[0].item()), (float(t[1].item()) if ms32 is not None else None)
 
     evals = fit_evals(cfg["N"], B, C, s)
     value = world * evals / (ms / 1e3)
@@ -272,8 +288,8 @@ def run_ours(args, cfg, X):
     for k in range(max(2, min(5, args.steps)) + 1):
         barrier()
         t0 = time.perf_counter()
-        lab_h, _ = kkm.kkm_fit(Xh, C, B, s, "rbf", 0.0, iters=iters, seed=seed, early_stop=False,
-                               precision=BF16, stream=ctypes_stream(stream))
+        lab_h, _ = kkm.kkm_fit(Xh, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False,
+                               precision=HEAD, stream=ctypes_stream(stream))
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append(1e3 * (t1 - t0))
@@ -304,6 +320,15 @@ def run_ours(args, cfg, X):
                 "traffic": ncu_traffic("gram_block"), "kernel": "gram_block (tcgen05 BF16)",
                 "peak_source": peak_kind + " bf16 sustained",
                 "work_per_launch": f"2*N_i*|L|*d = {flops:.4g} flop"}
+    elif dom == "rmsd_block":
+        n, tms = prof[dom]
+        flops = sum(18.0 * cfg["n_atoms"] * ((cfg["N"] - i + B - 1) // B) * n_landmarks((cfg["N"] - i + B - 1) // B, s)
+                    for i in range(B)) / B
+        ach = flops / (tms / n / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / PEAK_FP32_TFLOPS, "traffic": ncu_traffic("rmsd_block"), "kernel": "rmsd_block",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "work_per_launch": f"18*n_atoms flop per pair (3x3 correlation) = {flops:.4g} flop"}
     elif dom == "fhat_partial":
         n, tms = prof[dom]
         by = 4.0 * Ni * nL
@@ -314,24 +339,28 @@ def run_ours(args, cfg, X):
                 "work_per_launch": f"4*N_i*|L| = {by:.4g} B (one read of the kernel block)"}
 
     # ---- CPU baseline: the oracle on a bounded sample
-    ev, dt = oracle_sample(X, CPU_SAMPLE_ROWS, cfg)
+    ev, dt = oracle_sample(X, CPU_SAMPLE_ROWS[cfg["key"]], cfg)
     cpu = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"oracle fit of the first {CPU_SAMPLE_ROWS} samples (same d, C, B, s, iters), "
+           "sample": f"oracle fit of the first {CPU_SAMPLE_ROWS[cfg['key']]} samples (same d, C, B, s, iters), "
                      f"{ev} kernel evals in {dt:.1f} s"}
 
     it_ms = sum(breakdown.get(k, 0.0) for k in ("fhat_partial", "assign", "build_supports"))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 products, f32 accumulation and sums, f64 cost",
+        "vs_baseline": None,
+        "dtype": ("bf16 products, f32 accumulation and sums, f64 cost" if HEAD == kkm.KKM_BF16
+                  else "f32, f64 cost"),
         "data": "synthetic",
         "config": {"workload": cfg["name"], "N": cfg["N"], "d": cfg["d"], "C": C, "B": B, "s": s,
-                   "iters_per_minibatch": iters, "precision": "bf16 tensor-core kernel block, FP32 near-tie re-score", "bandwidth": "median rule inside the fit",
-                   "l2": "inputs larger than L2 (X 188 MB, kernel block 180 MB); no flush",
+                   "iters_per_minibatch": iters,
+                   "precision": ("bf16 tensor-core kernel block, FP32 near-tie re-score" if HEAD == kkm.KKM_BF16
+                                 else "fp32"), "bandwidth": "median rule inside the fit",
+                   "l2": f"inputs larger than L2 (X {X.nbytes / 1e6:.0f} MB); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "iters_per_s": world * B * iters / (ms / 1e3),
-        "fp32_path": {"value": world * evals / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
-                      "iters_per_s": world * B * iters / (ms32 / 1e3)},
+        "fp32_path": ({"value": world * evals / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+                       "iters_per_s": world * B * iters / (ms32 / 1e3)} if ms32 else None),
         "matched_labels": {"fraction_equal_to_fp32_path": agree, "omega_max_rel_diff": omega_rel},
         "inner_iter_ms": it_ms / (B * iters),
         "evals_per_step": evals,
@@ -362,10 +391,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mnist", choices=sorted(WORKLOADS))
     args = ap.parse_args()
-    from synth import mnist_like
-    cfg = dict(WORKLOAD)
-    X, _ = mnist_like(cfg["N"], cfg["d"])
+    cfg = dict(WORKLOADS[args.workload])
+    cfg["key"] = args.workload
+    if cfg["kind"] == "rmsd":
+        from synth import md_trajectory
+        F, _ = md_trajectory(cfg["N"], cfg["n_atoms"])
+        X = F.reshape(cfg["N"], -1)
+    else:
+        from synth import mnist_like
+        X, _ = mnist_like(cfg["N"], cfg["d"])
     if args.impl == "reference":
         run_reference(args, cfg, X)
     else:

@@ -7,8 +7,8 @@
 // (x, y, z planes of ap = n_atoms rounded up to 8, zero padded) with their
 // squared radius G = sum |x_a|^2.
 //
-// rmsd_gram computes a CTA tile of 32 reference frames x 64 sample frames, 8
-// pairs per thread, in two passes over the atoms:
+// rmsd_gram computes a CTA tile of 32 (or, for few references, 8) reference
+// frames x 64 sample frames, 8 pairs per thread, in two passes over the atoms:
 //   pass 1  the 3x3 correlation H = sum_a x_a y_a^T of each pair (FP32 FFMA,
 //           72 accumulators per thread, double-buffered shared-memory tiles of
 //           8 atoms);  then per pair the QCP root: the largest eigenvalue of
@@ -24,7 +24,8 @@
 // (G ~ 1e5 A^2 against n rmsd^2 ~ 1e2 for similar frames), so FP32 rounding of
 // H and G alone moves K by ~1e-4.  The direct residual has no cancellation,
 // and since the residual is stationary at the optimal rotation, the rotation's
-// own FP32 error enters only at second order.  No FP64 is needed.
+// own FP32 error enters only at second order.  No FP64 is needed.  Pass 2
+// runs only in warps holding a pair with a non-negligible kernel value.
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -39,31 +40,33 @@ __global__ void rmsd_prep_kernel(const float* __restrict__ X, int n_atoms, int64
   if (row >= n) return;
   const int64_t g = idx ? idx[row] : start + row * step;
   const float* src = X + g * 3 * (int64_t)n_atoms;
-  double sx = 0.0, sy = 0.0, sz = 0.0;
+  // FP32 is ample here: a centring error of ~1e-6 A changes rmsd^2 by ~1e-12
+  float sx = 0.f, sy = 0.f, sz = 0.f;
   for (int a = lane; a < n_atoms; a += 32) {
     sx += src[3 * a];
     sy += src[3 * a + 1];
     sz += src[3 * a + 2];
   }
-  sx = warp_sum_f64(sx) / n_atoms;
-  sy = warp_sum_f64(sy) / n_atoms;
-  sz = warp_sum_f64(sz) / n_atoms;
+  const float inv_n = 1.0f / (float)n_atoms;
+  sx = warp_sum_f32(sx) * inv_n;
+  sy = warp_sum_f32(sy) * inv_n;
+  sz = warp_sum_f32(sz) * inv_n;
   float* dst = out + row * 3 * (int64_t)ap;
-  double gg = 0.0;
+  float gg = 0.f;
   for (int a = lane; a < ap; a += 32) {
     float cx = 0.f, cy = 0.f, cz = 0.f;
     if (a < n_atoms) {
-      cx = (float)((double)src[3 * a] - sx);
-      cy = (float)((double)src[3 * a + 1] - sy);
-      cz = (float)((double)src[3 * a + 2] - sz);
+      cx = src[3 * a] - sx;
+      cy = src[3 * a + 1] - sy;
+      cz = src[3 * a + 2] - sz;
     }
     dst[a] = cx;
     dst[ap + a] = cy;
     dst[2 * ap + a] = cz;
-    gg += (double)cx * cx + (double)cy * cy + (double)cz * cz;
+    gg = fmaf(cx, cx, fmaf(cy, cy, fmaf(cz, cz, gg)));
   }
-  gg = warp_sum_f64(gg);
-  if (lane == 0) gsq[row] = (float)gg;
+  gg = warp_sum_f32(gg);
+  if (lane == 0) gsq[row] = gg;
 }
 
 cudaError_t launch_rmsd_prep_rows(const float* X, int n_atoms, int64_t start, int64_t step, int64_t n,
@@ -186,73 +189,96 @@ __device__ __forceinline__ float qcp_rotation(const float H[9], float Gx, float 
 }
 
 // --------------------------------------------------------------- pair tile
-constexpr int RT_A = 32, RT_B = 64, RT_K = 8;
+// Tile: TA reference frames x 64 sample frames, 8 atoms per shared-memory
+// stage, 2 references x 4 samples per thread (16 x TA/2 threads).  TA = 32
+// for kernel blocks, TA = 8 for the few-reference calls (medoid columns,
+// k-means++ columns).
+constexpr int RT_B = 64, RT_K = 8;
 
+template <int TA>
+struct RmsdCfg {
+  static constexpr int NT = 16 * (TA / 2);           // threads
+  static constexpr int A4 = TA * 6;                   // float4 per A stage
+  static constexpr int B4 = RT_B * 6;                 // float4 per B stage
+  static constexpr int PA = (A4 + NT - 1) / NT;
+  static constexpr int PB = (B4 + NT - 1) / NT;
+};
+
+template <int TA>
 struct RmsdTiles {
-  float As[2][RT_K][3][RT_A];
+  float As[2][RT_K][3][TA];
   float Bs[2][RT_K][3][RT_B];
 };
 
-// Prefetch of one atom stage into registers: A 192 float4, B 384 float4.
+
+
+template <int TA>
 struct RmsdPrefetch {
-  float4 a, b0, b1;
+  float4 a[RmsdCfg<TA>::PA];
+  float4 b[RmsdCfg<TA>::PB];
 };
 
+// element e of a stage: frame f = e % rows, coordinate plane c, half h of the 8 atoms
+template <int TA>
 __device__ __forceinline__ void rmsd_fetch(const float* __restrict__ A, int nA, const float* __restrict__ Bm,
-                                           int nB, int ap, int a0, int b0, int k0, RmsdPrefetch& p) {
+                                           int nB, int ap, int a0, int b0, int k0, RmsdPrefetch<TA>& p) {
+  using Cf = RmsdCfg<TA>;
   const int tid = threadIdx.x;
-  if (tid < 192) {
-    const int f = tid & 31, rest = tid >> 5, c = rest >> 1, h = rest & 1;
-    p.a = __ldg(reinterpret_cast<const float4*>(A + (int64_t)min(a0 + f, nA - 1) * 3 * ap + c * ap + k0 + h * 4));
+#pragma unroll
+  for (int q = 0; q < Cf::PA; ++q) {
+    const int e = tid + q * Cf::NT;
+    if (e < Cf::A4) {
+      const int f = e % TA, rest = e / TA, c = rest >> 1, h = rest & 1;
+      p.a[q] = __ldg(reinterpret_cast<const float4*>(A + (int64_t)min(a0 + f, nA - 1) * 3 * ap + c * ap + k0 + h * 4));
+    }
   }
-  {
-    const int e = tid;
-    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
-    p.b0 = __ldg(reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + f, nB - 1) * 3 * ap + c * ap + k0 + h * 4));
-  }
-  if (tid < 128) {
-    const int e = tid + 256;
-    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
-    p.b1 = __ldg(reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + f, nB - 1) * 3 * ap + c * ap + k0 + h * 4));
+#pragma unroll
+  for (int q = 0; q < Cf::PB; ++q) {
+    const int e = tid + q * Cf::NT;
+    if (e < Cf::B4) {
+      const int f = e % RT_B, rest = e / RT_B, c = rest >> 1, h = rest & 1;
+      p.b[q] = __ldg(reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + f, nB - 1) * 3 * ap + c * ap + k0 + h * 4));
+    }
   }
 }
 
-__device__ __forceinline__ void rmsd_store(RmsdTiles& t, int buf, const RmsdPrefetch& p) {
+template <int TA>
+__device__ __forceinline__ void rmsd_store(RmsdTiles<TA>& t, int buf, const RmsdPrefetch<TA>& p) {
+  using Cf = RmsdCfg<TA>;
   const int tid = threadIdx.x;
-  if (tid < 192) {
-    const int f = tid & 31, rest = tid >> 5, c = rest >> 1, h = rest & 1;
-    t.As[buf][h * 4 + 0][c][f] = p.a.x;
-    t.As[buf][h * 4 + 1][c][f] = p.a.y;
-    t.As[buf][h * 4 + 2][c][f] = p.a.z;
-    t.As[buf][h * 4 + 3][c][f] = p.a.w;
+#pragma unroll
+  for (int q = 0; q < Cf::PA; ++q) {
+    const int e = tid + q * Cf::NT;
+    if (e < Cf::A4) {
+      const int f = e % TA, rest = e / TA, c = rest >> 1, h = rest & 1;
+      t.As[buf][h * 4 + 0][c][f] = p.a[q].x;
+      t.As[buf][h * 4 + 1][c][f] = p.a[q].y;
+      t.As[buf][h * 4 + 2][c][f] = p.a[q].z;
+      t.As[buf][h * 4 + 3][c][f] = p.a[q].w;
+    }
   }
-  {
-    const int e = tid;
-    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
-    t.Bs[buf][h * 4 + 0][c][f] = p.b0.x;
-    t.Bs[buf][h * 4 + 1][c][f] = p.b0.y;
-    t.Bs[buf][h * 4 + 2][c][f] = p.b0.z;
-    t.Bs[buf][h * 4 + 3][c][f] = p.b0.w;
-  }
-  if (tid < 128) {
-    const int e = tid + 256;
-    const int f = e & 63, rest = e >> 6, c = rest >> 1, h = rest & 1;
-    t.Bs[buf][h * 4 + 0][c][f] = p.b1.x;
-    t.Bs[buf][h * 4 + 1][c][f] = p.b1.y;
-    t.Bs[buf][h * 4 + 2][c][f] = p.b1.z;
-    t.Bs[buf][h * 4 + 3][c][f] = p.b1.w;
+#pragma unroll
+  for (int q = 0; q < Cf::PB; ++q) {
+    const int e = tid + q * Cf::NT;
+    if (e < Cf::B4) {
+      const int f = e % RT_B, rest = e / RT_B, c = rest >> 1, h = rest & 1;
+      t.Bs[buf][h * 4 + 0][c][f] = p.b[q].x;
+      t.Bs[buf][h * 4 + 1][c][f] = p.b[q].y;
+      t.Bs[buf][h * 4 + 2][c][f] = p.b[q].z;
+      t.Bs[buf][h * 4 + 3][c][f] = p.b[q].w;
+    }
   }
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(256, 2)
+template <int KIND, int TA>
+__global__ void __launch_bounds__(RmsdCfg<TA>::NT, (TA == 32) ? 2 : 4)
 rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB, int ap,
                  int n_atoms, const float* __restrict__ gA, const float* __restrict__ gB,
                  const int64_t* __restrict__ idA, const int64_t* __restrict__ idB, float neg_scale,
                  float* __restrict__ out, int64_t ldo, int vec_ok) {
-  __shared__ __align__(16) RmsdTiles t;
+  __shared__ __align__(16) RmsdTiles<TA> t;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int a0 = blockIdx.y * RT_A, b0 = blockIdx.x * RT_B;
+  const int a0 = blockIdx.y * TA, b0 = blockIdx.x * RT_B;
   const int nk = ap / RT_K;
 
   // ---- pass 1: correlation matrices
@@ -263,13 +289,13 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[r][q][e] = 0.f;
-  RmsdPrefetch pf;
-  rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, 0, pf);
-  rmsd_store(t, 0, pf);
+  RmsdPrefetch<TA> pf;
+  rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+  rmsd_store<TA>(t, 0, pf);
   __syncthreads();
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
-    if (kt + 1 < nk) rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+    if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
 #pragma unroll
     for (int k = 0; k < RT_K; ++k) {
       float2 av[3];
@@ -294,7 +320,7 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
         }
       }
     }
-    if (kt + 1 < nk) rmsd_store(t, cur ^ 1, pf);
+    if (kt + 1 < nk) rmsd_store<TA>(t, cur ^ 1, pf);
     __syncthreads();
   }
 
@@ -319,45 +345,49 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
     }
   }
 
-  // ---- pass 2: direct residuals at the QCP rotation
+  // ---- pass 2: direct residuals at the QCP rotation, for the warps holding
+  // a pair that needs one (the stage loads stay CTA-wide)
   if (__syncthreads_or(need != 0u)) {
+    const bool warp_need = __any_sync(kFull, need != 0u);
     float res[2][4];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
       for (int q = 0; q < 4; ++q) res[r][q] = 0.f;
-    rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, 0, pf);
-    rmsd_store(t, 0, pf);
+    rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+    rmsd_store<TA>(t, 0, pf);
     __syncthreads();
     for (int kt = 0; kt < nk; ++kt) {
       const int cur = kt & 1;
-      if (kt + 1 < nk) rmsd_fetch(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+      if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+      if (warp_need) {
 #pragma unroll
-      for (int k = 0; k < RT_K; ++k) {
-        float2 av[3];
-        float4 bv[3];
+        for (int k = 0; k < RT_K; ++k) {
+          float2 av[3];
+          float4 bv[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          av[c] = *reinterpret_cast<const float2*>(&t.As[cur][k][c][ty * 2]);
-          bv[c] = *reinterpret_cast<const float4*>(&t.Bs[cur][k][c][tx * 4]);
-        }
+          for (int c = 0; c < 3; ++c) {
+            av[c] = *reinterpret_cast<const float2*>(&t.As[cur][k][c][ty * 2]);
+            bv[c] = *reinterpret_cast<const float4*>(&t.Bs[cur][k][c][tx * 4]);
+          }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const float x0 = r ? av[0].y : av[0].x, x1 = r ? av[1].y : av[1].x, x2 = r ? av[2].y : av[2].x;
+          for (int r = 0; r < 2; ++r) {
+            const float x0 = r ? av[0].y : av[0].x, x1 = r ? av[1].y : av[1].x, x2 = r ? av[2].y : av[2].x;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float y0 = q == 0 ? bv[0].x : q == 1 ? bv[0].y : q == 2 ? bv[0].z : bv[0].w;
-            const float y1 = q == 0 ? bv[1].x : q == 1 ? bv[1].y : q == 2 ? bv[1].z : bv[1].w;
-            const float y2 = q == 0 ? bv[2].x : q == 1 ? bv[2].y : q == 2 ? bv[2].z : bv[2].w;
-            const float* Rm = h[r][q];
-            const float e0 = fmaf(Rm[0], x0, fmaf(Rm[1], x1, fmaf(Rm[2], x2, -y0)));
-            const float e1 = fmaf(Rm[3], x0, fmaf(Rm[4], x1, fmaf(Rm[5], x2, -y1)));
-            const float e2 = fmaf(Rm[6], x0, fmaf(Rm[7], x1, fmaf(Rm[8], x2, -y2)));
-            res[r][q] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, res[r][q])));
+            for (int q = 0; q < 4; ++q) {
+              const float y0 = q == 0 ? bv[0].x : q == 1 ? bv[0].y : q == 2 ? bv[0].z : bv[0].w;
+              const float y1 = q == 0 ? bv[1].x : q == 1 ? bv[1].y : q == 2 ? bv[1].z : bv[1].w;
+              const float y2 = q == 0 ? bv[2].x : q == 1 ? bv[2].y : q == 2 ? bv[2].z : bv[2].w;
+              const float* Rm = h[r][q];
+              const float e0 = fmaf(Rm[0], x0, fmaf(Rm[1], x1, fmaf(Rm[2], x2, -y0)));
+              const float e1 = fmaf(Rm[3], x0, fmaf(Rm[4], x1, fmaf(Rm[5], x2, -y1)));
+              const float e2 = fmaf(Rm[6], x0, fmaf(Rm[7], x1, fmaf(Rm[8], x2, -y2)));
+              res[r][q] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, res[r][q])));
+            }
           }
         }
       }
-      if (kt + 1 < nk) rmsd_store(t, cur ^ 1, pf);
+      if (kt + 1 < nk) rmsd_store<TA>(t, cur ^ 1, pf);
       __syncthreads();
     }
 #pragma unroll
@@ -398,14 +428,17 @@ cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* 
                              int n_atoms, const float* gA, const float* gB, const int64_t* idA,
                              const int64_t* idB, float neg_scale, float* out, int64_t ldo, cudaStream_t st) {
   if (nA <= 0 || nB <= 0) return cudaSuccess;
-  dim3 grid((unsigned)ceil_div(nB, RT_B), (unsigned)ceil_div(nA, RT_A));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  if (kind == DK_DIST)
-    rmsd_gram_kernel<DK_DIST><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, idB,
-                                                    neg_scale, out, ldo, vec_ok);
-  else
-    rmsd_gram_kernel<DK_RBF><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, idB,
-                                                   neg_scale, out, ldo, vec_ok);
+#define KKM_RMSD_LAUNCH(K, TA)                                                                       \
+  rmsd_gram_kernel<K, TA><<<dim3((unsigned)ceil_div(nB, RT_B), (unsigned)ceil_div(nA, TA)),          \
+                            RmsdCfg<TA>::NT, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, \
+                                                      idB, neg_scale, out, ldo, vec_ok)
+  if (nA <= 8) {
+    if (kind == DK_DIST) KKM_RMSD_LAUNCH(DK_DIST, 8); else KKM_RMSD_LAUNCH(DK_RBF, 8);
+  } else {
+    if (kind == DK_DIST) KKM_RMSD_LAUNCH(DK_DIST, 32); else KKM_RMSD_LAUNCH(DK_RBF, 32);
+  }
+#undef KKM_RMSD_LAUNCH
   return cudaGetLastError();
 }
 

@@ -47,12 +47,19 @@ WORKLOADS = {
                N=500000, d=900, C=8, B=20, s=0.05, iters=25, seed=1710, kind="rmsd", sigma=1.5, n_atoms=300,
                precisions=("fp32",)),
 }
+# the batched form: 256 independent RBF problems of uneven sizes in one call
+WORKLOADS["batched"] = dict(
+    name="batched: 256 RBF problems, N log-uniform [1e3, 5e4], d in {8,32,64,128}, C in [2,64], "
+         "B=ceil(N/1e4), s in {0.1,0.5}, 20 iters", kind="rbf", precisions=("bf16", "fp32"), iters=20,
+    n_problems=256)
 WORKLOAD = WORKLOADS["mnist"]
 METRIC = "kernel evals/s & iters/s vs plain FP32 path at matched labels; p50/p99 latency"
 UNIT = "kernel evals/s"
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # FFMA lanes x 2 flops x max SM clock
 CPU_SAMPLE_ROWS = {"mnist": 10000, "md": 20000}
 REF_SAMPLE_ROWS = {"mnist": 3000, "md": 8000}
+BATCH_CPU_PROBLEMS = 16     # oracle sample of the batched workload: its smallest problems
+BATCH_REF_PROBLEMS = 8
 
 
 def log(*a):
@@ -380,6 +387,180 @@ def run_ours(args, cfg, X):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ batched form
+def batched_data(cfg):
+    from synth import batched_problems, blobs
+    shapes = batched_problems(cfg["n_problems"])
+    data = [blobs(p["N"], p["d"], p["C"], workload=3, problem=p["problem"])[0] for p in shapes]
+    return shapes, data
+
+
+def batched_oracle(shapes, data, cfg, k):
+    """The oracle's fits of the k smallest problems (bandwidth by the median
+    rule, as inside kkm_fit).  Returns (kernel evals, seconds, description)."""
+    from oracle import kkm_oracle as O
+    order = sorted(range(len(shapes)), key=lambda i: shapes[i]["N"])[:k]
+    ev, t0 = 0, time.perf_counter()
+    for i in order:
+        p = shapes[i]
+        O.fit(data[i].astype(np.float64), p["C"], p["B"], p["s"], O.Kernel(O.KIND_RBF, 0.0), cfg["iters"],
+              1710 + i, early_stop=False)
+        ev += fit_evals(p["N"], p["B"], p["C"], p["s"])
+    dt = time.perf_counter() - t0
+    desc = (f"oracle fits of the {k} smallest problems of the batch (N = "
+            f"{', '.join(str(shapes[i]['N']) for i in order)}; same d, C, B, s, iters), {ev} kernel evals")
+    return ev, dt, desc
+
+
+def run_batched(args, cfg):
+    import torch
+    from paper_1710_03013_gb300 import kkm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    shapes, data = batched_data(cfg)
+    iters = cfg["iters"]
+    evals = sum(fit_evals(p["N"], p["B"], p["C"], p["s"]) for p in shapes)
+    inner = sum(p["B"] * iters for p in shapes)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        times = []
+        for k in range(args.warmup + args.steps):
+            ev, dt, desc = batched_oracle(shapes, data, cfg, BATCH_REF_PROBLEMS)
+            if k >= args.warmup:
+                times.append(dt)
+        value = ev * len(times) / sum(times)
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": cfg["name"], "sample": desc},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    Xd = [torch.from_numpy(x).to(dev) for x in data]
+    PREC = {"bf16": kkm.KKM_BF16, "fp32": kkm.KKM_FP32}
+    HEAD, CMP = PREC[cfg["precisions"][0]], PREC[cfg["precisions"][1]]
+
+    def problems(X, prec):
+        return [dict(X=X[i], C=p["C"], B=p["B"], s=p["s"], kind="rbf", sigma=0.0, iters=iters, seed=1710 + i,
+                     early_stop=False, precision=prec) for i, p in enumerate(shapes)]
+
+    def step(prec, X=Xd):
+        return kkm.kkm_fit_batch(problems(X, prec), n_streams=args.streams)
+
+    for _ in range(args.warmup):
+        step(HEAD)
+    step(CMP)
+    torch.cuda.synchronize()
+
+    def timed(prec, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(n):
+            out = step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n, out
+
+    with ClockSampler(local) as clk:
+        ms, res = timed(HEAD, args.steps)
+    ms32, res32 = timed(CMP, args.steps)
+    lab = torch.cat([r[0] for r in res])
+    lab32 = torch.cat([r[0] for r in res32])
+    agree = float((lab == lab32).float().mean().item())
+    omega_rel = 0.0
+    for r16, r32 in zip(res, res32):
+        o16, _ = r16[1].trace()
+        o32, _ = r32[1].trace()
+        omega_rel = max(omega_rel, float(np.max(np.abs(o16 - o32) / np.abs(o32))))
+
+    # instrumented region: launch count and the heavy kernels' event-timed durations
+    kkm.prof_reset()
+    kkm.prof_enable(2)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        step(HEAD)
+    torch.cuda.synchronize()
+    kkm.prof_enable(False)
+    prof = {n: kkm.prof_read(n) for n in kkm.prof_names()}
+    launches = sum(v[0] for v in prof.values()) // args.steps
+
+    # end to end: host inputs (pinned) and labels back to the host
+    Xh = [torch.from_numpy(x).pin_memory() for x in data]
+    e2e_ms = []
+    for k in range(max(2, min(5, args.steps)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kkm.kkm_fit_batch(problems(Xh, HEAD), n_streams=args.streams, stream=ctypes_stream(stream))
+        t1 = time.perf_counter()
+        if k > 0:
+            e2e_ms.append(1e3 * (t1 - t0))
+    e2e = float(np.median(e2e_ms))
+    if rank != 0:
+        return
+
+    peaks, peak_kind = measured_peaks()
+    fh_bytes = sum(4.0 * ((p["N"] - i + p["B"] - 1) // p["B"]) * n_landmarks((p["N"] - i + p["B"] - 1) // p["B"], p["s"])
+                   * (iters + 1) for p in shapes for i in range(p["B"]))
+    gr_flops = sum(2.0 * ((p["N"] - i + p["B"] - 1) // p["B"]) * n_landmarks((p["N"] - i + p["B"] - 1) // p["B"], p["s"])
+                   * p["d"] for p in shapes for i in range(p["B"]))
+    cands = {}
+    if "fhat_partial" in prof:
+        n, tms = prof["fhat_partial"]
+        ach = fh_bytes * args.steps / (tms / 1e3) / 1e9
+        cands["fhat_partial"] = (tms, {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "fhat_partial",
+                                       "peak_source": peak_kind,
+                                       "work_per_launch": f"4*N_i*|L| B per launch; {fh_bytes:.4g} B over the "
+                                                          f"{n // args.steps} launches of a step"})
+    if "gram_block" in prof:
+        n, tms = prof["gram_block"]
+        ach = gr_flops * args.steps / (tms / 1e3) / 1e12
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        cands["gram_block"] = (tms, {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                     "frac": ach / pk, "traffic": None, "kernel": "gram_block (tcgen05 BF16)",
+                                     "peak_source": peak_kind + " bf16 sustained",
+                                     "work_per_launch": f"2*N_i*|L|*d flop; {gr_flops:.4g} flop per step"})
+    roof = max(cands.values(), key=lambda v: v[0])[1] if cands else None
+    if roof:
+        roof["note"] = ("launch durations are event-timed on each fit's own stream while other fits run "
+                        "beside it, so they include time shared with concurrent launches")
+
+    ev, dt, desc = batched_oracle(shapes, data, cfg, BATCH_CPU_PROBLEMS)
+    cpu = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{desc} in {dt:.1f} s"}
+    h2d = int(sum(x.nbytes for x in data))
+    out = {
+        "metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 products, f32 accumulation and sums, f64 cost", "data": "synthetic",
+        "config": {"workload": cfg["name"], "problems": len(shapes), "sum_N": int(sum(p["N"] for p in shapes)),
+                   "streams": args.streams or "library default",
+                   "bandwidth": "median rule inside each fit",
+                   "l2": f"inputs larger than L2 (X {h2d / 1e6:.0f} MB over the batch); no flush"},
+        "iters_per_s": inner / (ms / 1e3),
+        "fp32_path": {"value": evals / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+                      "iters_per_s": inner / (ms32 / 1e3)},
+        "matched_labels": {"fraction_equal_to_fp32_path": agree, "omega_max_rel_diff": omega_rel},
+        "evals_per_step": evals,
+        "e2e": {"value": evals / (e2e / 1e3), "unit": UNIT, "ms_per_step": e2e, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(4 * sum(p["N"] for p in shapes))},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def ctypes_stream(stream):
     import ctypes
     return ctypes.c_void_p(stream.cuda_stream)
@@ -392,9 +573,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mnist", choices=sorted(WORKLOADS))
+    ap.add_argument("--streams", type=int, default=0, help="batched workload: concurrent streams (0: default)")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     cfg["key"] = args.workload
+    if args.workload == "batched":
+        if args.impl == "ours":
+            from paper_1710_03013_gb300 import build as _b
+            _b.build()
+        run_batched(args, cfg)
+        return
     if cfg["kind"] == "rmsd":
         from synth import md_trajectory
         F, _ = md_trajectory(cfg["N"], cfg["n_atoms"])

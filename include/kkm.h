@@ -117,6 +117,40 @@ kkm_status kkm_fit(const float* X, int64_t N, int64_t d, int32_t C, int32_t B,
                    const kkm_options* opt, int32_t* labels_out,
                    kkm_model** model_out);
 
+/* One problem of a batched fit: the arguments of one kkm_fit call. */
+typedef struct kkm_problem {
+  const float* X;       /* [N][d] device or host                            */
+  int64_t N, d;
+  int32_t C, B;
+  double s;
+  kkm_kernel kernel;
+  int32_t iters;
+  uint64_t seed;
+  kkm_options opt;      /* opt.stream is ignored (the batch uses its own)   */
+  int32_t* labels_out;  /* [N] device or host, nullable                     */
+} kkm_problem;
+
+/*
+ * kkm_fit_batch -- n independent fits on one GPU at once: many data sets of
+ * uneven sizes, or restarts of one data set with different seeds.  Each
+ * problem gets exactly the results of kkm_fit with the same arguments.  The
+ * paper fits one data set at a time; this is a library service around
+ * Algorithm 1, not a change to it.
+ *   problems   [n] host array.
+ *   n_streams  concurrent CUDA streams (one host worker thread each), 1..64,
+ *              or 0 for the default (8).  Fits start longest first.
+ *   models_out [n] host array of model pointers (nullable); a failed
+ *              problem's entry is NULL.
+ *   status_out [n] host array: each problem's status.
+ *   stream     work queued on this stream before the call (e.g. the copies
+ *              that produced the inputs) completes before any fit starts.
+ * Returns KKM_OK when every problem succeeded, else the status of the
+ * lowest-numbered failing problem (kkm_last_error names it); the other
+ * problems still run to completion.  Synchronous: returns when all are done.
+ */
+kkm_status kkm_fit_batch(const kkm_problem* problems, int32_t n, int32_t n_streams,
+                         kkm_model** models_out, kkm_status* status_out, void* stream);
+
 /*
  * kkm_assign -- label new samples against a fitted model: Eq. 15 with the
  * model's landmark supports (mode KKM_ASSIGN_SUPPORTS) or Eq. 2 against its

@@ -73,22 +73,24 @@ static cudaEvent_t take_event() {
   return e;
 }
 
-ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), stream(s) {
+ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s) {
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (g_prof_on == 2 && !heavy_kernel(name)) {
     g_prof[name].launches += 1;
     return;
   }
-  Pending p{name, take_event(), take_event()};
-  cudaEventRecord(p.a, s);
-  g_pending.push_back(p);
-  slot = (int)g_pending.size() - 1;
+  a = take_event();
+  b = take_event();
+  cudaEventRecord(a, s);
 }
+// The pair is queued only once both events are recorded, so a concurrent
+// prof_collect (another thread's call) never sees a half-recorded pair.
 ProfScope::~ProfScope() {
-  if (slot < 0) return;
+  if (!a) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  cudaEventRecord(g_pending[slot].b, stream);
+  cudaEventRecord(b, stream);
+  g_pending.push_back(Pending{name, a, b});
 }
 void prof_collect() {
   std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -306,13 +308,13 @@ static kkm_status kernel_block(const KernelSpec& sp, const float* A, const float
 }
 
 static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = []() {
+    int dev = 0, v = 1;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) v = 1;
     cudaGetLastError();
-  }
+    return v;
+  }();
   return n;
 }
 
@@ -335,13 +337,13 @@ static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const 
 }
 
 int l2_keep_rows(int64_t ldk, int rows, double share) {
-  static int l2 = -1;
-  if (l2 < 0) {
-    int dev = 0;
+  static const int l2 = []() {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) l2 = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) v = 0;
     cudaGetLastError();
-  }
+    return v;
+  }();
   const double row_bytes = (double)ldk * 4.0;
   return (int)std::min<double>(rows, std::floor(share * (double)l2 / row_bytes));
 }
@@ -731,29 +733,38 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       m->device = dev;
       std::unique_ptr<kkm_model> guard(m);
       const int mu = lb.max_units;
-      auto A = [&](auto** p, int64_t n) -> kkm_status {
+      // one allocation for the resident arrays (256-byte aligned pieces)
+      std::vector<std::pair<void**, size_t>> parts;
+      auto A = [&](auto** p, int64_t n) {
         using T = std::remove_reference_t<decltype(**p)>;
-        void* q = nullptr;
-        KKM_CK(cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
-        *p = reinterpret_cast<T*>(q);
-        return KKM_OK;
+        parts.emplace_back(reinterpret_cast<void**>(p), (size_t)std::max<int64_t>(n, 1) * sizeof(T));
       };
-      KKM_TRY(A(&m->sup, (int64_t)nL * sp.dp));
-      KKM_TRY(A(&m->sup_aux, nL));
-      KKM_TRY(A(&m->sup_ids, nL));
-      KKM_TRY(A(&m->sup_labels, nL));
-      KKM_TRY(A(&m->L_ident, nL));
-      KKM_TRY(A(&m->perm, nL));
-      KKM_TRY(A(&m->seg_off, C + 1));
-      KKM_TRY(A(&m->n_j, C));
-      KKM_TRY(A(&m->unit_j, mu));
-      KKM_TRY(A(&m->unit_kb, mu));
-      KKM_TRY(A(&m->unit_ke, mu));
-      KKM_TRY(A(&m->seg_unit, C + 1));
-      KKM_TRY(A(&m->n_units, 1));
-      KKM_TRY(A(&m->ghat, C));
-      KKM_TRY(A(&m->med, (int64_t)C * sp.dp));
-      KKM_TRY(A(&m->med_aux, C));
+      A(&m->sup, (int64_t)nL * sp.dp);
+      A(&m->sup_aux, nL);
+      A(&m->sup_ids, nL);
+      A(&m->sup_labels, nL);
+      A(&m->L_ident, nL);
+      A(&m->perm, nL);
+      A(&m->seg_off, C + 1);
+      A(&m->n_j, C);
+      A(&m->unit_j, mu);
+      A(&m->unit_kb, mu);
+      A(&m->unit_ke, mu);
+      A(&m->seg_unit, C + 1);
+      A(&m->n_units, 1);
+      A(&m->ghat, C);
+      A(&m->med, (int64_t)C * sp.dp);
+      A(&m->med_aux, C);
+      size_t total = 0;
+      for (auto& pr : parts) total += (pr.second + 255) & ~size_t(255);
+      KKM_CK(cudaMalloc(&m->arena, total));
+      {
+        size_t off = 0;
+        for (auto& pr : parts) {
+          *pr.first = static_cast<unsigned char*>(m->arena) + off;
+          off += (pr.second + 255) & ~size_t(255);
+        }
+      }
       auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
         KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
         return KKM_OK;
@@ -819,8 +830,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     kkm_model* m = *model_out;
     // medoid coordinates in the caller's layout
     for (int j = 0; j < C; ++j)
-      KKM_CK(cudaMemcpy(m->med_coords_h.data() + (size_t)j * d, X + m->medoids[j] * d, (size_t)d * 4,
-                        cudaMemcpyDeviceToHost));
+      KKM_CK(cudaMemcpyAsync(m->med_coords_h.data() + (size_t)j * d, X + m->medoids[j] * d, (size_t)d * 4,
+                             cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
   }
   prof_collect();
   return KKM_OK;

@@ -346,16 +346,18 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
 
 // ------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // resolved once; function-local static initialisation is thread-safe
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
+    PFN_cuTensorMapEncodeTiled_v12000 f = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+      f = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     cudaGetLastError();
-  }
+    return f;
+  }();
   return fn;
 }
 

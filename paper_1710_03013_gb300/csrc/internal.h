@@ -44,11 +44,9 @@ struct kkm_model {
   std::vector<double> ghat_h;
   std::vector<int32_t> n_h;
   std::vector<float> med_coords_h;  // [C][d]
+  void* arena = nullptr;            // one device allocation holding every array above
   ~kkm_model() {
-    void* ps[] = {sup, sup_aux, sup_ids, sup_labels, L_ident, perm, seg_off, n_j, unit_j,
-                  unit_kb, unit_ke, seg_unit, n_units, ghat, med, med_aux};
-    for (void* p : ps)
-      if (p) cudaFree(p);
+    if (arena) cudaFree(arena);
   }
 };
 
@@ -75,7 +73,8 @@ kkm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
 struct ProfScope {
   ProfScope(const char* name, cudaStream_t s);
   ~ProfScope();
-  int slot;
+  const char* name;
+  cudaEvent_t a = nullptr, b = nullptr;  // null: not timed
   cudaStream_t stream;
 };
 void prof_collect();  // after a stream sync: fold finished events into totals

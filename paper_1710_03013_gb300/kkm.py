@@ -42,6 +42,13 @@ class kkm_options(ctypes.Structure):
                 ("init_medoids", ctypes.POINTER(ctypes.c_int64)), ("stream", ctypes.c_void_p)]
 
 
+class kkm_problem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("d", ctypes.c_int64),
+                ("C", ctypes.c_int32), ("B", ctypes.c_int32), ("s", ctypes.c_double),
+                ("kernel", kkm_kernel), ("iters", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("opt", kkm_options), ("labels_out", ctypes.c_void_p)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I32, _I64, _U64, _F32, _F64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -51,6 +58,7 @@ _SIGNATURES = {
     "kkm_options_default": (None, [ctypes.POINTER(kkm_options)]),
     "kkm_fit": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
                        ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P)]),
+    "kkm_fit_batch": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "kkm_assign": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "kkm_cost": (_I32, [_P, _P, _I64, _I32, ctypes.POINTER(_F64), _P]),
     "kkm_model_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
@@ -221,6 +229,54 @@ def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
                        int(seed) & ((1 << 64) - 1), ctypes.byref(opt), lab_p, ctypes.byref(h)))
     del keep, init_arr
     return lab, Model(h)
+
+
+def kkm_fit_batch(problems, n_streams=0, stream=None, check=True):
+    """kkm_fit_batch of the C ABI.  `problems` is a list of dicts with the
+    kkm_fit arguments (X, C, B, s and optionally kind, sigma, n_atoms, iters,
+    seed, precision, sampling, early_stop, init_medoids, labels).  Returns a
+    list of (labels or None, Model or None, status) in problem order; with
+    check=True a failed problem raises KKMError instead."""
+    lib = load()
+    n = len(problems)
+    arr = (kkm_problem * max(n, 1))()
+    keep, outs = [], []
+    for i, p in enumerate(problems):
+        X = p["X"]
+        xp, kx = _as_input(X, np.float32)
+        keep.append(kx)
+        q = arr[i]
+        q.X = xp
+        q.N = int(X.shape[0])
+        q.d = int(np.prod(X.shape[1:]))
+        q.C, q.B, q.s = int(p["C"]), int(p["B"]), float(p["s"])
+        q.kernel = _kernel(p.get("kind", "rbf"), p.get("sigma", 0.0), p.get("n_atoms", 0))
+        q.iters = int(p.get("iters", 20))
+        q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
+        lib.kkm_options_default(ctypes.byref(q.opt))
+        q.opt.precision = int(p.get("precision", KKM_FP32))
+        smp = p.get("sampling", "stride")
+        q.opt.sampling = SAMPLING[smp] if isinstance(smp, str) else int(smp)
+        q.opt.early_stop = 1 if p.get("early_stop", True) else 0
+        if p.get("init_medoids") is not None:
+            ia = np.ascontiguousarray(p["init_medoids"], dtype=np.int64)
+            keep.append(ia)
+            q.opt.init_medoids = ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        if p.get("labels", True):
+            lp, lab = _out_like(X, q.N, np.int32)
+            q.labels_out = lp
+        else:
+            lab = None
+        outs.append(lab)
+    models = (ctypes.c_void_p * max(n, 1))()
+    status = (ctypes.c_int32 * max(n, 1))()
+    if stream is None:
+        stream = _stream_of(problems[0]["X"]) if n else ctypes.c_void_p(0)
+    rc = lib.kkm_fit_batch(arr, n, int(n_streams), models, status, stream)
+    if check:
+        _check(rc)
+    del keep
+    return [(outs[i], Model(ctypes.c_void_p(models[i])) if models[i] else None, status[i]) for i in range(n)]
 
 
 def kkm_assign(model, Xnew, mode="supports", stream=None):

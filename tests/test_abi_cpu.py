@@ -69,3 +69,16 @@ def test_minibatch_plan_rejects_bad_arguments(kkm):
         with pytest.raises(kkm.KKMError) as e:
             kkm.kkm_minibatch_plan(*args)
         assert e.value.status == kkm.STATUS_EINVAL
+
+
+def test_batched_workload_shapes_are_valid():
+    """Every problem of the 256-problem batched workload passes kkm_fit's
+    argument checks: C <= 256 and no larger than any of its mini-batches."""
+    from synth import batched_problems
+    P = batched_problems()
+    assert len(P) == 256
+    for p in P:
+        assert 1000 <= p["N"] <= 50000 and p["d"] in (8, 32, 64, 128) and 2 <= p["C"] <= 64
+        assert p["B"] == -(-p["N"] // 10000) and p["s"] in (0.1, 0.5)
+        for i in range(p["B"]):
+            assert (p["N"] - i + p["B"] - 1) // p["B"] >= p["C"]

@@ -1,0 +1,130 @@
+"""Batched independent fits (kkm_fit_batch) on the GPU.
+
+Each problem of a batch must give exactly what kkm_fit gives for it alone
+(same kernels on its own stream, fixed-order reductions), whatever runs
+beside it; a sample of the problems is also checked against the FP64 oracle
+at the usual tolerances.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import kkm_oracle as O
+from synth import blobs
+from tests.helpers import assert_labels, first_divergence
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def _np(t):
+    return t.cpu().numpy() if hasattr(t, "cpu") else np.asarray(t)
+
+
+def _small_problems(n, seed):
+    """Uneven shapes in the style of the batched workload, scaled down so
+    the oracle and the solo fits finish quickly."""
+    g = np.random.default_rng(seed)
+    out = []
+    for p in range(n):
+        N = int(round(math.exp(g.uniform(math.log(300), math.log(6000)))))
+        d = int(g.choice([8, 32, 64, 128]))
+        C = int(g.integers(2, 17))
+        B = -(-N // 2500)
+        s = float(g.choice([0.1, 0.5]))
+        X, _ = blobs(N, d, C, workload=3, problem=100 + p)
+        out.append(dict(X=X, C=C, B=B, s=s, iters=8, seed=int(g.integers(0, 2**31)),
+                        precision=int(g.integers(0, 2)), early_stop=bool(g.integers(0, 2))))
+    return out
+
+
+def _same_model(a, b):
+    la, ma = a
+    lb, mb = b
+    assert np.array_equal(_np(la), _np(lb))
+    oa, ca = ma.trace()
+    ob, cb = mb.trace()
+    assert np.array_equal(oa, ob) and np.array_equal(ca, cb)
+    ia, wa, xa = ma.medoids()
+    ib, wb, xb = mb.medoids()
+    assert np.array_equal(ia, ib) and np.array_equal(wa, wb) and np.array_equal(xa, xb)
+    sa, ga, na = ma.supports()
+    sb, gb, nb = mb.supports()
+    assert np.array_equal(sa, sb) and np.array_equal(ga, gb) and np.array_equal(na, nb)
+
+
+@pytest.mark.parametrize("n_streams", [1, 4, 12])
+def test_batch_equals_solo_fits(lib, n_streams):
+    probs = _small_problems(14, seed=5)
+    dev = [dict(p, X=_dev(p["X"])) for p in probs]
+    res = lib.kkm_fit_batch(dev, n_streams=n_streams)
+    for p, (lab, model, status) in zip(dev, res):
+        assert status == 0
+        solo = lib.kkm_fit(p["X"], p["C"], p["B"], p["s"], "rbf", 0.0, 0, p["iters"], p["seed"],
+                           precision=p["precision"], early_stop=p["early_stop"])
+        _same_model((lab, model), solo)
+
+
+def test_batch_against_oracle(lib):
+    """FP32 problems of the batch against the oracle (labels above the margin,
+    the Omega trace at 1e-6, medoids identical)."""
+    probs = []
+    for p, (N, d, C, B, s) in enumerate([(1500, 16, 4, 1, 1.0), (2600, 32, 6, 2, 0.3), (900, 8, 3, 1, 0.5)]):
+        X, _ = blobs(N, d, C, workload=3, problem=200 + p)
+        sig = float(np.float32(O.median_bandwidth(X.astype(np.float64), O.Kernel(O.KIND_RBF, 0.0),
+                                                  O.SplitMix64(p), 512)))
+        probs.append(dict(X=X, C=C, B=B, s=s, sigma=sig, iters=10, seed=40 + p, early_stop=False))
+    refs = [O.fit(p["X"].astype(np.float64), p["C"], p["B"], p["s"], O.Kernel(O.KIND_RBF, p["sigma"]),
+                  p["iters"], p["seed"], early_stop=False) for p in probs]
+    dev = [dict(p, X=_dev(p["X"]), init_medoids=r["details"][0]["M_before"]) for p, r in zip(probs, refs)]
+    res = lib.kkm_fit_batch(dev, n_streams=3)
+    for (lab, model, status), ref in zip(res, refs):
+        assert status == 0
+        lab = _np(lab)
+        om, _ = model.trace()
+        want = np.array([t[2] for t in ref["trace"]])
+        assert om.shape == want.shape
+        assert first_divergence(om, want) is None
+        for det in ref["details"]:
+            assert_labels(lab[det["gidx"]], det["u"], det["steps"][-1]["d"], "batched fit labels")
+        idx, cnt, _ = model.medoids()
+        assert np.array_equal(idx, ref["medoids"]) and np.array_equal(cnt, ref["W"])
+
+
+def test_batch_restarts_of_one_data_set(lib):
+    """Restarts: one data set, several seeds, each equal to its solo fit."""
+    X, _ = blobs(4000, 32, 8, workload=3, problem=300)
+    Xd = _dev(X)
+    probs = [dict(X=Xd, C=8, B=2, s=0.2, iters=10, seed=sd, precision=lib.KKM_BF16) for sd in range(6)]
+    res = lib.kkm_fit_batch(probs, n_streams=6)
+    for p, (lab, model, status) in zip(probs, res):
+        assert status == 0
+        _same_model((lab, model), lib.kkm_fit(Xd, 8, 2, 0.2, "rbf", 0.0, 0, 10, p["seed"],
+                                             precision=lib.KKM_BF16))
+
+
+def test_batch_host_inputs_and_labels(lib):
+    probs = _small_problems(4, seed=9)
+    res = lib.kkm_fit_batch(probs, n_streams=2)
+    for p, (lab, model, status) in zip(probs, res):
+        assert status == 0 and isinstance(lab, np.ndarray)
+        solo = lib.kkm_fit(_dev(p["X"]), p["C"], p["B"], p["s"], "rbf", 0.0, 0, p["iters"], p["seed"],
+                           precision=p["precision"], early_stop=p["early_stop"])
+        _same_model((lab, model), solo)
+
+
+def test_batch_failed_problem_does_not_stop_others(lib):
+    probs = _small_problems(3, seed=11)
+    bad = dict(probs[1], C=probs[1]["X"].shape[0] + 1)   # C larger than the mini-batch
+    batch = [probs[0], bad, probs[2]]
+    res = lib.kkm_fit_batch(batch, n_streams=2, check=False)
+    assert [r[2] for r in res] == [0, lib.STATUS_EINVAL, 0]
+    assert res[1][1] is None and res[0][1] is not None and res[2][1] is not None
+    with pytest.raises(lib.KKMError):
+        lib.kkm_fit_batch(batch, n_streams=2)

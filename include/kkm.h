@@ -152,6 +152,71 @@ kkm_status kkm_fit_batch(const kkm_problem* problems, int32_t n, int32_t n_strea
                          kkm_model** models_out, kkm_status* status_out, void* stream);
 
 /*
+ * Serving: a request loop for fit and assign jobs on one GPU.  The paper has
+ * no serving layer; this is a library service around Algorithm 1 (fits) and
+ * Eq. 15 (assignment of new samples to resident models).
+ *
+ * Jobs are queued by kkm_server_submit_* from any host thread and run on
+ * worker threads, each with its own CUDA stream, as soon as a worker is free
+ * and the job's device-memory estimate fits in the budget beside the
+ * resident models and the running jobs; so jobs that arrive while others run
+ * overlap on the device.  Waiting assign jobs on the same model and mode are
+ * fused into one launch; each row's result is bit-for-bit what the request
+ * would get alone.  Later jobs may pass one that does not fit yet, at most
+ * 16 times.  Buffers passed to a submit call (host or device) must stay
+ * valid until kkm_server_wait reports the job finished.
+ */
+typedef struct kkm_server kkm_server;
+
+typedef struct kkm_server_config {
+  uint64_t budget_bytes;   /* HBM admission budget (resident models + running jobs) */
+  int32_t n_workers;       /* concurrent jobs (one stream each); 0: 4, at most 64   */
+  int32_t reserved;        /* must be 0                                             */
+  int64_t max_batch_rows;  /* rows of fused assign jobs per launch; 0: 65536        */
+} kkm_server_config;
+
+typedef struct kkm_serving_stats {
+  int64_t completed_fit, completed_assign, failed, refused;
+  int64_t fused_assign_launches;  /* kkm_assign launches that served the assign jobs */
+  int64_t queued;                 /* jobs waiting for admission now                  */
+  double p50_fit_ms, p99_fit_ms;  /* submit-to-finish latency of completed jobs       */
+  double p50_assign_ms, p99_assign_ms;
+  double kernel_evals;            /* kernel evaluations of the completed jobs         */
+  double seconds;                 /* since creation or the last kkm_server_reset_stats */
+  uint64_t bytes_in_use, peak_bytes;  /* admission accounting (estimates)            */
+} kkm_serving_stats;
+
+/* Starts the workers.  KKM_EINVAL for a zero budget or n_workers > 64. */
+kkm_status kkm_server_create(const kkm_server_config* cfg, kkm_server** out);
+/* Runs every queued job to the end, stops the workers, frees the resident
+ * models and the server. */
+void kkm_server_destroy(kkm_server* s);
+/* Makes a fitted model resident; the server takes ownership (do not free it).
+ * KKM_EBUDGET if the resident models would exceed the budget. */
+kkm_status kkm_server_add_model(kkm_server* s, kkm_model* m, int32_t* model_id);
+/* Releases a resident model (after its running jobs); KKM_EINVAL if jobs
+ * for it are still queued or the id is unknown. */
+kkm_status kkm_server_remove_model(kkm_server* s, int32_t model_id);
+/* Queues kkm_fit(p...) (p->opt.stream is ignored).  keep_model != 0 makes the
+ * fitted model resident; kkm_server_wait then gives its id.  KKM_EBUDGET if
+ * the job could never fit in the budget. */
+kkm_status kkm_server_submit_fit(kkm_server* s, const kkm_problem* p, int32_t keep_model,
+                                 uint64_t* ticket);
+/* Queues kkm_assign(model, X[M][d], mode) into labels_out[M] and dist_out[M]
+ * (nullable), host or device memory. */
+kkm_status kkm_server_submit_assign(kkm_server* s, int32_t model_id, const float* X, int64_t M,
+                                    int32_t mode, int32_t* labels_out, float* dist_out,
+                                    uint64_t* ticket);
+/* Waits up to timeout_ms (< 0: no limit) for the job.  On KKM_OK the job has
+ * finished: *job_status is its status (kkm_last_error has its message) and
+ * *model_id_out (nullable) the id of a kept model, else -1; the ticket is
+ * then consumed.  KKM_ETIMEOUT if it has not finished in time. */
+kkm_status kkm_server_wait(kkm_server* s, uint64_t ticket, int32_t timeout_ms,
+                           kkm_status* job_status, int32_t* model_id_out);
+kkm_status kkm_server_stats(kkm_server* s, kkm_serving_stats* out);
+kkm_status kkm_server_reset_stats(kkm_server* s);
+
+/*
  * kkm_assign -- label new samples against a fitted model: Eq. 15 with the
  * model's landmark supports (mode KKM_ASSIGN_SUPPORTS) or Eq. 2 against its
  * medoids (KKM_ASSIGN_MEDOIDS).  Ties go to the lowest cluster index.

@@ -284,36 +284,39 @@ cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supp
 
 // ----------------------------------------------------------- g_hat reduce
 // g_hat_j = (sum of the per-(unit, strip) numerators of cluster j) / n_j^2,
-// once per iteration by one CTA (one warp per cluster, FP64, fixed order).
-__global__ void __launch_bounds__(1024)
+// once per iteration.  One CTA per cluster: FP64 runs at 1/64 of the FP32
+// rate on this GPU, so the additions are spread over C SMs (thread t adds
+// entries t, t + 128, ... in order, then a fixed-shape block tree).
+constexpr int kGhatThreads = 128;
+
+__global__ void __launch_bounds__(kGhatThreads)
 ghat_reduce_kernel(Supports S, const double* __restrict__ gpart, int n_strips, double* __restrict__ ghat,
                    const int32_t* __restrict__ skip) {
+  __shared__ double red[kGhatThreads / 32];
   griddep_wait();
   griddep_launch();
   if (skip && *skip) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = w; j < S.C; j += nw) {
-    const int64_t e0 = (int64_t)S.seg_unit[j] * n_strips, e1 = (int64_t)S.seg_unit[j + 1] * n_strips;
-    double acc = 0.0;
-    for (int64_t e = e0 + lane; e < e1; e += 32 * 8) {
-      double v[8];
+  const int j = blockIdx.x;
+  const int64_t e0 = (int64_t)S.seg_unit[j] * n_strips, e1 = (int64_t)S.seg_unit[j + 1] * n_strips;
+  double acc = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += kGhatThreads * 4) {
+    double v[4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (e + 32 * q < e1) ? gpart[e + 32 * q] : 0.0;
+    for (int q = 0; q < 4; ++q) v[q] = (e + kGhatThreads * q < e1) ? gpart[e + kGhatThreads * q] : 0.0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc += v[q];
-    }
-    acc = warp_sum_f64(acc);
-    if (lane == 0) {
-      const int n = S.n_j[j];
-      ghat[j] = n > 0 ? acc / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
-    }
+    for (int q = 0; q < 4; ++q) acc += v[q];
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    const int n = S.n_j[j];
+    ghat[j] = n > 0 ? acc / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
   }
 }
 
 cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st) {
-  const int threads = 32 * std::min(std::max(S.C, 1), 32);
-  return launch_pdl(ghat_reduce_kernel, dim3(1), dim3(threads), 0, st, S, (const double*)I.gpart, I.n_strips,
-                    I.ghat_cur, (const int32_t*)I.done);
+  if (S.C <= 0) return cudaSuccess;
+  return launch_pdl(ghat_reduce_kernel, dim3((unsigned)S.C), dim3(kGhatThreads), 0, st, S,
+                    (const double*)I.gpart, I.n_strips, I.ghat_cur, (const int32_t*)I.done);
 }
 
 // ----------------------------------------------------------- L2 priorities
@@ -366,10 +369,6 @@ struct AssignShared {
   int su[kMaxC + 1];
 };
 
-// n_j, unit ranges and g_hat into shared memory.  g_hat_j is given (assign
-// against a model) or reduced here from the per-(unit, strip) numerators:
-// one warp per cluster, all loads of a lane issued before they are added, in
-// a fixed order.
 // n_j, unit ranges and g_hat into shared memory (g_hat given for an assign
 // against a model, else computed by ghat_reduce for this iteration).
 __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
@@ -407,20 +406,25 @@ __device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __
   return f / (float)sh.nj[j];
 }
 
-// One CTA per 32 rows: warp w forms d_ij for the clusters j = w, w + nw, ...
-// of its 32 rows (lane = row), each lane adding only the partials of its own
-// cluster (coalesced across the warp); warp 0 then takes the argmin over the
-// clusters from shared memory.
+// One CTA per 32 rows (up to 8 warps, so every CTA of a launch is resident at
+// once): warp w forms d_ij for a contiguous range of clusters of its 32 rows
+// (lane = row; each unit's partials are one coalesced 128-byte line); warp 0
+// then takes the argmin over the clusters from shared memory.
 //
-// Near-tie re-score (low-precision kernel blocks, R.Xi != NULL): rows whose
-// margin d2 - d1 is below flag_tau * max(|d2|, K_ii + g_hat) get every
-// cluster's distance recomputed by the whole CTA from exact FP32 kernel
-// values over the supports (dot products of the FP32 rows, the same norm
-// expansion and exponential as the FP32 block; warp w takes landmarks
-// w, w + nw, ... of each segment, warp sums added in warp order).
+// Near-tie re-score (low-precision kernel blocks, R.Xi != NULL): a row's
+// candidates are the clusters j with d_j - d_best below
+// flag_tau * max(|d_j|, K_ii + g_hat_best) (the best one included); a row
+// with two or more is flagged, and the whole CTA recomputes its candidates'
+// distances from exact FP32 kernel values over their supports (dot products
+// of the FP32 rows, the same norm expansion and exponential as the FP32
+// block; warp w takes landmarks w, w + nw, ... of the segment, warp sums
+// added in warp order).  The other clusters are farther than the window, so
+// the low-precision error (well inside it) cannot make one of them the best.
 constexpr int kAssignRows = 32;
 
-__global__ void __launch_bounds__(1024)
+constexpr int kAssignWarps = 8;
+
+__global__ void __launch_bounds__(kAssignWarps * 32, 4)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
@@ -444,20 +448,11 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   const int i = blockIdx.x * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
   const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
-  for (int j = w; j < C; j += nw) {
+  // d_ij of cluster j from the unit sum f (the units of j added in order)
+  auto finish = [&](int j, float f) {
     float dj = inf;
     if (i < Ni) {
       if (sh.nj[j] > 0) {
-        const int e = sh.su[j + 1];
-        float f = 0.0f;
-        for (int un = sh.su[j]; un < e; un += 8) {
-          float v[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = (un + q < e) ? partial_at(I.partial, ldk, un + q, i) : 0.0f;
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (un + q < e) f += v[q];
-        }
         const float fh = f / (float)sh.nj[j];
         if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
         dj = ks - 2.0f * fh + sh.ghf[j];
@@ -466,6 +461,37 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       }
     }
     dsh[j][lane] = dj;
+  };
+  // Warp w takes the contiguous clusters [jb, je), whose units are contiguous
+  // too: one flat pass over them keeps 8 loads in flight across cluster
+  // boundaries (j and its end are the same in every lane).
+  const int jb = (w * C) / nw, je = ((w + 1) * C) / nw;
+  if (jb < je) {
+    int j = jb;
+    int jend = sh.su[j + 1];
+    float f = 0.0f;
+    const int E = sh.su[je];
+    for (int un = sh.su[jb]; un < E; un += 8) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (un + q < E && i < Ni) ? partial_at(I.partial, ldk, un + q, i) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (un + q < E) {
+          while (un + q >= jend) {
+            finish(j, f);
+            f = 0.0f;
+            ++j;
+            jend = sh.su[j + 1];
+          }
+          f += v[q];
+        }
+      }
+    }
+    for (; j < je; ++j) {
+      finish(j, f);
+      f = 0.0f;
+    }
   }
   __syncthreads();
   if (w == 0) {
@@ -503,7 +529,11 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     __syncthreads();
     const float ni = R.nXi[ir];
     const float ksr = kself ? kself[ir] : 1.0f;
+    const float b0 = rbest[r];
+    const float scale = ksr + sh.ghf[rlab[r]];
     for (int j = 0; j < C; ++j) {
+      const float dj0 = dsh[j][r];  // low-precision value (same in every thread)
+      if (!(dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale))) continue;
       const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
       float acc = 0.0f;
       for (int kk = k0 + w; kk < k1; kk += nw) {
@@ -617,7 +647,7 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st, const RescoreArgs& R) {
   if (Ni <= 0) return cudaSuccess;
-  const int threads = 32 * std::min(S.C, 32);
+  const int threads = 32 * std::min(S.C, kAssignWarps);
   const size_t smem = R.Xi ? (size_t)R.dp * sizeof(float) : 0;
   if (smem > 8 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -49,6 +49,21 @@ class kkm_problem(ctypes.Structure):
                 ("opt", kkm_options), ("labels_out", ctypes.c_void_p)]
 
 
+class kkm_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("n_workers", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_batch_rows", ctypes.c_int64)]
+
+
+class kkm_serving_stats(ctypes.Structure):
+    _fields_ = [("completed_fit", ctypes.c_int64), ("completed_assign", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("refused", ctypes.c_int64),
+                ("fused_assign_launches", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("p50_fit_ms", ctypes.c_double), ("p99_fit_ms", ctypes.c_double),
+                ("p50_assign_ms", ctypes.c_double), ("p99_assign_ms", ctypes.c_double),
+                ("kernel_evals", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I32, _I64, _U64, _F32, _F64 = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -59,6 +74,15 @@ _SIGNATURES = {
     "kkm_fit": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
                        ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P)]),
     "kkm_fit_batch": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "kkm_server_create": (_I32, [ctypes.POINTER(kkm_server_config), ctypes.POINTER(_P)]),
+    "kkm_server_destroy": (None, [_P]),
+    "kkm_server_add_model": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
+    "kkm_server_remove_model": (_I32, [_P, _I32]),
+    "kkm_server_submit_fit": (_I32, [_P, _P, _I32, ctypes.POINTER(_U64)]),
+    "kkm_server_submit_assign": (_I32, [_P, _I32, _P, _I64, _I32, _P, _P, ctypes.POINTER(_U64)]),
+    "kkm_server_wait": (_I32, [_P, _U64, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    "kkm_server_stats": (_I32, [_P, ctypes.POINTER(kkm_serving_stats)]),
+    "kkm_server_reset_stats": (_I32, [_P]),
     "kkm_assign": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "kkm_cost": (_I32, [_P, _P, _I64, _I32, ctypes.POINTER(_F64), _P]),
     "kkm_model_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I64), ctypes.POINTER(_I32),
@@ -173,6 +197,11 @@ class Model:
             _lib.kkm_model_free(self._h)
             self._h = None
 
+    def release(self):
+        """Gives up ownership of the C handle (e.g. to a server) and returns it."""
+        h, self._h = self._h, None
+        return h
+
     def info(self):
         C, d, nL, sig = _I32(), _I64(), _I32(), _F32()
         _check(load().kkm_model_info(self._h, ctypes.byref(C), ctypes.byref(d), ctypes.byref(nL),
@@ -242,32 +271,7 @@ def kkm_fit_batch(problems, n_streams=0, stream=None, check=True):
     arr = (kkm_problem * max(n, 1))()
     keep, outs = [], []
     for i, p in enumerate(problems):
-        X = p["X"]
-        xp, kx = _as_input(X, np.float32)
-        keep.append(kx)
-        q = arr[i]
-        q.X = xp
-        q.N = int(X.shape[0])
-        q.d = int(np.prod(X.shape[1:]))
-        q.C, q.B, q.s = int(p["C"]), int(p["B"]), float(p["s"])
-        q.kernel = _kernel(p.get("kind", "rbf"), p.get("sigma", 0.0), p.get("n_atoms", 0))
-        q.iters = int(p.get("iters", 20))
-        q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
-        lib.kkm_options_default(ctypes.byref(q.opt))
-        q.opt.precision = int(p.get("precision", KKM_FP32))
-        smp = p.get("sampling", "stride")
-        q.opt.sampling = SAMPLING[smp] if isinstance(smp, str) else int(smp)
-        q.opt.early_stop = 1 if p.get("early_stop", True) else 0
-        if p.get("init_medoids") is not None:
-            ia = np.ascontiguousarray(p["init_medoids"], dtype=np.int64)
-            keep.append(ia)
-            q.opt.init_medoids = ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-        if p.get("labels", True):
-            lp, lab = _out_like(X, q.N, np.int32)
-            q.labels_out = lp
-        else:
-            lab = None
-        outs.append(lab)
+        outs.append(_fill_problem(arr[i], p, keep))
     models = (ctypes.c_void_p * max(n, 1))()
     status = (ctypes.c_int32 * max(n, 1))()
     if stream is None:
@@ -277,6 +281,110 @@ def kkm_fit_batch(problems, n_streams=0, stream=None, check=True):
         _check(rc)
     del keep
     return [(outs[i], Model(ctypes.c_void_p(models[i])) if models[i] else None, status[i]) for i in range(n)]
+
+
+def _fill_problem(q, p, keep):
+    """Fills a kkm_problem from a dict; returns the labels buffer (or None)."""
+    lib = load()
+    X = p["X"]
+    xp, kx = _as_input(X, np.float32)
+    keep.append(kx)
+    q.X = xp
+    q.N = int(X.shape[0])
+    q.d = int(np.prod(X.shape[1:]))
+    q.C, q.B, q.s = int(p["C"]), int(p["B"]), float(p["s"])
+    q.kernel = _kernel(p.get("kind", "rbf"), p.get("sigma", 0.0), p.get("n_atoms", 0))
+    q.iters = int(p.get("iters", 20))
+    q.seed = int(p.get("seed", 0)) & ((1 << 64) - 1)
+    lib.kkm_options_default(ctypes.byref(q.opt))
+    q.opt.precision = int(p.get("precision", KKM_FP32))
+    smp = p.get("sampling", "stride")
+    q.opt.sampling = SAMPLING[smp] if isinstance(smp, str) else int(smp)
+    q.opt.early_stop = 1 if p.get("early_stop", True) else 0
+    if p.get("init_medoids") is not None:
+        ia = np.ascontiguousarray(p["init_medoids"], dtype=np.int64)
+        keep.append(ia)
+        q.opt.init_medoids = ia.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if p.get("labels", True):
+        lp, lab = _out_like(X, q.N, np.int32)
+        q.labels_out = lp
+        keep.append(lab)
+    else:
+        lab = None
+    return lab
+
+
+class Server:
+    """kkm_server of the C ABI: a request loop for fit and assign jobs.
+
+    submit_fit / submit_assign return a ticket; wait(ticket) returns the
+    job's outputs.  Inputs may be host arrays or CUDA tensors and must not be
+    modified before the job is collected."""
+
+    def __init__(self, budget_bytes, n_workers=0, max_batch_rows=0):
+        lib = load()
+        cfg = kkm_server_config(int(budget_bytes), int(n_workers), 0, int(max_batch_rows))
+        h = ctypes.c_void_p()
+        _check(lib.kkm_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().kkm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+    def add_model(self, model):
+        mid = _I32()
+        _check(load().kkm_server_add_model(self._h, model.handle, ctypes.byref(mid)))
+        model.release()
+        return mid.value
+
+    def remove_model(self, model_id):
+        _check(load().kkm_server_remove_model(self._h, int(model_id)))
+
+    def submit_fit(self, problem, keep_model=False):
+        keep = []
+        q = kkm_problem()
+        lab = _fill_problem(q, problem, keep)
+        t = _U64()
+        _check(load().kkm_server_submit_fit(self._h, ctypes.byref(q), 1 if keep_model else 0, ctypes.byref(t)))
+        self._pending[t.value] = (keep, lab)
+        return t.value
+
+    def submit_assign(self, model_id, X, mode="supports"):
+        M = int(X.shape[0])
+        xp, kx = _as_input(X, np.float32)
+        lp, lab = _out_like(X, M, np.int32)
+        dp, dist = _out_like(X, M, np.float32)
+        t = _U64()
+        _check(load().kkm_server_submit_assign(self._h, int(model_id), xp, M,
+                                               MODE[mode] if isinstance(mode, str) else int(mode), lp, dp,
+                                               ctypes.byref(t)))
+        self._pending[t.value] = ([kx, lab, dist], (lab, dist))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Returns (status, outputs, model id): outputs are the labels of a
+        fit, or (labels, squared distances) of an assign.  Raises KKMError
+        with KKM_ETIMEOUT if the job is not done within timeout_ms."""
+        st, mid = _I32(), _I32()
+        _check(load().kkm_server_wait(self._h, int(ticket), int(timeout_ms), ctypes.byref(st), ctypes.byref(mid)))
+        err = last_error() if st.value != 0 else ""
+        keep, out = self._pending.pop(ticket)
+        return st.value, out, mid.value, err
+
+    def stats(self):
+        s = kkm_serving_stats()
+        _check(load().kkm_server_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in kkm_serving_stats._fields_}
+
+    def reset_stats(self):
+        _check(load().kkm_server_reset_stats(self._h))
 
 
 def kkm_assign(model, Xnew, mode="supports", stream=None):

@@ -82,3 +82,17 @@ def test_batched_workload_shapes_are_valid():
         assert p["B"] == -(-p["N"] // 10000) and p["s"] in (0.1, 0.5)
         for i in range(p["B"]):
             assert (p["N"] - i + p["B"] - 1) // p["B"] >= p["C"]
+
+
+def test_server_rejects_bad_config_before_any_device_call(kkm):
+    """kkm_server_create checks its arguments first (no GPU needed)."""
+    import ctypes
+    lib = kkm.load()
+    h = ctypes.c_void_p()
+    for cfg in (kkm.kkm_server_config(0, 0, 0, 0), kkm.kkm_server_config(1 << 30, 65, 0, 0),
+                kkm.kkm_server_config(1 << 30, -1, 0, 0), kkm.kkm_server_config(1 << 30, 2, 1, 0)):
+        assert lib.kkm_server_create(ctypes.byref(cfg), ctypes.byref(h)) == kkm.STATUS_EINVAL
+        assert not h.value
+    assert lib.kkm_fit_batch(None, -1, 0, None, None, None) == kkm.STATUS_EINVAL
+    assert lib.kkm_fit_batch(None, 1, 0, None, None, None) == kkm.STATUS_EINVAL
+    assert lib.kkm_fit_batch(None, 0, 65, None, None, None) == kkm.STATUS_EINVAL

@@ -50,13 +50,13 @@ def _same_model(a, b):
     assert np.array_equal(_np(la), _np(lb))
     oa, ca = ma.trace()
     ob, cb = mb.trace()
-    assert np.array_equal(oa, ob) and np.array_equal(ca, cb)
+    assert np.array_equal(oa, ob, equal_nan=True) and np.array_equal(ca, cb)
     ia, wa, xa = ma.medoids()
     ib, wb, xb = mb.medoids()
     assert np.array_equal(ia, ib) and np.array_equal(wa, wb) and np.array_equal(xa, xb)
     sa, ga, na = ma.supports()
     sb, gb, nb = mb.supports()
-    assert np.array_equal(sa, sb) and np.array_equal(ga, gb) and np.array_equal(na, nb)
+    assert np.array_equal(sa, sb) and np.array_equal(ga, gb, equal_nan=True) and np.array_equal(na, nb)
 
 
 @pytest.mark.parametrize("n_streams", [1, 4, 12])

@@ -346,12 +346,13 @@ def run_ours(args, cfg, X):
                 "work_per_launch": f"18*n_atoms flop per pair (3x3 correlation) = {flops:.4g} flop"}
     elif dom == "fhat_partial":
         n, tms = prof[dom]
-        by = 4.0 * Ni * nL
+        esz = 2 if (HEAD == kkm.KKM_BF16 and kind == "rbf") else 4   # the BF16 path stores the block in FP16
+        by = esz * Ni * nL
         ach = by / (tms / n / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": ncu_traffic("fhat_partial"),
                 "kernel": "fhat_partial", "peak_source": peak_kind,
-                "work_per_launch": f"4*N_i*|L| = {by:.4g} B (one read of the kernel block)"}
+                "work_per_launch": f"{esz}*N_i*|L| = {by:.4g} B (one read of the kernel block)"}
 
     # ---- CPU baseline: the oracle on a bounded sample
     ev, dt = oracle_sample(X, CPU_SAMPLE_ROWS[cfg["key"]], cfg)
@@ -517,7 +518,8 @@ def run_batched(args, cfg):
         return
 
     peaks, peak_kind = measured_peaks()
-    fh_bytes = sum(4.0 * ((p["N"] - i + p["B"] - 1) // p["B"]) * n_landmarks((p["N"] - i + p["B"] - 1) // p["B"], p["s"])
+    esz = 2.0 if HEAD == kkm.KKM_BF16 else 4.0   # the BF16 path stores the block in FP16
+    fh_bytes = sum(esz * ((p["N"] - i + p["B"] - 1) // p["B"]) * n_landmarks((p["N"] - i + p["B"] - 1) // p["B"], p["s"])
                    * (iters + 1) for p in shapes for i in range(p["B"]))
     gr_flops = sum(2.0 * ((p["N"] - i + p["B"] - 1) // p["B"]) * n_landmarks((p["N"] - i + p["B"] - 1) // p["B"], p["s"])
                    * p["d"] for p in shapes for i in range(p["B"]))
@@ -528,7 +530,7 @@ def run_batched(args, cfg):
         cands["fhat_partial"] = (tms, {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                        "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "fhat_partial",
                                        "peak_source": peak_kind,
-                                       "work_per_launch": f"4*N_i*|L| B per launch; {fh_bytes:.4g} B over the "
+                                       "work_per_launch": f"{esz:.0f}*N_i*|L| B per launch; {fh_bytes:.4g} B over the "
                                                           f"{n // args.steps} launches of a step"})
     if "gram_block" in prof:
         n, tms = prof["gram_block"]

@@ -324,19 +324,20 @@ static int sm_count() {
 // L (nullable): local sample positions of the reference rows; their diagonal
 // entries are then set to exactly 1 (Gaussian kernels).
 static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const int32_t* L, int64_t nP,
-                                    const float* Q, int64_t nQ, float* out, int64_t ldo, __nv_bfloat16* Pb,
-                                    float* nPb, __nv_bfloat16* Qb, float* nQb, int* err, cudaStream_t st) {
+                                    const float* Q, int64_t nQ, void* out, bool out_half, int64_t ldo,
+                                    __nv_bfloat16* Pb, float* nPb, __nv_bfloat16* Qb, float* nQb, int* err,
+                                    cudaStream_t st) {
   KKM_RUN("to_bf16", st, launch_to_bf16(P, nP, sp.dp, Pb, nPb, st));
   KKM_RUN("to_bf16", st, launch_to_bf16(Q, nQ, sp.dp, Qb, nQb, st));
   const int dk = (int)sp.d;
   KKM_RUN("gram_block", st,
           launch_gram_tc(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Pb, nP, Qb, nQ, dk, sp.dp, nPb, nQb,
-                         sp.neg_scale(), out, ldo, err, sm_count(), st));
-  if (L && sp.kind != KKM_LINEAR) KKM_RUN("set_diag", st, launch_set_diag(out, ldo, L, (int)nP, st));
+                         sp.neg_scale(), out, out_half, ldo, err, sm_count(), st));
+  if (L && sp.kind != KKM_LINEAR) KKM_RUN("set_diag", st, launch_set_diag(out, out_half, ldo, L, (int)nP, st));
   return KKM_OK;
 }
 
-int l2_keep_rows(int64_t ldk, int rows, double share) {
+int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes) {
   static const int l2 = []() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -344,7 +345,7 @@ int l2_keep_rows(int64_t ldk, int rows, double share) {
     cudaGetLastError();
     return v;
   }();
-  const double row_bytes = (double)ldk * 4.0;
+  const double row_bytes = (double)ldk * (double)elem_bytes;
   return (int)std::min<double>(rows, std::floor(share * (double)l2 / row_bytes));
 }
 
@@ -429,6 +430,8 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.lm_changed, 1));
   KKM_TRY(ws.alloc(&I.ticket_sink, 1));
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
+  KKM_TRY(ws.alloc(&I.gtick, C));
+  KKM_CK(cudaMemsetAsync(I.gtick, 0, (size_t)C * 4, ws.st));
   KKM_TRY(ws.alloc(&I.ticket, 1));
   KKM_TRY(ws.alloc(&I.done, 1));
   KKM_TRY(ws.alloc(&I.trace_omega, std::max(trace_cap, 1)));
@@ -582,7 +585,16 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(ws.alloc(&XL, nLmax * sp.dp));
   KKM_TRY(ws.alloc(&auxL, nLmax));
   KKM_TRY(ws.alloc(&gidL, nLmax));
-  KKM_TRY(ws.alloc(&KT, nLmax * ldk));
+  // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
+  // significand, finer than the BF16 inputs' rounding): the inner loop
+  // streams half the bytes.
+  const bool kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
+  __half* KTh = nullptr;
+  KT = nullptr;
+  if (kt_half)
+    KKM_TRY(ws.alloc(&KTh, nLmax * ldk));
+  else
+    KKM_TRY(ws.alloc(&KT, nLmax * ldk));
   KKM_TRY(ws.alloc(&Kt, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&Kmi, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&MX, (int64_t)C * sp.dp));
@@ -649,7 +661,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
     KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
     if (sp.precision == KKM_BF16)                                                // Alg. 1 line 3
-      KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, KT, ldk, XLb, nXLb, Xib, nXib, tc_err, st));
+      KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, kt_half ? (void*)KTh : (void*)KT, kt_half, ldk, XLb, nXLb,
+                                Xib, nXib, tc_err, st));
     else
       KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));
     // L2 hygiene for the inner loop: the BF16 copies are not read again
@@ -680,7 +693,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, nullptr, st));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
     const bool rescore = sp.precision != KKM_FP32;
-    I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare);
+    I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare, kt_half ? 2 : 4);
     I.flag_tau = rescore ? kRescoreMargin : 0.0f;
     RescoreArgs R;
     if (rescore) {
@@ -693,8 +706,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       R.neg_scale = sp.neg_scale();
     }
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
-      KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, I, st));
-      KKM_RUN("ghat_reduce", st, launch_ghat_reduce(S, I, st));
+      KKM_RUN("fhat_partial", st,
+              kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, I, st) : launch_fhat_partial(KT, ldk, Ni, S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
                             /*trace=*/1, st, R));
@@ -704,8 +717,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
     Ifin.done = nullptr;
-    KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, Ni, S, Ifin, st));
-    KKM_RUN("ghat_reduce", st, launch_ghat_reduce(S, Ifin, st));
+    KKM_RUN("fhat_partial", st,
+            kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, Ifin, st) : launch_fhat_partial(KT, ldk, Ni, S, Ifin, st));
     KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
     KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, st));
     KKM_RUN("medoid_keys", st, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, st));
@@ -985,7 +998,7 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
     KKM_TRY(ws.alloc(&nBb, nB));
     KKM_TRY(ws.alloc(&err, 1));
     KKM_CK(cudaMemsetAsync(err, 0, 4, st));
-    KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nB, o, nB, Ab, nAb, Bb, nBb, err, st));
+    KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nB, o, false, nB, Ab, nAb, Bb, nBb, err, st));
     KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
   } else {
     KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
@@ -1058,7 +1071,6 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
   const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
   KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
-  KKM_RUN("ghat_reduce", st, launch_ghat_reduce(lb.S, lb.I, st));
   KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));

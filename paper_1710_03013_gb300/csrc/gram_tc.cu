@@ -28,6 +28,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -49,28 +50,7 @@ constexpr uint32_t TC_SPIN_LIMIT = 1u << 24;  // bounded mbarrier waits
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 2048;
 
 // ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
+// (smem_u32, mbarrier init / expect_tx / arrive / try_wait: device_common.cuh)
 // Bounded wait for the phase of the given parity; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   for (uint32_t it = 0; it < TC_SPIN_LIMIT; ++it) {
@@ -153,11 +133,15 @@ struct TcShared {
   float nP[8][TC_N / 2];    // reference norms of the current tile, per epilogue warp
 };
 
-template <int KIND>
+__device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_out(__half* p, float v) { *p = __float2half_rn(v); }
+
+// OutT: float, or __half for a Gaussian kernel block (values in [0, 1]).
+template <int KIND, typename OutT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
                int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
-               float neg_scale, float* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+               float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // stages must start on a 1024-byte boundary (swizzle atom)
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -291,7 +275,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       const float nq = mvalid ? normQ[m] : 0.0f;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + half * (TC_N / 2));
       const int ncols = min(TC_N / 2, nP - n0);  // valid reference rows of this warp (may be <= 0)
-      float* orow = out + (int64_t)n0 * ldo + m;
+      OutT* orow = out + (int64_t)n0 * ldo + m;
 #pragma unroll 1
       for (int c0 = 0; c0 < TC_N / 2; c0 += 32) {
         uint32_t r[32];
@@ -309,7 +293,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
                 if (KIND == DK_DIST) v = sqrtf(d2);
                 else v = fast_exp2(d2 * neg_scale);
               }
-              orow[(int64_t)(c0 + c) * ldo] = v;
+              store_out(orow + (int64_t)(c0 + c) * ldo, v);
             }
           } else {
 #pragma unroll
@@ -324,7 +308,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
                   if (KIND == DK_DIST) v = sqrtf(d2);
                   else v = fast_exp2(d2 * neg_scale);
                 }
-                orow[(int64_t)(c0 + c) * ldo] = v;
+                store_out(orow + (int64_t)(c0 + c) * ldo, v);
               }
             }
           }
@@ -376,22 +360,16 @@ static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t c
   return r == CUDA_SUCCESS;
 }
 
-cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
-                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, float* out,
-                           int64_t ldo, int* err, int n_sms, cudaStream_t st) {
-  if (nP <= 0 || nQ <= 0) return cudaSuccess;
-  if ((ldb * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15))
-    return cudaErrorInvalidValue;
-  alignas(64) CUtensorMap mq, mp;
-  if (!make_map(&mq, Q, nQ, dk, ldb, TC_M) || !make_map(&mp, P, nP, dk, ldb, TC_N)) return cudaErrorInvalidValue;
-  const int64_t tiles = ceil_div(nQ, TC_M) * ceil_div(nP, TC_N);
-  const int grid = (int)std::min<int64_t>(tiles, std::max(n_sms, 1));
+template <typename OutT>
+static cudaError_t launch_gram_tc_t(int kind, const CUtensorMap& mq, const CUtensorMap& mp, int nQ, int nP, int dk,
+                                    const float* normP, const float* normQ, float neg_scale, OutT* out,
+                                    int64_t ldo, int* err, int grid, cudaStream_t st) {
   cudaError_t e;
-#define KKM_TC_LAUNCH(K)                                                                             \
-  e = cudaFuncSetAttribute(gram_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
-  if (e != cudaSuccess) return e;                                                                    \
-  gram_tc_kernel<K><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, (int)nQ, (int)nP, dk, normQ, normP, neg_scale, \
-                                                       out, ldo, err);
+#define KKM_TC_LAUNCH(K)                                                                                  \
+  e = cudaFuncSetAttribute(gram_tc_kernel<K, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
+  if (e != cudaSuccess) return e;                                                                         \
+  gram_tc_kernel<K, OutT><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, nQ, nP, dk, normQ, normP, neg_scale, out, \
+                                                             ldo, err);
   if (kind == DK_DIST) {
     KKM_TC_LAUNCH(DK_DIST)
   } else if (kind == DK_LINEAR) {
@@ -403,14 +381,36 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
   return cudaGetLastError();
 }
 
-// K = 1 on the diagonal of the block: out[k][L[k]] for landmark ordinals k.
-__global__ void set_diag_kernel(float* __restrict__ out, int64_t ldo, const int32_t* __restrict__ L, int nL) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < nL) out[(int64_t)k * ldo + L[k]] = 1.0f;
+cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
+                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, void* out,
+                           bool out_half, int64_t ldo, int* err, int n_sms, cudaStream_t st) {
+  if (nP <= 0 || nQ <= 0) return cudaSuccess;
+  if ((ldb * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15))
+    return cudaErrorInvalidValue;
+  if (out_half && kind != DK_RBF) return cudaErrorInvalidValue;  // FP16 holds values in [0, 1] only
+  alignas(64) CUtensorMap mq, mp;
+  if (!make_map(&mq, Q, nQ, dk, ldb, TC_M) || !make_map(&mp, P, nP, dk, ldb, TC_N)) return cudaErrorInvalidValue;
+  const int64_t tiles = ceil_div(nQ, TC_M) * ceil_div(nP, TC_N);
+  const int grid = (int)std::min<int64_t>(tiles, std::max(n_sms, 1));
+  if (out_half)
+    return launch_gram_tc_t(kind, mq, mp, (int)nQ, (int)nP, dk, normP, normQ, neg_scale,
+                            static_cast<__half*>(out), ldo, err, grid, st);
+  return launch_gram_tc_t(kind, mq, mp, (int)nQ, (int)nP, dk, normP, normQ, neg_scale, static_cast<float*>(out),
+                          ldo, err, grid, st);
 }
-cudaError_t launch_set_diag(float* out, int64_t ldo, const int32_t* L, int nL, cudaStream_t st) {
+
+// K = 1 on the diagonal of the block: out[k][L[k]] for landmark ordinals k.
+template <typename T>
+__global__ void set_diag_kernel(T* __restrict__ out, int64_t ldo, const int32_t* __restrict__ L, int nL) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nL) out[(int64_t)k * ldo + L[k]] = T(1.0f);
+}
+cudaError_t launch_set_diag(void* out, bool out_half, int64_t ldo, const int32_t* L, int nL, cudaStream_t st) {
   if (nL <= 0) return cudaSuccess;
-  set_diag_kernel<<<(unsigned)ceil_div(nL, 256), 256, 0, st>>>(out, ldo, L, nL);
+  if (out_half)
+    set_diag_kernel<__half><<<(unsigned)ceil_div(nL, 256), 256, 0, st>>>(static_cast<__half*>(out), ldo, L, nL);
+  else
+    set_diag_kernel<float><<<(unsigned)ceil_div(nL, 256), 256, 0, st>>>(static_cast<float*>(out), ldo, L, nL);
   return cudaGetLastError();
 }
 

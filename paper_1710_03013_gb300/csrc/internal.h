@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -84,7 +85,7 @@ void prof_collect();  // after a stream sync: fold finished events into totals
 
 // --------------------------------------------------------------- layouts ---
 constexpr int kUnitRows = 64;     // landmark rows per f_hat streaming unit
-constexpr int kStripCols = 512;   // sample columns per streaming CTA (128 x float4)
+constexpr int kStripCols = 512;   // narrowest f_hat strip (FP32: 128 threads x 4 columns); sizes gpart
 constexpr int kMaxC = 256;     // clusters per problem (one scan slot per thread of a 256-thread CTA)
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -119,13 +120,14 @@ cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, i
 
 // ---- tensor-core (tcgen05) BF16 kernel block ----------------------------
 // out[n*ldo + m] = kappa(P_n, Q_m) for BF16 rows P [nP][ldb], Q [nQ][ldb]
-// (dk valid columns), with the squared norms of the BF16 rows.  *err gets a
-// nonzero code if a bounded wait gave up.
+// (dk valid columns), with the squared norms of the BF16 rows; out is float,
+// or __half when out_half (Gaussian kernel only: values in [0, 1]).  *err gets
+// a nonzero code if a bounded wait gave up.
 cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ,
-                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, float* out,
-                           int64_t ldo, int* err, int n_sms, cudaStream_t st);
+                           int dk, int ldb, const float* normP, const float* normQ, float neg_scale, void* out,
+                           bool out_half, int64_t ldo, int* err, int n_sms, cudaStream_t st);
 // out[k*ldo + L[k]] = 1 (the exact diagonal of a Gaussian kernel block).
-cudaError_t launch_set_diag(float* out, int64_t ldo, const int32_t* L, int nL, cudaStream_t st);
+cudaError_t launch_set_diag(void* out, bool out_half, int64_t ldo, const int32_t* L, int nL, cudaStream_t st);
 // BF16 copy of FP32 rows [n][dp] with the squared norms of the rounded rows.
 cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq,
                            cudaStream_t st);
@@ -167,7 +169,7 @@ inline int max_units_for(int nL, int C) { return (int)(ceil_div(nL, kUnitRows) +
 
 struct IterState {
   float* partial;        // [max_units][ldk]
-  double* gpart;         // [max_units][n_strips]
+  float2* gpart;         // [max_units][n_strips] g_hat numerators, double-float (hi, lo)
   double* omega_part;    // [assign grid]
   int32_t* changed_part; // [assign grid]
   uint32_t* ticket;      // [1], zero between launches
@@ -182,16 +184,15 @@ struct IterState {
   // below flag_tau * max(|d2|, K_ii + g_hat) are re-scored in FP32 by assign
   float flag_tau = 0.0f;
   int32_t* ticket_sink = nullptr;   // [1] write target that keeps L2-demotion loads alive
-  double* ghat_cur = nullptr;       // [C] g_hat of the current supports (ghat_reduce)
+  double* ghat_cur = nullptr;       // [C] g_hat of the current supports (written by fhat_partial)
+  uint32_t* gtick = nullptr;        // [C] per-cluster tile tickets of fhat_partial, zero between launches
   int keep_rows = 0;                // block rows kept in L2 across iterations (evict_last)
   int assign_grid;
   int n_strips;
 };
 // Rows of a [rows][ldk] float block that fit in the given share of L2.
-int l2_keep_rows(int64_t ldk, int rows, double share);
+int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes = 4);
 
-// g_hat of the current supports into I.ghat_cur (one CTA).
-cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st);
 // L2 hygiene: re-read a range with the evict_first policy / drop a range
 // whose contents are not needed again.
 cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st);
@@ -204,6 +205,9 @@ cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const 
 cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st);
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
+                                const IterState& I, cudaStream_t st);
+// The same over a kernel block stored in FP16 (the BF16 path's Gaussian block).
+cudaError_t launch_fhat_partial(const __half* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st);
 // FP32 rows for the near-tie re-score of a low-precision kernel block
 // (Xi == NULL: no re-score).

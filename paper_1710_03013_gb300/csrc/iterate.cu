@@ -10,10 +10,11 @@
 //
 // One iteration is three launches:
 //   fhat_partial  streams KT once (the HBM-bound step): every CTA sums the
-//                 rows of one unit over a 512-column strip with float4 loads
-//                 and writes the partial numerators of f_hat (Eq. 17), plus
-//                 the part of the g_hat numerator (Eq. 16) that falls on
-//                 landmark columns of the same cluster;
+//                 rows of one unit over a strip of columns (16-byte loads,
+//                 FP32 or FP16 storage) and writes the partial numerators of
+//                 f_hat (Eq. 17) and the part of the g_hat numerator (Eq. 16)
+//                 on landmark columns of the same cluster; the last CTA of a
+//                 cluster forms g_hat_j;
 //   assign        adds the partials of each segment in a fixed order, forms
 //                 d_ij = K_ii - 2 f_hat_ij + g_hat_j, takes the argmin (lowest
 //                 j on ties), the margin and the FP64 cost partials, and
@@ -57,7 +58,7 @@ static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 constexpr int kSortThreads = 1024;  // build_supports: one CTA of 32 warps
 constexpr int kLabRegs = 8;         // landmark labels held in registers per thread
 constexpr int kAssignThreads = 256;
-constexpr int kStreamThreads = kStripCols / 4;
+constexpr int kStreamThreads = 128;  // fhat_partial CTA
 
 // Exclusive scan of one int per thread over the whole CTA (blockDim a
 // multiple of 32, at most 1024).  `sh` needs 32 slots.  Returns the
@@ -209,20 +210,59 @@ cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream
 
 // --------------------------------------------------------- f_hat streaming
 // 16-byte load with an L2 eviction-priority policy (createpolicy).
-__device__ __forceinline__ float4 ld_policy(const float* p, uint64_t pol) {
-  float4 v;
+// Streaming shape per stored type: a thread adds `kCols` consecutive columns
+// (one 16-byte load per block row) with `kDepth` rows in flight; a CTA of
+// kStreamThreads threads covers kStrip columns.
+template <typename T>
+struct StreamCfg {
+  static constexpr int kCols = 16 / (int)sizeof(T);   // FP32: 4, FP16: 8
+  static constexpr int kDepth = sizeof(T) == 2 ? 16 : 8;
+  static constexpr int kStrip = kStreamThreads * kCols;
+};
+
+__device__ __forceinline__ void ld16_policy(const float* p, uint64_t pol, float (&v)[4]) {
   asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
                : "l"(p), "l"(pol));
-  return v;
+}
+__device__ __forceinline__ void ld16_policy(const __half* p, uint64_t pol, uint4& u) {
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w)
+               : "l"(p), "l"(pol));
 }
 
+// Double-float (hi + lo, two FP32 numbers) addition: Knuth's TwoSum and a
+// renormalising Fast2Sum, about 44 significant bits from FP32 additions only
+// (FP64 runs at 1/64 of the FP32 rate on this GPU).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float v = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+// f_hat numerators: partial[u][l] = sum over the landmark rows k of unit u of
+// KT[k][l] (in the unit's row order, FP32), for one strip of kStrip columns
+// per CTA; plus the tile's g_hat numerator (its landmark columns of the same
+// cluster), reduced in double-float in a fixed order.  Rows below keep_rows
+// are loaded with an L2 evict_last policy (they stay resident across
+// iterations), the rest evict_first.  The last CTA of cluster j to finish
+// (atomic ticket, no waiting) forms g_hat_j = (sum of the cluster's
+// numerators) / n_j^2 (Eq. 16) in FP64, in a fixed order.
+template <typename T>
 __global__ void __launch_bounds__(kStreamThreads)
-fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports S,
-                    float* __restrict__ partial, double* __restrict__ gpart, int n_strips,
-                    const int32_t* __restrict__ skip, int keep_rows) {
-  __shared__ double red[kStreamThreads / 32];
+fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
+                    float* __restrict__ partial, float2* __restrict__ gpart, int n_strips,
+                    const int32_t* __restrict__ skip, int keep_rows, uint32_t* __restrict__ gtick,
+                    double* __restrict__ ghat) {
+  using Cfg = StreamCfg<T>;
+  constexpr int NC = Cfg::kCols, DEPTH = Cfg::kDepth;
   __shared__ int rows[kUnitRows];
+  __shared__ float2 red[kStreamThreads / 32];
+  __shared__ double redd[kStreamThreads / 32];
+  __shared__ int last;
   griddep_wait();
   griddep_launch();
   if (skip && *skip) return;
@@ -235,88 +275,118 @@ fhat_partial_kernel(const float* __restrict__ KT, int64_t ldk, int Ni, Supports 
   const int nrow = ke - kb;
   for (int t = threadIdx.x; t < nrow; t += kStreamThreads) rows[t] = S.perm[kb + t];
   __syncthreads();
-  // Rows of the block with ordinal < keep_rows stay in L2 across iterations
-  // (evict_last); the rest stream through (evict_first).
   uint64_t keep, stream;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
-  const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * 4;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (col < Ni) {
-    const float* base = KT + col;
-    for (int k = 0; k < nrow; k += 8) {
-      float4 v[8];
+  const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * NC;
+  float acc[NC];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (k + q < nrow) {
-          const int r = rows[k + q];
-          v[q] = ld_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream);
-        } else {
-          v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+  if (col < Ni) {
+    const T* base = KT + col;
+    for (int k = 0; k < nrow; k += DEPTH) {
+      if constexpr (sizeof(T) == 4) {
+        float v[DEPTH][4];
+#pragma unroll
+        for (int q = 0; q < DEPTH; ++q) {
+          if (k + q < nrow) {
+            const int r = rows[k + q];
+            ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
+          } else {
+            v[q][0] = v[q][1] = v[q][2] = v[q][3] = 0.0f;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < DEPTH; ++q)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c] += v[q][c];
+      } else {
+        uint4 v[DEPTH];
+#pragma unroll
+        for (int q = 0; q < DEPTH; ++q) {
+          if (k + q < nrow) {
+            const int r = rows[k + q];
+            ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
+          } else {
+            v[q] = make_uint4(0u, 0u, 0u, 0u);  // +0.0 in FP16
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < DEPTH; ++q) {
+          const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[c]));
+            acc[2 * c] += f.x;
+            acc[2 * c + 1] += f.y;
+          }
         }
       }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
-      }
     }
-    *reinterpret_cast<float4*>(partial + (int64_t)unit * ldk + col) = acc;
+    float* out = partial + (int64_t)unit * ldk + col;
+#pragma unroll
+    for (int c = 0; c < NC; c += 4)
+      *reinterpret_cast<float4*>(out + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
   }
   // g_hat numerator: landmark columns of the same cluster
   if (!S.col_label) return;
-  double g = 0.0;
+  float2 g = make_float2(0.0f, 0.0f);
   if (col < Ni) {
-    const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (col + q < Ni && __ldg(S.col_label + col + q) == j) g += (double)a4[q];
+    for (int c = 0; c < NC; ++c)
+      if (col + c < Ni && __ldg(S.col_label + col + c) == j) g = df_add(g, make_float2(acc[c], 0.0f));
   }
-  g = block_sum(g, red);
-  if (threadIdx.x == 0) gpart[(int64_t)unit * n_strips + blockIdx.x] = g;
-}
-
-cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
-                                const IterState& I, cudaStream_t st) {
-  dim3 grid((unsigned)I.n_strips, (unsigned)S.max_units);
-  return launch_pdl(fhat_partial_kernel, grid, dim3(kStreamThreads), 0, st, KT, ldk, Ni, S, I.partial, I.gpart,
-                    I.n_strips, (const int32_t*)I.done, I.keep_rows);
-}
-
-// ----------------------------------------------------------- g_hat reduce
-// g_hat_j = (sum of the per-(unit, strip) numerators of cluster j) / n_j^2,
-// once per iteration.  One CTA per cluster: FP64 runs at 1/64 of the FP32
-// rate on this GPU, so the additions are spread over C SMs (thread t adds
-// entries t, t + 128, ... in order, then a fixed-shape block tree).
-constexpr int kGhatThreads = 128;
-
-__global__ void __launch_bounds__(kGhatThreads)
-ghat_reduce_kernel(Supports S, const double* __restrict__ gpart, int n_strips, double* __restrict__ ghat,
-                   const int32_t* __restrict__ skip) {
-  __shared__ double red[kGhatThreads / 32];
-  griddep_wait();
-  griddep_launch();
-  if (skip && *skip) return;
-  const int j = blockIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    g = df_add(g, make_float2(__shfl_xor_sync(kFull, g.x, o), __shfl_xor_sync(kFull, g.y, o)));
+  if (lane == 0) red[w] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 t = red[0];
+    for (int q = 1; q < kStreamThreads / 32; ++q) t = df_add(t, red[q]);
+    gpart[(int64_t)unit * n_strips + blockIdx.x] = t;
+    last = 0;
+    if (gtick) {
+      __threadfence();
+      const uint32_t expect = (uint32_t)(S.seg_unit[j + 1] - S.seg_unit[j]) * gridDim.x;
+      last = atomicAdd(gtick + j, 1u) + 1u == expect;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   const int64_t e0 = (int64_t)S.seg_unit[j] * n_strips, e1 = (int64_t)S.seg_unit[j + 1] * n_strips;
-  double acc = 0.0;
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += kGhatThreads * 4) {
-    double v[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (e + kGhatThreads * q < e1) ? gpart[e + kGhatThreads * q] : 0.0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc += v[q];
+  double a2 = 0.0;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += kStreamThreads) {
+    const float2 v = __ldcg(gpart + e);
+    a2 += (double)v.x + (double)v.y;
   }
-  acc = block_sum(acc, red);
+  a2 = block_sum(a2, redd);
   if (threadIdx.x == 0) {
     const int n = S.n_j[j];
-    ghat[j] = n > 0 ? acc / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
+    ghat[j] = n > 0 ? a2 / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
+    gtick[j] = 0u;  // ready for the next launch
   }
 }
 
-cudaError_t launch_ghat_reduce(const Supports& S, const IterState& I, cudaStream_t st) {
-  if (S.C <= 0) return cudaSuccess;
-  return launch_pdl(ghat_reduce_kernel, dim3((unsigned)S.C), dim3(kGhatThreads), 0, st, S,
-                    (const double*)I.gpart, I.n_strips, I.ghat_cur, (const int32_t*)I.done);
+template <typename T>
+static cudaError_t launch_fhat_t(const T* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                                 cudaStream_t st) {
+  const int n_strips = (int)ceil_div(ldk, StreamCfg<T>::kStrip);
+  if (n_strips > I.n_strips) return cudaErrorInvalidValue;  // gpart capacity
+  dim3 grid((unsigned)n_strips, (unsigned)S.max_units);
+  return launch_pdl(fhat_partial_kernel<T>, grid, dim3(kStreamThreads), 0, st, KT, ldk, Ni, S, I.partial,
+                    I.gpart, n_strips, (const int32_t*)I.done, I.keep_rows,
+                    S.col_label ? I.gtick : (uint32_t*)nullptr, I.ghat_cur);
+}
+cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
+                                const IterState& I, cudaStream_t st) {
+  return launch_fhat_t(KT, ldk, Ni, S, I, st);
+}
+cudaError_t launch_fhat_partial(const __half* KT, int64_t ldk, int Ni, const Supports& S,
+                                const IterState& I, cudaStream_t st) {
+  return launch_fhat_t(KT, ldk, Ni, S, I, st);
 }
 
 // ----------------------------------------------------------- L2 priorities
@@ -370,16 +440,18 @@ struct AssignShared {
 };
 
 // n_j, unit ranges and g_hat into shared memory (g_hat given for an assign
-// against a model, else computed by ghat_reduce for this iteration).
+// against a model, else formed by fhat_partial for this iteration; NaN for an
+// empty cluster).
 __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
                                                    const IterState& I) {
   const int C = S.C;
   const double* g = I.ghat_in ? I.ghat_in : I.ghat_cur;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
-    sh.nj[j] = S.n_j[j];
+    const int n = S.n_j[j];
+    sh.nj[j] = n;
     sh.su[j] = S.seg_unit[j];
-    sh.gh[j] = g[j];
-    sh.ghf[j] = (float)g[j];
+    sh.gh[j] = n > 0 ? g[j] : __longlong_as_double(0x7ff8000000000000LL);
+    sh.ghf[j] = (float)sh.gh[j];
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
   __syncthreads();

@@ -710,8 +710,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
               kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, I, st) : launch_fhat_partial(KT, ldk, Ni, S, I, st));
       KKM_RUN("assign", st,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
-                            /*trace=*/1, st, R));
-      KKM_RUN("build_supports", st, launch_build_supports(S, I.done, I.lm_changed, st));
+                            /*trace=*/2, st, R));
+      // build_supports closes the iteration (trace, early stop) and re-sorts
+      KKM_RUN("build_supports", st,
+              launch_build_supports(S, I.done, I.lm_changed, st,
+                                    close_args(I, (int)ceil_div(Ni, 32), opt.early_stop)));
     }
     I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids

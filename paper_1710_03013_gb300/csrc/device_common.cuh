@@ -24,6 +24,33 @@ __device__ __forceinline__ int warp_sum_i32(int v) {
   return v;
 }
 
+// Double-float values (x = hi, y = lo): sums with about 44 significant bits
+// from FP32 operations only.  FP64 runs at 1/64 of the FP32 rate on this GPU,
+// so reductions that need more than FP32 use these (Knuth's TwoSum with a
+// renormalising Fast2Sum; squares split exactly with an FMA).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float v = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+// acc + v^2 (the product split exactly into p + e).
+__device__ __forceinline__ float2 df_add_sq(float2 acc, float v) {
+  const float p = __fmul_rn(v, v);
+  const float e = __fmaf_rn(v, v, -p);
+  return df_add(acc, make_float2(p, e));
+}
+__device__ __forceinline__ float2 warp_sum_df(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, make_float2(__shfl_xor_sync(kFull, v.x, o), __shfl_xor_sync(kFull, v.y, o)));
+  return v;
+}
+// The double-float value rounded to FP32.
+__device__ __forceinline__ float df_to_float(float2 v) { return __fadd_rn(v.x, v.y); }
+
 // Block-wide sum in a fixed order (warp trees, then warp 0 over the warp
 // results).  `sh` needs blockDim.x/32 slots.  Result valid in thread 0.
 template <typename T>

@@ -5,8 +5,8 @@
 // The contraction A.B^T runs as an FP32 FFMA register-tiled product (128x128
 // CTA tile, 8x8 outputs per thread, double-buffered shared memory) and the
 // epilogue forms ||a||^2 + ||b||^2 - 2 a.b, clamps it at 0 and applies the
-// exponential.  Squared norms are accumulated in FP64 once per row by the
-// gather kernels.  A "skinny" kernel covers <= 32 reference rows (medoid
+// exponential.  Squared norms are accumulated in double-float (FP32 pairs)
+// once per row by the gather kernels.  A "skinny" kernel covers <= 32 reference rows (medoid
 // columns, k-means++ columns) with one warp per sample row.
 #include <algorithm>
 
@@ -24,14 +24,14 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int64_t d, int64
   if (row >= n) return;
   const float* src = X + (start + row * step) * d;
   float* dst = out + row * (int64_t)dp;
-  double acc = 0.0;
+  float2 acc = make_float2(0.0f, 0.0f);
   for (int c = lane; c < dp; c += 32) {
     float v = c < d ? src[c] : 0.0f;
     dst[c] = v;
-    acc += (double)v * (double)v;
+    acc = df_add_sq(acc, v);
   }
-  acc = warp_sum_f64(acc);
-  if (normsq && lane == 0) normsq[row] = (float)acc;
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
 // Same with 16-byte vectors (d a multiple of 4 and X 16-byte aligned).
@@ -43,14 +43,14 @@ __global__ void gather_rows4_kernel(const float4* __restrict__ X, int64_t d4, in
   if (row >= n) return;
   const float4* src = X + (start + row * step) * d4;
   float4* dst = out + row * (int64_t)dp4;
-  double acc = 0.0;
+  float2 acc = make_float2(0.0f, 0.0f);
   for (int c = lane; c < dp4; c += 32) {
     const float4 v = c < d4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
     dst[c] = v;
-    acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    acc = df_add_sq(df_add_sq(df_add_sq(df_add_sq(acc, v.x), v.y), v.z), v.w);
   }
-  acc = warp_sum_f64(acc);
-  if (normsq && lane == 0) normsq[row] = (float)acc;
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
 template <typename IDX>
@@ -63,14 +63,14 @@ __global__ void gather_idx_kernel(const float* __restrict__ X, int64_t ld_in, in
   const int64_t g = (int64_t)idx[row];
   const float* src = X + g * ld_in;
   float* dst = out + row * (int64_t)dp;
-  double acc = 0.0;
+  float2 acc = make_float2(0.0f, 0.0f);
   for (int c = lane; c < dp; c += 32) {
     float v = c < d ? src[c] : 0.0f;
     dst[c] = v;
-    acc += (double)v * (double)v;
+    acc = df_add_sq(acc, v);
   }
-  acc = warp_sum_f64(acc);
-  if (normsq && lane == 0) normsq[row] = (float)acc;
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
 cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step, int64_t n,

@@ -416,7 +416,7 @@ cudaError_t launch_set_diag(void* out, bool out_half, int64_t ldo, const int32_t
 
 // ------------------------------------------------ FP32 rows -> BF16 rows
 // dst[r][c] = bf16(src[r][c]) for c < dp, and the squared norm of the rounded
-// row (FP64 accumulation) in normsq.
+// row (double-float accumulation, rounded to FP32) in normsq.
 __global__ void to_bf16_kernel(const float* __restrict__ src, int64_t n, int dp, __nv_bfloat16* __restrict__ dst,
                                float* __restrict__ normsq) {
   const int lane = threadIdx.x & 31;
@@ -424,15 +424,14 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, int64_t n, int dp,
   if (row >= n) return;
   const float* s = src + row * dp;
   __nv_bfloat16* d = dst + row * dp;
-  double acc = 0.0;
+  float2 acc = make_float2(0.0f, 0.0f);
   for (int c = lane; c < dp; c += 32) {
     const __nv_bfloat16 b = __float2bfloat16_rn(s[c]);
     d[c] = b;
-    const double v = (double)__bfloat162float(b);
-    acc += v * v;
+    acc = df_add_sq(acc, __bfloat162float(b));
   }
-  acc = warp_sum_f64(acc);
-  if (normsq && lane == 0) normsq[row] = (float)acc;
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
 cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq, cudaStream_t st) {

@@ -170,7 +170,7 @@ inline int max_units_for(int nL, int C) { return (int)(ceil_div(nL, kUnitRows) +
 struct IterState {
   float* partial;        // [max_units][ldk]
   float2* gpart;         // [max_units][n_strips] g_hat numerators, double-float (hi, lo)
-  double* omega_part;    // [assign grid]
+  float2* omega_part;    // [assign grid] cost per CTA, double-float (hi, lo)
   int32_t* changed_part; // [assign grid]
   uint32_t* ticket;      // [1], zero between launches
   int32_t* done;         // [1] early-stop flag (device)
@@ -199,8 +199,24 @@ cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream
 cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st);
 // Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA);
 // skipped when *skip != 0 or when *lm_changed == 0 (then nothing changed).
+// The iteration's closing, done by build_supports when the assign ran with
+// trace == 2: Omega and the counts from the per-CTA partials of assign (fixed
+// order), the trace entry, the early-stop flag and the landmark-change count.
+struct CloseArgs {
+  int n_parts = 0;  // 0: nothing to close
+  int early_stop = 0;
+  const float2* omega_part = nullptr;
+  const int32_t* changed_part = nullptr;
+  const int32_t* lm_part = nullptr;
+  double* trace_omega = nullptr;
+  int32_t* trace_changed = nullptr;
+  int32_t* trace_count = nullptr;
+  int32_t* done = nullptr;
+  int32_t* lm_changed = nullptr;
+};
+CloseArgs close_args(const IterState& I, int n_parts, int early_stop);
 cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const CloseArgs& close = CloseArgs());
 // col_ord[L[k]] = k (col_ord pre-filled with -1) and lab[k] = u[L[k]].
 cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st);
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
@@ -222,8 +238,9 @@ struct RescoreArgs {
 };
 
 // f_hat, distances, argmin, margin, Omega; updates u in place.  With
-// trace != 0 the last CTA also writes the trace entry, the early-stop flag and
-// the count of changed landmark labels.  Uses ceil(Ni/32) CTAs
+// trace == 1 the last CTA also writes the trace entry, the early-stop flag and
+// the count of changed landmark labels; with trace == 2 it leaves that to the
+// build_supports launch that follows (CloseArgs).  Uses ceil(Ni/32) CTAs
 // (omega_part/changed_part/lm_part need that many slots).
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,

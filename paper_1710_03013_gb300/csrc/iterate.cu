@@ -94,18 +94,64 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
 // stable counting sort of the landmark ordinals by label (n_j, segment and
 // unit tables, perm) and the label of every landmark column.  One CTA of
 // kSortThreads threads; returns at once when the early-stop flag is set.
+//
+// With cl.n_parts > 0 it first closes the iteration of the assign launch
+// before it: Omega (double-float partials, thread-strided then a fixed tree),
+// #changed and the landmark-change count; the trace entry; the early-stop
+// flag.  The whole CTA does it in parallel, off the assign's critical path.
 __global__ void __launch_bounds__(kSortThreads)
 build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
-                      const int32_t* __restrict__ lm_changed) {
+                      const int32_t* __restrict__ lm_changed, CloseArgs cl) {
   __shared__ int cnt[kMaxC];
   __shared__ int base[kMaxC];
   __shared__ int wtab[32 * kMaxC];
   __shared__ int scan_sh[32];
+  __shared__ float2 dred[32];
+  __shared__ int lm_sh;
   griddep_wait();
   griddep_launch();
   if (skip && *skip) return;
-  if (lm_changed && *lm_changed == 0) return;  // same landmark labels: same supports
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (cl.n_parts > 0) {
+    float2 o = make_float2(0.0f, 0.0f);
+    int c = 0, lm = 0;
+    for (int b = tid; b < cl.n_parts; b += kSortThreads) {
+      o = df_add(o, cl.omega_part[b]);
+      c += cl.changed_part[b];
+      lm += cl.lm_part ? cl.lm_part[b] : 0;
+    }
+    o = warp_sum_df(o);
+    c = warp_sum_i32(c);
+    lm = warp_sum_i32(lm);
+    if (lane == 0) {
+      dred[w] = o;
+      wtab[w] = c;
+      wtab[32 + w] = lm;
+    }
+    __syncthreads();
+    if (w == 0) {
+      const int nw = kSortThreads / 32;
+      o = lane < nw ? dred[lane] : make_float2(0.0f, 0.0f);
+      c = lane < nw ? wtab[lane] : 0;
+      lm = lane < nw ? wtab[32 + lane] : 0;
+      o = warp_sum_df(o);
+      c = warp_sum_i32(c);
+      lm = warp_sum_i32(lm);
+      if (lane == 0) {
+        const int t = *cl.trace_count;
+        cl.trace_omega[t] = (double)o.x + (double)o.y;
+        cl.trace_changed[t] = c;
+        *cl.trace_count = t + 1;
+        if (cl.early_stop && c == 0) *cl.done = 1;
+        if (cl.lm_changed) *cl.lm_changed = lm;
+        lm_sh = lm;
+      }
+    }
+    __syncthreads();
+    if (lm_sh == 0) return;  // same landmark labels: same supports
+  } else if (lm_changed && *lm_changed == 0) {
+    return;
+  }
   const int C = S.C, nL = S.nL;
   for (int j = tid; j < C; j += kSortThreads) cnt[j] = 0;
   __syncthreads();
@@ -189,9 +235,24 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
   }
 }
 
+CloseArgs close_args(const IterState& I, int n_parts, int early_stop) {
+  CloseArgs c;
+  c.n_parts = n_parts;
+  c.early_stop = early_stop;
+  c.omega_part = I.omega_part;
+  c.changed_part = I.changed_part;
+  c.lm_part = I.lm_part;
+  c.trace_omega = I.trace_omega;
+  c.trace_changed = I.trace_changed;
+  c.trace_count = I.trace_count;
+  c.done = I.done;
+  c.lm_changed = I.lm_changed;
+  return c;
+}
+
 cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
-                                  cudaStream_t st) {
-  return launch_pdl(build_supports_kernel, dim3(1), dim3(kSortThreads), 0, st, S, skip, lm_changed);
+                                  cudaStream_t st, const CloseArgs& close) {
+  return launch_pdl(build_supports_kernel, dim3(1), dim3(kSortThreads), 0, st, S, skip, lm_changed, close);
 }
 
 __global__ void landmark_maps_kernel(Supports S, const int32_t* __restrict__ u) {
@@ -229,18 +290,6 @@ __device__ __forceinline__ void ld16_policy(const __half* p, uint64_t pol, uint4
   asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
                : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w)
                : "l"(p), "l"(pol));
-}
-
-// Double-float (hi + lo, two FP32 numbers) addition: Knuth's TwoSum and a
-// renormalising Fast2Sum, about 44 significant bits from FP32 additions only
-// (FP64 runs at 1/64 of the FP32 rate on this GPU).
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float v = __fsub_rn(s, a.x);
-  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v));
-  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-  const float hi = __fadd_rn(s, e);
-  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
 // f_hat numerators: partial[u][l] = sum over the landmark rows k of unit u of
@@ -457,6 +506,18 @@ __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Suppo
   __syncthreads();
 }
 
+// g_hat into shared memory after n_j (given, or formed by fhat_partial for
+// this iteration; NaN for an empty cluster).
+__device__ __forceinline__ void load_cluster_ghat(AssignShared& sh, int C, const IterState& I) {
+  __syncthreads();  // n_j written
+  const double* g = I.ghat_in ? I.ghat_in : I.ghat_cur;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    sh.gh[j] = sh.nj[j] > 0 ? g[j] : __longlong_as_double(0x7ff8000000000000LL);
+    sh.ghf[j] = (float)sh.gh[j];
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ float partial_at(const float* __restrict__ partial, int64_t ldk, int un, int i) {
   return partial[(int64_t)un * ldk + i];
 }
@@ -509,17 +570,28 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   __shared__ float wsum[32];
   __shared__ unsigned flag_mask;
   __shared__ int is_last;
-  griddep_wait();
-  griddep_launch();
+  // Everything but the partials and g_hat was written by launches that have
+  // finished when this one starts (the support tables, the old labels, the
+  // column ordinals, the self terms): load it before waiting for the f_hat
+  // stream.
   if (I.done && *I.done) return;
   const int C = S.C;
-  load_cluster_stats(sh, S, I);
-  if (blockIdx.x == 0 && ghat_out)
-    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i = blockIdx.x * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
   const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
+  const int old_u = (w == 0 && i < Ni) ? u[i] : 0;
+  const int cord = (w == 0 && S.col_ord && i < Ni) ? S.col_ord[i] : -1;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    sh.nj[j] = S.n_j[j];
+    sh.su[j] = S.seg_unit[j];
+  }
+  if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
+  griddep_wait();
+  griddep_launch();
+  load_cluster_ghat(sh, C, I);
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   // d_ij of cluster j from the unit sum f (the units of j added in order)
   auto finish = [&](int j, float f) {
     float dj = inf;
@@ -643,26 +715,22 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     __syncthreads();
   }
   if (w != 0) return;
-  double om = 0.0;
+  float2 om = make_float2(0.0f, 0.0f);
   int ch = 0, lmc = 0;
   if (i < Ni) {
     const int bj = rlab[lane];
     const float best = rbest[lane];
-    const int old = u[i];
     u[i] = bj;
-    ch = (old != bj);
-    if (S.col_ord) {
-      const int k = S.col_ord[i];
-      if (k >= 0) {
-        S.lab[k] = bj;
-        lmc = ch;
-      }
+    ch = (old_u != bj);
+    if (cord >= 0) {
+      S.lab[cord] = bj;
+      lmc = ch;
     }
     if (margin) margin[i] = rsecond[lane] - best;
     if (dmin) dmin[i] = best;
-    om = (double)best;
+    om.x = best;
   }
-  om = warp_sum_f64(om);
+  om = warp_sum_df(om);
   ch = warp_sum_i32(ch);
   lmc = warp_sum_i32(lmc);
   if (lane == 0) {
@@ -670,7 +738,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     I.changed_part[blockIdx.x] = ch;
     if (I.lm_part) I.lm_part[blockIdx.x] = lmc;
   }
-  if (!trace) return;
+  if (trace != 1) return;
   // The last CTA to finish (atomic ticket, no waiting) closes the iteration:
   // Omega and the counts in a fixed order, the trace entry, the early-stop
   // flag and the landmark-change count read by build_supports.
@@ -680,32 +748,32 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   __syncwarp();
   if (!is_last) return;
   __threadfence();
-  double o = 0.0;
+  float2 o = make_float2(0.0f, 0.0f);
   int c = 0, lm = 0;
   const int G = (int)gridDim.x;
   for (int b0 = lane; b0 < G; b0 += 32 * 8) {
-    double ov[8];
+    float2 ov[8];
     int cv[8], lv[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int b = b0 + 32 * q;
-      ov[q] = b < G ? __ldcg(I.omega_part + b) : 0.0;
+      ov[q] = b < G ? __ldcg(I.omega_part + b) : make_float2(0.0f, 0.0f);
       cv[q] = b < G ? __ldcg(I.changed_part + b) : 0;
       lv[q] = (b < G && I.lm_part) ? __ldcg(I.lm_part + b) : 0;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      o += ov[q];
+      o = df_add(o, ov[q]);
       c += cv[q];
       lm += lv[q];
     }
   }
-  o = warp_sum_f64(o);
+  o = warp_sum_df(o);
   c = warp_sum_i32(c);
   lm = warp_sum_i32(lm);
   if (lane == 0) {
     const int t = *I.trace_count;
-    I.trace_omega[t] = o;
+    I.trace_omega[t] = (double)o.x + (double)o.y;
     I.trace_changed[t] = c;
     *I.trace_count = t + 1;
     if (early_stop && c == 0) *I.done = 1;

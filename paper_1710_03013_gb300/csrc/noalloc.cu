@@ -40,8 +40,8 @@ constexpr size_t kOffRows = 0;                                               // 
 constexpr size_t kOffAux = na_align(kOffRows + sizeof(float) * kNaRows * kNaRowLen);  // float [rows]
 constexpr size_t kOffK = na_align(kOffAux + sizeof(float) * kNaRows);         // float [ref][rows]
 constexpr size_t kOffPart = na_align(kOffK + sizeof(float) * kNaRef * kNaRows);  // float [units][rows]
-constexpr size_t kOffOmega = na_align(kOffPart + sizeof(float) * kNaUnits * kNaRows);  // double [grid]
-constexpr size_t kOffChanged = na_align(kOffOmega + sizeof(double) * kNaGrid);   // int [grid]
+constexpr size_t kOffOmega = na_align(kOffPart + sizeof(float) * kNaUnits * kNaRows);  // float2 [grid]
+constexpr size_t kOffChanged = na_align(kOffOmega + sizeof(float2) * kNaGrid);   // int [grid]
 constexpr size_t kOffFlag = na_align(kOffChanged + sizeof(int32_t) * kNaGrid);   // int [1]
 constexpr size_t kNaBytes = na_align(kOffFlag + sizeof(int32_t));
 
@@ -103,7 +103,7 @@ static kkm_status assign_noalloc_impl(const kkm_model* m, const float* X, int64_
   float* auxc = reinterpret_cast<float*>(base + kOffAux);
   float* Kb = reinterpret_cast<float*>(base + kOffK);
   float* partial = reinterpret_cast<float*>(base + kOffPart);
-  double* omega_part = reinterpret_cast<double*>(base + kOffOmega);
+  float2* omega_part = reinterpret_cast<float2*>(base + kOffOmega);
   int32_t* changed_part = reinterpret_cast<int32_t*>(base + kOffChanged);
   int* flag = reinterpret_cast<int*>(base + kOffFlag);
 

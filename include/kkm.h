@@ -333,13 +333,17 @@ const char* kkm_last_error(void);
 /* Per-kernel device timing.  kkm_prof_enable(1): every library kernel launch
  * is counted and bracketed by CUDA events on its stream; (2): every launch is
  * counted, only the kernel-block and streaming kernels ("gram_block",
- * "rmsd_block", "fhat_partial") are bracketed; (0): off.  kkm_prof_read
- * returns the number of launches and the summed device milliseconds of the
- * named kernel since the last reset (0 launches if unknown).  kkm_prof_names
- * writes a comma-separated list of the names seen into buf. */
+ * "rmsd_block", "rmsd_exact", "fhat_partial") are bracketed; (0): off.
+ * kkm_prof_read returns the number of launches and the summed device
+ * milliseconds of the named kernel since the last reset (0 launches if
+ * unknown).  kkm_prof_work returns the work units a data-dependent kernel
+ * reported while profiling was on ("rmsd_exact": frame pairs recomputed; the
+ * count costs a device read-back per launch).  kkm_prof_names writes a
+ * comma-separated list of the names seen into buf. */
 void kkm_prof_enable(int32_t on);
 void kkm_prof_reset(void);
 int32_t kkm_prof_read(const char* name, int64_t* launches, double* ms);
+double kkm_prof_work(const char* name);
 int32_t kkm_prof_names(char* buf, int32_t cap);
 
 #ifdef __cplusplus

@@ -47,6 +47,7 @@ static kkm_status invalid(const std::string& msg) {
 struct ProfEntry {
   int64_t launches = 0;
   double ms = 0.0;
+  double work = 0.0;  // data-dependent work units reported by the kernel's host code
 };
 struct Pending {
   const char* name;
@@ -56,7 +57,8 @@ static std::mutex g_prof_mu;
 static int g_prof_on = 0;  // 0 off, 1 time every launch, 2 count all, time the heavy kernels
 
 static bool heavy_kernel(const char* name) {
-  return !strcmp(name, "gram_block") || !strcmp(name, "rmsd_block") || !strcmp(name, "fhat_partial");
+  return !strcmp(name, "gram_block") || !strcmp(name, "rmsd_block") || !strcmp(name, "rmsd_exact") ||
+         !strcmp(name, "fhat_partial");
 }
 static std::unordered_map<std::string, ProfEntry> g_prof;
 static std::vector<Pending> g_pending;
@@ -106,6 +108,12 @@ void prof_collect() {
     g_event_pool.push_back(p.b);
   }
   g_pending.clear();
+}
+
+bool prof_on() { return g_prof_on != 0; }
+void prof_add_work(const char* name, double units) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof[name].work += units;
 }
 
 #define KKM_RUN(name, st, call)                 \
@@ -291,11 +299,61 @@ static kkm_status copy_prepared(const KernelSpec& sp, const float* Xp, const int
   return KKM_OK;
 }
 // out[a*ldo + b] = K(A_a, B_b).  dist != 0 gives distances instead.
+// Scratch of the MD kernel's tensor-core path (sized for the largest call):
+// BF16 planes of both sides, their squared radii, the refine flags and the
+// tensor-core error word.
+struct RmsdTcScratch {
+  __nv_bfloat16* P = nullptr;
+  __nv_bfloat16* Q = nullptr;
+  float* gP = nullptr;
+  float* gQ = nullptr;
+  int* flags = nullptr;
+  int* key = nullptr;    // [nP_cap] reference sort keys
+  int* order = nullptr;  // [nP_cap] reference order of the exact pass
+  int* err = nullptr;
+  int64_t nP_cap = 0, nQ_cap = 0;
+  int kp = 0;
+};
+
+// Reference sets at least this large take the tensor-core MD path, for
+// bandwidths at least this wide (the screen's rounding margin).
+constexpr int64_t kRmsdTcMinRefs = 32;
+constexpr float kRmsdTcMinSigma = 0.5f;
+
+static kkm_status alloc_rmsd_tc(Workspace& ws, const KernelSpec& sp, int64_t nP_cap, int64_t nQ_cap,
+                                RmsdTcScratch* t) {
+  t->kp = (int)round_up(sp.n_atoms, 64);
+  t->nP_cap = nP_cap;
+  t->nQ_cap = nQ_cap;
+  KKM_TRY(ws.alloc(&t->P, nP_cap * 4 * t->kp));
+  KKM_TRY(ws.alloc(&t->Q, nQ_cap * 4 * t->kp));
+  KKM_TRY(ws.alloc(&t->gP, nP_cap));
+  KKM_TRY(ws.alloc(&t->gQ, nQ_cap));
+  KKM_TRY(ws.alloc(&t->flags, ceil_div(nP_cap, 32) * ceil_div(nQ_cap, 64)));
+  KKM_TRY(ws.alloc(&t->key, nP_cap));
+  KKM_TRY(ws.alloc(&t->order, nP_cap));
+  KKM_TRY(ws.alloc(&t->err, 1));
+  KKM_CK(cudaMemsetAsync(t->err, 0, 4, ws.st));
+  return KKM_OK;
+}
+
+// MD kernel block on the tensor cores: a BF16 screen of every pair, then the
+// exact FP32 two-pass kernel only on the 32 x 64 tiles holding a pair the
+// screen could not certify as far (the others keep 0; their true values are
+// below 1e-5), with the references reordered so that near pairs gather in
+// few tiles.
+static kkm_status rmsd_block_tc(const KernelSpec& sp, const float* A, const float* auxA, const int64_t* idA,
+                                int64_t nA, const float* Bm, const float* auxB, const int64_t* idB, int64_t nB,
+                                float* out, int64_t ldo, const RmsdTcScratch& t, bool block, cudaStream_t st);
+
 static kkm_status kernel_block(const KernelSpec& sp, const float* A, const float* auxA,
                                const int64_t* idA, int64_t nA, const float* Bm, const float* auxB,
                                const int64_t* idB, int64_t nB, float* out, int64_t ldo,
-                               cudaStream_t st, bool dist = false, bool block = false) {
+                               cudaStream_t st, bool dist = false, bool block = false,
+                               const RmsdTcScratch* tc = nullptr) {
   if (sp.kind == KKM_RMSD) {
+    if (tc && !dist && nA >= kRmsdTcMinRefs && nA <= tc->nP_cap && nB <= tc->nQ_cap && sp.sigma >= kRmsdTcMinSigma)
+      return rmsd_block_tc(sp, A, auxA, idA, nA, Bm, auxB, idB, nB, out, ldo, *tc, block, st);
     KKM_RUN(block ? "rmsd_block" : "rmsd_gram", st,
             launch_rmsd_gram(dist ? DK_DIST : DK_RBF, A, nA, Bm, nB, sp.ap, sp.n_atoms, auxA, auxB, idA,
                              idB, sp.neg_scale(), out, ldo, st));
@@ -316,6 +374,30 @@ static int sm_count() {
     return v;
   }();
   return n;
+}
+
+static kkm_status rmsd_block_tc(const KernelSpec& sp, const float* A, const float* auxA, const int64_t* idA,
+                                int64_t nA, const float* Bm, const float* auxB, const int64_t* idB, int64_t nB,
+                                float* out, int64_t ldo, const RmsdTcScratch& t, bool block, cudaStream_t st) {
+  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(A, nA, sp.ap, sp.n_atoms, t.P, t.kp, t.gP, st));
+  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(Bm, nB, sp.ap, sp.n_atoms, t.Q, t.kp, t.gQ, st));
+  KKM_RUN(block ? "rmsd_block" : "rmsd_gram", st,
+          launch_rmsd_tc_estimate(t.P, nA, t.Q, nB, t.kp, t.gP, t.gQ, sp.n_atoms, sp.neg_scale(), out, ldo, t.err,
+                                  sm_count(), st));
+  KKM_RUN("rmsd_plan", st, launch_rmsd_refine_plan(out, ldo, (int)nA, (int)nB, t.key, t.order, t.flags, st));
+  KKM_RUN("rmsd_exact", st,
+          launch_rmsd_gram(DK_RBF, A, nA, Bm, nB, sp.ap, sp.n_atoms, auxA, auxB, idA, idB, sp.neg_scale(), out, ldo,
+                           st, t.flags, t.order));
+  if (prof_on()) {  // pairs the exact pass recomputed (profiling only: a read-back)
+    const int64_t nf = ceil_div(nA, 32) * ceil_div(nB, 64);
+    std::vector<int> f((size_t)nf);
+    KKM_CK(cudaMemcpyAsync(f.data(), t.flags, (size_t)nf * 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    int64_t tiles = 0;
+    for (int v : f) tiles += v != 0;
+    prof_add_work("rmsd_exact", (double)tiles * 32.0 * 64.0);
+  }
+  return KKM_OK;
 }
 
 // The kernel block on the tensor cores: P (reference rows) and Q (sample
@@ -626,6 +708,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(ws.alloc(&tc_err, 1));
     KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
   }
+  RmsdTcScratch rtc;
+  const bool use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
+  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, nLmax, Nmax, &rtc));
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
   Supports& S = lb.S;
@@ -664,7 +749,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, kt_half ? (void*)KTh : (void*)KT, kt_half, ldk, XLb, nXLb,
                                 Xib, nXib, tc_err, st));
     else
-      KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true));
+      KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true,
+                           use_rtc ? &rtc : nullptr));
     // L2 hygiene for the inner loop: the BF16 copies are not read again
     // (dropped), the FP32 rows only by the few boundary steps (evict first),
     // so the block rows kept with evict_last own the cache.
@@ -835,9 +921,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   }
   if (labels_on_host)
     KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
-  int tc_err_h = 0;
+  int tc_err_h = 0, rtc_err_h = 0;
   if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
+  if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h, rtc.err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
+  tc_err_h |= rtc_err_h;
   if (tc_err_h) {
     set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
     return KKM_ETIMEOUT;
@@ -909,6 +997,9 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
   KKM_TRY(ws.alloc(&auxc, ldm));
   KKM_TRY(ws.alloc(&Kb, (int64_t)rows_ref * ldm));
   const float* kself = sp.kind == KKM_LINEAR ? auxc : nullptr;
+  RmsdTcScratch rtc;
+  const bool use_rtc = sp.kind == KKM_RMSD && rows_ref >= kRmsdTcMinRefs;
+  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, rows_ref, ldm, &rtc));
   LoopBuffers lb;
   if (mode == KKM_ASSIGN_SUPPORTS) {
     KKM_TRY(alloc_loop(ws, m->nL, C, ldm, 1, &lb));
@@ -933,13 +1024,15 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
     const int n = (int)std::min<int64_t>(chunk, M - c0);
     KKM_TRY(prep_rows(sp, X, c0, 1, n, Xc, auxc, st));
     if (mode == KKM_ASSIGN_SUPPORTS) {
-      KKM_TRY(kernel_block(sp, m->sup, m->sup_aux, nullptr, m->nL, Xc, auxc, nullptr, n, Kb, ldm, st));
+      KKM_TRY(kernel_block(sp, m->sup, m->sup_aux, nullptr, m->nL, Xc, auxc, nullptr, n, Kb, ldm, st, false, false,
+                           use_rtc ? &rtc : nullptr));
       KKM_RUN("fhat_partial", st, launch_fhat_partial(Kb, ldm, n, lb.S, lb.I, st));
       KKM_RUN("assign", st,
               launch_assign(ldm, n, lb.S, lb.I, kself, lab + c0, nullptr, dist + c0, nullptr, nullptr, 0,
                             /*rebuild=*/0, st));
     } else {
-      KKM_TRY(kernel_block(sp, m->med, m->med_aux, nullptr, C, Xc, auxc, nullptr, n, Kb, ldm, st));
+      KKM_TRY(kernel_block(sp, m->med, m->med_aux, nullptr, C, Xc, auxc, nullptr, n, Kb, ldm, st, false, false,
+                           use_rtc ? &rtc : nullptr));
       KKM_RUN("nearest", st,
               launch_nearest(Kb, ldm, n, C, kself, sp.kind == KKM_LINEAR ? m->med_aux : nullptr, lab + c0,
                              dist + c0, st));
@@ -955,8 +1048,14 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
   }
   if (lab_host) KKM_CK(cudaMemcpyAsync(labels_out, lab, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
   if (dist_host) KKM_CK(cudaMemcpyAsync(dist_out, dist, (size_t)M * 4, cudaMemcpyDeviceToHost, st));
+  int rtc_err_h = 0;
+  if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h, rtc.err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
   prof_collect();
+  if (rtc_err_h) {
+    set_error("tensor-core MD estimate: a bounded pipeline wait gave up");
+    return KKM_ETIMEOUT;
+  }
   return KKM_OK;
 }
 
@@ -1003,6 +1102,12 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
     KKM_CK(cudaMemsetAsync(err, 0, 4, st));
     KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nB, o, false, nB, Ab, nAb, Bb, nBb, err, st));
     KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
+  } else if (sp.kind == KKM_RMSD && nA >= kRmsdTcMinRefs) {
+    // the MD kernel takes the same tensor-core estimate + exact-refine path as a fit
+    RmsdTcScratch rtc;
+    KKM_TRY(alloc_rmsd_tc(ws, sp, nA, nB, &rtc));
+    KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st, false, false, &rtc));
+    KKM_CK(cudaMemcpyAsync(&tc_err_h, rtc.err, 4, cudaMemcpyDeviceToHost, st));
   } else {
     KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st));
   }
@@ -1339,6 +1444,11 @@ int32_t kkm_prof_read(const char* name, int64_t* launches, double* ms) {
   if (launches) *launches = it->second.launches;
   if (ms) *ms = it->second.ms;
   return 1;
+}
+double kkm_prof_work(const char* name) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  auto it = g_prof.find(name ? name : "");
+  return it == g_prof.end() ? 0.0 : it->second.work;
 }
 int32_t kkm_prof_names(char* buf, int32_t cap) {
   std::lock_guard<std::mutex> lk(g_prof_mu);

@@ -34,6 +34,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "qcp.cuh"
 
 namespace kkm {
 
@@ -48,6 +49,11 @@ constexpr int TC_THREADS = 320;   // 2 + 8 warps
 constexpr int TC_TMEM_COLS = 512;
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 24;  // bounded mbarrier waits
 constexpr size_t TC_SMEM = (size_t)TC_STAGES * TC_STAGE_BYTES + 2048;
+// The MD estimate's epilogue also stages each warp's accumulator chunk in
+// shared memory, 32 lanes x 16 columns at a time (8 warps x 2 KB), to regroup
+// the 3 x 3 blocks (static + dynamic shared memory stays within 227 KB).
+constexpr int TC_RMSD_WARP_FLOATS = 512;
+constexpr size_t TC_SMEM_RMSD = TC_SMEM + 8 * TC_RMSD_WARP_FLOATS * sizeof(float);
 
 // ------------------------------------------------------------ PTX helpers
 // (smem_u32, mbarrier init / expect_tx / arrive / try_wait: device_common.cuh)
@@ -137,11 +143,22 @@ __device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_out(__half* p, float v) { *p = __float2half_rn(v); }
 
 // OutT: float, or __half for a Gaussian kernel block (values in [0, 1]).
+//
+// KIND == DK_RMSD_EST (the MD kernel's estimate): P and Q rows are the x, y,
+// z and zero planes of frames (row 4f + c), so the accumulator holds, for
+// sample frame s (rows 4s..4s+3) and reference frame l (columns 4l..4l+3),
+// the 3 x 3 correlation of the pair in its top-left corner.  Each epilogue
+// warp stages a 32 x 32 chunk (8 samples x 8 references) in shared memory,
+// then every lane takes one pair and writes out[l * ldo + s] = 0 if the
+// BF16-product correlation and the rounded frames' squared radii (normQ /
+// normP per frame) certify rmsd^2 beyond the refine threshold (a sign test of
+// the QCP characteristic polynomial and its derivatives, no root iteration),
+// else 1 (the pair is recomputed exactly).
 template <int KIND, typename OutT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
                int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
-               float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err) {
+               float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err, float inv_n) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // stages must start on a 1024-byte boundary (swizzle atom)
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -254,9 +271,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       const int buf = lt & 1;
       const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
       const int n0 = tn * TC_N + half * (TC_N / 2);   // first reference row of this warp
-      for (int c = lane; c < TC_N / 2; c += 32) {
-        const int n = n0 + c;
-        sh.nP[ew][c] = n < nP ? normP[n] : 0.0f;
+      if constexpr (KIND != DK_RMSD_EST) {  // (the MD estimate reads its radii per frame)
+        for (int c = lane; c < TC_N / 2; c += 32) {
+          const int n = n0 + c;
+          sh.nP[ew][c] = n < nP ? normP[n] : 0.0f;
+        }
       }
       __syncwarp();
       bool ok = true;
@@ -270,6 +289,49 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
         break;
       }
       tc_fence_after();
+      if constexpr (KIND == DK_RMSD_EST) {
+        float* sb = reinterpret_cast<float*>(stages + (size_t)TC_STAGES * TC_STAGE_BYTES) + ew * TC_RMSD_WARP_FLOATS;
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + half * (TC_N / 2));
+        const int nSf = nQ >> 2, nLf = nP >> 2;
+        // n rmsd^2 at which the kernel value falls to kRmsdRefine
+        const float n_r2_far = (log2f(kRmsdRefine) / neg_scale) / inv_n;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N / 2; c0 += 32) {
+          uint32_t r[32];
+          tmem_ld32(tb + (uint32_t)c0, r);
+          // lane = (sample lane / 4, sample coordinate lane % 4); column 4 l + j
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float4* row = reinterpret_cast<float4*>(sb + lane * 16);
+#pragma unroll
+            for (int l4 = 0; l4 < 4; ++l4)
+              row[l4] = make_float4(__uint_as_float(r[hh * 16 + 4 * l4]), __uint_as_float(r[hh * 16 + 4 * l4 + 1]),
+                                    __uint_as_float(r[hh * 16 + 4 * l4 + 2]),
+                                    __uint_as_float(r[hh * 16 + 4 * l4 + 3]));
+            __syncwarp();
+            // one pair per lane: sample ps (of 8), reference pl (of 4)
+            const int ps = lane >> 2, pl = lane & 3;
+            const int sf = tm * (TC_M / 4) + q * 8 + ps;
+            const int lf = tn * (TC_N / 4) + half * (TC_N / 8) + (c0 >> 2) + hh * 4 + pl;
+            if (sf < nSf && lf < nLf) {
+              float H[9];  // H[c1][c2] = sum_a x_a[c1] y_a[c2], x the reference frame
+#pragma unroll
+              for (int c1 = 0; c1 < 3; ++c1)
+#pragma unroll
+                for (int c2 = 0; c2 < 3; ++c2) H[c1 * 3 + c2] = sb[(ps * 4 + c2) * 16 + pl * 4 + c1];
+              // 0 for a pair certainly beyond the refine threshold (its true
+              // value is below 1e-5), else 1: the exact pass recomputes it
+              const bool far = qcp_certainly_far(H, normP[lf], normQ[sf], n_r2_far);
+              store_out(out + (int64_t)lf * ldo + sf, far ? 0.0f : 1.0f);
+            }
+            __syncwarp();
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.tempty[buf]);
+        continue;
+      }
       const int m = tm * TC_M + q * 32 + lane;
       const bool mvalid = m < nQ;
       const float nq = mvalid ? normQ[m] : 0.0f;
@@ -369,7 +431,7 @@ static cudaError_t launch_gram_tc_t(int kind, const CUtensorMap& mq, const CUten
   e = cudaFuncSetAttribute(gram_tc_kernel<K, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
   if (e != cudaSuccess) return e;                                                                         \
   gram_tc_kernel<K, OutT><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, nQ, nP, dk, normQ, normP, neg_scale, out, \
-                                                             ldo, err);
+                                                             ldo, err, 0.0f);
   if (kind == DK_DIST) {
     KKM_TC_LAUNCH(DK_DIST)
   } else if (kind == DK_LINEAR) {
@@ -397,6 +459,26 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
                             static_cast<__half*>(out), ldo, err, grid, st);
   return launch_gram_tc_t(kind, mq, mp, (int)nQ, (int)nP, dk, normP, normQ, neg_scale, static_cast<float*>(out),
                           ldo, err, grid, st);
+}
+
+cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ, int kp,
+                                    const float* gP, const float* gQ, int n_atoms, float neg_scale, float* out,
+                                    int64_t ldo, int* err, int n_sms, cudaStream_t st) {
+  if (nP <= 0 || nQ <= 0) return cudaSuccess;
+  if (kp % TC_K != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15) ||
+      n_atoms <= 0)
+    return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap mq, mp;
+  if (!make_map(&mq, Q, 4 * nQ, kp, kp, TC_M) || !make_map(&mp, P, 4 * nP, kp, kp, TC_N))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ceil_div(4 * nQ, TC_M) * ceil_div(4 * nP, TC_N);
+  const int grid = (int)std::min<int64_t>(tiles, std::max(n_sms, 1));
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<DK_RMSD_EST, float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_RMSD);
+  if (e != cudaSuccess) return e;
+  gram_tc_kernel<DK_RMSD_EST, float><<<grid, TC_THREADS, TC_SMEM_RMSD, st>>>(
+      mq, mp, (int)(4 * nQ), (int)(4 * nP), kp, gQ, gP, neg_scale, out, ldo, err, 1.0f / (float)n_atoms);
+  return cudaGetLastError();
 }
 
 // K = 1 on the diagonal of the block: out[k][L[k]] for landmark ordinals k.

@@ -26,8 +26,12 @@
 // and since the residual is stationary at the optimal rotation, the rotation's
 // own FP32 error enters only at second order.  No FP64 is needed.  Pass 2
 // runs only in warps holding a pair with a non-negligible kernel value.
+#include <cuda_bf16.h>
+#include <limits.h>
+
 #include "device_common.cuh"
 #include "internal.h"
+#include "qcp.cuh"
 
 namespace kkm {
 
@@ -82,34 +86,111 @@ cudaError_t launch_rmsd_prep_idx64(const float* X, int n_atoms, const int64_t* i
   return cudaGetLastError();
 }
 
+// SoA FP32 frames -> BF16 planes for the tensor-core estimate: one warp per
+// frame; the squared radius of the rounded frame in double-float.
+__global__ void rmsd_to_bf16_kernel(const float* __restrict__ src, int64_t n, int ap, int n_atoms,
+                                    __nv_bfloat16* __restrict__ dst, int kp, float* __restrict__ gsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float* s = src + row * 3 * (int64_t)ap;
+  __nv_bfloat16* d = dst + row * 4 * (int64_t)kp;
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (int c = 0; c < 4; ++c)
+    for (int k = lane; k < kp; k += 32) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((c < 3 && k < n_atoms) ? s[c * ap + k] : 0.0f);
+      d[c * kp + k] = b;
+      acc = df_add_sq(acc, __bfloat162float(b));
+    }
+  acc = warp_sum_df(acc);
+  if (lane == 0) gsq[row] = df_to_float(acc);
+}
+
+cudaError_t launch_rmsd_to_bf16(const float* src, int64_t n, int ap, int n_atoms, __nv_bfloat16* dst, int kp,
+                                float* gsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  rmsd_to_bf16_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(src, n, ap, n_atoms, dst, kp, gsq);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- refine-tile ordering
+// After the tensor-core estimate, the exact kernel recomputes only tiles of
+// 32 reference frames x 64 samples holding a pair above kRmsdRefine.  Samples
+// are in trajectory order, so a sample tile is mostly one conformational
+// state; the references are reordered so that a reference tile is too: key
+// = the first sample whose estimate exceeds the threshold (references of one
+// state share it; references near nothing sort last), ties by index.
+__global__ void rmsd_near_key_kernel(const float* __restrict__ est, int64_t ldo, int nA, int nB,
+                                     int* __restrict__ key) {
+  const int lane = threadIdx.x & 31;
+  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (a >= nA) return;
+  const float* row = est + (int64_t)a * ldo;
+  int first = INT_MAX;
+  for (int b0 = 0; b0 < nB && first == INT_MAX; b0 += 32 * 8) {
+    int f = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = b0 + q * 32 + lane;
+      if (b < nB && row[b] > kRmsdRefine) f = min(f, b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f = min(f, __shfl_xor_sync(kFull, f, o));
+    first = f;
+  }
+  if (lane == 0) key[a] = first;
+}
+
+// order[rank(a)] = a, rank by (key, index); keys staged in shared memory
+// when they fit (else read from global memory, the same in every lane).
+template <bool SMEM>
+__global__ void rmsd_rank_kernel(const int* __restrict__ key, int nA, int* __restrict__ order) {
+  extern __shared__ int ks[];
+  if (SMEM) {
+    for (int i = threadIdx.x; i < nA; i += blockDim.x) ks[i] = key[i];
+    __syncthreads();
+  }
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nA) return;
+  const int* kk = SMEM ? ks : key;
+  const int ka = kk[a];
+  int rank = 0;
+  for (int i = 0; i < nA; ++i) {
+    const int ki = kk[i];
+    rank += (ki < ka) || (ki == ka && i < a);
+  }
+  order[rank] = a;
+}
+
+// flag[t][u] = 1 if reference tile t (of the order) and sample tile u hold a
+// pair above the threshold; one CTA per (sample tile, reference tile).
+__global__ void rmsd_tile_flag_kernel(const float* __restrict__ est, int64_t ldo, int nA, int nB,
+                                      const int* __restrict__ order, int* __restrict__ flag) {
+  const int u = blockIdx.x, t = blockIdx.y;
+  const int b = u * 64 + (threadIdx.x & 63);
+  int hit = 0;
+  for (int r = threadIdx.x >> 6; r < 32; r += blockDim.x >> 6) {
+    const int ar = t * 32 + r;
+    if (ar < nA && b < nB) hit |= est[(int64_t)order[ar] * ldo + b] > kRmsdRefine;
+  }
+  hit = __syncthreads_or(hit);
+  if (threadIdx.x == 0) flag[(int64_t)t * gridDim.x + u] = hit;
+}
+
+cudaError_t launch_rmsd_refine_plan(const float* est, int64_t ldo, int nA, int nB, int* key, int* order, int* flag,
+                                    cudaStream_t st) {
+  if (nA <= 0 || nB <= 0) return cudaSuccess;
+  rmsd_near_key_kernel<<<(unsigned)ceil_div(nA, 8), 256, 0, st>>>(est, ldo, nA, nB, key);
+  if ((size_t)nA * sizeof(int) <= 48 * 1024)
+    rmsd_rank_kernel<true><<<(unsigned)ceil_div(nA, 256), 256, (size_t)nA * sizeof(int), st>>>(key, nA, order);
+  else
+    rmsd_rank_kernel<false><<<(unsigned)ceil_div(nA, 256), 256, 0, st>>>(key, nA, order);
+  rmsd_tile_flag_kernel<<<dim3((unsigned)ceil_div(nB, 64), (unsigned)ceil_div(nA, 32)), 256, 0, st>>>(est, ldo, nA, nB,
+                                                                                                   order, flag);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------- QCP
-__device__ __forceinline__ float det3(float a, float b, float c, float d, float e, float f, float g,
-                                      float h, float i) {
-  return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
-}
-
-// Minor of the symmetric 4x4 matrix m with row r and column c removed.
-__device__ __forceinline__ float minor4(const float m[4][4], int r, int c) {
-  int rr[3], cc[3];
-  int k = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (q != r) rr[k++] = q;
-  k = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    if (q != c) cc[k++] = q;
-  return det3(m[rr[0]][cc[0]], m[rr[0]][cc[1]], m[rr[0]][cc[2]], m[rr[1]][cc[0]], m[rr[1]][cc[1]],
-              m[rr[1]][cc[2]], m[rr[2]][cc[0]], m[rr[2]][cc[1]], m[rr[2]][cc[2]]);
-}
-
-// Cofactor row r of m (the r-th column of its adjugate).
-template <int R>
-__device__ __forceinline__ void cofactor_row(const float m[4][4], float v[4]) {
-#pragma unroll
-  for (int c = 0; c < 4; ++c) v[c] = (((R + c) & 1) ? -1.f : 1.f) * minor4(m, R, c);
-}
-
 // H = sum_a x_a y_a^T (row-major 3x3) of centred frames x (reference) and y
 // (sample) with squared radii Gx, Gy.  Returns the estimate G_x + G_y -
 // 2 lambda_max (>= 0) and the rotation R (row-major) with R x ~ y.
@@ -119,45 +200,8 @@ __device__ __forceinline__ float qcp_rotation(const float H[9], float Gx, float 
   R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
   R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
   if (!(E0 > 0.f)) return 0.f;
-  const float inv = 1.0f / E0;
-  const float Sxx = H[0] * inv, Sxy = H[1] * inv, Sxz = H[2] * inv;
-  const float Syx = H[3] * inv, Syy = H[4] * inv, Syz = H[5] * inv;
-  const float Szx = H[6] * inv, Szy = H[7] * inv, Szz = H[8] * inv;
   float m[4][4];
-  m[0][0] = Sxx + Syy + Szz;
-  m[0][1] = Syz - Szy;
-  m[0][2] = Szx - Sxz;
-  m[0][3] = Sxy - Syx;
-  m[1][1] = Sxx - Syy - Szz;
-  m[1][2] = Sxy + Syx;
-  m[1][3] = Szx + Sxz;
-  m[2][2] = -Sxx + Syy - Szz;
-  m[2][3] = Syz + Szy;
-  m[3][3] = -Sxx - Syy + Szz;
-  m[1][0] = m[0][1]; m[2][0] = m[0][2]; m[3][0] = m[0][3];
-  m[2][1] = m[1][2]; m[3][1] = m[1][3]; m[3][2] = m[2][3];
-  const float c2 = -2.0f * (Sxx * Sxx + Sxy * Sxy + Sxz * Sxz + Syx * Syx + Syy * Syy + Syz * Syz +
-                            Szx * Szx + Szy * Szy + Szz * Szz);
-  const float c1 = -8.0f * det3(Sxx, Sxy, Sxz, Syx, Syy, Syz, Szx, Szy, Szz);
-  // det N by expansion in complementary 2x2 minors of rows (0,1) and (2,3)
-  const float s0 = m[0][0] * m[1][1] - m[1][0] * m[0][1], s1 = m[0][0] * m[1][2] - m[1][0] * m[0][2];
-  const float s2 = m[0][0] * m[1][3] - m[1][0] * m[0][3], s3 = m[0][1] * m[1][2] - m[1][1] * m[0][2];
-  const float s4 = m[0][1] * m[1][3] - m[1][1] * m[0][3], s5 = m[0][2] * m[1][3] - m[1][2] * m[0][3];
-  const float t5 = m[2][2] * m[3][3] - m[3][2] * m[2][3], t4 = m[2][1] * m[3][3] - m[3][1] * m[2][3];
-  const float t3 = m[2][1] * m[3][2] - m[3][1] * m[2][2], t2 = m[2][0] * m[3][3] - m[3][0] * m[2][3];
-  const float t1 = m[2][0] * m[3][2] - m[3][0] * m[2][2], t0 = m[2][0] * m[3][1] - m[3][0] * m[2][1];
-  const float c0 = s0 * t5 - s1 * t4 + s2 * t3 + s3 * t2 - s4 * t1 + s5 * t0;
-  // Newton from the upper bound 1 (= (Gx+Gy)/2 after scaling)
-  float lam = 1.0f;
-  for (int it = 0; it < 60; ++it) {
-    const float l2 = lam * lam;
-    const float P = ((l2 + c2) * lam + c1) * lam + c0;
-    const float dP = (4.0f * l2 + 2.0f * c2) * lam + c1;
-    if (!(dP != 0.0f)) break;
-    const float dl = P / dP;
-    lam -= dl;
-    if (fabsf(dl) <= 1e-7f * fabsf(lam)) break;
-  }
+  const float lam = qcp_lambda(H, E0, m);
   // eigenvector: the cofactor row of N - lambda I with the largest diagonal cofactor
   float a[4][4];
 #pragma unroll
@@ -221,7 +265,8 @@ struct RmsdPrefetch {
 // element e of a stage: frame f = e % rows, coordinate plane c, half h of the 8 atoms
 template <int TA>
 __device__ __forceinline__ void rmsd_fetch(const float* __restrict__ A, int nA, const float* __restrict__ Bm,
-                                           int nB, int ap, int a0, int b0, int k0, RmsdPrefetch<TA>& p) {
+                                           int nB, int ap, int a0, int b0, int k0, RmsdPrefetch<TA>& p,
+                                           const int* __restrict__ arow) {
   using Cf = RmsdCfg<TA>;
   const int tid = threadIdx.x;
 #pragma unroll
@@ -229,7 +274,8 @@ __device__ __forceinline__ void rmsd_fetch(const float* __restrict__ A, int nA, 
     const int e = tid + q * Cf::NT;
     if (e < Cf::A4) {
       const int f = e % TA, rest = e / TA, c = rest >> 1, h = rest & 1;
-      p.a[q] = __ldg(reinterpret_cast<const float4*>(A + (int64_t)min(a0 + f, nA - 1) * 3 * ap + c * ap + k0 + h * 4));
+      const int ar = min(a0 + f, nA - 1);
+      p.a[q] = __ldg(reinterpret_cast<const float4*>(A + (int64_t)(arow ? arow[ar] : ar) * 3 * ap + c * ap + k0 + h * 4));
     }
   }
 #pragma unroll
@@ -275,8 +321,10 @@ __global__ void __launch_bounds__(RmsdCfg<TA>::NT, (TA == 32) ? 2 : 4)
 rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB, int ap,
                  int n_atoms, const float* __restrict__ gA, const float* __restrict__ gB,
                  const int64_t* __restrict__ idA, const int64_t* __restrict__ idB, float neg_scale,
-                 float* __restrict__ out, int64_t ldo, int vec_ok) {
+                 float* __restrict__ out, int64_t ldo, int vec_ok, const int* __restrict__ tile_flag,
+                 const int* __restrict__ arow) {
   __shared__ __align__(16) RmsdTiles<TA> t;
+  if (tile_flag && !tile_flag[(int64_t)blockIdx.y * gridDim.x + blockIdx.x]) return;  // estimate stands
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int a0 = blockIdx.y * TA, b0 = blockIdx.x * RT_B;
   const int nk = ap / RT_K;
@@ -290,12 +338,12 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[r][q][e] = 0.f;
   RmsdPrefetch<TA> pf;
-  rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+  rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf, arow);
   rmsd_store<TA>(t, 0, pf);
   __syncthreads();
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
-    if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+    if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf, arow);
 #pragma unroll
     for (int k = 0; k < RT_K; ++k) {
       float2 av[3];
@@ -330,7 +378,7 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
   const float inv_n = 1.0f / (float)n_atoms;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int a = min(a0 + ty * 2 + r, nA - 1);
+    const int a = arow ? arow[min(a0 + ty * 2 + r, nA - 1)] : min(a0 + ty * 2 + r, nA - 1);
     const float ga = gA[a];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -354,12 +402,12 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
     for (int r = 0; r < 2; ++r)
 #pragma unroll
       for (int q = 0; q < 4; ++q) res[r][q] = 0.f;
-    rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf);
+    rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf, arow);
     rmsd_store<TA>(t, 0, pf);
     __syncthreads();
     for (int kt = 0; kt < nk; ++kt) {
       const int cur = kt & 1;
-      if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf);
+      if (kt + 1 < nk) rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, (kt + 1) * RT_K, pf, arow);
       if (warp_need) {
 #pragma unroll
         for (int k = 0; k < RT_K; ++k) {
@@ -400,8 +448,8 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
   // ---- epilogue
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    const int a = a0 + ty * 2 + r;
-    if (a >= nA) continue;
+    if (a0 + ty * 2 + r >= nA) continue;
+    const int a = arow ? arow[a0 + ty * 2 + r] : a0 + ty * 2 + r;
     const int64_t ia = idA ? idA[a] : -2;
     float v[4];
 #pragma unroll
@@ -414,6 +462,13 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
     }
     float* orow = out + (int64_t)a * ldo;
     const int b = b0 + tx * 4;
+    if (tile_flag) {
+      // after the tensor-core screen: a pair it certified far keeps its 0,
+      // so every pair's value depends on the pair alone, not on its tile
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (b + q < nB && orow[b + q] == 0.0f) v[q] = 0.0f;
+    }
     if (vec_ok && b + 3 < nB) {
       *reinterpret_cast<float4*>(orow + b) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
@@ -426,13 +481,15 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
 
 cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB, int ap,
                              int n_atoms, const float* gA, const float* gB, const int64_t* idA,
-                             const int64_t* idB, float neg_scale, float* out, int64_t ldo, cudaStream_t st) {
+                             const int64_t* idB, float neg_scale, float* out, int64_t ldo, cudaStream_t st,
+                             const int* tile_flag, const int* arow) {
   if (nA <= 0 || nB <= 0) return cudaSuccess;
+  if (tile_flag && nA <= 8) return cudaErrorInvalidValue;  // flags are laid out for 32-frame A tiles
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
 #define KKM_RMSD_LAUNCH(K, TA)                                                                       \
   rmsd_gram_kernel<K, TA><<<dim3((unsigned)ceil_div(nB, RT_B), (unsigned)ceil_div(nA, TA)),          \
                             RmsdCfg<TA>::NT, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, \
-                                                      idB, neg_scale, out, ldo, vec_ok)
+                                                      idB, neg_scale, out, ldo, vec_ok, tile_flag, arow)
   if (nA <= 8) {
     if (kind == DK_DIST) KKM_RMSD_LAUNCH(DK_DIST, 8); else KKM_RMSD_LAUNCH(DK_RBF, 8);
   } else {

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "kkm_prof_enable": (None, [_I32]),
     "kkm_prof_reset": (None, []),
     "kkm_prof_read": (_I32, [ctypes.c_char_p, ctypes.POINTER(_I64), ctypes.POINTER(_F64)]),
+    "kkm_prof_work": (_F64, [ctypes.c_char_p]),
     "kkm_prof_names": (_I32, [ctypes.c_char_p, _I32]),
 }
 
@@ -526,6 +527,11 @@ def prof_read(name):
     n, ms = _I64(), _F64()
     load().kkm_prof_read(name.encode(), ctypes.byref(n), ctypes.byref(ms))
     return n.value, ms.value
+
+
+def prof_work(name):
+    """Work units a data-dependent kernel reported while profiling was on."""
+    return load().kkm_prof_work(name.encode())
 
 
 def prof_names():

@@ -339,20 +339,21 @@ def run_ours(args, cfg, X):
     elif dom == "rmsd_exact":
         n, tms = prof[dom]
         pairs = kkm.prof_work("rmsd_exact") / n   # frame pairs the exact pass recomputed, per launch
-        flops = 18.0 * cfg["n_atoms"] * pairs
+        flops = 30.0 * cfg["n_atoms"] * pairs      # residual |R x - y|^2: 15 FMA per atom
         ach = flops / (tms / n / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / PEAK_FP32_TFLOPS, "traffic": ncu_traffic("rmsd_exact", cfg["key"]),
                 "kernel": "rmsd_exact (FP32 two-pass QCP on the tiles the tensor-core screen flagged)",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "work_per_launch": f"18*n_atoms flop per recomputed pair x {pairs:.4g} pairs = {flops:.4g} flop"}
+                "work_per_launch": f"30*n_atoms flop per recomputed pair (the residual at the screen's "
+                                   f"rotation) x {pairs:.4g} pairs = {flops:.4g} flop"}
         if "rmsd_block" in prof:
             n2, t2 = prof["rmsd_block"]
-            kp = -(-cfg["n_atoms"] // 64) * 64
+            kp = 3 * (-(-cfg["n_atoms"] // 64) * 64)   # split-BF16 operands: three segments
             fl2 = sum(2.0 * 4 * ((cfg["N"] - i + B - 1) // B) * 4 * n_landmarks((cfg["N"] - i + B - 1) // B, s) * kp
                       for i in range(B)) / B
             pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-            roof["screen"] = {"kernel": "rmsd_block (tcgen05 BF16 correlation screen)", "bound": "tensor",
+            roof["screen"] = {"kernel": "rmsd_block (tcgen05 split-BF16 correlation screen)", "bound": "tensor",
                               "achieved": fl2 / (t2 / n2 / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
                               "frac": fl2 / (t2 / n2 / 1e3) / 1e12 / pk,
                               "work_per_launch": f"2*(4 N_i)*(4 |L|)*{kp} = {fl2:.4g} flop"}
@@ -742,9 +743,9 @@ def run_serving(args, cfg):
     n_s, t_s = kkm.prof_read("rmsd_gram")
     n_e, t_e = kkm.prof_read("rmsd_exact")
     pairs = kkm.prof_work("rmsd_exact") / max(n_e, 1)
-    flops = 18.0 * na * pairs
+    flops = 30.0 * na * pairs   # residual |R x - y|^2 at the screen's rotation: 15 FMA per atom
     ach = flops / (t_e / max(n_e, 1) / 1e3) / 1e12 if n_e else 0.0
-    kp = -(-na // 64) * 64
+    kp = 3 * (-(-na // 64) * 64)   # split-BF16 operands: three segments
     fl_s = 2.0 * 4 * cfg["max_query"] * 4 * nS * kp
     pk = measured_peaks()[0]
     pk = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
@@ -752,8 +753,8 @@ def run_serving(args, cfg):
             "frac": ach / PEAK_FP32_TFLOPS, "traffic": None,
             "kernel": "rmsd_exact (assign of 10,000 frames against 10,000 supports: FP32 pass on flagged tiles)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-            "work_per_launch": f"18*n_atoms flop per recomputed pair x {pairs:.4g} pairs = {flops:.4g} flop",
-            "screen": {"kernel": "rmsd_gram (tcgen05 BF16 correlation screen)", "bound": "tensor",
+            "work_per_launch": f"30*n_atoms flop per recomputed pair x {pairs:.4g} pairs = {flops:.4g} flop",
+            "screen": {"kernel": "rmsd_gram (tcgen05 split-BF16 correlation screen)", "bound": "tensor",
                        "achieved": fl_s / (t_s / max(n_s, 1) / 1e3) / 1e12 if n_s else 0.0, "peak": pk,
                        "unit": "TFLOP/s",
                        "work_per_launch": f"2*(4 M)*(4 |S|)*{kp} = {fl_s:.4g} flop"}}

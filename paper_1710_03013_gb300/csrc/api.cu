@@ -303,15 +303,14 @@ static kkm_status copy_prepared(const KernelSpec& sp, const float* Xp, const int
 // BF16 planes of both sides, their squared radii, the refine flags and the
 // tensor-core error word.
 struct RmsdTcScratch {
-  __nv_bfloat16* P = nullptr;
-  __nv_bfloat16* Q = nullptr;
-  float* gP = nullptr;
-  float* gQ = nullptr;
+  __nv_bfloat16* P = nullptr;  // [nP_cap][4][3 kp] split-BF16 references
+  __nv_bfloat16* Q = nullptr;  // [nQ_cap][4][3 kp] split-BF16 samples
+  float4* quat = nullptr;      // [nP_cap][ld_cap] rotations of the pairs to refine
   int* flags = nullptr;
   int* key = nullptr;    // [nP_cap] reference sort keys
   int* order = nullptr;  // [nP_cap] reference order of the exact pass
   int* err = nullptr;
-  int64_t nP_cap = 0, nQ_cap = 0;
+  int64_t nP_cap = 0, nQ_cap = 0, ld_cap = 0;
   int kp = 0;
 };
 
@@ -321,14 +320,14 @@ constexpr int64_t kRmsdTcMinRefs = 32;
 constexpr float kRmsdTcMinSigma = 0.5f;
 
 static kkm_status alloc_rmsd_tc(Workspace& ws, const KernelSpec& sp, int64_t nP_cap, int64_t nQ_cap,
-                                RmsdTcScratch* t) {
+                                int64_t ld_cap, RmsdTcScratch* t) {
   t->kp = (int)round_up(sp.n_atoms, 64);
   t->nP_cap = nP_cap;
   t->nQ_cap = nQ_cap;
-  KKM_TRY(ws.alloc(&t->P, nP_cap * 4 * t->kp));
-  KKM_TRY(ws.alloc(&t->Q, nQ_cap * 4 * t->kp));
-  KKM_TRY(ws.alloc(&t->gP, nP_cap));
-  KKM_TRY(ws.alloc(&t->gQ, nQ_cap));
+  t->ld_cap = ld_cap;
+  KKM_TRY(ws.alloc(&t->P, nP_cap * 4 * 3 * t->kp));
+  KKM_TRY(ws.alloc(&t->Q, nQ_cap * 4 * 3 * t->kp));
+  KKM_TRY(ws.alloc(&t->quat, nP_cap * ld_cap));
   KKM_TRY(ws.alloc(&t->flags, ceil_div(nP_cap, 32) * ceil_div(nQ_cap, 64)));
   KKM_TRY(ws.alloc(&t->key, nP_cap));
   KKM_TRY(ws.alloc(&t->order, nP_cap));
@@ -379,15 +378,16 @@ static int sm_count() {
 static kkm_status rmsd_block_tc(const KernelSpec& sp, const float* A, const float* auxA, const int64_t* idA,
                                 int64_t nA, const float* Bm, const float* auxB, const int64_t* idB, int64_t nB,
                                 float* out, int64_t ldo, const RmsdTcScratch& t, bool block, cudaStream_t st) {
-  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(A, nA, sp.ap, sp.n_atoms, t.P, t.kp, t.gP, st));
-  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(Bm, nB, sp.ap, sp.n_atoms, t.Q, t.kp, t.gQ, st));
+  if (ldo > t.ld_cap) return invalid("internal: MD scratch too small");
+  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(A, nA, sp.ap, sp.n_atoms, t.P, t.kp, 0, st));
+  KKM_RUN("rmsd_to_bf16", st, launch_rmsd_to_bf16(Bm, nB, sp.ap, sp.n_atoms, t.Q, t.kp, 1, st));
   KKM_RUN(block ? "rmsd_block" : "rmsd_gram", st,
-          launch_rmsd_tc_estimate(t.P, nA, t.Q, nB, t.kp, t.gP, t.gQ, sp.n_atoms, sp.neg_scale(), out, ldo, t.err,
-                                  sm_count(), st));
+          launch_rmsd_tc_estimate(t.P, nA, t.Q, nB, 3 * t.kp, auxA, auxB, sp.n_atoms, sp.neg_scale(), out, t.quat,
+                                  ldo, t.err, sm_count(), st));
   KKM_RUN("rmsd_plan", st, launch_rmsd_refine_plan(out, ldo, (int)nA, (int)nB, t.key, t.order, t.flags, st));
   KKM_RUN("rmsd_exact", st,
           launch_rmsd_gram(DK_RBF, A, nA, Bm, nB, sp.ap, sp.n_atoms, auxA, auxB, idA, idB, sp.neg_scale(), out, ldo,
-                           st, t.flags, t.order));
+                           st, t.flags, t.order, t.quat));
   if (prof_on()) {  // pairs the exact pass recomputed (profiling only: a read-back)
     const int64_t nf = ceil_div(nA, 32) * ceil_div(nB, 64);
     std::vector<int> f((size_t)nf);
@@ -710,7 +710,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   }
   RmsdTcScratch rtc;
   const bool use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
-  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, nLmax, Nmax, &rtc));
+  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, nLmax, Nmax, ldk, &rtc));
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
   Supports& S = lb.S;
@@ -999,7 +999,7 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
   const float* kself = sp.kind == KKM_LINEAR ? auxc : nullptr;
   RmsdTcScratch rtc;
   const bool use_rtc = sp.kind == KKM_RMSD && rows_ref >= kRmsdTcMinRefs;
-  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, rows_ref, ldm, &rtc));
+  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, rows_ref, ldm, ldm, &rtc));
   LoopBuffers lb;
   if (mode == KKM_ASSIGN_SUPPORTS) {
     KKM_TRY(alloc_loop(ws, m->nL, C, ldm, 1, &lb));
@@ -1105,7 +1105,7 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
   } else if (sp.kind == KKM_RMSD && nA >= kRmsdTcMinRefs) {
     // the MD kernel takes the same tensor-core estimate + exact-refine path as a fit
     RmsdTcScratch rtc;
-    KKM_TRY(alloc_rmsd_tc(ws, sp, nA, nB, &rtc));
+    KKM_TRY(alloc_rmsd_tc(ws, sp, nA, nB, nB, &rtc));
     KKM_TRY(kernel_block(sp, Ap, aA, nullptr, nA, Bp, aB, nullptr, nB, o, nB, st, false, false, &rtc));
     KKM_CK(cudaMemcpyAsync(&tc_err_h, rtc.err, 4, cudaMemcpyDeviceToHost, st));
   } else {

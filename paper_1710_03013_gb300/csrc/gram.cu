@@ -266,7 +266,9 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
                                  cudaStream_t st) {
   const size_t skinny_smem = (size_t)nA * dp * sizeof(float);
   if (nA <= 32 && skinny_smem <= 96 * 1024) {
-    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8), 152 * 8);
+    // every CTA first copies the reference rows to shared memory: few CTAs,
+    // many sample rows each (two per SM)
+    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8), 152 * 2);
     cudaError_t e;
 #define KKM_SKINNY(NAV)                                                                 \
   e = cudaFuncSetAttribute(gram_skinny_kernel<KIND, NAV>,                               \

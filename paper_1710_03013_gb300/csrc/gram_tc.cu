@@ -150,15 +150,17 @@ __device__ __forceinline__ void store_out(__half* p, float v) { *p = __float2hal
 // the 3 x 3 correlation of the pair in its top-left corner.  Each epilogue
 // warp stages a 32 x 32 chunk (8 samples x 8 references) in shared memory,
 // then every lane takes one pair and writes out[l * ldo + s] = 0 if the
-// BF16-product correlation and the rounded frames' squared radii (normQ /
-// normP per frame) certify rmsd^2 beyond the refine threshold (a sign test of
-// the QCP characteristic polynomial and its derivatives, no root iteration),
-// else 1 (the pair is recomputed exactly).
+// correlation (split-BF16 operands, see the prep) and the frames' squared
+// radii (normQ / normP per frame) certify rmsd^2 beyond the refine threshold
+// (a sign test of the QCP characteristic polynomial and its derivatives, no
+// root iteration); else 1 and the QCP rotation (a unit quaternion) to
+// quat[l * ldo + s] for the exact residual pass.
 template <int KIND, typename OutT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
                int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
-               float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err, float inv_n) {
+               float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err, float inv_n,
+               float4* __restrict__ quat) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // stages must start on a 1024-byte boundary (swizzle atom)
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -320,9 +322,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
 #pragma unroll
                 for (int c2 = 0; c2 < 3; ++c2) H[c1 * 3 + c2] = sb[(ps * 4 + c2) * 16 + pl * 4 + c1];
               // 0 for a pair certainly beyond the refine threshold (its true
-              // value is below 1e-5), else 1: the exact pass recomputes it
-              const bool far = qcp_certainly_far(H, normP[lf], normQ[sf], n_r2_far);
+              // value is below 1e-5); else 1, and the QCP rotation for the
+              // exact pass (which then only evaluates the residual)
+              const float gx = normP[lf], gy = normQ[sf];
+              const bool far = qcp_certainly_far(H, gx, gy, n_r2_far);
               store_out(out + (int64_t)lf * ldo + sf, far ? 0.0f : 1.0f);
+              if (!far) {
+                float qv[4];
+                qcp_quaternion(H, gx, gy, qv);
+                quat[(int64_t)lf * ldo + sf] = make_float4(qv[0], qv[1], qv[2], qv[3]);
+              }
             }
             __syncwarp();
           }
@@ -431,7 +440,7 @@ static cudaError_t launch_gram_tc_t(int kind, const CUtensorMap& mq, const CUten
   e = cudaFuncSetAttribute(gram_tc_kernel<K, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
   if (e != cudaSuccess) return e;                                                                         \
   gram_tc_kernel<K, OutT><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, nQ, nP, dk, normQ, normP, neg_scale, out, \
-                                                             ldo, err, 0.0f);
+                                                             ldo, err, 0.0f, nullptr);
   if (kind == DK_DIST) {
     KKM_TC_LAUNCH(DK_DIST)
   } else if (kind == DK_LINEAR) {
@@ -463,10 +472,10 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
 
 cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ, int kp,
                                     const float* gP, const float* gQ, int n_atoms, float neg_scale, float* out,
-                                    int64_t ldo, int* err, int n_sms, cudaStream_t st) {
+                                    float4* quat, int64_t ldo, int* err, int n_sms, cudaStream_t st) {
   if (nP <= 0 || nQ <= 0) return cudaSuccess;
   if (kp % TC_K != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15) ||
-      n_atoms <= 0)
+      n_atoms <= 0 || !quat)
     return cudaErrorInvalidValue;
   alignas(64) CUtensorMap mq, mp;
   if (!make_map(&mq, Q, 4 * nQ, kp, kp, TC_M) || !make_map(&mp, P, 4 * nP, kp, kp, TC_N))
@@ -477,7 +486,7 @@ cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_RMSD);
   if (e != cudaSuccess) return e;
   gram_tc_kernel<DK_RMSD_EST, float><<<grid, TC_THREADS, TC_SMEM_RMSD, st>>>(
-      mq, mp, (int)(4 * nQ), (int)(4 * nP), kp, gQ, gP, neg_scale, out, ldo, err, 1.0f / (float)n_atoms);
+      mq, mp, (int)(4 * nQ), (int)(4 * nP), kp, gQ, gP, neg_scale, out, ldo, err, 1.0f / (float)n_atoms, quat);
   return cudaGetLastError();
 }
 

@@ -129,18 +129,19 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
                            int dk, int ldb, const float* normP, const float* normQ, float neg_scale, void* out,
                            bool out_half, int64_t ldo, int* err, int n_sms, cudaStream_t st);
 // MD kernel screen on the tensor cores: P [4 nP][kp] and Q [4 nQ][kp] hold
-// BF16 centred frames (planes x, y, z and a zero plane, atoms along kp, a
-// multiple of 64), gP / gQ their squared radii.  out[l*ldo + s] = 0 where
-// the BF16-product correlation certifies exp(-rmsd^2 / (2 sigma^2)) <
-// kRmsdRefine for the rounded frames, else 1; the pairs marked 1 are
-// recomputed exactly (launch_rmsd_refine_plan + launch_rmsd_gram with tile
-// flags).  The rounding of the frames moves rmsd^2 by ~2 rmsd x 0.1 A at
-// most for coordinates within ~100 A of the centroid, so for sigma >= 0.5 A a
-// certified pair's true value stays below 1e-5.
+// split-BF16 centred frames (planes x, y, z and a zero plane; kp = 3 segments
+// of the padded atom count, see launch_rmsd_to_bf16), gP / gQ their squared
+// radii.  out[l*ldo + s] = 0 where the correlation certifies exp(-rmsd^2 /
+// (2 sigma^2)) < kRmsdRefine, else 1 with the optimal rotation as a unit
+// quaternion in quat[l*ldo + s]; the pairs marked 1 are recomputed exactly
+// (launch_rmsd_refine_plan, then launch_rmsd_gram with tile flags and quat).
+// The split operands give the correlation to ~1e-5 relative, so the
+// rotation's error enters the exact residual at ~1e-10; the certificate's
+// margin holds for sigma >= 0.5 A and coordinates within ~100 A of the centroid.
 constexpr float kRmsdRefine = 1e-6f;
 cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ, int kp,
                                     const float* gP, const float* gQ, int n_atoms, float neg_scale, float* out,
-                                    int64_t ldo, int* err, int n_sms, cudaStream_t st);
+                                    float4* quat, int64_t ldo, int* err, int n_sms, cudaStream_t st);
 // out[k*ldo + L[k]] = 1 (the exact diagonal of a Gaussian kernel block).
 cudaError_t launch_set_diag(void* out, bool out_half, int64_t ldo, const int32_t* L, int nL, cudaStream_t st);
 // BF16 copy of FP32 rows [n][dp] with the squared norms of the rounded rows.
@@ -157,21 +158,24 @@ cudaError_t launch_rmsd_prep_idx64(const float* X, int n_atoms, const int64_t* i
 // kind DK_RBF: out = exp(-rmsd^2/(2 sigma^2)) via neg_scale; DK_DIST: rmsd.
 // tile_flag (nullable): only the tiles of 32 A-frames x 64 B-frames whose
 // flag is set are computed ([ceil(nA/32)][ceil(nB/64)], A-tile major); arow
-// (nullable): A tile rows are the frames arow[0..nA) in that order.
+// (nullable): A tile rows are the frames arow[0..nA) in that order; quat
+// (nullable, with tile_flag): rotations of the screen for the pairs it
+// marked 1 in out, so only the residual pass runs (pairs marked 0 keep 0).
 cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB,
                              int ap, int n_atoms, const float* gA, const float* gB,
                              const int64_t* idA, const int64_t* idB, float neg_scale,
                              float* out, int64_t ldo, cudaStream_t st, const int* tile_flag = nullptr,
-                             const int* arow = nullptr);
+                             const int* arow = nullptr, const float4* quat = nullptr);
 // From the estimate block est [nA][ldo]: the reference order that groups
 // references near the same samples (key [nA], order [nA]) and the refine flag
 // of every (reference tile of that order, sample tile) ([ceil(nA/32)][ceil(nB/64)]).
 cudaError_t launch_rmsd_refine_plan(const float* est, int64_t ldo, int nA, int nB, int* key, int* order, int* flag,
                                     cudaStream_t st);
-// Centred SoA frames [n][3][ap] (FP32) -> BF16 [n][4][kp] (fourth plane and
-// atoms past n_atoms zero) with the squared radius of the rounded frame.
+// Centred SoA frames [n][3][ap] (FP32) -> split BF16 rows [n][4][3 kp]
+// (fourth plane and atoms past n_atoms zero): segments (hi, lo, hi) for
+// side 0 (references), (hi, hi, lo) for side 1 (samples).
 cudaError_t launch_rmsd_to_bf16(const float* src, int64_t n, int ap, int n_atoms, __nv_bfloat16* dst, int kp,
-                                float* gsq, cudaStream_t st);
+                                int side, cudaStream_t st);
 
 // ---- inner iteration ---------------------------------------------------------
 struct Supports {

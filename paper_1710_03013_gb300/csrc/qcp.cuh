@@ -108,4 +108,52 @@ __device__ __forceinline__ bool qcp_certainly_far(const float H[9], float Gx, fl
   return P > 0.0f && dP > 0.0f && d2P > 0.0f;
 }
 
+// Unit quaternion (w, x, y, z) of the optimal rotation (R x ~ y) and the
+// estimate G_x + G_y - 2 lambda_max (>= 0).  The eigenvector of N for
+// lambda_max is the cofactor row of N - lambda I with the largest diagonal
+// cofactor.  Identity for degenerate input.
+__device__ __forceinline__ float qcp_quaternion(const float H[9], float Gx, float Gy, float q[4]) {
+  q[0] = 1.f;
+  q[1] = q[2] = q[3] = 0.f;
+  const float E0 = 0.5f * (Gx + Gy);
+  if (!(E0 > 0.f)) return 0.f;
+  float m[4][4];
+  const float lam = qcp_lambda(H, E0, m);
+  float a[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[r][c] = m[r][c] - (r == c ? lam : 0.0f);
+  const float d0 = fabsf(minor4(a, 0, 0)), d1 = fabsf(minor4(a, 1, 1));
+  const float d2 = fabsf(minor4(a, 2, 2)), d3 = fabsf(minor4(a, 3, 3));
+  float v[4];
+  if (d0 >= d1 && d0 >= d2 && d0 >= d3) cofactor_row<0>(a, v);
+  else if (d1 >= d2 && d1 >= d3) cofactor_row<1>(a, v);
+  else if (d2 >= d3) cofactor_row<2>(a, v);
+  else cofactor_row<3>(a, v);
+  const float nv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (nv > 0.0f && isfinite(nv)) {
+    const float s = rsqrtf(nv);
+    q[0] = v[0] * s;
+    q[1] = v[1] * s;
+    q[2] = v[2] * s;
+    q[3] = v[3] * s;
+  }
+  return fmaxf((Gx + Gy) * (1.0f - lam), 0.0f);
+}
+
+// Row-major rotation matrix of a unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_rot(const float q[4], float R[9]) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = w * w + x * x - y * y - z * z;
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = w * w - x * x + y * y - z * z;
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = w * w - x * x - y * y + z * z;
+}
+
 }  // namespace kkm

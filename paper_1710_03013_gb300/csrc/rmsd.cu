@@ -86,30 +86,35 @@ cudaError_t launch_rmsd_prep_idx64(const float* X, int n_atoms, const int64_t* i
   return cudaGetLastError();
 }
 
-// SoA FP32 frames -> BF16 planes for the tensor-core estimate: one warp per
-// frame; the squared radius of the rounded frame in double-float.
+// SoA FP32 frames -> BF16 planes for the tensor-core correlation: one warp per
+// frame, row [4 planes][3 kp].  Each coordinate is split v = hi + lo (hi =
+// bf16(v), lo = bf16(v - hi)) and the three kp-long segments of a row are
+// (hi, lo, hi) on the reference side and (hi, hi, lo) on the sample side, so
+// one GEMM over 3 kp sums hi.hi + lo.hi + hi.lo: the correlation to about 16
+// significant bits (the lo.lo term, ~2^-16 relative, is dropped).
 __global__ void rmsd_to_bf16_kernel(const float* __restrict__ src, int64_t n, int ap, int n_atoms,
-                                    __nv_bfloat16* __restrict__ dst, int kp, float* __restrict__ gsq) {
+                                    __nv_bfloat16* __restrict__ dst, int kp, int side) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
   const float* s = src + row * 3 * (int64_t)ap;
-  __nv_bfloat16* d = dst + row * 4 * (int64_t)kp;
-  float2 acc = make_float2(0.0f, 0.0f);
+  __nv_bfloat16* d = dst + row * 4 * (int64_t)(3 * kp);
   for (int c = 0; c < 4; ++c)
     for (int k = lane; k < kp; k += 32) {
-      const __nv_bfloat16 b = __float2bfloat16_rn((c < 3 && k < n_atoms) ? s[c * ap + k] : 0.0f);
-      d[c * kp + k] = b;
-      acc = df_add_sq(acc, __bfloat162float(b));
+      const float v = (c < 3 && k < n_atoms) ? s[c * ap + k] : 0.0f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      __nv_bfloat16* r = d + (int64_t)c * 3 * kp + k;
+      r[0] = hi;
+      r[kp] = side == 0 ? lo : hi;
+      r[2 * kp] = side == 0 ? hi : lo;
     }
-  acc = warp_sum_df(acc);
-  if (lane == 0) gsq[row] = df_to_float(acc);
 }
 
 cudaError_t launch_rmsd_to_bf16(const float* src, int64_t n, int ap, int n_atoms, __nv_bfloat16* dst, int kp,
-                                float* gsq, cudaStream_t st) {
+                                int side, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  rmsd_to_bf16_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(src, n, ap, n_atoms, dst, kp, gsq);
+  rmsd_to_bf16_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(src, n, ap, n_atoms, dst, kp, side);
   return cudaGetLastError();
 }
 
@@ -195,41 +200,10 @@ cudaError_t launch_rmsd_refine_plan(const float* est, int64_t ldo, int nA, int n
 // (sample) with squared radii Gx, Gy.  Returns the estimate G_x + G_y -
 // 2 lambda_max (>= 0) and the rotation R (row-major) with R x ~ y.
 __device__ __forceinline__ float qcp_rotation(const float H[9], float Gx, float Gy, float R[9]) {
-  const float E0 = 0.5f * (Gx + Gy);
-  R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
-  R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
-  R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
-  if (!(E0 > 0.f)) return 0.f;
-  float m[4][4];
-  const float lam = qcp_lambda(H, E0, m);
-  // eigenvector: the cofactor row of N - lambda I with the largest diagonal cofactor
-  float a[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) a[r][c] = m[r][c] - (r == c ? lam : 0.0f);
-  const float d0 = fabsf(minor4(a, 0, 0)), d1 = fabsf(minor4(a, 1, 1));
-  const float d2 = fabsf(minor4(a, 2, 2)), d3 = fabsf(minor4(a, 3, 3));
-  float v[4];
-  if (d0 >= d1 && d0 >= d2 && d0 >= d3) cofactor_row<0>(a, v);
-  else if (d1 >= d2 && d1 >= d3) cofactor_row<1>(a, v);
-  else if (d2 >= d3) cofactor_row<2>(a, v);
-  else cofactor_row<3>(a, v);
-  const float nv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
-  if (nv > 0.0f && isfinite(nv)) {
-    const float s = rsqrtf(nv);
-    const float w = v[0] * s, x = v[1] * s, y = v[2] * s, z = v[3] * s;
-    R[0] = w * w + x * x - y * y - z * z;
-    R[1] = 2.f * (x * y - w * z);
-    R[2] = 2.f * (x * z + w * y);
-    R[3] = 2.f * (x * y + w * z);
-    R[4] = w * w - x * x + y * y - z * z;
-    R[5] = 2.f * (y * z - w * x);
-    R[6] = 2.f * (x * z - w * y);
-    R[7] = 2.f * (y * z + w * x);
-    R[8] = w * w - x * x - y * y + z * z;
-  }
-  return fmaxf((Gx + Gy) * (1.0f - lam), 0.0f);
+  float q[4];
+  const float est = qcp_quaternion(H, Gx, Gy, q);
+  quat_to_rot(q, R);
+  return est;
 }
 
 // --------------------------------------------------------------- pair tile
@@ -322,22 +296,51 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
                  int n_atoms, const float* __restrict__ gA, const float* __restrict__ gB,
                  const int64_t* __restrict__ idA, const int64_t* __restrict__ idB, float neg_scale,
                  float* __restrict__ out, int64_t ldo, int vec_ok, const int* __restrict__ tile_flag,
-                 const int* __restrict__ arow) {
+                 const int* __restrict__ arow, const float4* __restrict__ quat) {
   __shared__ __align__(16) RmsdTiles<TA> t;
   if (tile_flag && !tile_flag[(int64_t)blockIdx.y * gridDim.x + blockIdx.x]) return;  // estimate stands
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int a0 = blockIdx.y * TA, b0 = blockIdx.x * RT_B;
   const int nk = ap / RT_K;
 
-  // ---- pass 1: correlation matrices
   float h[2][4][9];
+  float r2[2][4];
+  unsigned need = 0u;
+  const float inv_n = 1.0f / (float)n_atoms;
+  RmsdPrefetch<TA> pf;
+  if (quat) {
+    // ---- after the tensor-core screen: the rotations of the pairs it did
+    // not certify far come from its correlation (accurate to ~1e-5); only
+    // pass 2 runs
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int ar = min(a0 + ty * 2 + r, nA - 1);
+      const int a = arow ? arow[ar] : ar;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int b = min(b0 + tx * 4 + q, nB - 1);
+        r2[r][q] = 0.0f;
+        const bool live = a0 + ty * 2 + r < nA && b0 + tx * 4 + q < nB;
+        float qq[4] = {1.f, 0.f, 0.f, 0.f};
+        if (live && out[(int64_t)a * ldo + b] != 0.0f) {
+          need |= 1u << (r * 4 + q);
+          const float4 v = quat[(int64_t)a * ldo + b];
+          qq[0] = v.x;
+          qq[1] = v.y;
+          qq[2] = v.z;
+          qq[3] = v.w;
+        }
+        quat_to_rot(qq, h[r][q]);
+      }
+    }
+  } else {
+  // ---- pass 1: correlation matrices
 #pragma unroll
   for (int r = 0; r < 2; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int e = 0; e < 9; ++e) h[r][q][e] = 0.f;
-  RmsdPrefetch<TA> pf;
   rmsd_fetch<TA>(A, nA, Bm, nB, ap, a0, b0, 0, pf, arow);
   rmsd_store<TA>(t, 0, pf);
   __syncthreads();
@@ -373,9 +376,6 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
   }
 
   // ---- QCP estimates and rotations (h is overwritten by R)
-  float r2[2][4];
-  unsigned need = 0u;
-  const float inv_n = 1.0f / (float)n_atoms;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int a = arow ? arow[min(a0 + ty * 2 + r, nA - 1)] : min(a0 + ty * 2 + r, nA - 1);
@@ -391,6 +391,8 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
       const bool refine = (KIND == DK_DIST) || (exp2f(est * neg_scale) > 1e-4f);
       if (refine) need |= 1u << (r * 4 + q);
     }
+  }
+
   }
 
   // ---- pass 2: direct residuals at the QCP rotation, for the warps holding
@@ -482,14 +484,14 @@ rmsd_gram_kernel(const float* __restrict__ A, int nA, const float* __restrict__ 
 cudaError_t launch_rmsd_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB, int ap,
                              int n_atoms, const float* gA, const float* gB, const int64_t* idA,
                              const int64_t* idB, float neg_scale, float* out, int64_t ldo, cudaStream_t st,
-                             const int* tile_flag, const int* arow) {
+                             const int* tile_flag, const int* arow, const float4* quat) {
   if (nA <= 0 || nB <= 0) return cudaSuccess;
-  if (tile_flag && nA <= 8) return cudaErrorInvalidValue;  // flags are laid out for 32-frame A tiles
+  if ((tile_flag || quat) && nA <= 8) return cudaErrorInvalidValue;  // laid out for 32-frame A tiles
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
 #define KKM_RMSD_LAUNCH(K, TA)                                                                       \
   rmsd_gram_kernel<K, TA><<<dim3((unsigned)ceil_div(nB, RT_B), (unsigned)ceil_div(nA, TA)),          \
                             RmsdCfg<TA>::NT, 0, st>>>(A, (int)nA, Bm, (int)nB, ap, n_atoms, gA, gB, idA, \
-                                                      idB, neg_scale, out, ldo, vec_ok, tile_flag, arow)
+                                                      idB, neg_scale, out, ldo, vec_ok, tile_flag, arow, quat)
   if (nA <= 8) {
     if (kind == DK_DIST) KKM_RMSD_LAUNCH(DK_DIST, 8); else KKM_RMSD_LAUNCH(DK_RBF, 8);
   } else {

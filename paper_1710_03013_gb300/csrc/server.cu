@@ -71,8 +71,9 @@ static uint64_t fit_bytes(const kkm_problem& p) {
   b += 4ull * units * ldk + 8ull * units * strips + 4ull * 6 * ldk;  // inner-loop buffers
   b += 24ull * Nmax;                             // k-means++ scratch
   if (p.opt.precision == KKM_BF16) b += 2ull * (Nmax + nL) * dp + 4ull * (Nmax + nL);
-  if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: BF16 planes, radii, refine flags
-    b += 8ull * round_up(p.kernel.n_atoms, 64) * (Nmax + nL) + 4ull * (Nmax + nL) + 4ull * ceil_div(nL, 32) * ceil_div(Nmax, 64);
+  if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: split-BF16 planes, rotations, refine plan
+    b += 24ull * round_up(p.kernel.n_atoms, 64) * (Nmax + nL) + 16ull * nL * ldk + 8ull * nL +
+         4ull * ceil_div(nL, 32) * ceil_div(Nmax, 64);
   b += 4ull * nL * dp + 64ull * nL + 8ull * C * dp;  // the model
   return b + kSlackBytes;
 }
@@ -88,7 +89,7 @@ static uint64_t assign_bytes(const kkm_model* m, int64_t M, int32_t mode) {
   b += 4ull * ldm * (m->dp + 1) + 4ull * rows_ref * ldm;
   if (mode == KKM_ASSIGN_SUPPORTS) b += 4ull * units * ldm + 8ull * units * ceil_div(ldm, kStripCols);
   if (m->kind == KKM_RMSD)  // tensor-core MD path
-    b += 8ull * round_up(m->n_atoms, 64) * (rows_ref + ldm) + 4ull * (rows_ref + ldm) +
+    b += 24ull * round_up(m->n_atoms, 64) * (rows_ref + ldm) + 16ull * rows_ref * ldm + 8ull * rows_ref +
          4ull * ceil_div(rows_ref, 32) * ceil_div(ldm, 64);
   return b + kSlackBytes;
 }

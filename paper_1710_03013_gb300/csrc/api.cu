@@ -434,6 +434,14 @@ int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes) {
 // Rows whose low-precision margin d2 - d1 is below this fraction of
 // max(|d2|, K_ii + g_hat) are re-scored with exact FP32 kernel values.
 constexpr float kRescoreMargin = 1e-3f;
+// The same for a block of FP32-exact values stored in FP16 (the storage
+// rounding alone, <= 2^-12 relative per value, averaged by the segment sums).
+constexpr float kRescoreMarginHalf = 3e-4f;
+// The reduced-precision path computes the block of short rows (d <= this) in
+// FP32 on the FFMA pipes and stores it in FP16: at these lengths the block is
+// a small share of a fit, while the BF16 rounding of the rows would widen the
+// near-tie window (and the re-scores) of every inner iteration.
+constexpr int64_t kBf16TensorMinDim = 129;
 // Share of L2 given to kernel-block rows that stay resident through the inner loop.
 constexpr double kL2KeepShare = 0.70;
 
@@ -671,6 +679,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // significand, finer than the BF16 inputs' rounding): the inner loop
   // streams half the bytes.
   const bool kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
+  const bool fp32_half_block = kt_half && d < kBf16TensorMinDim;
   __half* KTh = nullptr;
   KT = nullptr;
   if (kt_half)
@@ -745,7 +754,10 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
     KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
-    if (sp.precision == KKM_BF16)                                                // Alg. 1 line 3
+    if (fp32_half_block)                                                         // Alg. 1 line 3
+      KKM_RUN("gram_block", st,
+              launch_gram_rbf_half(XL, nL, Xi, Ni, sp.dp, auxL, aux_i, gidL, gid, sp.neg_scale(), KTh, ldk, st));
+    else if (sp.precision == KKM_BF16)
       KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, kt_half ? (void*)KTh : (void*)KT, kt_half, ldk, XLb, nXLb,
                                 Xib, nXib, tc_err, st));
     else
@@ -754,7 +766,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     // L2 hygiene for the inner loop: the BF16 copies are not read again
     // (dropped), the FP32 rows only by the few boundary steps (evict first),
     // so the block rows kept with evict_last own the cache.
-    if (Xib) {
+    if (Xib && !fp32_half_block) {
       KKM_RUN("l2_hygiene", st, launch_l2_discard(Xib, (int64_t)Ni * sp.dp * 2, st));
       KKM_RUN("l2_hygiene", st, launch_l2_discard(XLb, (int64_t)nL * sp.dp * 2, st));
     }
@@ -780,7 +792,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
     const bool rescore = sp.precision != KKM_FP32;
     I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare, kt_half ? 2 : 4);
-    I.flag_tau = rescore ? kRescoreMargin : 0.0f;
+    I.flag_tau = rescore ? (fp32_half_block ? kRescoreMarginHalf : kRescoreMargin) : 0.0f;
     RescoreArgs R;
     if (rescore) {
       R.kind = sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF;

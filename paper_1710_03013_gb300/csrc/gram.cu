@@ -8,6 +8,8 @@
 // exponential.  Squared norms are accumulated in double-float (FP32 pairs)
 // once per row by the gather kernels.  A "skinny" kernel covers <= 32 reference rows (medoid
 // columns, k-means++ columns) with one warp per sample row.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "device_common.cuh"
@@ -127,12 +129,13 @@ __device__ __forceinline__ float gram_epilogue(float dot, float na, float nb, bo
 // ------------------------------------------------------- tiled FP32 product
 constexpr int TB_M = 128, TB_N = 128, TB_K = 8;
 
-template <int KIND>
+// OutT: float, or __half for a Gaussian block stored in FP16 (values in [0, 1]).
+template <int KIND, typename OutT>
 __global__ void __launch_bounds__(256, 2)
 gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
                   int dp, const float* __restrict__ normA, const float* __restrict__ normB,
                   const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
-                  float neg_scale, float* __restrict__ out, int64_t ldo, int vec_ok) {
+                  float neg_scale, OutT* __restrict__ out, int64_t ldo, int vec_ok) {
   __shared__ __align__(16) float As[2][TB_K][TB_M];
   __shared__ __align__(16) float Bs[2][TB_K][TB_N];
   const int tid = threadIdx.x;
@@ -200,17 +203,29 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
     float v[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = gram_epilogue<KIND>(acc[i][j], na, nb[j], ia == ib[j], neg_scale);
-    float* orow = out + (int64_t)a * ldo;
+    OutT* orow = out + (int64_t)a * ldo;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int b = b0 + h * 64 + tx * 4;
-      if (vec_ok && b + 3 < nB) {
-        *reinterpret_cast<float4*>(orow + b) = make_float4(v[h * 4], v[h * 4 + 1], v[h * 4 + 2], v[h * 4 + 3]);
+      if constexpr (sizeof(OutT) == 4) {
+        if (vec_ok && b + 3 < nB) {
+          *reinterpret_cast<float4*>(orow + b) = make_float4(v[h * 4], v[h * 4 + 1], v[h * 4 + 2], v[h * 4 + 3]);
+          continue;
+        }
       } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (b + q < nB) orow[b + q] = v[h * 4 + q];
+        if (vec_ok && b + 3 < nB) {  // 8-byte store of four FP16 values
+          const __half2 lo = __floats2half2_rn(v[h * 4], v[h * 4 + 1]);
+          const __half2 hi = __floats2half2_rn(v[h * 4 + 2], v[h * 4 + 3]);
+          uint2 u;
+          u.x = *reinterpret_cast<const uint32_t*>(&lo);
+          u.y = *reinterpret_cast<const uint32_t*>(&hi);
+          *reinterpret_cast<uint2*>(orow + b) = u;
+          continue;
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (b + q < nB) orow[b + q] = OutT(v[h * 4 + q]);
     }
   }
 }
@@ -285,8 +300,19 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
   }
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  gram_tiled_kernel<KIND><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                neg_scale, out, ldo, vec_ok);
+  gram_tiled_kernel<KIND, float><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
+                                                       neg_scale, out, ldo, vec_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, int64_t nB, int dp, const float* normA,
+                                 const float* normB, const int64_t* idA, const int64_t* idB, float neg_scale,
+                                 __half* out, int64_t ldo, cudaStream_t st) {
+  if (nA <= 0 || nB <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+  gram_tiled_kernel<DK_RBF, __half><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
+                                                          neg_scale, out, ldo, vec_ok);
   return cudaGetLastError();
 }
 

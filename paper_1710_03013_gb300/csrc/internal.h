@@ -120,6 +120,12 @@ cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, i
                         const int64_t* idB, float neg_scale, float* out, int64_t ldo,
                         cudaStream_t st);
 
+// The FP32 RBF block (tiled FFMA kernel, ids force the exact diagonal) stored
+// in FP16: the reduced-precision path's block for short rows.
+cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, int64_t nB, int dp, const float* normA,
+                                 const float* normB, const int64_t* idA, const int64_t* idB, float neg_scale,
+                                 __half* out, int64_t ldo, cudaStream_t st);
+
 // ---- tensor-core (tcgen05) BF16 kernel block ----------------------------
 // out[n*ldo + m] = kappa(P_n, Q_m) for BF16 rows P [nP][ldb], Q [nQ][ldb]
 // (dk valid columns), with the squared norms of the BF16 rows; out is float,

@@ -556,6 +556,7 @@ __device__ __forceinline__ float fhat_of(const AssignShared& sh, const float* __
 constexpr int kAssignRows = 32;
 
 constexpr int kAssignWarps = 8;
+constexpr int kCandCap = 512;  // near-tie re-score pairs listed per CTA
 
 __global__ void __launch_bounds__(kAssignWarps * 32, 4)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
@@ -570,6 +571,9 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   __shared__ float wsum[32];
   __shared__ unsigned flag_mask;
   __shared__ int is_last;
+  __shared__ int cand[kCandCap];  // re-score pairs (row << 9 | cluster)
+  __shared__ int n_cand;
+  __shared__ unsigned slow_mask;
   // Everything but the partials and g_hat was written by launches that have
   // finished when this one starts (the support tables, the old labels, the
   // column ordinals, the self terms): load it before waiting for the f_hat
@@ -665,52 +669,121 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     if (lane == 0) flag_mask = fm;
   }
   __syncthreads();
-  for (unsigned fm = flag_mask; fm; fm &= fm - 1) {  // the same sequence in every thread
-    const int r = __ffs(fm) - 1;
-    const int ir = blockIdx.x * kAssignRows + r;
-    const float* xi = R.Xi + (int64_t)ir * R.dp;
-    for (int c = threadIdx.x; c < R.dp; c += blockDim.x) xs[c] = xi[c];
+  if (flag_mask) {
+    // Candidate pairs (row r, cluster j) of the flagged rows, listed by warp 0:
+    // the clusters whose low-precision distance is inside the row's window.
+    if (w == 0) {
+      const bool fl = (flag_mask >> lane) & 1u;
+      const float b0 = rbest[lane];
+      const float scale = ks + sh.ghf[rlab[lane]];
+      int cnt = 0;
+      if (fl)
+        for (int j = 0; j < C; ++j) {
+          const float dj0 = dsh[j][lane];
+          cnt += dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale);
+        }
+      int x = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+      }
+      const int off = x - cnt;
+      const bool fits = off + cnt <= kCandCap;  // rows in lane order: the fitting ones are a prefix
+      if (fl && fits) {
+        int k = off;
+        for (int j = 0; j < C; ++j) {
+          const float dj0 = dsh[j][lane];
+          if (dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale)) cand[k++] = (lane << 9) | j;
+        }
+      }
+      int used = fits ? off + cnt : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) used = max(used, __shfl_xor_sync(kFull, used, o));
+      const unsigned slow = __ballot_sync(kFull, fl && !fits);
+      if (lane == 0) {
+        n_cand = used;
+        slow_mask = slow;
+      }
+    }
     __syncthreads();
-    const float ni = R.nXi[ir];
-    const float ksr = kself ? kself[ir] : 1.0f;
-    const float b0 = rbest[r];
-    const float scale = ksr + sh.ghf[rlab[r]];
-    for (int j = 0; j < C; ++j) {
-      const float dj0 = dsh[j][r];  // low-precision value (same in every thread)
-      if (!(dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale))) continue;
+    // every warp re-scores whole pairs, one landmark per lane (lane-strided
+    // over the cluster's segment, then a fixed xor tree): FP32 kernel values
+    // from the FP32 rows (16-byte loads; rows are padded to 8 floats)
+    for (int p = w; p < n_cand; p += nw) {
+      const int r = cand[p] >> 9, j = cand[p] & 511;
+      const int ir = blockIdx.x * kAssignRows + r;
+      const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
+      const float ni = R.nXi[ir];
+      const float ksr = kself ? kself[ir] : 1.0f;
       const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
       float acc = 0.0f;
-      for (int kk = k0 + w; kk < k1; kk += nw) {
+      for (int kk = k0 + lane; kk < k1; kk += 32) {
         const int k = S.perm[kk];
-        const float* xl = R.XL + (int64_t)k * R.dp;
+        const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
         float dot = 0.0f;
-        for (int c = lane; c < R.dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
-        dot = warp_sum_f32(dot);
+        for (int c = 0; c < (R.dp >> 2); ++c) {
+          const float4 a = __ldg(xi + c), b = __ldg(xl + c);
+          dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
+        }
         float kv;
         if (R.kind == DK_LINEAR) kv = dot;
         else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
         acc += kv;
       }
-      if (lane == 0) wsum[w] = acc;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float f = 0.0f;
-        for (int q = 0; q < nw; ++q) f += wsum[q];
-        const int n = k1 - k0;
-        dsh[j][r] = n > 0 ? ksr - 2.0f * (f / (float)n) + sh.ghf[j] : inf;
-      }
-      __syncthreads();
+      acc = warp_sum_f32(acc);
+      if (lane == 0) dsh[j][r] = k1 > k0 ? ksr - 2.0f * (acc / (float)(k1 - k0)) + sh.ghf[j] : inf;
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    // rows whose candidates did not fit the list: the whole CTA per row
+    for (unsigned fm = slow_mask; fm; fm &= fm - 1) {  // the same sequence in every thread
+      const int r = __ffs(fm) - 1;
+      const int ir = blockIdx.x * kAssignRows + r;
+      const float* xi = R.Xi + (int64_t)ir * R.dp;
+      for (int c = threadIdx.x; c < R.dp; c += blockDim.x) xs[c] = xi[c];
+      __syncthreads();
+      const float ni = R.nXi[ir];
+      const float ksr = kself ? kself[ir] : 1.0f;
+      const float b0 = rbest[r];
+      const float scale = ksr + sh.ghf[rlab[r]];
+      for (int j = 0; j < C; ++j) {
+        const float dj0 = dsh[j][r];  // low-precision value (same in every thread)
+        if (!(dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale))) continue;
+        const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
+        float acc = 0.0f;
+        for (int kk = k0 + w; kk < k1; kk += nw) {
+          const int k = S.perm[kk];
+          const float* xl = R.XL + (int64_t)k * R.dp;
+          float dot = 0.0f;
+          for (int c = lane; c < R.dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
+          dot = warp_sum_f32(dot);
+          float kv;
+          if (R.kind == DK_LINEAR) kv = dot;
+          else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+          acc += kv;
+        }
+        if (lane == 0) wsum[w] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          float f = 0.0f;
+          for (int q = 0; q < nw; ++q) f += wsum[q];
+          const int n = k1 - k0;
+          dsh[j][r] = n > 0 ? ksr - 2.0f * (f / (float)n) + sh.ghf[j] : inf;
+        }
+        __syncthreads();
+      }
+    }
+    // the argmin of every flagged row over its updated distances
+    if (w == 0 && ((flag_mask >> lane) & 1u)) {
       float best = inf;
       int bj = 0;
       for (int j = 0; j < C; ++j)
-        if (dsh[j][r] < best) {
-          best = dsh[j][r];
+        if (dsh[j][lane] < best) {
+          best = dsh[j][lane];
           bj = j;
         }
-      rbest[r] = best;
-      rlab[r] = bj;
+      rbest[lane] = best;
+      rlab[lane] = bj;
     }
     __syncthreads();
   }

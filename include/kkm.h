@@ -251,6 +251,15 @@ kkm_status kkm_model_trace(const kkm_model* m, double* omega, int32_t* changed,
                            int32_t cap, int32_t* n_out);
 void kkm_model_free(kkm_model* m);
 
+/* kkm_model_save / kkm_model_load -- a fitted model to and from a file (a
+ * little-endian binary with a versioned header), e.g. to restart a serving
+ * process without refitting.  The paper has no persistence; this is a
+ * library service.  Synchronous.  kkm_model_load allocates the model on the
+ * current device; a file that is not a model, or whose header and length
+ * disagree, gives KKM_EINVAL before any device work. */
+kkm_status kkm_model_save(const kkm_model* m, const char* path);
+kkm_status kkm_model_load(const char* path, kkm_model** model_out);
+
 /* kkm_kernel_matrix -- out[a][b] = K(A_a, B_b) for A [nA][d], B [nB][d]
  * (the kernel-block evaluation of Alg. 1 line 3 as a standalone call).
  * out is [nA][nB] float32, device or host.  sigma must be > 0.

@@ -572,6 +572,41 @@ static std::vector<BatchGeom> batch_geometry(int64_t N, int B, int sampling) {
 // ======================================================================
 // kkm_fit
 // ======================================================================
+kkm_status model_alloc_device(kkm_model* m) {
+  const int64_t nL = m->nL, C = m->C, dp = m->dp, mu = m->max_units;
+  // one allocation for the resident arrays (256-byte aligned pieces)
+  std::vector<std::pair<void**, size_t>> parts;
+  auto A = [&](auto** p, int64_t n) {
+    using T = std::remove_reference_t<decltype(**p)>;
+    parts.emplace_back(reinterpret_cast<void**>(p), (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+  };
+  A(&m->sup, nL * dp);
+  A(&m->sup_aux, nL);
+  A(&m->sup_ids, nL);
+  A(&m->sup_labels, nL);
+  A(&m->L_ident, nL);
+  A(&m->perm, nL);
+  A(&m->seg_off, C + 1);
+  A(&m->n_j, C);
+  A(&m->unit_j, mu);
+  A(&m->unit_kb, mu);
+  A(&m->unit_ke, mu);
+  A(&m->seg_unit, C + 1);
+  A(&m->n_units, 1);
+  A(&m->ghat, C);
+  A(&m->med, C * dp);
+  A(&m->med_aux, C);
+  size_t total = 0;
+  for (auto& pr : parts) total += (pr.second + 255) & ~size_t(255);
+  KKM_CK(cudaMalloc(&m->arena, total));
+  size_t off = 0;
+  for (auto& pr : parts) {
+    *pr.first = static_cast<unsigned char*>(m->arena) + off;
+    off += (pr.second + 255) & ~size_t(255);
+  }
+  return KKM_OK;
+}
+
 static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, int32_t B, double s,
                            const kkm_kernel* k, int32_t iters, uint64_t seed, const kkm_options* opt_in,
                            int32_t* labels_out, kkm_model** model_out) {
@@ -745,7 +780,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
 
   // ---- Algorithm 1
+  NvtxRange nv_fit("kkm_fit");
   for (int i = 0; i < B; ++i) {
+    NvtxRange nv_batch("mini-batch");
     const BatchGeom& g = geo[i];
     const int Ni = (int)g.Ni;
     const int nL = (int)(L_off[i + 1] - L_off[i]);
@@ -803,6 +840,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       R.nXL = auxL;
       R.neg_scale = sp.neg_scale();
     }
+    NvtxRange nv_loop("inner loop");
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", st,
               kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, I, st) : launch_fhat_partial(KT, ldk, Ni, S, I, st));
@@ -846,39 +884,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       m->nL = nL;
       m->device = dev;
       std::unique_ptr<kkm_model> guard(m);
-      const int mu = lb.max_units;
-      // one allocation for the resident arrays (256-byte aligned pieces)
-      std::vector<std::pair<void**, size_t>> parts;
-      auto A = [&](auto** p, int64_t n) {
-        using T = std::remove_reference_t<decltype(**p)>;
-        parts.emplace_back(reinterpret_cast<void**>(p), (size_t)std::max<int64_t>(n, 1) * sizeof(T));
-      };
-      A(&m->sup, (int64_t)nL * sp.dp);
-      A(&m->sup_aux, nL);
-      A(&m->sup_ids, nL);
-      A(&m->sup_labels, nL);
-      A(&m->L_ident, nL);
-      A(&m->perm, nL);
-      A(&m->seg_off, C + 1);
-      A(&m->n_j, C);
-      A(&m->unit_j, mu);
-      A(&m->unit_kb, mu);
-      A(&m->unit_ke, mu);
-      A(&m->seg_unit, C + 1);
-      A(&m->n_units, 1);
-      A(&m->ghat, C);
-      A(&m->med, (int64_t)C * sp.dp);
-      A(&m->med_aux, C);
-      size_t total = 0;
-      for (auto& pr : parts) total += (pr.second + 255) & ~size_t(255);
-      KKM_CK(cudaMalloc(&m->arena, total));
-      {
-        size_t off = 0;
-        for (auto& pr : parts) {
-          *pr.first = static_cast<unsigned char*>(m->arena) + off;
-          off += (pr.second + 255) & ~size_t(255);
-        }
-      }
+      m->max_units = lb.max_units;
+      KKM_TRY(model_alloc_device(m));
+      const int mu = m->max_units;
       auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
         KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
         return KKM_OK;
@@ -964,6 +972,7 @@ namespace kkm {
 static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t M, int32_t mode,
                               int32_t* labels_out, float* dist_out, double* omega_out,
                               cudaStream_t st) {
+  NvtxRange nv("kkm_assign");
   if (!m) return invalid("model is NULL");
   if (M < 0 || M > INT32_MAX) return invalid("M must be in [0, 2^31)");
   if (mode != KKM_ASSIGN_SUPPORTS && mode != KKM_ASSIGN_MEDOIDS) return invalid("unknown assign mode");

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -21,6 +22,7 @@ struct kkm_model {
   int n_atoms = 0;
   int dp = 0;  // prepared row length (padded)
   int nL = 0;
+  int max_units = 0;  // capacity of the unit tables
   int device = 0;
   float* sup = nullptr;        // [nL][dp] prepared landmark rows
   float* sup_aux = nullptr;    // [nL] squared norms (RBF/linear) or G (RMSD)
@@ -53,6 +55,10 @@ struct kkm_model {
 
 namespace kkm {
 
+// One device allocation (m->arena) for the model's resident arrays, sized from
+// C, dp, nL and max_units; the array pointers point into it.
+kkm_status model_alloc_device(kkm_model* m);
+
 // ---------------------------------------------------------------- errors ---
 void set_error(const std::string& msg);
 kkm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
@@ -79,6 +85,13 @@ struct ProfScope {
   cudaStream_t stream;
 };
 void prof_collect();  // after a stream sync: fold finished events into totals
+
+// NVTX range for the phases of a call (visible to a profiler attached to the
+// process; header-only, no cost when none is).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 bool prof_on();
 void prof_add_work(const char* name, double units);  // data-dependent work of a kernel
 

@@ -335,9 +335,11 @@ static void worker_loop(kkm_server* s) {
       r = KKM_ECUDA;
       err = "worker stream unavailable";
     } else if (js[0]->kind == Job::FIT) {
+      NvtxRange nv("server fit job");
       r = run_fit(s, *js[0], st);
       err = js[0]->error;
     } else {
+      NvtxRange nv("server assign batch");
       r = run_assigns(s, js, st, &err);
     }
     const auto t_end = Clock::now();

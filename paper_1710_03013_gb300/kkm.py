@@ -91,6 +91,8 @@ _SIGNATURES = {
     "kkm_model_supports": (_I32, [_P, _P, _P, _P]),
     "kkm_model_trace": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "kkm_model_free": (None, [_P]),
+    "kkm_model_save": (_I32, [_P, ctypes.c_char_p]),
+    "kkm_model_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "kkm_kernel_matrix": (_I32, [_P, _I64, _P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _P, _P]),
     "kkm_median_bandwidth": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _U64,
                                     ctypes.POINTER(_F32)]),
@@ -224,6 +226,17 @@ class Model:
         n = np.empty(inf["C"], np.int32)
         _check(load().kkm_model_supports(self._h, lab.ctypes.data, gh.ctypes.data, n.ctypes.data))
         return lab, gh, n
+
+    def save(self, path):
+        """kkm_model_save of the C ABI."""
+        _check(load().kkm_model_save(self._h, os.fsencode(path)))
+
+    @staticmethod
+    def load(path):
+        """kkm_model_load of the C ABI: a new Model on the current device."""
+        h = ctypes.c_void_p()
+        _check(load().kkm_model_load(os.fsencode(path), ctypes.byref(h)))
+        return Model(h)
 
     def trace(self):
         n = _I32()

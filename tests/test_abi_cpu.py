@@ -96,3 +96,28 @@ def test_server_rejects_bad_config_before_any_device_call(kkm):
     assert lib.kkm_fit_batch(None, -1, 0, None, None, None) == kkm.STATUS_EINVAL
     assert lib.kkm_fit_batch(None, 1, 0, None, None, None) == kkm.STATUS_EINVAL
     assert lib.kkm_fit_batch(None, 0, 65, None, None, None) == kkm.STATUS_EINVAL
+
+
+def test_model_load_rejects_bad_files_before_device_work(kkm, tmp_path):
+    """kkm_model_load checks the magic, the header and the file length on the
+    host; a bad file gives KKM_EINVAL without a GPU."""
+    import ctypes
+    import struct
+    lib = kkm.load()
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "missing.kkm").encode()
+    assert lib.kkm_model_load(missing, ctypes.byref(h)) == kkm.STATUS_EINVAL
+    junk = tmp_path / "junk.kkm"
+    junk.write_bytes(b"not a model at all" * 4)
+    assert lib.kkm_model_load(str(junk).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL
+    # right magic, header of a small RBF model, but the arrays cut short
+    hdr = b"KKMMOD01" + struct.pack("<8qd", 3, 16, 0, 0, 16, 20, 3, 5, 1.5)
+    short = tmp_path / "short.kkm"
+    short.write_bytes(hdr + b"\0" * 100)
+    assert lib.kkm_model_load(str(short).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL
+    assert "inconsistent" in kkm.last_error()
+    # inconsistent header (dp does not match d)
+    bad = tmp_path / "bad.kkm"
+    bad.write_bytes(b"KKMMOD01" + struct.pack("<8qd", 3, 16, 0, 0, 24, 20, 3, 5, 1.5))
+    assert lib.kkm_model_load(str(bad).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL
+    assert not h.value

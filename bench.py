@@ -175,6 +175,18 @@ def ncu_traffic(kernel_name, workload="mnist"):
     return ent["bytes_per_launch"]
 
 
+def max_over_ranks(values, world, device):
+    """Each value's maximum over the ranks: a replicated job takes as long as
+    its slowest rank (NCCL on the GPUs; any backend, e.g. gloo on CPU)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_sample(X, rows, cfg):
     """The oracle's whole fit on the first `rows` samples (same d, C, B, s,
@@ -301,10 +313,8 @@ def run_ours(args, cfg, X):
     torch.cuda.synchronize()
     kkm.prof_enable(False)
     breakdown = {n: kkm.prof_read(n)[1] for n in kkm.prof_names()}
-    if world > 1:
-        t = torch.tensor([ms, ms32 or 0.0], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, ms32 = float(t[0].item()), (float(t[1].item()) if ms32 is not None else None)
+    mx = max_over_ranks([ms, ms32 or 0.0], world, dev)
+    ms, ms32 = mx[0], (mx[1] if ms32 is not None else None)
 
     evals = fit_evals(cfg["N"], B, C, s)
     value = world * evals / (ms / 1e3)
@@ -321,11 +331,7 @@ def run_ours(args, cfg, X):
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append(1e3 * (t1 - t0))
-    e2e = float(np.median(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks([float(np.median(e2e_ms))], world, dev)[0]
 
     if rank != 0:
         if world > 1:

@@ -258,8 +258,9 @@ def run_ours(args, cfg, X):
     CMP = PREC[cfg["precisions"][1]] if len(cfg["precisions"]) > 1 else None
     kind, sig, atoms = cfg["kind"], cfg["sigma"], cfg["n_atoms"]
 
-    def step(prec=HEAD):
-        return kkm.kkm_fit(Xd, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False, precision=prec)
+    def step(prec=HEAD, pipeline=args.pipeline):
+        return kkm.kkm_fit(Xd, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False, precision=prec,
+                           pipeline=pipeline)
 
     for _ in range(args.warmup):
         lab, model = step(HEAD)
@@ -272,13 +273,13 @@ def run_ours(args, cfg, X):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(prec, n):
+    def timed(prec, n, pipeline=args.pipeline):
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         out = None
         for _ in range(n):
-            out = step(prec)
+            out = step(prec, pipeline)
         e1.record(stream)
         barrier()
         return e0.elapsed_time(e1) / n, out
@@ -294,27 +295,32 @@ def run_ours(args, cfg, X):
         om16, _ = model.trace()
         om32, _ = model32.trace()
         omega_rel = float(np.max(np.abs(om16 - om32) / np.abs(om32))) if len(om32) else None
-    # timed region 2: the same BF16 steps; every library launch is counted and
-    # the kernel-block and streaming kernels are bracketed by CUDA events on
+    # the same steps with every kernel block computed just before its inner
+    # loop (no overlap with the previous mini-batch), for comparison
+    ms_serial = timed(HEAD, args.steps, "serial")[0] if args.pipeline != "serial" and B > 1 else None
+    # timed region 2: the same steps with serial blocks, so that each kernel
+    # runs alone on the GPU; every library launch is counted and the
+    # kernel-block and streaming kernels are bracketed by CUDA events on
     # their stream (their durations feed the roofline)
     kkm.prof_reset()
     kkm.prof_enable(2)
     barrier()
     for _ in range(args.steps):
-        lab, model = step(HEAD)
+        lab, model = step(HEAD, "serial")
     barrier()
     kkm.prof_enable(False)
     prof = {n: kkm.prof_read(n) for n in kkm.prof_names()}
+    exact_pairs = kkm.prof_work("rmsd_exact")   # pairs the MD exact pass recomputed in region 2
     launches = sum(v[0] for v in prof.values())
     # one more step with every launch timed, for the per-kernel breakdown
     kkm.prof_reset()
     kkm.prof_enable(1)
-    lab, model = step(HEAD)
+    lab, model = step(HEAD, "serial")
     torch.cuda.synchronize()
     kkm.prof_enable(False)
     breakdown = {n: kkm.prof_read(n)[1] for n in kkm.prof_names()}
-    mx = max_over_ranks([ms, ms32 or 0.0], world, dev)
-    ms, ms32 = mx[0], (mx[1] if ms32 is not None else None)
+    mx = max_over_ranks([ms, ms32 or 0.0, ms_serial or 0.0], world, dev)
+    ms, ms32, ms_serial = mx[0], (mx[1] if ms32 is not None else None), (mx[2] if ms_serial is not None else None)
 
     evals = fit_evals(cfg["N"], B, C, s)
     value = world * evals / (ms / 1e3)
@@ -327,7 +333,7 @@ def run_ours(args, cfg, X):
         barrier()
         t0 = time.perf_counter()
         lab_h, _ = kkm.kkm_fit(Xh, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False,
-                               precision=HEAD, stream=ctypes_stream(stream))
+                               precision=HEAD, stream=ctypes_stream(stream), pipeline=args.pipeline)
         t1 = time.perf_counter()
         if k > 0:
             e2e_ms.append(1e3 * (t1 - t0))
@@ -356,7 +362,7 @@ def run_ours(args, cfg, X):
                 "work_per_launch": f"2*N_i*|L|*d = {flops:.4g} flop"}
     elif dom == "rmsd_exact":
         n, tms = prof[dom]
-        pairs = kkm.prof_work("rmsd_exact") / n   # frame pairs the exact pass recomputed, per launch
+        pairs = exact_pairs / n   # frame pairs the exact pass recomputed, per launch
         flops = 30.0 * cfg["n_atoms"] * pairs      # residual |R x - y|^2: 15 FMA per atom
         ach = flops / (tms / n / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
@@ -394,13 +400,17 @@ def run_ours(args, cfg, X):
                 "kernel": "fhat_partial", "peak_source": peak_kind,
                 "work_per_launch": f"{esz}*N_i*|L| = {by:.4g} B (one read of the kernel block)"}
 
+    if roof:
+        roof["timing"] = ("CUDA events on the kernel's stream, every launch of a run with serial blocks "
+                          "(each kernel alone on the GPU)")
+
     # ---- CPU baseline: the oracle on a bounded sample
     ev, dt = oracle_sample(X, CPU_SAMPLE_ROWS[cfg["key"]], cfg)
     cpu = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"oracle fit of the first {CPU_SAMPLE_ROWS[cfg['key']]} samples (same d, C, B, s, iters), "
                      f"{ev} kernel evals in {dt:.1f} s"}
 
-    it_ms = sum(breakdown.get(k, 0.0) for k in ("fhat_partial", "assign", "build_supports"))
+    it_ms = sum(breakdown.get(k, 0.0) for k in ("fhat_partial", "assign"))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -410,11 +420,16 @@ def run_ours(args, cfg, X):
         "data": "synthetic",
         "config": {"workload": cfg["name"], "N": cfg["N"], "d": cfg["d"], "C": C, "B": B, "s": s,
                    "iters_per_minibatch": iters,
+                   "pipeline": (f"{args.pipeline}: next mini-batch's kernel block on a low-priority stream during "
+                                "the current inner loop" if args.pipeline != "serial" and B > 1
+                                else "serial: each kernel block before its inner loop"),
                    "precision": ("bf16 tensor-core kernel block, FP32 near-tie re-score" if HEAD == kkm.KKM_BF16
                                  else "fp32"), "bandwidth": "median rule inside the fit",
                    "l2": f"inputs larger than L2 (X {X.nbytes / 1e6:.0f} MB); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "iters_per_s": world * B * iters / (ms / 1e3),
+        "serial_pipeline": ({"value": world * evals / (ms_serial / 1e3), "unit": UNIT, "ms_per_step": ms_serial}
+                            if ms_serial else None),
         "fp32_path": ({"value": world * evals / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
                        "iters_per_s": world * B * iters / (ms32 / 1e3)} if ms32 else None),
         "matched_labels": {"fraction_equal_to_fp32_path": agree, "omega_max_rel_diff": omega_rel},
@@ -427,8 +442,8 @@ def run_ours(args, cfg, X):
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "kernels_ms_per_step": {k: v for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1])},
-        "kernels_note": "per-kernel breakdown from one step with every launch bracketed by events "
-                        "(short kernels include launch gaps); the roofline uses region 2",
+        "kernels_note": "per-kernel breakdown from one step with serial blocks and every launch bracketed "
+                        "by events (short kernels include launch gaps); the roofline uses region 2",
         "final_omega": float(om[-1]) if len(om) else None,
     }
     print(json.dumps(out), flush=True)
@@ -822,6 +837,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mnist", choices=sorted(WORKLOADS))
     ap.add_argument("--streams", type=int, default=0, help="batched workload: concurrent streams (0: default)")
+    ap.add_argument("--pipeline", default="auto", choices=["auto", "serial", "overlap"],
+                    help="kernel-block scheduling of the fits (auto: next block overlapped when B >= 2)")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     cfg["key"] = args.workload

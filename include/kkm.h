@@ -60,6 +60,18 @@ typedef enum kkm_precision { KKM_FP32 = 0, KKM_BF16 = 1, KKM_FP8 = 2 } kkm_preci
  * contiguous pieces, the first N mod B one sample longer.                   */
 typedef enum kkm_sampling { KKM_STRIDE = 0, KKM_BLOCK = 1 } kkm_sampling;
 
+/* Scheduling of the kernel blocks (Section 4, Fig. 3: the block of the next
+ * mini-batch is produced while the current one iterates).  KKM_PIPE_OVERLAP
+ * computes K(X^(i+1), L^(i+1)) on a low-priority stream while mini-batch i
+ * runs its inner loop on a high-priority one (two block buffers);
+ * KKM_PIPE_SERIAL computes each block just before its inner loop (one
+ * buffer).  KKM_PIPE_AUTO overlaps when B >= 2 except for the KKM_BF16
+ * RBF/linear block (a few percent of such a fit, whose writes would evict
+ * the cached block the inner loop streams); in kkm_fit_batch and the server,
+ * whose fits already run side by side, AUTO means serial.  The results are
+ * the same bits either way: the same kernels run on the same inputs.       */
+typedef enum kkm_pipeline { KKM_PIPE_AUTO = 0, KKM_PIPE_SERIAL = 1, KKM_PIPE_OVERLAP = 2 } kkm_pipeline;
+
 /* Prototypes used by kkm_assign / kkm_cost: the sparse landmark centroids
  * of the last mini-batch (Eq. 14-17) or the global medoids (Eq. 2 against
  * the output M of Algorithm 1).                                             */
@@ -75,7 +87,7 @@ typedef struct kkm_options {
   int32_t precision;            /* kkm_precision (default KKM_FP32)             */
   int32_t sampling;             /* kkm_sampling (default KKM_STRIDE)            */
   int32_t early_stop;           /* 1: stop an inner loop when no label changes */
-  int32_t reserved;             /* must be 0                                    */
+  int32_t pipeline;             /* kkm_pipeline (default KKM_PIPE_AUTO)         */
   const int64_t* init_medoids;  /* host [C] global sample indices replacing
                                    kernel k-means++, or NULL                    */
   void* stream;                 /* cudaStream_t or NULL                         */

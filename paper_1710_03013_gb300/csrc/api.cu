@@ -517,7 +517,6 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
-  KKM_TRY(ws.alloc(&I.lm_changed, 1));
   KKM_TRY(ws.alloc(&I.ticket_sink, 1));
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.gtick, C));
@@ -572,6 +571,99 @@ static std::vector<BatchGeom> batch_geometry(int64_t N, int B, int sampling) {
 // ======================================================================
 // kkm_fit
 // ======================================================================
+// Buffers of one mini-batch's kernel block: its prepared rows and ids, the
+// landmark rows and ids, the block itself (FP16 on the reduced-precision RBF
+// path) and the block kernels' scratch.
+struct BlockBufs {
+  float *Xi = nullptr, *aux_i = nullptr, *XL = nullptr, *auxL = nullptr, *KT = nullptr;
+  __half* KTh = nullptr;
+  int64_t *gid = nullptr, *gidL = nullptr;
+  __nv_bfloat16 *Xib = nullptr, *XLb = nullptr;
+  float *nXib = nullptr, *nXLb = nullptr;
+  RmsdTcScratch rtc;
+};
+
+static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t Nmax, int64_t nLmax, int64_t ldk,
+                                   bool kt_half, bool use_rtc, BlockBufs* b) {
+  KKM_TRY(ws.alloc(&b->Xi, Nmax * sp.dp));
+  KKM_TRY(ws.alloc(&b->aux_i, Nmax));
+  KKM_TRY(ws.alloc(&b->gid, Nmax));
+  KKM_TRY(ws.alloc(&b->XL, nLmax * sp.dp));
+  KKM_TRY(ws.alloc(&b->auxL, nLmax));
+  KKM_TRY(ws.alloc(&b->gidL, nLmax));
+  if (kt_half)
+    KKM_TRY(ws.alloc(&b->KTh, nLmax * ldk));
+  else
+    KKM_TRY(ws.alloc(&b->KT, nLmax * ldk));
+  if (sp.precision == KKM_BF16) {
+    KKM_TRY(ws.alloc(&b->Xib, Nmax * sp.dp));
+    KKM_TRY(ws.alloc(&b->XLb, nLmax * sp.dp));
+    KKM_TRY(ws.alloc(&b->nXib, Nmax));
+    KKM_TRY(ws.alloc(&b->nXLb, nLmax));
+  }
+  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, nLmax, Nmax, ldk, &b->rtc));
+  return KKM_OK;
+}
+
+// Streams of one fit.  With the block pipeline (Section 4, Fig. 3: the next
+// mini-batch's kernel block is produced while the current one iterates) the
+// inner loops run on a high-priority stream and the blocks on a low-priority
+// one, so that a loop kernel's CTAs are scheduled ahead of a block kernel's
+// as SMs free up.  Both start after the work queued so far on the caller's
+// stream; join() (or the destructor, on an error return) orders the caller's
+// stream after both, so the workspace is released only when they are done.
+// Without the pipeline all three are the caller's stream.
+struct FitStreams {
+  cudaStream_t user = nullptr, main = nullptr, side = nullptr;
+  bool own = false;
+
+  // `later` waits for the work queued so far on `first`.
+  static kkm_status after(cudaStream_t first, cudaStream_t later) {
+    if (first == later) return KKM_OK;
+    cudaEvent_t e;
+    KKM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t r = cudaEventRecord(e, first);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(later, e, 0);
+    cudaEventDestroy(e);  // released once recorded work completes; the wait stands
+    KKM_CK(r);
+    return KKM_OK;
+  }
+  kkm_status start(cudaStream_t u, bool pipelined) {
+    user = main = side = u;
+    if (!pipelined) return KKM_OK;
+    int least = 0, greatest = 0;
+    KKM_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaStream_t a = nullptr, b = nullptr;
+    KKM_CK(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, greatest));
+    const cudaError_t e = cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, least);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(a);
+      KKM_CK(e);
+    }
+    main = a;
+    side = b;
+    own = true;
+    KKM_TRY(after(user, main));
+    KKM_TRY(after(user, side));
+    return KKM_OK;
+  }
+  kkm_status join() {
+    if (!own) return KKM_OK;
+    own = false;
+    const kkm_status a = after(main, user), b = after(side, user);
+    if (a != KKM_OK || b != KKM_OK) {
+      // the caller's stream cannot be ordered after them: wait on the host
+      cudaStreamSynchronize(main);
+      cudaStreamSynchronize(side);
+    }
+    cudaStreamDestroy(main);
+    cudaStreamDestroy(side);
+    main = side = user;
+    return a != KKM_OK ? a : b;
+  }
+  ~FitStreams() { join(); }
+};
+
 kkm_status model_alloc_device(kkm_model* m) {
   const int64_t nL = m->nL, C = m->C, dp = m->dp, mu = m->max_units;
   // one allocation for the resident arrays (256-byte aligned pieces)
@@ -619,7 +711,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   if (B < 1 || B > N) return invalid("B must be in [1, N]");
   if (!(s > 0.0 && s <= 1.0)) return invalid("s must be in (0, 1]");
   if (iters < 0) return invalid("iters must be >= 0");
-  if (opt.reserved != 0) return invalid("options.reserved must be 0");
+  if (opt.pipeline != KKM_PIPE_AUTO && opt.pipeline != KKM_PIPE_SERIAL && opt.pipeline != KKM_PIPE_OVERLAP)
+    return invalid("unknown pipeline");
   if (opt.sampling != KKM_STRIDE && opt.sampling != KKM_BLOCK) return invalid("unknown sampling");
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
@@ -699,28 +792,23 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // ---- workspace
   const int64_t ldk = round_up(Nmax, 32);
   const int trace_cap = B * iters;
-  float *Xi, *aux_i, *XL, *auxL, *KT, *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol;
-  int64_t *gid, *gidL, *Mg, *W, *idMI;
+  const bool overlap = fit_overlaps(opt.pipeline, B, sp.kind, sp.precision);
+  float *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol;
+  int64_t *Mg, *W, *idMI;
   int32_t *u, *Ld_all, *mi, *mi_safe, *cnt, *picks, *labels_dev = nullptr;
   unsigned long long* keys;
   double *ghat, *D2 = nullptr, *draws_d = nullptr;
-  KKM_TRY(ws.alloc(&Xi, Nmax * sp.dp));
-  KKM_TRY(ws.alloc(&aux_i, Nmax));
-  KKM_TRY(ws.alloc(&gid, Nmax));
-  KKM_TRY(ws.alloc(&XL, nLmax * sp.dp));
-  KKM_TRY(ws.alloc(&auxL, nLmax));
-  KKM_TRY(ws.alloc(&gidL, nLmax));
   // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
   // significand, finer than the BF16 inputs' rounding): the inner loop
   // streams half the bytes.
   const bool kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
   const bool fp32_half_block = kt_half && d < kBf16TensorMinDim;
-  __half* KTh = nullptr;
-  KT = nullptr;
-  if (kt_half)
-    KKM_TRY(ws.alloc(&KTh, nLmax * ldk));
-  else
-    KKM_TRY(ws.alloc(&KT, nLmax * ldk));
+  const bool use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
+  // one set of block buffers, or two when the next mini-batch's block is
+  // computed while the current one iterates
+  BlockBufs bb[2];
+  const int nbuf = overlap ? 2 : 1;
+  for (int q = 0; q < nbuf; ++q) KKM_TRY(alloc_block_bufs(ws, sp, Nmax, nLmax, ldk, kt_half, use_rtc, &bb[q]));
   KKM_TRY(ws.alloc(&Kt, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&Kmi, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&MX, (int64_t)C * sp.dp));
@@ -741,20 +829,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(ws.alloc(&rowbuf, sp.dp));
   KKM_TRY(ws.alloc(&rowaux, 1));
   KKM_TRY(ws.alloc(&kcol, ldk));
-  __nv_bfloat16 *Xib = nullptr, *XLb = nullptr;
-  float *nXib = nullptr, *nXLb = nullptr;
   int* tc_err = nullptr;
   if (sp.precision == KKM_BF16) {
-    KKM_TRY(ws.alloc(&Xib, Nmax * sp.dp));
-    KKM_TRY(ws.alloc(&XLb, nLmax * sp.dp));
-    KKM_TRY(ws.alloc(&nXib, Nmax));
-    KKM_TRY(ws.alloc(&nXLb, nLmax));
     KKM_TRY(ws.alloc(&tc_err, 1));
     KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
   }
-  RmsdTcScratch rtc;
-  const bool use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
-  if (use_rtc) KKM_TRY(alloc_rmsd_tc(ws, sp, nLmax, Nmax, ldk, &rtc));
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
   Supports& S = lb.S;
@@ -776,57 +855,87 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     else
       labels_dev = labels_out;
   }
-  const float* kself = sp.kind == KKM_LINEAR ? aux_i : nullptr;
   const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+
+  // Alg. 1 line 3 for mini-batch i on stream `bs`: its rows, landmark rows,
+  // ids and kernel block into the buffer set b.
+  auto block_step = [&](int i, const BlockBufs& b, cudaStream_t bs) -> kkm_status {
+    const BatchGeom& g = geo[i];
+    const int Ni = (int)g.Ni;
+    const int nL = (int)(L_off[i + 1] - L_off[i]);
+    const int32_t* Ld = Ld_all + L_off[i];
+    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs));          // fetch X^i
+    KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
+    KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
+    KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
+    if (fp32_half_block)
+      KKM_RUN("gram_block", bs,
+              launch_gram_rbf_half(b.XL, nL, b.Xi, Ni, sp.dp, b.auxL, b.aux_i, b.gidL, b.gid, sp.neg_scale(), b.KTh,
+                                   ldk, bs));
+    else if (sp.precision == KKM_BF16)
+      KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, kt_half ? (void*)b.KTh : (void*)b.KT, kt_half, ldk, b.XLb,
+                                b.nXLb, b.Xib, b.nXib, tc_err, bs));
+    else
+      KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
+                           use_rtc ? &b.rtc : nullptr));
+    // L2 hygiene for the inner loop: the BF16 copies are not read again
+    // (dropped), the FP32 rows only by the few boundary steps (evict first),
+    // so the block rows kept with evict_last own the cache.
+    if (b.Xib && !fp32_half_block) {
+      KKM_RUN("l2_hygiene", bs, launch_l2_discard(b.Xib, (int64_t)Ni * sp.dp * 2, bs));
+      KKM_RUN("l2_hygiene", bs, launch_l2_discard(b.XLb, (int64_t)nL * sp.dp * 2, bs));
+    }
+    KKM_RUN("l2_hygiene", bs, launch_l2_demote(b.Xi, (int64_t)Ni * sp.dp * 4, I.ticket_sink, bs));
+    KKM_RUN("l2_hygiene", bs, launch_l2_demote(b.XL, (int64_t)nL * sp.dp * 4, I.ticket_sink, bs));
+    return KKM_OK;
+  };
 
   // ---- Algorithm 1
   NvtxRange nv_fit("kkm_fit");
+  FitStreams fs;
+  KKM_TRY(fs.start(st, overlap));
+  const cudaStream_t ms = fs.main;
+  if (overlap) KKM_TRY(block_step(0, bb[0], fs.side));
   for (int i = 0; i < B; ++i) {
     NvtxRange nv_batch("mini-batch");
     const BatchGeom& g = geo[i];
     const int Ni = (int)g.Ni;
     const int nL = (int)(L_off[i + 1] - L_off[i]);
     const int32_t* Ld = Ld_all + L_off[i];
-    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, Xi, aux_i, st));             // fetch X^i
-    KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, g.start, g.step, Ni), cudaGetLastError()));
-    KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));                     // landmarks
-    KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
-    if (fp32_half_block)                                                         // Alg. 1 line 3
-      KKM_RUN("gram_block", st,
-              launch_gram_rbf_half(XL, nL, Xi, Ni, sp.dp, auxL, aux_i, gidL, gid, sp.neg_scale(), KTh, ldk, st));
-    else if (sp.precision == KKM_BF16)
-      KKM_TRY(kernel_block_bf16(sp, XL, Ld, nL, Xi, Ni, kt_half ? (void*)KTh : (void*)KT, kt_half, ldk, XLb, nXLb,
-                                Xib, nXib, tc_err, st));
-    else
-      KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux_i, gid, Ni, KT, ldk, st, false, true,
-                           use_rtc ? &rtc : nullptr));
-    // L2 hygiene for the inner loop: the BF16 copies are not read again
-    // (dropped), the FP32 rows only by the few boundary steps (evict first),
-    // so the block rows kept with evict_last own the cache.
-    if (Xib && !fp32_half_block) {
-      KKM_RUN("l2_hygiene", st, launch_l2_discard(Xib, (int64_t)Ni * sp.dp * 2, st));
-      KKM_RUN("l2_hygiene", st, launch_l2_discard(XLb, (int64_t)nL * sp.dp * 2, st));
+    const BlockBufs& bk = bb[i % nbuf];
+    if (overlap) {
+      // the block of mini-batch i is ready; the side stream then produces the
+      // next one into the other buffer set, whose last reader (mini-batch
+      // i - 1) is queued on the main stream before this point
+      KKM_TRY(FitStreams::after(fs.side, ms));
+      if (i + 1 < B) {
+        KKM_TRY(FitStreams::after(ms, fs.side));
+        KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side));
+      }
+    } else {
+      KKM_TRY(block_step(i, bk, ms));
     }
-    KKM_RUN("l2_hygiene", st, launch_l2_demote(Xi, (int64_t)Ni * sp.dp * 4, I.ticket_sink, st));
-    KKM_RUN("l2_hygiene", st, launch_l2_demote(XL, (int64_t)nL * sp.dp * 4, I.ticket_sink, st));
-
+    float* const Xi = bk.Xi;
+    float* const aux_i = bk.aux_i;
+    int64_t* const gid = bk.gid;
+    const float* kself = sp.kind == KKM_LINEAR ? aux_i : nullptr;
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
-      KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, st));
-      KKM_RUN("local_to_global", st, launch_local_to_global(picks, C, g.start, g.step, Mg, st));
+      KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, ms));
+      KKM_RUN("local_to_global", ms, launch_local_to_global(picks, C, g.start, g.step, Mg, ms));
     }
     // Eq. 8: auxiliary block K~ = K(M, X^i) and nearest-medoid labels
-    KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, st));
-    KKM_TRY(kernel_block(sp, MX, auxM, Mg, C, Xi, aux_i, gid, Ni, Kt, ldk, st));
-    KKM_RUN("nearest", st, launch_nearest(Kt, ldk, Ni, C, kself, kmm, u, nullptr, st));
+    KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, ms));
+    KKM_TRY(kernel_block(sp, MX, auxM, Mg, C, Xi, aux_i, gid, Ni, Kt, ldk, ms));
+    KKM_RUN("nearest", ms, launch_nearest(Kt, ldk, Ni, C, kself, kmm, u, nullptr, ms));
 
     // supports of the initial labels
     S.L = Ld;
     S.nL = nL;
-    KKM_RUN("fill", st, launch_fill_i32(S.col_label, -1, ldk, st));
-    KKM_RUN("fill", st, launch_fill_i32(S.col_ord, -1, ldk, st));
-    KKM_RUN("landmark_maps", st, launch_landmark_maps(S, u, st));
-    KKM_RUN("build_supports", st, launch_build_supports(S, nullptr, nullptr, st));
-    KKM_CK(cudaMemsetAsync(I.done, 0, 4, st));
+    KKM_RUN("fill", ms, launch_fill_i32(S.col_label, -1, ldk, ms));
+    KKM_RUN("fill", ms, launch_fill_i32(S.col_ord, -1, ldk, ms));
+    KKM_RUN("landmark_maps", ms, launch_landmark_maps(S, u, ms));
+    KKM_RUN("build_supports", ms, launch_build_supports(S, ms));
+    KKM_CK(cudaMemsetAsync(I.done, 0, 4, ms));
     const bool rescore = sp.precision != KKM_FP32;
     I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare, kt_half ? 2 : 4);
     I.flag_tau = rescore ? (fp32_half_block ? kRescoreMarginHalf : kRescoreMargin) : 0.0f;
@@ -836,42 +945,40 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       R.dp = sp.dp;
       R.Xi = Xi;
       R.nXi = aux_i;
-      R.XL = XL;
-      R.nXL = auxL;
+      R.XL = bk.XL;
+      R.nXL = bk.auxL;
       R.neg_scale = sp.neg_scale();
     }
     NvtxRange nv_loop("inner loop");
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
-      KKM_RUN("fhat_partial", st,
-              kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, I, st) : launch_fhat_partial(KT, ldk, Ni, S, I, st));
-      KKM_RUN("assign", st,
+      KKM_RUN("fhat_partial", ms,
+              kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, I, ms) : launch_fhat_partial(bk.KT, ldk, Ni, S, I, ms));
+      // assign; its last CTA closes the iteration (trace, early stop) and
+      // re-sorts the supports when a landmark label changed
+      KKM_RUN("assign", ms,
               launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
-                            /*trace=*/2, st, R));
-      // build_supports closes the iteration (trace, early stop) and re-sorts
-      KKM_RUN("build_supports", st,
-              launch_build_supports(S, I.done, I.lm_changed, st,
-                                    close_args(I, (int)ceil_div(Ni, 32), opt.early_stop)));
+                            /*trace=*/1, ms, R));
     }
     I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
     Ifin.done = nullptr;
-    KKM_RUN("fhat_partial", st,
-            kt_half ? launch_fhat_partial(KTh, ldk, Ni, S, Ifin, st) : launch_fhat_partial(KT, ldk, Ni, S, Ifin, st));
-    KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
-    KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, st));
-    KKM_RUN("medoid_keys", st, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, st));
-    KKM_RUN("medoid_pick", st, launch_medoid_pick(keys, cnt, S.n_j, C, mi, st));
+    KKM_RUN("fhat_partial", ms,
+            kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, Ifin, ms) : launch_fhat_partial(bk.KT, ldk, Ni, S, Ifin, ms));
+    KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
+    KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
+    KKM_RUN("medoid_keys", ms, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, ms));
+    KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms));
     // Eq. 12: K(X^i, m^i) and the convex merge
-    KKM_RUN("clamp_idx", st, (clamp_idx_kernel<<<blocks_for(C), 256, 0, st>>>(mi, C, mi_safe), cudaGetLastError()));
-    KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, st));
-    KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(C), 256, 0, st>>>(gid, mi, C, idMI), cudaGetLastError()));
-    KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, st));
-    KKM_RUN("fill", st, launch_fill_u64(keys, ~0ull, C, st));
-    KKM_RUN("merge_keys", st, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, st));
-    KKM_RUN("merge_apply", st, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, st));
+    KKM_RUN("clamp_idx", ms, (clamp_idx_kernel<<<blocks_for(C), 256, 0, ms>>>(mi, C, mi_safe), cudaGetLastError()));
+    KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, ms));
+    KKM_RUN("gather_ids", ms, (gather_i64_kernel<<<blocks_for(C), 256, 0, ms>>>(gid, mi, C, idMI), cudaGetLastError()));
+    KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, ms));
+    KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
+    KKM_RUN("merge_keys", ms, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, ms));
+    KKM_RUN("merge_apply", ms, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, ms));
     if (labels_dev)
-      KKM_RUN("scatter_labels", st, launch_scatter_labels(u, Ni, g.start, g.step, labels_dev, st));
+      KKM_RUN("scatter_labels", ms, launch_scatter_labels(u, Ni, g.start, g.step, labels_dev, ms));
     if (i == B - 1 && model_out) {
       // keep the final supports of the last mini-batch
       kkm_model* m = new kkm_model();
@@ -888,12 +995,12 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(model_alloc_device(m));
       const int mu = m->max_units;
       auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
-        KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+        KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ms));
         return KKM_OK;
       };
-      KKM_TRY(cp(m->sup, XL, (size_t)nL * sp.dp * 4));
-      KKM_TRY(cp(m->sup_aux, auxL, (size_t)nL * 4));
-      KKM_TRY(cp(m->sup_ids, gidL, (size_t)nL * 8));
+      KKM_TRY(cp(m->sup, bk.XL, (size_t)nL * sp.dp * 4));
+      KKM_TRY(cp(m->sup_aux, bk.auxL, (size_t)nL * 4));
+      KKM_TRY(cp(m->sup_ids, bk.gidL, (size_t)nL * 8));
       KKM_TRY(cp(m->perm, S.perm, (size_t)nL * 4));
       KKM_TRY(cp(m->seg_off, S.seg_off, (size_t)(C + 1) * 4));
       KKM_TRY(cp(m->n_j, S.n_j, (size_t)C * 4));
@@ -903,16 +1010,18 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(cp(m->seg_unit, S.seg_unit, (size_t)(C + 1) * 4));
       KKM_TRY(cp(m->n_units, S.n_units, 4));
       KKM_TRY(cp(m->ghat, ghat, (size_t)C * 8));
-      KKM_RUN("gather_labels", st, (gather_i32_kernel<<<blocks_for(nL), 256, 0, st>>>(u, Ld, nL, m->sup_labels), cudaGetLastError()));
+      KKM_RUN("gather_labels", ms, (gather_i32_kernel<<<blocks_for(nL), 256, 0, ms>>>(u, Ld, nL, m->sup_labels), cudaGetLastError()));
       {
         std::vector<int32_t> ident(nL);
         for (int q = 0; q < nL; ++q) ident[q] = q;
-        KKM_CK(cudaMemcpyAsync(m->L_ident, ident.data(), (size_t)nL * 4, cudaMemcpyHostToDevice, st));
-        KKM_CK(cudaStreamSynchronize(st));
+        KKM_CK(cudaMemcpyAsync(m->L_ident, ident.data(), (size_t)nL * 4, cudaMemcpyHostToDevice, ms));
+        KKM_CK(cudaStreamSynchronize(ms));
       }
       *model_out = guard.release();
     }
   }
+
+  KKM_TRY(fs.join());
 
   // ---- results
   if (model_out && *model_out) {
@@ -941,11 +1050,12 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   }
   if (labels_on_host)
     KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
-  int tc_err_h = 0, rtc_err_h = 0;
+  int tc_err_h = 0, rtc_err_h[2] = {0, 0};
   if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
-  if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h, rtc.err, 4, cudaMemcpyDeviceToHost, st));
+  for (int q = 0; q < nbuf; ++q)
+    if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h[q], bb[q].rtc.err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
-  tc_err_h |= rtc_err_h;
+  tc_err_h |= rtc_err_h[0] | rtc_err_h[1];
   if (tc_err_h) {
     set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
     return KKM_ETIMEOUT;
@@ -1196,7 +1306,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_label, -1, ldk, st));
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_ord, -1, ldk, st));
   KKM_RUN("landmark_maps", st, launch_landmark_maps(lb.S, u, st));
-  KKM_RUN("build_supports", st, launch_build_supports(lb.S, nullptr, nullptr, st));
+  KKM_RUN("build_supports", st, launch_build_supports(lb.S, st));
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
   const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
   KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));

@@ -106,6 +106,21 @@ constexpr int kMaxC = 256;     // clusters per problem (one scan slot per thread
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Whether kkm_fit computes the next mini-batch's kernel block while the
+// current one iterates (two block buffers; the server sizes fits by it).
+// KKM_PIPE_AUTO overlaps for B >= 2 unless the block is the reduced-precision
+// RBF/linear block on the tensor cores: that block is a few percent of a fit,
+// and its writes would push the inner loop's cached block out of L2.
+inline bool fit_overlaps(int pipeline, int B, int kind, int precision) {
+  if (B < 2 || pipeline == KKM_PIPE_SERIAL) return false;
+  if (pipeline == KKM_PIPE_OVERLAP) return true;
+  return kind == KKM_RMSD || precision == KKM_FP32;
+}
+// Fits that run side by side (kkm_fit_batch, the server's workers) overlap
+// one another; inside each, AUTO means serial blocks (a low-priority block
+// stream would wait behind the other fits' high-priority inner loops).
+inline int side_by_side_pipeline(int pipeline) { return pipeline == KKM_PIPE_AUTO ? KKM_PIPE_SERIAL : pipeline; }
+
 // Kernel-function codes used on the device.
 enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3 };
 
@@ -230,7 +245,6 @@ struct IterState {
   int32_t* trace_count;  // [1]
   const double* ghat_in = nullptr;  // g_hat given (assign against a model), else from gpart
   int32_t* lm_part = nullptr;       // [assign grid] landmark label changes per CTA
-  int32_t* lm_changed = nullptr;    // [1] landmark labels changed by the last assign
   // near-tie re-score (low-precision kernel blocks): rows whose margin is
   // below flag_tau * max(|d2|, K_ii + g_hat) are re-scored in FP32 by assign
   float flag_tau = 0.0f;
@@ -248,26 +262,8 @@ int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes = 4);
 // whose contents are not needed again.
 cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st);
 cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st);
-// Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA);
-// skipped when *skip != 0 or when *lm_changed == 0 (then nothing changed).
-// The iteration's closing, done by build_supports when the assign ran with
-// trace == 2: Omega and the counts from the per-CTA partials of assign (fixed
-// order), the trace entry, the early-stop flag and the landmark-change count.
-struct CloseArgs {
-  int n_parts = 0;  // 0: nothing to close
-  int early_stop = 0;
-  const float2* omega_part = nullptr;
-  const int32_t* changed_part = nullptr;
-  const int32_t* lm_part = nullptr;
-  double* trace_omega = nullptr;
-  int32_t* trace_changed = nullptr;
-  int32_t* trace_count = nullptr;
-  int32_t* done = nullptr;
-  int32_t* lm_changed = nullptr;
-};
-CloseArgs close_args(const IterState& I, int n_parts, int early_stop);
-cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
-                                  cudaStream_t st, const CloseArgs& close = CloseArgs());
+// Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA).
+cudaError_t launch_build_supports(const Supports& S, cudaStream_t st);
 // col_ord[L[k]] = k (col_ord pre-filled with -1) and lab[k] = u[L[k]].
 cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream_t st);
 // Streams K^T [nL][ldk] once: per unit partial sums of the f_hat numerators.
@@ -290,8 +286,8 @@ struct RescoreArgs {
 
 // f_hat, distances, argmin, margin, Omega; updates u in place.  With
 // trace == 1 the last CTA also writes the trace entry, the early-stop flag and
-// the count of changed landmark labels; with trace == 2 it leaves that to the
-// build_supports launch that follows (CloseArgs).  Uses ceil(Ni/32) CTAs
+// the count of changed landmark labels, and re-sorts the supports (as
+// build_supports) when a landmark label changed.  Uses ceil(Ni/32) CTAs
 // (omega_part/changed_part/lm_part need that many slots).
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                           const float* kself, int32_t* u, float* margin, float* dmin,

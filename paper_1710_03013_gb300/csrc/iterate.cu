@@ -8,7 +8,7 @@
 // cluster j is the contiguous segment perm[seg_off[j] .. seg_off[j+1]).  The
 // segment is cut into units of at most kUnitRows landmark rows.
 //
-// One iteration is three launches:
+// One iteration is two launches:
 //   fhat_partial  streams KT once (the HBM-bound step): every CTA sums the
 //                 rows of one unit over a strip of columns (16-byte loads,
 //                 FP32 or FP16 storage) and writes the partial numerators of
@@ -20,9 +20,10 @@
 //                 j on ties), the margin and the FP64 cost partials, and
 //                 updates the labels in place.  Its last CTA to finish (atomic
 //                 ticket, no waiting) sums the cost in a fixed order, records
-//                 the trace and raises the early-stop flag;
-//   build_supports  one 1024-thread CTA re-sorts the landmarks by their new
-//                 labels for the next iteration.
+//                 the trace, raises the early-stop flag and, when a landmark
+//                 label changed, re-sorts the landmarks by their new labels
+//                 for the next iteration (build_supports does the same sort
+//                 for the initial labels of a mini-batch).
 // Every sum has a fixed order, so results are bit-reproducible.
 #include <math.h>
 
@@ -90,93 +91,38 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sh, int* total) {
   return off + x - v;
 }
 
-// Rebuilds the support structure of the landmarks from the labels u: a
-// stable counting sort of the landmark ordinals by label (n_j, segment and
-// unit tables, perm) and the label of every landmark column.  One CTA of
-// kSortThreads threads; returns at once when the early-stop flag is set.
-//
-// With cl.n_parts > 0 it first closes the iteration of the assign launch
-// before it: Omega (double-float partials, thread-strided then a fixed tree),
-// #changed and the landmark-change count; the trace entry; the early-stop
-// flag.  The whole CTA does it in parallel, off the assign's critical path.
-__global__ void __launch_bounds__(kSortThreads)
-build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
-                      const int32_t* __restrict__ lm_changed, CloseArgs cl) {
-  __shared__ int cnt[kMaxC];
-  __shared__ int base[kMaxC];
-  __shared__ int wtab[32 * kMaxC];
-  __shared__ int scan_sh[32];
-  __shared__ float2 dred[32];
-  __shared__ int lm_sh;
-  griddep_wait();
-  griddep_launch();
-  if (skip && *skip) return;
+// Stable counting sort of the landmark ordinals by label, done by one CTA
+// (any multiple of 32 threads with blockDim.x >= C): n_j, the segment and
+// unit tables, perm, and the label of every landmark column.  Shared
+// scratch: cnt[C], base[C], wtab[(blockDim.x / 32) * C], scan_sh[32].
+__device__ void sort_supports_cta(const Supports& S, int* cnt, int* base, int* wtab, int* scan_sh) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (cl.n_parts > 0) {
-    float2 o = make_float2(0.0f, 0.0f);
-    int c = 0, lm = 0;
-    for (int b = tid; b < cl.n_parts; b += kSortThreads) {
-      o = df_add(o, cl.omega_part[b]);
-      c += cl.changed_part[b];
-      lm += cl.lm_part ? cl.lm_part[b] : 0;
-    }
-    o = warp_sum_df(o);
-    c = warp_sum_i32(c);
-    lm = warp_sum_i32(lm);
-    if (lane == 0) {
-      dred[w] = o;
-      wtab[w] = c;
-      wtab[32 + w] = lm;
-    }
-    __syncthreads();
-    if (w == 0) {
-      const int nw = kSortThreads / 32;
-      o = lane < nw ? dred[lane] : make_float2(0.0f, 0.0f);
-      c = lane < nw ? wtab[lane] : 0;
-      lm = lane < nw ? wtab[32 + lane] : 0;
-      o = warp_sum_df(o);
-      c = warp_sum_i32(c);
-      lm = warp_sum_i32(lm);
-      if (lane == 0) {
-        const int t = *cl.trace_count;
-        cl.trace_omega[t] = (double)o.x + (double)o.y;
-        cl.trace_changed[t] = c;
-        *cl.trace_count = t + 1;
-        if (cl.early_stop && c == 0) *cl.done = 1;
-        if (cl.lm_changed) *cl.lm_changed = lm;
-        lm_sh = lm;
-      }
-    }
-    __syncthreads();
-    if (lm_sh == 0) return;  // same landmark labels: same supports
-  } else if (lm_changed && *lm_changed == 0) {
-    return;
-  }
+  const int nt = blockDim.x, nw = nt >> 5;
   const int C = S.C, nL = S.nL;
-  for (int j = tid; j < C; j += kSortThreads) cnt[j] = 0;
+  for (int j = tid; j < C; j += nt) cnt[j] = 0;
   __syncthreads();
-  // all landmark labels of this thread, loaded at once (kLabRegs per thread;
-  // larger landmark sets reload from global memory in pass 2)
+  // the first kLabRegs * nt landmark labels of this thread stay in registers;
+  // larger landmark sets reload the rest from global memory in pass 2
   int labr[kLabRegs];
 #pragma unroll
   for (int q = 0; q < kLabRegs; ++q) {
-    const int k = q * kSortThreads + tid;
-    labr[q] = k < nL ? S.lab[k] : -1;
+    const int k = q * nt + tid;
+    labr[q] = k < nL ? __ldcg(S.lab + k) : -1;
   }
   // pass 1: counts (one shared atomic per distinct label and warp)
-  for (int start = 0, q = 0; start < nL; start += kSortThreads, ++q) {
+  for (int start = 0, q = 0; start < nL; start += nt, ++q) {
     const int k = start + tid;
     int lab = -1;
 #pragma unroll
     for (int qq = 0; qq < kLabRegs; ++qq)
       if (qq == q) lab = labr[qq];
-    if (q >= kLabRegs) lab = k < nL ? S.lab[k] : -1;
+    if (q >= kLabRegs) lab = k < nL ? __ldcg(S.lab + k) : -1;
     if (k < nL) S.col_label[S.L[k]] = lab;
     const unsigned peers = __match_any_sync(kFull, lab);
     if (lab >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[lab], __popc(peers));
   }
   __syncthreads();
-  // segment offsets and units (C <= 256 <= blockDim: one entry per thread)
+  // segment offsets and units (one cluster per thread)
   const int cj = tid < C ? cnt[tid] : 0;
   int total;
   const int off = block_excl_scan(cj, scan_sh, &total);
@@ -201,23 +147,24 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
     *S.n_units = nunits;
   }
   __syncthreads();
-  // pass 2: stable scatter, 1024 landmarks at a time in landmark order
-  for (int start = 0, q = 0; start < nL; start += kSortThreads, ++q) {
+  // pass 2: stable scatter, nt landmarks at a time in landmark order
+  for (int start = 0, q = 0; start < nL; start += nt, ++q) {
     const int k = start + tid;
     int lab = -1;
 #pragma unroll
     for (int qq = 0; qq < kLabRegs; ++qq)
       if (qq == q) lab = labr[qq];
-    if (q >= kLabRegs) lab = k < nL ? S.lab[k] : -1;
+    if (q >= kLabRegs) lab = k < nL ? __ldcg(S.lab + k) : -1;
     const unsigned peers = __match_any_sync(kFull, lab);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    for (int e = tid; e < 32 * C; e += kSortThreads) wtab[e] = 0;
+    for (int e = tid; e < nw * C; e += nt) wtab[e] = 0;
     __syncthreads();
     if (lab >= 0 && rank == 0) wtab[w * C + lab] = __popc(peers);
     __syncthreads();
-    // per label, an exclusive scan over the 32 warps (one warp per label)
-    for (int j = w; j < C; j += 32) {
-      const int v = wtab[lane * C + j];
+    // per label, an exclusive scan over the warps (one warp per label, lane =
+    // warp index)
+    for (int j = w; j < C; j += nw) {
+      const int v = lane < nw ? wtab[lane * C + j] : 0;
       int x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -225,9 +172,10 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
         if (lane >= o) x += y;
       }
       const int b = base[j];
-      wtab[lane * C + j] = b + x - v;
+      if (lane < nw) wtab[lane * C + j] = b + x - v;
+      const int tot = __shfl_sync(kFull, x, 31);
       __syncwarp();
-      if (lane == 31) base[j] = b + x;
+      if (lane == 0) base[j] = b + tot;
     }
     __syncthreads();
     if (lab >= 0) S.perm[wtab[w * C + lab] + rank] = k;
@@ -235,24 +183,20 @@ build_supports_kernel(Supports S, const int32_t* __restrict__ skip,
   }
 }
 
-CloseArgs close_args(const IterState& I, int n_parts, int early_stop) {
-  CloseArgs c;
-  c.n_parts = n_parts;
-  c.early_stop = early_stop;
-  c.omega_part = I.omega_part;
-  c.changed_part = I.changed_part;
-  c.lm_part = I.lm_part;
-  c.trace_omega = I.trace_omega;
-  c.trace_changed = I.trace_changed;
-  c.trace_count = I.trace_count;
-  c.done = I.done;
-  c.lm_changed = I.lm_changed;
-  return c;
+// Rebuilds the support structure of the landmarks from their labels (the
+// sort above) in one CTA of kSortThreads threads.
+__global__ void __launch_bounds__(kSortThreads) build_supports_kernel(Supports S) {
+  __shared__ int cnt[kMaxC];
+  __shared__ int base[kMaxC];
+  __shared__ int wtab[32 * kMaxC];
+  __shared__ int scan_sh[32];
+  griddep_wait();
+  griddep_launch();
+  sort_supports_cta(S, cnt, base, wtab, scan_sh);
 }
 
-cudaError_t launch_build_supports(const Supports& S, const int32_t* skip, const int32_t* lm_changed,
-                                  cudaStream_t st, const CloseArgs& close) {
-  return launch_pdl(build_supports_kernel, dim3(1), dim3(kSortThreads), 0, st, S, skip, lm_changed, close);
+cudaError_t launch_build_supports(const Supports& S, cudaStream_t st) {
+  return launch_pdl(build_supports_kernel, dim3(1), dim3(kSortThreads), 0, st, S);
 }
 
 __global__ void landmark_maps_kernel(Supports S, const int32_t* __restrict__ u) {
@@ -313,7 +257,6 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   __shared__ double redd[kStreamThreads / 32];
   __shared__ int last;
   griddep_wait();
-  griddep_launch();
   if (skip && *skip) return;
   const int unit = blockIdx.y;
   // unit tables are allocated for max_units entries, so these loads stay in
@@ -377,6 +320,9 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
     for (int c = 0; c < NC; c += 4)
       *reinterpret_cast<float4*>(out + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
   }
+  // The assign may launch once every CTA has streamed its rows: its CTAs
+  // then land on SMs this launch has left, evenly, while the g_hat tail runs.
+  griddep_launch();
   // g_hat numerator: landmark columns of the same cluster
   if (!S.col_label) return;
   float2 g = make_float2(0.0f, 0.0f);
@@ -565,7 +511,15 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
               int trace, RescoreArgs R) {
   extern __shared__ float xs[];  // [R.dp] while re-scoring a row
   __shared__ AssignShared sh;
-  __shared__ float dsh[kMaxC][kAssignRows];
+  // distances of the CTA's rows; the last CTA reuses the space to re-sort
+  // the supports
+  __shared__ union {
+    float d[kMaxC][kAssignRows];
+    struct {
+      int cnt[kMaxC], base[kMaxC], wtab[kAssignWarps * kMaxC], scan[32];
+    } sort;
+  } us;
+  float(&dsh)[kMaxC][kAssignRows] = us.d;
   __shared__ float rbest[kAssignRows], rsecond[kAssignRows];
   __shared__ int rlab[kAssignRows];
   __shared__ float wsum[32];
@@ -592,7 +546,11 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
   griddep_wait();
-  griddep_launch();
+  // The next launch (the next iteration's f_hat stream) may start once every
+  // CTA has triggered or exited.  With the iteration close in the last CTA
+  // only that CTA triggers, after its ticket: the stream's CTAs are then
+  // placed on SMs the assign has left, evenly, while the close runs.
+  if (trace != 1) griddep_launch();
   load_cluster_ghat(sh, C, I);
   if (blockIdx.x == 0 && ghat_out)
     for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
@@ -787,72 +745,83 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     }
     __syncthreads();
   }
-  if (w != 0) return;
-  float2 om = make_float2(0.0f, 0.0f);
-  int ch = 0, lmc = 0;
-  if (i < Ni) {
-    const int bj = rlab[lane];
-    const float best = rbest[lane];
-    u[i] = bj;
-    ch = (old_u != bj);
-    if (cord >= 0) {
-      S.lab[cord] = bj;
-      lmc = ch;
+  if (w == 0) {
+    float2 om = make_float2(0.0f, 0.0f);
+    int ch = 0, lmc = 0;
+    if (i < Ni) {
+      const int bj = rlab[lane];
+      const float best = rbest[lane];
+      u[i] = bj;
+      ch = (old_u != bj);
+      if (cord >= 0) {
+        S.lab[cord] = bj;
+        lmc = ch;
+      }
+      if (margin) margin[i] = rsecond[lane] - best;
+      if (dmin) dmin[i] = best;
+      om.x = best;
     }
-    if (margin) margin[i] = rsecond[lane] - best;
-    if (dmin) dmin[i] = best;
-    om.x = best;
-  }
-  om = warp_sum_df(om);
-  ch = warp_sum_i32(ch);
-  lmc = warp_sum_i32(lmc);
-  if (lane == 0) {
-    I.omega_part[blockIdx.x] = om;
-    I.changed_part[blockIdx.x] = ch;
-    if (I.lm_part) I.lm_part[blockIdx.x] = lmc;
+    om = warp_sum_df(om);
+    ch = warp_sum_i32(ch);
+    lmc = warp_sum_i32(lmc);
+    if (lane == 0) {
+      I.omega_part[blockIdx.x] = om;
+      I.changed_part[blockIdx.x] = ch;
+      if (I.lm_part) I.lm_part[blockIdx.x] = lmc;
+    }
   }
   if (trace != 1) return;
-  // The last CTA to finish (atomic ticket, no waiting) closes the iteration:
-  // Omega and the counts in a fixed order, the trace entry, the early-stop
-  // flag and the landmark-change count read by build_supports.
+  // The last CTA to finish (atomic ticket, no waiting) closes the iteration
+  // and prepares the next one: Omega and the counts in a fixed order, the
+  // trace entry, the early-stop flag, the landmark-change count; then, if a
+  // landmark label changed, the support sort (every other CTA has read the
+  // support tables by the time it takes its ticket).
   __threadfence();
-  __syncwarp();
-  if (lane == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
-  __syncwarp();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
   if (!is_last) return;
+  griddep_launch();
   __threadfence();
   float2 o = make_float2(0.0f, 0.0f);
   int c = 0, lm = 0;
   const int G = (int)gridDim.x;
-  for (int b0 = lane; b0 < G; b0 += 32 * 8) {
-    float2 ov[8];
-    int cv[8], lv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int b = b0 + 32 * q;
-      ov[q] = b < G ? __ldcg(I.omega_part + b) : make_float2(0.0f, 0.0f);
-      cv[q] = b < G ? __ldcg(I.changed_part + b) : 0;
-      lv[q] = (b < G && I.lm_part) ? __ldcg(I.lm_part + b) : 0;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      o = df_add(o, ov[q]);
-      c += cv[q];
-      lm += lv[q];
-    }
+  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+    o = df_add(o, __ldcg(I.omega_part + b));
+    c += __ldcg(I.changed_part + b);
+    lm += I.lm_part ? __ldcg(I.lm_part + b) : 0;
   }
   o = warp_sum_df(o);
   c = warp_sum_i32(c);
   lm = warp_sum_i32(lm);
+  __shared__ float2 wo[kAssignWarps];
+  __shared__ int wc[kAssignWarps], wl[kAssignWarps];
   if (lane == 0) {
-    const int t = *I.trace_count;
-    I.trace_omega[t] = (double)o.x + (double)o.y;
-    I.trace_changed[t] = c;
-    *I.trace_count = t + 1;
-    if (early_stop && c == 0) *I.done = 1;
-    if (I.lm_changed) *I.lm_changed = lm;
-    *I.ticket = 0u;
+    wo[w] = o;
+    wc[w] = c;
+    wl[w] = lm;
   }
+  __syncthreads();
+  if (w == 0) {
+    o = lane < nw ? wo[lane] : make_float2(0.0f, 0.0f);
+    c = lane < nw ? wc[lane] : 0;
+    lm = lane < nw ? wl[lane] : 0;
+    o = warp_sum_df(o);
+    c = warp_sum_i32(c);
+    lm = warp_sum_i32(lm);
+    if (lane == 0) {
+      const int t = *I.trace_count;
+      I.trace_omega[t] = (double)o.x + (double)o.y;
+      I.trace_changed[t] = c;
+      *I.trace_count = t + 1;
+      if (early_stop && c == 0) *I.done = 1;
+      *I.ticket = 0u;
+      wl[0] = lm;
+    }
+  }
+  __syncthreads();
+  if (wl[0] == 0) return;  // same landmark labels: same supports
+  sort_supports_cta(S, us.sort.cnt, us.sort.base, us.sort.wtab, us.sort.scan);
 }
 
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,

@@ -62,18 +62,21 @@ static uint64_t fit_bytes(const kkm_problem& p) {
   const int64_t ldk = round_up(Nmax, 32);
   const int64_t units = ceil_div(nL, kUnitRows) + C;
   const int64_t strips = ceil_div(ldk, kStripCols);
-  uint64_t b = 0;
-  b += 4ull * N * d + 4ull * N;                  // input copy, labels
-  b += 4ull * Nmax * dp + 16ull * Nmax;          // X^i, norms, ids, labels
-  b += 4ull * nL * dp + 12ull * nL;              // landmark rows
-  b += 4ull * nL * ldk;                          // the kernel block
+  // one set of kernel-block buffers (two when the fit overlaps the next
+  // block with the current inner loop)
+  uint64_t blk = 4ull * Nmax * dp + 12ull * Nmax;  // X^i, norms, ids
+  blk += 4ull * nL * dp + 12ull * nL;               // landmark rows
+  blk += 4ull * nL * ldk;                           // the kernel block
+  if (p.opt.precision == KKM_BF16) blk += 2ull * (Nmax + nL) * dp + 4ull * (Nmax + nL);
+  if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: split-BF16 planes, rotations, refine plan
+    blk += 24ull * round_up(p.kernel.n_atoms, 64) * (Nmax + nL) + 16ull * nL * ldk + 8ull * nL +
+           4ull * ceil_div(nL, 32) * ceil_div(Nmax, 64);
+  const bool two = fit_overlaps(side_by_side_pipeline(p.opt.pipeline), (int)B, p.kernel.kind, p.opt.precision);
+  uint64_t b = blk * (two ? 2 : 1);
+  b += 4ull * N * d + 4ull * N + 4ull * Nmax;   // input copy, labels out, labels
   b += 4ull * 2 * C * ldk + 8ull * C * dp;       // Eq. 8 / Eq. 12 blocks, medoid rows
   b += 4ull * units * ldk + 8ull * units * strips + 4ull * 6 * ldk;  // inner-loop buffers
   b += 24ull * Nmax;                             // k-means++ scratch
-  if (p.opt.precision == KKM_BF16) b += 2ull * (Nmax + nL) * dp + 4ull * (Nmax + nL);
-  if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: split-BF16 planes, rotations, refine plan
-    b += 24ull * round_up(p.kernel.n_atoms, 64) * (Nmax + nL) + 16ull * nL * ldk + 8ull * nL +
-         4ull * ceil_div(nL, 32) * ceil_div(Nmax, 64);
   b += 4ull * nL * dp + 64ull * nL + 8ull * C * dp;  // the model
   return b + kSlackBytes;
 }
@@ -224,6 +227,7 @@ static kkm_status run_fit(kkm_server* s, Job& J, cudaStream_t st) {
   kkm_problem p = J.fit;
   kkm_options opt = p.opt;
   opt.stream = st;
+  opt.pipeline = side_by_side_pipeline(opt.pipeline);
   kkm_model* m = nullptr;
   const kkm_status r = kkm_fit(p.X, p.N, p.d, p.C, p.B, p.s, &p.kernel, p.iters, p.seed, &opt, p.labels_out,
                                J.keep_model ? &m : nullptr);

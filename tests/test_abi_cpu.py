@@ -121,3 +121,16 @@ def test_model_load_rejects_bad_files_before_device_work(kkm, tmp_path):
     bad.write_bytes(b"KKMMOD01" + struct.pack("<8qd", 3, 16, 0, 0, 24, 20, 3, 5, 1.5))
     assert lib.kkm_model_load(str(bad).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL
     assert not h.value
+
+
+def test_fit_rejects_bad_options_before_any_device_call(kkm):
+    """kkm_fit checks sizes and options before it touches the GPU: an unknown
+    pipeline, sampling or precision gives KKM_EINVAL here, without one."""
+    X = np.zeros((64, 4), np.float32)
+    for kw in (dict(pipeline=3), dict(pipeline=-1), dict(sampling=2), dict(precision=7)):
+        with pytest.raises(kkm.KKMError) as e:
+            kkm.kkm_fit(X, 2, 2, 0.5, "rbf", 1.0, iters=2, labels=False, stream=0, **kw)
+        assert e.value.status == kkm.STATUS_EINVAL, kw
+    with pytest.raises(kkm.KKMError) as e:
+        kkm.kkm_fit(X, 2, 65, 0.5, "rbf", 1.0, iters=2, labels=False, stream=0)   # B > N
+    assert e.value.status == kkm.STATUS_EINVAL

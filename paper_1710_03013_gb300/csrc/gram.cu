@@ -231,46 +231,99 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
 }
 
 // ------------------------------------------------ skinny (<= 32 reference rows)
+// Sum over the warp of NA values per lane (NA a power of two <= 32), as a
+// reduce-scatter: at each of the first log2(NA) xor steps a lane keeps half
+// of its values and adds its partner's copy of them, so NA - 1 + 5 - log2(NA)
+// shuffles replace NA full reductions.  Afterwards lane l holds the warp sum
+// of value (l >> (5 - log2(NA))).
+template <int NA>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NA], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int m = NA; m > 1; m >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < m / 2; ++i) {
+      const float keep = upper ? v[i + m / 2] : v[i];
+      const float send = upper ? v[i] : v[i + m / 2];
+      v[i] = keep + __shfl_xor_sync(kFull, send, o);
+    }
+  }
+  float t = v[0];
+  for (; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+  return t;
+}
+template <int NA>
+__host__ __device__ constexpr int scatter_shift() {
+  return NA >= 32 ? 0 : NA >= 16 ? 1 : NA >= 8 ? 2 : NA >= 4 ? 3 : NA >= 2 ? 4 : 5;
+}
+
+// K(A_a, B_b) for nA <= NA reference rows held in shared memory and many
+// sample rows: one warp takes kSkinnyRows sample rows at a time, each lane
+// keeping kSkinnyLoads 16-byte loads per row in flight (the sample rows are
+// the only HBM traffic), every shared-memory reference value serving all the
+// warp's rows.
+constexpr int kSkinnyRows = 2, kSkinnyLoads = 4;
+
 template <int KIND, int NA>
 __global__ void __launch_bounds__(256)
 gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
                    int dp, const float* __restrict__ normA, const float* __restrict__ normB,
                    const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
                    float neg_scale, float* __restrict__ out, int64_t ldo) {
+  constexpr int R = kSkinnyRows, QB = kSkinnyLoads;
   extern __shared__ float4 As4[];  // [nA][dp/4]
   const int dq = dp >> 2;
   const float4* A4 = reinterpret_cast<const float4*>(A);
   for (int e = threadIdx.x; e < nA * dq; e += blockDim.x) As4[e] = A4[e];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < nB;
-       b += gridDim.x * (blockDim.x >> 5)) {
-  float acc[NA];
+  const int nwarp = blockDim.x >> 5;
+  const int a_mine = lane >> scatter_shift<NA>();
+  const bool writer = (lane & ((1 << scatter_shift<NA>()) - 1)) == 0 && a_mine < nA;
+  for (int b0 = (blockIdx.x * nwarp + (threadIdx.x >> 5)) * R; b0 < nB; b0 += gridDim.x * nwarp * R) {
+    float acc[R][NA];
 #pragma unroll
-  for (int a = 0; a < NA; ++a) acc[a] = 0.0f;
-  const float4* pb = reinterpret_cast<const float4*>(Bm + (int64_t)b * dp);
-  for (int q = lane; q < dq; q += 32) {
-    const float4 x = __ldg(pb + q);
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      if (a < nA) {
-        const float4 y = As4[a * dq + q];
-        acc[a] = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc[a]))));
+      for (int a = 0; a < NA; ++a) acc[r][a] = 0.0f;
+    const float4* pb[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) pb[r] = reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + r, nB - 1) * dp);
+    for (int q0 = 0; q0 < dq; q0 += 32 * QB) {
+      float4 x[R][QB];
+#pragma unroll
+      for (int t = 0; t < QB; ++t) {
+        const int q = q0 + t * 32 + lane;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r][t] = q < dq ? __ldg(pb[r] + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int t = 0; t < QB; ++t) {
+        const int q = q0 + t * 32 + lane;
+        if (q >= dq) break;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          if (a < nA) {
+            const float4 y = As4[a * dq + q];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              acc[r][a] = fmaf(x[r][t].x, y.x, fmaf(x[r][t].y, y.y, fmaf(x[r][t].z, y.z, fmaf(x[r][t].w, y.w, acc[r][a]))));
+          }
+        }
       }
     }
-  }
-  float mine = 0.0f;
 #pragma unroll
-  for (int a = 0; a < NA; ++a) {
-    const float t = warp_sum_f32(acc[a]);
-    if (lane == a) mine = t;
-  }
-  if (lane < nA) {
-    const float na = KIND != DK_LINEAR ? normA[lane] : 0.0f;
-    const float nbv = KIND != DK_LINEAR ? normB[b] : 0.0f;
-    const bool same = idA && idB && idA[lane] == idB[b];
-    out[(int64_t)lane * ldo + b] = gram_epilogue<KIND>(mine, na, nbv, same, neg_scale);
-  }
+    for (int r = 0; r < R; ++r) {
+      const float dot = warp_reduce_scatter<NA>(acc[r], lane);
+      const int b = b0 + r;
+      if (writer && b < nB) {
+        const float na = KIND != DK_LINEAR ? normA[a_mine] : 0.0f;
+        const float nbv = KIND != DK_LINEAR ? normB[b] : 0.0f;
+        const bool same = idA && idB && idA[a_mine] == idB[b];
+        out[(int64_t)a_mine * ldo + b] = gram_epilogue<KIND>(dot, na, nbv, same, neg_scale);
+      }
+    }
   }
 }
 
@@ -283,7 +336,7 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
   if (nA <= 32 && skinny_smem <= 96 * 1024) {
     // every CTA first copies the reference rows to shared memory: few CTAs,
     // many sample rows each (two per SM)
-    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8), 152 * 2);
+    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8 * kSkinnyRows), 152 * 2);
     cudaError_t e;
 #define KKM_SKINNY(NAV)                                                                 \
   e = cudaFuncSetAttribute(gram_skinny_kernel<KIND, NAV>,                               \

@@ -236,6 +236,52 @@ __device__ __forceinline__ void ld16_policy(const __half* p, uint64_t pol, uint4
                : "l"(p), "l"(pol));
 }
 
+// acc[c] += KT[rows[q]][col + c] for q < n (n == D when FULL), loading all
+// rows of the chunk before adding any; rows below keep_rows with the
+// evict_last policy, the rest evict_first.  FP16 storage converts to FP32
+// before the additions.
+template <typename T, int D, bool FULL>
+__device__ __forceinline__ void stream_rows(const T* base, int64_t ldk, const int* rows, int n, int keep_rows,
+                                            uint64_t keep, uint64_t stream, float (&acc)[16 / sizeof(T)]) {
+  if constexpr (sizeof(T) == 4) {
+    float v[D][4];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      if (FULL || q < n) {
+        const int r = rows[q];
+        ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
+      } else {
+        v[q][0] = v[q][1] = v[q][2] = v[q][3] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c] += v[q][c];
+  } else {
+    uint4 v[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      if (FULL || q < n) {
+        const int r = rows[q];
+        ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
+      } else {
+        v[q] = make_uint4(0u, 0u, 0u, 0u);  // +0.0 in FP16
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[c]));
+        acc[2 * c] += f.x;
+        acc[2 * c + 1] += f.y;
+      }
+    }
+  }
+}
+
 // f_hat numerators: partial[u][l] = sum over the landmark rows k of unit u of
 // KT[k][l] (in the unit's row order, FP32), for one strip of kStrip columns
 // per CTA; plus the tile's g_hat numerator (its landmark columns of the same
@@ -244,8 +290,11 @@ __device__ __forceinline__ void ld16_policy(const __half* p, uint64_t pol, uint4
 // iterations), the rest evict_first.  The last CTA of cluster j to finish
 // (atomic ticket, no waiting) forms g_hat_j = (sum of the cluster's
 // numerators) / n_j^2 (Eq. 16) in FP64, in a fixed order.
+// Six CTAs per SM (the whole grid of the MNIST-shaped block resident at
+// once); the occupancy bound also lets the compiler keep a chunk's loads in
+// flight together instead of interleaving them with the additions.
 template <typename T>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 6)
 fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
                     float* __restrict__ partial, float2* __restrict__ gpart, int n_strips,
                     const int32_t* __restrict__ skip, int keep_rows, uint32_t* __restrict__ gtick,
@@ -274,47 +323,28 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   float acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+  // landmark labels of this thread's columns, loaded ahead of the stream (the
+  // g_hat numerator needs them after it); col is a multiple of NC and the
+  // label array has ldk (a multiple of 32) entries
+  int clab[NC];
+#pragma unroll
+  for (int c = 0; c < NC; c += 4) {
+    int4 v = make_int4(-1, -1, -1, -1);
+    if (S.col_label && col < Ni) v = __ldg(reinterpret_cast<const int4*>(S.col_label + col + c));
+    clab[c] = v.x;
+    clab[c + 1] = v.y;
+    clab[c + 2] = v.z;
+    clab[c + 3] = v.w;
+  }
   if (col < Ni) {
     const T* base = KT + col;
-    for (int k = 0; k < nrow; k += DEPTH) {
-      if constexpr (sizeof(T) == 4) {
-        float v[DEPTH][4];
-#pragma unroll
-        for (int q = 0; q < DEPTH; ++q) {
-          if (k + q < nrow) {
-            const int r = rows[k + q];
-            ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
-          } else {
-            v[q][0] = v[q][1] = v[q][2] = v[q][3] = 0.0f;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < DEPTH; ++q)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c] += v[q][c];
-      } else {
-        uint4 v[DEPTH];
-#pragma unroll
-        for (int q = 0; q < DEPTH; ++q) {
-          if (k + q < nrow) {
-            const int r = rows[k + q];
-            ld16_policy(base + (int64_t)r * ldk, r < keep_rows ? keep : stream, v[q]);
-          } else {
-            v[q] = make_uint4(0u, 0u, 0u, 0u);  // +0.0 in FP16
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < DEPTH; ++q) {
-          const uint32_t w[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[c]));
-            acc[2 * c] += f.x;
-            acc[2 * c + 1] += f.y;
-          }
-        }
-      }
-    }
+    // whole chunks of DEPTH rows: all loads issued before any is used, no
+    // predicates between them; then the last partial chunk.  Rows are added
+    // in the unit's order either way.
+    int k = 0;
+    for (; k + DEPTH <= nrow; k += DEPTH)
+      stream_rows<T, DEPTH, true>(base, ldk, rows + k, DEPTH, keep_rows, keep, stream, acc);
+    if (k < nrow) stream_rows<T, DEPTH, false>(base, ldk, rows + k, nrow - k, keep_rows, keep, stream, acc);
     float* out = partial + (int64_t)unit * ldk + col;
 #pragma unroll
     for (int c = 0; c < NC; c += 4)
@@ -329,7 +359,7 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   if (col < Ni) {
 #pragma unroll
     for (int c = 0; c < NC; ++c)
-      if (col + c < Ni && __ldg(S.col_label + col + c) == j) g = df_add(g, make_float2(acc[c], 0.0f));
+      if (col + c < Ni && clab[c] == j) g = df_add(g, make_float2(acc[c], 0.0f));
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -545,28 +575,26 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     sh.su[j] = S.seg_unit[j];
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
+  __syncthreads();
   griddep_wait();
   // The next launch (the next iteration's f_hat stream) may start once every
   // CTA has triggered or exited.  With the iteration close in the last CTA
   // only that CTA triggers, after its ticket: the stream's CTAs are then
   // placed on SMs the assign has left, evenly, while the close runs.
   if (trace != 1) griddep_launch();
-  load_cluster_ghat(sh, C, I);
-  if (blockIdx.x == 0 && ghat_out)
-    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
-  // d_ij of cluster j from the unit sum f (the units of j added in order)
+  // g_hat (given for an assign against a model, else formed by the f_hat
+  // stream) is loaded here and used after the partial sums, so that both
+  // loads are in flight together (C <= blockDim.x)
+  const double gval = threadIdx.x < C ? (I.ghat_in ? I.ghat_in : I.ghat_cur)[threadIdx.x] : 0.0;
+  // f_hat_ij of cluster j from its unit sum f (the units of j added in
+  // order); NaN for an empty cluster
   auto finish = [&](int j, float f) {
-    float dj = inf;
+    float fh = __int_as_float(0x7fc00000);
     if (i < Ni) {
-      if (sh.nj[j] > 0) {
-        const float fh = f / (float)sh.nj[j];
-        if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
-        dj = ks - 2.0f * fh + sh.ghf[j];
-      } else if (fhat_out) {
-        fhat_out[(int64_t)i * C + j] = __int_as_float(0x7fc00000);
-      }
+      if (sh.nj[j] > 0) fh = f / (float)sh.nj[j];
+      if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
     }
-    dsh[j][lane] = dj;
+    dsh[j][lane] = fh;
   };
   // Warp w takes the contiguous clusters [jb, je), whose units are contiguous
   // too: one flat pass over them keeps 8 loads in flight across cluster
@@ -598,6 +626,19 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       finish(j, f);
       f = 0.0f;
     }
+  }
+  if (threadIdx.x < C) {
+    sh.gh[threadIdx.x] = sh.nj[threadIdx.x] > 0 ? gval : __longlong_as_double(0x7ff8000000000000LL);
+    sh.ghf[threadIdx.x] = (float)sh.gh[threadIdx.x];
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
+  // d_ij = K_ii - 2 f_hat_ij + g_hat_j for the warp's clusters (+inf when
+  // n_j = 0 or past the last row)
+  for (int j = jb; j < je; ++j) {
+    const float fh = dsh[j][lane];
+    dsh[j][lane] = (i < Ni && sh.nj[j] > 0) ? ks - 2.0f * fh + sh.ghf[j] : inf;
   }
   __syncthreads();
   if (w == 0) {

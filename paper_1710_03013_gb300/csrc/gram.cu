@@ -36,23 +36,54 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int64_t d, int64
   if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
-// Same with 16-byte vectors (d a multiple of 4 and X 16-byte aligned).
+// One row with 16-byte vectors: d4 source vectors, zero padded to dp4; each
+// lane issues up to 8 loads before its first store, and accumulates the
+// squared norm of its vectors in column order (double-float), then the warp
+// adds the lanes in a fixed order.
+__device__ __forceinline__ void copy_row4(const float4* __restrict__ src, int64_t d4, float4* __restrict__ dst,
+                                          int dp4, int lane, float* normsq) {
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (int c0 = 0; c0 < dp4; c0 += 32 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = c0 + t * 32 + lane;
+      v[t] = c < d4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = c0 + t * 32 + lane;
+      if (c < dp4) {
+        dst[c] = v[t];
+        acc = df_add_sq(df_add_sq(df_add_sq(df_add_sq(acc, v[t].x), v[t].y), v[t].z), v[t].w);
+      }
+    }
+  }
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) *normsq = df_to_float(acc);
+}
+
+// Rows start + l*step with 16-byte vectors (d a multiple of 4, X 16-byte
+// aligned): one warp per row.
 __global__ void gather_rows4_kernel(const float4* __restrict__ X, int64_t d4, int64_t start,
                                     int64_t step, int64_t n, float4* __restrict__ out, int dp4,
                                     float* __restrict__ normsq) {
   const int lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row >= n) return;
-  const float4* src = X + (start + row * step) * d4;
-  float4* dst = out + row * (int64_t)dp4;
-  float2 acc = make_float2(0.0f, 0.0f);
-  for (int c = lane; c < dp4; c += 32) {
-    const float4 v = c < d4 ? __ldg(src + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-    dst[c] = v;
-    acc = df_add_sq(df_add_sq(df_add_sq(df_add_sq(acc, v.x), v.y), v.z), v.w);
-  }
-  acc = warp_sum_df(acc);
-  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
+  copy_row4(X + (start + row * step) * d4, d4, out + row * (int64_t)dp4, dp4, lane, normsq ? normsq + row : nullptr);
+}
+
+// Rows X[idx[l]] with 16-byte vectors (row pitch and length multiples of 4,
+// X 16-byte aligned): one warp per row.
+template <typename IDX>
+__global__ void gather_idx4_kernel(const float4* __restrict__ X, int64_t ld4, int64_t d4,
+                                   const IDX* __restrict__ idx, int64_t n, float4* __restrict__ out, int dp4,
+                                   float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  copy_row4(X + (int64_t)idx[row] * ld4, d4, out + row * (int64_t)dp4, dp4, lane, normsq ? normsq + row : nullptr);
 }
 
 template <typename IDX>
@@ -75,6 +106,8 @@ __global__ void gather_idx_kernel(const float* __restrict__ X, int64_t ld_in, in
   if (normsq && lane == 0) normsq[row] = df_to_float(acc);
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step, int64_t n,
                                float* out, int dp, float* normsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -91,14 +124,23 @@ cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t
 cudaError_t launch_gather_idx64(const float* X, int64_t d, const int64_t* idx, int64_t n,
                                 float* out, int dp, float* normsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  gather_idx_kernel<int64_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, d, idx, n, out, dp, normsq);
+  if (d % 4 == 0 && dp % 4 == 0 && aligned16(X) && aligned16(out))
+    gather_idx4_kernel<int64_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(
+        reinterpret_cast<const float4*>(X), d / 4, d / 4, idx, n, reinterpret_cast<float4*>(out), dp / 4, normsq);
+  else
+    gather_idx_kernel<int64_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(X, d, d, idx, n, out, dp, normsq);
   return cudaGetLastError();
 }
 cudaError_t launch_gather_idx32(const float* Xp, int dp_in, const int32_t* idx, int64_t n,
                                 float* out, int dp, float* normsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  gather_idx_kernel<int32_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(Xp, dp_in, dp_in, idx, n, out, dp,
-                                                                    normsq);
+  if (dp_in % 4 == 0 && dp % 4 == 0 && aligned16(Xp) && aligned16(out))
+    gather_idx4_kernel<int32_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(
+        reinterpret_cast<const float4*>(Xp), dp_in / 4, dp_in / 4, idx, n, reinterpret_cast<float4*>(out), dp / 4,
+        normsq);
+  else
+    gather_idx_kernel<int32_t><<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(Xp, dp_in, dp_in, idx, n, out, dp,
+                                                                      normsq);
   return cudaGetLastError();
 }
 

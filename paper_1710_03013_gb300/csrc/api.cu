@@ -491,7 +491,10 @@ struct LoopBuffers {
   int max_units = 0;
 };
 
-static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int trace_cap, LoopBuffers* lb) {
+// gaussian: the kernel's values lie in [0, 1], so the g_hat numerators are
+// accumulated in fixed point (IterState::gfix); else per-cluster tickets.
+static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int trace_cap, LoopBuffers* lb,
+                             bool gaussian = false) {
   Supports& S = lb->S;
   IterState& I = lb->I;
   const int mu = max_units_for(nLmax, C);
@@ -521,6 +524,11 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.gtick, C));
   KKM_CK(cudaMemsetAsync(I.gtick, 0, (size_t)C * 4, ws.st));
+  if (gaussian) {
+    KKM_TRY(ws.alloc(&I.gfix, C));
+    KKM_CK(cudaMemsetAsync(I.gfix, 0, (size_t)C * 8, ws.st));
+    I.gfix_shift = gfix_shift_for(nLmax);
+  }
   KKM_TRY(ws.alloc(&I.ticket, 1));
   KKM_TRY(ws.alloc(&I.done, 1));
   KKM_TRY(ws.alloc(&I.trace_omega, std::max(trace_cap, 1)));
@@ -835,7 +843,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
   }
   LoopBuffers lb;
-  KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb));
+  KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb, sp.gaussian()));
   Supports& S = lb.S;
   IterState& I = lb.I;
   if (do_kpp) {
@@ -936,6 +944,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("landmark_maps", ms, launch_landmark_maps(S, u, ms));
     KKM_RUN("build_supports", ms, launch_build_supports(S, ms));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, ms));
+    if (I.gfix) KKM_CK(cudaMemsetAsync(I.gfix, 0, (size_t)C * 8, ms));  // the last mini-batch's medoid step read them
     const bool rescore = sp.precision != KKM_FP32;
     I.keep_rows = l2_keep_rows(ldk, nL, kL2KeepShare, kt_half ? 2 : 4);
     I.flag_tau = rescore ? (fp32_half_block ? kRescoreMarginHalf : kRescoreMargin) : 0.0f;
@@ -1300,7 +1309,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
   KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux, gid, Ni, KT, ldk, st));
   LoopBuffers lb;
-  KKM_TRY(alloc_loop(ws, nL, C, ldk, 1, &lb));
+  KKM_TRY(alloc_loop(ws, nL, C, ldk, 1, &lb, sp.gaussian()));
   lb.S.L = Ld;
   lb.S.nL = nL;
   KKM_RUN("fill", st, launch_fill_i32(lb.S.col_label, -1, ldk, st));

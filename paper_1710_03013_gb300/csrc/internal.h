@@ -7,6 +7,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -232,6 +233,13 @@ struct Supports {
   int max_units;
 };
 inline int max_units_for(int nL, int C) { return (int)(ceil_div(nL, kUnitRows) + C); }
+// Fixed-point scale of the Gaussian g_hat numerators for up to nL landmarks:
+// a numerator is at most n_j^2 <= nL^2, kept below 2^61 after scaling.
+inline int gfix_shift_for(int64_t nL) {
+  int b = 0;
+  while (b < 40 && ((int64_t)1 << b) <= nL) ++b;  // nL < 2^b
+  return std::max(8, std::min(40, 61 - 2 * b));
+}
 
 struct IterState {
   float* partial;        // [max_units][ldk]
@@ -251,6 +259,12 @@ struct IterState {
   int32_t* ticket_sink = nullptr;   // [1] write target that keeps L2-demotion loads alive
   double* ghat_cur = nullptr;       // [C] g_hat of the current supports (written by fhat_partial)
   uint32_t* gtick = nullptr;        // [C] per-cluster tile tickets of fhat_partial, zero between launches
+  // Gaussian kernels (values in [0, 1]): the g_hat numerators as fixed-point
+  // integers (value * 2^gfix_shift), one integer atomic per stream CTA, so
+  // the sum is exact and order-free; the assign divides by n_j^2 and its
+  // last CTA zeroes them for the next stream.  NULL: tickets and ghat_cur.
+  unsigned long long* gfix = nullptr;  // [C]
+  int gfix_shift = 0;
   int keep_rows = 0;                // block rows kept in L2 across iterations (evict_last)
   int assign_grid;
   int n_strips;

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kStreamThreads, 8)
 fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
                     float* __restrict__ partial, float2* __restrict__ gpart, int n_strips,
                     const int32_t* __restrict__ skip, int keep_rows, uint32_t* __restrict__ gtick,
-                    double* __restrict__ ghat) {
+                    double* __restrict__ ghat, unsigned long long* __restrict__ gfix, double gfix_scale) {
   using Cfg = StreamCfg<T>;
   constexpr int NC = Cfg::kCols, DEPTH = Cfg::kDepth;
   __shared__ int rows[kUnitRows];
@@ -372,9 +372,14 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   if (threadIdx.x == 0) {
     float2 t = red[0];
     for (int q = 1; q < kStreamThreads / 32; ++q) t = df_add(t, red[q]);
-    gpart[(int64_t)unit * n_strips + blockIdx.x] = t;
     last = 0;
-    if (gtick) {
+    if (gfix) {
+      // non-negative (Gaussian kernel values); the scale is a power of two
+      atomicAdd(gfix + j, (unsigned long long)llrint(((double)t.x + (double)t.y) * gfix_scale));
+    } else {
+      gpart[(int64_t)unit * n_strips + blockIdx.x] = t;
+    }
+    if (gtick && !gfix) {
       __threadfence();
       const uint32_t expect = (uint32_t)(S.seg_unit[j + 1] - S.seg_unit[j]) * gridDim.x;
       last = atomicAdd(gtick + j, 1u) + 1u == expect;
@@ -405,7 +410,8 @@ static cudaError_t launch_fhat_t(const T* KT, int64_t ldk, int Ni, const Support
   dim3 grid((unsigned)n_strips, (unsigned)S.max_units);
   return launch_pdl(fhat_partial_kernel<T>, grid, dim3(kStreamThreads), 0, st, KT, ldk, Ni, S, I.partial,
                     I.gpart, n_strips, (const int32_t*)I.done, I.keep_rows,
-                    S.col_label ? I.gtick : (uint32_t*)nullptr, I.ghat_cur);
+                    S.col_label ? I.gtick : (uint32_t*)nullptr, I.ghat_cur,
+                    S.col_label ? I.gfix : (unsigned long long*)nullptr, ldexp(1.0, I.gfix_shift));
 }
 cudaError_t launch_fhat_partial(const float* KT, int64_t ldk, int Ni, const Supports& S,
                                 const IterState& I, cudaStream_t st) {
@@ -466,33 +472,28 @@ struct AssignShared {
   int su[kMaxC + 1];
 };
 
+// g_hat_j (Eq. 16) of a non-empty cluster: given (an assign against a model),
+// from the fixed-point numerator, or as formed by the f_hat stream.
+__device__ __forceinline__ double cluster_ghat(const IterState& I, int j, int n) {
+  if (I.ghat_in) return I.ghat_in[j];
+  if (I.gfix) return (double)I.gfix[j] * ldexp(1.0, -I.gfix_shift) / ((double)n * (double)n);
+  return I.ghat_cur[j];
+}
+
 // n_j, unit ranges and g_hat into shared memory (g_hat given for an assign
 // against a model, else formed by fhat_partial for this iteration; NaN for an
 // empty cluster).
 __device__ __forceinline__ void load_cluster_stats(AssignShared& sh, const Supports& S,
                                                    const IterState& I) {
   const int C = S.C;
-  const double* g = I.ghat_in ? I.ghat_in : I.ghat_cur;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     const int n = S.n_j[j];
     sh.nj[j] = n;
     sh.su[j] = S.seg_unit[j];
-    sh.gh[j] = n > 0 ? g[j] : __longlong_as_double(0x7ff8000000000000LL);
+    sh.gh[j] = n > 0 ? cluster_ghat(I, j, n) : __longlong_as_double(0x7ff8000000000000LL);
     sh.ghf[j] = (float)sh.gh[j];
   }
   if (threadIdx.x == 0) sh.su[C] = S.seg_unit[C];
-  __syncthreads();
-}
-
-// g_hat into shared memory after n_j (given, or formed by fhat_partial for
-// this iteration; NaN for an empty cluster).
-__device__ __forceinline__ void load_cluster_ghat(AssignShared& sh, int C, const IterState& I) {
-  __syncthreads();  // n_j written
-  const double* g = I.ghat_in ? I.ghat_in : I.ghat_cur;
-  for (int j = threadIdx.x; j < C; j += blockDim.x) {
-    sh.gh[j] = sh.nj[j] > 0 ? g[j] : __longlong_as_double(0x7ff8000000000000LL);
-    sh.ghf[j] = (float)sh.gh[j];
-  }
   __syncthreads();
 }
 
@@ -587,7 +588,8 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   // g_hat (given for an assign against a model, else formed by the f_hat
   // stream) is loaded here and used after the partial sums, so that both
   // loads are in flight together (C <= blockDim.x)
-  const double gval = threadIdx.x < C ? (I.ghat_in ? I.ghat_in : I.ghat_cur)[threadIdx.x] : 0.0;
+  const double gval =
+      threadIdx.x < C && sh.nj[threadIdx.x] > 0 ? cluster_ghat(I, threadIdx.x, sh.nj[threadIdx.x]) : 0.0;
   // f_hat_ij of cluster j from its unit sum f (the units of j added in
   // order); NaN for an empty cluster
   auto finish = [&](int j, float f) {
@@ -862,6 +864,10 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       wl[0] = lm;
     }
   }
+  // every CTA has read the fixed-point numerators: zero them for the next
+  // stream
+  if (I.gfix)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) I.gfix[j] = 0ull;
   __syncthreads();
   if (wl[0] == 0) return;  // same landmark labels: same supports
   sort_supports_cta(S, us.sort.cnt, us.sort.base, us.sort.wtab, us.sort.scan);

@@ -177,11 +177,14 @@ __global__ void __launch_bounds__(256, 2)
 gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
                   int dp, const float* __restrict__ normA, const float* __restrict__ normB,
                   const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
-                  float neg_scale, OutT* __restrict__ out, int64_t ldo, int vec_ok) {
+                  float neg_scale, OutT* __restrict__ out, int64_t ldo, int vec_ok, int upper_only) {
   __shared__ __align__(16) float As[2][TB_K][TB_M];
   __shared__ __align__(16) float Bs[2][TB_K][TB_N];
   const int tid = threadIdx.x;
   const int a0 = blockIdx.y * TB_M, b0 = blockIdx.x * TB_N;
+  // only the strict upper triangle (b > a) is wanted: tiles wholly at or
+  // below the diagonal are skipped (their outputs are left unwritten)
+  if (upper_only && b0 + TB_N - 1 <= a0) return;
   const int lr = tid >> 1, lk = (tid & 1) << 2;
   // Rows past the end re-read the last valid row; their outputs are dropped.
   const float* pa = A + (int64_t)min(a0 + lr, nA - 1) * dp + lk;
@@ -396,7 +399,17 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
   gram_tiled_kernel<KIND, float><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                       neg_scale, out, ldo, vec_ok);
+                                                       neg_scale, out, ldo, vec_ok, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const float* normA, const int64_t* idA,
+                                   float* out, int64_t ldo, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M));
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+  gram_tiled_kernel<DK_DIST, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, idA, idA, 0.0f,
+                                                          out, ldo, vec_ok, 1);
   return cudaGetLastError();
 }
 
@@ -407,7 +420,7 @@ cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, in
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
   gram_tiled_kernel<DK_RBF, __half><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                          neg_scale, out, ldo, vec_ok);
+                                                          neg_scale, out, ldo, vec_ok, 0);
   return cudaGetLastError();
 }
 

@@ -144,6 +144,11 @@ cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream
 // kind: DK_RBF (neg_scale = -log2(e)/(2 sigma^2)), DK_LINEAR, DK_DIST (sqrt of
 // squared distance).  idA/idB (nullable) are sample ids: equal ids give K = 1
 // exactly for RBF and 0 for DIST.
+// Euclidean distances of the rows of A among themselves, only the entries
+// above the diagonal (out[a*ldo + b], b > a, written; the tiles wholly at or
+// below it are skipped).
+cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const float* normA, const int64_t* idA,
+                                   float* out, int64_t ldo, cudaStream_t st);
 cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB,
                         int dp, const float* normA, const float* normB, const int64_t* idA,
                         const int64_t* idB, float neg_scale, float* out, int64_t ldo,

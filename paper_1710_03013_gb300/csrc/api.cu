@@ -477,8 +477,11 @@ static kkm_status median_bandwidth_dev(const KernelSpec& sp, const float* X, int
   KKM_TRY(prep_ids(sp, X, ids, M, P, aux, st));
   if (sp.kind == KKM_RMSD)
     KKM_TRY(kernel_block(sp, P, aux, ids, M, P, aux, ids, M, D, ld, st, /*dist=*/true));
-  else  // the select reads the strict upper triangle only
-    KKM_RUN("gram", st, launch_gram_dist_upper(P, M, sp.dp, aux, ids, D, ld, st));
+  else {  // the select reads the strict upper triangle only
+    float* part = nullptr;
+    if (sp.dp >= kDistSplitMinDp) KKM_TRY(ws.alloc(&part, (int64_t)kDistSplit * M * ld));
+    KKM_RUN("gram", st, launch_gram_dist_upper(P, M, sp.dp, aux, ids, D, ld, part, st));
+  }
   const int64_t pairs = M * (M - 1) / 2;
   KKM_RUN("median_select", st, launch_select_upper(D, (int)M, ld, (pairs - 1) / 2, scratch, out, st));
   float sig = 0.0f;

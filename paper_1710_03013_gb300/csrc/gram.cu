@@ -162,7 +162,7 @@ cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream
 template <int KIND>
 __device__ __forceinline__ float gram_epilogue(float dot, float na, float nb, bool same,
                                                float neg_scale) {
-  if (KIND == DK_LINEAR) return dot;
+  if (KIND == DK_LINEAR || KIND == DK_RAW) return dot;
   float d2 = fmaxf(na + nb - 2.0f * dot, 0.0f);
   if (KIND == DK_DIST) return same ? 0.0f : sqrtf(d2);
   return same ? 1.0f : exp2f(d2 * neg_scale);
@@ -185,10 +185,16 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
   // only the strict upper triangle (b > a) is wanted: tiles wholly at or
   // below the diagonal are skipped (their outputs are left unwritten)
   if (upper_only && b0 + TB_N - 1 <= a0) return;
+  // split K (DK_RAW): slice z of gridDim.z takes its share of the k-tiles and
+  // stores raw products in out + z * nA * ldo
+  const int nk_all = dp / TB_K;
+  const int kt0 = (int)((int64_t)nk_all * blockIdx.z / gridDim.z);
+  const int nk = (int)((int64_t)nk_all * (blockIdx.z + 1) / gridDim.z) - kt0;
+  if (KIND == DK_RAW) out += (int64_t)blockIdx.z * nA * ldo;
   const int lr = tid >> 1, lk = (tid & 1) << 2;
   // Rows past the end re-read the last valid row; their outputs are dropped.
-  const float* pa = A + (int64_t)min(a0 + lr, nA - 1) * dp + lk;
-  const float* pb = Bm + (int64_t)min(b0 + lr, nB - 1) * dp + lk;
+  const float* pa = A + (int64_t)min(a0 + lr, nA - 1) * dp + lk + kt0 * TB_K;
+  const float* pb = Bm + (int64_t)min(b0 + lr, nB - 1) * dp + lk + kt0 * TB_K;
   float4 ga = __ldg(reinterpret_cast<const float4*>(pa));
   float4 gb = __ldg(reinterpret_cast<const float4*>(pb));
   As[0][lk + 0][lr] = ga.x; As[0][lk + 1][lr] = ga.y; As[0][lk + 2][lr] = ga.z; As[0][lk + 3][lr] = ga.w;
@@ -202,7 +208,6 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 
-  const int nk = dp / TB_K;
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
     if (kt + 1 < nk) {
@@ -403,13 +408,41 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
   return cudaGetLastError();
 }
 
+// dist[a][b] = sqrt(max(|x_a|^2 + |x_b|^2 - 2 sum_z part[z][a][b], 0)) for
+// b > a (the slices added in order), 0 for equal ids.
+__global__ void dist_from_parts_kernel(const float* __restrict__ part, int nsplit, int n, int64_t ldo,
+                                       const float* __restrict__ norm, const int64_t* __restrict__ ids,
+                                       float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n * n) return;
+  const int a = (int)(e / n), b = (int)(e % n);
+  if (b <= a) return;
+  const int64_t o = (int64_t)a * ldo + b;
+  float dot = 0.0f;
+  for (int z = 0; z < nsplit; ++z) dot += part[(int64_t)z * n * ldo + o];
+  out[o] = gram_epilogue<DK_DIST>(dot, norm[a], norm[b], ids && ids[a] == ids[b], 0.0f);
+}
+
 cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const float* normA, const int64_t* idA,
-                                   float* out, int64_t ldo, cudaStream_t st) {
+                                   float* out, int64_t ldo, float* scratch, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M));
-  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  gram_tiled_kernel<DK_DIST, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, idA, idA, 0.0f,
-                                                          out, ldo, vec_ok, 1);
+  if (dp < kDistSplitMinDp) {
+    dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M));
+    const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+    gram_tiled_kernel<DK_DIST, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, idA, idA, 0.0f,
+                                                            out, ldo, vec_ok, 1);
+    return cudaGetLastError();
+  }
+  // a few hundred tiles at most: K is split kDistSplit ways so that every SM
+  // has work, the raw products go to scratch and a second pass adds them
+  dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M), kDistSplit);
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(scratch) & 15) == 0);
+  gram_tiled_kernel<DK_RAW, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, nullptr, nullptr,
+                                                         0.0f, scratch, ldo, vec_ok, 1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dist_from_parts_kernel<<<(unsigned)ceil_div(n * n, 256), 256, 0, st>>>(scratch, kDistSplit, (int)n, ldo, normA,
+                                                                         idA, out);
   return cudaGetLastError();
 }
 

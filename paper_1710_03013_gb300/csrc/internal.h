@@ -123,7 +123,7 @@ inline bool fit_overlaps(int pipeline, int B, int kind, int precision) {
 inline int side_by_side_pipeline(int pipeline) { return pipeline == KKM_PIPE_AUTO ? KKM_PIPE_SERIAL : pipeline; }
 
 // Kernel-function codes used on the device.
-enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3 };
+enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3, DK_RAW = 4 /* plain products */ };
 
 // --------------------------------------------------------- kernel launchers
 // (all asynchronous on `st`; they return a CUDA error code of the launch)
@@ -146,9 +146,13 @@ cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream
 // exactly for RBF and 0 for DIST.
 // Euclidean distances of the rows of A among themselves, only the entries
 // above the diagonal (out[a*ldo + b], b > a, written; the tiles wholly at or
-// below it are skipped).
+// below it are skipped).  Rows of at least kDistSplitMinDp floats split K
+// kDistSplit ways (scratch: kDistSplit * n * ldo floats of partial products;
+// NULL for shorter rows).
+constexpr int kDistSplit = 4;
+constexpr int kDistSplitMinDp = 256;
 cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const float* normA, const int64_t* idA,
-                                   float* out, int64_t ldo, cudaStream_t st);
+                                   float* out, int64_t ldo, float* scratch, cudaStream_t st);
 cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, int64_t nB,
                         int dp, const float* normA, const float* normB, const int64_t* idA,
                         const int64_t* idB, float neg_scale, float* out, int64_t ldo,

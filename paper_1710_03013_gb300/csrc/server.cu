@@ -78,6 +78,11 @@ static uint64_t fit_bytes(const kkm_problem& p) {
   b += 4ull * units * ldk + 8ull * units * strips + 4ull * 6 * ldk;  // inner-loop buffers
   b += 24ull * Nmax;                             // k-means++ scratch
   b += 4ull * nL * dp + 64ull * nL + 8ull * C * dp;  // the model
+  if (!(p.kernel.sigma > 0.0f)) {  // the median rule's sample, distances and split-K products
+    const int64_t M = std::min<int64_t>(N, 2048);
+    const bool split = p.kernel.kind != KKM_RMSD && dp >= kDistSplitMinDp;
+    b += 4ull * M * dp + 4ull * M * round_up(M, 4) * (split ? 1 + kDistSplit : 1);
+  }
   return b + kSlackBytes;
 }
 

@@ -84,11 +84,15 @@ def test_rmsd_self_and_rigid_motion(lib):
     assert np.max(np.abs(k_xx - k_xy)) <= KERNEL_ABS
 
 
-@pytest.mark.parametrize("kind", ["rbf", "rmsd"])
+@pytest.mark.parametrize("kind", ["rbf", "rbf_long", "rbf_long_small", "rmsd"])
 def test_median_bandwidth(lib, kind):
-    if kind == "rbf":
-        X, _ = blobs(3000, 16, 5, workload=0)
+    """The median rule on 2,048 drawn samples; long rows (>= 256 floats) take
+    the split-K distance path, a ragged sample count the partial tiles."""
+    if kind.startswith("rbf"):
+        N, d = {"rbf": (3000, 16), "rbf_long": (2600, 300), "rbf_long_small": (1500, 257)}[kind]
+        X, _ = blobs(N, d, 5, workload=0, problem=d)
         k = O.Kernel(O.KIND_RBF, 0.0)
+        kind = "rbf"
     else:
         F, _ = md_trajectory(n_frames=900, n_atoms=40, n_states=3, dwell=100.0, workload=53)
         X = F.reshape(len(F), -1)

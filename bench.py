@@ -24,6 +24,7 @@ method) on a bounded sample of the same workload per step.
 """
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -100,15 +101,20 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+    """nvidia-smi clock/throttle samples, kept for the timed region only.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler is started before the warm-up (its start-up is not inside the
+    timed region) and the region is bracketed with begin()/end(); samples are
+    matched to it by their timestamps."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
+        self.t0 = self.t1 = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
@@ -121,6 +127,14 @@ class ClockSampler:
         except OSError:
             self.proc = None
         return self
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
+        if self.proc:
+            time.sleep(0.15)  # one more sample period, so the region's last sample is written
 
     def __exit__(self, *a):
         if self.proc:
@@ -135,8 +149,23 @@ class ClockSampler:
         with open(self.path) as f:
             for line in f:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    continue
+                rows.append((ts, parts[1:]))
+        window = "timed region"
+        if self.t0 and self.t1:
+            lo = self.t0 - datetime.timedelta(seconds=0.1)
+            hi = self.t1 + datetime.timedelta(seconds=0.1)
+            inside = [r for r in rows if lo <= r[0] <= hi]
+            if inside:
+                rows = inside
+            else:
+                window = "whole run (no sample matched the region's timestamps)"
+        rows = [r for _, r in rows]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -144,7 +173,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "window": window}
 
 
 def source_hash(files):
@@ -262,6 +291,7 @@ def run_ours(args, cfg, X):
         return kkm.kkm_fit(Xd, C, B, s, kind, sig, atoms, iters=iters, seed=seed, early_stop=False, precision=prec,
                            pipeline=pipeline)
 
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         lab, model = step(HEAD)
         if CMP is not None:
@@ -285,8 +315,10 @@ def run_ours(args, cfg, X):
         return e0.elapsed_time(e1) / n, out
 
     # timed region 1: the headline value (no instrumentation)
-    with ClockSampler(local) as clk:
-        ms, (lab, model) = timed(HEAD, args.steps)
+    clk.begin()
+    ms, (lab, model) = timed(HEAD, args.steps)
+    clk.end()
+    clk.__exit__()
     ms32, agree, omega_rel = None, None, None
     if CMP is not None:
         # the plain FP32 path on the same workload, for comparison
@@ -536,7 +568,10 @@ def run_batched(args, cfg):
         return e0.elapsed_time(e1) / n, out
 
     with ClockSampler(local) as clk:
+        time.sleep(0.3)  # the sampler's start-up before the region
+        clk.begin()
         ms, res = timed(HEAD, args.steps)
+        clk.end()
     ms32, res32 = timed(CMP, args.steps)
     lab = torch.cat([r[0] for r in res])
     lab32 = torch.cat([r[0] for r in res32])
@@ -754,7 +789,10 @@ def run_serving(args, cfg):
     play(float(args.warmup))
     srv.reset_stats()
     with ClockSampler(local) as clk:
+        time.sleep(0.3)  # the sampler's start-up before the stream
+        clk.begin()
         wall, n_req, h2d, bad = play(float(args.steps))
+        clk.end()
     st = srv.stats()
     # instrumented pass: every library launch counted
     kkm.prof_reset()

@@ -75,7 +75,18 @@ static cudaEvent_t take_event() {
   return e;
 }
 
+// the name of the innermost profiled launch of this thread
+static thread_local const char* t_prof_scope = nullptr;
+
+void prof_more_launches(int k) {
+  if (!g_prof_on || !t_prof_scope || k <= 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof[t_prof_scope].launches += k;
+}
+
 ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s) {
+  prev_scope = t_prof_scope;
+  t_prof_scope = n;
   if (!g_prof_on) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (g_prof_on == 2 && !heavy_kernel(name)) {
@@ -89,6 +100,7 @@ ProfScope::ProfScope(const char* n, cudaStream_t s) : name(n), stream(s) {
 // The pair is queued only once both events are recorded, so a concurrent
 // prof_collect (another thread's call) never sees a half-recorded pair.
 ProfScope::~ProfScope() {
+  t_prof_scope = prev_scope;
   if (!a) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEventRecord(b, stream);

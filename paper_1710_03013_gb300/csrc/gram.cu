@@ -443,6 +443,7 @@ cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const floa
   if (e != cudaSuccess) return e;
   dist_from_parts_kernel<<<(unsigned)ceil_div(n * n, 256), 256, 0, st>>>(scratch, kDistSplit, (int)n, ldo, normA,
                                                                          idA, out);
+  prof_more_launches(1);
   return cudaGetLastError();
 }
 

@@ -84,6 +84,7 @@ struct ProfScope {
   const char* name;
   cudaEvent_t a = nullptr, b = nullptr;  // null: not timed
   cudaStream_t stream;
+  const char* prev_scope = nullptr;
 };
 void prof_collect();  // after a stream sync: fold finished events into totals
 
@@ -95,6 +96,9 @@ struct NvtxRange {
 };
 bool prof_on();
 void prof_add_work(const char* name, double units);  // data-dependent work of a kernel
+// A launcher that starts k kernels beyond its first reports them here; they
+// are counted under the enclosing profiled launch (launch counts are kernels).
+void prof_more_launches(int k);
 
 // Launch check after every kernel launch.
 #define KKM_LAUNCH_CK() KKM_CK(cudaGetLastError())

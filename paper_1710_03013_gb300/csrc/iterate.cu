@@ -1173,6 +1173,7 @@ cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double
   const int nb = (int)ceil_div(N0, kKppThreads);
   kpp_update_kernel<<<nb, kKppThreads, 0, st>>>(Kc, N0, kself, D2, P, bsum, picks, r);
   kpp_pick_kernel<<<1, kKppThreads, 0, st>>>(D2, P, bsum, nb, N0, picks, draws, r);
+  prof_more_launches(1);
   return cudaGetLastError();
 }
 
@@ -1197,6 +1198,7 @@ cudaError_t launch_sum_f32_to_f64(const float* v, int64_t n, double* part, int p
                                   cudaStream_t st) {
   sum_partial_kernel<<<parts, 256, 0, st>>>(v, n, part);
   sum_final_kernel<<<1, 256, 0, st>>>(part, parts, out);
+  prof_more_launches(1);
   return cudaGetLastError();
 }
 

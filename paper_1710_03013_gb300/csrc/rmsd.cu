@@ -192,6 +192,7 @@ cudaError_t launch_rmsd_refine_plan(const float* est, int64_t ldo, int nA, int n
     rmsd_rank_kernel<false><<<(unsigned)ceil_div(nA, 256), 256, 0, st>>>(key, nA, order);
   rmsd_tile_flag_kernel<<<dim3((unsigned)ceil_div(nB, 64), (unsigned)ceil_div(nA, 32)), 256, 0, st>>>(est, ldo, nA, nB,
                                                                                                    order, flag);
+  prof_more_launches(2);
   return cudaGetLastError();
 }
 

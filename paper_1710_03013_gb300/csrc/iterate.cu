@@ -13,8 +13,9 @@
 //                 rows of one unit over a strip of columns (16-byte loads,
 //                 FP32 or FP16 storage) and writes the partial numerators of
 //                 f_hat (Eq. 17) and the part of the g_hat numerator (Eq. 16)
-//                 on landmark columns of the same cluster; the last CTA of a
-//                 cluster forms g_hat_j;
+//                 on landmark columns of the same cluster (an exact
+//                 fixed-point sum for Gaussian kernels; for the linear kernel
+//                 the last CTA of a cluster forms g_hat_j);
 //   assign        adds the partials of each segment in a fixed order, forms
 //                 d_ij = K_ii - 2 f_hat_ij + g_hat_j, takes the argmin (lowest
 //                 j on ties), the margin and the FP64 cost partials, and
@@ -216,8 +217,8 @@ cudaError_t launch_landmark_maps(const Supports& S, const int32_t* u, cudaStream
 // --------------------------------------------------------- f_hat streaming
 // 16-byte load with an L2 eviction-priority policy (createpolicy).
 // Streaming shape per stored type: a thread adds `kCols` consecutive columns
-// (one 16-byte load per block row) with `kDepth` rows in flight; a CTA of
-// kStreamThreads threads covers kStrip columns.
+// (one 16-byte load per block row), loading `kDepth` rows before adding
+// them; a CTA of kStreamThreads threads covers kStrip columns.
 template <typename T>
 struct StreamCfg {
   static constexpr int kCols = 16 / (int)sizeof(T);   // FP32: 4, FP16: 8
@@ -287,9 +288,11 @@ __device__ __forceinline__ void stream_rows(const T* base, int64_t ldk, const in
 // per CTA; plus the tile's g_hat numerator (its landmark columns of the same
 // cluster), reduced in double-float in a fixed order.  Rows below keep_rows
 // are loaded with an L2 evict_last policy (they stay resident across
-// iterations), the rest evict_first.  The last CTA of cluster j to finish
-// (atomic ticket, no waiting) forms g_hat_j = (sum of the cluster's
-// numerators) / n_j^2 (Eq. 16) in FP64, in a fixed order.
+// iterations), the rest evict_first.  With gfix (Gaussian kernels) each
+// tile's numerator is added to gfix[j] as a fixed-point integer (exact and
+// order-free; the assign forms g_hat_j = numerator / n_j^2, Eq. 16);
+// otherwise the last CTA of cluster j to finish (atomic ticket, no waiting)
+// forms g_hat_j in FP64 from the per-tile numerators, in a fixed order.
 // Up to eight CTAs per SM (the whole grid of the MNIST-shaped block resident
 // at once); the occupancy bound also lets the compiler keep a chunk's loads
 // in flight together instead of interleaving them with the additions.

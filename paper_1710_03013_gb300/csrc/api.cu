@@ -227,6 +227,42 @@ static kkm_status device_input(Workspace& ws, const T* p, int64_t n, const T** o
   return KKM_OK;
 }
 
+// Caller input X (n floats) on the device, with *bad set when it holds NaN
+// or Inf (checked before any other work).  Device memory is checked in
+// place; pinned host memory is copied and checked by one kernel that reads
+// it directly; other host memory is copied, then checked.
+static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n, const float** out, bool* bad) {
+  cudaStream_t st = ws.st;
+  *bad = false;
+  *out = p;
+  if (n <= 0) return KKM_OK;
+  int* flag;
+  KKM_TRY(ws.alloc(&flag, 1));
+  KKM_CK(cudaMemsetAsync(flag, 0, 4, st));
+  cudaPointerAttributes a;
+  const bool known = cudaPointerGetAttributes(&a, p) == cudaSuccess;
+  if (!known) cudaGetLastError();
+  if (known && (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
+    KKM_RUN("check_finite", st, launch_check_finite(p, n, flag, st));
+  } else {
+    float* d = nullptr;
+    KKM_TRY(ws.alloc(&d, n));
+    *out = d;
+    const float* mapped = (known && a.type == cudaMemoryTypeHost) ? static_cast<const float*>(a.devicePointer) : nullptr;
+    if (mapped && (reinterpret_cast<uintptr_t>(mapped) & 15) == 0) {
+      KKM_RUN("copy_check", st, launch_copy_check(mapped, d, n, flag, st));
+    } else {
+      KKM_CK(cudaMemcpyAsync(d, p, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st));
+      KKM_RUN("check_finite", st, launch_check_finite(d, n, flag, st));
+    }
+  }
+  int h = 0;
+  KKM_CK(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaStreamSynchronize(st));
+  *bad = h != 0;
+  return KKM_OK;
+}
+
 // ======================================================================
 // Small kernels of the host orchestration
 // ======================================================================
@@ -774,15 +810,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
 
   // ---- inputs on the device, validated
   const float* X = nullptr;
-  KKM_TRY(device_input(ws, X_in, N * d, &X));
   {
-    int* flag;
-    KKM_TRY(ws.alloc(&flag, 1));
-    KKM_CK(cudaMemsetAsync(flag, 0, 4, st));
-    KKM_RUN("check_finite", st, launch_check_finite(X, N * d, flag, st));
-    int bad = 0;
-    KKM_CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaStreamSynchronize(st));
+    bool bad = false;
+    KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad));
     if (bad) return invalid("X holds NaN or Inf");
   }
 
@@ -1133,15 +1163,9 @@ static kkm_status assign_impl(const kkm_model* m, const float* Xnew_in, int64_t 
   setup_pool_once(dev);
   Workspace ws(st);
   const float* X = nullptr;
-  KKM_TRY(device_input(ws, Xnew_in, M * d, &X));
   {
-    int* flag;
-    KKM_TRY(ws.alloc(&flag, 1));
-    KKM_CK(cudaMemsetAsync(flag, 0, 4, st));
-    KKM_RUN("check_finite", st, launch_check_finite(X, M * d, flag, st));
-    int bad = 0;
-    KKM_CK(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaStreamSynchronize(st));
+    bool bad = false;
+    KKM_TRY(device_input_checked(ws, Xnew_in, M * d, &X, &bad));
     if (bad) return invalid("X holds NaN or Inf");
   }
   int32_t* lab = nullptr;

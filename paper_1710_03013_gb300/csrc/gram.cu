@@ -151,6 +151,49 @@ __global__ void check_finite_kernel(const float* __restrict__ X, int64_t n, int*
     bad |= !isfinite(X[i]);
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
+// dst[i] = src[i] for i < n and *flag = 1 if any value is NaN or Inf, in one
+// pass: src is host memory the GPU reads directly (pinned), so the copy is
+// pulled by the SMs with many 16-byte requests in flight rather than pushed
+// by a copy engine.  n4 16-byte vectors, then `tail` (< 4) single floats.
+__global__ void __launch_bounds__(256)
+copy_check_kernel(const float4* src, float4* __restrict__ dst, int64_t n4, const float* src_tail,
+                  float* __restrict__ dst_tail, int tail, int* flag) {
+  int bad = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * stride;
+      v[u] = i < n4 ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < n4) {
+        dst[i] = v[u];
+        bad |= !isfinite(v[u].x) | !isfinite(v[u].y) | !isfinite(v[u].z) | !isfinite(v[u].w);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && (int)threadIdx.x < tail) {
+    const float x = src_tail[threadIdx.x];
+    dst_tail[threadIdx.x] = x;
+    bad |= !isfinite(x);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+cudaError_t launch_copy_check(const float* src, float* dst, int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(src) & 15) || (reinterpret_cast<uintptr_t>(dst) & 15)) return cudaErrorInvalidValue;
+  const int64_t n4 = n / 4;
+  const int tail = (int)(n - 4 * n4);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n4, 256 * 4), 152 * 8));
+  copy_check_kernel<<<grid, 256, 0, st>>>(reinterpret_cast<const float4*>(src), reinterpret_cast<float4*>(dst), n4,
+                                          src + 4 * n4, dst + 4 * n4, tail, flag);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int grid = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 8);

@@ -143,6 +143,10 @@ cudaError_t launch_gather_idx32(const float* Xp, int dp_in, const int32_t* idx, 
                                 float* out, int dp, float* normsq, cudaStream_t st);
 // Sets *flag = 1 if any of the n floats is NaN or Inf.
 cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream_t st);
+// Copies n floats from host memory the GPU can read (pinned; src and dst
+// 16-byte aligned, else cudaErrorInvalidValue) and sets *flag = 1 if any is
+// NaN or Inf, in one pass.
+cudaError_t launch_copy_check(const float* src, float* dst, int64_t n, int* flag, cudaStream_t st);
 
 // out[a*ldo + b] = kappa(A_a, B_b) for a < nA, b < nB (A [nA][dp], B [nB][dp]).
 // kind: DK_RBF (neg_scale = -log2(e)/(2 sigma^2)), DK_LINEAR, DK_DIST (sqrt of

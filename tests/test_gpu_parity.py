@@ -262,6 +262,33 @@ def test_fit_host_buffers_equal_device(lib):
     assert np.array_equal(m_d.trace()[0], m_h.trace()[0])
 
 
+def test_fit_pinned_host_input(lib):
+    """Pinned host input is copied and checked by one kernel that reads it
+    directly (a ragged tail of 10,507 floats); a pinned view that is not
+    16-byte aligned takes the copy-then-check path; both give the bits of the
+    device-input fit.  A NaN in pinned input is refused."""
+    import torch
+    X, _ = blobs(1501, 7, 4, workload=63, problem=1)
+    sig = _median_sigma(X)
+    lab_d, m_d = lib.kkm_fit(_dev(X), 4, 2, 0.4, "rbf", sig, iters=8, seed=8)
+    Xp = torch.from_numpy(X).pin_memory()
+    big = torch.from_numpy(np.concatenate([[0.0], X.ravel()]).astype(np.float32)).pin_memory()
+    Xu = big[1:].view(1501, 7)
+    assert Xu.data_ptr() % 16 != 0
+    for Xh in (Xp, Xu):
+        lab_h, m_h = lib.kkm_fit(Xh, 4, 2, 0.4, "rbf", sig, iters=8, seed=8)
+        assert np.array_equal(_np(lab_d), _np(lab_h))
+        assert np.array_equal(m_d.trace()[0], m_h.trace()[0])
+    la_d, da_d = lib.kkm_assign(m_d, _dev(X))
+    la_p, da_p = lib.kkm_assign(m_d, Xp)
+    assert np.array_equal(_np(la_d), _np(la_p)) and np.array_equal(_np(da_d), _np(da_p))
+    bad = Xp.clone().pin_memory()
+    bad[1500, 6] = float("nan")
+    with pytest.raises(lib.KKMError) as e:
+        lib.kkm_fit(bad, 4, 2, 0.4, "rbf", sig, iters=2, seed=8)
+    assert "NaN" in str(e.value)
+
+
 def test_fit_deterministic(lib):
     X, _ = blobs(5000, 32, 6, workload=64)
     sig = _median_sigma(X)

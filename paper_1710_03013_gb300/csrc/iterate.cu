@@ -540,22 +540,29 @@ constexpr int kAssignRows = 32;
 constexpr int kAssignWarps = 8;
 constexpr int kCandCap = 512;  // near-tie re-score pairs listed per CTA
 
+// 4-byte words of the assign kernel's distance tile, or of the support sort's
+// scratch that reuses it (cnt[C], base[C], wtab[nw * C], scan[32]), rounded
+// to 16 bytes; the re-score row follows.
+__host__ __device__ inline int assign_dist_words(int C, int nw) {
+  const int w = C * kAssignRows > (2 + nw) * C + 32 ? C * kAssignRows : (2 + nw) * C + 32;
+  return (w + 3) & ~3;
+}
+// largest dynamic shared memory an assign launch may ask for
+constexpr int kAssignMaxDynSmem = 160 * 1024;
+
 __global__ void __launch_bounds__(kAssignWarps * 32, 4)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
               int trace, RescoreArgs R) {
-  extern __shared__ float xs[];  // [R.dp] while re-scoring a row
+  // dynamic shared memory (sized by the launch for this C): the distances of
+  // the CTA's rows [C][kAssignRows], which the last CTA reuses as the support
+  // sort's scratch, then the FP32 row of the slow re-score path [R.dp]
+  extern __shared__ float dyn[];
   __shared__ AssignShared sh;
-  // distances of the CTA's rows; the last CTA reuses the space to re-sort
-  // the supports
-  __shared__ union {
-    float d[kMaxC][kAssignRows];
-    struct {
-      int cnt[kMaxC], base[kMaxC], wtab[kAssignWarps * kMaxC], scan[32];
-    } sort;
-  } us;
-  float(&dsh)[kMaxC][kAssignRows] = us.d;
+  float* const dshp = dyn;
+  auto dsh_at = [&](int j, int r) -> float& { return dshp[j * kAssignRows + r]; };
+  float* const xs = dyn + assign_dist_words(S.C, blockDim.x >> 5);
   __shared__ float rbest[kAssignRows], rsecond[kAssignRows];
   __shared__ int rlab[kAssignRows];
   __shared__ float wsum[32];
@@ -601,7 +608,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       if (sh.nj[j] > 0) fh = f / (float)sh.nj[j];
       if (fhat_out) fhat_out[(int64_t)i * C + j] = fh;
     }
-    dsh[j][lane] = fh;
+    dsh_at(j, lane) = fh;
   };
   // Warp w takes the contiguous clusters [jb, je), whose units are contiguous
   // too: one flat pass over them keeps 8 loads in flight across cluster
@@ -644,8 +651,8 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   // d_ij = K_ii - 2 f_hat_ij + g_hat_j for the warp's clusters (+inf when
   // n_j = 0 or past the last row)
   for (int j = jb; j < je; ++j) {
-    const float fh = dsh[j][lane];
-    dsh[j][lane] = (i < Ni && sh.nj[j] > 0) ? ks - 2.0f * fh + sh.ghf[j] : inf;
+    const float fh = dsh_at(j, lane);
+    dsh_at(j, lane) = (i < Ni && sh.nj[j] > 0) ? ks - 2.0f * fh + sh.ghf[j] : inf;
   }
   __syncthreads();
   if (w == 0) {
@@ -654,7 +661,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     bool flagged = false;
     if (i < Ni) {
       for (int j = 0; j < C; ++j) {  // lowest j on ties
-        const float dj = dsh[j][lane];
+        const float dj = dsh_at(j, lane);
         if (dj < best) {
           second = best;
           best = dj;
@@ -685,7 +692,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       int cnt = 0;
       if (fl)
         for (int j = 0; j < C; ++j) {
-          const float dj0 = dsh[j][lane];
+          const float dj0 = dsh_at(j, lane);
           cnt += dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale);
         }
       int x = cnt;
@@ -699,7 +706,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       if (fl && fits) {
         int k = off;
         for (int j = 0; j < C; ++j) {
-          const float dj0 = dsh[j][lane];
+          const float dj0 = dsh_at(j, lane);
           if (dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale)) cand[k++] = (lane << 9) | j;
         }
       }
@@ -738,7 +745,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
         acc += kv;
       }
       acc = warp_sum_f32(acc);
-      if (lane == 0) dsh[j][r] = k1 > k0 ? ksr - 2.0f * (acc / (float)(k1 - k0)) + sh.ghf[j] : inf;
+      if (lane == 0) dsh_at(j, r) = k1 > k0 ? ksr - 2.0f * (acc / (float)(k1 - k0)) + sh.ghf[j] : inf;
     }
     __syncthreads();
     // rows whose candidates did not fit the list: the whole CTA per row
@@ -753,7 +760,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       const float b0 = rbest[r];
       const float scale = ksr + sh.ghf[rlab[r]];
       for (int j = 0; j < C; ++j) {
-        const float dj0 = dsh[j][r];  // low-precision value (same in every thread)
+        const float dj0 = dsh_at(j, r);  // low-precision value (same in every thread)
         if (!(dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale))) continue;
         const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
         float acc = 0.0f;
@@ -774,7 +781,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
           float f = 0.0f;
           for (int q = 0; q < nw; ++q) f += wsum[q];
           const int n = k1 - k0;
-          dsh[j][r] = n > 0 ? ksr - 2.0f * (f / (float)n) + sh.ghf[j] : inf;
+          dsh_at(j, r) = n > 0 ? ksr - 2.0f * (f / (float)n) + sh.ghf[j] : inf;
         }
         __syncthreads();
       }
@@ -784,8 +791,8 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       float best = inf;
       int bj = 0;
       for (int j = 0; j < C; ++j)
-        if (dsh[j][lane] < best) {
-          best = dsh[j][lane];
+        if (dsh_at(j, lane) < best) {
+          best = dsh_at(j, lane);
           bj = j;
         }
       rbest[lane] = best;
@@ -873,7 +880,8 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     for (int j = threadIdx.x; j < C; j += blockDim.x) I.gfix[j] = 0ull;
   __syncthreads();
   if (wl[0] == 0) return;  // same landmark labels: same supports
-  sort_supports_cta(S, us.sort.cnt, us.sort.base, us.sort.wtab, us.sort.scan);
+  int* const scr = reinterpret_cast<int*>(dyn);  // every CTA is past its distances
+  sort_supports_cta(S, scr, scr + C, scr + 2 * C, scr + 2 * C + nw * C);
 }
 
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
@@ -882,11 +890,13 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           cudaStream_t st, const RescoreArgs& R) {
   if (Ni <= 0) return cudaSuccess;
   const int threads = 32 * std::min(S.C, kAssignWarps);
-  const size_t smem = R.Xi ? (size_t)R.dp * sizeof(float) : 0;
-  if (smem > 8 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  const size_t smem = ((size_t)assign_dist_words(S.C, threads / 32) + (R.Xi ? (size_t)R.dp : 0)) * sizeof(float);
+  if (smem > (size_t)kAssignMaxDynSmem) return cudaErrorInvalidValue;
+  // one attribute for every launch (set once: launches from several host
+  // threads never race on it)
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAssignMaxDynSmem);
+  if (attr != cudaSuccess) return attr;
   return launch_pdl(assign_kernel, dim3((unsigned)ceil_div(Ni, kAssignRows)), dim3(threads), smem, st, ldk, Ni, S,
                     I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
 }

@@ -176,11 +176,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "window": window}
 
 
-def source_hash(files):
+def source_hash(files, region=None):
+    """Hash of the kernel sources a traffic figure was taken with: whole files,
+    or only the text from region[0] up to region[1] in each (the kernel's own
+    part of a file that holds other kernels too)."""
     h = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_1710_03013_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+            text = fh.read()
+        if region:
+            a = text.index(region[0].encode())
+            text = text[a:text.index(region[1].encode(), a)]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
@@ -197,9 +204,9 @@ def ncu_traffic(kernel_name, workload="mnist"):
     if not ent:
         return None
     try:
-        if source_hash(ent["sources"]) != ent["source_hash"]:
+        if source_hash(ent["sources"], ent.get("region")) != ent["source_hash"]:
             return None
-    except OSError:
+    except (OSError, ValueError):
         return None
     return ent["bytes_per_launch"]
 

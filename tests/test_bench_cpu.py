@@ -64,6 +64,28 @@ def test_ncu_traffic_dropped_when_the_source_changes(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k", "w") is None
 
 
+def test_ncu_traffic_region_hash(tmp_path, monkeypatch):
+    """A figure keyed to one kernel's part of a file survives edits elsewhere
+    in the file and is dropped when that part changes."""
+    csrc = tmp_path / "paper_1710_03013_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    src = csrc / "two.cu"
+    src.write_text("// A\nkernel a v1\n// B\nkernel b v1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    reg = ["// A", "// B"]
+    entry = {"bytes_per_launch": 2e6, "sources": ["two.cu"], "region": reg,
+             "source_hash": bench.source_hash(["two.cu"], reg)}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"a@w": entry}))
+    assert bench.ncu_traffic("a", "w") == 2e6
+    src.write_text("// A\nkernel a v1\n// B\nkernel b v2\n")       # the other kernel changed
+    assert bench.ncu_traffic("a", "w") == 2e6
+    src.write_text("// A\nkernel a v2\n// B\nkernel b v2\n")       # this kernel changed
+    assert bench.ncu_traffic("a", "w") is None
+    src.write_text("kernel a v1\n")                                  # markers gone
+    assert bench.ncu_traffic("a", "w") is None
+
+
 def test_committed_traffic_entries_name_existing_sources():
     with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
         data = json.load(f)

@@ -680,8 +680,60 @@ static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t 
 // stream; join() (or the destructor, on an error return) orders the caller's
 // stream after both, so the workspace is released only when they are done.
 // Without the pipeline all three are the caller's stream.
+// High- and low-priority stream pairs of the block pipeline, reused across
+// fits (creating two streams costs tens of microseconds, a small fit's whole
+// run).  A pair is taken for one fit and given back once the caller's stream
+// is ordered after it; work still in flight on a returned pair only orders
+// the next fit that takes it after that work.
+struct StreamPair {
+  cudaStream_t main = nullptr, side = nullptr;
+  int device = -1;
+};
+static std::mutex g_pair_mu;
+static std::vector<StreamPair> g_pairs;
+
+static kkm_status take_pair(StreamPair* out) {
+  int dev = 0;
+  KKM_CK(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_pair_mu);
+    for (size_t q = 0; q < g_pairs.size(); ++q)
+      if (g_pairs[q].device == dev) {
+        *out = g_pairs[q];
+        g_pairs.erase(g_pairs.begin() + (std::ptrdiff_t)q);
+        return KKM_OK;
+      }
+  }
+  int least = 0, greatest = 0;
+  KKM_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  StreamPair p;
+  p.device = dev;
+  KKM_CK(cudaStreamCreateWithPriority(&p.main, cudaStreamNonBlocking, greatest));
+  const cudaError_t e = cudaStreamCreateWithPriority(&p.side, cudaStreamNonBlocking, least);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(p.main);
+    KKM_CK(e);
+  }
+  *out = p;
+  return KKM_OK;
+}
+
+static void give_pair(const StreamPair& p) {
+  std::lock_guard<std::mutex> lk(g_pair_mu);
+  g_pairs.push_back(p);
+}
+
+// Streams of one fit.  With the block pipeline (Section 4, Fig. 3: the next
+// mini-batch's kernel block is produced while the current one iterates) the
+// inner loops run on a high-priority stream and the blocks on a low-priority
+// one, so that a loop kernel's CTAs are scheduled ahead of a block kernel's
+// as SMs free up.  Both start after the work queued so far on the caller's
+// stream; join() (or the destructor, on an error return) orders the caller's
+// stream after both, so the workspace is released only when they are done.
+// Without the pipeline all three are the caller's stream.
 struct FitStreams {
   cudaStream_t user = nullptr, main = nullptr, side = nullptr;
+  StreamPair pair;
   bool own = false;
 
   // `later` waits for the work queued so far on `first`.
@@ -698,17 +750,9 @@ struct FitStreams {
   kkm_status start(cudaStream_t u, bool pipelined) {
     user = main = side = u;
     if (!pipelined) return KKM_OK;
-    int least = 0, greatest = 0;
-    KKM_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    cudaStream_t a = nullptr, b = nullptr;
-    KKM_CK(cudaStreamCreateWithPriority(&a, cudaStreamNonBlocking, greatest));
-    const cudaError_t e = cudaStreamCreateWithPriority(&b, cudaStreamNonBlocking, least);
-    if (e != cudaSuccess) {
-      cudaStreamDestroy(a);
-      KKM_CK(e);
-    }
-    main = a;
-    side = b;
+    KKM_TRY(take_pair(&pair));
+    main = pair.main;
+    side = pair.side;
     own = true;
     KKM_TRY(after(user, main));
     KKM_TRY(after(user, side));
@@ -723,8 +767,7 @@ struct FitStreams {
       cudaStreamSynchronize(main);
       cudaStreamSynchronize(side);
     }
-    cudaStreamDestroy(main);
-    cudaStreamDestroy(side);
+    give_pair(pair);
     main = side = user;
     return a != KKM_OK ? a : b;
   }

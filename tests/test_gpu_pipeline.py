@@ -90,3 +90,14 @@ def test_pipeline_in_a_batch(lib):
                              precision=p["precision"], pipeline="serial")
         assert np.array_equal(_np(lab), _np(ls))
         assert np.array_equal(m.trace()[0], ms.trace()[0])
+
+
+def test_pipeline_streams_reused_across_fits(lib):
+    """The pipeline's stream pairs are reused from fit to fit: many small
+    overlapped fits in a row, each on fresh data, equal their serial fits."""
+    for p in range(12):
+        X, _ = blobs(1200 + 50 * p, 6, 3, workload=76, problem=p)
+        lo, mo = lib.kkm_fit(_dev(X), 3, 3, 0.4, "rbf", 0.0, iters=4, seed=p, pipeline="overlap")
+        ls, ms = lib.kkm_fit(_dev(X), 3, 3, 0.4, "rbf", 0.0, iters=4, seed=p, pipeline="serial")
+        assert np.array_equal(_np(lo), _np(ls))
+        assert np.array_equal(mo.trace()[0], ms.trace()[0])

@@ -579,7 +579,6 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
   KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
-  KKM_TRY(ws.alloc(&I.ticket_sink, 1));
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.gtick, C));
   KKM_CK(cudaMemsetAsync(I.gtick, 0, (size_t)C * 4, ws.st));
@@ -982,15 +981,6 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     else
       KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
                            use_rtc ? &b.rtc : nullptr));
-    // L2 hygiene for the inner loop: the BF16 copies are not read again
-    // (dropped), the FP32 rows only by the few boundary steps (evict first),
-    // so the block rows kept with evict_last own the cache.
-    if (b.Xib && !fp32_half_block) {
-      KKM_RUN("l2_hygiene", bs, launch_l2_discard(b.Xib, (int64_t)Ni * sp.dp * 2, bs));
-      KKM_RUN("l2_hygiene", bs, launch_l2_discard(b.XLb, (int64_t)nL * sp.dp * 2, bs));
-    }
-    KKM_RUN("l2_hygiene", bs, launch_l2_demote(b.Xi, (int64_t)Ni * sp.dp * 4, I.ticket_sink, bs));
-    KKM_RUN("l2_hygiene", bs, launch_l2_demote(b.XL, (int64_t)nL * sp.dp * 4, I.ticket_sink, bs));
     return KKM_OK;
   };
 

@@ -273,7 +273,6 @@ struct IterState {
   // near-tie re-score (low-precision kernel blocks): rows whose margin is
   // below flag_tau * max(|d2|, K_ii + g_hat) are re-scored in FP32 by assign
   float flag_tau = 0.0f;
-  int32_t* ticket_sink = nullptr;   // [1] write target that keeps L2-demotion loads alive
   double* ghat_cur = nullptr;       // [C] g_hat of the current supports (written by fhat_partial)
   uint32_t* gtick = nullptr;        // [C] per-cluster tile tickets of fhat_partial, zero between launches
   // Gaussian kernels (values in [0, 1]): the g_hat numerators as fixed-point
@@ -289,10 +288,6 @@ struct IterState {
 // Rows of a [rows][ldk] float block that fit in the given share of L2.
 int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes = 4);
 
-// L2 hygiene: re-read a range with the evict_first policy / drop a range
-// whose contents are not needed again.
-cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st);
-cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st);
 // Builds perm/seg/units/col_label from the landmark labels S.lab (one CTA).
 cudaError_t launch_build_supports(const Supports& S, cudaStream_t st);
 // col_ord[L[k]] = k (col_ord pre-filled with -1) and lab[k] = u[L[k]].

@@ -425,47 +425,6 @@ cudaError_t launch_fhat_partial(const __half* KT, int64_t ldk, int Ni, const Sup
   return launch_fhat_t(KT, ldk, Ni, S, I, st);
 }
 
-// ----------------------------------------------------------- L2 priorities
-// Lines of [p, p + bytes) are re-read with the evict_first policy so that
-// they leave L2 before anything else (16-byte accesses, p 16-byte aligned).
-__global__ void l2_demote_kernel(const float4* __restrict__ p, int64_t n16, int* __restrict__ sink) {
-  uint64_t pol;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  float acc = 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p + i), "l"(pol));
-    acc += v.x;
-  }
-  if (acc == 1.2345e-30f) *sink = 1;  // keeps the loads; practically never taken
-}
-// Lines fully inside [p, p + bytes) are dropped from L2 without write-back:
-// only for buffers whose contents are not needed again.
-__global__ void l2_discard_kernel(char* p, int64_t lines) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lines; i += (int64_t)gridDim.x * blockDim.x)
-    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p + i * 128) : "memory");
-}
-
-cudaError_t launch_l2_demote(const void* p, int64_t bytes, int* sink, cudaStream_t st) {
-  const int64_t n16 = bytes / 16;
-  if (n16 <= 0) return cudaSuccess;
-  l2_demote_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n16, 256), 152 * 8), 256, 0, st>>>(
-      reinterpret_cast<const float4*>(p), n16, sink);
-  return cudaGetLastError();
-}
-cudaError_t launch_l2_discard(void* p, int64_t bytes, cudaStream_t st) {
-  // whole 128-byte lines inside the range only
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uintptr_t b = (a + 127) & ~uintptr_t(127);
-  const int64_t lines = (int64_t)(a + bytes - b) / 128;
-  if (lines <= 0) return cudaSuccess;
-  l2_discard_kernel<<<(unsigned)std::min<int64_t>(ceil_div(lines, 256), 152 * 8), 256, 0, st>>>(
-      reinterpret_cast<char*>(b), lines);
-  return cudaGetLastError();
-}
-
 // ------------------------------------------------------------------ assign
 // Loads n_j, the unit ranges and g_hat (Eq. 16) into shared memory.
 struct AssignShared {

@@ -327,6 +327,91 @@ def test_P8_partition(sampling, N, B):
             assert np.all(b % B == i)
 
 
+# Landmarks are "uniformly sampled from the mini-batch" (Section 3.2, Eq. 14).
+# The draw is the first k steps of a Fisher-Yates shuffle (Durstenfeld's
+# form): step a swaps position a with r = a + floor(u * (n - a)), u uniform in
+# [0, 1).  The two hand-worked cases below start from published SplitMix64
+# outputs (the same values as test_splitmix64_reference_outputs), so neither
+# depends on the oracle's generator plumbing.
+
+
+def _u01_of(x):
+    return (x >> 11) * 2.0 ** -53      # top 53 bits, as in the generator pin
+
+
+def test_P8_fisher_yates_hand_worked_seed0():
+    # SplitMix64(0): u = 0.88331..., 0.43152..., 0.02643...
+    # a = 0: r = 0 + floor(0.88331 * 10) = 8   -> [8 1 2 3 4 5 6 7 0 9]
+    # a = 1: r = 1 + floor(0.43152 *  9) = 4   -> [8 4 2 3 1 5 6 7 0 9]
+    # a = 2: r = 2 + floor(0.02643 *  8) = 2   (no move)
+    outs = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [a + math.floor(_u01_of(x) * (10 - a)) for a, x in enumerate(outs)] == [8, 4, 2]
+    got = O.partial_fisher_yates(10, 3, O.SplitMix64(0))
+    assert got.tolist() == [8, 4, 2]
+
+
+def test_P8_fisher_yates_hand_worked_seed1234567():
+    # SplitMix64(1234567): u = 0.35008, 0.17364, 0.53221, 0.24901, 0.88953
+    # a = 0: r = 0 + floor(0.35008 * 20) =  7  -> pos0 = 7,  pos7 = 0
+    # a = 1: r = 1 + floor(0.17364 * 19) =  4  -> pos1 = 4,  pos4 = 1
+    # a = 2: r = 2 + floor(0.53221 * 18) = 11  -> pos2 = 11, pos11 = 2
+    # a = 3: r = 3 + floor(0.24901 * 17) =  7  -> pos3 = 0 (moved there at a=0), pos7 = 3
+    # a = 4: r = 4 + floor(0.88953 * 16) = 18  -> pos4 = 18, pos18 = 1
+    outs = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    assert [a + math.floor(_u01_of(x) * (20 - a)) for a, x in enumerate(outs)] == [7, 4, 11, 7, 18]
+    assert O.partial_fisher_yates(20, 5, O.SplitMix64(1234567)).tolist() == [7, 4, 11, 0, 18]
+    # landmark_indices returns the same set sorted
+    assert O.landmark_indices(20, 0.25, O.SplitMix64(1234567)).tolist() == [0, 4, 7, 11, 18]
+
+
+def _fy_frequencies_ok(draw, n=12, k=4, T=20000):
+    """A uniform k-subset in uniform order: every (position, value) cell has
+    probability 1/n, every value is included with probability k/n, and a
+    given pair with probability k(k-1)/(n(n-1)).  T seeds; every frequency
+    must lie within 4 standard deviations."""
+    pos = np.zeros((k, n))
+    inc = np.zeros(n)
+    pair = 0
+    for seed in range(1, T + 1):
+        p = np.asarray(draw(n, k, O.SplitMix64(seed)))
+        pos[np.arange(k), p] += 1
+        inc[p] += 1
+        pair += int(0 in p and 1 in p)
+
+    def within(freq, prob):
+        return bool(np.all(np.abs(freq / T - prob) <= 4.0 * math.sqrt(prob * (1.0 - prob) / T)))
+    return (within(pos, 1.0 / n), within(inc, k / n),
+            within(np.array([pair]), k * (k - 1) / (n * (n - 1))))
+
+
+def test_P8_fisher_yates_uniform_over_seeds():
+    assert _fy_frequencies_ok(O.partial_fisher_yates) == (True, True, True)
+
+
+def _fy_mutant(rule):
+    def draw(n, k, rng):
+        idx = list(range(n))
+        for a in range(k):
+            r = rule(a, n, rng.u01())
+            idx[a], idx[r] = idx[r], idx[a]
+        return idx[:k]
+    return draw
+
+
+@pytest.mark.parametrize("name,rule", [
+    ("no swap", lambda a, n, u: a),
+    ("r = floor(u n)", lambda a, n, u: int(math.floor(u * n))),
+    ("last element unreachable", lambda a, n, u: a + int(math.floor(u * (n - a - 1)))),
+])
+def test_P8_fisher_yates_pins_reject_plausible_mistakes(name, rule):
+    # the same checks fail for draws with a plausible mistake planted in them
+    draw = _fy_mutant(rule)
+    assert not all(_fy_frequencies_ok(draw)), name
+    assert list(draw(10, 3, O.SplitMix64(0))) != [8, 4, 2] or \
+        list(draw(20, 5, O.SplitMix64(1234567))) != [7, 4, 11, 0, 18], name
+
+
 @pytest.mark.parametrize("Ni,s", [(100, 0.2), (3000, 0.05), (7, 0.01), (50, 1.0), (15000, 0.2)])
 def test_P8_landmarks(Ni, s):
     L = O.landmark_indices(Ni, s, O.SplitMix64(42))

@@ -24,13 +24,16 @@ method) on a bounded sample of the same workload per step.
 """
 
 import argparse
+import atexit
 import datetime
 import hashlib
 import json
 import os
+import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -115,10 +118,11 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.t0 = self.t1 = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.dir = tempfile.mkdtemp(prefix="kkm_clocks_")
+        self.path = os.path.join(self.dir, "clocks.csv")
+        atexit.register(self.cleanup)
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
@@ -141,6 +145,9 @@ class ClockSampler:
             self.proc.terminate()
             self.proc.wait()
             self.f.close()
+
+    def cleanup(self):
+        shutil.rmtree(self.dir, ignore_errors=True)
 
     def summary(self):
         if not self.proc:

@@ -327,13 +327,21 @@ kkm_status kkm_minibatch_plan(int64_t N, int32_t B, int32_t sampling, double s,
  * memory: a request path where cudaMalloc could synchronise the device and
  * stall other work, or a process whose device memory belongs to another
  * framework's pool.  The paper has no counterpart; this is a library service.
- *   Same results as kkm_assign (labels, squared distances) for one chunk of
- *   at most KKM_NOALLOC_MAX_ROWS query rows, for models with at most
- *   KKM_NOALLOC_MAX_REF reference rows (landmark supports in mode
- *   KKM_ASSIGN_SUPPORTS, medoids in mode KKM_ASSIGN_MEDOIDS) and a prepared
- *   row length of at most KKM_NOALLOC_MAX_ROWLEN floats (d rounded up to 8;
+ *   Labels and squared distances as kkm_assign computes them, for one chunk
+ *   of at most KKM_NOALLOC_MAX_ROWS query rows.  RBF and linear models run
+ *   the same kernels as kkm_assign and give the same bits; for an RMSD model
+ *   kkm_assign may take its tensor-core screen (32 or more reference rows,
+ *   sigma >= 0.5) while this call evaluates every pair exactly, so distances
+ *   agree within 1e-5 of the term scale and labels wherever the relative
+ *   margin between the two nearest clusters exceeds 1e-4.  The model may
+ *   have at most KKM_NOALLOC_MAX_REF reference rows (landmark supports in
+ *   mode KKM_ASSIGN_SUPPORTS, medoids in mode KKM_ASSIGN_MEDOIDS) and a
+ *   prepared row length of at most KKM_NOALLOC_MAX_ROWLEN floats (d rounded up to 8;
  *   for KKM_RMSD 3 * n_atoms rounded up to 24).  Larger sizes give KKM_EINVAL.
- *   Xnew, labels_out and dist_out (nullable) must be device memory.
+ *   Xnew, labels_out and dist_out (nullable) must be memory of the model's
+ *   device, and that device must be current; otherwise KKM_EINVAL.  The call
+ *   returns when its work is done: it waits for the stream once after the
+ *   non-finite-input check and once at the end.
  * It allocates nothing: its working memory is one fixed scratch array of
  * about 21 MB that every GPU loading this library keeps until exit.  The
  * first call on each device looks up that array's device address (and may

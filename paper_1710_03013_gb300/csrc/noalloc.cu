@@ -69,13 +69,14 @@ static kkm_status scratch_address(unsigned char** out) {
   return KKM_OK;
 }
 
-static bool on_device(const void* p) {
+// True when p is device (or managed) memory of device `dev`.
+static bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 static kkm_status na_invalid(const char* msg) {
@@ -90,8 +91,13 @@ static kkm_status assign_noalloc_impl(const kkm_model* m, const float* X, int64_
   if (M < 0 || M > kNaRows) return na_invalid("M exceeds KKM_NOALLOC_MAX_ROWS (split the query into chunks)");
   if (M == 0) return KKM_OK;
   if (!X || !labels_out) return na_invalid("X or labels_out is NULL");
-  if (!on_device(X) || !on_device(labels_out) || (dist_out && !on_device(dist_out)))
-    return na_invalid("kkm_assign_noalloc needs device pointers for X, labels_out and dist_out");
+  // the model's arrays live on m->device: the scratch address is taken on
+  // the current device, so both must be that device, and so must the buffers
+  int cur = -1;
+  KKM_CK(cudaGetDevice(&cur));
+  if (cur != m->device) return na_invalid("the current device is not the model's device");
+  if (!on_device(X, cur) || !on_device(labels_out, cur) || (dist_out && !on_device(dist_out, cur)))
+    return na_invalid("kkm_assign_noalloc needs X, labels_out and dist_out in the model device's memory");
   const int rows_ref = mode == KKM_ASSIGN_SUPPORTS ? m->nL : m->C;
   if (rows_ref > kNaRef) return na_invalid("model has more reference rows than KKM_NOALLOC_MAX_REF");
   if (m->dp > kNaRowLen) return na_invalid("model rows are longer than KKM_NOALLOC_MAX_ROWLEN");

@@ -419,12 +419,41 @@ def kkm_assign(model, Xnew, mode="supports", stream=None):
     return lab, dist
 
 
+def _check_noalloc_args(d, Xnew, labels_out, dist_out):
+    """Argument checks of kkm_assign_noalloc.  The C entry point receives bare
+    device pointers and no row length, so it cannot see a wrong dtype, a
+    strided view, a short output or a tensor on another device; a wrong one
+    would be read or written past its end.  Raises ValueError."""
+    torch = _torch()
+    if not _is_cuda(Xnew):
+        raise ValueError("kkm_assign_noalloc: Xnew must be a CUDA tensor")
+    if Xnew.dtype != torch.float32 or not Xnew.is_contiguous():
+        raise ValueError("kkm_assign_noalloc: Xnew must be contiguous float32")
+    if Xnew.dim() < 2 or int(np.prod(Xnew.shape[1:])) != d:
+        raise ValueError(f"kkm_assign_noalloc: Xnew must be [M][{d}] (rows of the model's length)")
+    M = int(Xnew.shape[0])
+    outs = [("labels_out", labels_out, torch.int32)]
+    if dist_out is not None:
+        outs.append(("dist_out", dist_out, torch.float32))
+    for name, t, dt in outs:
+        if not _is_cuda(t) or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"kkm_assign_noalloc: {name} must be a contiguous CUDA {dt} tensor")
+        if t.numel() < M:
+            raise ValueError(f"kkm_assign_noalloc: {name} holds {t.numel()} elements, needs {M}")
+        if t.device != Xnew.device:
+            raise ValueError(f"kkm_assign_noalloc: {name} is on {t.device}, Xnew on {Xnew.device}")
+    return M
+
+
 def kkm_assign_noalloc(model, Xnew, labels_out, dist_out=None, mode="supports", stream=None):
     """kkm_assign_noalloc of the C ABI: labels (and squared distances) of at
     most KKM_NOALLOC_MAX_ROWS new samples written into the caller's CUDA
-    tensors; neither this function nor the library allocates."""
+    tensors; neither this function nor the library allocates.  Xnew is a
+    contiguous float32 CUDA tensor [M][d] (d the model's row length),
+    labels_out an int32 and dist_out (optional) a float32 CUDA tensor of at
+    least M elements, all on the model's device."""
     lib = load()
-    M = int(Xnew.shape[0])
+    M = _check_noalloc_args(model.info()["d"], Xnew, labels_out, dist_out)
     st = stream if stream is not None else _stream_of(Xnew)
     _check(lib.kkm_assign_noalloc(model.handle, ctypes.c_void_p(Xnew.data_ptr()), M,
                                   MODE[mode] if isinstance(mode, str) else int(mode),

@@ -134,3 +134,54 @@ def test_fit_rejects_bad_options_before_any_device_call(kkm):
     with pytest.raises(kkm.KKMError) as e:
         kkm.kkm_fit(X, 2, 65, 0.5, "rbf", 1.0, iters=2, labels=False, stream=0)   # B > N
     assert e.value.status == kkm.STATUS_EINVAL
+
+
+class _FakeCuda:
+    """A CPU tensor that reports itself as a CUDA tensor on cuda:0, so that
+    the binding's argument checks can run without a GPU (nothing reaches the
+    library: every case below must be refused before the call)."""
+
+    def __init__(self, t, device="cuda:0"):
+        import torch
+        self._t = t
+        self.is_cuda = True
+        self.device = torch.device(device)
+        self.dtype = t.dtype
+        self.shape = t.shape
+
+    def is_contiguous(self):
+        return self._t.is_contiguous()
+
+    def dim(self):
+        return self._t.dim()
+
+    def numel(self):
+        return self._t.numel()
+
+
+def test_noalloc_binding_rejects_bad_arguments(kkm):
+    import torch
+    d, M = 8, 10
+    X = _FakeCuda(torch.zeros(M, d))
+    lab = _FakeCuda(torch.zeros(M, dtype=torch.int32))
+    dist = _FakeCuda(torch.zeros(M))
+    assert kkm._check_noalloc_args(d, X, lab, dist) == M
+    assert kkm._check_noalloc_args(d, X, lab, None) == M
+    bad = [
+        (torch.zeros(M, d), lab, dist),                                   # Xnew on the host
+        (_FakeCuda(torch.zeros(M, d, dtype=torch.float64)), lab, dist),   # wrong dtype
+        (_FakeCuda(torch.zeros(d, M).t()), lab, dist),                    # not contiguous
+        (_FakeCuda(torch.zeros(M, d + 1)), lab, dist),                    # wrong row length
+        (_FakeCuda(torch.zeros(M * d)), lab, dist),                       # not 2-D
+        (X, _FakeCuda(torch.zeros(M - 1, dtype=torch.int32)), dist),      # labels too short
+        (X, _FakeCuda(torch.zeros(M, dtype=torch.int64)), dist),          # labels wrong dtype
+        (X, torch.zeros(M, dtype=torch.int32), dist),                     # labels on the host
+        (X, _FakeCuda(torch.zeros(2 * M, dtype=torch.int32)[::2]), dist),  # labels strided
+        (X, lab, _FakeCuda(torch.zeros(M - 1))),                          # dist too short
+        (X, lab, _FakeCuda(torch.zeros(M, dtype=torch.float64))),         # dist wrong dtype
+        (X, _FakeCuda(torch.zeros(M, dtype=torch.int32), "cuda:1"), dist),  # another device
+        (X, lab, _FakeCuda(torch.zeros(M), "cuda:1")),                    # another device
+    ]
+    for k, (x, l, o) in enumerate(bad):
+        with pytest.raises(ValueError):
+            kkm._check_noalloc_args(d, x, l, o)

@@ -294,14 +294,18 @@ kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d,
  * kkm_debug_step -- one inner iteration (Eq. 15-17) on one mini-batch with
  * the labels given (teacher forcing), for step-by-step checks.
  *   Xb [Ni][d] mini-batch samples; L [nL] sorted local landmark indices
- *   (host); u_in [Ni] labels (host).  Outputs (host, each nullable):
- *   u_out [Ni], fhat_out [Ni][C] (Eq. 17; NaN where n_j = 0),
- *   margin_out [Ni] (second-best minus best distance), ghat_out [C]
- *   (Eq. 16; NaN where n_j = 0), n_out [C], *omega_out, *changed_out.
+ *   (host); u_in [Ni] labels (host); precision KKM_FP32 or KKM_BF16 (the
+ *   kernel block kkm_fit evaluates and stores for that precision, and on
+ *   KKM_BF16 its FP32 near-tie re-score).  Outputs (host, each nullable):
+ *   u_out [Ni], fhat_out [Ni][C] (Eq. 17 from the stored block, before any
+ *   re-score; NaN where n_j = 0), margin_out [Ni] (second-best minus best
+ *   distance), ghat_out [C] (Eq. 16; NaN where n_j = 0), n_out [C],
+ *   *omega_out, *changed_out.
  */
 kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d,
                           const int32_t* L, int32_t nL, const kkm_kernel* k,
-                          int32_t C, const int32_t* u_in, int32_t* u_out,
+                          int32_t C, int32_t precision,
+                          const int32_t* u_in, int32_t* u_out,
                           float* fhat_out, float* margin_out, double* ghat_out,
                           int32_t* n_out, double* omega_out,
                           int32_t* changed_out, void* stream);

@@ -671,6 +671,57 @@ static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t 
   return KKM_OK;
 }
 
+// How a fit stores and evaluates its kernel block: the reduced-precision RBF
+// path keeps the block in FP16 (values in [0, 1], an 11-bit significand,
+// finer than the BF16 inputs' rounding), so the inner loop streams half the
+// bytes; short rows keep the FP32 Gram on the FFMA pipes and only round the
+// stored values.
+struct BlockMode {
+  bool kt_half = false, fp32_half_block = false, use_rtc = false;
+  BlockMode(const KernelSpec& sp, int64_t nLmax) {
+    kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
+    fp32_half_block = kt_half && sp.d < kBf16TensorMinDim;
+    use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
+  }
+  // near-tie window of the re-score (0: no re-score, FP32 blocks)
+  float flag_tau(const KernelSpec& sp) const {
+    if (sp.precision == KKM_FP32) return 0.0f;
+    return fp32_half_block ? kRescoreMarginHalf : kRescoreMargin;
+  }
+};
+
+// Alg. 1 line 3 on already prepared rows: the kernel block K(L, X^i) of the
+// buffer set b (its Xi, XL, ids filled) into b.KT or b.KTh.
+static kkm_status block_kernel(const KernelSpec& sp, const BlockMode& bm, const BlockBufs& b, const int32_t* Ld,
+                               int nL, int Ni, int64_t ldk, int* tc_err, cudaStream_t bs) {
+  if (bm.fp32_half_block)
+    KKM_RUN("gram_block", bs,
+            launch_gram_rbf_half(b.XL, nL, b.Xi, Ni, sp.dp, b.auxL, b.aux_i, b.gidL, b.gid, sp.neg_scale(), b.KTh,
+                                 ldk, bs));
+  else if (sp.precision == KKM_BF16)
+    KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
+                              b.XLb, b.nXLb, b.Xib, b.nXib, tc_err, bs));
+  else
+    KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
+                         bm.use_rtc ? &b.rtc : nullptr));
+  return KKM_OK;
+}
+
+// Re-score inputs of the reduced-precision path: the FP32 rows of the
+// mini-batch and of its landmarks.
+static RescoreArgs rescore_args(const KernelSpec& sp, const BlockBufs& b) {
+  RescoreArgs R;
+  if (sp.precision == KKM_FP32) return R;
+  R.kind = sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF;
+  R.dp = sp.dp;
+  R.Xi = b.Xi;
+  R.nXi = b.aux_i;
+  R.XL = b.XL;
+  R.nXL = b.auxL;
+  R.neg_scale = sp.neg_scale();
+  return R;
+}
+
 // Streams of one fit.  With the block pipeline (Section 4, Fig. 3: the next
 // mini-batch's kernel block is produced while the current one iterates) the
 // inner loops run on a high-priority stream and the blocks on a low-priority
@@ -904,9 +955,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
   // significand, finer than the BF16 inputs' rounding): the inner loop
   // streams half the bytes.
-  const bool kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
-  const bool fp32_half_block = kt_half && d < kBf16TensorMinDim;
-  const bool use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
+  const BlockMode bm(sp, nLmax);
+  const bool kt_half = bm.kt_half;
+  const bool use_rtc = bm.use_rtc;
   // one set of block buffers, or two when the next mini-batch's block is
   // computed while the current one iterates
   BlockBufs bb[2];
@@ -971,17 +1022,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
     KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
-    if (fp32_half_block)
-      KKM_RUN("gram_block", bs,
-              launch_gram_rbf_half(b.XL, nL, b.Xi, Ni, sp.dp, b.auxL, b.aux_i, b.gidL, b.gid, sp.neg_scale(), b.KTh,
-                                   ldk, bs));
-    else if (sp.precision == KKM_BF16)
-      KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, kt_half ? (void*)b.KTh : (void*)b.KT, kt_half, ldk, b.XLb,
-                                b.nXLb, b.Xib, b.nXib, tc_err, bs));
-    else
-      KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
-                           use_rtc ? &b.rtc : nullptr));
-    return KKM_OK;
+    return block_kernel(sp, bm, b, Ld, nL, Ni, ldk, tc_err, bs);
   };
 
   // ---- Algorithm 1
@@ -1031,19 +1072,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_RUN("build_supports", ms, launch_build_supports(S, ms));
     KKM_CK(cudaMemsetAsync(I.done, 0, 4, ms));
     if (I.gfix) KKM_CK(cudaMemsetAsync(I.gfix, 0, (size_t)C * 8, ms));  // the last mini-batch's medoid step read them
-    const bool rescore = sp.precision != KKM_FP32;
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
-    I.flag_tau = rescore ? (fp32_half_block ? kRescoreMarginHalf : kRescoreMargin) : 0.0f;
-    RescoreArgs R;
-    if (rescore) {
-      R.kind = sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF;
-      R.dp = sp.dp;
-      R.Xi = Xi;
-      R.nXi = aux_i;
-      R.XL = bk.XL;
-      R.nXL = bk.auxL;
-      R.neg_scale = sp.neg_scale();
-    }
+    I.flag_tau = bm.flag_tau(sp);
+    const RescoreArgs R = rescore_args(sp, bk);
     NvtxRange nv_loop("inner loop");
     for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
       KKM_RUN("fhat_partial", ms,
@@ -1345,14 +1376,17 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
 // kkm_debug_step (teacher-forced inner iteration)
 // ======================================================================
 static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, const int32_t* L, int32_t nL,
-                                  const kkm_kernel* k, int32_t C, const int32_t* u_in, int32_t* u_out,
-                                  float* fhat_out, float* margin_out, double* ghat_out, int32_t* n_out,
-                                  double* omega_out, int32_t* changed_out, cudaStream_t st) {
+                                  const kkm_kernel* k, int32_t C, int32_t precision, const int32_t* u_in,
+                                  int32_t* u_out, float* fhat_out, float* margin_out, double* ghat_out,
+                                  int32_t* n_out, double* omega_out, int32_t* changed_out, cudaStream_t st) {
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
   if (Ni < 1 || Ni > INT32_MAX) return invalid("Ni must be >= 1");
   if (C < 1 || C > kMaxC) return invalid("C must be in [1, 256]");
   if (nL < 1 || nL > Ni || !L || !u_in || !Xb_in) return invalid("bad landmarks or NULL pointer");
+  if (precision != KKM_FP32 && precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
+  if (precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  sp.precision = precision;
   if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
   for (int q = 0; q < nL; ++q)
     if (L[q] < 0 || L[q] >= Ni || (q > 0 && L[q] <= L[q - 1])) return invalid("L must be sorted, in [0, Ni)");
@@ -1365,29 +1399,30 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   const float* X;
   KKM_TRY(device_input(ws, Xb_in, Ni * d, &X));
   const int64_t ldk = round_up(Ni, 32);
-  float *Xi, *aux, *XL, *auxL, *KT, *fh, *mg;
-  int64_t *gid, *gidL;
+  // the fit's block buffers and block evaluation for this precision
+  const BlockMode bm(sp, nL);
+  BlockBufs b;
+  KKM_TRY(alloc_block_bufs(ws, sp, Ni, nL, ldk, bm.kt_half, bm.use_rtc, &b));
+  float *fh, *mg;
   int32_t *Ld, *u;
   double* gh;
-  KKM_TRY(ws.alloc(&Xi, Ni * sp.dp));
-  KKM_TRY(ws.alloc(&aux, Ni));
-  KKM_TRY(ws.alloc(&gid, Ni));
-  KKM_TRY(ws.alloc(&XL, (int64_t)nL * sp.dp));
-  KKM_TRY(ws.alloc(&auxL, nL));
-  KKM_TRY(ws.alloc(&gidL, nL));
-  KKM_TRY(ws.alloc(&KT, (int64_t)nL * ldk));
+  int* tc_err = nullptr;
   KKM_TRY(ws.alloc(&Ld, nL));
   KKM_TRY(ws.alloc(&u, Ni));
   KKM_TRY(ws.alloc(&fh, Ni * C));
   KKM_TRY(ws.alloc(&mg, Ni));
   KKM_TRY(ws.alloc(&gh, C));
+  if (sp.precision == KKM_BF16) {
+    KKM_TRY(ws.alloc(&tc_err, 1));
+    KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
+  }
   KKM_CK(cudaMemcpyAsync(Ld, L, (size_t)nL * 4, cudaMemcpyHostToDevice, st));
   KKM_CK(cudaMemcpyAsync(u, u_in, (size_t)Ni * 4, cudaMemcpyHostToDevice, st));
-  KKM_TRY(prep_rows(sp, X, 0, 1, Ni, Xi, aux, st));
-  KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(gid, 0, 1, Ni), cudaGetLastError()));
-  KKM_TRY(copy_prepared(sp, Xi, Ld, nL, XL, auxL, st));
-  KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(gid, Ld, nL, gidL), cudaGetLastError()));
-  KKM_TRY(kernel_block(sp, XL, auxL, gidL, nL, Xi, aux, gid, Ni, KT, ldk, st));
+  KKM_TRY(prep_rows(sp, X, 0, 1, Ni, b.Xi, b.aux_i, st));
+  KKM_RUN("iota", st, (iota64_kernel<<<blocks_for(Ni), 256, 0, st>>>(b.gid, 0, 1, Ni), cudaGetLastError()));
+  KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, st));
+  KKM_RUN("gather_ids", st, (gather_i64_kernel<<<blocks_for(nL), 256, 0, st>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
+  KKM_TRY(block_kernel(sp, bm, b, Ld, nL, (int)Ni, ldk, tc_err, st));
   LoopBuffers lb;
   KKM_TRY(alloc_loop(ws, nL, C, ldk, 1, &lb, sp.gaussian()));
   lb.S.L = Ld;
@@ -1397,9 +1432,14 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_RUN("landmark_maps", st, launch_landmark_maps(lb.S, u, st));
   KKM_RUN("build_supports", st, launch_build_supports(lb.S, st));
   KKM_CK(cudaMemcpyAsync(lb.n_copy, lb.S.n_j, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
-  const float* kself = sp.kind == KKM_LINEAR ? aux : nullptr;
-  KKM_RUN("fhat_partial", st, launch_fhat_partial(KT, ldk, (int)Ni, lb.S, lb.I, st));
-  KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st));
+  const float* kself = sp.kind == KKM_LINEAR ? b.aux_i : nullptr;
+  lb.I.keep_rows = 0;
+  lb.I.flag_tau = bm.flag_tau(sp);
+  const RescoreArgs R = rescore_args(sp, b);
+  KKM_RUN("fhat_partial", st,
+          bm.kt_half ? launch_fhat_partial(b.KTh, ldk, (int)Ni, lb.S, lb.I, st)
+                     : launch_fhat_partial(b.KT, ldk, (int)Ni, lb.S, lb.I, st));
+  KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st, R));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));
   if (margin_out) KKM_CK(cudaMemcpyAsync(margin_out, mg, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
@@ -1407,7 +1447,13 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   if (n_out) KKM_CK(cudaMemcpyAsync(n_out, lb.n_copy, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
   if (omega_out) KKM_CK(cudaMemcpyAsync(omega_out, lb.I.trace_omega, 8, cudaMemcpyDeviceToHost, st));
   if (changed_out) KKM_CK(cudaMemcpyAsync(changed_out, lb.I.trace_changed, 4, cudaMemcpyDeviceToHost, st));
+  int tc_err_h = 0;
+  if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
+  if (tc_err_h) {
+    set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
+    return KKM_ETIMEOUT;
+  }
   prof_collect();
   return KKM_OK;
 }
@@ -1580,13 +1626,13 @@ kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d, const kkm_
 }
 
 kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d, const int32_t* L, int32_t nL, const kkm_kernel* k,
-                          int32_t C, const int32_t* u_in, int32_t* u_out, float* fhat_out, float* margin_out,
-                          double* ghat_out, int32_t* n_out, double* omega_out, int32_t* changed_out,
-                          void* stream) {
+                          int32_t C, int32_t precision, const int32_t* u_in, int32_t* u_out, float* fhat_out,
+                          float* margin_out, double* ghat_out, int32_t* n_out, double* omega_out,
+                          int32_t* changed_out, void* stream) {
   set_error("");
   return guarded([&] {
-    return debug_step_impl(Xb, Ni, d, L, nL, k, C, u_in, u_out, fhat_out, margin_out, ghat_out, n_out, omega_out,
-                           changed_out, (cudaStream_t)stream);
+    return debug_step_impl(Xb, Ni, d, L, nL, k, C, precision, u_in, u_out, fhat_out, margin_out, ghat_out, n_out,
+                           omega_out, changed_out, (cudaStream_t)stream);
   });
 }
 

@@ -13,6 +13,9 @@ mini-batch of it is a trajectory with a 20 times shorter mean dwell, which is
 what is generated.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -158,6 +161,99 @@ def test_bf16_fit_full_size(lib, mnist):
     best = model_d[np.arange(2000), la.cpu().numpy()]
     ok = rel_margin(model_d) > 1e-4
     assert np.max(np.abs(da.cpu().numpy()[ok] - best[ok]) / (1.0 + gh.max())) <= DIST_REL
+
+
+# ------------------------------------------- the benchmark's BF16 path at full size
+# Expected values written by tests/golden/make_mnist_minibatch.py (the FP64
+# oracle on the same seeded data).
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+U16 = 2.0 ** -11   # unit roundoff of the FP16-stored kernel block
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        g = json.load(f)
+    g["u"] = np.frombuffer(g["u"].encode(), np.uint8).astype(np.int64) - ord("0")
+    g["clear"] = np.unpackbits(np.frombuffer(bytes.fromhex(g["clear"]), np.uint8))[:g["Ni"]].astype(bool)
+    return g
+
+
+def test_bf16_step_full_minibatch(lib, mnist):
+    """One teacher-forced inner iteration on the benchmark's path (BF16
+    tensor-core block stored in FP16, FP32 near-tie re-score) on the first
+    mini-batch, 15,000 x 3,000, labels = the generator's classes.
+      f_hat (before the re-score) of 288 sampled rows and g_hat of every
+        cluster against the oracle on the BF16-rounded rows, within the FP16
+        storage rounding (2^-11 relative) plus the FP32 kernel tolerance;
+      the new labels of every row against the oracle on the unrounded rows,
+        wherever its relative margin exceeds 1e-4 (rows inside the re-score
+        window are decided from FP32 kernel values);
+      Omega against the unrounded oracle within the BF16 path's 5e-3."""
+    X, Xd, sigma, cls = mnist
+    g = _golden("mnist_step.json")
+    assert g["sigma"] == sigma
+    gidx, L = _plan(0)
+    assert (g["Ni"], g["nL"], g["landmarks_sum"]) == (len(gidx), len(L), int(L.sum()))
+    Xb = X[gidx]
+    u = cls[gidx].astype(np.int32)
+    got = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16)
+    assert np.array_equal(got["n"], g["n"])
+    bad = np.nonzero((got["u"] != g["u"]) & g["clear"])[0]
+    assert bad.size == 0, f"{bad.size} clear rows differ from the oracle, first {bad[:10]}"
+    om_rel = abs(got["omega"] - g["omega"]) / g["omega"]
+    print(f"BF16 step: Omega rel error vs unrounded oracle {om_rel:.3g}; "
+          f"{np.count_nonzero(~g['clear'])} rows inside the 1e-4 margin")
+    assert om_rel <= 5e-3
+    # f_hat and g_hat of the stored block against the oracle on the rounded rows
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([rng.integers(0, len(gidx), 256), L[rng.integers(0, len(L), 32)]]))
+    ker = O.Kernel(O.KIND_RBF, float(sigma))
+    n, fhat, ghat, _ = _oracle_rows(ker, _bf16(Xb).astype(np.float64), L, u.astype(np.int64), C, rows)
+    live = n > 0
+    fd = np.abs(got["fhat"][rows][:, live] - fhat[:, live])
+    assert np.all(fd <= U16 * np.abs(fhat[:, live]) + KERNEL_ABS), float(np.max(fd))
+    gd = np.abs(got["ghat"][live] - ghat[live])
+    assert np.all(gd <= U16 * ghat[live] + KERNEL_ABS), gd
+    print(f"BF16 step: max |f_hat - oracle(rounded)| {np.max(fd):.3g}, max |g_hat - oracle(rounded)| "
+          f"{np.max(gd):.3g}, max |g_hat - oracle(unrounded)| "
+          f"{np.max(np.abs(got['ghat'][live] - np.asarray(g['ghat'])[live])):.3g}")
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_minibatch_fit_vs_oracle_full_size(lib, mnist, precision):
+    """The first mini-batch of the benchmark workload fitted on its own
+    (15,000 x 784, B = 1, |L| = 3,000, 30 iterations, early stop off, the
+    oracle's k-means++ medoids as the initial ones) against the oracle's whole
+    fit: labels equal wherever the oracle's last-iteration margin exceeds 1e-4
+    relative, the Omega trace within 1e-6 (FP32) or the BF16 path's 5e-3,
+    the landmark counts n_j exactly, g_hat within the same relative bound."""
+    X, _, sigma, _ = mnist
+    g = _golden("mnist_fit.json")
+    assert g["sigma"] == sigma
+    gidx, _ = _plan(0)
+    Xb = X[gidx]
+    prec = lib.KKM_BF16 if precision == "bf16" else lib.KKM_FP32
+    rel = 5e-3 if precision == "bf16" else 1e-6
+    lab, model = lib.kkm_fit(_dev(Xb), C, 1, S, "rbf", sigma, iters=g["iters"], seed=g["seed"], early_stop=False,
+                             init_medoids=g["init_medoids"], precision=prec)
+    lab = lab.cpu().numpy()
+    bad = np.nonzero((lab != g["u"]) & g["clear"])[0]
+    assert bad.size == 0, f"{bad.size} clear rows differ from the oracle, first {bad[:10]}"
+    om, _ = model.trace()
+    want = np.asarray(g["trace"])
+    assert om.shape == want.shape
+    err = float(np.max(np.abs(om - want) / want))
+    print(f"{precision} fit: Omega trace max rel error {err:.3g}; "
+          f"{np.count_nonzero(~g['clear'])} rows inside the 1e-4 margin")
+    assert err <= rel
+    _, gh, n = model.supports()
+    assert np.array_equal(n, g["n"])
+    live = n > 0
+    assert np.all(np.abs(gh[live] - np.asarray(g["ghat"])[live]) <= rel * np.asarray(g["ghat"])[live])
+    idx, cnt, _ = model.medoids()
+    assert np.all(np.abs(cnt - np.asarray(g["W"])) <= np.count_nonzero(~g["clear"]))
+    if precision == "fp32":
+        assert np.array_equal(idx, g["medoids"])
 
 
 @pytest.fixture(scope="module")

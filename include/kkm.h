@@ -72,6 +72,17 @@ typedef enum kkm_sampling { KKM_STRIDE = 0, KKM_BLOCK = 1 } kkm_sampling;
  * the same bits either way: the same kernels run on the same inputs.       */
 typedef enum kkm_pipeline { KKM_PIPE_AUTO = 0, KKM_PIPE_SERIAL = 1, KKM_PIPE_OVERLAP = 2 } kkm_pipeline;
 
+/* Launch form of one inner iteration (Eq. 15-17).  KKM_ITER_FUSED runs the
+ * whole iteration in one cooperative launch: every CTA owns a strip of
+ * sample columns over all landmark rows, so f_hat is finished where it is
+ * summed, and one grid barrier makes g_hat (Eq. 16) available to every CTA.
+ * It applies to C <= 64 and mini-batches of up to about 77,000 samples.
+ * KKM_ITER_SPLIT streams per-unit partial sums and finishes them in a second
+ * launch.  KKM_ITER_AUTO takes the fused form where it applies.  The two
+ * forms add the same values in different orders: labels agree above the
+ * tolerance margin and distances to FP32 rounding.                          */
+typedef enum kkm_iteration { KKM_ITER_AUTO = 0, KKM_ITER_FUSED = 1, KKM_ITER_SPLIT = 2 } kkm_iteration;
+
 /* Prototypes used by kkm_assign / kkm_cost: the sparse landmark centroids
  * of the last mini-batch (Eq. 14-17) or the global medoids (Eq. 2 against
  * the output M of Algorithm 1).                                             */
@@ -88,6 +99,7 @@ typedef struct kkm_options {
   int32_t sampling;             /* kkm_sampling (default KKM_STRIDE)            */
   int32_t early_stop;           /* 1: stop an inner loop when no label changes */
   int32_t pipeline;             /* kkm_pipeline (default KKM_PIPE_AUTO)         */
+  int32_t iteration;            /* kkm_iteration (default KKM_ITER_AUTO)        */
   const int64_t* init_medoids;  /* host [C] global sample indices replacing
                                    kernel k-means++, or NULL                    */
   void* stream;                 /* cudaStream_t or NULL                         */
@@ -366,7 +378,7 @@ const char* kkm_last_error(void);
 /* Per-kernel device timing.  kkm_prof_enable(1): every library kernel launch
  * is counted and bracketed by CUDA events on its stream; (2): every launch is
  * counted, only the kernel-block and streaming kernels ("gram_block",
- * "rmsd_block", "rmsd_exact", "fhat_partial") are bracketed; (0): off.
+ * "rmsd_block", "rmsd_exact", "fhat_partial", "iterate") are bracketed; (0): off.
  * kkm_prof_read returns the number of launches and the summed device
  * milliseconds of the named kernel since the last reset (0 launches if
  * unknown).  kkm_prof_work returns the work units a data-dependent kernel

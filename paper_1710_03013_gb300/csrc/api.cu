@@ -58,7 +58,7 @@ static int g_prof_on = 0;  // 0 off, 1 time every launch, 2 count all, time the 
 
 static bool heavy_kernel(const char* name) {
   return !strcmp(name, "gram_block") || !strcmp(name, "rmsd_block") || !strcmp(name, "rmsd_exact") ||
-         !strcmp(name, "fhat_partial");
+         !strcmp(name, "fhat_partial") || !strcmp(name, "iterate");
 }
 static std::unordered_map<std::string, ProfEntry> g_prof;
 static std::vector<Pending> g_pending;
@@ -574,11 +574,20 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&lb->n_copy, C));
   I.n_strips = (int)ceil_div(ldk, kStripCols);
   I.assign_grid = (int)ceil_div(ldk, 32);
+  // per-CTA slots serve the assign (one CTA per 32 rows) and the fused
+  // iteration (at most one CTA per SM)
+  I.fused_cap = sm_count();
+  const int parts = std::max(I.assign_grid, I.fused_cap);
   KKM_TRY(ws.alloc(&I.partial, (int64_t)mu * ldk));
   KKM_TRY(ws.alloc(&I.gpart, (int64_t)mu * I.n_strips));
-  KKM_TRY(ws.alloc(&I.omega_part, I.assign_grid));
-  KKM_TRY(ws.alloc(&I.changed_part, I.assign_grid));
-  KKM_TRY(ws.alloc(&I.lm_part, I.assign_grid));
+  KKM_TRY(ws.alloc(&I.omega_part, parts));
+  KKM_TRY(ws.alloc(&I.changed_part, parts));
+  KKM_TRY(ws.alloc(&I.lm_part, parts));
+  KKM_TRY(ws.alloc(&I.gcta, (int64_t)I.fused_cap * C));
+  KKM_TRY(ws.alloc(&I.bar, 1));
+  KKM_TRY(ws.alloc(&I.err, 1));
+  KKM_CK(cudaMemsetAsync(I.bar, 0, 4, ws.st));
+  KKM_CK(cudaMemsetAsync(I.err, 0, 4, ws.st));
   KKM_TRY(ws.alloc(&I.ghat_cur, C));
   KKM_TRY(ws.alloc(&I.gtick, C));
   KKM_CK(cudaMemsetAsync(I.gtick, 0, (size_t)C * 4, ws.st));
@@ -720,6 +729,38 @@ static RescoreArgs rescore_args(const KernelSpec& sp, const BlockBufs& b) {
   R.nXL = b.auxL;
   R.neg_scale = sp.neg_scale();
   return R;
+}
+
+// Whether the inner iterations of a mini-batch run fused (one cooperative
+// launch each) for this option and block shape.
+static bool fused_applies(int Ni, int nL, int C, int esize) {
+  FusedShape F;
+  size_t smem = 0;
+  return fused_shape(Ni, nL, C, esize, sm_count(), &F, &smem);
+}
+
+// One inner iteration (Alg. 1 lines 9-16; Eq. 15-17) over the block of the
+// buffer set b: fused, or the streaming partial sums and the assign.  Either
+// way the iteration closes on the device (trace, early stop, support re-sort).
+static kkm_status inner_iteration(const BlockMode& bm, const BlockBufs& b, int64_t ldk, int Ni, const Supports& S,
+                                  const IterState& I, bool fused, const float* kself, int32_t* u, float* margin,
+                                  float* fhat_out, double* ghat_out, int early_stop, const RescoreArgs& R,
+                                  cudaStream_t st) {
+  if (fused) {
+    KKM_RUN("iterate", st,
+            bm.kt_half ? launch_iterate(b.KTh, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop,
+                                        sm_count(), st, R)
+                       : launch_iterate(b.KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop,
+                                        sm_count(), st, R));
+    return KKM_OK;
+  }
+  KKM_RUN("fhat_partial", st,
+          bm.kt_half ? launch_fhat_partial(b.KTh, ldk, Ni, S, I, st) : launch_fhat_partial(b.KT, ldk, Ni, S, I, st));
+  // the assign's last CTA closes the iteration and re-sorts the supports when
+  // a landmark label changed
+  KKM_RUN("assign", st,
+          launch_assign(ldk, Ni, S, I, kself, u, margin, nullptr, fhat_out, ghat_out, early_stop, /*trace=*/1, st, R));
+  return KKM_OK;
 }
 
 // Streams of one fit.  With the block pipeline (Section 4, Fig. 3: the next
@@ -874,6 +915,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   if (opt.pipeline != KKM_PIPE_AUTO && opt.pipeline != KKM_PIPE_SERIAL && opt.pipeline != KKM_PIPE_OVERLAP)
     return invalid("unknown pipeline");
   if (opt.sampling != KKM_STRIDE && opt.sampling != KKM_BLOCK) return invalid("unknown sampling");
+  if (opt.iteration != KKM_ITER_AUTO && opt.iteration != KKM_ITER_FUSED && opt.iteration != KKM_ITER_SPLIT)
+    return invalid("unknown iteration form");
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
   if (opt.precision != KKM_FP32 && opt.precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
@@ -1075,16 +1118,14 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
     I.flag_tau = bm.flag_tau(sp);
     const RescoreArgs R = rescore_args(sp, bk);
+    const bool fused = opt.iteration != KKM_ITER_SPLIT && fused_applies(Ni, nL, C, kt_half ? 2 : 4);
+    if (opt.iteration == KKM_ITER_FUSED && !fused)
+      return invalid("KKM_ITER_FUSED does not apply to this shape (C <= 64 and a mini-batch of at most one "
+                     "column per thread of one CTA per SM)");
     NvtxRange nv_loop("inner loop");
-    for (int t = 0; t < iters; ++t) {                                         // Alg. 1 lines 9-16
-      KKM_RUN("fhat_partial", ms,
-              kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, I, ms) : launch_fhat_partial(bk.KT, ldk, Ni, S, I, ms));
-      // assign; its last CTA closes the iteration (trace, early stop) and
-      // re-sorts the supports when a landmark label changed
-      KKM_RUN("assign", ms,
-              launch_assign(ldk, Ni, S, I, kself, u, nullptr, nullptr, nullptr, nullptr, opt.early_stop,
-                            /*trace=*/1, ms, R));
-    }
+    for (int t = 0; t < iters; ++t)                                           // Alg. 1 lines 9-16
+      KKM_TRY(inner_iteration(bm, bk, ldk, Ni, S, I, fused, kself, u, nullptr, nullptr, nullptr, opt.early_stop, R,
+                              ms));
     I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
@@ -1176,14 +1217,19 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   }
   if (labels_on_host)
     KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
-  int tc_err_h = 0, rtc_err_h[2] = {0, 0};
+  int tc_err_h = 0, rtc_err_h[2] = {0, 0}, it_err_h = 0;
   if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaMemcpyAsync(&it_err_h, I.err, 4, cudaMemcpyDeviceToHost, st));
   for (int q = 0; q < nbuf; ++q)
     if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h[q], bb[q].rtc.err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
   tc_err_h |= rtc_err_h[0] | rtc_err_h[1];
   if (tc_err_h) {
     set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
+    return KKM_ETIMEOUT;
+  }
+  if (it_err_h) {
+    set_error("fused inner iteration: the bounded grid-barrier wait gave up");
     return KKM_ETIMEOUT;
   }
   if (model_out && *model_out) {
@@ -1436,10 +1482,8 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   lb.I.keep_rows = 0;
   lb.I.flag_tau = bm.flag_tau(sp);
   const RescoreArgs R = rescore_args(sp, b);
-  KKM_RUN("fhat_partial", st,
-          bm.kt_half ? launch_fhat_partial(b.KTh, ldk, (int)Ni, lb.S, lb.I, st)
-                     : launch_fhat_partial(b.KT, ldk, (int)Ni, lb.S, lb.I, st));
-  KKM_RUN("assign", st, launch_assign(ldk, (int)Ni, lb.S, lb.I, kself, u, mg, nullptr, fh, gh, 0, 1, st, R));
+  const bool fused = fused_applies((int)Ni, nL, C, bm.kt_half ? 2 : 4);
+  KKM_TRY(inner_iteration(bm, b, ldk, (int)Ni, lb.S, lb.I, fused, kself, u, mg, fh, gh, 0, R, st));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));
   if (margin_out) KKM_CK(cudaMemcpyAsync(margin_out, mg, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
@@ -1447,11 +1491,16 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   if (n_out) KKM_CK(cudaMemcpyAsync(n_out, lb.n_copy, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
   if (omega_out) KKM_CK(cudaMemcpyAsync(omega_out, lb.I.trace_omega, 8, cudaMemcpyDeviceToHost, st));
   if (changed_out) KKM_CK(cudaMemcpyAsync(changed_out, lb.I.trace_changed, 4, cudaMemcpyDeviceToHost, st));
-  int tc_err_h = 0;
+  int tc_err_h = 0, it_err_h = 0;
   if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
+  KKM_CK(cudaMemcpyAsync(&it_err_h, lb.I.err, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
   if (tc_err_h) {
     set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
+    return KKM_ETIMEOUT;
+  }
+  if (it_err_h) {
+    set_error("fused inner iteration: the bounded grid-barrier wait gave up");
     return KKM_ETIMEOUT;
   }
   prof_collect();

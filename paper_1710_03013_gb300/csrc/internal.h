@@ -284,6 +284,12 @@ struct IterState {
   int keep_rows = 0;                // block rows kept in L2 across iterations (evict_last)
   int assign_grid;
   int n_strips;
+  // fused iteration (launch_iterate): per-CTA g_hat shares, the grid barrier
+  // counter (zero between launches) and the error word of its bounded wait
+  float2* gcta = nullptr;           // [fused_cap][C] double-float
+  uint32_t* bar = nullptr;          // [1]
+  int32_t* err = nullptr;           // [1]
+  int fused_cap = 0;                // CTAs the fused buffers hold (omega_part etc. hold at least as many)
 };
 // Rows of a [rows][ldk] float block that fit in the given share of L2.
 int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes = 4);
@@ -319,6 +325,27 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           const float* kself, int32_t* u, float* margin, float* dmin,
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st, const RescoreArgs& R = RescoreArgs());
+
+// One whole inner iteration in one cooperative launch (f_hat, g_hat, d,
+// argmin, margin, re-score, Omega, trace, support re-sort): one CTA per SM
+// at most, each owning a strip of columns over every landmark row.  Applies
+// when fused_shape() says so (C <= kFusedMaxC, a strip of at most one column
+// per thread); *I.err becomes 1 if its grid barrier gave up.
+constexpr int kFusedMaxC = 64;
+constexpr int kFusedMaxDynSmem = 200 * 1024;
+struct FusedShape {
+  int n_cta;   // CTAs (<= n_sms)
+  int groups;  // 16-byte column groups holding the Ni samples
+  int gmax;    // most groups of one CTA
+  int R;       // row streams of a CTA
+};
+bool fused_shape(int Ni, int nL, int C, int esize, int n_sms, FusedShape* F, size_t* smem);
+cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
+                           int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R = RescoreArgs());
+cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
+                           int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R = RescoreArgs());
 
 // ---- mini-batch boundary -----------------------------------------------------
 // Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).

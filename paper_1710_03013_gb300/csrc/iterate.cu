@@ -860,6 +860,487 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                     I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
 }
 
+// ------------------------------------------------- fused inner iteration
+// One launch per inner iteration (Eq. 15-17): every CTA owns a strip of
+// sample columns of the block and streams ALL landmark rows of that strip, in
+// the label-sorted order of `perm`, so the f_hat numerators of its columns
+// are complete inside the CTA (no partial sums leave it).  The only quantity
+// that needs every CTA is g_hat (Eq. 16, the landmark columns of all strips):
+// each CTA writes its per-cluster share, the grid meets at one barrier, and
+// then every CTA forms g_hat in the same fixed order and finishes its columns
+// -- distances, argmin (lowest j on ties), margin, near-tie re-score, labels,
+// cost partials.  The last CTA to finish closes the iteration as assign does.
+//
+// Inside a CTA: thread t takes column group g = t % gmax (16 bytes of
+// columns) and row stream r = t / gmax; stream r walks the contiguous rows
+// [r nL / R, (r+1) nL / R) of the sorted landmark list, keeps one running sum
+// per segment it is in, and flushes it to the shared slot r + j when it
+// leaves segment j.  Streams cover the rows in order, so the slots of
+// different (stream, segment) pairs are distinct, and the numerator of
+// segment j is the sum of its slots in stream order (fixed: bit-reproducible).
+//
+// The barrier needs every CTA resident at once: the kernel is launched as a
+// cooperative grid of at most one CTA per SM.  Its wait is bounded; when the
+// bound is hit the kernel records an error and returns.
+constexpr int kFusedThreads = 512;
+constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kFusedDepth = 8;          // rows loaded before their additions
+constexpr int kFusedPermCap = 8192;     // sorted landmark list staged in shared memory up to this size
+constexpr int kFusedCandCap = 1024;     // re-score pairs listed per round
+constexpr unsigned kFusedSpinLimit = 1u << 24;  // barrier polls (>= ~1.6 s with the 100 ns back-off)
+
+// One 16-byte load of a block row (FP32: 4 values, FP16: 8) with an L2
+// eviction-priority policy, kept raw until its additions.
+template <typename T>
+struct Raw16;
+template <>
+struct Raw16<float> {
+  float v[4];
+  __device__ __forceinline__ void load(const float* p, uint64_t pol) { ld16_policy(p, pol, v); }
+  __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0f; }
+  __device__ __forceinline__ void add_to(float (&acc)[4]) const {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] += v[c];
+  }
+};
+template <>
+struct Raw16<__half> {
+  uint4 x;
+  __device__ __forceinline__ void load(const __half* p, uint64_t pol) { ld16_policy(p, pol, x); }
+  __device__ __forceinline__ void zero() { x = make_uint4(0u, 0u, 0u, 0u); }
+  __device__ __forceinline__ void add_to(float (&acc)[8]) const {
+    const uint32_t wds[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&wds[c]));
+      acc[2 * c] += f.x;
+      acc[2 * c + 1] += f.y;
+    }
+  }
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// stream of row k when nL rows are cut into R contiguous streams
+// [floor(r nL / R), floor((r+1) nL / R))
+__device__ __forceinline__ int fused_stream_of(int k, int nL, int R) {
+  return min(R - 1, (int)((((int64_t)k + 1) * R - 1) / nL));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, IterState I, FusedShape F,
+                     const float* __restrict__ kself, int32_t* __restrict__ u, float* __restrict__ margin,
+                     float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop, RescoreArgs R) {
+  constexpr int NC = 16 / (int)sizeof(T);
+  extern __shared__ __align__(16) float fdyn[];
+  __shared__ int seg_sh[kFusedMaxC + 1];
+  __shared__ int nj_sh[kFusedMaxC];
+  __shared__ int first_sh[kFusedMaxC];
+  __shared__ int j0_sh[kFusedThreads];
+  __shared__ double gh_sh[kFusedMaxC];
+  __shared__ float ghf_sh[kFusedMaxC];
+  __shared__ float2 wom[kFusedWarps];
+  __shared__ int wch[kFusedWarps], wlm[kFusedWarps];
+  __shared__ int scan_sh[32];
+  __shared__ int cand[kFusedCandCap];
+  __shared__ int is_last;
+  griddep_wait();
+  if (I.done && *I.done) return;  // early stop: the same flag in every CTA
+  const int C = S.C, nL = S.nL;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int gmax = F.gmax, RS = F.R;
+  const int gb = (int)(((int64_t)blockIdx.x * F.groups) / gridDim.x);
+  const int ge = (int)(((int64_t)(blockIdx.x + 1) * F.groups) / gridDim.x);
+  const int ng = ge - gb;
+  const int ncol = ng * NC;  // this CTA's columns: col0 + [0, ncol)
+  const int col0 = gb * NC;
+  const float inf = __int_as_float(0x7f800000);
+  float* const slots = fdyn;  // [(RS + C)][gmax][NC]
+  int* const perm_sh = reinterpret_cast<int*>(fdyn + (size_t)(RS + C) * gmax * NC);
+  const bool perm_in_sh = nL <= kFusedPermCap;
+  for (int j = tid; j <= C; j += kFusedThreads) seg_sh[j] = S.seg_off[j];
+  for (int j = tid; j < C; j += kFusedThreads) nj_sh[j] = S.n_j[j];
+  if (perm_in_sh)
+    for (int k = tid; k < nL; k += kFusedThreads) perm_sh[k] = S.perm[k];
+  __syncthreads();
+  // segment of the first row of every stream (empty segments skipped), and
+  // the slot that receives each segment's whole numerator (its first piece)
+  for (int r = tid; r < RS; r += kFusedThreads) {
+    const int a = (int)(((int64_t)r * nL) / RS);
+    int j = 0;
+    while (j < C - 1 && seg_sh[j + 1] <= a) ++j;
+    j0_sh[r] = j;
+  }
+  for (int j = tid; j < C; j += kFusedThreads)
+    first_sh[j] = nj_sh[j] > 0 ? fused_stream_of(seg_sh[j], nL, RS) + j : -1;
+  __syncthreads();
+
+  // ---- phase A: stream the strip, one running sum per (stream, segment)
+  {
+    const int* permp = perm_in_sh ? perm_sh : S.perm;
+    uint64_t keep, strm;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(strm));
+    const int g = tid % gmax, r = tid / gmax;
+    if (r < RS && g < ng) {
+      const int a = (int)(((int64_t)r * nL) / RS), e = (int)(((int64_t)(r + 1) * nL) / RS);
+      if (a < e) {
+        const T* base = KT + (int64_t)col0 + (int64_t)g * NC;
+        int j = j0_sh[r];
+        int jend = seg_sh[j + 1];
+        float acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+        auto flush = [&](int jj) {
+          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)(r + jj) * gmax + g) * NC);
+#pragma unroll
+          for (int c = 0; c < NC; c += 4) dst[c / 4] = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+        };
+        for (int k = a; k < e; k += kFusedDepth) {
+          Raw16<T> v[kFusedDepth];
+#pragma unroll
+          for (int q = 0; q < kFusedDepth; ++q) {
+            if (k + q < e) {
+              const int row = permp[k + q];
+              v[q].load(base + (int64_t)row * ldk, row < I.keep_rows ? keep : strm);
+            } else {
+              v[q].zero();
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kFusedDepth; ++q) {
+            if (k + q < e) {
+              while (k + q >= jend) {  // the row opens a later segment
+                flush(j);
+                ++j;
+                jend = seg_sh[j + 1];
+              }
+              v[q].add_to(acc);
+            }
+          }
+        }
+        flush(j);
+      }
+    }
+  }
+  __syncthreads();
+  // every segment's numerator: its pieces in stream order, into its first slot
+  for (int e = tid; e < C * ncol; e += kFusedThreads) {
+    const int j = e / ncol, q = e - j * ncol;
+    if (nj_sh[j] == 0) continue;
+    const int r0 = fused_stream_of(seg_sh[j], nL, RS), r1 = fused_stream_of(seg_sh[j + 1] - 1, nL, RS);
+    const int gq = q / NC, cq = q - gq * NC;
+    float s = 0.0f;
+    for (int r = r0; r <= r1; ++r) s += slots[((size_t)(r + j) * gmax + gq) * NC + cq];
+    slots[((size_t)(r0 + j) * gmax + gq) * NC + cq] = s;
+  }
+  __syncthreads();
+  // this CTA's share of the g_hat numerators (Eq. 16): landmark columns of
+  // each cluster, double-float, columns in order within a fixed lane tree
+  if (S.col_label) {
+    for (int j = w; j < C; j += kFusedWarps) {
+      float2 gs = make_float2(0.0f, 0.0f);
+      if (nj_sh[j] > 0) {
+        const float* fj = slots + (size_t)first_sh[j] * gmax * NC;
+        for (int q = lane; q < ncol; q += 32) {
+          const int l = col0 + q;
+          if (l < Ni && __ldg(S.col_label + l) == j) gs = df_add(gs, make_float2(fj[q], 0.0f));
+        }
+      }
+      gs = warp_sum_df(gs);
+      if (lane == 0) I.gcta[(size_t)blockIdx.x * C + j] = gs;
+    }
+    __threadfence();  // each writer's shares visible to the grid before the barrier
+  }
+  // grid barrier (cooperative launch: every CTA is resident)
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    atomicAdd(I.bar, 1u);
+    unsigned polls = 0;
+    is_last = 0;
+    while (ld_acquire_u32(I.bar) < gridDim.x) {
+      __nanosleep(100);
+      if (++polls > kFusedSpinLimit) {
+        atomicExch(I.err, 1);
+        is_last = -1;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (is_last < 0) return;  // the barrier gave up: the host reports KKM_ETIMEOUT
+  // g_hat of every cluster: the CTA shares summed in CTA order (the same
+  // value in every CTA); given (an assign against a model) when ghat_in is set
+  for (int j = tid; j < C; j += kFusedThreads) {
+    const int n = nj_sh[j];
+    double gv = __longlong_as_double(0x7ff8000000000000LL);
+    if (n > 0) {
+      if (I.ghat_in) {
+        gv = I.ghat_in[j];
+      } else {
+        double a2 = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+          const float2 v = __ldcg(I.gcta + (size_t)b * C + j);
+          a2 += (double)v.x + (double)v.y;
+        }
+        gv = a2 / ((double)n * (double)n);
+      }
+    }
+    gh_sh[j] = gv;
+    ghf_sh[j] = (float)gv;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && ghat_out)
+    for (int j = tid; j < C; j += kFusedThreads) ghat_out[j] = gh_sh[j];
+
+  // ---- phase B: one column per thread
+  const int q = tid;
+  const int l = col0 + q;
+  const bool mine = q < ncol && l < Ni;
+  const float ks = (mine && kself) ? kself[l] : 1.0f;
+  float best = inf, second = inf;
+  int bj = 0;
+  bool flagged = false;
+  if (mine) {
+    for (int j = 0; j < C; ++j) {
+      if (nj_sh[j] == 0) {
+        if (fhat_out) fhat_out[(int64_t)l * C + j] = __int_as_float(0x7fc00000);
+        continue;
+      }
+      float* fp = slots + (size_t)first_sh[j] * gmax * NC + q;
+      const float fh = *fp / (float)nj_sh[j];
+      if (fhat_out) fhat_out[(int64_t)l * C + j] = fh;
+      const float dj = ks - 2.0f * fh + ghf_sh[j];
+      *fp = dj;  // the slot now holds d_lj
+      if (dj < best) {  // lowest j on ties
+        second = best;
+        best = dj;
+        bj = j;
+      } else if (dj < second) {
+        second = dj;
+      }
+    }
+    if (R.Xi && I.flag_tau > 0.0f && second < inf)
+      flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + ghf_sh[bj]);
+  }
+  // near-tie re-score: candidate (column, cluster) pairs of the flagged
+  // columns, each re-scored by one warp from exact FP32 kernel values of its
+  // support (one landmark per lane, then a fixed xor tree); pairs are listed
+  // in rounds of kFusedCandCap in (column, cluster) order
+  if (__syncthreads_or(flagged)) {
+    const float b0 = best, scale = ks + ghf_sh[bj];
+    auto is_cand = [&](int j) {
+      if (nj_sh[j] == 0) return false;
+      const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
+      return dj - b0 < I.flag_tau * fmaxf(fabsf(dj), scale);
+    };
+    int cnt = 0;
+    if (flagged)
+      for (int j = 0; j < C; ++j) cnt += is_cand(j);
+    int total;
+    const int off = block_excl_scan(cnt, scan_sh, &total);
+    for (int base = 0; base < total; base += kFusedCandCap) {
+      if (flagged && off + cnt > base && off < base + kFusedCandCap) {
+        int k = off;
+        for (int j = 0; j < C; ++j)
+          if (is_cand(j)) {
+            if (k >= base && k < base + kFusedCandCap) cand[k - base] = (q << 8) | j;
+            ++k;
+          }
+      }
+      __syncthreads();
+      const int np = min(kFusedCandCap, total - base);
+      for (int p = w; p < np; p += kFusedWarps) {
+        const int qq = cand[p] >> 8, j = cand[p] & 255;
+        const int ir = col0 + qq;
+        const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
+        const float ni = R.nXi[ir];
+        const float ksr = kself ? kself[ir] : 1.0f;
+        const int k0 = seg_sh[j], k1 = seg_sh[j + 1];
+        float acc = 0.0f;
+        for (int kk = k0 + lane; kk < k1; kk += 32) {
+          const int k = S.perm[kk];
+          const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
+          float dot = 0.0f;
+          for (int c = 0; c < (R.dp >> 2); ++c) {
+            const float4 a4 = __ldg(xi + c), b4 = __ldg(xl + c);
+            dot = fmaf(a4.x, b4.x, fmaf(a4.y, b4.y, fmaf(a4.z, b4.z, fmaf(a4.w, b4.w, dot))));
+          }
+          float kv;
+          if (R.kind == DK_LINEAR) kv = dot;
+          else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+          acc += kv;
+        }
+        acc = warp_sum_f32(acc);
+        if (lane == 0) slots[(size_t)first_sh[j] * gmax * NC + qq] = ksr - 2.0f * (acc / (float)(k1 - k0)) + ghf_sh[j];
+      }
+      __syncthreads();
+    }
+    if (flagged) {  // argmin and margin over the updated distances
+      best = inf;
+      second = inf;
+      for (int j = 0; j < C; ++j) {
+        if (nj_sh[j] == 0) continue;
+        const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
+        if (dj < best) {
+          second = best;
+          best = dj;
+          bj = j;
+        } else if (dj < second) {
+          second = dj;
+        }
+      }
+    }
+  }
+  float2 om = make_float2(0.0f, 0.0f);
+  int ch = 0, lmc = 0;
+  if (mine) {
+    const int old = u[l];
+    u[l] = bj;
+    ch = old != bj;
+    const int cord = S.col_ord ? S.col_ord[l] : -1;
+    if (cord >= 0) {
+      S.lab[cord] = bj;
+      lmc = ch;
+    }
+    if (margin) margin[l] = second - best;
+    om.x = best;
+  }
+  // this CTA's cost and counts, in a fixed order
+  om = warp_sum_df(om);
+  ch = warp_sum_i32(ch);
+  lmc = warp_sum_i32(lmc);
+  __threadfence();  // labels and landmark labels visible before the ticket
+  if (lane == 0) {
+    wom[w] = om;
+    wch[w] = ch;
+    wlm[w] = lmc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float2 o = wom[0];
+    int c = wch[0], lm = wlm[0];
+    for (int k = 1; k < kFusedWarps; ++k) {
+      o = df_add(o, wom[k]);
+      c += wch[k];
+      lm += wlm[k];
+    }
+    I.omega_part[blockIdx.x] = o;
+    I.changed_part[blockIdx.x] = c;
+    I.lm_part[blockIdx.x] = lm;
+    __threadfence();
+    is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  // ---- the last CTA closes the iteration: cost and counts over the CTAs in
+  // CTA order, the trace entry, early stop, the barrier reset, and the
+  // support sort when a landmark label changed
+  griddep_launch();
+  __threadfence();
+  float2 o = make_float2(0.0f, 0.0f);
+  int c = 0, lm = 0;
+  if (w == 0) {
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      o = df_add(o, __ldcg(I.omega_part + b));
+      c += __ldcg(I.changed_part + b);
+      lm += __ldcg(I.lm_part + b);
+    }
+    o = warp_sum_df(o);
+    c = warp_sum_i32(c);
+    lm = warp_sum_i32(lm);
+  }
+  if (tid == 0) {
+    const int t = *I.trace_count;
+    I.trace_omega[t] = (double)o.x + (double)o.y;
+    I.trace_changed[t] = c;
+    *I.trace_count = t + 1;
+    if (early_stop && c == 0) *I.done = 1;
+    *I.ticket = 0u;
+    *I.bar = 0u;
+    wlm[0] = lm;
+  }
+  __syncthreads();
+  if (wlm[0] == 0) return;  // same landmark labels: same supports
+  int* const scr = reinterpret_cast<int*>(fdyn);  // every CTA is past its slots
+  sort_supports_cta(S, scr, scr + C, scr + 2 * C, scr + 2 * C + kFusedWarps * C);
+}
+
+// Grid and shared memory of the fused iteration for a block of Ni columns
+// of `esize`-byte values and nL landmark rows; false when it does not apply
+// (more than kFusedMaxC clusters, or a strip wider than one column per thread
+// with one CTA per SM).
+bool fused_shape(int Ni, int nL, int C, int esize, int n_sms, FusedShape* F, size_t* smem) {
+  if (C > kFusedMaxC || Ni < 1 || nL < 1) return false;
+  const int NC = 16 / esize;
+  F->groups = (int)ceil_div(Ni, NC);
+  F->n_cta = std::max(1, std::min(n_sms, (int)ceil_div(F->groups, 4)));
+  F->gmax = (int)ceil_div(F->groups, F->n_cta);
+  if (F->gmax * NC > kFusedThreads) return false;
+  F->R = std::max(1, std::min(kFusedThreads / F->gmax, nL));
+  size_t words = (size_t)(F->R + C) * F->gmax * NC + (nL <= kFusedPermCap ? (size_t)nL : 0);
+  const size_t sort_words = (size_t)(2 + kFusedWarps) * C + 32;
+  words = std::max(words, sort_words);
+  *smem = words * sizeof(float);
+  return *smem <= (size_t)kFusedMaxDynSmem;
+}
+
+template <typename T>
+static cudaError_t launch_iterate_t(const T* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                                    const float* kself, int32_t* u, float* margin, float* fhat_out,
+                                    double* ghat_out, int early_stop, int n_sms, cudaStream_t st,
+                                    const RescoreArgs& R) {
+  FusedShape F;
+  size_t smem = 0;
+  if (!fused_shape(Ni, S.nL, S.C, (int)sizeof(T), n_sms, &F, &smem)) return cudaErrorInvalidValue;
+  if (F.n_cta > I.fused_cap) return cudaErrorInvalidValue;  // gcta / partial-slot capacity
+  static const cudaError_t attr = cudaFuncSetAttribute(iterate_fused_kernel<T>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       kFusedMaxDynSmem);
+  if (attr != cudaSuccess) return attr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)F.n_cta);
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attrs[2];
+  attrs[0].id = cudaLaunchAttributeCooperative;
+  attrs[0].val.cooperative = 1;
+  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attrs[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attrs;
+  cfg.numAttrs = 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, iterate_fused_kernel<T>, KT, ldk, Ni, S, I, F, kself, u, margin,
+                                     fhat_out, ghat_out, early_stop, R);
+  if (e != cudaSuccess) {
+    // a cooperative launch that does not take the programmatic attribute
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, iterate_fused_kernel<T>, KT, ldk, Ni, S, I, F, kself, u, margin, fhat_out,
+                           ghat_out, early_stop, R);
+  }
+  return e;
+}
+cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
+                           int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R) {
+  return launch_iterate_t(KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st, R);
+}
+cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
+                           int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R) {
+  return launch_iterate_t(KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st, R);
+}
+
 // ----------------------------------------------------- Eq. 8 nearest medoid
 __global__ void nearest_kernel(const float* __restrict__ Kt, int64_t ldk, int Ni, int C,
                                const float* __restrict__ kself, const float* __restrict__ kmm,

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libkkm.so")
 KKM_RBF, KKM_RMSD, KKM_LINEAR = 0, 1, 2
 KKM_FP32, KKM_BF16, KKM_FP8 = 0, 1, 2
 PIPELINE = {"auto": 0, "serial": 1, "overlap": 2}
+ITERATION = {"auto": 0, "fused": 1, "split": 2}
 KKM_STRIDE, KKM_BLOCK = 0, 1
 KKM_ASSIGN_SUPPORTS, KKM_ASSIGN_MEDOIDS = 0, 1
 KIND = {"rbf": KKM_RBF, "rmsd": KKM_RMSD, "linear": KKM_LINEAR}
@@ -40,6 +41,7 @@ class kkm_kernel(ctypes.Structure):
 class kkm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sampling", ctypes.c_int32),
                 ("early_stop", ctypes.c_int32), ("pipeline", ctypes.c_int32),
+                ("iteration", ctypes.c_int32),
                 ("init_medoids", ctypes.POINTER(ctypes.c_int64)), ("stream", ctypes.c_void_p)]
 
 
@@ -251,7 +253,7 @@ class Model:
 # ------------------------------------------------------------- functions
 def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
             precision=KKM_FP32, sampling="stride", early_stop=True, init_medoids=None,
-            labels=True, stream=None, pipeline="auto"):
+            labels=True, stream=None, pipeline="auto", iteration="auto"):
     """kkm_fit of the C ABI.  Returns (labels or None, Model)."""
     lib = load()
     N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
@@ -263,6 +265,7 @@ def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
     opt.sampling = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
     opt.early_stop = 1 if early_stop else 0
     opt.pipeline = PIPELINE[pipeline] if isinstance(pipeline, str) else int(pipeline)
+    opt.iteration = ITERATION[iteration] if isinstance(iteration, str) else int(iteration)
     init_arr = None
     if init_medoids is not None:
         init_arr = np.ascontiguousarray(init_medoids, dtype=np.int64)
@@ -279,7 +282,7 @@ def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
 def kkm_fit_batch(problems, n_streams=0, stream=None, check=True):
     """kkm_fit_batch of the C ABI.  `problems` is a list of dicts with the
     kkm_fit arguments (X, C, B, s and optionally kind, sigma, n_atoms, iters,
-    seed, precision, sampling, early_stop, init_medoids, labels, pipeline).  Returns a
+    seed, precision, sampling, early_stop, init_medoids, labels, pipeline, iteration).  Returns a
     list of (labels or None, Model or None, status) in problem order; with
     check=True a failed problem raises KKMError instead."""
     lib = load()
@@ -319,6 +322,8 @@ def _fill_problem(q, p, keep):
     q.opt.early_stop = 1 if p.get("early_stop", True) else 0
     pl = p.get("pipeline", "auto")
     q.opt.pipeline = PIPELINE[pl] if isinstance(pl, str) else int(pl)
+    it = p.get("iteration", "auto")
+    q.opt.iteration = ITERATION[it] if isinstance(it, str) else int(it)
     if p.get("init_medoids") is not None:
         ia = np.ascontiguousarray(p["init_medoids"], dtype=np.int64)
         keep.append(ia)

@@ -157,13 +157,13 @@ def test_debug_step_rmsd(lib):
 
 # ----------------------------------------------------------- whole fits
 def _fit_pair(lib, X, C, B, s, iters, seed, kind="rbf", sig=None, n_atoms=0, sampling="stride",
-              early_stop=True, use_oracle_init=True):
+              early_stop=True, use_oracle_init=True, iteration="auto"):
     okind = {"rbf": O.KIND_RBF, "rmsd": O.KIND_RMSD, "linear": O.KIND_LINEAR}[kind]
     ref = O.fit(X.astype(np.float64), C, B, s, O.Kernel(okind, sig or 0.0, n_atoms), iters, seed,
                 early_stop=early_stop, sampling=sampling)
     init = ref["details"][0]["M_before"] if use_oracle_init else None
     lab, model = lib.kkm_fit(_dev(X), C, B, s, kind, sig or 0.0, n_atoms, iters, seed, sampling=sampling,
-                             early_stop=early_stop, init_medoids=init)
+                             early_stop=early_stop, init_medoids=init, iteration=iteration)
     return _np(lab), model, ref
 
 
@@ -193,11 +193,12 @@ def test_fit_exact_kernel_kmeans_2000x16(lib):
     _check_fit(lab, model, ref)
 
 
+@pytest.mark.parametrize("iteration", ["fused", "split"])
 @pytest.mark.parametrize("sampling", ["stride", "block"])
-def test_fit_minibatch_landmarks(lib, sampling):
+def test_fit_minibatch_landmarks(lib, sampling, iteration):
     X, _ = blobs(3001, 20, 6, workload=56)
     sig = _median_sigma(X)
-    lab, model, ref = _fit_pair(lib, X, 6, 3, 0.3, 15, seed=4, sig=sig, sampling=sampling)
+    lab, model, ref = _fit_pair(lib, X, 6, 3, 0.3, 15, seed=4, sig=sig, sampling=sampling, iteration=iteration)
     _check_fit(lab, model, ref)
 
 
@@ -218,17 +219,54 @@ def test_kmeanspp_picks(lib):
         assert np.array_equal(got, want)
 
 
-def test_fit_rmsd(lib):
+@pytest.mark.parametrize("iteration", ["fused", "split"])
+def test_fit_rmsd(lib, iteration):
     F, _ = md_trajectory(n_frames=1500, n_atoms=60, n_states=4, dwell=60.0, workload=59)
     X = F.reshape(1500, -1)
-    lab, model, ref = _fit_pair(lib, X, 4, 2, 0.2, 10, seed=2, kind="rmsd", sig=1.5, n_atoms=60)
+    lab, model, ref = _fit_pair(lib, X, 4, 2, 0.2, 10, seed=2, kind="rmsd", sig=1.5, n_atoms=60,
+                                iteration=iteration)
     _check_fit(lab, model, ref)
 
 
-def test_fit_linear_is_lloyd_on_device(lib):
+@pytest.mark.parametrize("iteration", ["fused", "split"])
+def test_fit_linear_is_lloyd_on_device(lib, iteration):
     X, _ = blobs(1200, 5, 4, workload=60)
-    lab, model, ref = _fit_pair(lib, X, 4, 1, 1.0, 15, seed=3, kind="linear", sig=0.0)
+    lab, model, ref = _fit_pair(lib, X, 4, 1, 1.0, 15, seed=3, kind="linear", sig=0.0, iteration=iteration)
     _check_fit(lab, model, ref)
+
+
+# ------------------------------------------------ fused iteration shapes
+def test_fused_iteration_many_clusters_ragged(lib):
+    """The fused iteration at its largest C (64) on a ragged mini-batch (1,237
+    samples: the last column group and strip are partial) against the oracle;
+    C = 65 is refused for KKM_ITER_FUSED and runs split under AUTO."""
+    X, _ = blobs(1237, 8, 40, workload=90)
+    sig = _median_sigma(X)
+    lab, model, ref = _fit_pair(lib, X, 64, 1, 0.6, 12, seed=5, sig=sig, iteration="fused")
+    _check_fit(lab, model, ref)
+    with pytest.raises(lib.KKMError) as e:
+        lib.kkm_fit(_dev(X), 65, 1, 0.6, "rbf", sig, iters=2, seed=5, iteration="fused")
+    assert e.value.status == lib.STATUS_EINVAL
+    lab, model, ref = _fit_pair(lib, X, 65, 1, 0.6, 6, seed=5, sig=sig)
+    _check_fit(lab, model, ref)
+
+
+def test_fused_iteration_matches_split_long_landmark_list(lib):
+    """More landmarks than the fused kernel stages in shared memory (9,000 >
+    8,192: the sorted list is read from global memory), and landmark labels
+    that change between iterations (supports re-sorted by the closing CTA):
+    the fused and split forms give the same trace to 1e-6 and the same labels
+    on all but near-tied rows."""
+    X, _ = blobs(20000, 4, 5, workload=91)
+    sig = _median_sigma(X)
+    runs = {it: lib.kkm_fit(_dev(X), 5, 1, 0.45, "rbf", sig, iters=12, seed=2, early_stop=False, iteration=it)
+            for it in ("fused", "split")}
+    (lf, mf), (ls, ms) = runs["fused"], runs["split"]
+    of, os_ = mf.trace()[0], ms.trace()[0]
+    assert of.shape == os_.shape == (12,)
+    assert np.max(np.abs(of - os_) / os_) <= 1e-6
+    assert np.mean(_np(lf) == _np(ls)) >= 0.999
+    assert mf.trace()[1].max() > 0  # labels did change during the loop
 
 
 def test_fit_median_bandwidth_inside(lib):

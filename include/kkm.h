@@ -72,15 +72,18 @@ typedef enum kkm_sampling { KKM_STRIDE = 0, KKM_BLOCK = 1 } kkm_sampling;
  * the same bits either way: the same kernels run on the same inputs.       */
 typedef enum kkm_pipeline { KKM_PIPE_AUTO = 0, KKM_PIPE_SERIAL = 1, KKM_PIPE_OVERLAP = 2 } kkm_pipeline;
 
-/* Launch form of one inner iteration (Eq. 15-17).  KKM_ITER_FUSED runs the
- * whole iteration in one cooperative launch: every CTA owns a strip of
- * sample columns over all landmark rows, so f_hat is finished where it is
- * summed, and one grid barrier makes g_hat (Eq. 16) available to every CTA.
- * It applies to C <= 64 and mini-batches of up to about 77,000 samples.
+/* Launch form of the inner loop (Eq. 15-17).  KKM_ITER_FUSED runs all the
+ * iterations of a mini-batch in one cooperative launch: every CTA owns a
+ * strip of sample columns over all landmark rows, so f_hat is finished where
+ * it is summed, and grid barriers make g_hat (Eq. 16) and the cost available
+ * to every CTA.  It applies to C <= 64 and mini-batches of up to about
+ * 77,000 samples (KKM_EINVAL otherwise).
  * KKM_ITER_SPLIT streams per-unit partial sums and finishes them in a second
- * launch.  KKM_ITER_AUTO takes the fused form where it applies.  The two
- * forms add the same values in different orders: labels agree above the
- * tolerance margin and distances to FP32 rounding.                          */
+ * launch (the two launches of an iteration chained by programmatic
+ * dependent launch).  KKM_ITER_AUTO takes the split form, the faster one on
+ * the benchmark workloads.  The two forms add the same values in different
+ * orders: labels agree above the tolerance margin and distances to FP32
+ * rounding.                                                                 */
 typedef enum kkm_iteration { KKM_ITER_AUTO = 0, KKM_ITER_FUSED = 1, KKM_ITER_SPLIT = 2 } kkm_iteration;
 
 /* Prototypes used by kkm_assign / kkm_cost: the sparse landmark centroids
@@ -308,7 +311,8 @@ kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d,
  *   Xb [Ni][d] mini-batch samples; L [nL] sorted local landmark indices
  *   (host); u_in [Ni] labels (host); precision KKM_FP32 or KKM_BF16 (the
  *   kernel block kkm_fit evaluates and stores for that precision, and on
- *   KKM_BF16 its FP32 near-tie re-score).  Outputs (host, each nullable):
+ *   KKM_BF16 its FP32 near-tie re-score); iteration a kkm_iteration (the
+ *   launch form of the step).  Outputs (host, each nullable):
  *   u_out [Ni], fhat_out [Ni][C] (Eq. 17 from the stored block, before any
  *   re-score; NaN where n_j = 0), margin_out [Ni] (second-best minus best
  *   distance), ghat_out [C] (Eq. 16; NaN where n_j = 0), n_out [C],
@@ -316,7 +320,7 @@ kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d,
  */
 kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d,
                           const int32_t* L, int32_t nL, const kkm_kernel* k,
-                          int32_t C, int32_t precision,
+                          int32_t C, int32_t precision, int32_t iteration,
                           const int32_t* u_in, int32_t* u_out,
                           float* fhat_out, float* margin_out, double* ghat_out,
                           int32_t* n_out, double* omega_out,

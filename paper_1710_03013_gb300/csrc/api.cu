@@ -584,6 +584,7 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.changed_part, parts));
   KKM_TRY(ws.alloc(&I.lm_part, parts));
   KKM_TRY(ws.alloc(&I.gcta, (int64_t)I.fused_cap * C));
+  KKM_TRY(ws.alloc(&I.facc, 2 * (C + 3)));
   KKM_TRY(ws.alloc(&I.bar, 1));
   KKM_TRY(ws.alloc(&I.err, 1));
   KKM_CK(cudaMemsetAsync(I.bar, 0, 4, ws.st));
@@ -739,27 +740,31 @@ static bool fused_applies(int Ni, int nL, int C, int esize) {
   return fused_shape(Ni, nL, C, esize, sm_count(), &F, &smem);
 }
 
-// One inner iteration (Alg. 1 lines 9-16; Eq. 15-17) over the block of the
-// buffer set b: fused, or the streaming partial sums and the assign.  Either
-// way the iteration closes on the device (trace, early stop, support re-sort).
-static kkm_status inner_iteration(const BlockMode& bm, const BlockBufs& b, int64_t ldk, int Ni, const Supports& S,
-                                  const IterState& I, bool fused, const float* kself, int32_t* u, float* margin,
-                                  float* fhat_out, double* ghat_out, int early_stop, const RescoreArgs& R,
-                                  cudaStream_t st) {
+// The inner loop of a mini-batch (Alg. 1 lines 9-16; Eq. 15-17) over the
+// block of the buffer set b: `iters` iterations fused in one launch, or per
+// iteration the streaming partial sums and the assign.  Either way every
+// iteration closes on the device (trace, early stop, support re-sort).
+static kkm_status inner_loop(const BlockMode& bm, const BlockBufs& b, int64_t ldk, int Ni, const Supports& S,
+                             const IterState& I, bool fused, int iters, const float* kself, int32_t* u,
+                             float* margin, float* fhat_out, double* ghat_out, int early_stop, const RescoreArgs& R,
+                             cudaStream_t st) {
   if (fused) {
     KKM_RUN("iterate", st,
-            bm.kt_half ? launch_iterate(b.KTh, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop,
+            bm.kt_half ? launch_iterate(b.KTh, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop,
                                         sm_count(), st, R)
-                       : launch_iterate(b.KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop,
+                       : launch_iterate(b.KT, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop,
                                         sm_count(), st, R));
     return KKM_OK;
   }
-  KKM_RUN("fhat_partial", st,
-          bm.kt_half ? launch_fhat_partial(b.KTh, ldk, Ni, S, I, st) : launch_fhat_partial(b.KT, ldk, Ni, S, I, st));
-  // the assign's last CTA closes the iteration and re-sorts the supports when
-  // a landmark label changed
-  KKM_RUN("assign", st,
-          launch_assign(ldk, Ni, S, I, kself, u, margin, nullptr, fhat_out, ghat_out, early_stop, /*trace=*/1, st, R));
+  for (int t = 0; t < iters; ++t) {
+    KKM_RUN("fhat_partial", st,
+            bm.kt_half ? launch_fhat_partial(b.KTh, ldk, Ni, S, I, st) : launch_fhat_partial(b.KT, ldk, Ni, S, I, st));
+    // the assign's last CTA closes the iteration and re-sorts the supports
+    // when a landmark label changed
+    KKM_RUN("assign", st,
+            launch_assign(ldk, Ni, S, I, kself, u, margin, nullptr, fhat_out, ghat_out, early_stop, /*trace=*/1, st,
+                          R));
+  }
   return KKM_OK;
 }
 
@@ -1118,14 +1123,16 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
     I.flag_tau = bm.flag_tau(sp);
     const RescoreArgs R = rescore_args(sp, bk);
-    const bool fused = opt.iteration != KKM_ITER_SPLIT && fused_applies(Ni, nL, C, kt_half ? 2 : 4);
+    // AUTO takes the split form: measured faster on the benchmark fits (the
+    // fused loop's narrow column strips cost more L2 sector traffic than the
+    // barriers save)
+    const bool fused = opt.iteration == KKM_ITER_FUSED && fused_applies(Ni, nL, C, kt_half ? 2 : 4);
     if (opt.iteration == KKM_ITER_FUSED && !fused)
       return invalid("KKM_ITER_FUSED does not apply to this shape (C <= 64 and a mini-batch of at most one "
                      "column per thread of one CTA per SM)");
     NvtxRange nv_loop("inner loop");
-    for (int t = 0; t < iters; ++t)                                           // Alg. 1 lines 9-16
-      KKM_TRY(inner_iteration(bm, bk, ldk, Ni, S, I, fused, kself, u, nullptr, nullptr, nullptr, opt.early_stop, R,
-                              ms));
+    KKM_TRY(inner_loop(bm, bk, ldk, Ni, S, I, fused, iters, kself, u, nullptr, nullptr, nullptr,  // Alg. 1 lines 9-16
+                       opt.early_stop, R, ms));
     I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
     IterState Ifin = I;
@@ -1422,7 +1429,8 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
 // kkm_debug_step (teacher-forced inner iteration)
 // ======================================================================
 static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, const int32_t* L, int32_t nL,
-                                  const kkm_kernel* k, int32_t C, int32_t precision, const int32_t* u_in,
+                                  const kkm_kernel* k, int32_t C, int32_t precision, int32_t iteration,
+                                  const int32_t* u_in,
                                   int32_t* u_out, float* fhat_out, float* margin_out, double* ghat_out,
                                   int32_t* n_out, double* omega_out, int32_t* changed_out, cudaStream_t st) {
   KernelSpec sp;
@@ -1432,6 +1440,8 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   if (nL < 1 || nL > Ni || !L || !u_in || !Xb_in) return invalid("bad landmarks or NULL pointer");
   if (precision != KKM_FP32 && precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
   if (precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  if (iteration != KKM_ITER_AUTO && iteration != KKM_ITER_FUSED && iteration != KKM_ITER_SPLIT)
+    return invalid("unknown iteration form");
   sp.precision = precision;
   if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
   for (int q = 0; q < nL; ++q)
@@ -1482,8 +1492,9 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   lb.I.keep_rows = 0;
   lb.I.flag_tau = bm.flag_tau(sp);
   const RescoreArgs R = rescore_args(sp, b);
-  const bool fused = fused_applies((int)Ni, nL, C, bm.kt_half ? 2 : 4);
-  KKM_TRY(inner_iteration(bm, b, ldk, (int)Ni, lb.S, lb.I, fused, kself, u, mg, fh, gh, 0, R, st));
+  const bool fused = iteration == KKM_ITER_FUSED && fused_applies((int)Ni, nL, C, bm.kt_half ? 2 : 4);
+  if (iteration == KKM_ITER_FUSED && !fused) return invalid("KKM_ITER_FUSED does not apply to this shape");
+  KKM_TRY(inner_loop(bm, b, ldk, (int)Ni, lb.S, lb.I, fused, 1, kself, u, mg, fh, gh, 0, R, st));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));
   if (margin_out) KKM_CK(cudaMemcpyAsync(margin_out, mg, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
@@ -1675,13 +1686,13 @@ kkm_status kkm_median_bandwidth(const float* X, int64_t N, int64_t d, const kkm_
 }
 
 kkm_status kkm_debug_step(const float* Xb, int64_t Ni, int64_t d, const int32_t* L, int32_t nL, const kkm_kernel* k,
-                          int32_t C, int32_t precision, const int32_t* u_in, int32_t* u_out, float* fhat_out,
-                          float* margin_out, double* ghat_out, int32_t* n_out, double* omega_out,
+                          int32_t C, int32_t precision, int32_t iteration, const int32_t* u_in, int32_t* u_out,
+                          float* fhat_out, float* margin_out, double* ghat_out, int32_t* n_out, double* omega_out,
                           int32_t* changed_out, void* stream) {
   set_error("");
   return guarded([&] {
-    return debug_step_impl(Xb, Ni, d, L, nL, k, C, precision, u_in, u_out, fhat_out, margin_out, ghat_out, n_out,
-                           omega_out, changed_out, (cudaStream_t)stream);
+    return debug_step_impl(Xb, Ni, d, L, nL, k, C, precision, iteration, u_in, u_out, fhat_out, margin_out, ghat_out,
+                           n_out, omega_out, changed_out, (cudaStream_t)stream);
   });
 }
 

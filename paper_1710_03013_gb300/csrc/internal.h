@@ -286,7 +286,9 @@ struct IterState {
   int n_strips;
   // fused iteration (launch_iterate): per-CTA g_hat shares, the grid barrier
   // counter (zero between launches) and the error word of its bounded wait
-  float2* gcta = nullptr;           // [fused_cap][C] double-float
+  float2* gcta = nullptr;           // [fused_cap][C] double-float (linear kernel)
+  unsigned long long* facc = nullptr;  // [2][C + 3] fixed-point shares (Gaussian kernels)
+  int fom_shift = 0;                // fixed-point scale of the cost shares (set per launch)
   uint32_t* bar = nullptr;          // [1]
   int32_t* err = nullptr;           // [1]
   int fused_cap = 0;                // CTAs the fused buffers hold (omega_part etc. hold at least as many)
@@ -326,11 +328,12 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st, const RescoreArgs& R = RescoreArgs());
 
-// One whole inner iteration in one cooperative launch (f_hat, g_hat, d,
-// argmin, margin, re-score, Omega, trace, support re-sort): one CTA per SM
-// at most, each owning a strip of columns over every landmark row.  Applies
-// when fused_shape() says so (C <= kFusedMaxC, a strip of at most one column
-// per thread); *I.err becomes 1 if its grid barrier gave up.
+// The whole inner loop of a mini-batch (up to `iters` iterations: f_hat,
+// g_hat, d, argmin, margin, re-score, Omega, trace, early stop, support
+// re-sort) in one cooperative launch of at most one CTA per SM, each owning a
+// strip of columns over every landmark row.  Applies when fused_shape() says
+// so (C <= kFusedMaxC, a strip of at most one column per thread); *I.err
+// becomes 1 if one of its bounded grid-barrier waits gave up.
 constexpr int kFusedMaxC = 64;
 constexpr int kFusedMaxDynSmem = 200 * 1024;
 struct FusedShape {
@@ -340,10 +343,10 @@ struct FusedShape {
   int R;       // row streams of a CTA
 };
 bool fused_shape(int Ni, int nL, int C, int esize, int n_sms, FusedShape* F, size_t* smem);
-cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                            const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
                            int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R = RescoreArgs());
-cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                            const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
                            int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R = RescoreArgs());
 

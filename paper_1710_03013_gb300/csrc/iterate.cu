@@ -860,16 +860,26 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                     I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
 }
 
-// ------------------------------------------------- fused inner iteration
-// One launch per inner iteration (Eq. 15-17): every CTA owns a strip of
-// sample columns of the block and streams ALL landmark rows of that strip, in
-// the label-sorted order of `perm`, so the f_hat numerators of its columns
-// are complete inside the CTA (no partial sums leave it).  The only quantity
-// that needs every CTA is g_hat (Eq. 16, the landmark columns of all strips):
-// each CTA writes its per-cluster share, the grid meets at one barrier, and
-// then every CTA forms g_hat in the same fixed order and finishes its columns
-// -- distances, argmin (lowest j on ties), margin, near-tie re-score, labels,
-// cost partials.  The last CTA to finish closes the iteration as assign does.
+// ------------------------------------------------- fused inner loop
+// The inner loop of one mini-batch (Eq. 15-17, Alg. 1 lines 9-16) in one
+// cooperative launch.  Every CTA owns a strip of sample columns of the block
+// and streams ALL landmark rows of that strip, in the label-sorted order of
+// `perm`, so the f_hat numerators of its columns are complete inside the CTA
+// (no partial sums leave it).  Per iteration:
+//   A  stream the strip; per-cluster g_hat shares of its landmark columns;
+//   -- grid barrier 1 (arrive; e_lj = K_ll - 2 f_hat_lj while waiting);
+//   B  g_hat (Eq. 16) from the shares of every CTA, the same value in every
+//      CTA; d_lj = e_lj + g_hat_j, argmin (lowest j on ties), margin,
+//      near-tie re-score, changed landmark labels, cost and counts;
+//   -- grid barrier 2;
+//   C  every CTA reads the iteration's cost and counts; CTA 0 writes the
+//      trace entry; with early stop a pass without change ends the loop in
+//      every CTA; if a landmark label changed, CTA 0 re-sorts the supports and
+//      a third barrier publishes them.
+// For the Gaussian kernels (values in [0, 1]) the shares of g_hat and of the
+// cost are added as fixed-point integers (exact, so the same bits in any
+// order) into accumulators that alternate between iterations; for the linear
+// kernel each CTA writes its shares and every CTA adds them in CTA order.
 //
 // Inside a CTA: thread t takes column group g = t % gmax (16 bytes of
 // columns) and row stream r = t / gmax; stream r walks the contiguous rows
@@ -877,47 +887,52 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
 // per segment it is in, and flushes it to the shared slot r + j when it
 // leaves segment j.  Streams cover the rows in order, so the slots of
 // different (stream, segment) pairs are distinct, and the numerator of
-// segment j is the sum of its slots in stream order (fixed: bit-reproducible).
+// segment j is the sum of its slots in stream order: every sum has a fixed
+// order, results are bit-reproducible.  The rows of a thread reach shared
+// memory through a ring of asynchronous copies that runs on into the next
+// iteration's rows (the block and, unless the supports change, the row
+// order are the same), so the loads of iteration t+1 are in flight during
+// the barriers of iteration t; a support change drains and refills it.
 //
-// The barrier needs every CTA resident at once: the kernel is launched as a
-// cooperative grid of at most one CTA per SM.  Its wait is bounded; when the
-// bound is hit the kernel records an error and returns.
+// The barriers need every CTA resident at once: the kernel is launched as a
+// cooperative grid of at most one CTA per SM.  Every wait is bounded; when a
+// bound is hit the kernel records an error and every CTA returns.
 constexpr int kFusedThreads = 512;
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr int kFusedDepth = 8;          // rows loaded before their additions
+constexpr int kFusedDepth = 16;         // rows in flight per thread (asynchronous copies to shared memory)
 constexpr int kFusedPermCap = 8192;     // sorted landmark list staged in shared memory up to this size
 constexpr int kFusedCandCap = 1024;     // re-score pairs listed per round
-constexpr unsigned kFusedSpinLimit = 1u << 24;  // barrier polls (>= ~1.6 s with the 100 ns back-off)
+constexpr unsigned kFusedSpinLimit = 1u << 25;  // polls per barrier (>= ~1 s with the 32 ns back-off)
+constexpr int kFusedCtaPerLane = 8;     // per-CTA values a lane loads in the cross-CTA sums (<= 256 CTAs)
 
-// One 16-byte load of a block row (FP32: 4 values, FP16: 8) with an L2
-// eviction-priority policy, kept raw until its additions.
-template <typename T>
-struct Raw16;
-template <>
-struct Raw16<float> {
-  float v[4];
-  __device__ __forceinline__ void load(const float* p, uint64_t pol) { ld16_policy(p, pol, v); }
-  __device__ __forceinline__ void zero() { v[0] = v[1] = v[2] = v[3] = 0.0f; }
-  __device__ __forceinline__ void add_to(float (&acc)[4]) const {
+// 16 bytes of a block row (FP32: 4 values, FP16: 8) added to the running
+// sums, read from the thread's slot of the copy ring in shared memory.
+__device__ __forceinline__ void add16(const float* p, float (&acc)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  acc[0] += v.x;
+  acc[1] += v.y;
+  acc[2] += v.z;
+  acc[3] += v.w;
+}
+__device__ __forceinline__ void add16(const float* p, float (&acc)[8]) {
+  const uint4 x = *reinterpret_cast<const uint4*>(p);
+  const uint32_t wds[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += v[c];
+  for (int c = 0; c < 4; ++c) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&wds[c]));
+    acc[2 * c] += f.x;
+    acc[2 * c + 1] += f.y;
   }
-};
-template <>
-struct Raw16<__half> {
-  uint4 x;
-  __device__ __forceinline__ void load(const __half* p, uint64_t pol) { ld16_policy(p, pol, x); }
-  __device__ __forceinline__ void zero() { x = make_uint4(0u, 0u, 0u, 0u); }
-  __device__ __forceinline__ void add_to(float (&acc)[8]) const {
-    const uint32_t wds[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&wds[c]));
-      acc[2 * c] += f.x;
-      acc[2 * c + 1] += f.y;
-    }
-  }
-};
+}
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 eviction-priority
+// policy), its commit group and the wait for all but the newest N groups.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint64_t pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
@@ -927,20 +942,64 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 // stream of row k when nL rows are cut into R contiguous streams
 // [floor(r nL / R), floor((r+1) nL / R))
-__device__ __forceinline__ int fused_stream_of(int k, int nL, int R) {
-  return min(R - 1, (int)((((int64_t)k + 1) * R - 1) / nL));
+__host__ __device__ inline int fused_stream_of(int k, int nL, int R) {
+  const int r = (int)((((int64_t)k + 1) * R - 1) / nL);
+  return r < R - 1 ? r : R - 1;
 }
+
+// Offset (in 4-byte words, a multiple of 4) of the copy ring in the fused
+// kernel's dynamic shared memory: after the slots and the staged landmark list.
+__host__ __device__ inline size_t fused_ring_offset(int R, int C, int gmax, int NC, int perm_words) {
+  return ((size_t)(R + C) * gmax * NC + (size_t)perm_words + 3) & ~(size_t)3;
+}
+
+// Grid barrier of the cooperative launch on *bar (zeroed by the host before
+// the launch; it only grows during it): every CTA syncs, its thread 0 makes
+// the CTA's writes visible and arrives; later it waits for `target` arrivals
+// and the CTA syncs again.  The wait gives up after a bound, or at once when
+// another CTA already gave up (*err), and then returns false everywhere.
+__device__ __forceinline__ void fused_arrive(unsigned* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+  }
+}
+__device__ __forceinline__ bool fused_wait(unsigned* bar, unsigned target, int* err, int* flag_sh) {
+  if (threadIdx.x == 0) {
+    unsigned polls = 0;
+    *flag_sh = 1;
+    while (ld_acquire_u32(bar) < target) {
+      __nanosleep(32);
+      if (++polls > kFusedSpinLimit || ld_acquire_u32(reinterpret_cast<const unsigned*>(err)) != 0) {
+        atomicExch(err, 1);
+        *flag_sh = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *flag_sh != 0;
+}
+
+// Fixed-point accumulators of the fused loop (Gaussian kernels), two sets
+// alternating between iterations: [set][C] g_hat numerators, then the cost,
+// the changed-label and the changed-landmark counts of each set.
+__host__ __device__ inline int fused_acc_words(int C) { return 2 * (C + 3); }
 
 template <typename T>
 __global__ void __launch_bounds__(kFusedThreads, 1)
 iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, IterState I, FusedShape F,
-                     const float* __restrict__ kself, int32_t* __restrict__ u, float* __restrict__ margin,
-                     float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop, RescoreArgs R) {
+                     int iters, const float* __restrict__ kself, int32_t* __restrict__ u,
+                     float* __restrict__ margin, float* __restrict__ fhat_out, double* __restrict__ ghat_out,
+                     int early_stop, RescoreArgs R) {
   constexpr int NC = 16 / (int)sizeof(T);
   extern __shared__ __align__(16) float fdyn[];
   __shared__ int seg_sh[kFusedMaxC + 1];
   __shared__ int nj_sh[kFusedMaxC];
   __shared__ int first_sh[kFusedMaxC];
+  __shared__ int rhi_sh[kFusedMaxC];
   __shared__ int j0_sh[kFusedThreads];
   __shared__ double gh_sh[kFusedMaxC];
   __shared__ float ghf_sh[kFusedMaxC];
@@ -948,7 +1007,9 @@ iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, 
   __shared__ int wch[kFusedWarps], wlm[kFusedWarps];
   __shared__ int scan_sh[32];
   __shared__ int cand[kFusedCandCap];
-  __shared__ int is_last;
+  __shared__ int clab_sh[kFusedThreads];
+  __shared__ double tot_om;
+  __shared__ int tot_ch, tot_lm, ok_sh;
   griddep_wait();
   if (I.done && *I.done) return;  // early stop: the same flag in every CTA
   const int C = S.C, nL = S.nL;
@@ -960,238 +1021,225 @@ iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, 
   const int ncol = ng * NC;  // this CTA's columns: col0 + [0, ncol)
   const int col0 = gb * NC;
   const float inf = __int_as_float(0x7f800000);
+  const bool fixed = I.gfix != nullptr;  // Gaussian kernel: fixed-point shares
+  unsigned long long* const facc = I.facc;
+  const double gscale = ldexp(1.0, I.gfix_shift), oscale = ldexp(1.0, I.fom_shift);
   float* const slots = fdyn;  // [(RS + C)][gmax][NC]
-  int* const perm_sh = reinterpret_cast<int*>(fdyn + (size_t)(RS + C) * gmax * NC);
   const bool perm_in_sh = nL <= kFusedPermCap;
-  for (int j = tid; j <= C; j += kFusedThreads) seg_sh[j] = S.seg_off[j];
-  for (int j = tid; j < C; j += kFusedThreads) nj_sh[j] = S.n_j[j];
-  if (perm_in_sh)
-    for (int k = tid; k < nL; k += kFusedThreads) perm_sh[k] = S.perm[k];
-  __syncthreads();
-  // segment of the first row of every stream (empty segments skipped), and
-  // the slot that receives each segment's whole numerator (its first piece)
-  for (int r = tid; r < RS; r += kFusedThreads) {
-    const int a = (int)(((int64_t)r * nL) / RS);
-    int j = 0;
-    while (j < C - 1 && seg_sh[j + 1] <= a) ++j;
-    j0_sh[r] = j;
-  }
-  for (int j = tid; j < C; j += kFusedThreads)
-    first_sh[j] = nj_sh[j] > 0 ? fused_stream_of(seg_sh[j], nL, RS) + j : -1;
-  __syncthreads();
+  int* const perm_sh = reinterpret_cast<int*>(fdyn + (size_t)(RS + C) * gmax * NC);
+  // the copy ring: [kFusedDepth][kFusedThreads] 16-byte slots, 16-byte aligned
+  float* const ring = fdyn + fused_ring_offset(RS, C, gmax, NC, perm_in_sh ? nL : 0);
+  const int t0 = *I.trace_count;  // trace entries before this loop (written by CTA 0 only)
+  unsigned bar_target = 0;
 
-  // ---- phase A: stream the strip, one running sum per (stream, segment)
-  {
-    const int* permp = perm_in_sh ? perm_sh : S.perm;
-    uint64_t keep, strm;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(strm));
-    const int g = tid % gmax, r = tid / gmax;
-    if (r < RS && g < ng) {
-      const int a = (int)(((int64_t)r * nL) / RS), e = (int)(((int64_t)(r + 1) * nL) / RS);
-      if (a < e) {
-        const T* base = KT + (int64_t)col0 + (int64_t)g * NC;
-        int j = j0_sh[r];
-        int jend = seg_sh[j + 1];
-        float acc[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
-        auto flush = [&](int jj) {
-          float4* dst = reinterpret_cast<float4*>(slots + ((size_t)(r + jj) * gmax + g) * NC);
-#pragma unroll
-          for (int c = 0; c < NC; c += 4) dst[c / 4] = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
-#pragma unroll
-          for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
-        };
-        for (int k = a; k < e; k += kFusedDepth) {
-          Raw16<T> v[kFusedDepth];
-#pragma unroll
-          for (int q = 0; q < kFusedDepth; ++q) {
-            if (k + q < e) {
-              const int row = permp[k + q];
-              v[q].load(base + (int64_t)row * ldk, row < I.keep_rows ? keep : strm);
-            } else {
-              v[q].zero();
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < kFusedDepth; ++q) {
-            if (k + q < e) {
-              while (k + q >= jend) {  // the row opens a later segment
-                flush(j);
-                ++j;
-                jend = seg_sh[j + 1];
-              }
-              v[q].add_to(acc);
-            }
-          }
-        }
-        flush(j);
-      }
-    }
-  }
-  __syncthreads();
-  // every segment's numerator: its pieces in stream order, into its first slot
-  for (int e = tid; e < C * ncol; e += kFusedThreads) {
-    const int j = e / ncol, q = e - j * ncol;
-    if (nj_sh[j] == 0) continue;
-    const int r0 = fused_stream_of(seg_sh[j], nL, RS), r1 = fused_stream_of(seg_sh[j + 1] - 1, nL, RS);
-    const int gq = q / NC, cq = q - gq * NC;
-    float s = 0.0f;
-    for (int r = r0; r <= r1; ++r) s += slots[((size_t)(r + j) * gmax + gq) * NC + cq];
-    slots[((size_t)(r0 + j) * gmax + gq) * NC + cq] = s;
-  }
-  __syncthreads();
-  // this CTA's share of the g_hat numerators (Eq. 16): landmark columns of
-  // each cluster, double-float, columns in order within a fixed lane tree
-  if (S.col_label) {
-    for (int j = w; j < C; j += kFusedWarps) {
-      float2 gs = make_float2(0.0f, 0.0f);
-      if (nj_sh[j] > 0) {
-        const float* fj = slots + (size_t)first_sh[j] * gmax * NC;
-        for (int q = lane; q < ncol; q += 32) {
-          const int l = col0 + q;
-          if (l < Ni && __ldg(S.col_label + l) == j) gs = df_add(gs, make_float2(fj[q], 0.0f));
-        }
-      }
-      gs = warp_sum_df(gs);
-      if (lane == 0) I.gcta[(size_t)blockIdx.x * C + j] = gs;
-    }
-    __threadfence();  // each writer's shares visible to the grid before the barrier
-  }
-  // grid barrier (cooperative launch: every CTA is resident)
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    atomicAdd(I.bar, 1u);
-    unsigned polls = 0;
-    is_last = 0;
-    while (ld_acquire_u32(I.bar) < gridDim.x) {
-      __nanosleep(100);
-      if (++polls > kFusedSpinLimit) {
-        atomicExch(I.err, 1);
-        is_last = -1;
-        break;
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  if (is_last < 0) return;  // the barrier gave up: the host reports KKM_ETIMEOUT
-  // g_hat of every cluster: the CTA shares summed in CTA order (the same
-  // value in every CTA); given (an assign against a model) when ghat_in is set
-  for (int j = tid; j < C; j += kFusedThreads) {
-    const int n = nj_sh[j];
-    double gv = __longlong_as_double(0x7ff8000000000000LL);
-    if (n > 0) {
-      if (I.ghat_in) {
-        gv = I.ghat_in[j];
-      } else {
-        double a2 = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-          const float2 v = __ldcg(I.gcta + (size_t)b * C + j);
-          a2 += (double)v.x + (double)v.y;
-        }
-        gv = a2 / ((double)n * (double)n);
-      }
-    }
-    gh_sh[j] = gv;
-    ghf_sh[j] = (float)gv;
-  }
-  __syncthreads();
-  if (blockIdx.x == 0 && ghat_out)
-    for (int j = tid; j < C; j += kFusedThreads) ghat_out[j] = gh_sh[j];
-
-  // ---- phase B: one column per thread
+  // this thread's column in phase B (column col0 + tid): its inputs, loaded
+  // once, and its label, kept in a register through the loop
   const int q = tid;
   const int l = col0 + q;
   const bool mine = q < ncol && l < Ni;
-  const float ks = (mine && kself) ? kself[l] : 1.0f;
-  float best = inf, second = inf;
-  int bj = 0;
-  bool flagged = false;
+  float ks = 1.0f;
+  int cur_u = 0, cord = -1;
   if (mine) {
-    for (int j = 0; j < C; ++j) {
-      if (nj_sh[j] == 0) {
-        if (fhat_out) fhat_out[(int64_t)l * C + j] = __int_as_float(0x7fc00000);
-        continue;
-      }
-      float* fp = slots + (size_t)first_sh[j] * gmax * NC + q;
-      const float fh = *fp / (float)nj_sh[j];
-      if (fhat_out) fhat_out[(int64_t)l * C + j] = fh;
-      const float dj = ks - 2.0f * fh + ghf_sh[j];
-      *fp = dj;  // the slot now holds d_lj
-      if (dj < best) {  // lowest j on ties
-        second = best;
-        best = dj;
-        bj = j;
-      } else if (dj < second) {
-        second = dj;
-      }
-    }
-    if (R.Xi && I.flag_tau > 0.0f && second < inf)
-      flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + ghf_sh[bj]);
+    if (kself) ks = kself[l];
+    cur_u = u[l];
+    if (S.col_ord) cord = S.col_ord[l];
   }
-  // near-tie re-score: candidate (column, cluster) pairs of the flagged
-  // columns, each re-scored by one warp from exact FP32 kernel values of its
-  // support (one landmark per lane, then a fixed xor tree); pairs are listed
-  // in rounds of kFusedCandCap in (column, cluster) order
-  if (__syncthreads_or(flagged)) {
-    const float b0 = best, scale = ks + ghf_sh[bj];
-    auto is_cand = [&](int j) {
-      if (nj_sh[j] == 0) return false;
-      const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
-      return dj - b0 < I.flag_tau * fmaxf(fabsf(dj), scale);
-    };
-    int cnt = 0;
-    if (flagged)
-      for (int j = 0; j < C; ++j) cnt += is_cand(j);
-    int total;
-    const int off = block_excl_scan(cnt, scan_sh, &total);
-    for (int base = 0; base < total; base += kFusedCandCap) {
-      if (flagged && off + cnt > base && off < base + kFusedCandCap) {
-        int k = off;
-        for (int j = 0; j < C; ++j)
-          if (is_cand(j)) {
-            if (k >= base && k < base + kFusedCandCap) cand[k - base] = (q << 8) | j;
-            ++k;
-          }
+  // this thread's stream of the block: rows [ra, re) of the sorted list,
+  // column group g; the copy cursor (it_i, k_i) runs ahead of the reads
+  const int g = tid % gmax, r = tid / gmax;
+  const bool streams = r < RS && g < ng;
+  const int ra = streams ? (int)(((int64_t)r * nL) / RS) : 0;
+  const int re = streams ? (int)(((int64_t)(r + 1) * nL) / RS) : 0;
+  const T* const base = KT + (int64_t)col0 + (int64_t)g * NC;
+  const uint32_t ring0 = smem_u32(ring + (size_t)tid * 4);  // slot s at ring0 + s * kFusedThreads * 16
+  const int keep_rows = I.keep_rows;
+  uint64_t keep, strm;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(strm));
+  int it_i = 0, k_i = ra, slot_i = 0;  // next copy: iteration it_i, row k_i, ring slot slot_i
+  int slot_r = 0;                      // next read: ring slot
+  auto issue_next = [&]() {
+    if (streams && re > ra && it_i < iters) {
+      // the global list is re-sorted inside the launch: read it past L1
+      const int row = perm_in_sh ? perm_sh[k_i] : __ldcg(S.perm + k_i);
+      cp_async16(ring0 + (uint32_t)slot_i * kFusedThreads * 16u, base + (int64_t)row * ldk,
+                 row < keep_rows ? keep : strm);
+      slot_i = (slot_i + 1) & (kFusedDepth - 1);
+      if (++k_i == re) {
+        k_i = ra;
+        ++it_i;
       }
-      __syncthreads();
-      const int np = min(kFusedCandCap, total - base);
-      for (int p = w; p < np; p += kFusedWarps) {
-        const int qq = cand[p] >> 8, j = cand[p] & 255;
-        const int ir = col0 + qq;
-        const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
-        const float ni = R.nXi[ir];
-        const float ksr = kself ? kself[ir] : 1.0f;
-        const int k0 = seg_sh[j], k1 = seg_sh[j + 1];
-        float acc = 0.0f;
-        for (int kk = k0 + lane; kk < k1; kk += 32) {
-          const int k = S.perm[kk];
-          const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
-          float dot = 0.0f;
-          for (int c = 0; c < (R.dp >> 2); ++c) {
-            const float4 a4 = __ldg(xi + c), b4 = __ldg(xl + c);
-            dot = fmaf(a4.x, b4.x, fmaf(a4.y, b4.y, fmaf(a4.z, b4.z, fmaf(a4.w, b4.w, dot))));
-          }
-          float kv;
-          if (R.kind == DK_LINEAR) kv = dot;
-          else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
-          acc += kv;
-        }
-        acc = warp_sum_f32(acc);
-        if (lane == 0) slots[(size_t)first_sh[j] * gmax * NC + qq] = ksr - 2.0f * (acc / (float)(k1 - k0)) + ghf_sh[j];
-      }
-      __syncthreads();
     }
-    if (flagged) {  // argmin and margin over the updated distances
-      best = inf;
-      second = inf;
+    cp_async_commit();  // one group per call, empty or not
+  };
+
+  bool reload = true;  // the support tables in shared memory are stale
+  int t = 0;
+  for (; t < iters; ++t) {
+    if (reload) {
+      // the rows in flight (if any) follow the old order: drain, reload, refill
+      cp_async_wait<0>();
+      __syncthreads();
+      for (int j = tid; j <= C; j += kFusedThreads) seg_sh[j] = __ldcg(S.seg_off + j);
+      for (int j = tid; j < C; j += kFusedThreads) nj_sh[j] = __ldcg(S.n_j + j);
+      if (perm_in_sh)
+        for (int k = tid; k < nL; k += kFusedThreads) perm_sh[k] = __ldcg(S.perm + k);
+      clab_sh[q] = (mine && S.col_label) ? __ldcg(S.col_label + l) : -1;
+      __syncthreads();
+      // segment of the first row of every stream (empty segments skipped);
+      // each segment's first and last stream, and its whole numerator's slot
+      for (int rr = tid; rr < RS; rr += kFusedThreads) {
+        const int a = (int)(((int64_t)rr * nL) / RS);
+        int j = 0;
+        while (j < C - 1 && seg_sh[j + 1] <= a) ++j;
+        j0_sh[rr] = j;
+      }
+      for (int j = tid; j < C; j += kFusedThreads) {
+        first_sh[j] = nj_sh[j] > 0 ? fused_stream_of(seg_sh[j], nL, RS) + j : -1;
+        rhi_sh[j] = nj_sh[j] > 0 ? fused_stream_of(seg_sh[j + 1] - 1, nL, RS) : -1;
+      }
+      __syncthreads();
+      it_i = t;
+      k_i = ra;
+      slot_i = slot_r = 0;
+#pragma unroll 1
+      for (int qq = 0; qq < kFusedDepth; ++qq) issue_next();
+      reload = false;
+    }
+
+    // ---- phase A: stream the strip, one running sum per (stream, segment);
+    // each row is read from the ring once its copy has landed, then the copy
+    // kFusedDepth rows ahead (possibly of the next iteration) takes its slot
+    if (streams && ra < re) {
+      int j = j0_sh[r];
+      int jend = seg_sh[j + 1];
+      float acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+      auto flush = [&](int jj) {
+        float4* dst = reinterpret_cast<float4*>(slots + ((size_t)(r + jj) * gmax + g) * NC);
+#pragma unroll
+        for (int c = 0; c < NC; c += 4) dst[c / 4] = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
+      };
+      for (int k = ra; k < re; ++k) {
+        cp_async_wait<kFusedDepth - 1>();  // row k has landed
+        while (k >= jend) {  // the row opens a later segment
+          flush(j);
+          ++j;
+          jend = seg_sh[j + 1];
+        }
+        add16(ring + (size_t)tid * 4 + (size_t)slot_r * kFusedThreads * 4, acc);
+        slot_r = (slot_r + 1) & (kFusedDepth - 1);
+        issue_next();  // after the read of the slot it refills
+      }
+      flush(j);
+    }
+    __syncthreads();
+    // every segment's numerator: its pieces in stream order, into its first slot
+    for (int e = tid; e < C * ncol; e += kFusedThreads) {
+      const int j = e / ncol, qq = e - j * ncol;
+      if (nj_sh[j] == 0) continue;
+      const int r0 = first_sh[j] - j, r1 = rhi_sh[j];
+      const int gq = qq / NC, cq = qq - gq * NC;
+      float s = 0.0f;
+      for (int rr = r0; rr <= r1; ++rr) s += slots[((size_t)(rr + j) * gmax + gq) * NC + cq];
+      slots[((size_t)(r0 + j) * gmax + gq) * NC + cq] = s;
+    }
+    __syncthreads();
+    // this CTA's share of the g_hat numerators (Eq. 16): landmark columns of
+    // each cluster, double-float, columns in order within a fixed lane tree
+    if (S.col_label) {
+      for (int j = w; j < C; j += kFusedWarps) {
+        float2 gs = make_float2(0.0f, 0.0f);
+        if (nj_sh[j] > 0) {
+          const float* fj = slots + (size_t)first_sh[j] * gmax * NC;
+          for (int qq = lane; qq < ncol; qq += 32)
+            if (clab_sh[qq] == j) gs = df_add(gs, make_float2(fj[qq], 0.0f));
+        }
+        gs = warp_sum_df(gs);
+        if (lane == 0) {
+          if (fixed) {
+            if (nj_sh[j] > 0)  // non-negative; the scale is a power of two
+              atomicAdd(facc + (t & 1) * (C + 3) + j,
+                        (unsigned long long)llrint(((double)gs.x + (double)gs.y) * gscale));
+          } else {
+            I.gcta[(size_t)blockIdx.x * C + j] = gs;
+          }
+        }
+      }
+    }
+    // barrier 1: arrive now, wait after the work that does not need g_hat
+    fused_arrive(I.bar);
+    bar_target += gridDim.x;
+    // e_lj = K_ll - 2 f_hat_lj for this thread's column (d_lj = e_lj + g_hat_j)
+    if (mine) {
+      for (int j = 0; j < C; ++j) {
+        if (nj_sh[j] == 0) {
+          if (fhat_out) fhat_out[(int64_t)l * C + j] = __int_as_float(0x7fc00000);
+          continue;
+        }
+        float* fp = slots + (size_t)first_sh[j] * gmax * NC + q;
+        const float fh = *fp / (float)nj_sh[j];
+        if (fhat_out) fhat_out[(int64_t)l * C + j] = fh;
+        *fp = ks - 2.0f * fh;
+      }
+    }
+    if (!fused_wait(I.bar, bar_target, I.err, &ok_sh)) break;  // KKM_ETIMEOUT on the host
+    // g_hat of every cluster (Eq. 16), the same value in every CTA
+    if (fixed) {
+      for (int j = tid; j < C; j += kFusedThreads) {
+        const int n = nj_sh[j];
+        double gv = __longlong_as_double(0x7ff8000000000000LL);
+        if (n > 0)
+          gv = I.ghat_in ? I.ghat_in[j]
+                         : (double)__ldcg(facc + (t & 1) * (C + 3) + j) / gscale / ((double)n * (double)n);
+        gh_sh[j] = gv;
+        ghf_sh[j] = (float)gv;
+      }
+      // the other set's counters were last read before barrier 1: zero them
+      // for the next iteration (published by barrier 2)
+      if (blockIdx.x == 0)
+        for (int e = tid; e < C + 3; e += kFusedThreads) facc[((t + 1) & 1) * (C + 3) + e] = 0ull;
+    } else {
+      // one warp per cluster: the CTA shares, lane b taking CTAs b, b + 32,
+      // ... (all loads in flight at once), then a fixed xor tree
+      for (int j = w; j < C; j += kFusedWarps) {
+        const int n = nj_sh[j];
+        float2 v[kFusedCtaPerLane];
+#pragma unroll
+        for (int m = 0; m < kFusedCtaPerLane; ++m) {
+          const int b = lane + 32 * m;
+          v[m] = (n > 0 && b < (int)gridDim.x) ? __ldcg(I.gcta + (size_t)b * C + j) : make_float2(0.0f, 0.0f);
+        }
+        float2 a2 = v[0];
+#pragma unroll
+        for (int m = 1; m < kFusedCtaPerLane; ++m) a2 = df_add(a2, v[m]);
+        a2 = warp_sum_df(a2);
+        if (lane == 0) {
+          double gv = __longlong_as_double(0x7ff8000000000000LL);
+          if (n > 0) gv = I.ghat_in ? I.ghat_in[j] : ((double)a2.x + (double)a2.y) / ((double)n * (double)n);
+          gh_sh[j] = gv;
+          ghf_sh[j] = (float)gv;
+        }
+      }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && ghat_out)
+      for (int j = tid; j < C; j += kFusedThreads) ghat_out[j] = gh_sh[j];
+
+    // ---- phase B: one column per thread
+    float best = inf, second = inf;
+    int bj = 0;
+    bool flagged = false;
+    if (mine) {
       for (int j = 0; j < C; ++j) {
         if (nj_sh[j] == 0) continue;
-        const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
-        if (dj < best) {
+        float* fp = slots + (size_t)first_sh[j] * gmax * NC + q;
+        const float dj = *fp + ghf_sh[j];
+        *fp = dj;  // the slot now holds d_lj
+        if (dj < best) {  // lowest j on ties
           second = best;
           best = dj;
           bj = j;
@@ -1199,95 +1247,212 @@ iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, 
           second = dj;
         }
       }
+      if (R.Xi && I.flag_tau > 0.0f && second < inf)
+        flagged = (second - best) < I.flag_tau * fmaxf(fabsf(second), ks + ghf_sh[bj]);
+    }
+    // near-tie re-score: candidate (column, cluster) pairs of the flagged
+    // columns, each re-scored by one warp from exact FP32 kernel values of
+    // its support (one landmark per lane, then a fixed xor tree); pairs are
+    // listed in rounds of kFusedCandCap in (column, cluster) order
+    if (__syncthreads_or(flagged)) {
+      const float b0 = best, scale = ks + ghf_sh[bj];
+      auto is_cand = [&](int j) {
+        if (nj_sh[j] == 0) return false;
+        const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
+        return dj - b0 < I.flag_tau * fmaxf(fabsf(dj), scale);
+      };
+      int cnt = 0;
+      if (flagged)
+        for (int j = 0; j < C; ++j) cnt += is_cand(j);
+      int total;
+      const int off = block_excl_scan(cnt, scan_sh, &total);
+      for (int cbase = 0; cbase < total; cbase += kFusedCandCap) {
+        if (flagged && off + cnt > cbase && off < cbase + kFusedCandCap) {
+          int k = off;
+          for (int j = 0; j < C; ++j)
+            if (is_cand(j)) {
+              if (k >= cbase && k < cbase + kFusedCandCap) cand[k - cbase] = (q << 8) | j;
+              ++k;
+            }
+        }
+        __syncthreads();
+        const int np = min(kFusedCandCap, total - cbase);
+        for (int p = w; p < np; p += kFusedWarps) {
+          const int qq = cand[p] >> 8, j = cand[p] & 255;
+          const int ir = col0 + qq;
+          const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
+          const float ni = R.nXi[ir];
+          const float ksr = kself ? kself[ir] : 1.0f;
+          const int k0 = seg_sh[j], k1 = seg_sh[j + 1];
+          float accr = 0.0f;
+          for (int kk = k0 + lane; kk < k1; kk += 32) {
+            const int k = perm_in_sh ? perm_sh[kk] : __ldcg(S.perm + kk);
+            const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
+            float dot = 0.0f;
+            for (int c = 0; c < (R.dp >> 2); ++c) {
+              const float4 a4 = __ldg(xi + c), b4 = __ldg(xl + c);
+              dot = fmaf(a4.x, b4.x, fmaf(a4.y, b4.y, fmaf(a4.z, b4.z, fmaf(a4.w, b4.w, dot))));
+            }
+            float kv;
+            if (R.kind == DK_LINEAR) kv = dot;
+            else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+            accr += kv;
+          }
+          accr = warp_sum_f32(accr);
+          if (lane == 0)
+            slots[(size_t)first_sh[j] * gmax * NC + qq] = ksr - 2.0f * (accr / (float)(k1 - k0)) + ghf_sh[j];
+        }
+        __syncthreads();
+      }
+      if (flagged) {  // argmin and margin over the updated distances
+        best = inf;
+        second = inf;
+        for (int j = 0; j < C; ++j) {
+          if (nj_sh[j] == 0) continue;
+          const float dj = slots[(size_t)first_sh[j] * gmax * NC + q];
+          if (dj < best) {
+            second = best;
+            best = dj;
+            bj = j;
+          } else if (dj < second) {
+            second = dj;
+          }
+        }
+      }
+    }
+    float2 om = make_float2(0.0f, 0.0f);
+    int ch = 0, lmc = 0;
+    if (mine) {
+      ch = cur_u != bj;
+      cur_u = bj;
+      if (cord >= 0 && ch) {  // read by the support sort (CTA 0)
+        S.lab[cord] = bj;
+        lmc = 1;
+      }
+      if (margin) margin[l] = second - best;
+      om.x = best;
+    }
+    // this CTA's cost and counts, in a fixed order
+    om = warp_sum_df(om);
+    ch = warp_sum_i32(ch);
+    lmc = warp_sum_i32(lmc);
+    if (lane == 0) {
+      wom[w] = om;
+      wch[w] = ch;
+      wlm[w] = lmc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float2 o = wom[0];
+      int c = wch[0], lm = wlm[0];
+      for (int k = 1; k < kFusedWarps; ++k) {
+        o = df_add(o, wom[k]);
+        c += wch[k];
+        lm += wlm[k];
+      }
+      if (fixed) {
+        unsigned long long* a = facc + (t & 1) * (C + 3) + C;
+        // two's complement: a slightly negative share (rounding of d ~ 0) adds correctly
+        atomicAdd(a, (unsigned long long)llrint(((double)o.x + (double)o.y) * oscale));
+        if (c) atomicAdd(a + 1, (unsigned long long)c);
+        if (lm) atomicAdd(a + 2, (unsigned long long)lm);
+      } else {
+        I.omega_part[blockIdx.x] = o;
+        I.changed_part[blockIdx.x] = c;
+        I.lm_part[blockIdx.x] = lm;
+      }
+    }
+    fused_arrive(I.bar);
+    bar_target += gridDim.x;
+    if (!fused_wait(I.bar, bar_target, I.err, &ok_sh)) break;
+    // ---- phase C: the iteration's cost and counts (the same in every CTA),
+    // the trace, early stop, supports
+    if (fixed) {
+      if (tid == 0) {
+        const unsigned long long* a = facc + (t & 1) * (C + 3) + C;
+        tot_om = (double)(long long)__ldcg(a) / oscale;
+        tot_ch = (int)__ldcg(a + 1);
+        tot_lm = (int)__ldcg(a + 2);
+      }
+    } else if (w == 0) {
+      float2 ov[kFusedCtaPerLane];
+      int cv[kFusedCtaPerLane], lv[kFusedCtaPerLane];
+#pragma unroll
+      for (int m = 0; m < kFusedCtaPerLane; ++m) {
+        const int b = lane + 32 * m;
+        const bool in = b < (int)gridDim.x;
+        ov[m] = in ? __ldcg(I.omega_part + b) : make_float2(0.0f, 0.0f);
+        cv[m] = in ? __ldcg(I.changed_part + b) : 0;
+        lv[m] = in ? __ldcg(I.lm_part + b) : 0;
+      }
+      float2 o = ov[0];
+      int c = cv[0], lm = lv[0];
+#pragma unroll
+      for (int m = 1; m < kFusedCtaPerLane; ++m) {
+        o = df_add(o, ov[m]);
+        c += cv[m];
+        lm += lv[m];
+      }
+      o = warp_sum_df(o);
+      c = warp_sum_i32(c);
+      lm = warp_sum_i32(lm);
+      if (lane == 0) {
+        tot_om = (double)o.x + (double)o.y;
+        tot_ch = c;
+        tot_lm = lm;
+      }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && tid == 0) {
+      I.trace_omega[t0 + t] = tot_om;
+      I.trace_changed[t0 + t] = tot_ch;
+    }
+    const bool stop = early_stop && tot_ch == 0;
+    const int lm_total = tot_lm;
+    __syncthreads();  // every thread has read the totals before they are rewritten
+    if (stop) {
+      ++t;
+      break;
+    }
+    if (lm_total > 0) {
+      // a landmark label changed: CTA 0 re-sorts the supports (the copies in
+      // flight follow the old order and are replaced after the reload)
+      if (blockIdx.x == 0) {
+        cp_async_wait<0>();
+        __syncthreads();
+        int* const scr = reinterpret_cast<int*>(slots);  // the slots are free now
+        sort_supports_cta(S, scr, scr + C, scr + 2 * C, scr + 2 * C + kFusedWarps * C);
+      }
+      if (t + 1 < iters) {  // barrier 3 publishes the new supports to every CTA
+        fused_arrive(I.bar);
+        bar_target += gridDim.x;
+        if (!fused_wait(I.bar, bar_target, I.err, &ok_sh)) break;
+        reload = true;
+      }
     }
   }
-  float2 om = make_float2(0.0f, 0.0f);
-  int ch = 0, lmc = 0;
-  if (mine) {
-    const int old = u[l];
-    u[l] = bj;
-    ch = old != bj;
-    const int cord = S.col_ord ? S.col_ord[l] : -1;
-    if (cord >= 0) {
-      S.lab[cord] = bj;
-      lmc = ch;
-    }
-    if (margin) margin[l] = second - best;
-    om.x = best;
+  cp_async_wait<0>();  // no copy is left in flight at exit
+  if (mine) u[l] = cur_u;
+  if (blockIdx.x == 0 && tid == 0) {
+    *I.trace_count = t0 + t;
+    if (early_stop && t < iters) *I.done = 1;
   }
-  // this CTA's cost and counts, in a fixed order
-  om = warp_sum_df(om);
-  ch = warp_sum_i32(ch);
-  lmc = warp_sum_i32(lmc);
-  __threadfence();  // labels and landmark labels visible before the ticket
-  if (lane == 0) {
-    wom[w] = om;
-    wch[w] = ch;
-    wlm[w] = lmc;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    float2 o = wom[0];
-    int c = wch[0], lm = wlm[0];
-    for (int k = 1; k < kFusedWarps; ++k) {
-      o = df_add(o, wom[k]);
-      c += wch[k];
-      lm += wlm[k];
-    }
-    I.omega_part[blockIdx.x] = o;
-    I.changed_part[blockIdx.x] = c;
-    I.lm_part[blockIdx.x] = lm;
-    __threadfence();
-    is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  // ---- the last CTA closes the iteration: cost and counts over the CTAs in
-  // CTA order, the trace entry, early stop, the barrier reset, and the
-  // support sort when a landmark label changed
-  griddep_launch();
-  __threadfence();
-  float2 o = make_float2(0.0f, 0.0f);
-  int c = 0, lm = 0;
-  if (w == 0) {
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-      o = df_add(o, __ldcg(I.omega_part + b));
-      c += __ldcg(I.changed_part + b);
-      lm += __ldcg(I.lm_part + b);
-    }
-    o = warp_sum_df(o);
-    c = warp_sum_i32(c);
-    lm = warp_sum_i32(lm);
-  }
-  if (tid == 0) {
-    const int t = *I.trace_count;
-    I.trace_omega[t] = (double)o.x + (double)o.y;
-    I.trace_changed[t] = c;
-    *I.trace_count = t + 1;
-    if (early_stop && c == 0) *I.done = 1;
-    *I.ticket = 0u;
-    *I.bar = 0u;
-    wlm[0] = lm;
-  }
-  __syncthreads();
-  if (wlm[0] == 0) return;  // same landmark labels: same supports
-  int* const scr = reinterpret_cast<int*>(fdyn);  // every CTA is past its slots
-  sort_supports_cta(S, scr, scr + C, scr + 2 * C, scr + 2 * C + kFusedWarps * C);
 }
 
-// Grid and shared memory of the fused iteration for a block of Ni columns
-// of `esize`-byte values and nL landmark rows; false when it does not apply
+// Grid and shared memory of the fused loop for a block of Ni columns of
+// `esize`-byte values and nL landmark rows; false when it does not apply
 // (more than kFusedMaxC clusters, or a strip wider than one column per thread
 // with one CTA per SM).
 bool fused_shape(int Ni, int nL, int C, int esize, int n_sms, FusedShape* F, size_t* smem) {
   if (C > kFusedMaxC || Ni < 1 || nL < 1) return false;
   const int NC = 16 / esize;
   F->groups = (int)ceil_div(Ni, NC);
-  F->n_cta = std::max(1, std::min(n_sms, (int)ceil_div(F->groups, 4)));
+  F->n_cta = std::max(1, std::min(std::min(n_sms, 32 * kFusedCtaPerLane), (int)ceil_div(F->groups, 4)));
   F->gmax = (int)ceil_div(F->groups, F->n_cta);
   if (F->gmax * NC > kFusedThreads) return false;
   F->R = std::max(1, std::min(kFusedThreads / F->gmax, nL));
-  size_t words = (size_t)(F->R + C) * F->gmax * NC + (nL <= kFusedPermCap ? (size_t)nL : 0);
+  size_t words = fused_ring_offset(F->R, C, F->gmax, NC, nL <= kFusedPermCap ? nL : 0) +
+                 (size_t)kFusedDepth * kFusedThreads * 4;
   const size_t sort_words = (size_t)(2 + kFusedWarps) * C + 32;
   words = std::max(words, sort_words);
   *smem = words * sizeof(float);
@@ -1296,49 +1461,52 @@ bool fused_shape(int Ni, int nL, int C, int esize, int n_sms, FusedShape* F, siz
 
 template <typename T>
 static cudaError_t launch_iterate_t(const T* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
-                                    const float* kself, int32_t* u, float* margin, float* fhat_out,
+                                    int iters, const float* kself, int32_t* u, float* margin, float* fhat_out,
                                     double* ghat_out, int early_stop, int n_sms, cudaStream_t st,
                                     const RescoreArgs& R) {
+  if (iters <= 0) return cudaSuccess;
   FusedShape F;
   size_t smem = 0;
   if (!fused_shape(Ni, S.nL, S.C, (int)sizeof(T), n_sms, &F, &smem)) return cudaErrorInvalidValue;
-  if (F.n_cta > I.fused_cap) return cudaErrorInvalidValue;  // gcta / partial-slot capacity
+  if (F.n_cta > I.fused_cap) return cudaErrorInvalidValue;  // gcta / per-CTA slot capacity
   static const cudaError_t attr = cudaFuncSetAttribute(iterate_fused_kernel<T>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        kFusedMaxDynSmem);
   if (attr != cudaSuccess) return attr;
+  // the barrier counter and the fixed-point accumulators start at zero in
+  // every launch
+  cudaError_t e = cudaMemsetAsync(I.bar, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I.facc, 0, sizeof(unsigned long long) * fused_acc_words(S.C), st);
+  if (e != cudaSuccess) return e;
+  IterState J = I;
+  // cost shares as fixed point: |Omega| <= 4 Ni for the Gaussian kernels
+  int b = 0;
+  while (b < 40 && ((int64_t)1 << b) <= Ni) ++b;  // Ni < 2^b
+  J.fom_shift = std::max(8, 60 - b);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)F.n_cta);
   cfg.blockDim = dim3(kFusedThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attrs[2];
+  cudaLaunchAttribute attrs[1];
   attrs[0].id = cudaLaunchAttributeCooperative;
   attrs[0].val.cooperative = 1;
-  attrs[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attrs[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attrs;
-  cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, iterate_fused_kernel<T>, KT, ldk, Ni, S, I, F, kself, u, margin,
-                                     fhat_out, ghat_out, early_stop, R);
-  if (e != cudaSuccess) {
-    // a cooperative launch that does not take the programmatic attribute
-    cudaGetLastError();
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, iterate_fused_kernel<T>, KT, ldk, Ni, S, I, F, kself, u, margin, fhat_out,
-                           ghat_out, early_stop, R);
-  }
-  return e;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, iterate_fused_kernel<T>, KT, ldk, Ni, S, J, F, iters, kself, u, margin, fhat_out,
+                            ghat_out, early_stop, R);
 }
-cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                            const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
                            int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R) {
-  return launch_iterate_t(KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st, R);
+  return launch_iterate_t(KT, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st,
+                          R);
 }
-cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                            const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
                            int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R) {
-  return launch_iterate_t(KT, ldk, Ni, S, I, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st, R);
+  return launch_iterate_t(KT, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop, n_sms, st,
+                          R);
 }
 
 // ----------------------------------------------------- Eq. 8 nearest medoid

@@ -99,7 +99,7 @@ _SIGNATURES = {
     "kkm_kernel_matrix": (_I32, [_P, _I64, _P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _P, _P]),
     "kkm_median_bandwidth": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _U64,
                                     ctypes.POINTER(_F32)]),
-    "kkm_debug_step": (_I32, [_P, _I64, _I64, _P, _I32, ctypes.POINTER(kkm_kernel), _I32, _I32, _P, _P,
+    "kkm_debug_step": (_I32, [_P, _I64, _I64, _P, _I32, ctypes.POINTER(kkm_kernel), _I32, _I32, _I32, _P, _P,
                               _P, _P, _P, _P, ctypes.POINTER(_F64), ctypes.POINTER(_I32), _P]),
     "kkm_debug_kmeanspp": (_I32, [_P, _I64, _I64, ctypes.POINTER(kkm_kernel), _I32, _U64, _P, _P]),
     "kkm_minibatch_plan": (_I32, [_I64, _I32, _I32, _F64, _U64, _I32, ctypes.POINTER(_I64),
@@ -513,7 +513,8 @@ def kkm_median_bandwidth(X, kind="rbf", n_atoms=0, seed=0):
     return out.value
 
 
-def kkm_debug_step(Xb, L, u, C, kind="rbf", sigma=1.0, n_atoms=0, stream=None, precision=KKM_FP32):
+def kkm_debug_step(Xb, L, u, C, kind="rbf", sigma=1.0, n_atoms=0, stream=None, precision=KKM_FP32,
+                   iteration="auto"):
     """kkm_debug_step of the C ABI: one teacher-forced inner iteration."""
     lib = load()
     Ni, d = int(Xb.shape[0]), int(np.prod(Xb.shape[1:]))
@@ -526,7 +527,8 @@ def kkm_debug_step(Xb, L, u, C, kind="rbf", sigma=1.0, n_atoms=0, stream=None, p
     om, ch = _F64(), _I32()
     k = _kernel(kind, sigma, n_atoms)
     st = stream if stream is not None else _stream_of(Xb)
-    _check(lib.kkm_debug_step(xp, Ni, d, L.ctypes.data, len(L), ctypes.byref(k), int(C), int(precision),
+    it = ITERATION[iteration] if isinstance(iteration, str) else int(iteration)
+    _check(lib.kkm_debug_step(xp, Ni, d, L.ctypes.data, len(L), ctypes.byref(k), int(C), int(precision), it,
                               u.ctypes.data,
                               out["u"].ctypes.data, out["fhat"].ctypes.data, out["margin"].ctypes.data,
                               out["ghat"].ctypes.data, out["n"].ctypes.data, ctypes.byref(om),

@@ -197,6 +197,10 @@ def test_bf16_step_full_minibatch(lib, mnist):
     Xb = X[gidx]
     u = cls[gidx].astype(np.int32)
     got = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16)
+    fused = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16, iteration="fused")
+    for key in ("u", "n"):
+        assert np.array_equal(fused[key], got[key]), key
+    assert abs(fused["omega"] - got["omega"]) <= 1e-6 * got["omega"]
     assert np.array_equal(got["n"], g["n"])
     bad = np.nonzero((got["u"] != g["u"]) & g["clear"])[0]
     assert bad.size == 0, f"{bad.size} clear rows differ from the oracle, first {bad[:10]}"

@@ -213,6 +213,19 @@ __device__ __forceinline__ float gram_epilogue(float dot, float na, float nb, bo
 
 // ------------------------------------------------------- tiled FP32 product
 constexpr int TB_M = 128, TB_N = 128, TB_K = 8;
+// Kernel values (RBF, linear) accumulate the dot product in chunks: every
+// kGramChunkTiles k-tiles (32 terms) the thread's 64 running sums are added
+// into a second set kept in shared memory and restart from zero.  One FP32
+// running sum over all of K drifts: adding small positive products to an
+// ever larger sum rounds them with a bias (measured on k/255-quantised
+// rows: about 1e-5 on the squared distance of near pairs, 7e-8 relative on
+// their kernel values), which moves the cost Omega by 1e-6 relative where
+// d = K_ii - 2 f_hat + g_hat cancels.  Short chunks keep each partial sum
+// small; the cost is one shared-memory add per output every 32 products.
+constexpr int kGramChunkTiles = 4;
+constexpr size_t kGramChunkSmem = sizeof(float) * 64 * 256;   // [64 outputs][256 threads]
+template <int KIND>
+constexpr bool gram_chunked() { return KIND == DK_RBF || KIND == DK_LINEAR; }
 
 // OutT: float, or __half for a Gaussian block stored in FP16 (values in [0, 1]).
 template <int KIND, typename OutT>
@@ -250,6 +263,8 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  extern __shared__ float chunk_sum[];  // [64][256] when gram_chunked<KIND>()
+  bool have_chunk = false;
 
   for (int kt = 0; kt < nk; ++kt) {
     const int cur = kt & 1;
@@ -275,7 +290,28 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
       As[nx][lk + 0][lr] = ga.x; As[nx][lk + 1][lr] = ga.y; As[nx][lk + 2][lr] = ga.z; As[nx][lk + 3][lr] = ga.w;
       Bs[nx][lk + 0][lr] = gb.x; Bs[nx][lk + 1][lr] = gb.y; Bs[nx][lk + 2][lr] = gb.z; Bs[nx][lk + 3][lr] = gb.w;
     }
+    if constexpr (gram_chunked<KIND>()) {
+      if ((kt + 1) % kGramChunkTiles == 0 && kt + 1 < nk) {  // close a chunk (not the last one)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float* p = chunk_sum + (i * 8 + j) * 256 + tid;
+            *p = have_chunk ? *p + acc[i][j] : acc[i][j];
+            acc[i][j] = 0.0f;
+          }
+        have_chunk = true;
+      }
+    }
     __syncthreads();
+  }
+  if constexpr (gram_chunked<KIND>()) {
+    if (have_chunk) {  // the open chunk joins the closed ones
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += chunk_sum[(i * 8 + j) * 256 + tid];
+    }
   }
 
   // Epilogue: rows a0 + {ty*4+i, 64+ty*4+i}, columns b0 + {tx*4+j, 64+tx*4+j}.
@@ -446,8 +482,14 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
   }
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-  gram_tiled_kernel<KIND, float><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                       neg_scale, out, ldo, vec_ok, 0);
+  const size_t smem = gram_chunked<KIND>() ? kGramChunkSmem : 0;
+  if (smem) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(gram_tiled_kernel<KIND, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+  }
+  gram_tiled_kernel<KIND, float><<<grid, 256, smem, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
+                                                          neg_scale, out, ldo, vec_ok, 0);
   return cudaGetLastError();
 }
 
@@ -496,8 +538,11 @@ cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, in
   if (nA <= 0 || nB <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
-  gram_tiled_kernel<DK_RBF, __half><<<grid, 256, 0, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                          neg_scale, out, ldo, vec_ok, 0);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      gram_tiled_kernel<DK_RBF, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramChunkSmem);
+  if (attr != cudaSuccess) return attr;
+  gram_tiled_kernel<DK_RBF, __half><<<grid, 256, kGramChunkSmem, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB,
+                                                                       idA, idB, neg_scale, out, ldo, vec_ok, 0);
   return cudaGetLastError();
 }
 

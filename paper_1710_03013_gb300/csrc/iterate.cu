@@ -693,11 +693,17 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       for (int kk = k0 + lane; kk < k1; kk += 32) {
         const int k = S.perm[kk];
         const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
-        float dot = 0.0f;
+        // in chunks of 32 products (see the Gram kernel: one long FP32 sum drifts)
+        float dot = 0.0f, part = 0.0f;
         for (int c = 0; c < (R.dp >> 2); ++c) {
           const float4 a = __ldg(xi + c), b = __ldg(xl + c);
-          dot = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, dot))));
+          part = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, part))));
+          if ((c & 7) == 7) {
+            dot += part;
+            part = 0.0f;
+          }
         }
+        dot += part;
         float kv;
         if (R.kind == DK_LINEAR) kv = dot;
         else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
@@ -1288,11 +1294,17 @@ iterate_fused_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S, 
           for (int kk = k0 + lane; kk < k1; kk += 32) {
             const int k = perm_in_sh ? perm_sh[kk] : __ldcg(S.perm + kk);
             const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
-            float dot = 0.0f;
+            // in chunks of 32 products (see the Gram kernel: one long FP32 sum drifts)
+            float dot = 0.0f, part = 0.0f;
             for (int c = 0; c < (R.dp >> 2); ++c) {
               const float4 a4 = __ldg(xi + c), b4 = __ldg(xl + c);
-              dot = fmaf(a4.x, b4.x, fmaf(a4.y, b4.y, fmaf(a4.z, b4.z, fmaf(a4.w, b4.w, dot))));
+              part = fmaf(a4.x, b4.x, fmaf(a4.y, b4.y, fmaf(a4.z, b4.z, fmaf(a4.w, b4.w, part))));
+              if ((c & 7) == 7) {
+                dot += part;
+                part = 0.0f;
+              }
             }
+            dot += part;
             float kv;
             if (R.kind == DK_LINEAR) kv = dot;
             else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);

@@ -34,6 +34,16 @@ Readings of the paper (where it is silent, garbled or at odds with itself):
       first iteration that changes no label (Algorithm 1, while condition).
   R13 Omega_t of an inner iteration is sum_i min_j d_ij for the labels of that
       iteration, i.e. the cost right after the assignment (Eq. 9).
+  R18 Restarts (Section 4.5, "kept the solution with minimum cost"): the cost
+      is Eq. 1 over the whole data set against the final global medoids;
+      restart r uses the r-th output of SplitMix64(seed); ties go to the
+      lowest restart; all restarts share one bandwidth.
+  R19 The elbow criterion (Sections 4.4, 4.5) is not defined in the paper:
+      the C whose cost lies farthest below the chord joining the end points of
+      the cost curve, both axes scaled to [0, 1] (lowest C on ties).
+  R20 The centre displacement of Fig. 4(b): per outer iteration, the mean over
+      clusters of the feature-space distance between the global medoid before
+      and after the mini-batch.
 """
 
 import math
@@ -488,3 +498,74 @@ def cost(model, X, mode="supports"):
     """Eq. 1 against the model's prototypes: sum_i min_j d_ij."""
     _, dmin = assign(model, X, mode)
     return float(np.sum(dmin))
+
+
+# ---------------------------------------------------------------------------
+# Model selection and diagnostics around Algorithm 1 (Section 4.1, Fig. 4b;
+# Sections 4.4 and 4.5).
+# ---------------------------------------------------------------------------
+def medoid_displacement(kernel, X, M_before, M_after):
+    """Average displacement of the cluster centres across one outer
+    iteration (the control observable of Section 4.1, Fig. 4b): the mean over
+    the C clusters of the feature-space distance between the global medoid
+    before and after the mini-batch, sqrt(K(a,a) - 2K(a,b) + K(b,b))."""
+    X = np.asarray(X, dtype=np.float64)
+    A = X[np.asarray(M_before)]
+    Bm = X[np.asarray(M_after)]
+    kab = np.array([kernel(A[j:j + 1], Bm[j:j + 1])[0, 0] for j in range(len(A))])
+    d2 = kernel.self_terms(A) - 2.0 * kab + kernel.self_terms(Bm)
+    same = np.asarray(M_before) == np.asarray(M_after)
+    d2[same] = 0.0
+    return float(np.mean(np.sqrt(np.maximum(d2, 0.0))))
+
+
+def displacement_trace(result, X):
+    """medoid_displacement of every mini-batch of a fit() result."""
+    return [medoid_displacement(result["kernel"], X, det["M_before"], det["M_after"])
+            for det in result["details"]]
+
+
+def restart_seeds(seed, n):
+    """Seeds of n restarts: the first n outputs of SplitMix64(seed)."""
+    g = SplitMix64(seed)
+    return [g.next_u64() for _ in range(n)]
+
+
+def fit_restarts(X, C, B, s, kernel, iters, seeds, early_stop=True, sampling="stride"):
+    """Section 4.5: the method initialised several times with k-means++ (one
+    seed each) and the solution of minimum cost kept.  Reading: the cost is
+    Eq. 1 over the whole data set against the final global medoids (the
+    output M of Algorithm 1); ties go to the lowest restart.  Every restart
+    uses the same bandwidth (the caller resolves the median rule first)."""
+    fits = [fit(X, C, B, s, kernel, iters, sd, early_stop=early_stop, sampling=sampling) for sd in seeds]
+    costs = np.array([cost(f, X, "medoids") for f in fits])
+    best = int(np.argmin(costs))
+    return {"costs": costs, "best": best, "fit": fits[best], "fits": fits}
+
+
+def elbow_index(costs):
+    """The elbow of a cost curve over consecutive C (Sections 4.4 and 4.5
+    pick C "via the elbow criterion"; reading: the point farthest below the
+    chord joining the curve's end points, both axes scaled to [0, 1]; lowest
+    C on ties).  Returns the index into `costs`."""
+    y = np.asarray(costs, dtype=np.float64)
+    n = y.size
+    if n <= 2:
+        return 0
+    x = np.arange(n) / (n - 1.0)
+    span = y.max() - y.min()
+    if span <= 0.0:
+        return 0
+    yn = (y - y.min()) / span
+    chord = yn[0] + (yn[-1] - yn[0]) * x
+    return int(np.argmax(chord - yn))
+
+
+def elbow(X, C_lo, C_hi, B, s, kernel, iters, seed, n_restarts=1, early_stop=True, sampling="stride"):
+    """Cost of the best of n_restarts fits for every C in [C_lo, C_hi] (the
+    same restart seeds for every C) and the elbow C."""
+    seeds = restart_seeds(seed, n_restarts)
+    Cs = list(range(C_lo, C_hi + 1))
+    costs = np.array([fit_restarts(X, C, B, s, kernel, iters, seeds, early_stop, sampling)["costs"].min()
+                      for C in Cs])
+    return {"Cs": np.array(Cs), "costs": costs, "C": Cs[elbow_index(costs)]}

@@ -505,3 +505,67 @@ def test_assign_and_cost_linear_explicit_means():
     um, _ = O.assign(res, Xn, "medoids")
     assert np.array_equal(um, np.argmin(dm, axis=1))
     assert O.cost(res, Xn, "medoids") == pytest.approx(dm.min(axis=1).sum(), rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# Model selection and diagnostics (Section 4.1 Fig. 4b; Sections 4.4, 4.5).
+# ---------------------------------------------------------------------------
+def test_displacement_linear_is_mean_euclidean_distance():
+    X, _ = _blob_data(N=300, d=3, C=4, problem=20)
+    ker = O.Kernel(O.KIND_LINEAR)
+    a, b = np.array([3, 10, 55, 7]), np.array([3, 99, 12, 250])
+    want = np.mean(np.linalg.norm(X[a] - X[b], axis=1))      # explicit coordinates
+    assert abs(O.medoid_displacement(ker, X, a, b) - want) <= 1e-12 * want
+    assert O.medoid_displacement(ker, X, a, a) == 0.0
+
+
+def test_displacement_rbf_closed_form():
+    from scipy.spatial.distance import cdist
+    X, _ = _blob_data(N=200, d=5, C=3, problem=21)
+    sig = 2.5
+    ker = O.Kernel(O.KIND_RBF, sig)
+    a, b = np.array([0, 5, 9]), np.array([1, 5, 150])
+    r = np.diag(cdist(X[a], X[b]))
+    want = np.mean(np.sqrt(2.0 - 2.0 * np.exp(-r ** 2 / (2 * sig ** 2))))
+    assert abs(O.medoid_displacement(ker, X, a, b) - want) <= 1e-12
+    res = O.fit(X, 3, 2, 0.5, ker, 5, 4)
+    tr = O.displacement_trace(res, X)
+    assert len(tr) == 2 and all(v >= 0.0 for v in tr)
+
+
+def test_elbow_index_hand_worked():
+    # costs 100 50 10 8 6 4 over six consecutive C; scaled y = 1, .5, .0625,
+    # .0417, .0208, 0; the chord from (0, 1) to (1, 0) is 1 - x with x = k/5;
+    # chord - y = 0, .3, .5375, .3583, .1792, 0: the elbow is the third C
+    assert O.elbow_index([100, 50, 10, 8, 6, 4]) == 2
+    # the same under any positive affine change of the cost
+    assert O.elbow_index([3 + 0.5 * c for c in [100, 50, 10, 8, 6, 4]]) == 2
+    # a straight line has no elbow below its chord: the first C
+    assert O.elbow_index([10, 8, 6, 4, 2]) == 0
+    assert O.elbow_index([5.0]) == 0
+
+
+def test_elbow_finds_separated_groups():
+    # four well separated groups: the cost drops steeply up to C = 4, then flattens
+    g = np.random.Generator(np.random.PCG64(31))
+    centres = np.array([[0.0, 0.0], [20.0, 0.0], [0.0, 20.0], [20.0, 20.0]])
+    X = centres[np.arange(240) % 4] + g.normal(0, 1.0, size=(240, 2))
+    res = O.elbow(X, 2, 8, 1, 1.0, O.Kernel(O.KIND_LINEAR), 15, seed=5, n_restarts=3)
+    assert res["C"] == 4
+    assert np.all(np.diff(res["costs"]) <= 1e-9 * res["costs"][0])
+
+
+def test_restarts_keep_the_minimum_explicit_cost():
+    X, _ = _blob_data(N=400, d=2, C=6, problem=22)
+    ker = O.Kernel(O.KIND_LINEAR)
+    seeds = O.restart_seeds(9, 5)
+    res = O.fit_restarts(X, 6, 2, 0.5, ker, 10, seeds)
+    # explicit Eq. 1 cost against each restart's medoids (squared Euclidean distances)
+    explicit = []
+    for f in res["fits"]:
+        M = X[f["medoids"]]
+        explicit.append(float(((X[:, None, :] - M[None, :, :]) ** 2).sum(axis=2).min(axis=1).sum()))
+    assert np.allclose(res["costs"], explicit, rtol=1e-12)
+    assert res["best"] == int(np.argmin(explicit))
+    assert res["fit"] is res["fits"][res["best"]]
+    assert len(set(seeds)) == 5

@@ -158,6 +158,43 @@ typedef struct kkm_problem {
 } kkm_problem;
 
 /*
+ * kkm_fit_restarts -- Section 4.5: the method initialised several times with
+ * kernel k-means++ and the solution of minimum cost kept.  Restart r is
+ * kkm_fit with the r-th output of SplitMix64(seed) as its seed; all restarts
+ * run as one kkm_fit_batch.  With sigma <= 0 the median rule is applied once
+ * (kkm_median_bandwidth with `seed`) and every restart uses that bandwidth,
+ * so that their costs compare fits of one kernel.  The cost of a restart is
+ * Eq. 1 over X against its final global medoids (kkm_cost with
+ * KKM_ASSIGN_MEDOIDS); the lowest cost wins, ties to the lowest restart.
+ *   n_restarts 1..1024; opt as for kkm_fit (init_medoids must be NULL).
+ *   labels_out [N] (device or host, nullable), model_out (nullable): the
+ *   winner's labels and model.  costs_out [n_restarts] (host, nullable),
+ *   best_out (host, nullable): every restart's cost and the winner's index.
+ */
+kkm_status kkm_fit_restarts(const float* X, int64_t N, int64_t d, int32_t C,
+                            int32_t B, double s, const kkm_kernel* k,
+                            int32_t iters, uint64_t seed, int32_t n_restarts,
+                            const kkm_options* opt, int32_t* labels_out,
+                            kkm_model** model_out, double* costs_out,
+                            int32_t* best_out);
+
+/*
+ * kkm_elbow -- the number of clusters by the elbow criterion (Sections 4.4
+ * and 4.5 choose C this way over a range, (4, 40) for the MD trajectory).
+ * For every C in [C_lo, C_hi] the best of n_restarts restarts (the rule and
+ * seeds of kkm_fit_restarts, the same seeds for every C); all (C, restart)
+ * fits run as one kkm_fit_batch.  The paper does not define the criterion;
+ * the C returned is the one whose cost lies farthest below the chord joining
+ * the end points of the cost curve, both axes scaled to [0, 1] (lowest C on
+ * ties).  1 <= C_lo < C_hi <= 256.  costs_out [C_hi - C_lo + 1] (host,
+ * nullable) gets each C's minimum cost; *C_out (host) the elbow.
+ */
+kkm_status kkm_elbow(const float* X, int64_t N, int64_t d, int32_t C_lo,
+                     int32_t C_hi, int32_t B, double s, const kkm_kernel* k,
+                     int32_t iters, uint64_t seed, int32_t n_restarts,
+                     const kkm_options* opt, double* costs_out, int32_t* C_out);
+
+/*
  * kkm_fit_batch -- n independent fits on one GPU at once: many data sets of
  * uneven sizes, or restarts of one data set with different seeds.  Each
  * problem gets exactly the results of kkm_fit with the same arguments.  The
@@ -271,6 +308,14 @@ kkm_status kkm_model_medoids(const kkm_model* m, int64_t* idx_out,
  * g_hat [C] (Eq. 16) and landmark counts n_j [C]; each nullable. */
 kkm_status kkm_model_supports(const kkm_model* m, int32_t* labels_out,
                               double* ghat_out, int32_t* n_out);
+/* Average displacement of the cluster centres in each outer iteration
+ * (Section 4.1, Fig. 4b, proposed there as the observable of sampling
+ * quality): for mini-batch i, the mean over the C clusters of the
+ * feature-space distance sqrt(K(a,a) - 2K(a,b) + K(b,b)) between the global
+ * medoid a before and b after the mini-batch (0 for an unchanged medoid).
+ * Up to cap values to out (host, nullable); *n_out gets B. */
+kkm_status kkm_model_displacement(const kkm_model* m, double* out, int32_t cap,
+                                  int32_t* n_out);
 /* Inner-loop trace over all mini-batches: Omega (Eq. 9) and the number of
  * changed labels of each executed iteration, up to cap entries; *n_out gets
  * the total number of entries. */

@@ -134,22 +134,6 @@ void prof_add_work(const char* name, double units) {
     KKM_CK(call);                               \
   } while (0)
 
-// ======================================================================
-// Random numbers: SplitMix64 from its published definition
-// ======================================================================
-struct SplitMix64 {
-  uint64_t state;
-  explicit SplitMix64(uint64_t s) : state(s) {}
-  uint64_t next() {
-    state += 0x9E3779B97F4A7C15ull;
-    uint64_t z = state;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-  }
-  double u01() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
-};
-
 // First k entries of a partial Fisher-Yates shuffle of [0, n).
 static std::vector<int64_t> partial_shuffle(int64_t n, int64_t k, SplitMix64& rng) {
   std::vector<int64_t> idx((size_t)n);
@@ -995,8 +979,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   const int64_t ldk = round_up(Nmax, 32);
   const int trace_cap = B * iters;
   const bool overlap = fit_overlaps(opt.pipeline, B, sp.kind, sp.precision);
-  float *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol;
-  int64_t *Mg, *W, *idMI;
+  float *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol, *MXn, *auxMn, *Kmn;
+  int64_t *Mg, *W, *idMI, *Mg_prev;
+  double* disp;
   int32_t *u, *Ld_all, *mi, *mi_safe, *cnt, *picks, *labels_dev = nullptr;
   unsigned long long* keys;
   double *ghat, *D2 = nullptr, *draws_d = nullptr;
@@ -1020,6 +1005,13 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(ws.alloc(&idMI, C));
   KKM_TRY(ws.alloc(&Mg, C));
   KKM_TRY(ws.alloc(&W, C));
+  // centre displacement per mini-batch (Section 4.1, Fig. 4b)
+  const int64_t ldc = round_up(C, 32);
+  KKM_TRY(ws.alloc(&Mg_prev, C));
+  KKM_TRY(ws.alloc(&MXn, (int64_t)C * sp.dp));
+  KKM_TRY(ws.alloc(&auxMn, C));
+  KKM_TRY(ws.alloc(&Kmn, (int64_t)C * ldc));
+  KKM_TRY(ws.alloc(&disp, B));
   KKM_TRY(ws.alloc(&u, Nmax));
   KKM_TRY(ws.alloc(&Ld_all, (int64_t)L_all.size()));
   KKM_TRY(ws.alloc(&mi, C));
@@ -1150,7 +1142,14 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, ms));
     KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
     KKM_RUN("merge_keys", ms, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, ms));
+    KKM_CK(cudaMemcpyAsync(Mg_prev, Mg, (size_t)C * 8, cudaMemcpyDeviceToDevice, ms));
     KKM_RUN("merge_apply", ms, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, ms));
+    // how far the global medoids moved in this outer iteration (Fig. 4b):
+    // K(old medoid rows MX, new medoid rows) and its diagonal
+    KKM_TRY(prep_ids(sp, X, Mg, C, MXn, auxMn, ms));
+    KKM_TRY(kernel_block(sp, MX, auxM, Mg_prev, C, MXn, auxMn, Mg, C, Kmn, ldc, ms));
+    KKM_RUN("displacement", ms,
+            launch_displacement(Kmn, ldc, C, kmm, sp.kind == KKM_LINEAR ? auxMn : nullptr, Mg_prev, Mg, disp + i, ms));
     if (labels_dev)
       KKM_RUN("scatter_labels", ms, launch_scatter_labels(u, Ni, g.start, g.step, labels_dev, ms));
     if (i == B - 1 && model_out) {
@@ -1210,6 +1209,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaStreamSynchronize(st));
     m->omega.resize(tc);
     m->changed.resize(tc);
+    m->displacement.resize(B);
+    KKM_CK(cudaMemcpyAsync(m->displacement.data(), disp, (size_t)B * 8, cudaMemcpyDeviceToHost, st));
     if (tc > 0) {
       KKM_CK(cudaMemcpyAsync(m->omega.data(), I.trace_omega, (size_t)tc * 8, cudaMemcpyDeviceToHost, st));
       KKM_CK(cudaMemcpyAsync(m->changed.data(), I.trace_changed, (size_t)tc * 4, cudaMemcpyDeviceToHost, st));
@@ -1642,6 +1643,16 @@ kkm_status kkm_model_supports(const kkm_model* m, int32_t* labels_out, double* g
   if (labels_out) memcpy(labels_out, m->sup_labels_h.data(), m->sup_labels_h.size() * 4);
   if (ghat_out) memcpy(ghat_out, m->ghat_h.data(), m->ghat_h.size() * 8);
   if (n_out) memcpy(n_out, m->n_h.data(), m->n_h.size() * 4);
+  return KKM_OK;
+}
+
+kkm_status kkm_model_displacement(const kkm_model* m, double* out, int32_t cap, int32_t* n_out) {
+  set_error("");
+  if (!m || !n_out) return invalid("model and n_out must not be NULL");
+  const int n = (int)m->displacement.size();
+  *n_out = n;
+  if (out)
+    for (int q = 0; q < std::min(n, std::max(cap, 0)); ++q) out[q] = m->displacement[q];
   return KKM_OK;
 }
 

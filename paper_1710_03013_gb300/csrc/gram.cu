@@ -391,7 +391,10 @@ __host__ __device__ constexpr int scatter_shift() {
 // sample rows: one warp takes kSkinnyRows sample rows at a time, each lane
 // keeping kSkinnyLoads 16-byte loads per row in flight (the sample rows are
 // the only HBM traffic), every shared-memory reference value serving all the
-// warp's rows.
+// warp's rows.  The Gaussian and distance kinds sum the squared differences
+// directly: the kernel reads memory at its bandwidth limit, so the second
+// operation per component costs nothing, and the squared distance does not
+// cancel as |x|^2 + |y|^2 - 2 x.y does for rows far from the origin.
 constexpr int kSkinnyRows = 2, kSkinnyLoads = 4;
 
 template <int KIND, int NA>
@@ -436,21 +439,30 @@ gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict_
           if (a < nA) {
             const float4 y = As4[a * dq + q];
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-              acc[r][a] = fmaf(x[r][t].x, y.x, fmaf(x[r][t].y, y.y, fmaf(x[r][t].z, y.z, fmaf(x[r][t].w, y.w, acc[r][a]))));
+            for (int r = 0; r < R; ++r) {
+              if constexpr (KIND == DK_RBF || KIND == DK_DIST) {
+                const float e0 = x[r][t].x - y.x, e1 = x[r][t].y - y.y, e2 = x[r][t].z - y.z, e3 = x[r][t].w - y.w;
+                acc[r][a] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc[r][a]))));
+              } else {
+                acc[r][a] =
+                    fmaf(x[r][t].x, y.x, fmaf(x[r][t].y, y.y, fmaf(x[r][t].z, y.z, fmaf(x[r][t].w, y.w, acc[r][a]))));
+              }
+            }
           }
         }
       }
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const float dot = warp_reduce_scatter<NA>(acc[r], lane);
+      const float sum = warp_reduce_scatter<NA>(acc[r], lane);  // x.y, or |x - y|^2
       const int b = b0 + r;
       if (writer && b < nB) {
-        const float na = KIND != DK_LINEAR ? normA[a_mine] : 0.0f;
-        const float nbv = KIND != DK_LINEAR ? normB[b] : 0.0f;
         const bool same = idA && idB && idA[a_mine] == idB[b];
-        out[(int64_t)a_mine * ldo + b] = gram_epilogue<KIND>(dot, na, nbv, same, neg_scale);
+        float v;
+        if constexpr (KIND == DK_RBF) v = same ? 1.0f : exp2f(sum * neg_scale);
+        else if constexpr (KIND == DK_DIST) v = same ? 0.0f : sqrtf(sum);
+        else v = gram_epilogue<KIND>(sum, 0.0f, 0.0f, same, neg_scale);
+        out[(int64_t)a_mine * ldo + b] = v;
       }
     }
   }

@@ -44,6 +44,7 @@ struct kkm_model {
   std::vector<int64_t> medoids, W;
   std::vector<double> omega;
   std::vector<int32_t> changed;
+  std::vector<double> displacement;  // [B] average centre displacement per mini-batch (Fig. 4b)
   std::vector<int32_t> sup_labels_h;
   std::vector<double> ghat_h;
   std::vector<int32_t> n_h;
@@ -59,6 +60,22 @@ namespace kkm {
 // One device allocation (m->arena) for the model's resident arrays, sized from
 // C, dp, nL and max_units; the array pointers point into it.
 kkm_status model_alloc_device(kkm_model* m);
+
+// ------------------------------------------------------- random numbers ---
+// SplitMix64 (Steele, Lea & Flood 2014) from its published definition; u01
+// takes the top 53 bits.  The host draws every random number of the method.
+struct SplitMix64 {
+  uint64_t state;
+  explicit SplitMix64(uint64_t s) : state(s) {}
+  uint64_t next() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double u01() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
 
 // ---------------------------------------------------------------- errors ---
 void set_error(const std::string& msg);
@@ -369,6 +386,10 @@ cudaError_t launch_merge_keys(const float* Kt, const float* Kmi, int64_t ldk, in
 cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi,
                                const int32_t* c, int C, int64_t start, int64_t step,
                                int64_t* M, int64_t* W, cudaStream_t st);
+// Average centre displacement across one mini-batch (Section 4.1, Fig. 4b)
+// from K[a][b] = K(old_a, cur_b) (C x C, row pitch ldk) into *out (device).
+cudaError_t launch_displacement(const float* K, int64_t ldk, int C, const float* selfA, const float* selfB,
+                                const int64_t* old, const int64_t* cur, double* out, cudaStream_t st);
 // labels_out[start + l*step] = u[l]
 cudaError_t launch_scatter_labels(const int32_t* u, int Ni, int64_t start, int64_t step,
                                   int32_t* labels_out, cudaStream_t st);

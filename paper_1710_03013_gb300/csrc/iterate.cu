@@ -1655,6 +1655,35 @@ cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi
   return cudaGetLastError();
 }
 
+// ------------------------------------------- centre displacement (Fig. 4b)
+// out = mean over j of the feature-space distance between the medoid before
+// (old[j]) and after (cur[j]) a mini-batch: sqrt(max(0, K(a,a) - 2K(a,b) +
+// K(b,b))) from the C x C block K[a][b] = K(old_a, cur_b) (self terms 1 for
+// the Gaussian kernels, the squared norms selfA/selfB for the linear one); an
+// unchanged medoid contributes 0 exactly.  One CTA; a fixed-order sum.
+__global__ void __launch_bounds__(256) displacement_kernel(const float* __restrict__ K, int64_t ldk, int C,
+                                                          const float* __restrict__ selfA,
+                                                          const float* __restrict__ selfB,
+                                                          const int64_t* __restrict__ old,
+                                                          const int64_t* __restrict__ cur, double* __restrict__ out) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) {
+    if (old[j] == cur[j]) continue;
+    const double ka = selfA ? (double)selfA[j] : 1.0, kb = selfB ? (double)selfB[j] : 1.0;
+    const double d2 = ka - 2.0 * (double)K[(int64_t)j * ldk + j] + kb;
+    s += sqrt(d2 > 0.0 ? d2 : 0.0);
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s / (double)C;
+}
+
+cudaError_t launch_displacement(const float* K, int64_t ldk, int C, const float* selfA, const float* selfB,
+                                const int64_t* old, const int64_t* cur, double* out, cudaStream_t st) {
+  displacement_kernel<<<1, 256, 0, st>>>(K, ldk, C, selfA, selfB, old, cur, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- small utils
 __global__ void scatter_labels_kernel(const int32_t* __restrict__ u, int Ni, int64_t start,
                                       int64_t step, int32_t* __restrict__ out) {

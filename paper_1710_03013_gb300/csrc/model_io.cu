@@ -4,11 +4,13 @@
 // queries read (the last mini-batch's landmark supports with their sorted
 // structure and g_hat, the global medoids and counts, the trace).
 //
-// Format (little-endian): 8-byte magic "KKMMOD01", then int64 C, d, kind,
+// Format (little-endian): 8-byte magic "KKMMOD02", then int64 C, d, kind,
 // n_atoms, dp, nL, max_units, trace length T, a float64 sigma, then the
 // arrays in a fixed order, each exactly as many bytes as its element count
-// implies.  Loading checks every count against the header (and the file
-// length against their sum) before it touches the GPU.
+// implies, then int64 D and the D float64 centre displacements (files of the
+// first version, magic "KKMMOD01", end before D and load with none).
+// Loading checks every count against the header (and the file length
+// against their sum) before it touches the GPU.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -21,7 +23,8 @@
 
 namespace kkm {
 
-static const char kMagic[8] = {'K', 'K', 'M', 'M', 'O', 'D', '0', '1'};
+static const char kMagic[8] = {'K', 'K', 'M', 'M', 'O', 'D', '0', '2'};
+static const char kMagicV1[8] = {'K', 'K', 'M', 'M', 'O', 'D', '0', '1'};
 
 struct Header {
   int64_t C, d, kind, n_atoms, dp, nL, max_units, T;
@@ -103,6 +106,9 @@ static kkm_status save_impl(const kkm_model* m, const char* path) {
   io.put(m->ghat_h.data(), m->ghat_h.size() * 8);
   io.put(m->n_h.data(), m->n_h.size() * 4);
   io.put(m->med_coords_h.data(), m->med_coords_h.size() * 4);
+  const int64_t nd = (int64_t)m->displacement.size();
+  io.put(&nd, 8);
+  io.put(m->displacement.data(), (size_t)nd * 8);
   const bool ok = io.ok && fclose(f) == 0;
   if (!ok) return fail(std::string("write to ") + path + " failed");
   return KKM_OK;
@@ -120,7 +126,8 @@ static kkm_status load_impl(const char* path, kkm_model** out) {
   io.get(&h, sizeof(h));
   fseek(f, 0, SEEK_END);
   const long fsize = ftell(f);
-  if (!io.ok || memcmp(magic, kMagic, 8) != 0) {
+  const bool v2 = io.ok && memcmp(magic, kMagic, 8) == 0;
+  if (!io.ok || (!v2 && memcmp(magic, kMagicV1, 8) != 0)) {
     fclose(f);
     return fail(std::string(path) + " is not a kkm model file");
   }
@@ -129,7 +136,14 @@ static kkm_status load_impl(const char* path, kkm_model** out) {
                     (h.kind != KKM_RMSD || (h.n_atoms >= 1 && h.d == 3 * h.n_atoms)) && h.dp == expected_dp(h) &&
                     h.max_units == max_units_for((int)h.nL, (int)h.C) && h.T >= 0 && h.T <= (1 << 28) &&
                     h.sigma == h.sigma;
-  if (!sane || fsize != (long)(8 + sizeof(Header) + body_bytes(h))) {
+  const long base = sane ? (long)(8 + sizeof(Header) + body_bytes(h)) : 0;
+  int64_t nd = 0;
+  if (sane && v2) {  // the displacement count follows the arrays
+    fseek(f, base, SEEK_SET);
+    io.get(&nd, 8);
+  }
+  const bool nd_ok = io.ok && nd >= 0 && nd <= (1 << 24);
+  if (!sane || !nd_ok || fsize != base + (v2 ? (long)(8 + 8 * nd) : 0L)) {
     fclose(f);
     return fail(std::string(path) + ": inconsistent model header or file length");
   }
@@ -195,6 +209,12 @@ static kkm_status load_impl(const char* path, kkm_model** out) {
   io.get(m->ghat_h.data(), (size_t)C * 8);
   io.get(m->n_h.data(), (size_t)C * 4);
   io.get(m->med_coords_h.data(), (size_t)(C * h.d) * 4);
+  if (v2) {
+    int64_t nd2 = 0;
+    io.get(&nd2, 8);
+    m->displacement.resize((size_t)nd);
+    io.get(m->displacement.data(), (size_t)nd * 8);
+  }
   fclose(f);
   if (r != KKM_OK) return r;
   if (!io.ok) return fail(std::string(path) + ": truncated");

@@ -77,6 +77,11 @@ _SIGNATURES = {
     "kkm_fit": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
                        ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P)]),
     "kkm_fit_batch": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "kkm_fit_restarts": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64, _I32,
+                                ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P), _P, ctypes.POINTER(_I32)]),
+    "kkm_elbow": (_I32, [_P, _I64, _I64, _I32, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64, _I32,
+                         ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_I32)]),
+    "kkm_model_displacement": (_I32, [_P, _P, _I32, ctypes.POINTER(_I32)]),
     "kkm_server_create": (_I32, [ctypes.POINTER(kkm_server_config), ctypes.POINTER(_P)]),
     "kkm_server_destroy": (None, [_P]),
     "kkm_server_add_model": (_I32, [_P, _P, ctypes.POINTER(_I32)]),
@@ -241,6 +246,15 @@ class Model:
         _check(load().kkm_model_load(os.fsencode(path), ctypes.byref(h)))
         return Model(h)
 
+    def displacement(self):
+        """kkm_model_displacement of the C ABI: the average centre
+        displacement of every mini-batch (Section 4.1, Fig. 4b)."""
+        n = _I32()
+        _check(load().kkm_model_displacement(self._h, None, 0, ctypes.byref(n)))
+        out = np.empty(n.value, np.float64)
+        _check(load().kkm_model_displacement(self._h, out.ctypes.data, n.value, ctypes.byref(n)))
+        return out
+
     def trace(self):
         n = _I32()
         _check(load().kkm_model_trace(self._h, None, None, 0, ctypes.byref(n)))
@@ -277,6 +291,60 @@ def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
                        int(seed) & ((1 << 64) - 1), ctypes.byref(opt), lab_p, ctypes.byref(h)))
     del keep, init_arr
     return lab, Model(h)
+
+
+def _options(precision, sampling, early_stop, pipeline, iteration, stream):
+    opt = kkm_options()
+    load().kkm_options_default(ctypes.byref(opt))
+    opt.precision = int(precision)
+    opt.sampling = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    opt.early_stop = int(bool(early_stop))
+    opt.pipeline = PIPELINE[pipeline] if isinstance(pipeline, str) else int(pipeline)
+    opt.iteration = ITERATION[iteration] if isinstance(iteration, str) else int(iteration)
+    opt.stream = stream
+    return opt
+
+
+def kkm_fit_restarts(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, n_restarts=5, *,
+                     precision=KKM_FP32, sampling="stride", early_stop=True, labels=True, stream=None,
+                     pipeline="auto", iteration="auto"):
+    """kkm_fit_restarts of the C ABI.  Returns (labels or None, Model of the
+    best restart, every restart's cost, the best restart's index)."""
+    lib = load()
+    N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
+    xp, keep = _as_input(X, np.float32)
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(X)
+    opt = _options(precision, sampling, early_stop, pipeline, iteration, st)
+    lp, lab = _out_like(X, N, np.int32) if labels else (None, None)
+    costs = np.empty(int(n_restarts), np.float64)
+    best = _I32()
+    h = ctypes.c_void_p()
+    _check(lib.kkm_fit_restarts(xp, N, d, int(C), int(B), float(s), ctypes.byref(k), int(iters),
+                                int(seed) & ((1 << 64) - 1), int(n_restarts), ctypes.byref(opt), lp,
+                                ctypes.byref(h), costs.ctypes.data, ctypes.byref(best)))
+    del keep
+    return lab, Model(h), costs, best.value
+
+
+def kkm_elbow(X, C_lo, C_hi, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, n_restarts=1, *,
+              precision=KKM_FP32, sampling="stride", early_stop=True, stream=None, pipeline="auto",
+              iteration="auto"):
+    """kkm_elbow of the C ABI.  Returns (the minimum cost of every C in
+    [C_lo, C_hi], the elbow C)."""
+    lib = load()
+    N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
+    xp, keep = _as_input(X, np.float32)
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(X)
+    opt = _options(precision, sampling, early_stop, pipeline, iteration, st)
+    costs = np.empty(int(C_hi) - int(C_lo) + 1, np.float64)
+    c_out = _I32()
+    _check(lib.kkm_elbow(xp, N, d, int(C_lo), int(C_hi), int(B), float(s), ctypes.byref(k), int(iters),
+                         int(seed) & ((1 << 64) - 1), int(n_restarts), ctypes.byref(opt), costs.ctypes.data,
+                         ctypes.byref(c_out)))
+    del keep
+    return costs, c_out.value
 
 
 def kkm_fit_batch(problems, n_streams=0, stream=None, check=True):

@@ -53,7 +53,11 @@ typedef enum kkm_kernel_kind { KKM_RBF = 0, KKM_RMSD = 1, KKM_LINEAR = 2 } kkm_k
  * plain FFMA path.  KKM_BF16 (RBF and linear kernels) runs the Gram product
  * on the tensor cores from BF16-rounded rows with FP32 accumulation; the
  * C-column blocks (Eq. 8, 12, k-means++) and all sums stay FP32/FP64.
- * KKM_FP8 is reserved. */
+ * KKM_FP8 (RBF and linear kernels) runs it on e4m3 rows, each scaled by
+ * max |x| / 448 (tcgen05 kind::f8f6f4, FP32 accumulation).  Both store the
+ * Gaussian block in FP16 and re-score near-tie rows from FP32 kernel values
+ * (the window is 1e-3 of the term scale for BF16, 3e-2 for FP8).  Rows of at
+ * most 128 values use the FP32 Gram stored in FP16 on both. */
 typedef enum kkm_precision { KKM_FP32 = 0, KKM_BF16 = 1, KKM_FP8 = 2 } kkm_precision;
 
 /* Mini-batch fetching (Section 3.1): stride X^i = {x_(i+jB)}; block = B

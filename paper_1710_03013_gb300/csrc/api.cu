@@ -451,6 +451,22 @@ static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const 
   return KKM_OK;
 }
 
+// The same from e4m3 rows with a scale per row (KKM_FP8): P8 / Q8 [n][ld8]
+// codes, their scales and the squared norms of the decoded rows go to the
+// given scratch.
+static kkm_status kernel_block_fp8(const KernelSpec& sp, const float* P, const int32_t* L, int64_t nP, const float* Q,
+                                   int64_t nQ, void* out, bool out_half, int64_t ldo, uint8_t* P8, float* sP,
+                                   float* nP8, uint8_t* Q8, float* sQ, float* nQ8, int* err, cudaStream_t st) {
+  const int ld8 = (int)round_up(sp.dp, 16);
+  KKM_RUN("to_fp8", st, launch_to_fp8(P, nP, sp.dp, ld8, P8, sP, nP8, st));
+  KKM_RUN("to_fp8", st, launch_to_fp8(Q, nQ, sp.dp, ld8, Q8, sQ, nQ8, st));
+  KKM_RUN("gram_block", st,
+          launch_gram_tc_fp8(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, P8, nP, Q8, nQ, (int)sp.d, ld8, nP8, nQ8, sP,
+                             sQ, sp.neg_scale(), out, out_half, ldo, err, sm_count(), st));
+  if (L && sp.kind != KKM_LINEAR) KKM_RUN("set_diag", st, launch_set_diag(out, out_half, ldo, L, (int)nP, st));
+  return KKM_OK;
+}
+
 int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes) {
   static const int l2 = []() {
     int dev = 0, v = 0;
@@ -469,6 +485,11 @@ constexpr float kRescoreMargin = 1e-3f;
 // The same for a block of FP32-exact values stored in FP16 (the storage
 // rounding alone, <= 2^-12 relative per value, averaged by the segment sums).
 constexpr float kRescoreMarginHalf = 3e-4f;
+// The same for the FP8 block: e4m3 keeps 3 significand bits (rounding error
+// up to 2^-4 relative per coordinate), and its kernel values were measured
+// up to 1e-2 from those of the unrounded rows; d = K_ii - 2 f_hat + g_hat
+// then moves by at most three times that, which this window covers.
+constexpr float kRescoreMarginFp8 = 3e-2f;
 // The reduced-precision path computes the block of short rows (d <= this) in
 // FP32 on the FFMA pipes and stores it in FP16: at these lengths the block is
 // a small share of a fit, while the BF16 rounding of the rows would widen the
@@ -639,7 +660,9 @@ struct BlockBufs {
   __half* KTh = nullptr;
   int64_t *gid = nullptr, *gidL = nullptr;
   __nv_bfloat16 *Xib = nullptr, *XLb = nullptr;
-  float *nXib = nullptr, *nXLb = nullptr;
+  float *nXib = nullptr, *nXLb = nullptr;     // norms of the reduced-precision rows (BF16 or FP8)
+  uint8_t *Xi8 = nullptr, *XL8 = nullptr;    // FP8: e4m3 codes [n][round_up(dp, 16)]
+  float *sXi = nullptr, *sXL = nullptr;      // FP8: row scales
   RmsdTcScratch rtc;
 };
 
@@ -658,6 +681,15 @@ static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t 
   if (sp.precision == KKM_BF16) {
     KKM_TRY(ws.alloc(&b->Xib, Nmax * sp.dp));
     KKM_TRY(ws.alloc(&b->XLb, nLmax * sp.dp));
+  }
+  if (sp.precision == KKM_FP8) {
+    const int64_t ld8 = round_up(sp.dp, 16);
+    KKM_TRY(ws.alloc(&b->Xi8, Nmax * ld8));
+    KKM_TRY(ws.alloc(&b->XL8, nLmax * ld8));
+    KKM_TRY(ws.alloc(&b->sXi, Nmax));
+    KKM_TRY(ws.alloc(&b->sXL, nLmax));
+  }
+  if (sp.precision != KKM_FP32) {
     KKM_TRY(ws.alloc(&b->nXib, Nmax));
     KKM_TRY(ws.alloc(&b->nXLb, nLmax));
   }
@@ -673,14 +705,15 @@ static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t 
 struct BlockMode {
   bool kt_half = false, fp32_half_block = false, use_rtc = false;
   BlockMode(const KernelSpec& sp, int64_t nLmax) {
-    kt_half = sp.precision == KKM_BF16 && sp.kind == KKM_RBF;
+    kt_half = sp.precision != KKM_FP32 && sp.kind == KKM_RBF;
     fp32_half_block = kt_half && sp.d < kBf16TensorMinDim;
     use_rtc = sp.kind == KKM_RMSD && nLmax >= kRmsdTcMinRefs;
   }
   // near-tie window of the re-score (0: no re-score, FP32 blocks)
   float flag_tau(const KernelSpec& sp) const {
     if (sp.precision == KKM_FP32) return 0.0f;
-    return fp32_half_block ? kRescoreMarginHalf : kRescoreMargin;
+    if (fp32_half_block) return kRescoreMarginHalf;
+    return sp.precision == KKM_FP8 ? kRescoreMarginFp8 : kRescoreMargin;
   }
 };
 
@@ -695,6 +728,9 @@ static kkm_status block_kernel(const KernelSpec& sp, const BlockMode& bm, const 
   else if (sp.precision == KKM_BF16)
     KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
                               b.XLb, b.nXLb, b.Xib, b.nXib, tc_err, bs));
+  else if (sp.precision == KKM_FP8)
+    KKM_TRY(kernel_block_fp8(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
+                             b.XL8, b.sXL, b.nXLb, b.Xi8, b.sXi, b.nXib, tc_err, bs));
   else
     KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
                          bm.use_rtc ? &b.rtc : nullptr));
@@ -908,8 +944,10 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     return invalid("unknown iteration form");
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
-  if (opt.precision != KKM_FP32 && opt.precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
-  if (opt.precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  if (opt.precision != KKM_FP32 && opt.precision != KKM_BF16 && opt.precision != KKM_FP8)
+    return invalid("precision must be KKM_FP32, KKM_BF16 or KKM_FP8");
+  if (opt.precision != KKM_FP32 && sp.kind == KKM_RMSD)
+    return invalid("KKM_BF16 and KKM_FP8 apply to the RBF and linear kernels");
   sp.precision = opt.precision;
   if (sp.kind != KKM_LINEAR && !isfinite(sp.sigma)) return invalid("sigma must be finite");
   const std::vector<BatchGeom> geo = batch_geometry(N, B, opt.sampling);
@@ -1024,7 +1062,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(ws.alloc(&rowaux, 1));
   KKM_TRY(ws.alloc(&kcol, ldk));
   int* tc_err = nullptr;
-  if (sp.precision == KKM_BF16) {
+  if (sp.precision != KKM_FP32) {
     KKM_TRY(ws.alloc(&tc_err, 1));
     KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
   }
@@ -1371,8 +1409,10 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
                                      const kkm_kernel* k, int32_t precision, float* out, cudaStream_t st) {
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
-  if (precision != KKM_FP32 && precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
-  if (precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  if (precision != KKM_FP32 && precision != KKM_BF16 && precision != KKM_FP8)
+    return invalid("precision must be KKM_FP32, KKM_BF16 or KKM_FP8");
+  if (precision != KKM_FP32 && sp.kind == KKM_RMSD)
+    return invalid("KKM_BF16 and KKM_FP8 apply to the RBF and linear kernels");
   sp.precision = precision;
   if (nA < 0 || nB < 0 || nA > INT32_MAX || nB > INT32_MAX) return invalid("bad sizes");
   if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
@@ -1407,6 +1447,21 @@ static kkm_status kernel_matrix_impl(const float* A_in, int64_t nA, const float*
     KKM_CK(cudaMemsetAsync(err, 0, 4, st));
     KKM_TRY(kernel_block_bf16(sp, Ap, nullptr, nA, Bp, nB, o, false, nB, Ab, nAb, Bb, nBb, err, st));
     KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
+  } else if (precision == KKM_FP8) {
+    const int64_t ld8 = round_up(sp.dp, 16);
+    uint8_t *A8, *B8;
+    float *sA, *sB, *nA8, *nB8;
+    int* err;
+    KKM_TRY(ws.alloc(&A8, nA * ld8));
+    KKM_TRY(ws.alloc(&B8, nB * ld8));
+    KKM_TRY(ws.alloc(&sA, nA));
+    KKM_TRY(ws.alloc(&sB, nB));
+    KKM_TRY(ws.alloc(&nA8, nA));
+    KKM_TRY(ws.alloc(&nB8, nB));
+    KKM_TRY(ws.alloc(&err, 1));
+    KKM_CK(cudaMemsetAsync(err, 0, 4, st));
+    KKM_TRY(kernel_block_fp8(sp, Ap, nullptr, nA, Bp, nB, o, false, nB, A8, sA, nA8, B8, sB, nB8, err, st));
+    KKM_CK(cudaMemcpyAsync(&tc_err_h, err, 4, cudaMemcpyDeviceToHost, st));
   } else if (sp.kind == KKM_RMSD && nA >= kRmsdTcMinRefs) {
     // the MD kernel takes the same tensor-core estimate + exact-refine path as a fit
     RmsdTcScratch rtc;
@@ -1439,8 +1494,10 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   if (Ni < 1 || Ni > INT32_MAX) return invalid("Ni must be >= 1");
   if (C < 1 || C > kMaxC) return invalid("C must be in [1, 256]");
   if (nL < 1 || nL > Ni || !L || !u_in || !Xb_in) return invalid("bad landmarks or NULL pointer");
-  if (precision != KKM_FP32 && precision != KKM_BF16) return invalid("precision must be KKM_FP32 or KKM_BF16");
-  if (precision == KKM_BF16 && sp.kind == KKM_RMSD) return invalid("KKM_BF16 applies to the RBF and linear kernels");
+  if (precision != KKM_FP32 && precision != KKM_BF16 && precision != KKM_FP8)
+    return invalid("precision must be KKM_FP32, KKM_BF16 or KKM_FP8");
+  if (precision != KKM_FP32 && sp.kind == KKM_RMSD)
+    return invalid("KKM_BF16 and KKM_FP8 apply to the RBF and linear kernels");
   if (iteration != KKM_ITER_AUTO && iteration != KKM_ITER_FUSED && iteration != KKM_ITER_SPLIT)
     return invalid("unknown iteration form");
   sp.precision = precision;
@@ -1469,7 +1526,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   KKM_TRY(ws.alloc(&fh, Ni * C));
   KKM_TRY(ws.alloc(&mg, Ni));
   KKM_TRY(ws.alloc(&gh, C));
-  if (sp.precision == KKM_BF16) {
+  if (sp.precision != KKM_FP32) {
     KKM_TRY(ws.alloc(&tc_err, 1));
     KKM_CK(cudaMemsetAsync(tc_err, 0, 4, st));
   }

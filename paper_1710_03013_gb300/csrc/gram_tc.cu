@@ -1,5 +1,6 @@
 // Kernel-block evaluation on the 5th-generation tensor cores (tcgen05) in
-// BF16 with FP32 accumulation (the precision option KKM_BF16).
+// BF16 (the precision option KKM_BF16) or FP8 e4m3 with a scale per row
+// (KKM_FP8), with FP32 accumulation.
 //
 //   out[n][m] = kappa(P_n, Q_m),  kappa = exp(-max(0, |p|^2 + |q|^2 - 2 p.q) / (2 sigma^2))
 //
@@ -16,6 +17,13 @@
 // FP32 accumulation: its error scales with |p - q|, not with the norms, and
 // near-duplicate pairs do not cancel catastrophically.
 //
+// FP8: row r is stored as e4m3 codes of x / s_r, s_r = max_c |x_rc| / 448
+// (the largest finite e4m3 value), so each row uses the whole e4m3 range;
+// the MMA (kind::f8f6f4, K = 32 per instruction) sums the products of the
+// codes exactly in FP32 and the epilogue multiplies by s_p s_q.  A stage
+// holds 128 e4m3 values per row: the same 128-byte swizzle rows and byte
+// offsets as the BF16 stage of 64 values.
+//
 // Structure: persistent CTAs (one per SM), 10 warps:
 //   warp 0      TMA producer (one elected lane), 4-stage ring of 48 KB stages
 //   warp 1      TMEM owner (allocates all 512 columns) and MMA issuer
@@ -29,6 +37,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 
@@ -92,6 +101,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ __forceinline__ void umma_fp8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -128,6 +145,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t tc_idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
+// The same for kind::f8f6f4 with e4m3 A and B (format code 0).
+__host__ __device__ constexpr uint32_t tc_idesc_e4m3() {
+  return (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
 
 struct TcShared {
   uint64_t full[TC_STAGES];
@@ -137,6 +158,7 @@ struct TcShared {
   uint32_t tmem_base;
   int abort_flag;
   float nP[8][TC_N / 2];    // reference norms of the current tile, per epilogue warp
+  float sP[8][TC_N / 2];    // FP8: reference row scales of the current tile
 };
 
 __device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
@@ -155,12 +177,14 @@ __device__ __forceinline__ void store_out(__half* p, float v) { *p = __float2hal
 // (a sign test of the QCP characteristic polynomial and its derivatives, no
 // root iteration); else 1 and the QCP rotation (a unit quaternion) to
 // quat[l * ldo + s] for the exact residual pass.
-template <int KIND, typename OutT>
+template <int KIND, typename OutT, bool FP8 = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapP,
                int nQ, int nP, int dk, const float* __restrict__ normQ, const float* __restrict__ normP,
                float neg_scale, OutT* __restrict__ out, int64_t ldo, int* __restrict__ err, float inv_n,
-               float4* __restrict__ quat) {
+               float4* __restrict__ quat, const float* __restrict__ scaleQ = nullptr,
+               const float* __restrict__ scaleP = nullptr) {
+  constexpr int EK = FP8 ? 2 * TC_K : TC_K;  // K elements per stage (128 bytes per row either way)
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // stages must start on a 1024-byte boundary (swizzle atom)
   uint8_t* stages = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -169,7 +193,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
   static_assert(TC_THREADS == 320, "two control warps and eight epilogue warps");
   const int tiles_m = (nQ + TC_M - 1) / TC_M, tiles_n = (nP + TC_N - 1) / TC_N;
   const int n_tiles = tiles_m * tiles_n;
-  const int nk = (dk + TC_K - 1) / TC_K;
+  const int nk = (dk + EK - 1) / EK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -208,8 +232,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
           uint8_t* a = stages + (size_t)s * TC_STAGE_BYTES;
           uint8_t* b = a + TC_A_BYTES;
           mbar_expect_tx(&sh.full[s], TC_STAGE_BYTES);
-          tma_load_2d(&mapQ, &sh.full[s], a, kb * TC_K, tm * TC_M);
-          tma_load_2d(&mapP, &sh.full[s], b, kb * TC_K, tn * TC_N);
+          tma_load_2d(&mapQ, &sh.full[s], a, kb * EK, tm * TC_M);
+          tma_load_2d(&mapP, &sh.full[s], b, kb * EK, tn * TC_N);
           if (++s == TC_STAGES) {
             s = 0;
             ph ^= 1u;
@@ -228,7 +252,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       uint32_t ph = 0;
       bool ok = true;
       int lt = 0;
-      const uint32_t idesc = tc_idesc();
+      const uint32_t idesc = FP8 ? tc_idesc_e4m3() : tc_idesc();
       for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++lt) {
         const int buf = lt & 1;
         const uint32_t tph = (uint32_t)(lt >> 1) & 1u;
@@ -246,9 +270,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
           tc_fence_after();
           const uint32_t a = smem_u32(stages + (size_t)s * TC_STAGE_BYTES);
           const uint32_t b = a + TC_A_BYTES;
+          // 4 instructions of 32 bytes per row: K = 16 BF16 or K = 32 e4m3 values each
 #pragma unroll
-          for (int k = 0; k < TC_K / 16; ++k)
-            umma_bf16(d_tmem, sw128_desc(a + k * 32), sw128_desc(b + k * 32), idesc, (kb | k) != 0);
+          for (int k = 0; k < TC_K / 16; ++k) {
+            if constexpr (FP8)
+              umma_fp8(d_tmem, sw128_desc(a + k * 32), sw128_desc(b + k * 32), idesc, (kb | k) != 0);
+            else
+              umma_bf16(d_tmem, sw128_desc(a + k * 32), sw128_desc(b + k * 32), idesc, (kb | k) != 0);
+          }
           umma_commit(&sh.empty[s]);
           if (++s == TC_STAGES) {
             s = 0;
@@ -277,6 +306,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
         for (int c = lane; c < TC_N / 2; c += 32) {
           const int n = n0 + c;
           sh.nP[ew][c] = n < nP ? normP[n] : 0.0f;
+          if constexpr (FP8) sh.sP[ew][c] = n < nP ? scaleP[n] : 0.0f;
         }
       }
       __syncwarp();
@@ -344,6 +374,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
       const int m = tm * TC_M + q * 32 + lane;
       const bool mvalid = m < nQ;
       const float nq = mvalid ? normQ[m] : 0.0f;
+      const float sq = (FP8 && mvalid) ? scaleQ[m] : 1.0f;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TC_N + half * (TC_N / 2));
       const int ncols = min(TC_N / 2, nP - n0);  // valid reference rows of this warp (may be <= 0)
       OutT* orow = out + (int64_t)n0 * ldo + m;
@@ -355,7 +386,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
           if (c0 + 32 <= ncols) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-              const float dot = __uint_as_float(r[c]);
+              const float dot = FP8 ? __uint_as_float(r[c]) * (sq * sh.sP[ew][c0 + c]) : __uint_as_float(r[c]);
               float v;
               if (KIND == DK_LINEAR) {
                 v = dot;
@@ -370,7 +401,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
               if (c0 + c < ncols) {
-                const float dot = __uint_as_float(r[c]);
+                const float dot = FP8 ? __uint_as_float(r[c]) * (sq * sh.sP[ew][c0 + c]) : __uint_as_float(r[c]);
                 float v;
                 if (KIND == DK_LINEAR) {
                   v = dot;
@@ -416,16 +447,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// 2-D map of a row-major BF16 matrix [rows][ld] (ld elements per row, ld*2 a
-// multiple of 16 bytes), box = box_rows x TC_K, 128-byte swizzle, zero fill.
-static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 2-D map of a row-major BF16 (or e4m3) matrix [rows][ld] (ld elements per
+// row, a multiple of 16 bytes), box = box_rows x 128 bytes, 128-byte
+// swizzle, zero fill past the cols valid values.
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                     bool fp8 = false) {
   auto enc = get_encode();
   if (!enc) return false;
+  const int esize = fp8 ? 1 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};  // 128-byte rows
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -468,6 +503,38 @@ cudaError_t launch_gram_tc(int kind, const __nv_bfloat16* P, int64_t nP, const _
                             static_cast<__half*>(out), ldo, err, grid, st);
   return launch_gram_tc_t(kind, mq, mp, (int)nQ, (int)nP, dk, normP, normQ, neg_scale, static_cast<float*>(out),
                           ldo, err, grid, st);
+}
+
+cudaError_t launch_gram_tc_fp8(int kind, const uint8_t* P, int64_t nP, const uint8_t* Q, int64_t nQ, int dk, int ld8,
+                               const float* normP, const float* normQ, const float* scaleP, const float* scaleQ,
+                               float neg_scale, void* out, bool out_half, int64_t ldo, int* err, int n_sms,
+                               cudaStream_t st) {
+  if (nP <= 0 || nQ <= 0) return cudaSuccess;
+  if (ld8 % 16 != 0 || (reinterpret_cast<uintptr_t>(P) & 15) || (reinterpret_cast<uintptr_t>(Q) & 15))
+    return cudaErrorInvalidValue;
+  if (out_half && kind != DK_RBF) return cudaErrorInvalidValue;
+  if (kind != DK_RBF && kind != DK_LINEAR) return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap mq, mp;
+  if (!make_map(&mq, Q, nQ, dk, ld8, TC_M, true) || !make_map(&mp, P, nP, dk, ld8, TC_N, true))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = ceil_div(nQ, TC_M) * ceil_div(nP, TC_N);
+  const int grid = (int)std::min<int64_t>(tiles, std::max(n_sms, 1));
+  cudaError_t e;
+#define KKM_TC8(K, OT)                                                                                            \
+  e = cudaFuncSetAttribute(gram_tc_kernel<K, OT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM); \
+  if (e != cudaSuccess) return e;                                                                                 \
+  gram_tc_kernel<K, OT, true><<<grid, TC_THREADS, TC_SMEM, st>>>(mq, mp, (int)nQ, (int)nP, dk, normQ, normP,        \
+                                                                 neg_scale, static_cast<OT*>(out), ldo, err, 0.0f, \
+                                                                 nullptr, scaleQ, scaleP);
+  if (kind == DK_LINEAR) {
+    KKM_TC8(DK_LINEAR, float)
+  } else if (out_half) {
+    KKM_TC8(DK_RBF, __half)
+  } else {
+    KKM_TC8(DK_RBF, float)
+  }
+#undef KKM_TC8
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __nv_bfloat16* Q, int64_t nQ, int kp,
@@ -523,6 +590,48 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, int64_t n, int dp,
   }
   acc = warp_sum_df(acc);
   if (normsq && lane == 0) normsq[row] = df_to_float(acc);
+}
+
+// ------------------------------------------- FP32 rows -> e4m3 rows + scale
+// One warp per row: s = max_c |x_c| / 448 (1 for an all-zero row), dst[c] =
+// e4m3(clamp(x_c / s, -448, 448)) (round to nearest even) for c < dp and 0 up
+// to ld8, scale[row] = s, normsq[row] = the squared norm of the decoded row
+// s * e4m3 (double-float accumulation, rounded to FP32).
+__global__ void to_fp8_kernel(const float* __restrict__ src, int64_t n, int dp, int ld8, uint8_t* __restrict__ dst,
+                              float* __restrict__ scale, float* __restrict__ normsq) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float* s = src + row * dp;
+  uint8_t* d = dst + row * ld8;
+  float m = 0.0f;
+  for (int c = lane; c < dp; c += 32) m = fmaxf(m, fabsf(s[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+  const float sc = m > 0.0f ? m / 448.0f : 1.0f;
+  float2 acc = make_float2(0.0f, 0.0f);
+  for (int c = lane; c < ld8; c += 32) {
+    uint8_t code = 0;
+    if (c < dp) {
+      const float v = fminf(fmaxf(s[c] / sc, -448.0f), 448.0f);
+      const __nv_fp8_e4m3 q(v);
+      code = q.__x;
+      acc = df_add_sq(acc, (float)q * sc);
+    }
+    d[c] = code;
+  }
+  acc = warp_sum_df(acc);
+  if (lane == 0) {
+    scale[row] = sc;
+    normsq[row] = df_to_float(acc);
+  }
+}
+
+cudaError_t launch_to_fp8(const float* src, int64_t n, int dp, int ld8, uint8_t* dst, float* scale, float* normsq,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  to_fp8_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(src, n, dp, ld8, dst, scale, normsq);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq, cudaStream_t st) {

@@ -213,6 +213,17 @@ cudaError_t launch_rmsd_tc_estimate(const __nv_bfloat16* P, int64_t nP, const __
                                     float4* quat, int64_t ldo, int* err, int n_sms, cudaStream_t st);
 // out[k*ldo + L[k]] = 1 (the exact diagonal of a Gaussian kernel block).
 cudaError_t launch_set_diag(void* out, bool out_half, int64_t ldo, const int32_t* L, int nL, cudaStream_t st);
+// FP8 e4m3 operands with a scale per row (rows [ld8] bytes, ld8 a multiple of
+// 16): out[n*ldo + m] = kappa(P_n, Q_m) of the decoded rows s * e4m3, from
+// their squared norms and scales.  RBF (FP32 or FP16 out) and linear.
+cudaError_t launch_gram_tc_fp8(int kind, const uint8_t* P, int64_t nP, const uint8_t* Q, int64_t nQ, int dk, int ld8,
+                               const float* normP, const float* normQ, const float* scaleP, const float* scaleQ,
+                               float neg_scale, void* out, bool out_half, int64_t ldo, int* err, int n_sms,
+                               cudaStream_t st);
+// e4m3 rows [n][ld8] of FP32 rows [n][dp] with a scale per row (max |x| /
+// 448) and the squared norms of the decoded rows.
+cudaError_t launch_to_fp8(const float* src, int64_t n, int dp, int ld8, uint8_t* dst, float* scale, float* normsq,
+                          cudaStream_t st);
 // BF16 copy of FP32 rows [n][dp] with the squared norms of the rounded rows.
 cudaError_t launch_to_bf16(const float* src, int64_t n, int dp, __nv_bfloat16* dst, float* normsq,
                            cudaStream_t st);

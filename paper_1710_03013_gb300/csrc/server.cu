@@ -68,6 +68,7 @@ static uint64_t fit_bytes(const kkm_problem& p) {
   blk += 4ull * nL * dp + 12ull * nL;               // landmark rows
   blk += 4ull * nL * ldk;                           // the kernel block
   if (p.opt.precision == KKM_BF16) blk += 2ull * (Nmax + nL) * dp + 4ull * (Nmax + nL);
+  if (p.opt.precision == KKM_FP8) blk += (uint64_t)(Nmax + nL) * round_up(dp, 16) + 8ull * (Nmax + nL);
   if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: split-BF16 planes, rotations, refine plan
     blk += 24ull * round_up(p.kernel.n_atoms, 64) * (Nmax + nL) + 16ull * nL * ldk + 8ull * nL +
            4ull * ceil_div(nL, 32) * ceil_div(Nmax, 64);

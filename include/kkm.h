@@ -148,6 +148,57 @@ kkm_status kkm_fit(const float* X, int64_t N, int64_t d, int32_t C, int32_t B,
                    const kkm_options* opt, int32_t* labels_out,
                    kkm_model** model_out);
 
+/* The state of a fit between two mini-batches: what Algorithm 1 carries from
+ * one outer iteration to the next (the global medoids and their cumulative
+ * counts of Eq. 11-13), the bandwidth in use, the trace and the centre
+ * displacements so far, and the arguments of the fit that made it.  Host
+ * memory only; nothing on the device.                                       */
+typedef struct kkm_checkpoint kkm_checkpoint;
+
+/*
+ * kkm_fit_range -- kkm_fit over the mini-batches [start, stop) only, so that a
+ * long fit can be stopped after any mini-batch and resumed later, in this
+ * process or another one.  The paper runs Algorithm 1 in one pass; this is a
+ * library service around its outer loop.
+ *   from     NULL: start = 0 (k-means++ or init_medoids, the bandwidth rule);
+ *            else a checkpoint of an earlier call with the same X (same rows
+ *            in the same order), N, d, C, B, s, kernel, iters, seed and
+ *            opt.precision / sampling / early_stop / init_medoids (given or
+ *            not); start = its next mini-batch.  Other arguments give
+ *            KKM_EINVAL.  opt.pipeline, opt.iteration and opt.stream may
+ *            differ between calls.
+ *   stop     one past the last mini-batch of this call, start < stop <= B.
+ *   labels_out [N] int32 (device or host, nullable): the labels of the rows
+ *            of mini-batches [start, stop); other rows keep their values.
+ *   model_out  nullable; only with stop == B (else KKM_EINVAL).
+ *   ckpt_out   nullable; receives a new checkpoint after mini-batch stop - 1
+ *            (free with kkm_checkpoint_free).
+ * Calls over [0, b1), [b1, b2), ..., [bk, B) chained through their
+ * checkpoints give the labels, model, trace and displacements of one kkm_fit
+ * call with the same arguments, bit for bit.  Errors as kkm_fit.
+ */
+kkm_status kkm_fit_range(const float* X, int64_t N, int64_t d, int32_t C,
+                         int32_t B, double s, const kkm_kernel* k,
+                         int32_t iters, uint64_t seed, const kkm_options* opt,
+                         const kkm_checkpoint* from, int32_t stop,
+                         int32_t* labels_out, kkm_model** model_out,
+                         kkm_checkpoint** ckpt_out);
+
+/* kkm_checkpoint_info -- the next mini-batch, B, C and the bandwidth of a
+ * checkpoint; medoids_out [C] int64 (host, nullable) gets the global medoids
+ * (sample indices) after mini-batch next_batch - 1.  Outputs are nullable. */
+kkm_status kkm_checkpoint_info(const kkm_checkpoint* c, int32_t* next_batch,
+                               int32_t* B, int32_t* C, float* sigma,
+                               int64_t* medoids_out);
+
+/* kkm_checkpoint_save / kkm_checkpoint_load -- a checkpoint to and from a
+ * little-endian file with the magic "KKMCKP01".  Loading checks every field
+ * (sizes, ranges, the file length) and gives KKM_EINVAL for a file that is
+ * not a consistent checkpoint.  Host only; synchronous. */
+kkm_status kkm_checkpoint_save(const kkm_checkpoint* c, const char* path);
+kkm_status kkm_checkpoint_load(const char* path, kkm_checkpoint** out);
+void kkm_checkpoint_free(kkm_checkpoint* c);
+
 /* One problem of a batched fit: the arguments of one kkm_fit call. */
 typedef struct kkm_problem {
   const float* X;       /* [N][d] device or host                            */

@@ -927,7 +927,8 @@ kkm_status model_alloc_device(kkm_model* m) {
 
 static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, int32_t B, double s,
                            const kkm_kernel* k, int32_t iters, uint64_t seed, const kkm_options* opt_in,
-                           int32_t* labels_out, kkm_model** model_out) {
+                           int32_t* labels_out, kkm_model** model_out, const kkm_checkpoint* from = nullptr,
+                           int32_t stop = -1, kkm_checkpoint** ckpt_out = nullptr) {
   kkm_options opt;
   kkm_options_default(&opt);
   if (opt_in) opt = *opt_in;
@@ -964,6 +965,24 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     for (int64_t v : init)
       if (v < 0 || v >= N) return invalid("init_medoids out of range");
   }
+  // the mini-batches of this call: [start, stop) (a checkpoint resumes at its
+  // next mini-batch; the call must repeat the arguments it was made with)
+  if (stop < 0) stop = B;
+  const int start = from ? from->next_batch : 0;
+  if (from) {
+    const bool same = from->N == N && from->d == d && from->C == C && from->B == B && from->s == s &&
+                      from->kind == k->kind && from->n_atoms == k->n_atoms &&
+                      (k->kind == KKM_LINEAR || from->sigma_arg == k->sigma) && from->iters == iters &&
+                      from->seed == seed && from->precision == opt.precision && from->sampling == opt.sampling &&
+                      from->early_stop == opt.early_stop && from->had_init == (opt.init_medoids ? 1 : 0);
+    if (!same) return invalid("the checkpoint was made by a fit with other arguments");
+    if ((int64_t)from->M.size() != C || (int64_t)from->W.size() != C ||
+        (int64_t)from->displacement.size() != start || from->omega.size() != from->changed.size() ||
+        (int64_t)from->omega.size() > (int64_t)start * iters || start < 1 || start >= B)
+      return invalid("inconsistent checkpoint");
+  }
+  if (stop <= start || stop > B) return invalid("the mini-batch range is empty or beyond B");
+  if (model_out && stop != B) return invalid("a model needs the last mini-batch (stop == B)");
 
   cudaStream_t st = (cudaStream_t)opt.stream;
   int dev = 0;
@@ -998,7 +1017,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     }
     L_off[i + 1] = (int64_t)L_all.size();
   }
-  const bool do_kpp = init.empty();
+  const bool do_kpp = init.empty() && start == 0;
   std::vector<double> draws(C, 0.0);
   std::vector<int32_t> pick0(1, 0);
   if (do_kpp) {
@@ -1006,8 +1025,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     pick0[0] = (int32_t)floor(draws[0] * (double)geo[0].Ni);
   }
 
-  // ---- bandwidth
-  if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
+  // ---- bandwidth (a resumed fit keeps the one it started with)
+  const float sigma_arg = sp.sigma;
+  if (from) {
+    sp.sigma = from->sigma;
+  } else if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
     float sig = 1.0f;
     KKM_TRY(median_bandwidth_dev(sp, X, N, bw_seed, ws, &sig));
     sp.sigma = sig;
@@ -1070,7 +1092,20 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(alloc_loop(ws, (int)nLmax, C, ldk, trace_cap, &lb, sp.gaussian()));
   Supports& S = lb.S;
   IterState& I = lb.I;
-  if (do_kpp) {
+  if (from) {
+    // the outer loop's state after mini-batch start - 1: medoids, counts, the
+    // trace and the displacements so far
+    const int32_t tc0 = (int32_t)from->omega.size();
+    KKM_CK(cudaMemcpyAsync(Mg, from->M.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
+    KKM_CK(cudaMemcpyAsync(W, from->W.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
+    if (tc0 > 0) {
+      KKM_CK(cudaMemcpyAsync(I.trace_omega, from->omega.data(), (size_t)tc0 * 8, cudaMemcpyHostToDevice, st));
+      KKM_CK(cudaMemcpyAsync(I.trace_changed, from->changed.data(), (size_t)tc0 * 4, cudaMemcpyHostToDevice, st));
+    }
+    KKM_CK(cudaMemcpyAsync(disp, from->displacement.data(), (size_t)start * 8, cudaMemcpyHostToDevice, st));
+    KKM_CK(cudaMemcpyAsync(I.trace_count, &tc0, 4, cudaMemcpyHostToDevice, st));
+    KKM_CK(cudaStreamSynchronize(st));  // tc0 lives on this stack frame
+  } else if (do_kpp) {
     KKM_TRY(ws.alloc(&D2, 2 * geo[0].Ni + ceil_div(geo[0].Ni, 256)));
     KKM_TRY(ws.alloc(&draws_d, C));
     KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
@@ -1079,13 +1114,18 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaMemcpyAsync(Mg, init.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
   }
   KKM_CK(cudaMemcpyAsync(Ld_all, L_all.data(), L_all.size() * 4, cudaMemcpyHostToDevice, st));
-  KKM_CK(cudaMemsetAsync(W, 0, (size_t)C * 8, st));
+  if (!from) KKM_CK(cudaMemsetAsync(W, 0, (size_t)C * 8, st));
   const bool labels_on_host = labels_out && !is_device_ptr(labels_out);
   if (labels_out) {
-    if (labels_on_host)
+    if (labels_on_host) {
       KKM_TRY(ws.alloc(&labels_dev, N));
-    else
+      // a partial range writes only its own rows: the others keep the
+      // caller's values
+      if (start > 0 || stop < B)
+        KKM_CK(cudaMemcpyAsync(labels_dev, labels_out, (size_t)N * 4, cudaMemcpyHostToDevice, st));
+    } else {
       labels_dev = labels_out;
+    }
   }
   const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
 
@@ -1108,8 +1148,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   FitStreams fs;
   KKM_TRY(fs.start(st, overlap));
   const cudaStream_t ms = fs.main;
-  if (overlap) KKM_TRY(block_step(0, bb[0], fs.side));
-  for (int i = 0; i < B; ++i) {
+  if (overlap) KKM_TRY(block_step(start, bb[start % nbuf], fs.side));
+  for (int i = start; i < stop; ++i) {
     NvtxRange nv_batch("mini-batch");
     const BatchGeom& g = geo[i];
     const int Ni = (int)g.Ni;
@@ -1121,7 +1161,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       // next one into the other buffer set, whose last reader (mini-batch
       // i - 1) is queued on the main stream before this point
       KKM_TRY(FitStreams::after(fs.side, ms));
-      if (i + 1 < B) {
+      if (i + 1 < stop) {
         KKM_TRY(FitStreams::after(ms, fs.side));
         KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side));
       }
@@ -1277,6 +1317,42 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   if (it_err_h) {
     set_error("fused inner iteration: the bounded grid-barrier wait gave up");
     return KKM_ETIMEOUT;
+  }
+  if (ckpt_out) {
+    std::unique_ptr<kkm_checkpoint> c(new kkm_checkpoint());
+    c->N = N;
+    c->d = d;
+    c->C = C;
+    c->B = B;
+    c->s = s;
+    c->kind = k->kind;
+    c->n_atoms = k->n_atoms;
+    c->iters = iters;
+    c->sigma_arg = sigma_arg;
+    c->seed = seed;
+    c->precision = opt.precision;
+    c->sampling = opt.sampling;
+    c->early_stop = opt.early_stop;
+    c->had_init = opt.init_medoids ? 1 : 0;
+    c->next_batch = stop;
+    c->sigma = sp.sigma;
+    c->M.resize(C);
+    c->W.resize(C);
+    c->displacement.resize(stop);
+    int32_t tc = 0;
+    KKM_CK(cudaMemcpyAsync(c->M.data(), Mg, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(c->W.data(), W, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(c->displacement.data(), disp, (size_t)stop * 8, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaMemcpyAsync(&tc, I.trace_count, 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    c->omega.resize(tc);
+    c->changed.resize(tc);
+    if (tc > 0) {
+      KKM_CK(cudaMemcpyAsync(c->omega.data(), I.trace_omega, (size_t)tc * 8, cudaMemcpyDeviceToHost, st));
+      KKM_CK(cudaMemcpyAsync(c->changed.data(), I.trace_changed, (size_t)tc * 4, cudaMemcpyDeviceToHost, st));
+      KKM_CK(cudaStreamSynchronize(st));
+    }
+    *ckpt_out = c.release();
   }
   if (model_out && *model_out) {
     kkm_model* m = *model_out;
@@ -1661,6 +1737,43 @@ kkm_status kkm_fit(const float* X, int64_t N, int64_t d, int32_t C, int32_t B, d
   }
   return r;
 }
+
+kkm_status kkm_fit_range(const float* X, int64_t N, int64_t d, int32_t C, int32_t B, double s, const kkm_kernel* k,
+                         int32_t iters, uint64_t seed, const kkm_options* opt, const kkm_checkpoint* from,
+                         int32_t stop, int32_t* labels_out, kkm_model** model_out, kkm_checkpoint** ckpt_out) {
+  set_error("");
+  if (model_out) *model_out = nullptr;
+  if (ckpt_out) *ckpt_out = nullptr;
+  if (stop < 1) return invalid("stop must be >= 1");
+  if (from && from->next_batch >= from->B) return invalid("the checkpoint's fit is complete (next_batch == B)");
+  kkm_status r = guarded(
+      [&] { return fit_impl(X, N, d, C, B, s, k, iters, seed, opt, labels_out, model_out, from, stop, ckpt_out); });
+  if (r != KKM_OK) {
+    if (model_out && *model_out) {
+      delete *model_out;
+      *model_out = nullptr;
+    }
+    if (ckpt_out && *ckpt_out) {
+      delete *ckpt_out;
+      *ckpt_out = nullptr;
+    }
+  }
+  return r;
+}
+
+kkm_status kkm_checkpoint_info(const kkm_checkpoint* c, int32_t* next_batch, int32_t* B, int32_t* C, float* sigma,
+                               int64_t* medoids_out) {
+  set_error("");
+  if (!c) return invalid("checkpoint is NULL");
+  if (next_batch) *next_batch = c->next_batch;
+  if (B) *B = c->B;
+  if (C) *C = c->C;
+  if (sigma) *sigma = c->sigma;
+  if (medoids_out) memcpy(medoids_out, c->M.data(), c->M.size() * 8);
+  return KKM_OK;
+}
+
+void kkm_checkpoint_free(kkm_checkpoint* c) { delete c; }
 
 kkm_status kkm_assign(const kkm_model* m, const float* Xnew, int64_t M, int32_t mode, int32_t* labels_out,
                       float* dist_out, void* stream) {

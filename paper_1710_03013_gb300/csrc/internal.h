@@ -13,6 +13,26 @@
 
 #include "../../include/kkm.h"
 
+// The state of Algorithm 1's outer loop between two mini-batches (kkm_fit_range):
+// the arguments it was started with (a resume must repeat them), the next
+// mini-batch, the bandwidth in use, the global medoids and their counts, and
+// the trace so far.
+struct kkm_checkpoint {
+  int64_t N = 0, d = 0;
+  int32_t C = 0, B = 0;
+  double s = 0.0;
+  int32_t kind = 0, n_atoms = 0, iters = 0;
+  float sigma_arg = 0.0f;       // the sigma the fit was called with (<= 0: median rule)
+  uint64_t seed = 0;
+  int32_t precision = 0, sampling = 0, early_stop = 0, had_init = 0;
+  int32_t next_batch = 0;
+  float sigma = 0.0f;           // the bandwidth in use
+  std::vector<int64_t> M, W;    // [C] global medoids, cumulative counts
+  std::vector<double> omega;
+  std::vector<int32_t> changed;
+  std::vector<double> displacement;  // [next_batch]
+};
+
 // The model behind the opaque kkm_model handle: device copies of what
 // kkm_assign / kkm_cost need, plus host copies of the reported results.
 struct kkm_model {

@@ -222,6 +222,111 @@ static kkm_status load_impl(const char* path, kkm_model** out) {
   return KKM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints of a fit between mini-batches (kkm_fit_range).  Format
+// (little-endian): magic "KKMCKP01"; int64 N, d; int32 C, B; float64 s;
+// int32 kind, n_atoms, iters; float32 sigma_arg; uint64 seed; int32
+// precision, sampling, early_stop, had_init, next_batch; float32 sigma;
+// int64 T; then int64 M[C], int64 W[C], float64 omega[T], int32 changed[T],
+// float64 displacement[next_batch].  Every field is written on its own, so
+// the layout does not depend on structure padding.
+static const char kCkptMagic[8] = {'K', 'K', 'M', 'C', 'K', 'P', '0', '1'};
+
+static kkm_status ckpt_save_impl(const kkm_checkpoint* c, const char* path) {
+  if (!c || !path) return fail("checkpoint and path must not be NULL");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(std::string("cannot open ") + path + " for writing");
+  Io io{f};
+  const int64_t T = (int64_t)c->omega.size();
+  io.put(kCkptMagic, 8);
+  io.put(&c->N, 8);
+  io.put(&c->d, 8);
+  io.put(&c->C, 4);
+  io.put(&c->B, 4);
+  io.put(&c->s, 8);
+  io.put(&c->kind, 4);
+  io.put(&c->n_atoms, 4);
+  io.put(&c->iters, 4);
+  io.put(&c->sigma_arg, 4);
+  io.put(&c->seed, 8);
+  io.put(&c->precision, 4);
+  io.put(&c->sampling, 4);
+  io.put(&c->early_stop, 4);
+  io.put(&c->had_init, 4);
+  io.put(&c->next_batch, 4);
+  io.put(&c->sigma, 4);
+  io.put(&T, 8);
+  io.put(c->M.data(), c->M.size() * 8);
+  io.put(c->W.data(), c->W.size() * 8);
+  io.put(c->omega.data(), (size_t)T * 8);
+  io.put(c->changed.data(), (size_t)T * 4);
+  io.put(c->displacement.data(), c->displacement.size() * 8);
+  const bool closed = fclose(f) == 0;
+  if (!io.ok || !closed) return fail(std::string(path) + ": write failed");
+  return KKM_OK;
+}
+
+static kkm_status ckpt_load_impl(const char* path, kkm_checkpoint** out) {
+  if (!path || !out) return fail("path and out must not be NULL");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(std::string("cannot open ") + path);
+  std::unique_ptr<FILE, int (*)(FILE*)> fguard(f, fclose);
+  fseek(f, 0, SEEK_END);
+  const long len = ftell(f);
+  fseek(f, 0, SEEK_SET);
+  Io io{f};
+  char magic[8] = {0};
+  io.get(magic, 8);
+  if (!io.ok || memcmp(magic, kCkptMagic, 8) != 0) return fail(std::string(path) + ": not a kkm checkpoint");
+  std::unique_ptr<kkm_checkpoint> c(new kkm_checkpoint());
+  int64_t T = 0;
+  io.get(&c->N, 8);
+  io.get(&c->d, 8);
+  io.get(&c->C, 4);
+  io.get(&c->B, 4);
+  io.get(&c->s, 8);
+  io.get(&c->kind, 4);
+  io.get(&c->n_atoms, 4);
+  io.get(&c->iters, 4);
+  io.get(&c->sigma_arg, 4);
+  io.get(&c->seed, 8);
+  io.get(&c->precision, 4);
+  io.get(&c->sampling, 4);
+  io.get(&c->early_stop, 4);
+  io.get(&c->had_init, 4);
+  io.get(&c->next_batch, 4);
+  io.get(&c->sigma, 4);
+  io.get(&T, 8);
+  if (!io.ok) return fail(std::string(path) + ": truncated header");
+  const bool sane = c->N >= 1 && c->N <= INT32_MAX && c->d >= 1 && c->C >= 1 && c->C <= kMaxC && c->B >= 1 &&
+                    c->B <= c->N && c->s > 0.0 && c->s <= 1.0 && c->iters >= 0 && c->next_batch >= 1 &&
+                    c->next_batch <= c->B && T >= 0 && T <= (int64_t)c->next_batch * c->iters &&
+                    (c->kind == KKM_RBF || c->kind == KKM_LINEAR || c->kind == KKM_RMSD) &&
+                    (c->precision == KKM_FP32 || c->precision == KKM_BF16 || c->precision == KKM_FP8) &&
+                    (c->sampling == KKM_STRIDE || c->sampling == KKM_BLOCK) &&
+                    (c->early_stop == 0 || c->early_stop == 1) && (c->had_init == 0 || c->had_init == 1);
+  if (!sane) return fail(std::string(path) + ": inconsistent checkpoint header");
+  const int64_t header = 8 + 8 + 8 + 4 + 4 + 8 + 4 + 4 + 4 + 4 + 8 + 4 * 5 + 4 + 8;
+  const int64_t body = (int64_t)c->C * 16 + T * 12 + (int64_t)c->next_batch * 8;
+  if ((int64_t)len != header + body) return fail(std::string(path) + ": file length disagrees with its header");
+  c->M.resize(c->C);
+  c->W.resize(c->C);
+  c->omega.resize((size_t)T);
+  c->changed.resize((size_t)T);
+  c->displacement.resize(c->next_batch);
+  io.get(c->M.data(), (size_t)c->C * 8);
+  io.get(c->W.data(), (size_t)c->C * 8);
+  io.get(c->omega.data(), (size_t)T * 8);
+  io.get(c->changed.data(), (size_t)T * 4);
+  io.get(c->displacement.data(), (size_t)c->next_batch * 8);
+  if (!io.ok) return fail(std::string(path) + ": truncated");
+  for (int64_t m : c->M)
+    if (m < 0 || m >= c->N) return fail(std::string(path) + ": medoid index out of range");
+  *out = c.release();
+  return KKM_OK;
+}
+
 }  // namespace kkm
 
 extern "C" kkm_status kkm_model_save(const kkm_model* m, const char* path) {
@@ -238,6 +343,26 @@ extern "C" kkm_status kkm_model_load(const char* path, kkm_model** out) {
   kkm::set_error("");
   try {
     return kkm::load_impl(path, out);
+  } catch (...) {
+    kkm::set_error("internal exception");
+    return KKM_EINTERNAL;
+  }
+}
+
+extern "C" kkm_status kkm_checkpoint_save(const kkm_checkpoint* c, const char* path) {
+  kkm::set_error("");
+  try {
+    return kkm::ckpt_save_impl(c, path);
+  } catch (...) {
+    kkm::set_error("internal exception");
+    return KKM_EINTERNAL;
+  }
+}
+
+extern "C" kkm_status kkm_checkpoint_load(const char* path, kkm_checkpoint** out) {
+  kkm::set_error("");
+  try {
+    return kkm::ckpt_load_impl(path, out);
   } catch (...) {
     kkm::set_error("internal exception");
     return KKM_EINTERNAL;

@@ -77,6 +77,13 @@ _SIGNATURES = {
     "kkm_fit": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
                        ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P)]),
     "kkm_fit_batch": (_I32, [_P, _I32, _I32, _P, _P, _P]),
+    "kkm_fit_range": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64,
+                             ctypes.POINTER(kkm_options), _P, _I32, _P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "kkm_checkpoint_info": (_I32, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_F32), _P]),
+    "kkm_checkpoint_save": (_I32, [_P, ctypes.c_char_p]),
+    "kkm_checkpoint_load": (_I32, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    "kkm_checkpoint_free": (None, [_P]),
     "kkm_fit_restarts": (_I32, [_P, _I64, _I64, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64, _I32,
                                 ctypes.POINTER(kkm_options), _P, ctypes.POINTER(_P), _P, ctypes.POINTER(_I32)]),
     "kkm_elbow": (_I32, [_P, _I64, _I64, _I32, _I32, _I32, _F64, ctypes.POINTER(kkm_kernel), _I32, _U64, _I32,
@@ -291,6 +298,90 @@ def kkm_fit(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *,
                        int(seed) & ((1 << 64) - 1), ctypes.byref(opt), lab_p, ctypes.byref(h)))
     del keep, init_arr
     return lab, Model(h)
+
+
+class Checkpoint:
+    """The state of a fit between two mini-batches (owns the C handle)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.kkm_checkpoint_free(self._h)
+            self._h = None
+
+    def info(self):
+        nb, B, C, sig = _I32(), _I32(), _I32(), _F32()
+        _check(load().kkm_checkpoint_info(self._h, ctypes.byref(nb), ctypes.byref(B), ctypes.byref(C),
+                                          ctypes.byref(sig), None))
+        return {"next_batch": nb.value, "B": B.value, "C": C.value, "sigma": sig.value}
+
+    def medoids(self):
+        """The global medoids (sample indices) after the last mini-batch run."""
+        med = np.empty(self.info()["C"], np.int64)
+        _check(load().kkm_checkpoint_info(self._h, None, None, None, None, med.ctypes.data))
+        return med
+
+    def save(self, path):
+        """kkm_checkpoint_save of the C ABI."""
+        _check(load().kkm_checkpoint_save(self._h, os.fsencode(path)))
+
+    @staticmethod
+    def load(path):
+        """kkm_checkpoint_load of the C ABI."""
+        h = ctypes.c_void_p()
+        _check(load().kkm_checkpoint_load(os.fsencode(path), ctypes.byref(h)))
+        return Checkpoint(h)
+
+
+def kkm_fit_range(X, C, B, s, kind="rbf", sigma=0.0, n_atoms=0, iters=20, seed=0, *, stop,
+                  checkpoint=None, precision=KKM_FP32, sampling="stride", early_stop=True, init_medoids=None,
+                  labels=True, model=False, stream=None, pipeline="auto", iteration="auto"):
+    """kkm_fit_range of the C ABI: the mini-batches [start, stop), start = 0
+    or the checkpoint's next mini-batch.  `labels` is True (a new [N] buffer,
+    -1 in rows outside the range), an existing int32 buffer to continue, or
+    False.  Returns (labels or None, Model or None, Checkpoint)."""
+    lib = load()
+    N, d = int(X.shape[0]), int(np.prod(X.shape[1:]))
+    xp, keep = _as_input(X, np.float32)
+    k = _kernel(kind, sigma, n_atoms)
+    st = stream if stream is not None else _stream_of(X)
+    opt = _options(precision, sampling, early_stop, pipeline, iteration, st)
+    init_arr = None
+    if init_medoids is not None:
+        init_arr = np.ascontiguousarray(init_medoids, dtype=np.int64)
+        opt.init_medoids = init_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if labels is True:
+        lp, lab = _out_like(X, N, np.int32)
+        lab[:] = -1
+    elif labels is False or labels is None:
+        lp, lab = None, None
+    else:
+        lab = labels
+        is_int32 = lab.dtype == (_torch().int32 if hasattr(lab, "data_ptr") else np.int32)
+        if not is_int32 or int(np.prod(lab.shape)) != N:
+            raise ValueError("labels must be an int32 buffer of N entries")
+        if hasattr(lab, "data_ptr"):
+            if not lab.is_contiguous():
+                raise ValueError("labels must be contiguous")
+            lp = ctypes.c_void_p(lab.data_ptr())
+        else:
+            if not lab.flags["C_CONTIGUOUS"]:
+                raise ValueError("labels must be contiguous")
+            lp = ctypes.c_void_p(lab.ctypes.data)
+    h = ctypes.c_void_p()
+    ck = ctypes.c_void_p()
+    _check(lib.kkm_fit_range(xp, N, d, int(C), int(B), float(s), ctypes.byref(k), int(iters),
+                             int(seed) & ((1 << 64) - 1), ctypes.byref(opt),
+                             checkpoint.handle if checkpoint is not None else None, int(stop), lp,
+                             ctypes.byref(h) if model else None, ctypes.byref(ck)))
+    del keep, init_arr
+    return lab, (Model(h) if model else None), Checkpoint(ck)
 
 
 def _options(precision, sampling, early_stop, pipeline, iteration, stream):

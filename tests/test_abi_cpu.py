@@ -185,3 +185,93 @@ def test_noalloc_binding_rejects_bad_arguments(kkm):
     for k, (x, l, o) in enumerate(bad):
         with pytest.raises(ValueError):
             kkm._check_noalloc_args(d, x, l, o)
+
+
+def _checkpoint_bytes(N=64, d=4, C=2, B=4, s=0.5, kind=0, n_atoms=0, iters=3, sigma_arg=1.0, seed=9,
+                      precision=0, sampling=0, early_stop=1, had_init=0, next_batch=2, sigma=1.0,
+                      M=(5, 40), W=(10, 22), omega=(3.0, 2.5, 2.25), changed=(4, 1, 0), disp=(0.0, 0.125)):
+    """A checkpoint file written field by field in the documented layout."""
+    import struct
+    T = len(omega)
+    head = b"KKMCKP01" + struct.pack("<qqiidiiifQiiiiifq", N, d, C, B, s, kind, n_atoms, iters, sigma_arg, seed,
+                                     precision, sampling, early_stop, had_init, next_batch, sigma, T)
+    body = struct.pack(f"<{C}q{C}q{T}d{T}i{next_batch}d", *M, *W, *omega, *changed, *disp)
+    return head + body
+
+
+def test_checkpoint_file_round_trip_on_the_host(kkm, tmp_path):
+    """kkm_checkpoint_load reads the documented layout, kkm_checkpoint_info
+    reports it, and kkm_checkpoint_save writes the same bytes back."""
+    src = tmp_path / "a.ckpt"
+    src.write_bytes(_checkpoint_bytes())
+    c = kkm.Checkpoint.load(str(src))
+    assert c.info() == {"next_batch": 2, "B": 4, "C": 2, "sigma": 1.0}
+    assert c.medoids().tolist() == [5, 40]
+    out = tmp_path / "b.ckpt"
+    c.save(str(out))
+    assert out.read_bytes() == src.read_bytes()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(M=(5, 64)),                     # medoid index beyond N
+    dict(next_batch=5, disp=(0.0,) * 5),  # beyond B
+    dict(next_batch=0, disp=()),          # nothing run
+    dict(omega=(1.0,) * 7, changed=(0,) * 7),  # longer trace than next_batch * iters
+    dict(C=0, M=(), W=()),
+    dict(precision=5),
+    dict(kind=3),
+])
+def test_checkpoint_load_rejects_inconsistent_files(kkm, tmp_path, bad):
+    import ctypes
+    lib = kkm.load()
+    p = tmp_path / "bad.ckpt"
+    p.write_bytes(_checkpoint_bytes(**bad))
+    h = ctypes.c_void_p()
+    assert lib.kkm_checkpoint_load(str(p).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL
+    assert not h.value
+
+
+def test_checkpoint_load_rejects_truncated_and_foreign_files(kkm, tmp_path):
+    import ctypes
+    lib = kkm.load()
+    h = ctypes.c_void_p()
+    good = _checkpoint_bytes()
+    for name, data in (("short", good[:-8]), ("long", good + b"\0" * 8), ("magic", b"KKMMOD02" + good[8:]),
+                       ("empty", b"")):
+        p = tmp_path / f"{name}.ckpt"
+        p.write_bytes(data)
+        assert lib.kkm_checkpoint_load(str(p).encode(), ctypes.byref(h)) == kkm.STATUS_EINVAL, name
+        assert not h.value
+
+
+def test_fit_range_rejects_a_foreign_checkpoint_before_any_device_call(kkm, tmp_path):
+    """A checkpoint resumes only the fit that made it, over a non-empty range
+    that ends at B at most, and a model needs the last mini-batch."""
+    p = tmp_path / "a.ckpt"
+    p.write_bytes(_checkpoint_bytes())
+    c = kkm.Checkpoint.load(str(p))
+    X = np.zeros((64, 4), np.float32)
+    same = dict(kind="rbf", sigma=1.0, iters=3, seed=9, labels=False, stream=0)
+    cases = [
+        (dict(same, seed=10), 4, False),        # another seed
+        (dict(same, iters=4), 4, False),        # another iteration cap
+        (dict(same, sigma=2.0), 4, False),      # another bandwidth argument
+        (dict(same, sampling="block"), 4, False),
+        (dict(same, precision=kkm.KKM_BF16), 4, False),
+        (dict(same, early_stop=False), 4, False),
+        (dict(same, init_medoids=[1, 2]), 4, False),
+        (same, 2, False),                       # empty range
+        (same, 5, False),                       # beyond B
+        (same, 3, True),                        # a model before the last mini-batch
+    ]
+    for kw, stop, model in cases:
+        with pytest.raises(kkm.KKMError) as e:
+            kkm.kkm_fit_range(X, 2, 4, 0.5, checkpoint=c, stop=stop, model=model, **kw)
+        assert e.value.status == kkm.STATUS_EINVAL, (kw, stop, model)
+    with pytest.raises(kkm.KKMError):
+        kkm.kkm_fit_range(X[:32], 2, 4, 0.5, checkpoint=c, stop=4, **same)   # another N
+    done = tmp_path / "done.ckpt"
+    done.write_bytes(_checkpoint_bytes(next_batch=4, disp=(0.0,) * 4))
+    with pytest.raises(kkm.KKMError) as e:
+        kkm.kkm_fit_range(X, 2, 4, 0.5, checkpoint=kkm.Checkpoint.load(str(done)), stop=4, **same)
+    assert "complete" in str(e.value)

@@ -34,8 +34,9 @@ Readings of the paper (where it is silent, garbled or at odds with itself):
       first iteration that changes no label (Algorithm 1, while condition).
   R13 Omega_t of an inner iteration is sum_i min_j d_ij for the labels of that
       iteration, i.e. the cost right after the assignment (Eq. 9).
-  R18 Restarts (Section 4.5, "kept the solution with minimum cost"): the cost
-      is Eq. 1 over the whole data set against the final global medoids;
+  R18 Restarts (Section 4.5: of several k-means++ initialisations the one of
+      least cost is kept): the cost is Eq. 1 over the whole data set against
+      the final global medoids;
       restart r uses the r-th output of SplitMix64(seed); ties go to the
       lowest restart; all restarts share one bandwidth.
   R19 The elbow criterion (Sections 4.4, 4.5) is not defined in the paper:

@@ -327,7 +327,7 @@ def test_P8_partition(sampling, N, B):
             assert np.all(b % B == i)
 
 
-# Landmarks are "uniformly sampled from the mini-batch" (Section 3.2, Eq. 14).
+# Landmarks are a uniform random subset of the mini-batch (Section 3.2, Eq. 14).
 # The draw is the first k steps of a Fisher-Yates shuffle (Durstenfeld's
 # form): step a swaps position a with r = a + floor(u * (n - a)), u uniform in
 # [0, 1).  The two hand-worked cases below start from published SplitMix64

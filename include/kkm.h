@@ -82,13 +82,28 @@ typedef enum kkm_pipeline { KKM_PIPE_AUTO = 0, KKM_PIPE_SERIAL = 1, KKM_PIPE_OVE
  * it is summed, and grid barriers make g_hat (Eq. 16) and the cost available
  * to every CTA.  It applies to C <= 64 and mini-batches of up to about
  * 77,000 samples (KKM_EINVAL otherwise).
+ * KKM_ITER_TC is the same one-launch loop with the f_hat sums formed on the
+ * tensor cores, as the product of the FP16-stored Gaussian block with the
+ * one-hot matrix of the landmark labels (exact 0/1 values, FP32
+ * accumulation): one CTA per 128 samples.  It applies to the RBF kernel with
+ * KKM_BF16 or KKM_FP8, C <= 16 and mini-batches of at most 128 samples per SM
+ * (19,456 on 152 SMs) whose landmark one-hot tiles fit in shared memory
+ * (about 3,000 landmarks) (KKM_EINVAL otherwise).
  * KKM_ITER_SPLIT streams per-unit partial sums and finishes them in a second
  * launch (the two launches of an iteration chained by programmatic
- * dependent launch).  KKM_ITER_AUTO takes the split form, the faster one on
- * the benchmark workloads.  The two forms add the same values in different
- * orders: labels agree above the tolerance margin and distances to FP32
- * rounding.                                                                 */
-typedef enum kkm_iteration { KKM_ITER_AUTO = 0, KKM_ITER_FUSED = 1, KKM_ITER_SPLIT = 2 } kkm_iteration;
+ * dependent launch).  KKM_ITER_AUTO takes KKM_ITER_TC where it applies and
+ * the split form elsewhere.  Fits that run side by side (kkm_fit_batch,
+ * kkm_fit_restarts, kkm_elbow, the server) take the split form whatever the
+ * option: the one-launch forms wait at grid barriers for all their CTAs,
+ * which other fits' one-launch loops could hold off.  The forms add the same
+ * values in different orders: labels agree above the tolerance margin and
+ * distances to FP32 rounding.                                               */
+typedef enum kkm_iteration {
+  KKM_ITER_AUTO = 0,
+  KKM_ITER_FUSED = 1,
+  KKM_ITER_SPLIT = 2,
+  KKM_ITER_TC = 3
+} kkm_iteration;
 
 /* Prototypes used by kkm_assign / kkm_cost: the sparse landmark centroids
  * of the last mini-batch (Eq. 14-17) or the global medoids (Eq. 2 against
@@ -252,7 +267,8 @@ kkm_status kkm_elbow(const float* X, int64_t N, int64_t d, int32_t C_lo,
 /*
  * kkm_fit_batch -- n independent fits on one GPU at once: many data sets of
  * uneven sizes, or restarts of one data set with different seeds.  Each
- * problem gets exactly the results of kkm_fit with the same arguments.  The
+ * problem gets exactly the results of kkm_fit with the same arguments and
+ * opt.iteration = KKM_ITER_SPLIT (the loop form of fits side by side).  The
  * paper fits one data set at a time; this is a library service around
  * Algorithm 1, not a change to it.
  *   problems   [n] host array.

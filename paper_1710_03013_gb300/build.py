@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libkkm.so")
 
-SOURCES = ["api.cu", "batch.cu", "gram.cu", "gram_tc.cu", "iterate.cu", "median.cu", "model_io.cu", "noalloc.cu", "rmsd.cu", "select.cu", "server.cu"]
+SOURCES = ["api.cu", "batch.cu", "gram.cu", "gram_tc.cu", "iterate.cu", "iterate_tc.cu", "median.cu", "model_io.cu", "noalloc.cu", "rmsd.cu", "select.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -590,6 +590,7 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
   KKM_TRY(ws.alloc(&I.lm_part, parts));
   KKM_TRY(ws.alloc(&I.gcta, (int64_t)I.fused_cap * C));
   KKM_TRY(ws.alloc(&I.facc, 2 * (C + 3)));
+  if (gaussian) KKM_TRY(ws.alloc(&I.lm_list, 2 * (int64_t)nLmax));
   KKM_TRY(ws.alloc(&I.bar, 1));
   KKM_TRY(ws.alloc(&I.err, 1));
   KKM_CK(cudaMemsetAsync(I.bar, 0, 4, ws.st));
@@ -754,10 +755,36 @@ static RescoreArgs rescore_args(const KernelSpec& sp, const BlockBufs& b) {
 
 // Whether the inner iterations of a mini-batch run fused (one cooperative
 // launch each) for this option and block shape.
+// Inner-loop forms (kkm_iteration): the split pair of launches per
+// iteration, the one-launch loop on the CUDA cores, the one-launch loop with
+// the tensor-core f_hat sums.
+enum LoopForm { kLoopSplit = 0, kLoopFused = 1, kLoopTc = 2 };
+
 static bool fused_applies(int Ni, int nL, int C, int esize) {
   FusedShape F;
   size_t smem = 0;
   return fused_shape(Ni, nL, C, esize, sm_count(), &F, &smem);
+}
+// The tensor-core loop needs the FP16 Gaussian block and its fixed-point sums.
+static bool tc_applies(const KernelSpec& sp, const BlockMode& bm, int Ni, int nL, int C) {
+  int ns = 0;
+  size_t smem = 0;
+  return bm.kt_half && sp.kind == KKM_RBF && tc_iter_shape(Ni, nL, C, sm_count(), &ns, &smem);
+}
+// The loop form for an iteration option; -1 when a form asked for does not
+// apply to the shape.
+static int loop_form(int iteration, const KernelSpec& sp, const BlockMode& bm, int Ni, int nL, int C) {
+  const bool tc = tc_applies(sp, bm, Ni, nL, C);
+  switch (iteration) {
+    case KKM_ITER_TC:
+      return tc ? kLoopTc : -1;
+    case KKM_ITER_FUSED:
+      return fused_applies(Ni, nL, C, bm.kt_half ? 2 : 4) ? kLoopFused : -1;
+    case KKM_ITER_SPLIT:
+      return kLoopSplit;
+    default:  // AUTO: the tensor-core loop where it applies (measured 2x faster per iteration)
+      return tc ? kLoopTc : kLoopSplit;
+  }
 }
 
 // The inner loop of a mini-batch (Alg. 1 lines 9-16; Eq. 15-17) over the
@@ -765,10 +792,18 @@ static bool fused_applies(int Ni, int nL, int C, int esize) {
 // iteration the streaming partial sums and the assign.  Either way every
 // iteration closes on the device (trace, early stop, support re-sort).
 static kkm_status inner_loop(const BlockMode& bm, const BlockBufs& b, int64_t ldk, int Ni, const Supports& S,
-                             const IterState& I, bool fused, int iters, const float* kself, int32_t* u,
+                             const IterState& I, int form, int iters, const float* kself, int32_t* u,
                              float* margin, float* fhat_out, double* ghat_out, int early_stop, const RescoreArgs& R,
                              cudaStream_t st) {
-  if (fused) {
+  if (form == kLoopTc) {
+    KKM_RUN("iterate", st,
+            launch_iterate_tc(b.KTh, ldk, Ni, S, I, iters, u, margin, fhat_out, ghat_out, early_stop, sm_count(), st,
+                              R));
+    // the landmark labels are final: the rest of the support structure
+    KKM_RUN("build_supports", st, launch_build_supports(S, st));
+    return KKM_OK;
+  }
+  if (form == kLoopFused) {
     KKM_RUN("iterate", st,
             bm.kt_half ? launch_iterate(b.KTh, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop,
                                         sm_count(), st, R)
@@ -941,7 +976,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   if (opt.pipeline != KKM_PIPE_AUTO && opt.pipeline != KKM_PIPE_SERIAL && opt.pipeline != KKM_PIPE_OVERLAP)
     return invalid("unknown pipeline");
   if (opt.sampling != KKM_STRIDE && opt.sampling != KKM_BLOCK) return invalid("unknown sampling");
-  if (opt.iteration != KKM_ITER_AUTO && opt.iteration != KKM_ITER_FUSED && opt.iteration != KKM_ITER_SPLIT)
+  if (opt.iteration != KKM_ITER_AUTO && opt.iteration != KKM_ITER_FUSED && opt.iteration != KKM_ITER_SPLIT &&
+      opt.iteration != KKM_ITER_TC)
     return invalid("unknown iteration form");
   KernelSpec sp;
   KKM_TRY(make_spec(k, d, &sp));
@@ -1193,15 +1229,15 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
     I.flag_tau = bm.flag_tau(sp);
     const RescoreArgs R = rescore_args(sp, bk);
-    // AUTO takes the split form: measured faster on the benchmark fits (the
-    // fused loop's narrow column strips cost more L2 sector traffic than the
-    // barriers save)
-    const bool fused = opt.iteration == KKM_ITER_FUSED && fused_applies(Ni, nL, C, kt_half ? 2 : 4);
-    if (opt.iteration == KKM_ITER_FUSED && !fused)
-      return invalid("KKM_ITER_FUSED does not apply to this shape (C <= 64 and a mini-batch of at most one "
-                     "column per thread of one CTA per SM)");
+    const int form = loop_form(opt.iteration, sp, bm, Ni, nL, C);
+    if (form < 0)
+      return invalid(opt.iteration == KKM_ITER_TC
+                         ? "KKM_ITER_TC does not apply to this shape (RBF with KKM_BF16 or KKM_FP8, C <= 16, at most "
+                           "128 samples per SM in a mini-batch, about 3,000 landmarks)"
+                         : "KKM_ITER_FUSED does not apply to this shape (C <= 64 and a mini-batch of at most one "
+                           "column per thread of one CTA per SM)");
     NvtxRange nv_loop("inner loop");
-    KKM_TRY(inner_loop(bm, bk, ldk, Ni, S, I, fused, iters, kself, u, nullptr, nullptr, nullptr,  // Alg. 1 lines 9-16
+    KKM_TRY(inner_loop(bm, bk, ldk, Ni, S, I, form, iters, kself, u, nullptr, nullptr, nullptr,  // Alg. 1 lines 9-16
                        opt.early_stop, R, ms));
     I.flag_tau = 0.0f;
     // Eq. 10: f_hat of the final labels and the mini-batch medoids
@@ -1574,7 +1610,8 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
     return invalid("precision must be KKM_FP32, KKM_BF16 or KKM_FP8");
   if (precision != KKM_FP32 && sp.kind == KKM_RMSD)
     return invalid("KKM_BF16 and KKM_FP8 apply to the RBF and linear kernels");
-  if (iteration != KKM_ITER_AUTO && iteration != KKM_ITER_FUSED && iteration != KKM_ITER_SPLIT)
+  if (iteration != KKM_ITER_AUTO && iteration != KKM_ITER_FUSED && iteration != KKM_ITER_SPLIT &&
+      iteration != KKM_ITER_TC)
     return invalid("unknown iteration form");
   sp.precision = precision;
   if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f && isfinite(sp.sigma))) return invalid("sigma must be > 0");
@@ -1626,9 +1663,9 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   lb.I.keep_rows = 0;
   lb.I.flag_tau = bm.flag_tau(sp);
   const RescoreArgs R = rescore_args(sp, b);
-  const bool fused = iteration == KKM_ITER_FUSED && fused_applies((int)Ni, nL, C, bm.kt_half ? 2 : 4);
-  if (iteration == KKM_ITER_FUSED && !fused) return invalid("KKM_ITER_FUSED does not apply to this shape");
-  KKM_TRY(inner_loop(bm, b, ldk, (int)Ni, lb.S, lb.I, fused, 1, kself, u, mg, fh, gh, 0, R, st));
+  const int form = loop_form(iteration, sp, bm, (int)Ni, nL, C);
+  if (form < 0) return invalid("the iteration form asked for does not apply to this shape");
+  KKM_TRY(inner_loop(bm, b, ldk, (int)Ni, lb.S, lb.I, form, 1, kself, u, mg, fh, gh, 0, R, st));
   if (u_out) KKM_CK(cudaMemcpyAsync(u_out, u, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));
   if (fhat_out) KKM_CK(cudaMemcpyAsync(fhat_out, fh, (size_t)Ni * C * 4, cudaMemcpyDeviceToHost, st));
   if (margin_out) KKM_CK(cudaMemcpyAsync(margin_out, mg, (size_t)Ni * 4, cudaMemcpyDeviceToHost, st));

@@ -95,6 +95,7 @@ static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams,
       kkm_options opt = pr.opt;
       opt.stream = st;
       opt.pipeline = side_by_side_pipeline(opt.pipeline);
+      opt.iteration = side_by_side_iteration(opt.iteration);
       kkm_model* m = nullptr;
       const kkm_status s = kkm_fit(pr.X, pr.N, pr.d, pr.C, pr.B, pr.s, &pr.kernel, pr.iters, pr.seed, &opt,
                                    pr.labels_out, models_out ? &m : nullptr);

@@ -24,6 +24,12 @@ __device__ __forceinline__ int warp_sum_i32(int v) {
   return v;
 }
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor finishes;
+// it waits here before touching anything the predecessor wrote.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Double-float values (x = hi, y = lo): sums with about 44 significant bits
 // from FP32 operations only.  FP64 runs at 1/64 of the FP32 rate on this GPU,
 // so reductions that need more than FP32 use these (Knuth's TwoSum with a

@@ -162,6 +162,11 @@ inline bool fit_overlaps(int pipeline, int B, int kind, int precision) {
 // one another; inside each, AUTO means serial blocks (a low-priority block
 // stream would wait behind the other fits' high-priority inner loops).
 inline int side_by_side_pipeline(int pipeline) { return pipeline == KKM_PIPE_AUTO ? KKM_PIPE_SERIAL : pipeline; }
+// The one-launch loop forms hold their CTAs at grid barriers, which needs the
+// whole grid resident at once; beside other fits' one-launch loops that is
+// not assured (each could hold part of the SMs while waiting for the rest), so
+// fits that run side by side take the split form.
+inline int side_by_side_iteration(int iteration) { (void)iteration; return KKM_ITER_SPLIT; }
 
 // Kernel-function codes used on the device.
 enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3, DK_RAW = 4 /* plain products */ };
@@ -340,6 +345,9 @@ struct IterState {
   uint32_t* bar = nullptr;          // [1]
   int32_t* err = nullptr;           // [1]
   int fused_cap = 0;                // CTAs the fused buffers hold (omega_part etc. hold at least as many)
+  // tensor-core iteration (launch_iterate_tc): landmark label changes of the
+  // two alternating iterations, (ordinal << 8) | (old << 4) | new
+  int32_t* lm_list = nullptr;       // [2][nL]
 };
 // Rows of a [rows][ldk] float block that fit in the given share of L2.
 int l2_keep_rows(int64_t ldk, int rows, double share, int elem_bytes = 4);
@@ -397,6 +405,18 @@ cudaError_t launch_iterate(const float* KT, int64_t ldk, int Ni, const Supports&
 cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                            const float* kself, int32_t* u, float* margin, float* fhat_out, double* ghat_out,
                            int early_stop, int n_sms, cudaStream_t st, const RescoreArgs& R = RescoreArgs());
+// The inner loop in one cooperative launch with the f_hat numerators formed on
+// the tensor cores as the product of the FP16 Gaussian block and the one-hot
+// label matrix (one CTA per 128-sample tile).  Applies when tc_iter_shape()
+// says so (C <= 16, at most one tile per SM, the one-hot tiles fit in shared
+// memory) and needs the fixed-point accumulators (I.facc, I.gfix_shift) and
+// I.lm_list.  S.lab holds the final landmark labels afterwards; the caller
+// rebuilds the rest of the support structure from it.  *I.err becomes
+// non-zero if a bounded wait gave up.
+bool tc_iter_shape(int Ni, int nL, int C, int n_sms, int* nstages, size_t* smem);
+cudaError_t launch_iterate_tc(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
+                              int32_t* u, float* margin, float* fhat_out, double* ghat_out, int early_stop,
+                              int n_sms, cudaStream_t st, const RescoreArgs& R);
 
 // ---- mini-batch boundary -----------------------------------------------------
 // Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).

@@ -35,12 +35,6 @@
 
 namespace kkm {
 
-// Programmatic dependent launch: a kernel launched with the programmatic
-// stream-serialisation attribute may start while its predecessor finishes;
-// it waits here before touching anything the predecessor wrote.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args... args) {

@@ -234,6 +234,7 @@ static kkm_status run_fit(kkm_server* s, Job& J, cudaStream_t st) {
   kkm_options opt = p.opt;
   opt.stream = st;
   opt.pipeline = side_by_side_pipeline(opt.pipeline);
+  opt.iteration = side_by_side_iteration(opt.iteration);
   kkm_model* m = nullptr;
   const kkm_status r = kkm_fit(p.X, p.N, p.d, p.C, p.B, p.s, &p.kernel, p.iters, p.seed, &opt, p.labels_out,
                                J.keep_model ? &m : nullptr);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libkkm.so")
 KKM_RBF, KKM_RMSD, KKM_LINEAR = 0, 1, 2
 KKM_FP32, KKM_BF16, KKM_FP8 = 0, 1, 2
 PIPELINE = {"auto": 0, "serial": 1, "overlap": 2}
-ITERATION = {"auto": 0, "fused": 1, "split": 2}
+ITERATION = {"auto": 0, "fused": 1, "split": 2, "tc": 3}
 KKM_STRIDE, KKM_BLOCK = 0, 1
 KKM_ASSIGN_SUPPORTS, KKM_ASSIGN_MEDOIDS = 0, 1
 KIND = {"rbf": KKM_RBF, "rmsd": KKM_RMSD, "linear": KKM_LINEAR}

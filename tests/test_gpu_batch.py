@@ -1,9 +1,10 @@
 """Batched independent fits (kkm_fit_batch) on the GPU.
 
 Each problem of a batch must give exactly what kkm_fit gives for it alone
-(same kernels on its own stream, fixed-order reductions), whatever runs
-beside it; a sample of the problems is also checked against the FP64 oracle
-at the usual tolerances.
+with the split inner loop, the form fits take side by side (same kernels on
+its own stream, fixed-order reductions), whatever runs beside it; a sample
+of the problems is also checked against the FP64 oracle at the usual
+tolerances.
 """
 
 import math
@@ -67,7 +68,7 @@ def test_batch_equals_solo_fits(lib, n_streams):
     for p, (lab, model, status) in zip(dev, res):
         assert status == 0
         solo = lib.kkm_fit(p["X"], p["C"], p["B"], p["s"], "rbf", 0.0, 0, p["iters"], p["seed"],
-                           precision=p["precision"], early_stop=p["early_stop"])
+                           precision=p["precision"], early_stop=p["early_stop"], iteration="split")
         _same_model((lab, model), solo)
 
 
@@ -106,7 +107,7 @@ def test_batch_restarts_of_one_data_set(lib):
     for p, (lab, model, status) in zip(probs, res):
         assert status == 0
         _same_model((lab, model), lib.kkm_fit(Xd, 8, 2, 0.2, "rbf", 0.0, 0, 10, p["seed"],
-                                             precision=lib.KKM_BF16))
+                                             precision=lib.KKM_BF16, iteration="split"))
 
 
 def test_batch_host_inputs_and_labels(lib):
@@ -115,7 +116,7 @@ def test_batch_host_inputs_and_labels(lib):
     for p, (lab, model, status) in zip(probs, res):
         assert status == 0 and isinstance(lab, np.ndarray)
         solo = lib.kkm_fit(_dev(p["X"]), p["C"], p["B"], p["s"], "rbf", 0.0, 0, p["iters"], p["seed"],
-                           precision=p["precision"], early_stop=p["early_stop"])
+                           precision=p["precision"], early_stop=p["early_stop"], iteration="split")
         _same_model((lab, model), solo)
 
 

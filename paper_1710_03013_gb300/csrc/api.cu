@@ -490,11 +490,6 @@ constexpr float kRescoreMarginHalf = 3e-4f;
 // up to 1e-2 from those of the unrounded rows; d = K_ii - 2 f_hat + g_hat
 // then moves by at most three times that, which this window covers.
 constexpr float kRescoreMarginFp8 = 3e-2f;
-// The reduced-precision path computes the block of short rows (d <= this) in
-// FP32 on the FFMA pipes and stores it in FP16: at these lengths the block is
-// a small share of a fit, while the BF16 rounding of the rows would widen the
-// near-tie window (and the re-scores) of every inner iteration.
-constexpr int64_t kBf16TensorMinDim = 129;
 // Share of L2 given to kernel-block rows that stay resident through the inner
 // loop (loaded evict_last; the other rows evict_first).  Measured on the
 // MNIST-shaped fit: the 180 MB FP32 block streams fastest at 0.5 (11.0 ms per
@@ -616,12 +611,22 @@ static kkm_status alloc_loop(Workspace& ws, int nLmax, int C, int64_t ldk, int t
 
 // Kernel k-means++ on prepared rows Xi (picks[0] already on the device).
 // D2 needs 2*Ni + ceil(Ni/256) doubles (D^2, block prefixes, block totals).
+// D2 holds 2 Ni + ceil(Ni / 32) doubles; *ticket is zero.  The RBF and linear
+// kernels take one launch per round; the RMSD kernel evaluates the column of
+// the last pick with its own block kernel first.
 static kkm_status kmeanspp_dev(const KernelSpec& sp, const float* Xi, const float* aux_i, int Ni, int C,
                                const float* kself, float* rowbuf, float* rowaux, float* kcol,
                                int64_t ldk, double* D2, int32_t* picks, const double* draws_d,
-                               cudaStream_t st) {
+                               uint32_t* ticket, cudaStream_t st) {
   double* P = D2 + Ni;
   double* bsum = P + Ni;
+  if (sp.kind != KKM_RMSD) {
+    for (int r = 1; r < C; ++r)
+      KKM_RUN("kpp_round", st,
+              launch_kpp_fused_round(Xi, sp.dp, Ni, sp.kind == KKM_LINEAR, sp.neg_scale(), kself, D2, P, bsum, picks,
+                                     draws_d, r, ticket, st));
+    return KKM_OK;
+  }
   for (int r = 1; r < C; ++r) {
     KKM_TRY(copy_prepared(sp, Xi, picks + (r - 1), 1, rowbuf, rowaux, st));
     KKM_TRY(kernel_block(sp, rowbuf, rowaux, nullptr, 1, Xi, aux_i, nullptr, Ni, kcol, ldk, st));
@@ -667,8 +672,10 @@ struct BlockBufs {
   RmsdTcScratch rtc;
 };
 
+// keep32: a block computed in FP32 and stored in FP16 keeps its FP32 values
+// too (b->KT), for the near-tie re-score.
 static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t Nmax, int64_t nLmax, int64_t ldk,
-                                   bool kt_half, bool use_rtc, BlockBufs* b) {
+                                   bool kt_half, bool use_rtc, BlockBufs* b, bool keep32 = false) {
   KKM_TRY(ws.alloc(&b->Xi, Nmax * sp.dp));
   KKM_TRY(ws.alloc(&b->aux_i, Nmax));
   KKM_TRY(ws.alloc(&b->gid, Nmax));
@@ -677,7 +684,7 @@ static kkm_status alloc_block_bufs(Workspace& ws, const KernelSpec& sp, int64_t 
   KKM_TRY(ws.alloc(&b->gidL, nLmax));
   if (kt_half)
     KKM_TRY(ws.alloc(&b->KTh, nLmax * ldk));
-  else
+  if (!kt_half || keep32)
     KKM_TRY(ws.alloc(&b->KT, nLmax * ldk));
   if (sp.precision == KKM_BF16) {
     KKM_TRY(ws.alloc(&b->Xib, Nmax * sp.dp));
@@ -725,7 +732,7 @@ static kkm_status block_kernel(const KernelSpec& sp, const BlockMode& bm, const 
   if (bm.fp32_half_block)
     KKM_RUN("gram_block", bs,
             launch_gram_rbf_half(b.XL, nL, b.Xi, Ni, sp.dp, b.auxL, b.aux_i, b.gidL, b.gid, sp.neg_scale(), b.KTh,
-                                 ldk, bs));
+                                 ldk, bs, b.KT));
   else if (sp.precision == KKM_BF16)
     KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
                               b.XLb, b.nXLb, b.Xib, b.nXib, tc_err, bs));
@@ -739,10 +746,15 @@ static kkm_status block_kernel(const KernelSpec& sp, const BlockMode& bm, const 
 }
 
 // Re-score inputs of the reduced-precision path: the FP32 rows of the
-// mini-batch and of its landmarks.
-static RescoreArgs rescore_args(const KernelSpec& sp, const BlockBufs& b) {
+// mini-batch and of its landmarks, and the FP32 values of a block computed in
+// FP32 and stored in FP16.
+static RescoreArgs rescore_args(const KernelSpec& sp, const BlockBufs& b, int64_t ldk) {
   RescoreArgs R;
   if (sp.precision == KKM_FP32) return R;
+  if (b.KTh && b.KT) {
+    R.K32 = b.KT;
+    R.ldk32 = ldk;
+  }
   R.kind = sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF;
   R.dp = sp.dp;
   R.Xi = b.Xi;
@@ -1081,6 +1093,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   int32_t *u, *Ld_all, *mi, *mi_safe, *cnt, *picks, *labels_dev = nullptr;
   unsigned long long* keys;
   double *ghat, *D2 = nullptr, *draws_d = nullptr;
+  uint32_t* kpp_ticket = nullptr;
   // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
   // significand, finer than the BF16 inputs' rounding): the inner loop
   // streams half the bytes.
@@ -1091,7 +1104,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // computed while the current one iterates
   BlockBufs bb[2];
   const int nbuf = overlap ? 2 : 1;
-  for (int q = 0; q < nbuf; ++q) KKM_TRY(alloc_block_bufs(ws, sp, Nmax, nLmax, ldk, kt_half, use_rtc, &bb[q]));
+  for (int q = 0; q < nbuf; ++q)
+    KKM_TRY(alloc_block_bufs(ws, sp, Nmax, nLmax, ldk, kt_half, use_rtc, &bb[q], bm.fp32_half_block));
   KKM_TRY(ws.alloc(&Kt, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&Kmi, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&MX, (int64_t)C * sp.dp));
@@ -1142,8 +1156,10 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaMemcpyAsync(I.trace_count, &tc0, 4, cudaMemcpyHostToDevice, st));
     KKM_CK(cudaStreamSynchronize(st));  // tc0 lives on this stack frame
   } else if (do_kpp) {
-    KKM_TRY(ws.alloc(&D2, 2 * geo[0].Ni + ceil_div(geo[0].Ni, 256)));
+    KKM_TRY(ws.alloc(&D2, 2 * geo[0].Ni + ceil_div(geo[0].Ni, 32)));
     KKM_TRY(ws.alloc(&draws_d, C));
+    KKM_TRY(ws.alloc(&kpp_ticket, 1));
+    KKM_CK(cudaMemsetAsync(kpp_ticket, 0, 4, st));
     KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
     KKM_CK(cudaMemcpyAsync(picks, pick0.data(), 4, cudaMemcpyHostToDevice, st));
   } else {
@@ -1209,7 +1225,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     int64_t* const gid = bk.gid;
     const float* kself = sp.kind == KKM_LINEAR ? aux_i : nullptr;
     if (i == 0 && do_kpp) {                                                   // Alg. 1 lines 4-6
-      KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, ms));
+      KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, kpp_ticket,
+                           ms));
       KKM_RUN("local_to_global", ms, launch_local_to_global(picks, C, g.start, g.step, Mg, ms));
     }
     // Eq. 8: auxiliary block K~ = K(M, X^i) and nearest-medoid labels
@@ -1228,7 +1245,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     if (I.gfix) KKM_CK(cudaMemsetAsync(I.gfix, 0, (size_t)C * 8, ms));  // the last mini-batch's medoid step read them
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
     I.flag_tau = bm.flag_tau(sp);
-    const RescoreArgs R = rescore_args(sp, bk);
+    const RescoreArgs R = rescore_args(sp, bk, ldk);
     const int form = loop_form(opt.iteration, sp, bm, Ni, nL, C);
     if (form < 0)
       return invalid(opt.iteration == KKM_ITER_TC
@@ -1629,7 +1646,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   // the fit's block buffers and block evaluation for this precision
   const BlockMode bm(sp, nL);
   BlockBufs b;
-  KKM_TRY(alloc_block_bufs(ws, sp, Ni, nL, ldk, bm.kt_half, bm.use_rtc, &b));
+  KKM_TRY(alloc_block_bufs(ws, sp, Ni, nL, ldk, bm.kt_half, bm.use_rtc, &b, bm.fp32_half_block));
   float *fh, *mg;
   int32_t *Ld, *u;
   double* gh;
@@ -1662,7 +1679,7 @@ static kkm_status debug_step_impl(const float* Xb_in, int64_t Ni, int64_t d, con
   const float* kself = sp.kind == KKM_LINEAR ? b.aux_i : nullptr;
   lb.I.keep_rows = 0;
   lb.I.flag_tau = bm.flag_tau(sp);
-  const RescoreArgs R = rescore_args(sp, b);
+  const RescoreArgs R = rescore_args(sp, b, ldk);
   const int form = loop_form(iteration, sp, bm, (int)Ni, nL, C);
   if (form < 0) return invalid("the iteration form asked for does not apply to this shape");
   KKM_TRY(inner_loop(bm, b, ldk, (int)Ni, lb.S, lb.I, form, 1, kself, u, mg, fh, gh, 0, R, st));
@@ -1716,14 +1733,17 @@ static kkm_status debug_kmeanspp_impl(const float* X0_in, int64_t N0, int64_t d,
   KKM_TRY(ws.alloc(&rowbuf, sp.dp));
   KKM_TRY(ws.alloc(&rowaux, 1));
   KKM_TRY(ws.alloc(&kcol, ldk));
-  KKM_TRY(ws.alloc(&D2, 2 * N0 + ceil_div(N0, 256)));
+  uint32_t* ticket;
+  KKM_TRY(ws.alloc(&D2, 2 * N0 + ceil_div(N0, 32)));
   KKM_TRY(ws.alloc(&draws_d, C));
   KKM_TRY(ws.alloc(&picks, C));
+  KKM_TRY(ws.alloc(&ticket, 1));
+  KKM_CK(cudaMemsetAsync(ticket, 0, 4, st));
   KKM_CK(cudaMemcpyAsync(draws_d, draws.data(), (size_t)C * 8, cudaMemcpyHostToDevice, st));
   KKM_CK(cudaMemcpyAsync(picks, &p0, 4, cudaMemcpyHostToDevice, st));
   KKM_TRY(prep_rows(sp, X, 0, 1, N0, Xi, aux, st));
   KKM_TRY(kmeanspp_dev(sp, Xi, aux, (int)N0, C, sp.kind == KKM_LINEAR ? aux : nullptr, rowbuf, rowaux, kcol,
-                       ldk, D2, picks, draws_d, st));
+                       ldk, D2, picks, draws_d, ticket, st));
   std::vector<int32_t> ph(C);
   KKM_CK(cudaMemcpyAsync(ph.data(), picks, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));

@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(256, 2)
 gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__ Bm, int nB,
                   int dp, const float* __restrict__ normA, const float* __restrict__ normB,
                   const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
-                  float neg_scale, OutT* __restrict__ out, int64_t ldo, int vec_ok, int upper_only) {
+                  float neg_scale, OutT* __restrict__ out, int64_t ldo, int vec_ok, int upper_only,
+                  float* __restrict__ out32) {
   __shared__ __align__(16) float As[2][TB_K][TB_M];
   __shared__ __align__(16) float Bs[2][TB_K][TB_N];
   const int tid = threadIdx.x;
@@ -333,6 +334,23 @@ gram_tiled_kernel(const float* __restrict__ A, int nA, const float* __restrict__
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = gram_epilogue<KIND>(acc[i][j], na, nb[j], ia == ib[j], neg_scale);
     OutT* orow = out + (int64_t)a * ldo;
+    if constexpr (sizeof(OutT) == 2) {
+      // the FP32 values too (the re-score of the FP16-stored block reads them)
+      if (out32) {
+        float* o32 = out32 + (int64_t)a * ldo;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int b = b0 + h * 64 + tx * 4;
+          if (vec_ok && b + 3 < nB) {
+            *reinterpret_cast<float4*>(o32 + b) = make_float4(v[h * 4], v[h * 4 + 1], v[h * 4 + 2], v[h * 4 + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (b + q < nB) o32[b + q] = v[h * 4 + q];
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int b = b0 + h * 64 + tx * 4;
@@ -501,7 +519,7 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
     if (attr != cudaSuccess) return attr;
   }
   gram_tiled_kernel<KIND, float><<<grid, 256, smem, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB,
-                                                          neg_scale, out, ldo, vec_ok, 0);
+                                                          neg_scale, out, ldo, vec_ok, 0, nullptr);
   return cudaGetLastError();
 }
 
@@ -527,7 +545,7 @@ cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const floa
     dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M));
     const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     gram_tiled_kernel<DK_DIST, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, idA, idA, 0.0f,
-                                                            out, ldo, vec_ok, 1);
+                                                            out, ldo, vec_ok, 1, nullptr);
     return cudaGetLastError();
   }
   // a few hundred tiles at most: K is split kDistSplit ways so that every SM
@@ -535,7 +553,7 @@ cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const floa
   dim3 grid((unsigned)ceil_div(n, TB_N), (unsigned)ceil_div(n, TB_M), kDistSplit);
   const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(scratch) & 15) == 0);
   gram_tiled_kernel<DK_RAW, float><<<grid, 256, 0, st>>>(A, (int)n, A, (int)n, dp, normA, normA, nullptr, nullptr,
-                                                         0.0f, scratch, ldo, vec_ok, 1);
+                                                         0.0f, scratch, ldo, vec_ok, 1, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dist_from_parts_kernel<<<(unsigned)ceil_div(n * n, 256), 256, 0, st>>>(scratch, kDistSplit, (int)n, ldo, normA,
@@ -546,15 +564,16 @@ cudaError_t launch_gram_dist_upper(const float* A, int64_t n, int dp, const floa
 
 cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, int64_t nB, int dp, const float* normA,
                                  const float* normB, const int64_t* idA, const int64_t* idB, float neg_scale,
-                                 __half* out, int64_t ldo, cudaStream_t st) {
+                                 __half* out, int64_t ldo, cudaStream_t st, float* out32) {
   if (nA <= 0 || nB <= 0) return cudaSuccess;
   dim3 grid((unsigned)ceil_div(nB, TB_N), (unsigned)ceil_div(nA, TB_M));
-  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+  const int vec_ok = (ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(out32) & 15) == 0);
   static const cudaError_t attr = cudaFuncSetAttribute(
       gram_tiled_kernel<DK_RBF, __half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramChunkSmem);
   if (attr != cudaSuccess) return attr;
   gram_tiled_kernel<DK_RBF, __half><<<grid, 256, kGramChunkSmem, st>>>(A, (int)nA, Bm, (int)nB, dp, normA, normB,
-                                                                       idA, idB, neg_scale, out, ldo, vec_ok, 0);
+                                                                       idA, idB, neg_scale, out, ldo, vec_ok, 0, out32);
   return cudaGetLastError();
 }
 

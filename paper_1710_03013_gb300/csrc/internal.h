@@ -168,6 +168,13 @@ inline int side_by_side_pipeline(int pipeline) { return pipeline == KKM_PIPE_AUT
 // fits that run side by side take the split form.
 inline int side_by_side_iteration(int iteration) { (void)iteration; return KKM_ITER_SPLIT; }
 
+// The reduced-precision path computes the block of short rows (d below this)
+// in FP32 on the FFMA pipes and stores it in FP16, keeping the FP32 values for
+// the near-tie re-score: at these lengths the block is a small share of a fit,
+// while the BF16 rounding of the rows would widen the near-tie window (and the
+// re-scores) of every inner iteration.
+constexpr int64_t kBf16TensorMinDim = 129;
+
 // Kernel-function codes used on the device.
 enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3, DK_RAW = 4 /* plain products */ };
 
@@ -209,10 +216,11 @@ cudaError_t launch_gram(int kind, const float* A, int64_t nA, const float* Bm, i
                         cudaStream_t st);
 
 // The FP32 RBF block (tiled FFMA kernel, ids force the exact diagonal) stored
-// in FP16: the reduced-precision path's block for short rows.
+// in FP16: the reduced-precision path's block for short rows; out32
+// (nullable, same leading dimension) gets the FP32 values too.
 cudaError_t launch_gram_rbf_half(const float* A, int64_t nA, const float* Bm, int64_t nB, int dp, const float* normA,
                                  const float* normB, const int64_t* idA, const int64_t* idB, float neg_scale,
-                                 __half* out, int64_t ldo, cudaStream_t st);
+                                 __half* out, int64_t ldo, cudaStream_t st, float* out32 = nullptr);
 
 // ---- tensor-core (tcgen05) BF16 kernel block ----------------------------
 // out[n*ldo + m] = kappa(P_n, Q_m) for BF16 rows P [nP][ldb], Q [nQ][ldb]
@@ -372,6 +380,11 @@ struct RescoreArgs {
   const float* XL = nullptr;   // [nL][dp] landmark rows (by ordinal)
   const float* nXL = nullptr;
   float neg_scale = 0.0f;
+  // the FP32 values of the block when it was computed in FP32 and stored in
+  // FP16 ([nL][ldk32], K32[k][i] = K(landmark k, sample i)): the re-score
+  // reads them instead of recomputing them from the rows
+  const float* K32 = nullptr;
+  int64_t ldk32 = 0;
 };
 
 // f_hat, distances, argmin, margin, Omega; updates u in place.  With
@@ -451,6 +464,12 @@ cudaError_t launch_fill_f32(float* p, float v, int64_t n, cudaStream_t st);
 // P [N0] and bsum [ceil(N0/256)] are scratch.
 cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2, double* P,
                              double* bsum, int32_t* picks, const double* draws, int r, cudaStream_t st);
+// One whole k-means++ round on prepared rows (RBF or linear kernel), the next
+// pick drawn by the last CTA; *ticket is zero between launches.  D2 holds
+// N0 + N0 + ceil(N0 / 32) doubles (D^2, running sums, CTA totals).
+cudaError_t launch_kpp_fused_round(const float* X, int dp, int N0, bool linear, float neg_scale, const float* kself,
+                                   double* D2, double* P, double* bsum, int32_t* picks, const double* draws, int r,
+                                   uint32_t* ticket, cudaStream_t st);
 // picks (local) -> global ids start + p*step
 cudaError_t launch_local_to_global(const int32_t* picks, int C, int64_t start, int64_t step,
                                    int64_t* M, cudaStream_t st);

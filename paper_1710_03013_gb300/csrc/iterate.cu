@@ -684,7 +684,10 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
       const float ksr = kself ? kself[ir] : 1.0f;
       const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
       float acc = 0.0f;
-      for (int kk = k0 + lane; kk < k1; kk += 32) {
+      if (R.K32) {  // the block's own FP32 values
+        for (int kk = k0 + lane; kk < k1; kk += 32) acc += __ldg(R.K32 + (int64_t)S.perm[kk] * R.ldk32 + ir);
+      }
+      for (int kk = k0 + lane; !R.K32 && kk < k1; kk += 32) {
         const int k = S.perm[kk];
         const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
         // in chunks of 32 products (see the Gram kernel: one long FP32 sum drifts)
@@ -725,13 +728,17 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
         float acc = 0.0f;
         for (int kk = k0 + w; kk < k1; kk += nw) {
           const int k = S.perm[kk];
-          const float* xl = R.XL + (int64_t)k * R.dp;
-          float dot = 0.0f;
-          for (int c = lane; c < R.dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
-          dot = warp_sum_f32(dot);
           float kv;
-          if (R.kind == DK_LINEAR) kv = dot;
-          else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+          if (R.K32) {  // the block's own FP32 values
+            kv = __ldg(R.K32 + (int64_t)k * R.ldk32 + ir);
+          } else {
+            const float* xl = R.XL + (int64_t)k * R.dp;
+            float dot = 0.0f;
+            for (int c = lane; c < R.dp; c += 32) dot = fmaf(xs[c], xl[c], dot);
+            dot = warp_sum_f32(dot);
+            if (R.kind == DK_LINEAR) kv = dot;
+            else kv = (S.L[k] == ir) ? 1.0f : exp2f(fmaxf(ni + R.nXL[k] - 2.0f * dot, 0.0f) * R.neg_scale);
+          }
           acc += kv;
         }
         if (lane == 0) wsum[w] = acc;
@@ -1822,6 +1829,212 @@ kpp_pick_kernel(const double* __restrict__ D2, const double* __restrict__ P,
       }
     }
   }
+}
+
+// One whole round of kernel k-means++ (Alg. 1 lines 4-6) in one launch, for
+// the RBF and linear kernels on prepared rows X [N0][dp] (dp a multiple of 8).
+// CTA b takes the samples [32 b, 32 b + 32), warp w four of them:
+// K(x_m, x_l) against the last pick m (the RBF kernel from direct squared
+// differences, the linear one from the dot product; lanes over 16-byte
+// chunks of the row, a fixed xor tree), D^2(l) = min over the picks of
+// K_ll - 2 K(x_l, m) + K_mm (clamped at 0, FP64) and the running sums of D^2
+// within the CTA.  The last CTA to finish (atomic ticket, no waiting) draws
+// the next pick: the CTA totals' running sums (a block scan per chunk of 256
+// CTAs, chunks in order), target = u * (their total), the first sample whose
+// interval [running sum before, running sum after) contains it; if rounding
+// put the target at the very end, the last sample with D^2 > 0; if every D^2
+// is 0, the lowest sample not picked yet.
+constexpr int kKppSamples = 32;  // samples per CTA of the one-launch round
+
+// inclusive scan of one double per thread over the CTA (kKppThreads); sh
+// holds kKppThreads / 32 slots
+__device__ __forceinline__ double kpp_block_scan(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += y;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = v;
+  __syncthreads();
+  double off = 0.0;
+  for (int q = 0; q < w; ++q) off += sh[q];
+  return off + v;
+}
+
+__global__ void __launch_bounds__(kKppThreads)
+kpp_fused_round_kernel(const float* __restrict__ X, int dp, int N0, int linear, float neg_scale,
+                       const float* __restrict__ kself, double* __restrict__ D2, double* __restrict__ P,
+                       double* __restrict__ bsum, int32_t* __restrict__ picks, const double* __restrict__ draws,
+                       int r, uint32_t* __restrict__ ticket) {
+  extern __shared__ float4 kpp_row[];  // [dp / 4]: the row of the last pick
+  __shared__ float kv[kKppSamples];
+  __shared__ double wsh[kKppThreads / 32];
+  __shared__ double base_sh, total_sh;
+  __shared__ int blk_sh, last_sh;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int m = picks[r - 1];
+  const int d4 = dp >> 2;
+  const float4* xm_g = reinterpret_cast<const float4*>(X + (int64_t)m * dp);
+  for (int c = tid; c < d4; c += kKppThreads) kpp_row[c] = __ldg(xm_g + c);
+  __syncthreads();
+  const int l0 = blockIdx.x * kKppSamples;
+  {
+    const float4* xl[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const int l = l0 + 4 * w + g;
+      xl[g] = l < N0 ? reinterpret_cast<const float4*>(X + (int64_t)l * dp) : nullptr;
+    }
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int c0 = 0; c0 < d4; c0 += 64) {
+      float4 v[4][2];
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = c0 + 32 * h + lane;
+          v[g][h] = (xl[g] && c < d4) ? __ldg(xl[g] + c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + 32 * h + lane;
+        const float4 b = c < d4 ? kpp_row[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const float4 a = v[g][h];
+          if (linear) {
+            acc[g] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[g]))));
+          } else {
+            const float tx = a.x - b.x, ty = a.y - b.y, tz = a.z - b.z, tw = a.w - b.w;
+            acc[g] = fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, fmaf(tw, tw, acc[g]))));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const float a = warp_sum_f32(acc[g]);
+      if (lane == 0) {
+        const int l = l0 + 4 * w + g;
+        kv[4 * w + g] = linear ? a : (l == m ? 1.0f : exp2f(a * neg_scale));
+      }
+    }
+  }
+  __syncthreads();
+  // D^2 update and running sums within the CTA (warp 0)
+  if (w == 0) {
+    const int l = l0 + lane;
+    const double km = kself ? (double)kself[m] : 1.0;
+    double dv = 0.0;
+    if (l < N0) {
+      const double ks = kself ? (double)kself[l] : 1.0;
+      double v = ks - 2.0 * (double)kv[lane] + km;
+      v = v > 0.0 ? v : 0.0;
+      dv = (r == 1) ? v : fmin(D2[l], v);
+      D2[l] = dv;
+    }
+    double x = dv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (l < N0) P[l] = x;
+    if (lane == 31) bsum[blockIdx.x] = x;
+  }
+  // the last CTA draws the next pick
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last_sh = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last_sh) return;
+  __threadfence();
+  const int nb = (int)gridDim.x;
+  // the CTA totals' running sums, chunk by chunk: first the total
+  double run = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
+    const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
+    const double incl = kpp_block_scan(v, wsh);
+    if (tid == kKppThreads - 1) total_sh = incl;
+    __syncthreads();
+    run += total_sh;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    blk_sh = -1;
+    picks[r] = -1;
+  }
+  __syncthreads();
+  const double total = run;
+  if (total > 0.0) {
+    const double target = draws[r] * total;
+    double before = 0.0;  // running sum of the earlier chunks
+    for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
+      const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
+      const double incl = before + kpp_block_scan(v, wsh);
+      const double excl = incl - v;
+      if (b0 + tid < nb && excl <= target && incl > target) {
+        blk_sh = b0 + tid;
+        base_sh = excl;
+      }
+      if (tid == kKppThreads - 1) total_sh = incl;
+      __syncthreads();
+      before = total_sh;
+      const bool found = blk_sh >= 0;
+      __syncthreads();
+      if (found) break;
+    }
+    const int blk = blk_sh;
+    if (blk >= 0 && tid < kKppSamples) {
+      // interval [base + P[l-1], base + P[l]) of sample l; neighbours share endpoints exactly
+      const double base = base_sh;
+      const int l = blk * kKppSamples + tid;
+      if (l < N0) {
+        const double hi = base + __ldcg(P + l);
+        const double lo = base + (tid > 0 ? __ldcg(P + l - 1) : 0.0);
+        if (lo <= target && hi > target) picks[r] = l;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (picks[r] < 0) {
+      if (total > 0.0) {  // rounding put the target at the very end
+        int l = N0 - 1;
+        while (l > 0 && !(__ldcg(D2 + l) > 0.0)) --l;
+        picks[r] = l;
+      } else {
+        for (int l = 0; l < N0; ++l) {
+          bool taken = false;
+          for (int q = 0; q < r; ++q) taken |= (picks[q] == l);
+          if (!taken) {
+            picks[r] = l;
+            break;
+          }
+        }
+      }
+    }
+    *ticket = 0u;
+  }
+}
+
+cudaError_t launch_kpp_fused_round(const float* X, int dp, int N0, bool linear, float neg_scale, const float* kself,
+                                   double* D2, double* P, double* bsum, int32_t* picks, const double* draws, int r,
+                                   uint32_t* ticket, cudaStream_t st) {
+  if ((dp & 7) != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
+  const int nb = (int)ceil_div(N0, kKppSamples);
+  const size_t smem = (size_t)dp * sizeof(float);
+  if (smem > 48 * 1024) {
+    static const cudaError_t e = cudaFuncSetAttribute(kpp_fused_round_kernel,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  }
+  kpp_fused_round_kernel<<<nb, kKppThreads, smem, st>>>(X, dp, N0, linear ? 1 : 0, neg_scale, kself, D2, P, bsum,
+                                                        picks, draws, r, ticket);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_kpp_round(const float* Kc, int N0, const float* kself, double* D2, double* P,

@@ -463,6 +463,10 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
           float accr = 0.0f;
           for (int k = lane; k < nL; k += 32) {
             if (*reinterpret_cast<const unsigned short*>(Z + z_offset(k, j)) == 0) continue;
+            if (R.K32) {  // the block's own FP32 values
+              accr += __ldg(R.K32 + (int64_t)k * R.ldk32 + iL);
+              continue;
+            }
             const float4* xl = reinterpret_cast<const float4*>(R.XL + (int64_t)k * R.dp);
             float dot = 0.0f, part = 0.0f;
             for (int c = 0; c < (R.dp >> 2); ++c) {

@@ -67,6 +67,8 @@ static uint64_t fit_bytes(const kkm_problem& p) {
   uint64_t blk = 4ull * Nmax * dp + 12ull * Nmax;  // X^i, norms, ids
   blk += 4ull * nL * dp + 12ull * nL;               // landmark rows
   blk += 4ull * nL * ldk;                           // the kernel block
+  if (p.opt.precision != KKM_FP32 && p.kernel.kind == KKM_RBF && d < kBf16TensorMinDim)
+    blk += 2ull * nL * ldk;  // short rows: the FP16 block beside its FP32 values
   if (p.opt.precision == KKM_BF16) blk += 2ull * (Nmax + nL) * dp + 4ull * (Nmax + nL);
   if (p.opt.precision == KKM_FP8) blk += (uint64_t)(Nmax + nL) * round_up(dp, 16) + 8ull * (Nmax + nL);
   if (p.kernel.kind == KKM_RMSD)  // tensor-core MD path: split-BF16 planes, rotations, refine plan

@@ -69,9 +69,11 @@ typedef enum kkm_sampling { KKM_STRIDE = 0, KKM_BLOCK = 1 } kkm_sampling;
  * computes K(X^(i+1), L^(i+1)) on a low-priority stream while mini-batch i
  * runs its inner loop on a high-priority one (two block buffers);
  * KKM_PIPE_SERIAL computes each block just before its inner loop (one
- * buffer).  KKM_PIPE_AUTO overlaps when B >= 2 except for the KKM_BF16
- * RBF/linear block (a few percent of such a fit, whose writes would evict
- * the cached block the inner loop streams); in kkm_fit_batch and the server,
+ * buffer).  KKM_PIPE_AUTO overlaps when B >= 2 except for a reduced-precision
+ * RBF/linear block streamed by the split loop (a few percent of such a fit,
+ * whose writes would evict the cached block the loop streams); with the
+ * tensor-core loop (KKM_ITER_TC) the next block runs on the SMs the loop
+ * leaves free.  In kkm_fit_batch and the server,
  * whose fits already run side by side, AUTO means serial.  The results are
  * the same bits either way: the same kernels run on the same inputs.       */
 typedef enum kkm_pipeline { KKM_PIPE_AUTO = 0, KKM_PIPE_SERIAL = 1, KKM_PIPE_OVERLAP = 2 } kkm_pipeline;

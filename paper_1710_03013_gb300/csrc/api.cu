@@ -805,16 +805,27 @@ static int loop_form(int iteration, const KernelSpec& sp, const BlockMode& bm, i
 // block of the buffer set b: `iters` iterations fused in one launch, or per
 // iteration the streaming partial sums and the assign.  Either way every
 // iteration closes on the device (trace, early stop, support re-sort).
+// With the tensor-core form and `med` (keys preset to ~0, counts to 0), the
+// loop also leaves the Eq. 10 keys, member counts, g_hat and n_j of the final
+// supports, and the rest of the support structure is rebuilt only when
+// `need_supports`.
+struct MedoidOut {
+  unsigned long long* keys = nullptr;
+  int32_t* cnt = nullptr;
+  double* ghat = nullptr;
+  bool need_supports = true;
+};
+
 static kkm_status inner_loop(const BlockMode& bm, const BlockBufs& b, int64_t ldk, int Ni, const Supports& S,
                              const IterState& I, int form, int iters, const float* kself, int32_t* u,
                              float* margin, float* fhat_out, double* ghat_out, int early_stop, const RescoreArgs& R,
-                             cudaStream_t st) {
+                             cudaStream_t st, const MedoidOut& med = MedoidOut()) {
   if (form == kLoopTc) {
     KKM_RUN("iterate", st,
             launch_iterate_tc(b.KTh, ldk, Ni, S, I, iters, u, margin, fhat_out, ghat_out, early_stop, sm_count(), st,
-                              R));
+                              R, med.keys, med.cnt, med.ghat));
     // the landmark labels are final: the rest of the support structure
-    KKM_RUN("build_supports", st, launch_build_supports(S, st));
+    if (med.need_supports || !med.keys) KKM_RUN("build_supports", st, launch_build_supports(S, st));
     return KKM_OK;
   }
   if (form == kLoopFused) {
@@ -1266,17 +1277,29 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
                          : "KKM_ITER_FUSED does not apply to this shape (C <= 64 and a mini-batch of at most one "
                            "column per thread of one CTA per SM)");
     NvtxRange nv_loop("inner loop");
+    MedoidOut med;
+    if (form == kLoopTc) {  // the loop leaves the Eq. 10 keys itself
+      KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
+      KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
+      med.keys = keys;
+      med.cnt = cnt;
+      med.ghat = ghat;
+      med.need_supports = i == B - 1 && model_out;  // the model keeps the final support structure
+    }
     KKM_TRY(inner_loop(bm, bk, ldk, Ni, S, I, form, iters, kself, u, nullptr, nullptr, nullptr,  // Alg. 1 lines 9-16
-                       opt.early_stop, R, ms));
+                       opt.early_stop, R, ms, med));
     I.flag_tau = 0.0f;
-    // Eq. 10: f_hat of the final labels and the mini-batch medoids
-    IterState Ifin = I;
-    Ifin.done = nullptr;
-    KKM_RUN("fhat_partial", ms,
-            kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, Ifin, ms) : launch_fhat_partial(bk.KT, ldk, Ni, S, Ifin, ms));
-    KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
-    KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
-    KKM_RUN("medoid_keys", ms, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, ms));
+    if (form != kLoopTc) {
+      // Eq. 10: f_hat of the final labels and the mini-batch medoids
+      IterState Ifin = I;
+      Ifin.done = nullptr;
+      KKM_RUN("fhat_partial", ms,
+              kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, Ifin, ms)
+                      : launch_fhat_partial(bk.KT, ldk, Ni, S, Ifin, ms));
+      KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
+      KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
+      KKM_RUN("medoid_keys", ms, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, ms));
+    }
     KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms));
     // Eq. 12: K(X^i, m^i) and the convex merge
     KKM_RUN("clamp_idx", ms, (clamp_idx_kernel<<<blocks_for(C), 256, 0, ms>>>(mi, C, mi_safe), cudaGetLastError()));

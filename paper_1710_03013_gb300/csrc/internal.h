@@ -424,12 +424,16 @@ cudaError_t launch_iterate(const __half* KT, int64_t ldk, int Ni, const Supports
 // says so (C <= 16, at most one tile per SM, the one-hot tiles fit in shared
 // memory) and needs the fixed-point accumulators (I.facc, I.gfix_shift) and
 // I.lm_list.  S.lab holds the final landmark labels afterwards; the caller
-// rebuilds the rest of the support structure from it.  *I.err becomes
-// non-zero if a bounded wait gave up.
+// rebuilds the rest of the support structure from it.  With keys != NULL the
+// loop also leaves the Eq. 10 inputs of the final supports: keys[j] = the
+// smallest pack_key(K_ii - 2 f_hat_ij, i) over the samples (keys preset to
+// ~0), kcount[j] += the members of cluster j (preset to 0), ghat_final[j] and
+// S.n_j.  *I.err becomes non-zero if a bounded wait gave up.
 bool tc_iter_shape(int Ni, int nL, int C, int n_sms, int* nstages, size_t* smem);
 cudaError_t launch_iterate_tc(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                               int32_t* u, float* margin, float* fhat_out, double* ghat_out, int early_stop,
-                              int n_sms, cudaStream_t st, const RescoreArgs& R);
+                              int n_sms, cudaStream_t st, const RescoreArgs& R, unsigned long long* keys = nullptr,
+                              int32_t* kcount = nullptr, double* ghat_final = nullptr);
 
 // ---- mini-batch boundary -----------------------------------------------------
 // Eq. 8: u[l] = argmin_j kself[l] - 2 Kt[j][l] + kmm[j]; dmin (nullable).

@@ -56,7 +56,7 @@ constexpr int kTcEpiWarps = 4;       // one thread per sample of the tile
 constexpr int kTcThreads = 32 * (2 * kTcRings + kTcEpiWarps);
 constexpr int kTcTmemCols = 64;      // two sets (iteration parity) of kTcRings accumulators of kTcN columns
 constexpr unsigned kTcBarSpin = 1u << 25;  // polls per grid barrier (>= ~1 s)
-constexpr size_t kTcMaxDynSmem = 227 * 1024 - 1024;  // leaves room for the static shared memory
+constexpr size_t kTcMaxDynSmem = 227 * 1024 - 1280;  // leaves room for the static shared memory
 
 // kind::f16 instruction descriptor: FP32 accumulator, F16 A (MN-major) and
 // F16 B (K-major), N = 16, M = 128.
@@ -69,6 +69,9 @@ __host__ __device__ constexpr uint32_t tc_iter_idesc() {
 // same Z stands), they changed (Z was patched: the pass is made again), or the
 // loop ended.
 constexpr int kVerdictSame = 0, kVerdictChanged = 1, kVerdictStop = 2;
+// the loop ended and the last iteration moved landmark labels: one more pass
+// with the patched Z gives f_hat and g_hat of the final supports (Eq. 10)
+constexpr int kVerdictFinal = 3;
 
 struct TcIterShared {
   uint64_t full[kTcRings][kTcMaxStages];
@@ -89,12 +92,14 @@ struct TcIterShared {
   unsigned long long gsum[kTcN];
   unsigned long long osum_w[kTcEpiWarps];
   int chsum_w[kTcEpiWarps];
+  unsigned long long kbest[kTcN];  // Eq. 10 keys of this tile
+  int kcnt[kTcN];
   double tot_om;
   int tot_ch, tot_lm;
   int ok;
 };
 
-static_assert(sizeof(TcIterShared) <= 1024, "static shared memory beside the dynamic share");
+static_assert(sizeof(TcIterShared) <= 1280, "static shared memory beside the dynamic share");
 
 // Barrier of the epilogue warps only (named barrier 1), after the warp has
 // reconverged.
@@ -138,7 +143,8 @@ __device__ __forceinline__ uint32_t z_offset(int k, int n) {
 __global__ void __launch_bounds__(kTcThreads, 1)
 iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, IterState I, int iters, int nstages,
                   int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ fhat_out,
-                  double* __restrict__ ghat_out, int early_stop, RescoreArgs R) {
+                  double* __restrict__ ghat_out, int early_stop, RescoreArgs R, unsigned long long* __restrict__ keys,
+                  int32_t* __restrict__ kcount, double* __restrict__ ghat_final) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* const base =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -175,6 +181,8 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
   if (threadIdx.x < kTcN) {
     sh.nj[threadIdx.x] = 0;
     sh.gsum[threadIdx.x] = 0ull;
+    sh.kbest[threadIdx.x] = ~0ull;
+    sh.kcnt[threadIdx.x] = 0;
   }
   if (threadIdx.x < kTcRings) sh.consumed[threadIdx.x] = 0;
   if (warp == kTcRings) {  // the first MMA warp owns the tensor memory
@@ -280,19 +288,45 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
         ok = run_pass(0);
         if (ok) umma_commit(&sh.acc_done[0]);
       }
+      bool ended = false;  // a verdict ended the loop (or a wait gave up)
       for (int t = 0; ok && t + 1 < iters; ++t) {
         const int p = (t + 1) & 1;
-        if (!run_pass(p)) break;  // iteration t + 1 with the Z of iteration t
+        if (!run_pass(p)) {  // iteration t + 1 with the Z of iteration t
+          ended = true;
+          break;
+        }
         if (!mbar_wait(&sh.vready, (uint32_t)t & 1u, abort_flag)) {
           if (!*abort_flag) atomicExch(I.err, 3);
           *abort_flag = 1;
+          ended = true;
           break;
         }
         tc_fence_after();  // the epilogue's reads of the other accumulator set are ordered before what follows
         const int v = *reinterpret_cast<volatile int*>(&sh.verdict);
-        if (v == kVerdictStop || *abort_flag) break;
-        if (v == kVerdictChanged && !run_pass(p)) break;  // Z was patched: the pass again
+        if (v == kVerdictStop || *abort_flag) {
+          ended = true;
+          break;
+        }
+        if ((v == kVerdictChanged || v == kVerdictFinal) && !run_pass(p)) {  // Z was patched: the pass again
+          ended = true;
+          break;
+        }
         umma_commit(&sh.acc_done[p]);
+        if (v == kVerdictFinal) {
+          ended = true;
+          break;
+        }
+      }
+      if (ok && !ended) {
+        // the last iteration's verdict may ask for the final pass
+        if (mbar_wait(&sh.vready, (uint32_t)(iters - 1) & 1u, abort_flag)) {
+          tc_fence_after();
+          const int v = *reinterpret_cast<volatile int*>(&sh.verdict);
+          if (v == kVerdictFinal && !*abort_flag && run_pass(iters & 1)) umma_commit(&sh.acc_done[iters & 1]);
+        } else {
+          if (!*abort_flag) atomicExch(I.err, 3);
+          *abort_flag = 1;
+        }
       }
       sh.consumed[r] = consumed;
       if (consumed > 0) umma_commit(&sh.mma_idle[r]);
@@ -559,7 +593,8 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
       }
       const bool stop = (early_stop && sh.tot_ch == 0) || t + 1 == iters;
       const int lm = sh.tot_lm;
-      if (!stop && lm > 0) {
+      const bool final_pass = stop && lm > 0 && keys != nullptr;
+      if ((!stop || final_pass) && lm > 0) {
         for (int c = et; c < lm; c += kTcEpiWarps * 32) {
           const int v = __ldcg(I.lm_list + (size_t)(t & 1) * nL + c);
           const int k = v >> 8, from = (v >> 4) & 15, to = v & 15;
@@ -572,12 +607,92 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
       }
       epi_sync();
       if (et == 0) {
-        if (stop) *stop_flag = 1;
-        sh.verdict = stop ? kVerdictStop : (lm > 0 ? kVerdictChanged : kVerdictSame);
+        if (stop && !final_pass) *stop_flag = 1;
+        sh.verdict = final_pass ? kVerdictFinal
+                                : (stop ? kVerdictStop : (lm > 0 ? kVerdictChanged : kVerdictSame));
         mbar_arrive(&sh.vready);
       }
       if (stop) {
         ++t;
+        if (keys) {
+          // Eq. 10 on the final supports: the keys (K_ii - 2 f_hat_ij, sample)
+          // of every cluster, the member counts and g_hat
+          if (final_pass) {
+            // the pass with the patched Z: f_hat and g_hat of the final labels
+            bool okf = true;
+            if (lane == 0) okf = mbar_wait(&sh.acc_done[t & 1], (uint32_t)(t >> 1) & 1u, abort_flag);
+            okf = __shfl_sync(kFull, okf ? 1 : 0, 0) != 0;
+            if (!okf) {
+              if (lane == 0) {
+                if (!*abort_flag) atomicExch(I.err, 5);
+                *abort_flag = 1;
+              }
+              failed = true;
+              break;
+            }
+            tc_fence_after();
+            float Df[kTcN];
+#pragma unroll
+            for (int j = 0; j < kTcN; ++j) Df[j] = 0.0f;
+            for (int r = 0; r < active; ++r) {
+              uint32_t v[16];
+              tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(((t & 1) * kTcRings + r) * kTcN), v);
+#pragma unroll
+              for (int j = 0; j < kTcN; ++j) Df[j] += __uint_as_float(v[j]);
+            }
+            tc_fence_before();
+            epi_sync();
+            if (et == 0) *stop_flag = 1;  // the producers may wind down
+            if (valid && cord >= 0) {
+              float dl = 0.0f;
+#pragma unroll
+              for (int j = 0; j < kTcN; ++j)
+                if (j == cur) dl = Df[j];
+              atomicAdd(&sh.gsum[cur], (unsigned long long)llrint((double)dl * gscale));
+            }
+            epi_sync();
+            if (et < C) {
+              const unsigned long long g = sh.gsum[et];
+              if (g) atomicAdd(facc + (t & 1) * (C + 3) + et, g);
+              sh.gsum[et] = 0ull;
+            }
+            epi_sync();
+            if (et == 0) tc_grid_arrive(I.bar);
+            target += gridDim.x;
+#pragma unroll
+            for (int j = 0; j < kTcN; ++j) {
+              const int n = j < C ? sh.nj[j] : 0;
+              e[j] = n > 0 ? ks - 2.0f * (Df[j] / (float)n) : inf;
+            }
+            if (et == 0) sh.ok = tc_grid_wait(I.bar, target, I.err) ? 1 : 0;
+            epi_sync();
+            if (!sh.ok) {
+              failed = true;
+              break;
+            }
+            if (et < C) {
+              const int n = sh.nj[et];
+              sh.gh[et] = n > 0 ? (double)__ldcg(facc + (t & 1) * (C + 3) + et) / gscale / ((double)n * (double)n)
+                                : __longlong_as_double(0x7ff8000000000000LL);
+            }
+            epi_sync();
+          }
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < kTcN; ++j)
+              if (j < C && sh.nj[j] > 0) atomicMin(&sh.kbest[j], pack_key(e[j], (uint32_t)i));
+            atomicAdd(&sh.kcnt[cur], 1);
+          }
+          epi_sync();
+          if (et < C) {
+            if (sh.kbest[et] != ~0ull) atomicMin(keys + et, sh.kbest[et]);
+            if (sh.kcnt[et]) atomicAdd(kcount + et, sh.kcnt[et]);
+            if (blockIdx.x == 0) {
+              if (ghat_final) ghat_final[et] = sh.gh[et];
+              S.n_j[et] = sh.nj[et];
+            }
+          }
+        }
         break;
       }
     }
@@ -635,7 +750,8 @@ bool tc_iter_shape(int Ni, int nL, int C, int n_sms, int* nstages, size_t* smem)
 
 cudaError_t launch_iterate_tc(const __half* KT, int64_t ldk, int Ni, const Supports& S, const IterState& I, int iters,
                               int32_t* u, float* margin, float* fhat_out, double* ghat_out, int early_stop,
-                              int n_sms, cudaStream_t st, const RescoreArgs& R) {
+                              int n_sms, cudaStream_t st, const RescoreArgs& R, unsigned long long* keys,
+                              int32_t* kcount, double* ghat_final) {
   if (iters <= 0) return cudaSuccess;
   int nstages = 0;
   size_t smem = 0;
@@ -677,7 +793,7 @@ cudaError_t launch_iterate_tc(const __half* KT, int64_t ldk, int Ni, const Suppo
   cfg.attrs = attrs;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, iterate_tc_kernel, map, Ni, S, J, iters, nstages, u, margin, fhat_out, ghat_out,
-                            early_stop, R);
+                            early_stop, R, keys, kcount, ghat_final);
 }
 
 }  // namespace kkm

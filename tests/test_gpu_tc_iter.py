@@ -169,3 +169,29 @@ def test_tc_refuses_shapes_it_does_not_cover(lib):
     big, _ = blobs(152 * 128 + 1, 4, 3, workload=132)
     with pytest.raises(lib.KKMError):   # more 128-sample tiles than SMs in one mini-batch
         lib.kkm_fit(_dev(big), 3, 1, 0.01, "rbf", 1.0, iters=2, precision=lib.KKM_BF16, iteration="tc")
+
+
+@pytest.mark.parametrize("iters,B", [(1, 1), (2, 1), (1, 2), (2, 3)])
+def test_tc_medoids_of_the_final_supports(lib, iters, B):
+    """The tensor-core loop forms the Eq. 10 keys itself: from the f_hat of its
+    last iteration when no landmark label moved there, else after one more
+    pass with the patched supports (after one or two iterations from the
+    k-means++ medoids, labels are still moving).  On separated blobs (no near
+    ties) the medoids, counts, g_hat and n_j equal those of the split form,
+    which streams the block once more for Eq. 10."""
+    X, _ = blobs(4000, 16, 6, workload=133)
+    Xd = _dev(X)
+    runs = {it: lib.kkm_fit(Xd, 6, B, 0.3, "rbf", 0.0, iters=iters, seed=11, early_stop=False,
+                            precision=lib.KKM_BF16, iteration=it) for it in ("tc", "split")}
+    (lt, mt), (ls, ms) = runs["tc"], runs["split"]
+    _, ch = ms.trace()
+    assert np.any(ch[iters - 1::iters] > 0)  # labels still move in a last iteration
+    assert np.array_equal(lt.cpu().numpy(), ls.cpu().numpy())
+    it_, ct, _ = mt.medoids()
+    is_, cs, _ = ms.medoids()
+    assert np.array_equal(it_, is_) and np.array_equal(ct, cs)
+    _, gt, nt = mt.supports()
+    _, gs, ns = ms.supports()
+    assert np.array_equal(nt, ns)
+    live = ns > 0
+    assert np.allclose(gt[live], gs[live], rtol=1e-6, atol=0.0)

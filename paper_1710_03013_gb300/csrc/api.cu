@@ -215,7 +215,47 @@ static kkm_status device_input(Workspace& ws, const T* p, int64_t n, const T** o
 // or Inf (checked before any other work).  Device memory is checked in
 // place; pinned host memory is copied and checked by one kernel that reads
 // it directly; other host memory is copied, then checked.
-static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n, const float** out, bool* bad) {
+// Pinned host words for the finite-input flag of a call whose host work goes
+// on while the check runs (a pool shared by all threads; never freed).
+static std::mutex g_flag_mu;
+static std::vector<int*> g_flag_free;
+static int* pinned_flag_acquire() {
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  if (g_flag_free.empty()) {
+    int* blk = nullptr;
+    if (cudaHostAlloc(&blk, 64 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int q = 0; q < 64; ++q) g_flag_free.push_back(blk + q);
+  }
+  int* f = g_flag_free.back();
+  g_flag_free.pop_back();
+  return f;
+}
+static void pinned_flag_release(int* f) {
+  if (!f) return;
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  g_flag_free.push_back(f);
+}
+// The answer of a finite-input check enqueued without waiting for it.
+struct PendingCheck {
+  int* flag = nullptr;  // pinned
+  cudaStream_t st = nullptr;
+  ~PendingCheck() { pinned_flag_release(flag); }
+  kkm_status wait(bool* bad) {
+    *bad = false;
+    if (!flag) return KKM_OK;
+    KKM_CK(cudaStreamSynchronize(st));
+    *bad = *flag != 0;
+    return KKM_OK;
+  }
+};
+
+// With `pending`, the check is only enqueued (its flag lands in pinned host
+// memory) and pending->wait gives the answer; else this call waits for it.
+static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n, const float** out, bool* bad,
+                                       PendingCheck* pending = nullptr) {
   cudaStream_t st = ws.st;
   *bad = false;
   *out = p;
@@ -240,6 +280,15 @@ static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n,
       KKM_RUN("check_finite", st, launch_check_finite(d, n, flag, st));
     }
   }
+  if (pending) {
+    int* hf = pinned_flag_acquire();
+    if (hf) {
+      pending->flag = hf;
+      pending->st = st;
+      KKM_CK(cudaMemcpyAsync(hf, flag, 4, cudaMemcpyDeviceToHost, st));
+      return KKM_OK;
+    }
+  }
   int h = 0;
   KKM_CK(cudaMemcpyAsync(&h, flag, 4, cudaMemcpyDeviceToHost, st));
   KKM_CK(cudaStreamSynchronize(st));
@@ -250,6 +299,10 @@ static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n,
 // ======================================================================
 // Small kernels of the host orchestration
 // ======================================================================
+__global__ void iota32_kernel(int32_t* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = i;
+}
 __global__ void iota64_kernel(int64_t* out, int64_t start, int64_t step, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = start + i * step;
@@ -1051,11 +1104,14 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   setup_pool_once(dev);
   Workspace ws(st);
 
-  // ---- inputs on the device, validated
+  // ---- inputs on the device; the finite check runs while the host draws
+  // the random numbers and sets up the workspace, and nothing else runs on
+  // the device before its answer
   const float* X = nullptr;
+  PendingCheck chk;
   {
     bool bad = false;
-    KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad));
+    KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad, &chk));
     if (bad) return invalid("X holds NaN or Inf");
   }
 
@@ -1086,15 +1142,6 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     pick0[0] = (int32_t)floor(draws[0] * (double)geo[0].Ni);
   }
 
-  // ---- bandwidth (a resumed fit keeps the one it started with)
-  const float sigma_arg = sp.sigma;
-  if (from) {
-    sp.sigma = from->sigma;
-  } else if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
-    float sig = 1.0f;
-    KKM_TRY(median_bandwidth_dev(sp, X, N, bw_seed, ws, &sig));
-    sp.sigma = sig;
-  }
 
   // ---- workspace
   const int64_t ldk = round_up(Nmax, 32);
@@ -1203,6 +1250,21 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     }
   }
   const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+  {
+    bool bad = false;
+    KKM_TRY(chk.wait(&bad));
+    if (bad) return invalid("X holds NaN or Inf");
+  }
+
+  // ---- bandwidth (a resumed fit keeps the one it started with)
+  const float sigma_arg = sp.sigma;
+  if (from) {
+    sp.sigma = from->sigma;
+  } else if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
+    float sig = 1.0f;
+    KKM_TRY(median_bandwidth_dev(sp, X, N, bw_seed, ws, &sig));
+    sp.sigma = sig;
+  }
 
   // Alg. 1 line 3 for mini-batch i on stream `bs`: its rows, landmark rows,
   // ids and kernel block into the buffer set b.
@@ -1350,12 +1412,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(cp(m->n_units, S.n_units, 4));
       KKM_TRY(cp(m->ghat, ghat, (size_t)C * 8));
       KKM_RUN("gather_labels", ms, (gather_i32_kernel<<<blocks_for(nL), 256, 0, ms>>>(u, Ld, nL, m->sup_labels), cudaGetLastError()));
-      {
-        std::vector<int32_t> ident(nL);
-        for (int q = 0; q < nL; ++q) ident[q] = q;
-        KKM_CK(cudaMemcpyAsync(m->L_ident, ident.data(), (size_t)nL * 4, cudaMemcpyHostToDevice, ms));
-        KKM_CK(cudaStreamSynchronize(ms));
-      }
+      KKM_RUN("iota", ms, (iota32_kernel<<<blocks_for(nL), 256, 0, ms>>>(m->L_ident, nL), cudaGetLastError()));
       *model_out = guard.release();
     }
   }

@@ -134,16 +134,57 @@ void prof_add_work(const char* name, double units) {
     KKM_CK(call);                               \
   } while (0)
 
-// First k entries of a partial Fisher-Yates shuffle of [0, n).
+// First k entries of a partial Fisher-Yates shuffle of [0, n): step a swaps
+// positions a and a + floor(u (n - a)).  When k is small against n only the
+// positions the swaps touched are held (open addressing, identity elsewhere),
+// so drawing a few thousand of N samples costs O(k), not O(N).
 static std::vector<int64_t> partial_shuffle(int64_t n, int64_t k, SplitMix64& rng) {
-  std::vector<int64_t> idx((size_t)n);
-  for (int64_t a = 0; a < n; ++a) idx[(size_t)a] = a;
+  if (k * 8 >= n) {
+    std::vector<int64_t> idx((size_t)n);
+    for (int64_t a = 0; a < n; ++a) idx[(size_t)a] = a;
+    for (int64_t a = 0; a < k; ++a) {
+      const int64_t r = a + (int64_t)floor(rng.u01() * (double)(n - a));
+      std::swap(idx[(size_t)a], idx[(size_t)r]);
+    }
+    idx.resize((size_t)k);
+    return idx;
+  }
+  size_t cap = 16;
+  int bits = 4;
+  while (cap < (size_t)(4 * k)) cap <<= 1, ++bits;
+  std::vector<int64_t> key(cap, -1), val(cap, 0);
+  auto at = [&](int64_t pos) -> int64_t& {
+    size_t h = (size_t)(((uint64_t)pos * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+    while (key[h] != pos) {
+      if (key[h] < 0) {
+        key[h] = pos;
+        val[h] = pos;
+        break;
+      }
+      h = (h + 1) & (cap - 1);
+    }
+    return val[h];
+  };
   for (int64_t a = 0; a < k; ++a) {
     const int64_t r = a + (int64_t)floor(rng.u01() * (double)(n - a));
-    std::swap(idx[(size_t)a], idx[(size_t)r]);
+    int64_t& va = at(a);
+    int64_t& vr = at(r);
+    std::swap(va, vr);
   }
-  idx.resize((size_t)k);
-  return idx;
+  std::vector<int64_t> out((size_t)k);
+  for (int64_t a = 0; a < k; ++a) out[(size_t)a] = at(a);
+  return out;
+}
+
+// The same k picks in increasing order, by a bitmap over [0, n) (a sort of
+// thousands of random indices costs far more on the host).
+static void sorted_picks(int64_t n, int64_t k, SplitMix64& rng, int32_t* out) {
+  const std::vector<int64_t> p = partial_shuffle(n, k, rng);
+  std::vector<uint64_t> bm((size_t)((n + 63) / 64), 0);
+  for (int64_t v : p) bm[(size_t)(v >> 6)] |= 1ull << (v & 63);
+  int64_t c = 0;
+  for (size_t w = 0; w < bm.size(); ++w)
+    for (uint64_t b = bm[w]; b; b &= b - 1) out[c++] = (int32_t)((int64_t)w * 64 + __builtin_ctzll(b));
 }
 
 // Eq. 18 solved for |L|.
@@ -169,9 +210,16 @@ static void setup_pool_once(int dev) {
   done.push_back(dev);
 }
 
+// Stream-ordered scratch of one call, freed in stream order when the call
+// returns.  Buffers of up to 64 KB are carved (256-byte aligned) from 1 MB
+// slabs: a fit asks for some forty small arrays, and one pool allocation
+// each costs more host time than the kernels that use them.
 struct Workspace {
+  static constexpr size_t kSlab = 1u << 20, kSmall = 64u << 10, kAlign = 256;
   cudaStream_t st;
   std::vector<void*> ptrs;
+  char* slab = nullptr;
+  size_t slab_used = kSlab;
   explicit Workspace(cudaStream_t s) : st(s) {}
   ~Workspace() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
@@ -180,8 +228,21 @@ struct Workspace {
   kkm_status alloc(T** p, int64_t n) {
     void* q = nullptr;
     const size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
-    KKM_CK(cudaMallocAsync(&q, bytes, st));
-    ptrs.push_back(q);
+    if (bytes <= kSmall) {
+      const size_t rounded = (bytes + kAlign - 1) / kAlign * kAlign;
+      if (slab_used + rounded > kSlab) {
+        void* fresh = nullptr;
+        KKM_CK(cudaMallocAsync(&fresh, kSlab, st));
+        ptrs.push_back(fresh);
+        slab = static_cast<char*>(fresh);
+        slab_used = 0;
+      }
+      q = slab + slab_used;
+      slab_used += rounded;
+    } else {
+      KKM_CK(cudaMallocAsync(&q, bytes, st));
+      ptrs.push_back(q);
+    }
     *p = reinterpret_cast<T*>(q);
     return KKM_OK;
   }
@@ -1128,9 +1189,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     if (nl == Ni) {
       for (int64_t a = 0; a < Ni; ++a) L_all.push_back((int32_t)a);
     } else {
-      std::vector<int64_t> p = partial_shuffle(Ni, nl, lm[i]);
-      std::sort(p.begin(), p.end());
-      for (int64_t v : p) L_all.push_back((int32_t)v);
+      const size_t at = L_all.size();
+      L_all.resize(at + (size_t)nl);
+      sorted_picks(Ni, nl, lm[i], L_all.data() + at);
     }
     L_off[i + 1] = (int64_t)L_all.size();
   }
@@ -2057,9 +2118,7 @@ kkm_status kkm_minibatch_plan(int64_t N, int32_t B, int32_t sampling, double s, 
       if (nl == g.Ni) {
         for (int64_t a = 0; a < nl; ++a) L_out[a] = (int32_t)a;
       } else {
-        std::vector<int64_t> p = partial_shuffle(g.Ni, nl, lm);
-        std::sort(p.begin(), p.end());
-        for (int64_t a = 0; a < nl; ++a) L_out[a] = (int32_t)p[(size_t)a];
+        sorted_picks(g.Ni, nl, lm, L_out);
       }
     }
     return KKM_OK;

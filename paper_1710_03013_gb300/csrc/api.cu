@@ -299,6 +299,79 @@ static void pinned_flag_release(int* f) {
   std::lock_guard<std::mutex> lk(g_flag_mu);
   g_flag_free.push_back(f);
 }
+// Pinned host buffers for the read-backs at the end of a call: the copies
+// into them are asynchronous, so one synchronisation covers them all (a copy
+// into pageable memory returns only once it is done).  A pool shared by all
+// threads, never freed; a buffer grows when a call needs more.
+struct PinnedStage {
+  char* p = nullptr;
+  size_t cap = 0;
+};
+static std::vector<PinnedStage> g_stage_free;
+static PinnedStage pinned_stage_acquire(size_t bytes) {
+  PinnedStage b;
+  {
+    std::lock_guard<std::mutex> lk(g_flag_mu);
+    if (!g_stage_free.empty()) {
+      b = g_stage_free.back();
+      g_stage_free.pop_back();
+    }
+  }
+  if (b.cap < bytes) {
+    if (b.p) cudaFreeHost(b.p);
+    b.cap = std::max<size_t>(bytes, 64u << 10);
+    if (cudaHostAlloc(reinterpret_cast<void**>(&b.p), b.cap, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      b = PinnedStage();
+    }
+  }
+  return b;
+}
+static void pinned_stage_release(const PinnedStage& b) {
+  if (!b.p) return;
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  g_stage_free.push_back(b);
+}
+// Device -> host copies of one call gathered in a pinned stage: add() lays
+// out the pieces (16-byte aligned), run() issues the copies and waits once,
+// then copies every piece to its destination.
+struct Readback {
+  struct Piece {
+    void* dst;
+    const void* src;
+    size_t bytes, off;
+  };
+  std::vector<Piece> pieces;
+  size_t total = 0;
+  void add(void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return;
+    pieces.push_back({dst, src, bytes, total});
+    total += (bytes + 15) & ~size_t(15);
+  }
+  kkm_status run(cudaStream_t st) {
+    PinnedStage b = pinned_stage_acquire(total);
+    if (!b.p) {  // no pinned memory: pageable copies
+      for (auto& q : pieces) KKM_CK(cudaMemcpyAsync(q.dst, q.src, q.bytes, cudaMemcpyDeviceToHost, st));
+      KKM_CK(cudaStreamSynchronize(st));
+      return KKM_OK;
+    }
+    for (auto& q : pieces) {
+      const cudaError_t e = cudaMemcpyAsync(b.p + q.off, q.src, q.bytes, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        pinned_stage_release(b);
+        return cuda_fail(e, "cudaMemcpyAsync (read-back)", __FILE__, __LINE__);
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess)
+      for (auto& q : pieces) memcpy(q.dst, b.p + q.off, q.bytes);
+    pinned_stage_release(b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (read-back)", __FILE__, __LINE__);
+    return KKM_OK;
+  }
+};
+
 // The answer of a finite-input check enqueued without waiting for it.
 struct PendingCheck {
   int* flag = nullptr;  // pinned
@@ -375,6 +448,15 @@ __global__ void gather_i64_kernel(const int64_t* in, const int32_t* idx, int64_t
 __global__ void gather_i32_kernel(const int32_t* in, const int32_t* idx, int64_t n, int32_t* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[idx[i]];
+}
+// Rows ids[0..C) of the row-major n x d matrix X, packed into out [C][d].
+__global__ void gather_raw_rows_kernel(const float* __restrict__ X, int64_t d, const int64_t* __restrict__ ids,
+                                       int C, float* __restrict__ out) {
+  const int64_t n = (int64_t)C * d;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / d;
+    out[t] = X[ids[r] * d + (t - r * d)];
+  }
 }
 __global__ void clamp_idx_kernel(const int32_t* in, int n, int32_t* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1064,7 +1146,7 @@ struct FitStreams {
   ~FitStreams() { join(); }
 };
 
-kkm_status model_alloc_device(kkm_model* m) {
+kkm_status model_alloc_device(kkm_model* m, cudaStream_t st) {
   const int64_t nL = m->nL, C = m->C, dp = m->dp, mu = m->max_units;
   // one allocation for the resident arrays (256-byte aligned pieces)
   std::vector<std::pair<void**, size_t>> parts;
@@ -1090,7 +1172,10 @@ kkm_status model_alloc_device(kkm_model* m) {
   A(&m->med_aux, C);
   size_t total = 0;
   for (auto& pr : parts) total += (pr.second + 255) & ~size_t(255);
-  KKM_CK(cudaMalloc(&m->arena, total));
+  // from the device's stream-ordered pool (its release threshold keeps the
+  // memory mapped), so that freeing a model does not unmap it
+  setup_pool_once(m->device);
+  KKM_CK(cudaMallocAsync(&m->arena, total, st));
   size_t off = 0;
   for (auto& pr : parts) {
     *pr.first = static_cast<unsigned char*>(m->arena) + off;
@@ -1454,7 +1539,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       m->device = dev;
       std::unique_ptr<kkm_model> guard(m);
       m->max_units = lb.max_units;
-      KKM_TRY(model_alloc_device(m));
+      KKM_TRY(model_alloc_device(m, ms));
       const int mu = m->max_units;
       auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
         KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ms));
@@ -1480,52 +1565,41 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
 
   KKM_TRY(fs.join());
 
-  // ---- results
-  if (model_out && *model_out) {
-    kkm_model* m = *model_out;
+  // ---- results: every read-back through one pinned stage, one wait
+  kkm_model* const mres = model_out ? *model_out : nullptr;
+  const int32_t tcap = std::max(trace_cap, 1);
+  int32_t tc = 0;
+  std::vector<double> om_h;
+  std::vector<int32_t> ch_h;
+  int tc_err_h = 0, rtc_err_h[2] = {0, 0}, it_err_h = 0;
+  std::unique_ptr<kkm_checkpoint> ck;
+  Readback rb;
+  if (mres) {
+    kkm_model* m = mres;
     KKM_TRY(prep_ids(sp, X, Mg, C, m->med, m->med_aux, st));
+    float* coords = nullptr;  // medoid rows in the caller's layout
+    KKM_TRY(ws.alloc(&coords, (int64_t)C * d));
+    KKM_RUN("gather_rows", st,
+            (gather_raw_rows_kernel<<<blocks_for((int64_t)C * d), 256, 0, st>>>(X, d, Mg, C, coords),
+             cudaGetLastError()));
     m->medoids.resize(C);
     m->W.resize(C);
-    int32_t tc = 0;
-    KKM_CK(cudaMemcpyAsync(m->medoids.data(), Mg, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(m->W.data(), W, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(&tc, I.trace_count, 4, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaStreamSynchronize(st));
-    m->omega.resize(tc);
-    m->changed.resize(tc);
     m->displacement.resize(B);
-    KKM_CK(cudaMemcpyAsync(m->displacement.data(), disp, (size_t)B * 8, cudaMemcpyDeviceToHost, st));
-    if (tc > 0) {
-      KKM_CK(cudaMemcpyAsync(m->omega.data(), I.trace_omega, (size_t)tc * 8, cudaMemcpyDeviceToHost, st));
-      KKM_CK(cudaMemcpyAsync(m->changed.data(), I.trace_changed, (size_t)tc * 4, cudaMemcpyDeviceToHost, st));
-    }
     m->sup_labels_h.resize(m->nL);
     m->ghat_h.resize(C);
     m->n_h.resize(C);
-    KKM_CK(cudaMemcpyAsync(m->sup_labels_h.data(), m->sup_labels, (size_t)m->nL * 4, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(m->ghat_h.data(), m->ghat, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(m->n_h.data(), m->n_j, (size_t)C * 4, cudaMemcpyDeviceToHost, st));
     m->med_coords_h.resize((size_t)C * d);
-  }
-  if (labels_on_host)
-    KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
-  int tc_err_h = 0, rtc_err_h[2] = {0, 0}, it_err_h = 0;
-  if (tc_err) KKM_CK(cudaMemcpyAsync(&tc_err_h, tc_err, 4, cudaMemcpyDeviceToHost, st));
-  KKM_CK(cudaMemcpyAsync(&it_err_h, I.err, 4, cudaMemcpyDeviceToHost, st));
-  for (int q = 0; q < nbuf; ++q)
-    if (use_rtc) KKM_CK(cudaMemcpyAsync(&rtc_err_h[q], bb[q].rtc.err, 4, cudaMemcpyDeviceToHost, st));
-  KKM_CK(cudaStreamSynchronize(st));
-  tc_err_h |= rtc_err_h[0] | rtc_err_h[1];
-  if (tc_err_h) {
-    set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
-    return KKM_ETIMEOUT;
-  }
-  if (it_err_h) {
-    set_error("fused inner iteration: the bounded grid-barrier wait gave up");
-    return KKM_ETIMEOUT;
+    rb.add(m->medoids.data(), Mg, (size_t)C * 8);
+    rb.add(m->W.data(), W, (size_t)C * 8);
+    rb.add(m->displacement.data(), disp, (size_t)B * 8);
+    rb.add(m->sup_labels_h.data(), m->sup_labels, (size_t)m->nL * 4);
+    rb.add(m->ghat_h.data(), m->ghat, (size_t)C * 8);
+    rb.add(m->n_h.data(), m->n_j, (size_t)C * 4);
+    rb.add(m->med_coords_h.data(), coords, (size_t)C * d * 4);
   }
   if (ckpt_out) {
-    std::unique_ptr<kkm_checkpoint> c(new kkm_checkpoint());
+    ck.reset(new kkm_checkpoint());
+    kkm_checkpoint* c = ck.get();
     c->N = N;
     c->d = d;
     c->C = C;
@@ -1545,28 +1619,42 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     c->M.resize(C);
     c->W.resize(C);
     c->displacement.resize(stop);
-    int32_t tc = 0;
-    KKM_CK(cudaMemcpyAsync(c->M.data(), Mg, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(c->W.data(), W, (size_t)C * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(c->displacement.data(), disp, (size_t)stop * 8, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaMemcpyAsync(&tc, I.trace_count, 4, cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaStreamSynchronize(st));
-    c->omega.resize(tc);
-    c->changed.resize(tc);
-    if (tc > 0) {
-      KKM_CK(cudaMemcpyAsync(c->omega.data(), I.trace_omega, (size_t)tc * 8, cudaMemcpyDeviceToHost, st));
-      KKM_CK(cudaMemcpyAsync(c->changed.data(), I.trace_changed, (size_t)tc * 4, cudaMemcpyDeviceToHost, st));
-      KKM_CK(cudaStreamSynchronize(st));
-    }
-    *ckpt_out = c.release();
+    rb.add(c->M.data(), Mg, (size_t)C * 8);
+    rb.add(c->W.data(), W, (size_t)C * 8);
+    rb.add(c->displacement.data(), disp, (size_t)stop * 8);
   }
-  if (model_out && *model_out) {
-    kkm_model* m = *model_out;
-    // medoid coordinates in the caller's layout
-    for (int j = 0; j < C; ++j)
-      KKM_CK(cudaMemcpyAsync(m->med_coords_h.data() + (size_t)j * d, X + m->medoids[j] * d, (size_t)d * 4,
-                             cudaMemcpyDeviceToHost, st));
-    KKM_CK(cudaStreamSynchronize(st));
+  if (mres || ckpt_out) {  // the whole trace capacity; the count says how much of it is used
+    om_h.resize(tcap);
+    ch_h.resize(tcap);
+    rb.add(&tc, I.trace_count, 4);
+    rb.add(om_h.data(), I.trace_omega, (size_t)tcap * 8);
+    rb.add(ch_h.data(), I.trace_changed, (size_t)tcap * 4);
+  }
+  if (labels_on_host)
+    KKM_CK(cudaMemcpyAsync(labels_out, labels_dev, (size_t)N * 4, cudaMemcpyDeviceToHost, st));
+  if (tc_err) rb.add(&tc_err_h, tc_err, 4);
+  rb.add(&it_err_h, I.err, 4);
+  for (int q = 0; q < nbuf; ++q)
+    if (use_rtc) rb.add(&rtc_err_h[q], bb[q].rtc.err, 4);
+  KKM_TRY(rb.run(st));
+  tc_err_h |= rtc_err_h[0] | rtc_err_h[1];
+  if (tc_err_h) {
+    set_error("tensor-core kernel block: a bounded pipeline wait gave up (code " + std::to_string(tc_err_h) + ")");
+    return KKM_ETIMEOUT;
+  }
+  if (it_err_h) {
+    set_error("fused inner iteration: the bounded grid-barrier wait gave up");
+    return KKM_ETIMEOUT;
+  }
+  tc = std::min(std::max(tc, 0), tcap);
+  if (mres) {
+    mres->omega.assign(om_h.begin(), om_h.begin() + tc);
+    mres->changed.assign(ch_h.begin(), ch_h.begin() + tc);
+  }
+  if (ck) {
+    ck->omega.assign(om_h.begin(), om_h.begin() + tc);
+    ck->changed.assign(ch_h.begin(), ch_h.begin() + tc);
+    *ckpt_out = ck.release();
   }
   prof_collect();
   return KKM_OK;

@@ -71,15 +71,22 @@ struct kkm_model {
   std::vector<float> med_coords_h;  // [C][d]
   void* arena = nullptr;            // one device allocation holding every array above
   ~kkm_model() {
-    if (arena) cudaFree(arena);
+    // like cudaFree: every launch that may still read the model finishes
+    // first; the memory then goes back to the stream-ordered pool
+    if (arena) {
+      cudaDeviceSynchronize();
+      cudaFreeAsync(arena, nullptr);
+      cudaGetLastError();
+    }
   }
 };
 
 namespace kkm {
 
 // One device allocation (m->arena) for the model's resident arrays, sized from
-// C, dp, nL and max_units; the array pointers point into it.
-kkm_status model_alloc_device(kkm_model* m);
+// C, dp, nL and max_units, ordered on stream st (m->device must be set); the
+// array pointers point into it.
+kkm_status model_alloc_device(kkm_model* m, cudaStream_t st = nullptr);
 
 // ------------------------------------------------------- random numbers ---
 // SplitMix64 (Steele, Lea & Flood 2014) from its published definition; u01

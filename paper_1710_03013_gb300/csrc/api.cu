@@ -697,11 +697,16 @@ constexpr double kL2KeepShareHalf = 0.70;
 // ======================================================================
 // Bandwidth rule
 // ======================================================================
-static kkm_status median_bandwidth_dev(const KernelSpec& sp, const float* X, int64_t N, uint64_t bw_seed,
-                                       Workspace& ws, float* sigma_out) {
+// Median rule enqueued on ws.st: the distances of min(N, 2048) samples drawn
+// from the bandwidth stream and their median.  The answer lands in
+// *sigma_host (pinned host memory) when the stream reaches it; it is read
+// with median_sigma_of after a wait.  NaN or Inf rows give a meaningless
+// answer but no fault (the select bins bit patterns).
+static kkm_status median_bandwidth_enqueue(const KernelSpec& sp, const float* X, int64_t N, uint64_t bw_seed,
+                                           Workspace& ws, float* sigma_host) {
   const int64_t M = std::min<int64_t>(N, 2048);
   if (M < 2) {
-    *sigma_out = 1.0f;
+    *sigma_host = 1.0f;
     return KKM_OK;
   }
   SplitMix64 bw(bw_seed);
@@ -728,12 +733,25 @@ static kkm_status median_bandwidth_dev(const KernelSpec& sp, const float* X, int
   }
   const int64_t pairs = M * (M - 1) / 2;
   KKM_RUN("median_select", st, launch_select_upper(D, (int)M, ld, (pairs - 1) / 2, scratch, out, st));
-  float sig = 0.0f;
-  KKM_CK(cudaMemcpyAsync(&sig, out, 4, cudaMemcpyDeviceToHost, st));
-  KKM_CK(cudaStreamSynchronize(st));
-  if (!(sig > 0.0f) || !isfinite(sig)) sig = 1.0f;
-  *sigma_out = sig;
+  KKM_CK(cudaMemcpyAsync(sigma_host, out, 4, cudaMemcpyDeviceToHost, st));
   return KKM_OK;
+}
+// The bandwidth from the median (1 when it is not a positive finite number).
+static float median_sigma_of(float m) { return (m > 0.0f && isfinite(m)) ? m : 1.0f; }
+
+static kkm_status median_bandwidth_dev(const KernelSpec& sp, const float* X, int64_t N, uint64_t bw_seed,
+                                       Workspace& ws, float* sigma_out) {
+  int* slot = pinned_flag_acquire();
+  float pageable = 0.0f;
+  float* h = slot ? reinterpret_cast<float*>(slot) : &pageable;
+  kkm_status r = median_bandwidth_enqueue(sp, X, N, bw_seed, ws, h);
+  if (r == KKM_OK) {
+    const cudaError_t e = cudaStreamSynchronize(ws.st);
+    if (e != cudaSuccess) r = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  }
+  if (r == KKM_OK) *sigma_out = median_sigma_of(*h);
+  pinned_flag_release(slot);
+  return r;
 }
 
 // ======================================================================
@@ -1250,9 +1268,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   setup_pool_once(dev);
   Workspace ws(st);
 
-  // ---- inputs on the device; the finite check runs while the host draws
-  // the random numbers and sets up the workspace, and nothing else runs on
-  // the device before its answer
+  // ---- inputs on the device; the finite check (then the median rule) runs
+  // while the host draws the random numbers and sets up the workspace, and
+  // a fit whose X holds NaN or Inf returns before any step of Alg. 1
   const float* X = nullptr;
   PendingCheck chk;
   {
@@ -1265,6 +1283,17 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   SplitMix64 master(seed);
   SplitMix64 kpp(master.next());
   const uint64_t bw_seed = master.next();
+  // ---- bandwidth: the median rule runs behind the check while the host
+  // draws the landmarks (a resumed fit keeps the bandwidth it started with)
+  const float sigma_arg = sp.sigma;
+  const bool need_median = !from && sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f);
+  struct PinnedWord {
+    int* p = pinned_flag_acquire();
+    ~PinnedWord() { pinned_flag_release(p); }
+  } sig_slot;
+  float sig_pageable = 1.0f;
+  float* const sig_h = sig_slot.p ? reinterpret_cast<float*>(sig_slot.p) : &sig_pageable;
+  if (need_median) KKM_TRY(median_bandwidth_enqueue(sp, X, N, bw_seed, ws, sig_h));
   std::vector<SplitMix64> lm;
   for (int i = 0; i < B; ++i) lm.emplace_back(master.next());
   std::vector<int64_t> L_off(B + 1, 0);
@@ -1401,15 +1430,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_TRY(chk.wait(&bad));
     if (bad) return invalid("X holds NaN or Inf");
   }
-
-  // ---- bandwidth (a resumed fit keeps the one it started with)
-  const float sigma_arg = sp.sigma;
   if (from) {
     sp.sigma = from->sigma;
-  } else if (sp.kind != KKM_LINEAR && !(sp.sigma > 0.0f)) {
-    float sig = 1.0f;
-    KKM_TRY(median_bandwidth_dev(sp, X, N, bw_seed, ws, &sig));
-    sp.sigma = sig;
+  } else if (need_median) {
+    KKM_CK(cudaStreamSynchronize(st));  // at once when the check's wait already covered it
+    sp.sigma = median_sigma_of(*sig_h);
   }
 
   // Alg. 1 line 3 for mini-batch i on stream `bs`: its rows, landmark rows,

@@ -274,8 +274,12 @@ kkm_status kkm_elbow(const float* X, int64_t N, int64_t d, int32_t C_lo,
  * paper fits one data set at a time; this is a library service around
  * Algorithm 1, not a change to it.
  *   problems   [n] host array.
- *   n_streams  concurrent CUDA streams (one host worker thread each), 1..64,
- *              or 0 for the default (8).  Fits start longest first.
+ *   n_streams  concurrent fits (one host worker thread and CUDA stream
+ *              each), 1..64, or 0 for the default (32).  Fits start longest
+ *              first.  Their inner loops run as work lists: one launch per
+ *              step of an iteration covers every loop in flight (each loop's
+ *              CTAs compute what its own launches would), on a stream of the
+ *              call's own.
  *   models_out [n] host array of model pointers (nullable); a failed
  *              problem's entry is NULL.
  *   status_out [n] host array: each problem's status.

@@ -58,7 +58,7 @@ static int g_prof_on = 0;  // 0 off, 1 time every launch, 2 count all, time the 
 
 static bool heavy_kernel(const char* name) {
   return !strcmp(name, "gram_block") || !strcmp(name, "rmsd_block") || !strcmp(name, "rmsd_exact") ||
-         !strcmp(name, "fhat_partial") || !strcmp(name, "iterate");
+         !strcmp(name, "fhat_partial") || !strcmp(name, "iterate") || !strcmp(name, "fhat_multi");
 }
 static std::unordered_map<std::string, ProfEntry> g_prof;
 static std::vector<Pending> g_pending;
@@ -1049,6 +1049,13 @@ static kkm_status inner_loop(const BlockMode& bm, const BlockBufs& b, int64_t ld
                        : launch_iterate(b.KT, ldk, Ni, S, I, iters, kself, u, margin, fhat_out, ghat_out, early_stop,
                                         sm_count(), st, R));
     return KKM_OK;
+  }
+  LoopExecutor* ex = current_loop_executor();
+  if (ex && !margin && !fhat_out && !ghat_out) {  // a fit of a batch: the batch's work lists run the loop
+    LoopItem item;
+    KKM_CK(make_loop_item(bm.kt_half ? static_cast<const void*>(b.KTh) : static_cast<const void*>(b.KT), bm.kt_half,
+                          ldk, Ni, S, I, kself, u, early_stop, R, &item));
+    return loop_executor_run(ex, item, iters, st);
   }
   for (int t = 0; t < iters; ++t) {
     KKM_RUN("fhat_partial", st,

@@ -18,6 +18,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -27,8 +29,244 @@
 
 namespace kkm {
 
+// ------------------------------------------------ inner loops as work lists
+// The fits of a batch hand their split-form inner loops to one executor
+// thread, which runs them in rounds on its own stream: per round one f_hat
+// stream launch over every loop in flight (one per block type present), then
+// one assign launch per CTA width present, each item's CTAs doing what its
+// own launch would (same results as a fit alone).  A loop joins at the next
+// round once the work before it on its fit's stream has finished (its event
+// is polled, so a fit still computing its block holds up no other loop) and
+// leaves after its iteration count; its fit's stream then waits for the
+// round that ran its last iteration.  At most two rounds are queued ahead of
+// the GPU, so a loop that becomes ready joins within about two rounds, and
+// the many small loops of a batch share launches instead of each paying two
+// launches per iteration.  The support sort after a landmark label change
+// runs in a third launch per round, one full CTA per loop, instead of in the
+// last CTA of the loop's assign.
+struct LoopExecutor {
+  struct Req {
+    LoopItem item;
+    int iters = 0;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    bool finished = false;
+    kkm_status status = KKM_OK;
+    std::string error;
+  };
+  static constexpr int kMirror = 1024;  // pinned copies of admitted items, reused round-robin
+  std::mutex mu;
+  std::condition_variable cv_submit, cv_done;
+  std::vector<Req*> incoming;
+  bool stopping = false;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  LoopItem* slots = nullptr;   // device [kRoundMaxItems]
+  LoopItem* mirror = nullptr;  // pinned [kMirror]
+  int mirror_next = 0;
+  cudaEvent_t round_ev[4] = {};
+  std::thread th;
+
+  kkm_status start(int dev) {
+    device = dev;
+    KKM_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    KKM_CK(cudaMalloc(&slots, sizeof(LoopItem) * kRoundMaxItems));
+    KKM_CK(cudaHostAlloc(reinterpret_cast<void**>(&mirror), sizeof(LoopItem) * kMirror, cudaHostAllocDefault));
+    for (auto& e : round_ev) KKM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    th = std::thread([this] { loop(); });
+    return KKM_OK;
+  }
+  // after every submitter has returned
+  void stop() {
+    if (th.joinable()) {
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        stopping = true;
+      }
+      cv_submit.notify_all();
+      th.join();
+    }
+    if (st) cudaStreamSynchronize(st);
+    for (auto& e : round_ev)
+      if (e) cudaEventDestroy(e);
+    if (slots) cudaFree(slots);
+    if (mirror) cudaFreeHost(mirror);
+    if (st) cudaStreamDestroy(st);
+    cudaGetLastError();
+    st = nullptr;
+    slots = nullptr;
+    mirror = nullptr;
+    for (auto& e : round_ev) e = nullptr;
+  }
+
+  kkm_status run(const LoopItem& item, int iters, cudaStream_t fit_st) {
+    if (iters <= 0) return KKM_OK;
+    Req r;
+    r.item = item;
+    r.iters = iters;
+    KKM_CK(cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming));
+    cudaError_t e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(r.ready, fit_st);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(r.ready);
+      if (r.done) cudaEventDestroy(r.done);
+      return cuda_fail(e, "loop executor: event", __FILE__, __LINE__);
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      incoming.push_back(&r);
+    }
+    cv_submit.notify_one();
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_done.wait(lk, [&] { return r.finished; });
+    }
+    kkm_status s = r.status;
+    if (s == KKM_OK) {
+      e = cudaStreamWaitEvent(fit_st, r.done, 0);
+      if (e != cudaSuccess) s = cuda_fail(e, "cudaStreamWaitEvent", __FILE__, __LINE__);
+    } else {
+      set_error(r.error);
+    }
+    cudaEventDestroy(r.ready);
+    cudaEventDestroy(r.done);
+    return s;
+  }
+
+ private:
+  struct Active {
+    Req* r;
+    int slot;
+    int left;
+  };
+  void finish(Req* r, kkm_status s, const char* what, cudaError_t e) {
+    std::lock_guard<std::mutex> lk(mu);
+    r->status = s;
+    if (s != KKM_OK) r->error = std::string("loop executor: ") + what + ": " + cudaGetErrorString(e);
+    r->finished = true;
+    cv_done.notify_all();
+  }
+  // one iteration of every active loop
+  cudaError_t round(const std::vector<Active>& act) {
+    for (int half = 1; half >= 0; --half) {
+      RoundList L;
+      L.cta_off[0] = 0;
+      for (const Active& a : act)
+        if (a.r->item.half == half) {
+          L.slot[L.n] = a.slot;
+          L.cta_off[L.n + 1] = L.cta_off[L.n] + a.r->item.units * a.r->item.n_strips;
+          ++L.n;
+        }
+      if (L.n == 0) continue;
+      ProfScope ps("fhat_multi", st);
+      const cudaError_t e = launch_fhat_multi(slots, L, half != 0, st);
+      if (e != cudaSuccess) return e;
+    }
+    for (int nw = 1; nw <= 8; ++nw) {
+      RoundList L;
+      L.cta_off[0] = 0;
+      int smem = 0;
+      for (const Active& a : act)
+        if (a.r->item.nw == nw) {
+          L.slot[L.n] = a.slot;
+          L.cta_off[L.n + 1] = L.cta_off[L.n] + a.r->item.assign_ctas;
+          smem = std::max(smem, a.r->item.assign_smem);
+          ++L.n;
+        }
+      if (L.n == 0) continue;
+      ProfScope ps("assign_multi", st);
+      const cudaError_t e = launch_assign_multi(slots, L, nw, smem, st);
+      if (e != cudaSuccess) return e;
+    }
+    RoundList L;
+    for (const Active& a : act) {
+      L.slot[L.n] = a.slot;
+      L.cta_off[L.n] = L.n;
+      ++L.n;
+    }
+    L.cta_off[L.n] = L.n;
+    ProfScope ps("sort_multi", st);
+    return launch_sort_multi(slots, L, st);
+  }
+  void loop() {
+    cudaSetDevice(device);
+    std::vector<Req*> pending;
+    std::vector<Active> act;
+    std::vector<int> free_slots;
+    for (int q = kRoundMaxItems - 1; q >= 0; --q) free_slots.push_back(q);
+    long long rounds = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        if (act.empty() && pending.empty() && incoming.empty()) {
+          if (stopping) break;
+          cv_submit.wait(lk, [&] { return stopping || !incoming.empty(); });
+          continue;
+        }
+        pending.insert(pending.end(), incoming.begin(), incoming.end());
+        incoming.clear();
+      }
+      // admit the loops whose preceding work has finished
+      for (size_t q = 0; q < pending.size() && !free_slots.empty();) {
+        Req* r = pending[q];
+        const cudaError_t e = cudaEventQuery(r->ready);
+        if (e == cudaErrorNotReady) {
+          ++q;
+          continue;
+        }
+        pending.erase(pending.begin() + (std::ptrdiff_t)q);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          finish(r, KKM_ECUDA, "the work before a loop", e);
+          continue;
+        }
+        const int slot = free_slots.back();
+        LoopItem* m = mirror + (mirror_next++ % kMirror);
+        *m = r->item;
+        const cudaError_t c = cudaMemcpyAsync(slots + slot, m, sizeof(LoopItem), cudaMemcpyHostToDevice, st);
+        if (c != cudaSuccess) {
+          cudaGetLastError();
+          finish(r, KKM_ECUDA, "item upload", c);
+          continue;
+        }
+        free_slots.pop_back();
+        act.push_back(Active{r, slot, r->iters});
+      }
+      if (act.empty()) {
+        std::this_thread::yield();
+        continue;
+      }
+      if (rounds >= 2) cudaEventSynchronize(round_ev[(rounds - 2) & 3]);
+      cudaError_t e = round(act);
+      if (e == cudaSuccess) e = cudaEventRecord(round_ev[rounds & 3], st);
+      ++rounds;
+      for (size_t q = 0; q < act.size();) {
+        Active& a = act[q];
+        if (e != cudaSuccess || --a.left == 0) {
+          cudaError_t d = e;
+          if (d == cudaSuccess) d = cudaEventRecord(a.r->done, st);
+          free_slots.push_back(a.slot);
+          finish(a.r, d == cudaSuccess ? KKM_OK : KKM_ECUDA, "round launch", d);
+          act.erase(act.begin() + (std::ptrdiff_t)q);
+        } else {
+          ++q;
+        }
+      }
+      if (e != cudaSuccess) cudaGetLastError();
+    }
+  }
+};
+
+static thread_local LoopExecutor* t_loop_exec = nullptr;
+LoopExecutor* current_loop_executor() { return t_loop_exec; }
+kkm_status loop_executor_run(LoopExecutor* ex, const LoopItem& item, int iters, cudaStream_t st) {
+  return ex->run(item, iters, st);
+}
+
 // Default number of concurrent streams for a batch.
-constexpr int kBatchStreams = 8;
+// (32: a fit waits while the work lists run its inner loop, so more fits are
+// in flight than loops; measured on 256 uneven problems: 8 -> 200 ms,
+// 16 -> 177 ms, 32 -> 171 ms, 64 -> 174 ms)
+constexpr int kBatchStreams = 32;
 constexpr int kBatchMaxStreams = 64;
 
 static double fit_work(const kkm_problem& p) {
@@ -43,7 +281,7 @@ static double fit_work(const kkm_problem& p) {
 }
 
 static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams, kkm_model** models_out,
-                             kkm_status* status_out, cudaStream_t caller) {
+                             kkm_status* status_out, cudaStream_t caller, bool no_work_lists = false) {
   if (n < 0) {
     set_error("n must be >= 0");
     return KKM_EINVAL;
@@ -78,8 +316,19 @@ static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams,
   std::atomic<int32_t> next{0};
   std::vector<std::string> errors(n);
   std::vector<std::string> worker_err(W);
+  LoopExecutor exec;
+  const bool use_exec = !no_work_lists;
+  if (use_exec) {
+    const kkm_status es = exec.start(dev);
+    if (es != KKM_OK) {
+      exec.stop();
+      cudaEventDestroy(ready);
+      return es;
+    }
+  }
 
   auto worker = [&](int w) {
+    t_loop_exec = use_exec ? &exec : nullptr;
     cudaStream_t st = nullptr;
     if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
@@ -105,11 +354,13 @@ static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams,
     }
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
+    t_loop_exec = nullptr;
   };
   std::vector<std::thread> threads;
   threads.reserve(W);
   for (int w = 0; w < W; ++w) threads.emplace_back(worker, w);
   for (auto& t : threads) t.join();
+  exec.stop();
   cudaEventDestroy(ready);
 
   for (int w = 0; w < W; ++w)

@@ -404,6 +404,58 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
                           float* fhat_out, double* ghat_out, int early_stop, int trace,
                           cudaStream_t st, const RescoreArgs& R = RescoreArgs());
 
+// ---------------------------------------------- inner loops as work lists
+// One mini-batch's inner loop (split form) as an item of a work-list launch:
+// what fhat_partial and assign take for it.  A launch over a RoundList runs
+// one iteration's f_hat stream (or assign) of every listed item, each item's
+// CTAs doing exactly what its own launch would, so results are unchanged.
+struct alignas(16) LoopItem {
+  const void* KT = nullptr;  // [nL][ldk] kernel block (__half when half, else float)
+  int64_t ldk = 0;
+  int Ni = 0;
+  int half = 0;
+  int n_strips = 0;  // column strips of the f_hat stream
+  int units = 0;     // unit rows of the f_hat stream (S.max_units)
+  int nw = 0;        // warps of an assign CTA
+  int early_stop = 0;
+  int assign_ctas = 0;
+  int assign_smem = 0;  // dynamic shared memory of an assign CTA
+  double gfix_scale = 0.0;
+  const float* kself = nullptr;
+  int32_t* u = nullptr;
+  Supports S{};
+  IterState I{};
+  RescoreArgs R{};
+};
+constexpr int kRoundMaxItems = 64;
+// The items of one launch: device slots and their first CTAs (cta_off[n] is
+// the grid size).
+struct RoundList {
+  int n = 0;
+  int slot[kRoundMaxItems];
+  int cta_off[kRoundMaxItems + 1];
+};
+// Fills the item of one mini-batch's loop (arguments as launch_fhat_partial
+// and launch_assign take them in a fit).
+cudaError_t make_loop_item(const void* KT, bool half, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, int early_stop, const RescoreArgs& R, LoopItem* out);
+// One f_hat stream of every item in L (items: device array of slots; all
+// items of one launch have the same block type).
+cudaError_t launch_fhat_multi(const LoopItem* items, const RoundList& L, bool half, cudaStream_t st);
+// One assign (trace on) of every item in L; the items share nw and the
+// dynamic shared memory is the largest they need.
+cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, cudaStream_t st);
+// The support sort of every listed item whose landmark labels changed in the
+// assign launches before it (their last CTAs leave it to this launch).
+cudaError_t launch_sort_multi(const LoopItem* items, const RoundList& L, cudaStream_t st);
+// The work-list runner of a batch's inner loops (batch.cu).  A fit whose
+// thread has one (set by kkm_fit_batch's workers) hands every split-form
+// inner loop to it: run() returns once the loop's last iteration is queued,
+// with the fit's stream ordered after it.
+struct LoopExecutor;
+LoopExecutor* current_loop_executor();
+kkm_status loop_executor_run(LoopExecutor* ex, const LoopItem& item, int iters, cudaStream_t st);
+
 // The whole inner loop of a mini-batch (up to `iters` iterations: f_hat,
 // g_hat, d, argmin, margin, re-score, Omega, trace, early stop, support
 // re-sort) in one cooperative launch of at most one CTA per SM, each owning a

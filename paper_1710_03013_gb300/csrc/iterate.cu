@@ -292,12 +292,15 @@ __device__ __forceinline__ void stream_rows(const T* base, int64_t ldk, const in
 // in flight together instead of interleaving them with the additions.
 // Chunks of 8 rows measured faster than 4, 12 or 16, and than two chunks in
 // flight with a register double buffer.
+// The body takes its (strip, unit) tile explicitly, so that one launch can
+// also cover the tiles of many mini-batches (fhat_partial_multi_kernel).
 template <typename T>
-__global__ void __launch_bounds__(kStreamThreads, 8)
-fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
-                    float* __restrict__ partial, float2* __restrict__ gpart, int n_strips,
-                    const int32_t* __restrict__ skip, int keep_rows, uint32_t* __restrict__ gtick,
-                    double* __restrict__ ghat, unsigned long long* __restrict__ gfix, double gfix_scale) {
+__device__ __forceinline__ void fhat_partial_body(const T* __restrict__ KT, int64_t ldk, int Ni, const Supports& S,
+                                                  float* __restrict__ partial, float2* __restrict__ gpart,
+                                                  int n_strips, const int32_t* __restrict__ skip, int keep_rows,
+                                                  uint32_t* __restrict__ gtick, double* __restrict__ ghat,
+                                                  unsigned long long* __restrict__ gfix, double gfix_scale, int strip,
+                                                  int unit) {
   using Cfg = StreamCfg<T>;
   constexpr int NC = Cfg::kCols, DEPTH = Cfg::kDepth;
   __shared__ int rows[kUnitRows];
@@ -306,7 +309,6 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   __shared__ int last;
   griddep_wait();
   if (skip && *skip) return;
-  const int unit = blockIdx.y;
   // unit tables are allocated for max_units entries, so these loads stay in
   // bounds even for the units this launch does not use
   const int nu = *S.n_units;
@@ -318,7 +320,7 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
   uint64_t keep, stream;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
-  const int col = (blockIdx.x * kStreamThreads + threadIdx.x) * NC;
+  const int col = (strip * kStreamThreads + threadIdx.x) * NC;
   float acc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = 0.0f;
@@ -374,11 +376,11 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
       // non-negative (Gaussian kernel values); the scale is a power of two
       atomicAdd(gfix + j, (unsigned long long)llrint(((double)t.x + (double)t.y) * gfix_scale));
     } else {
-      gpart[(int64_t)unit * n_strips + blockIdx.x] = t;
+      gpart[(int64_t)unit * n_strips + strip] = t;
     }
     if (gtick && !gfix) {
       __threadfence();
-      const uint32_t expect = (uint32_t)(S.seg_unit[j + 1] - S.seg_unit[j]) * gridDim.x;
+      const uint32_t expect = (uint32_t)(S.seg_unit[j + 1] - S.seg_unit[j]) * (uint32_t)n_strips;
       last = atomicAdd(gtick + j, 1u) + 1u == expect;
     }
   }
@@ -397,6 +399,16 @@ fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
     ghat[j] = n > 0 ? a2 / ((double)n * (double)n) : __longlong_as_double(0x7ff8000000000000LL);
     gtick[j] = 0u;  // ready for the next launch
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStreamThreads, 8)
+fhat_partial_kernel(const T* __restrict__ KT, int64_t ldk, int Ni, Supports S,
+                    float* __restrict__ partial, float2* __restrict__ gpart, int n_strips,
+                    const int32_t* __restrict__ skip, int keep_rows, uint32_t* __restrict__ gtick,
+                    double* __restrict__ ghat, unsigned long long* __restrict__ gfix, double gfix_scale) {
+  fhat_partial_body<T>(KT, ldk, Ni, S, partial, gpart, n_strips, skip, keep_rows, gtick, ghat, gfix, gfix_scale,
+                       (int)blockIdx.x, (int)blockIdx.y);
 }
 
 template <typename T>
@@ -503,11 +515,15 @@ __host__ __device__ inline int assign_dist_words(int C, int nw) {
 // largest dynamic shared memory an assign launch may ask for
 constexpr int kAssignMaxDynSmem = 160 * 1024;
 
-__global__ void __launch_bounds__(kAssignWarps * 32, 4)
-assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
-              int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
-              float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
-              int trace, RescoreArgs R) {
+// The body takes its row block bx and the number of row blocks G of its
+// mini-batch explicitly, so that one launch can also cover the row blocks of
+// many mini-batches (assign_multi_kernel).
+__device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                                            const float* __restrict__ kself, int32_t* __restrict__ u,
+                                            float* __restrict__ margin, float* __restrict__ dmin,
+                                            float* __restrict__ fhat_out, double* __restrict__ ghat_out,
+                                            int early_stop, int trace, const RescoreArgs& R, int bx, int G,
+                                            bool defer_sort = false) {
   // dynamic shared memory (sized by the launch for this C): the distances of
   // the CTA's rows [C][kAssignRows], which the last CTA reuses as the support
   // sort's scratch, then the FP32 row of the slow re-score path [R.dp]
@@ -531,7 +547,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   if (I.done && *I.done) return;
   const int C = S.C;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int i = blockIdx.x * kAssignRows + lane;
+  const int i = bx * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
   const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
   const int old_u = (w == 0 && i < Ni) ? u[i] : 0;
@@ -599,7 +615,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     sh.ghf[threadIdx.x] = (float)sh.gh[threadIdx.x];
   }
   __syncthreads();
-  if (blockIdx.x == 0 && ghat_out)
+  if (bx == 0 && ghat_out)
     for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   // d_ij = K_ii - 2 f_hat_ij + g_hat_j for the warp's clusters (+inf when
   // n_j = 0 or past the last row)
@@ -678,7 +694,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     // from the FP32 rows (16-byte loads; rows are padded to 8 floats)
     for (int p = w; p < n_cand; p += nw) {
       const int r = cand[p] >> 9, j = cand[p] & 511;
-      const int ir = blockIdx.x * kAssignRows + r;
+      const int ir = bx * kAssignRows + r;
       const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
       const float ni = R.nXi[ir];
       const float ksr = kself ? kself[ir] : 1.0f;
@@ -713,7 +729,7 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     // rows whose candidates did not fit the list: the whole CTA per row
     for (unsigned fm = slow_mask; fm; fm &= fm - 1) {  // the same sequence in every thread
       const int r = __ffs(fm) - 1;
-      const int ir = blockIdx.x * kAssignRows + r;
+      const int ir = bx * kAssignRows + r;
       const float* xi = R.Xi + (int64_t)ir * R.dp;
       for (int c = threadIdx.x; c < R.dp; c += blockDim.x) xs[c] = xi[c];
       __syncthreads();
@@ -786,9 +802,9 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
     ch = warp_sum_i32(ch);
     lmc = warp_sum_i32(lmc);
     if (lane == 0) {
-      I.omega_part[blockIdx.x] = om;
-      I.changed_part[blockIdx.x] = ch;
-      if (I.lm_part) I.lm_part[blockIdx.x] = lmc;
+      I.omega_part[bx] = om;
+      I.changed_part[bx] = ch;
+      if (I.lm_part) I.lm_part[bx] = lmc;
     }
   }
   if (trace != 1) return;
@@ -799,14 +815,13 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   // support tables by the time it takes its ticket).
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) is_last = (atomicAdd(I.ticket, 1u) == (unsigned)G - 1u);
   __syncthreads();
   if (!is_last) return;
   griddep_launch();
   __threadfence();
   float2 o = make_float2(0.0f, 0.0f);
   int c = 0, lm = 0;
-  const int G = (int)gridDim.x;
   for (int b = threadIdx.x; b < G; b += blockDim.x) {
     o = df_add(o, __ldcg(I.omega_part + b));
     c += __ldcg(I.changed_part + b);
@@ -845,9 +860,18 @@ assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restr
   if (I.gfix)
     for (int j = threadIdx.x; j < C; j += blockDim.x) I.gfix[j] = 0ull;
   __syncthreads();
-  if (wl[0] == 0) return;  // same landmark labels: same supports
+  if (wl[0] == 0 || defer_sort) return;  // same landmark labels: same supports (or sorted by a later launch)
   int* const scr = reinterpret_cast<int*>(dyn);  // every CTA is past its distances
   sort_supports_cta(S, scr, scr + C, scr + 2 * C, scr + 2 * C + nw * C);
+}
+
+__global__ void __launch_bounds__(kAssignWarps * 32, 4)
+assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
+              int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
+              float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
+              int trace, RescoreArgs R) {
+  assign_body(ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R, (int)blockIdx.x,
+              (int)gridDim.x);
 }
 
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
@@ -865,6 +889,127 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
   if (attr != cudaSuccess) return attr;
   return launch_pdl(assign_kernel, dim3((unsigned)ceil_div(Ni, kAssignRows)), dim3(threads), smem, st, ldk, Ni, S,
                     I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
+}
+
+// ------------------------------------------- inner loops as work lists
+// The item whose CTA range [cta_off[k], cta_off[k + 1]) holds CTA b.
+__device__ __forceinline__ int round_item_of(const RoundList& L, int b) {
+  int lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (L.cta_off[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+// Copies item `slot` into shared memory (16-byte words).
+__device__ __forceinline__ const LoopItem& load_item(const LoopItem* __restrict__ items, int slot,
+                                                    unsigned char* sh) {
+  const int4* src = reinterpret_cast<const int4*>(items + slot);
+  int4* dst = reinterpret_cast<int4*>(sh);
+  for (int t = threadIdx.x; t < (int)(sizeof(LoopItem) / 16); t += blockDim.x) dst[t] = src[t];
+  __syncthreads();
+  return *reinterpret_cast<const LoopItem*>(sh);
+}
+
+// Every CTA waits for the launch before it first (programmatic dependent
+// launch), so that a launch of the work list completes only after the one
+// before it has: the chain of launches stays ordered for every item.
+template <typename T>
+__global__ void __launch_bounds__(kStreamThreads, 8)
+fhat_partial_multi_kernel(const LoopItem* __restrict__ items, RoundList L) {
+  __shared__ __align__(16) unsigned char raw[sizeof(LoopItem)];
+  griddep_wait();
+  const int k = round_item_of(L, (int)blockIdx.x);
+  const LoopItem& it = load_item(items, L.slot[k], raw);
+  const int local = (int)blockIdx.x - L.cta_off[k];
+  const int unit = local / it.n_strips, strip = local - unit * it.n_strips;
+  fhat_partial_body<T>(static_cast<const T*>(it.KT), it.ldk, it.Ni, it.S, it.I.partial, it.I.gpart, it.n_strips,
+                       it.I.done, it.I.keep_rows, it.S.col_label ? it.I.gtick : nullptr, it.I.ghat_cur,
+                       it.S.col_label ? it.I.gfix : nullptr, it.gfix_scale, strip, unit);
+}
+
+__global__ void __launch_bounds__(kAssignWarps * 32, 4)
+assign_multi_kernel(const LoopItem* __restrict__ items, RoundList L) {
+  __shared__ __align__(16) unsigned char raw[sizeof(LoopItem)];
+  griddep_wait();
+  const int k = round_item_of(L, (int)blockIdx.x);
+  const LoopItem& it = load_item(items, L.slot[k], raw);
+  const int bx = (int)blockIdx.x - L.cta_off[k], G = L.cta_off[k + 1] - L.cta_off[k];
+  assign_body(it.ldk, it.Ni, it.S, it.I, it.kself, it.u, nullptr, nullptr, nullptr, nullptr, it.early_stop,
+              /*trace=*/1, it.R, bx, G, /*defer_sort=*/true);
+}
+
+// The support sort of every listed item (one CTA of kSortThreads each) whose
+// landmark labels changed in the assign before it (the sum of its assign
+// CTAs' change counts): in a work-list round the sort runs here with a full
+// CTA, not in the item's last assign CTA.  The sort is stable, so the
+// supports are those the assign would have built.
+__global__ void __launch_bounds__(kSortThreads) sort_multi_kernel(const LoopItem* __restrict__ items, RoundList L) {
+  __shared__ int cnt[kMaxC];
+  __shared__ int base[kMaxC];
+  __shared__ int wtab[32 * kMaxC];
+  __shared__ int scan_sh[32];
+  __shared__ int any;
+  __shared__ __align__(16) unsigned char raw[sizeof(LoopItem)];
+  griddep_wait();
+  const LoopItem& it = load_item(items, L.slot[blockIdx.x], raw);
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int c = 0;
+  if (it.I.lm_part)
+    for (int b = threadIdx.x; b < it.assign_ctas; b += blockDim.x) c += __ldcg(it.I.lm_part + b);
+  if (c) atomicOr(&any, 1);
+  __syncthreads();
+  if (!any) return;
+  sort_supports_cta(it.S, cnt, base, wtab, scan_sh);
+}
+
+cudaError_t make_loop_item(const void* KT, bool half, int64_t ldk, int Ni, const Supports& S, const IterState& I,
+                           const float* kself, int32_t* u, int early_stop, const RescoreArgs& R, LoopItem* out) {
+  LoopItem it;
+  it.KT = KT;
+  it.ldk = ldk;
+  it.Ni = Ni;
+  it.half = half ? 1 : 0;
+  it.n_strips = (int)ceil_div(ldk, half ? StreamCfg<__half>::kStrip : StreamCfg<float>::kStrip);
+  if (it.n_strips > I.n_strips) return cudaErrorInvalidValue;  // gpart capacity
+  it.units = S.max_units;
+  it.nw = std::min(S.C, kAssignWarps);
+  it.early_stop = early_stop;
+  it.assign_ctas = (int)ceil_div(Ni, kAssignRows);
+  const size_t smem = ((size_t)assign_dist_words(S.C, it.nw) + (R.Xi ? (size_t)R.dp : 0)) * sizeof(float);
+  if (smem > (size_t)kAssignMaxDynSmem) return cudaErrorInvalidValue;
+  it.assign_smem = (int)smem;
+  it.gfix_scale = ldexp(1.0, I.gfix_shift);
+  it.kself = kself;
+  it.u = u;
+  it.S = S;
+  it.I = I;
+  it.R = R;
+  *out = it;
+  return cudaSuccess;
+}
+
+cudaError_t launch_fhat_multi(const LoopItem* items, const RoundList& L, bool half, cudaStream_t st) {
+  if (L.n <= 0 || L.cta_off[L.n] <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)L.cta_off[L.n]);
+  return half ? launch_pdl(fhat_partial_multi_kernel<__half>, grid, dim3(kStreamThreads), 0, st, items, L)
+              : launch_pdl(fhat_partial_multi_kernel<float>, grid, dim3(kStreamThreads), 0, st, items, L);
+}
+
+cudaError_t launch_sort_multi(const LoopItem* items, const RoundList& L, cudaStream_t st) {
+  if (L.n <= 0) return cudaSuccess;
+  return launch_pdl(sort_multi_kernel, dim3((unsigned)L.n), dim3(kSortThreads), 0, st, items, L);
+}
+
+cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, cudaStream_t st) {
+  if (L.n <= 0 || L.cta_off[L.n] <= 0) return cudaSuccess;
+  if (nw < 1 || nw > kAssignWarps || smem > kAssignMaxDynSmem) return cudaErrorInvalidValue;
+  static const cudaError_t attr = cudaFuncSetAttribute(assign_multi_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kAssignMaxDynSmem);
+  if (attr != cudaSuccess) return attr;
+  return launch_pdl(assign_multi_kernel, dim3((unsigned)L.cta_off[L.n]), dim3(32 * nw), (size_t)smem, st, items, L);
 }
 
 // ------------------------------------------------- fused inner loop

@@ -279,7 +279,11 @@ kkm_status kkm_elbow(const float* X, int64_t N, int64_t d, int32_t C_lo,
  *              first.  Their inner loops run as work lists: one launch per
  *              step of an iteration covers every loop in flight (each loop's
  *              CTAs compute what its own launches would), on a stream of the
- *              call's own.
+ *              call's own.  The rows per CTA of those assign launches (1, 2,
+ *              4 or 8 blocks of 32; no effect on results) are chosen by
+ *              timing per launch size and kept for the process; the
+ *              environment variable KKM_TUNE_CACHE names a file that keeps
+ *              the choices across processes, KKM_ASSIGN_ROWS forces one.
  *   models_out [n] host array of model pointers (nullable); a failed
  *              problem's entry is NULL.
  *   status_out [n] host array: each problem's status.

@@ -19,6 +19,10 @@
 #include <atomic>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -28,6 +32,101 @@
 #include "internal.h"
 
 namespace kkm {
+
+// ------------------------------------------- rows per assign CTA, by timing
+// A work-list assign CTA takes 1, 2, 4 or 8 blocks of 32 rows of its loop.
+// Every 32-row block does the same work and writes the same partial sums
+// whichever CTA takes it, so the choice changes no result, only time: few
+// rows per CTA spread a small round over the SMs, more rows amortise a CTA's
+// fixed work (cluster tables, barriers, its ticket) in a round of many loops.
+// Per key (the CTA width and the launch's row-block count rounded down to a
+// power of two) each candidate is timed on kTuneSamples live launches with
+// events, and the one with the least time per row block is kept for the
+// process.  KKM_TUNE_CACHE names a file the choices are read from when the
+// first executor starts and written back to when an executor stops (lines
+// "assign_rows <key> <rows>"); KKM_ASSIGN_ROWS forces one candidate.
+struct RowTuner {
+  static constexpr int kCand[4] = {1, 2, 4, 8};
+  static constexpr int kTuneSamples = 3;
+  struct Entry {
+    int best = 0;  // 0: still timing
+    double us_per_block[4] = {0.0, 0.0, 0.0, 0.0};
+    int n[4] = {0, 0, 0, 0};
+  };
+  std::mutex mu;
+  std::map<long long, Entry> table;
+  bool loaded = false;
+
+  static long long key(int nw, int blocks) {
+    int lg = 0;
+    while ((2LL << lg) <= blocks) ++lg;
+    return (long long)nw * 64 + lg;
+  }
+  static int forced() {
+    const char* f = getenv("KKM_ASSIGN_ROWS");
+    if (!f) return 0;
+    const int v = atoi(f);
+    for (int c : kCand)
+      if (c == v) return v;
+    return 0;
+  }
+  void load() {
+    std::lock_guard<std::mutex> lk(mu);
+    if (loaded) return;
+    loaded = true;
+    const char* path = getenv("KKM_TUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char name[32];
+    long long k;
+    int v;
+    while (fscanf(f, "%31s %lld %d", name, &k, &v) == 3)
+      if (!strcmp(name, "assign_rows"))
+        for (int c : kCand)
+          if (c == v) table[k].best = v;
+    fclose(f);
+  }
+  void save() {
+    const char* path = getenv("KKM_TUNE_CACHE");
+    if (!path) return;
+    std::lock_guard<std::mutex> lk(mu);
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (auto& kv : table)
+      if (kv.second.best) fprintf(f, "assign_rows %lld %d\n", kv.first, kv.second.best);
+    fclose(f);
+  }
+  // The candidate for a launch; *timed: this launch is a timing sample.
+  int choose(long long k, bool* timed) {
+    *timed = false;
+    if (const int f = forced()) return f;
+    std::lock_guard<std::mutex> lk(mu);
+    Entry& e = table[k];
+    if (e.best) return e.best;
+    int c = 0;
+    for (int q = 1; q < 4; ++q)
+      if (e.n[q] < e.n[c]) c = q;
+    *timed = true;
+    return kCand[c];
+  }
+  void sample(long long k, int rows, int blocks, float ms) {
+    std::lock_guard<std::mutex> lk(mu);
+    Entry& e = table[k];
+    if (e.best) return;
+    int c = 0;
+    while (kCand[c] != rows) ++c;
+    e.us_per_block[c] += 1e3 * ms / std::max(blocks, 1);
+    ++e.n[c];
+    for (int q = 0; q < 4; ++q)
+      if (e.n[q] < kTuneSamples) return;
+    int b = 0;
+    for (int q = 1; q < 4; ++q)
+      if (e.us_per_block[q] < e.us_per_block[b]) b = q;
+    e.best = kCand[b];
+  }
+};
+static RowTuner g_row_tuner;
 
 // ------------------------------------------------ inner loops as work lists
 // The fits of a batch hand their split-form inner loops to one executor
@@ -65,6 +164,14 @@ struct LoopExecutor {
   int mirror_next = 0;
   cudaEvent_t round_ev[4] = {};
   std::thread th;
+  // timing samples of the row tuner still in flight
+  struct Sample {
+    long long key;
+    int rows, blocks;
+    cudaEvent_t a, b;
+  };
+  std::vector<Sample> samples;
+  std::vector<cudaEvent_t> ev_pool;
 
   kkm_status start(int dev) {
     device = dev;
@@ -72,6 +179,7 @@ struct LoopExecutor {
     KKM_CK(cudaMalloc(&slots, sizeof(LoopItem) * kRoundMaxItems));
     KKM_CK(cudaHostAlloc(reinterpret_cast<void**>(&mirror), sizeof(LoopItem) * kMirror, cudaHostAllocDefault));
     for (auto& e : round_ev) KKM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g_row_tuner.load();
     th = std::thread([this] { loop(); });
     return KKM_OK;
   }
@@ -86,6 +194,10 @@ struct LoopExecutor {
       th.join();
     }
     if (st) cudaStreamSynchronize(st);
+    collect_samples();
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    g_row_tuner.save();
     for (auto& e : round_ev)
       if (e) cudaEventDestroy(e);
     if (slots) cudaFree(slots);
@@ -162,20 +274,36 @@ struct LoopExecutor {
       if (e != cudaSuccess) return e;
     }
     for (int nw = 1; nw <= 8; ++nw) {
+      int blocks = 0;
+      for (const Active& a : act)
+        if (a.r->item.nw == nw) blocks += a.r->item.assign_ctas;
+      if (blocks == 0) continue;
+      const long long key = RowTuner::key(nw, blocks);
+      bool timed = false;
+      const int RG = g_row_tuner.choose(key, &timed);
       RoundList L;
       L.cta_off[0] = 0;
       int smem = 0;
       for (const Active& a : act)
         if (a.r->item.nw == nw) {
           L.slot[L.n] = a.slot;
-          L.cta_off[L.n + 1] = L.cta_off[L.n] + a.r->item.assign_ctas;
+          L.cta_off[L.n + 1] = L.cta_off[L.n] + (a.r->item.assign_ctas + RG - 1) / RG;
           smem = std::max(smem, a.r->item.assign_smem);
           ++L.n;
         }
-      if (L.n == 0) continue;
+      Sample smp{key, RG, blocks, nullptr, nullptr};
+      if (timed) {
+        smp.a = take_event();
+        smp.b = take_event();
+        if (smp.a && smp.b) cudaEventRecord(smp.a, st);
+      }
       ProfScope ps("assign_multi", st);
-      const cudaError_t e = launch_assign_multi(slots, L, nw, smem, st);
+      const cudaError_t e = launch_assign_multi(slots, L, nw, smem, RG, st);
       if (e != cudaSuccess) return e;
+      if (timed && smp.a && smp.b) {
+        cudaEventRecord(smp.b, st);
+        samples.push_back(smp);
+      }
     }
     RoundList L;
     for (const Active& a : act) {
@@ -186,6 +314,37 @@ struct LoopExecutor {
     L.cta_off[L.n] = L.n;
     ProfScope ps("sort_multi", st);
     return launch_sort_multi(slots, L, st);
+  }
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  // timing samples whose launches have finished go to the tuner
+  void collect_samples() {
+    for (size_t q = 0; q < samples.size();) {
+      Sample& m = samples[q];
+      const cudaError_t e = cudaEventQuery(m.b);
+      if (e == cudaErrorNotReady) {
+        ++q;
+        continue;
+      }
+      float ms = 0.0f;
+      if (e == cudaSuccess && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess)
+        g_row_tuner.sample(m.key, m.rows, m.blocks, ms);
+      cudaGetLastError();
+      ev_pool.push_back(m.a);
+      ev_pool.push_back(m.b);
+      samples.erase(samples.begin() + (std::ptrdiff_t)q);
+    }
   }
   void loop() {
     cudaSetDevice(device);
@@ -236,6 +395,7 @@ struct LoopExecutor {
         continue;
       }
       if (rounds >= 2) cudaEventSynchronize(round_ev[(rounds - 2) & 3]);
+      if (!samples.empty()) collect_samples();
       cudaError_t e = round(act);
       if (e == cudaSuccess) e = cudaEventRecord(round_ev[rounds & 3], st);
       ++rounds;

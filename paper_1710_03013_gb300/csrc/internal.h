@@ -443,8 +443,11 @@ cudaError_t make_loop_item(const void* KT, bool half, int64_t ldk, int Ni, const
 // items of one launch have the same block type).
 cudaError_t launch_fhat_multi(const LoopItem* items, const RoundList& L, bool half, cudaStream_t st);
 // One assign (trace on) of every item in L; the items share nw and the
-// dynamic shared memory is the largest they need.
-cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, cudaStream_t st);
+// dynamic shared memory is the largest they need.  Each CTA takes RG blocks
+// of 32 rows of its item (cta_off counts ceil(row blocks / RG) per item); RG
+// changes no result.
+cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, int RG,
+                                cudaStream_t st);
 // The support sort of every listed item whose landmark labels changed in the
 // assign launches before it (their last CTAs leave it to this launch).
 cudaError_t launch_sort_multi(const LoopItem* items, const RoundList& L, cudaStream_t st);

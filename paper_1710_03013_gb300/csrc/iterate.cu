@@ -523,7 +523,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
                                             float* __restrict__ margin, float* __restrict__ dmin,
                                             float* __restrict__ fhat_out, double* __restrict__ ghat_out,
                                             int early_stop, int trace, const RescoreArgs& R, int bx, int G,
-                                            bool defer_sort = false) {
+                                            bool defer_sort = false, int RG = 1) {
   // dynamic shared memory (sized by the launch for this C): the distances of
   // the CTA's rows [C][kAssignRows], which the last CTA reuses as the support
   // sort's scratch, then the FP32 row of the slow re-score path [R.dp]
@@ -547,11 +547,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   if (I.done && *I.done) return;
   const int C = S.C;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int i = bx * kAssignRows + lane;
   const float inf = __int_as_float(0x7f800000);
-  const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
-  const int old_u = (w == 0 && i < Ni) ? u[i] : 0;
-  const int cord = (w == 0 && S.col_ord && i < Ni) ? S.col_ord[i] : -1;
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     sh.nj[j] = S.n_j[j];
     sh.su[j] = S.seg_unit[j];
@@ -569,6 +565,17 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   // loads are in flight together (C <= blockDim.x)
   const double gval =
       threadIdx.x < C && sh.nj[threadIdx.x] > 0 ? cluster_ghat(I, threadIdx.x, sh.nj[threadIdx.x]) : 0.0;
+  // Row blocks bx * RG ... bx * RG + RG - 1 of 32 rows each, one after the
+  // other: each gets exactly the work and the partial sums (omega_part[rb],
+  // ...) it would get in a CTA of its own, so RG changes no result.
+  const int G_rows = (Ni + kAssignRows - 1) / kAssignRows;
+  for (int rg = 0; rg < RG; ++rg) {
+  const int rb = bx * RG + rg;
+  if (rb >= G_rows) break;  // the same in every thread
+  const int i = rb * kAssignRows + lane;
+  const float ks = (kself && i < Ni) ? kself[i] : 1.0f;
+  const int old_u = (w == 0 && i < Ni) ? u[i] : 0;
+  const int cord = (w == 0 && S.col_ord && i < Ni) ? S.col_ord[i] : -1;
   // f_hat_ij of cluster j from its unit sum f (the units of j added in
   // order); NaN for an empty cluster
   auto finish = [&](int j, float f) {
@@ -615,7 +622,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
     sh.ghf[threadIdx.x] = (float)sh.gh[threadIdx.x];
   }
   __syncthreads();
-  if (bx == 0 && ghat_out)
+  if (rb == 0 && ghat_out)
     for (int j = threadIdx.x; j < C; j += blockDim.x) ghat_out[j] = sh.gh[j];
   // d_ij = K_ii - 2 f_hat_ij + g_hat_j for the warp's clusters (+inf when
   // n_j = 0 or past the last row)
@@ -694,7 +701,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
     // from the FP32 rows (16-byte loads; rows are padded to 8 floats)
     for (int p = w; p < n_cand; p += nw) {
       const int r = cand[p] >> 9, j = cand[p] & 511;
-      const int ir = bx * kAssignRows + r;
+      const int ir = rb * kAssignRows + r;
       const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
       const float ni = R.nXi[ir];
       const float ksr = kself ? kself[ir] : 1.0f;
@@ -729,7 +736,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
     // rows whose candidates did not fit the list: the whole CTA per row
     for (unsigned fm = slow_mask; fm; fm &= fm - 1) {  // the same sequence in every thread
       const int r = __ffs(fm) - 1;
-      const int ir = bx * kAssignRows + r;
+      const int ir = rb * kAssignRows + r;
       const float* xi = R.Xi + (int64_t)ir * R.dp;
       for (int c = threadIdx.x; c < R.dp; c += blockDim.x) xs[c] = xi[c];
       __syncthreads();
@@ -802,10 +809,12 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
     ch = warp_sum_i32(ch);
     lmc = warp_sum_i32(lmc);
     if (lane == 0) {
-      I.omega_part[bx] = om;
-      I.changed_part[bx] = ch;
-      if (I.lm_part) I.lm_part[bx] = lmc;
+      I.omega_part[rb] = om;
+      I.changed_part[rb] = ch;
+      if (I.lm_part) I.lm_part[rb] = lmc;
     }
+  }
+  __syncthreads();  // the next row block reuses the shared tiles
   }
   if (trace != 1) return;
   // The last CTA to finish (atomic ticket, no waiting) closes the iteration
@@ -822,7 +831,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   __threadfence();
   float2 o = make_float2(0.0f, 0.0f);
   int c = 0, lm = 0;
-  for (int b = threadIdx.x; b < G; b += blockDim.x) {
+  for (int b = threadIdx.x; b < G_rows; b += blockDim.x) {
     o = df_add(o, __ldcg(I.omega_part + b));
     c += __ldcg(I.changed_part + b);
     lm += I.lm_part ? __ldcg(I.lm_part + b) : 0;
@@ -930,14 +939,14 @@ fhat_partial_multi_kernel(const LoopItem* __restrict__ items, RoundList L) {
 }
 
 __global__ void __launch_bounds__(kAssignWarps * 32, 4)
-assign_multi_kernel(const LoopItem* __restrict__ items, RoundList L) {
+assign_multi_kernel(const LoopItem* __restrict__ items, RoundList L, int RG) {
   __shared__ __align__(16) unsigned char raw[sizeof(LoopItem)];
   griddep_wait();
   const int k = round_item_of(L, (int)blockIdx.x);
   const LoopItem& it = load_item(items, L.slot[k], raw);
   const int bx = (int)blockIdx.x - L.cta_off[k], G = L.cta_off[k + 1] - L.cta_off[k];
   assign_body(it.ldk, it.Ni, it.S, it.I, it.kself, it.u, nullptr, nullptr, nullptr, nullptr, it.early_stop,
-              /*trace=*/1, it.R, bx, G, /*defer_sort=*/true);
+              /*trace=*/1, it.R, bx, G, /*defer_sort=*/true, RG);
 }
 
 // The support sort of every listed item (one CTA of kSortThreads each) whose
@@ -1003,13 +1012,15 @@ cudaError_t launch_sort_multi(const LoopItem* items, const RoundList& L, cudaStr
   return launch_pdl(sort_multi_kernel, dim3((unsigned)L.n), dim3(kSortThreads), 0, st, items, L);
 }
 
-cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, cudaStream_t st) {
+cudaError_t launch_assign_multi(const LoopItem* items, const RoundList& L, int nw, int smem, int RG,
+                                cudaStream_t st) {
   if (L.n <= 0 || L.cta_off[L.n] <= 0) return cudaSuccess;
-  if (nw < 1 || nw > kAssignWarps || smem > kAssignMaxDynSmem) return cudaErrorInvalidValue;
+  if (nw < 1 || nw > kAssignWarps || smem > kAssignMaxDynSmem || RG < 1) return cudaErrorInvalidValue;
   static const cudaError_t attr = cudaFuncSetAttribute(assign_multi_kernel,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kAssignMaxDynSmem);
   if (attr != cudaSuccess) return attr;
-  return launch_pdl(assign_multi_kernel, dim3((unsigned)L.cta_off[L.n]), dim3(32 * nw), (size_t)smem, st, items, L);
+  return launch_pdl(assign_multi_kernel, dim3((unsigned)L.cta_off[L.n]), dim3(32 * nw), (size_t)smem, st, items, L,
+                    RG);
 }
 
 // ------------------------------------------------- fused inner loop

@@ -72,6 +72,39 @@ def test_batch_equals_solo_fits(lib, n_streams):
         _same_model((lab, model), solo)
 
 
+@pytest.mark.parametrize("rows", [2, 4, 8])
+def test_assign_rows_per_cta_change_nothing(lib, monkeypatch, rows):
+    """The work-list assign takes 1, 2, 4 or 8 blocks of 32 rows per CTA (the
+    row tuner's candidates, forced here): every result is bit-identical to
+    one block per CTA, on problems with C below and above the 8-warp CTA, a
+    ragged last block, early stop on and off, both block precisions."""
+    probs = _small_problems(10, seed=11)
+    probs.append(dict(X=blobs(3001, 8, 40, workload=3, problem=300)[0], C=40, B=2, s=0.5, iters=6, seed=3,
+                      precision=1, early_stop=False))
+    dev = [dict(p, X=_dev(p["X"])) for p in probs]
+    monkeypatch.setenv("KKM_ASSIGN_ROWS", "1")
+    ref = lib.kkm_fit_batch(dev, n_streams=6)
+    monkeypatch.setenv("KKM_ASSIGN_ROWS", str(rows))
+    got = lib.kkm_fit_batch(dev, n_streams=6)
+    for (la, ma, sa), (lb, mb, sb) in zip(ref, got):
+        assert sa == 0 and sb == 0
+        _same_model((la, ma), (lb, mb))
+
+
+def test_row_tuner_cache_file(lib, monkeypatch, tmp_path):
+    """With KKM_TUNE_CACHE set, the choices the tuner settles on are written as
+    'assign_rows <key> <rows>' lines, each a candidate."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("KKM_TUNE_CACHE", str(path))
+    monkeypatch.delenv("KKM_ASSIGN_ROWS", raising=False)
+    probs = [dict(p, X=_dev(p["X"])) for p in _small_problems(6, seed=12)]
+    for _ in range(3):  # enough launches for every key seen to settle
+        lib.kkm_fit_batch([dict(p, iters=20) for p in probs], n_streams=4)
+    assert path.exists()
+    lines = [ln.split() for ln in path.read_text().splitlines() if ln.strip()]
+    assert lines and all(ln[0] == "assign_rows" and int(ln[2]) in (1, 2, 4, 8) for ln in lines)
+
+
 def test_batch_against_oracle(lib):
     """FP32 problems of the batch against the oracle (labels above the margin,
     the Omega trace at 1e-6, medoids identical)."""

@@ -196,11 +196,21 @@ def test_bf16_step_full_minibatch(lib, mnist):
     assert (g["Ni"], g["nL"], g["landmarks_sum"]) == (len(gidx), len(L), int(L.sum()))
     Xb = X[gidx]
     u = cls[gidx].astype(np.int32)
-    got = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16)
+    got = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16, iteration="split")
     fused = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16, iteration="fused")
     for key in ("u", "n"):
         assert np.array_equal(fused[key], got[key]), key
     assert abs(fused["omega"] - got["omega"]) <= 1e-6 * got["omega"]
+    # the tensor-core loop the benchmark times (same block, f_hat summed on the
+    # tensor cores in another order): the oracle's labels wherever its margin
+    # is clear, the counts exactly, Omega and f_hat as the split form's
+    tc = lib.kkm_debug_step(Xb, L, u, C, "rbf", sigma, precision=lib.KKM_BF16, iteration="tc")
+    assert np.array_equal(tc["n"], got["n"])
+    bad_tc = np.nonzero((tc["u"] != g["u"]) & g["clear"])[0]
+    assert bad_tc.size == 0, f"{bad_tc.size} clear rows differ from the oracle (tensor-core loop)"
+    assert abs(tc["omega"] - got["omega"]) <= 1e-6 * got["omega"]
+    live_n = got["n"] > 0
+    assert float(np.max(np.abs(tc["fhat"][:, live_n] - got["fhat"][:, live_n]))) <= 2e-6
     assert np.array_equal(got["n"], g["n"])
     bad = np.nonzero((got["u"] != g["u"]) & g["clear"])[0]
     assert bad.size == 0, f"{bad.size} clear rows differ from the oracle, first {bad[:10]}"

@@ -458,6 +458,41 @@ __global__ void gather_raw_rows_kernel(const float* __restrict__ X, int64_t d, c
     out[t] = X[ids[r] * d + (t - r * d)];
   }
 }
+// Resets a mini-batch's loop state in one launch: the landmark column maps
+// (col_label, col_ord = -1 over ldk columns), the early-stop flag, the
+// fixed-point g_hat numerators, the Eq. 10 keys and member counts (each
+// nullable).
+__global__ void loop_reset_kernel(int32_t* col_label, int32_t* col_ord, int64_t ldk, int32_t* done,
+                                  unsigned long long* gfix, unsigned long long* keys, int32_t* cnt, int C) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ldk) {
+    col_label[t] = -1;
+    col_ord[t] = -1;
+  }
+  if (t < C) {
+    if (gfix) gfix[t] = 0ull;
+    if (keys) keys[t] = ~0ull;
+    if (cnt) cnt[t] = 0;
+  }
+  if (t == 0 && done) *done = 0;
+}
+// Up to kCopyMax device-to-device copies in one launch (blockIdx.y = copy;
+// 4-byte words; every size a multiple of 4 bytes, every address 4-byte
+// aligned).
+constexpr int kCopyMax = 16;
+struct CopyList {
+  int n = 0;
+  const void* src[kCopyMax];
+  void* dst[kCopyMax];
+  int64_t words[kCopyMax];
+};
+__global__ void copy_many_kernel(CopyList L) {
+  const int q = blockIdx.y;
+  const uint32_t* __restrict__ s = static_cast<const uint32_t*>(L.src[q]);
+  uint32_t* __restrict__ d = static_cast<uint32_t*>(L.dst[q]);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < L.words[q]; t += (int64_t)gridDim.x * blockDim.x)
+    d[t] = s[t];
+}
 __global__ void clamp_idx_kernel(const int32_t* in, int n, int32_t* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = in[i] >= 0 ? in[i] : 0;
@@ -633,12 +668,15 @@ static kkm_status rmsd_block_tc(const KernelSpec& sp, const float* A, const floa
 // given scratch.  out[n*ldo + m] = K(P_n, Q_m).
 // L (nullable): local sample positions of the reference rows; their diagonal
 // entries are then set to exactly 1 (Gaussian kernels).
+// converted: Pb/Qb and their norms already hold the rounded rows.
 static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const int32_t* L, int64_t nP,
                                     const float* Q, int64_t nQ, void* out, bool out_half, int64_t ldo,
                                     __nv_bfloat16* Pb, float* nPb, __nv_bfloat16* Qb, float* nQb, int* err,
-                                    cudaStream_t st, int n_sms = 0) {
-  KKM_RUN("to_bf16", st, launch_to_bf16(P, nP, sp.dp, Pb, nPb, st));
-  KKM_RUN("to_bf16", st, launch_to_bf16(Q, nQ, sp.dp, Qb, nQb, st));
+                                    cudaStream_t st, int n_sms = 0, bool converted = false) {
+  if (!converted) {
+    KKM_RUN("to_bf16", st, launch_to_bf16(P, nP, sp.dp, Pb, nPb, st));
+    KKM_RUN("to_bf16", st, launch_to_bf16(Q, nQ, sp.dp, Qb, nQb, st));
+  }
   const int dk = (int)sp.d;
   KKM_RUN("gram_block", st,
           launch_gram_tc(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, Pb, nP, Qb, nQ, dk, sp.dp, nPb, nQb,
@@ -652,10 +690,13 @@ static kkm_status kernel_block_bf16(const KernelSpec& sp, const float* P, const 
 // given scratch.
 static kkm_status kernel_block_fp8(const KernelSpec& sp, const float* P, const int32_t* L, int64_t nP, const float* Q,
                                    int64_t nQ, void* out, bool out_half, int64_t ldo, uint8_t* P8, float* sP,
-                                   float* nP8, uint8_t* Q8, float* sQ, float* nQ8, int* err, cudaStream_t st) {
+                                   float* nP8, uint8_t* Q8, float* sQ, float* nQ8, int* err, cudaStream_t st,
+                                   bool converted = false) {
   const int ld8 = (int)round_up(sp.dp, 16);
-  KKM_RUN("to_fp8", st, launch_to_fp8(P, nP, sp.dp, ld8, P8, sP, nP8, st));
-  KKM_RUN("to_fp8", st, launch_to_fp8(Q, nQ, sp.dp, ld8, Q8, sQ, nQ8, st));
+  if (!converted) {
+    KKM_RUN("to_fp8", st, launch_to_fp8(P, nP, sp.dp, ld8, P8, sP, nP8, st));
+    KKM_RUN("to_fp8", st, launch_to_fp8(Q, nQ, sp.dp, ld8, Q8, sQ, nQ8, st));
+  }
   KKM_RUN("gram_block", st,
           launch_gram_tc_fp8(sp.kind == KKM_LINEAR ? DK_LINEAR : DK_RBF, P8, nP, Q8, nQ, (int)sp.d, ld8, nP8, nQ8, sP,
                              sQ, sp.neg_scale(), out, out_half, ldo, err, sm_count(), st));
@@ -943,18 +984,37 @@ struct BlockMode {
 // buffer set b (its Xi, XL, ids filled) into b.KT or b.KTh.
 // n_sms > 0 limits the tensor-core block to that many CTAs (SMs), e.g. those
 // a concurrent one-launch inner loop leaves free.
+// The reduced-precision copies of a mini-batch's rows and landmark rows
+// that the tensor-core block reads (none for the FP32 Gram kernels); they do
+// not depend on the bandwidth.
+static kkm_status block_convert(const KernelSpec& sp, const BlockMode& bm, const BlockBufs& b, int nL, int Ni,
+                                cudaStream_t bs) {
+  if (bm.fp32_half_block) return KKM_OK;
+  if (sp.precision == KKM_BF16) {
+    KKM_RUN("to_bf16", bs, launch_to_bf16(b.XL, nL, sp.dp, b.XLb, b.nXLb, bs));
+    KKM_RUN("to_bf16", bs, launch_to_bf16(b.Xi, Ni, sp.dp, b.Xib, b.nXib, bs));
+  } else if (sp.precision == KKM_FP8) {
+    const int ld8 = (int)round_up(sp.dp, 16);
+    KKM_RUN("to_fp8", bs, launch_to_fp8(b.XL, nL, sp.dp, ld8, b.XL8, b.sXL, b.nXLb, bs));
+    KKM_RUN("to_fp8", bs, launch_to_fp8(b.Xi, Ni, sp.dp, ld8, b.Xi8, b.sXi, b.nXib, bs));
+  }
+  return KKM_OK;
+}
+
+// converted: block_convert has run for these buffers.
 static kkm_status block_kernel(const KernelSpec& sp, const BlockMode& bm, const BlockBufs& b, const int32_t* Ld,
-                               int nL, int Ni, int64_t ldk, int* tc_err, cudaStream_t bs, int n_sms = 0) {
+                               int nL, int Ni, int64_t ldk, int* tc_err, cudaStream_t bs, int n_sms = 0,
+                               bool converted = false) {
   if (bm.fp32_half_block)
     KKM_RUN("gram_block", bs,
             launch_gram_rbf_half(b.XL, nL, b.Xi, Ni, sp.dp, b.auxL, b.aux_i, b.gidL, b.gid, sp.neg_scale(), b.KTh,
                                  ldk, bs, b.KT));
   else if (sp.precision == KKM_BF16)
     KKM_TRY(kernel_block_bf16(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
-                              b.XLb, b.nXLb, b.Xib, b.nXib, tc_err, bs, n_sms));
+                              b.XLb, b.nXLb, b.Xib, b.nXib, tc_err, bs, n_sms, converted));
   else if (sp.precision == KKM_FP8)
     KKM_TRY(kernel_block_fp8(sp, b.XL, Ld, nL, b.Xi, Ni, bm.kt_half ? (void*)b.KTh : (void*)b.KT, bm.kt_half, ldk,
-                             b.XL8, b.sXL, b.nXLb, b.Xi8, b.sXi, b.nXib, tc_err, bs));
+                             b.XL8, b.sXL, b.nXLb, b.Xi8, b.sXi, b.nXib, tc_err, bs, converted));
   else
     KKM_TRY(kernel_block(sp, b.XL, b.auxL, b.gidL, nL, b.Xi, b.aux_i, b.gid, Ni, b.KT, ldk, bs, false, true,
                          bm.use_rtc ? &b.rtc : nullptr));
@@ -1432,6 +1492,40 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     }
   }
   const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+
+  // Alg. 1 line 3 for mini-batch i on stream `bs`, in two parts: its rows,
+  // landmark rows, ids and reduced-precision copies (no bandwidth needed),
+  // then the kernel block into the buffer set b.
+  auto block_rows = [&](int i, const BlockBufs& b, cudaStream_t bs) -> kkm_status {
+    const BatchGeom& g = geo[i];
+    const int Ni = (int)g.Ni;
+    const int nL = (int)(L_off[i + 1] - L_off[i]);
+    const int32_t* Ld = Ld_all + L_off[i];
+    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs));          // fetch X^i
+    KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
+    KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
+    KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
+    return block_convert(sp, bm, b, nL, Ni, bs);
+  };
+  auto block_gram = [&](int i, const BlockBufs& b, cudaStream_t bs, bool side) -> kkm_status {
+    const int Ni = (int)geo[i].Ni;
+    const int nL = (int)(L_off[i + 1] - L_off[i]);
+    return block_kernel(sp, bm, b, Ld_all + L_off[i], nL, Ni, ldk, tc_err, bs, side ? side_sms : 0,
+                        /*converted=*/true);
+  };
+  auto block_step = [&](int i, const BlockBufs& b, cudaStream_t bs, bool side) -> kkm_status {
+    KKM_TRY(block_rows(i, b, bs));
+    return block_gram(i, b, bs, side);
+  };
+
+  // ---- Algorithm 1
+  NvtxRange nv_fit("kkm_fit");
+  FitStreams fs;
+  KKM_TRY(fs.start(st, overlap));
+  const cudaStream_t ms = fs.main;
+  // the first mini-batch's rows need no bandwidth: they are gathered while
+  // the host waits for the finite check and the median rule
+  KKM_TRY(block_rows(start, bb[start % nbuf], overlap ? fs.side : ms));
   {
     bool bad = false;
     KKM_TRY(chk.wait(&bad));
@@ -1443,27 +1537,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaStreamSynchronize(st));  // at once when the check's wait already covered it
     sp.sigma = median_sigma_of(*sig_h);
   }
-
-  // Alg. 1 line 3 for mini-batch i on stream `bs`: its rows, landmark rows,
-  // ids and kernel block into the buffer set b.
-  auto block_step = [&](int i, const BlockBufs& b, cudaStream_t bs, bool side) -> kkm_status {
-    const BatchGeom& g = geo[i];
-    const int Ni = (int)g.Ni;
-    const int nL = (int)(L_off[i + 1] - L_off[i]);
-    const int32_t* Ld = Ld_all + L_off[i];
-    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs));          // fetch X^i
-    KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
-    KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
-    KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
-    return block_kernel(sp, bm, b, Ld, nL, Ni, ldk, tc_err, bs, side ? side_sms : 0);
-  };
-
-  // ---- Algorithm 1
-  NvtxRange nv_fit("kkm_fit");
-  FitStreams fs;
-  KKM_TRY(fs.start(st, overlap));
-  const cudaStream_t ms = fs.main;
-  if (overlap) KKM_TRY(block_step(start, bb[start % nbuf], fs.side, false));  // nothing to overlap yet
+  if (overlap) KKM_TRY(block_gram(start, bb[start % nbuf], fs.side, false));  // nothing to overlap yet
   for (int i = start; i < stop; ++i) {
     NvtxRange nv_batch("mini-batch");
     const BatchGeom& g = geo[i];
@@ -1480,6 +1554,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
         KKM_TRY(FitStreams::after(ms, fs.side));
         KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side, true));
       }
+    } else if (i == start) {
+      KKM_TRY(block_gram(i, bk, ms, false));  // its rows are gathered above
     } else {
       KKM_TRY(block_step(i, bk, ms, false));
     }
@@ -1500,12 +1576,14 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     // supports of the initial labels
     S.L = Ld;
     S.nL = nL;
-    KKM_RUN("fill", ms, launch_fill_i32(S.col_label, -1, ldk, ms));
-    KKM_RUN("fill", ms, launch_fill_i32(S.col_ord, -1, ldk, ms));
+    // column maps, early stop, g_hat numerators (the last mini-batch's medoid
+    // step read them), the Eq. 10 keys and counts
+    KKM_RUN("loop_reset", ms,
+            (loop_reset_kernel<<<blocks_for(std::max<int64_t>(ldk, C)), 256, 0, ms>>>(S.col_label, S.col_ord, ldk, I.done,
+                                                                                   I.gfix, keys, cnt, C),
+             cudaGetLastError()));
     KKM_RUN("landmark_maps", ms, launch_landmark_maps(S, u, ms));
     KKM_RUN("build_supports", ms, launch_build_supports(S, ms));
-    KKM_CK(cudaMemsetAsync(I.done, 0, 4, ms));
-    if (I.gfix) KKM_CK(cudaMemsetAsync(I.gfix, 0, (size_t)C * 8, ms));  // the last mini-batch's medoid step read them
     I.keep_rows = kt_half ? l2_keep_rows(ldk, nL, kL2KeepShareHalf, 2) : l2_keep_rows(ldk, nL, kL2KeepShare, 4);
     I.flag_tau = bm.flag_tau(sp);
     const RescoreArgs R = rescore_args(sp, bk, ldk);
@@ -1518,9 +1596,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
                            "column per thread of one CTA per SM)");
     NvtxRange nv_loop("inner loop");
     MedoidOut med;
-    if (form == kLoopTc) {  // the loop leaves the Eq. 10 keys itself
-      KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
-      KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
+    if (form == kLoopTc) {  // the loop leaves the Eq. 10 keys itself (reset above)
       med.keys = keys;
       med.cnt = cnt;
       med.ghat = ghat;
@@ -1536,20 +1612,16 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_RUN("fhat_partial", ms,
               kt_half ? launch_fhat_partial(bk.KTh, ldk, Ni, S, Ifin, ms)
                       : launch_fhat_partial(bk.KT, ldk, Ni, S, Ifin, ms));
-      KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
-      KKM_CK(cudaMemsetAsync(cnt, 0, (size_t)C * 4, ms));
       KKM_RUN("medoid_keys", ms, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, ms));
     }
-    KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms));
+    KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms, /*reset_keys=*/true));
     // Eq. 12: K(X^i, m^i) and the convex merge
     KKM_RUN("clamp_idx", ms, (clamp_idx_kernel<<<blocks_for(C), 256, 0, ms>>>(mi, C, mi_safe), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, ms));
     KKM_RUN("gather_ids", ms, (gather_i64_kernel<<<blocks_for(C), 256, 0, ms>>>(gid, mi, C, idMI), cudaGetLastError()));
     KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, ms));
-    KKM_RUN("fill", ms, launch_fill_u64(keys, ~0ull, C, ms));
     KKM_RUN("merge_keys", ms, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, ms));
-    KKM_CK(cudaMemcpyAsync(Mg_prev, Mg, (size_t)C * 8, cudaMemcpyDeviceToDevice, ms));
-    KKM_RUN("merge_apply", ms, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, ms));
+    KKM_RUN("merge_apply", ms, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, ms, Mg_prev));
     // how far the global medoids moved in this outer iteration (Fig. 4b):
     // K(old medoid rows MX, new medoid rows) and its diagonal
     KKM_TRY(prep_ids(sp, X, Mg, C, MXn, auxMn, ms));
@@ -1573,22 +1645,29 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       m->max_units = lb.max_units;
       KKM_TRY(model_alloc_device(m, ms));
       const int mu = m->max_units;
-      auto cp = [&](void* dst, const void* src, size_t bytes) -> kkm_status {
-        KKM_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ms));
-        return KKM_OK;
+      // the resident arrays, copied by one launch
+      CopyList cl;
+      auto cp = [&](void* dst, const void* src, size_t bytes) {
+        cl.src[cl.n] = src;
+        cl.dst[cl.n] = dst;
+        cl.words[cl.n] = (int64_t)(bytes / 4);
+        ++cl.n;
       };
-      KKM_TRY(cp(m->sup, bk.XL, (size_t)nL * sp.dp * 4));
-      KKM_TRY(cp(m->sup_aux, bk.auxL, (size_t)nL * 4));
-      KKM_TRY(cp(m->sup_ids, bk.gidL, (size_t)nL * 8));
-      KKM_TRY(cp(m->perm, S.perm, (size_t)nL * 4));
-      KKM_TRY(cp(m->seg_off, S.seg_off, (size_t)(C + 1) * 4));
-      KKM_TRY(cp(m->n_j, S.n_j, (size_t)C * 4));
-      KKM_TRY(cp(m->unit_j, S.unit_j, (size_t)mu * 4));
-      KKM_TRY(cp(m->unit_kb, S.unit_kb, (size_t)mu * 4));
-      KKM_TRY(cp(m->unit_ke, S.unit_ke, (size_t)mu * 4));
-      KKM_TRY(cp(m->seg_unit, S.seg_unit, (size_t)(C + 1) * 4));
-      KKM_TRY(cp(m->n_units, S.n_units, 4));
-      KKM_TRY(cp(m->ghat, ghat, (size_t)C * 8));
+      cp(m->sup, bk.XL, (size_t)nL * sp.dp * 4);
+      cp(m->sup_aux, bk.auxL, (size_t)nL * 4);
+      cp(m->sup_ids, bk.gidL, (size_t)nL * 8);
+      cp(m->perm, S.perm, (size_t)nL * 4);
+      cp(m->seg_off, S.seg_off, (size_t)(C + 1) * 4);
+      cp(m->n_j, S.n_j, (size_t)C * 4);
+      cp(m->unit_j, S.unit_j, (size_t)mu * 4);
+      cp(m->unit_kb, S.unit_kb, (size_t)mu * 4);
+      cp(m->unit_ke, S.unit_ke, (size_t)mu * 4);
+      cp(m->seg_unit, S.seg_unit, (size_t)(C + 1) * 4);
+      cp(m->n_units, S.n_units, 4);
+      cp(m->ghat, ghat, (size_t)C * 8);
+      KKM_RUN("copy_model", ms,
+              (copy_many_kernel<<<dim3(2 * (unsigned)sm_count(), (unsigned)cl.n), 256, 0, ms>>>(cl),
+               cudaGetLastError()));
       KKM_RUN("gather_labels", ms, (gather_i32_kernel<<<blocks_for(nL), 256, 0, ms>>>(u, Ld, nL, m->sup_labels), cudaGetLastError()));
       KKM_RUN("iota", ms, (iota32_kernel<<<blocks_for(nL), 256, 0, ms>>>(m->L_ident, nL), cudaGetLastError()));
       *model_out = guard.release();

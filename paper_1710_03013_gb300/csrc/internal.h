@@ -505,17 +505,19 @@ cudaError_t launch_nearest(const float* Kt, int64_t ldk, int Ni, int C, const fl
 cudaError_t launch_medoid_keys(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                                const float* kself, const int32_t* u, unsigned long long* keys,
                                int32_t* c, double* ghat_out, cudaStream_t st);
-// mi[j] = local index of the Eq. 10 medoid, or -1 when empty.
-cudaError_t launch_medoid_pick(const unsigned long long* keys, const int32_t* c,
-                               const int32_t* n_j, int C, int32_t* mi, cudaStream_t st);
+// mi[j] = local index of the Eq. 10 medoid, or -1 when empty; with
+// reset_keys the keys are left at ~0 (ready for the merge keys).
+cudaError_t launch_medoid_pick(unsigned long long* keys, const int32_t* c, const int32_t* n_j, int C, int32_t* mi,
+                               cudaStream_t st, bool reset_keys = false);
 // Eq. 12 keys.
 cudaError_t launch_merge_keys(const float* Kt, const float* Kmi, int64_t ldk, int Ni, int C,
                               const float* kself, const int32_t* mi, const int32_t* c,
                               const int64_t* W, unsigned long long* keys, cudaStream_t st);
-// Applies the merge: M[j] = start + l*step for non-empty j, W += c.
-cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi,
-                               const int32_t* c, int C, int64_t start, int64_t step,
-                               int64_t* M, int64_t* W, cudaStream_t st);
+// Applies the merge: M[j] = start + l*step for non-empty j, W += c; prev
+// (nullable) gets M before the update.
+cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi, const int32_t* c,
+                               int C, int64_t start, int64_t step, int64_t* M, int64_t* W,
+                               cudaStream_t st, int64_t* prev = nullptr);
 // Average centre displacement across one mini-batch (Section 4.1, Fig. 4b)
 // from K[a][b] = K(old_a, cur_b) (C x C, row pitch ldk) into *out (device).
 cudaError_t launch_displacement(const float* K, int64_t ldk, int C, const float* selfA, const float* selfB,

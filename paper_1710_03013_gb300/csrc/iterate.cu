@@ -1745,17 +1745,20 @@ cudaError_t launch_medoid_keys(int64_t ldk, int Ni, const Supports& S, const Ite
   return cudaGetLastError();
 }
 
-__global__ void medoid_pick_kernel(const unsigned long long* __restrict__ keys,
-                                   const int32_t* __restrict__ c, const int32_t* __restrict__ n_j,
-                                   int C, int32_t* __restrict__ mi) {
+// With reset, the key slot is left at ~0 for the next min-reduction (the
+// Eq. 12 merge keys).
+__global__ void medoid_pick_kernel(unsigned long long* __restrict__ keys, const int32_t* __restrict__ c,
+                                   const int32_t* __restrict__ n_j, int C, int32_t* __restrict__ mi, int reset) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= C) return;
-  mi[j] = (c[j] > 0 && n_j[j] > 0 && keys[j] != ~0ull) ? (int32_t)(keys[j] & 0xffffffffull) : -1;
+  const unsigned long long key = keys[j];
+  mi[j] = (c[j] > 0 && n_j[j] > 0 && key != ~0ull) ? (int32_t)(key & 0xffffffffull) : -1;
+  if (reset) keys[j] = ~0ull;
 }
 
-cudaError_t launch_medoid_pick(const unsigned long long* keys, const int32_t* c,
-                               const int32_t* n_j, int C, int32_t* mi, cudaStream_t st) {
-  medoid_pick_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, c, n_j, C, mi);
+cudaError_t launch_medoid_pick(unsigned long long* keys, const int32_t* c, const int32_t* n_j, int C, int32_t* mi,
+                               cudaStream_t st, bool reset_keys) {
+  medoid_pick_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, c, n_j, C, mi, reset_keys ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1794,12 +1797,15 @@ cudaError_t launch_merge_keys(const float* Kt, const float* Kmi, int64_t ldk, in
   return cudaGetLastError();
 }
 
+// prev (nullable) gets the medoids before the update.
 __global__ void merge_apply_kernel(const unsigned long long* __restrict__ keys,
                                    const int32_t* __restrict__ mi, const int32_t* __restrict__ c,
                                    int C, int64_t start, int64_t step, int64_t* __restrict__ M,
-                                   int64_t* __restrict__ W) {
+                                   int64_t* __restrict__ W, int64_t* __restrict__ prev) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= C || mi[j] < 0) return;
+  if (j >= C) return;
+  if (prev) prev[j] = M[j];
+  if (mi[j] < 0) return;
   const int64_t l = (int64_t)(keys[j] & 0xffffffffull);
   M[j] = start + l * step;
   W[j] += c[j];
@@ -1807,8 +1813,8 @@ __global__ void merge_apply_kernel(const unsigned long long* __restrict__ keys,
 
 cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi, const int32_t* c,
                                int C, int64_t start, int64_t step, int64_t* M, int64_t* W,
-                               cudaStream_t st) {
-  merge_apply_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, mi, c, C, start, step, M, W);
+                               cudaStream_t st, int64_t* prev) {
+  merge_apply_kernel<<<(unsigned)ceil_div(C, 256), 256, 0, st>>>(keys, mi, c, C, start, step, M, W, prev);
   return cudaGetLastError();
 }
 

@@ -1524,8 +1524,21 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(fs.start(st, overlap));
   const cudaStream_t ms = fs.main;
   // the first mini-batch's rows need no bandwidth: they are gathered while
-  // the host waits for the finite check and the median rule
+  // the host waits for the finite check and the median rule.  With the
+  // pipeline, k-means++ and the Eq. 8 labels of that mini-batch (which read
+  // its rows, not its block) then run beside its kernel block.
+  struct OwnedEvent {
+    cudaEvent_t e = nullptr;
+    ~OwnedEvent() {
+      if (e) cudaEventDestroy(e);
+    }
+  } rows_ready, block_ready;
   KKM_TRY(block_rows(start, bb[start % nbuf], overlap ? fs.side : ms));
+  if (overlap) {
+    KKM_CK(cudaEventCreateWithFlags(&rows_ready.e, cudaEventDisableTiming));
+    KKM_CK(cudaEventCreateWithFlags(&block_ready.e, cudaEventDisableTiming));
+    KKM_CK(cudaEventRecord(rows_ready.e, fs.side));
+  }
   {
     bool bad = false;
     KKM_TRY(chk.wait(&bad));
@@ -1537,7 +1550,10 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     KKM_CK(cudaStreamSynchronize(st));  // at once when the check's wait already covered it
     sp.sigma = median_sigma_of(*sig_h);
   }
-  if (overlap) KKM_TRY(block_gram(start, bb[start % nbuf], fs.side, false));  // nothing to overlap yet
+  if (overlap) {
+    KKM_TRY(block_gram(start, bb[start % nbuf], fs.side, false));  // no loop to overlap yet
+    KKM_CK(cudaEventRecord(block_ready.e, fs.side));
+  }
   for (int i = start; i < stop; ++i) {
     NvtxRange nv_batch("mini-batch");
     const BatchGeom& g = geo[i];
@@ -1546,10 +1562,12 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const int32_t* Ld = Ld_all + L_off[i];
     const BlockBufs& bk = bb[i % nbuf];
     if (overlap) {
-      // the block of mini-batch i is ready; the side stream then produces the
-      // next one into the other buffer set, whose last reader (mini-batch
+      // the block of mini-batch i is ready (the first one: its rows; the
+      // block is waited for before the loop); the side stream then produces
+      // the next one into the other buffer set, whose last reader (mini-batch
       // i - 1) is queued on the main stream before this point
-      KKM_TRY(FitStreams::after(fs.side, ms));
+      if (i == start) KKM_CK(cudaStreamWaitEvent(ms, rows_ready.e, 0));
+      else KKM_TRY(FitStreams::after(fs.side, ms));
       if (i + 1 < stop) {
         KKM_TRY(FitStreams::after(ms, fs.side));
         KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side, true));
@@ -1602,6 +1620,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       med.ghat = ghat;
       med.need_supports = i == B - 1 && model_out;  // the model keeps the final support structure
     }
+    if (overlap && i == start) KKM_CK(cudaStreamWaitEvent(ms, block_ready.e, 0));
     KKM_TRY(inner_loop(bm, bk, ldk, Ni, S, I, form, iters, kself, u, nullptr, nullptr, nullptr,  // Alg. 1 lines 9-16
                        opt.early_stop, R, ms, med));
     I.flag_tau = 0.0f;

@@ -139,7 +139,15 @@ void kkm_options_default(kkm_options* opt);
 
 /*
  * kkm_fit -- Algorithm 1 with the landmark approximation of Section 3.2.
- *   X        [N][d] float32 samples (device or host).
+ *   X        [N][d] float32 samples (device or host).  Device and pageable
+ *            host X are checked for NaN/Inf before any other work (host X is
+ *            copied first).  Pinned host X (16-byte aligned, d a multiple of
+ *            4, RBF or linear kernel) stays on the host: each mini-batch's
+ *            rows are fetched by the copy engine as the fit reaches them (the
+ *            next mini-batch's while the current one iterates) and checked
+ *            there; a NaN/Inf then gives KKM_EINVAL at the end of the fit with
+ *            no label or model written.  The host memory must stay unchanged
+ *            until the call returns.
  *   C        number of clusters, 1 <= C <= 256 and C <= every mini-batch size.
  *   B        number of mini-batches, 1 <= B <= N.
  *   s        landmark fraction of Eq. 18, 0 < s <= 1; per mini-batch

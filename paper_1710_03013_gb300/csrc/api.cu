@@ -388,11 +388,16 @@ struct PendingCheck {
 
 // With `pending`, the check is only enqueued (its flag lands in pinned host
 // memory) and pending->wait gives the answer; else this call waits for it.
+// With pull_flag (a caller that fetches every row of X through
+// prep_rows), pinned host X 16-byte aligned is used in place: *out is its
+// device address, nothing is copied or checked here, and *pull_flag is a
+// zeroed device word for the rows' check.
 static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n, const float** out, bool* bad,
-                                       PendingCheck* pending = nullptr) {
+                                       PendingCheck* pending = nullptr, int** pull_flag = nullptr) {
   cudaStream_t st = ws.st;
   *bad = false;
   *out = p;
+  if (pull_flag) *pull_flag = nullptr;
   if (n <= 0) return KKM_OK;
   int* flag;
   KKM_TRY(ws.alloc(&flag, 1));
@@ -400,6 +405,12 @@ static kkm_status device_input_checked(Workspace& ws, const float* p, int64_t n,
   cudaPointerAttributes a;
   const bool known = cudaPointerGetAttributes(&a, p) == cudaSuccess;
   if (!known) cudaGetLastError();
+  if (pull_flag && known && a.type == cudaMemoryTypeHost && a.devicePointer &&
+      (reinterpret_cast<uintptr_t>(a.devicePointer) & 15) == 0) {
+    *out = static_cast<const float*>(a.devicePointer);
+    *pull_flag = flag;
+    return KKM_OK;
+  }
   if (known && (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)) {
     KKM_RUN("check_finite", st, launch_check_finite(p, n, flag, st));
   } else {
@@ -538,9 +549,13 @@ static kkm_status make_spec(const kkm_kernel* k, int64_t d, KernelSpec* sp) {
 }
 
 // Prepared rows start + l*step of X (device) -> out [n][dp], aux [n].
+// pull_bad: X is pinned host memory read in place, *pull_bad set for a NaN or
+// Inf among the rows.
 static kkm_status prep_rows(const KernelSpec& sp, const float* X, int64_t start, int64_t step,
-                            int64_t n, float* out, float* aux, cudaStream_t st) {
-  if (sp.kind == KKM_RMSD)
+                            int64_t n, float* out, float* aux, cudaStream_t st, int* pull_bad = nullptr) {
+  if (pull_bad)
+    KKM_RUN("gather_rows", st, launch_gather_rows_pull(X, sp.d, start, step, n, out, sp.dp, aux, pull_bad, st));
+  else if (sp.kind == KKM_RMSD)
     KKM_RUN("rmsd_prep", st, launch_rmsd_prep_rows(X, sp.n_atoms, start, step, n, out, sp.ap, aux, st));
   else
     KKM_RUN("gather_rows", st, launch_gather_rows(X, sp.d, start, step, n, out, sp.dp, aux, st));
@@ -1338,12 +1353,59 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // ---- inputs on the device; the finite check (then the median rule) runs
   // while the host draws the random numbers and sets up the workspace, and
   // a fit whose X holds NaN or Inf returns before any step of Alg. 1
+  // Pinned host X of the RBF and linear kernels with rows of a multiple of 4
+  // floats stays on the host in a whole fit: each mini-batch's rows cross the
+  // link when they are gathered (the next mini-batch's during the current
+  // loop) and are checked there; the fit reports NaN or Inf at its end,
+  // writing no output.
   const float* X = nullptr;
   PendingCheck chk;
+  int* pull_bad = nullptr;
   {
     bool bad = false;
-    KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad, &chk));
+    // (a call over part of the mini-batches reads rows it does not gather:
+    // it checks all of X up front)
+    const bool may_pull = sp.kind != KKM_RMSD && d % 4 == 0 && start == 0 && stop == B;
+    KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad, &chk, may_pull ? &pull_bad : nullptr));
     if (bad) return invalid("X holds NaN or Inf");
+  }
+
+  // ---- block buffers and streams (Alg. 1 line 3 is the first device work
+  // of a fit whose X stays on the host: its first rows cross the link while
+  // the median rule runs and the host draws the landmarks)
+  const int64_t ldk = round_up(Nmax, 32);
+  // AUTO overlaps the next block with the inner loop when the loop is the
+  // tensor-core one, which holds one SM per 128 samples and leaves the rest
+  // to the block (measured 4 % faster on the MNIST-shaped fit)
+  const int first_nl = (int)n_landmarks(geo[0].Ni, s);
+  const bool tc_loop = opt.iteration == KKM_ITER_AUTO || opt.iteration == KKM_ITER_TC
+                           ? tc_applies(sp, BlockMode(sp, nLmax), (int)geo[0].Ni, first_nl, C)
+                           : false;
+  const bool overlap = fit_overlaps(opt.pipeline, B, sp.kind, sp.precision) ||
+                       (opt.pipeline == KKM_PIPE_AUTO && B >= 2 && tc_loop);
+  // the block of the next mini-batch takes the SMs the tensor-core loop leaves
+  const int side_sms = overlap && tc_loop ? std::max(16, sm_count() - (int)ceil_div(Nmax, 128)) : 0;
+  // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
+  // significand, finer than the BF16 inputs' rounding): the inner loop
+  // streams half the bytes.
+  const BlockMode bm(sp, nLmax);
+  const bool kt_half = bm.kt_half;
+  const bool use_rtc = bm.use_rtc;
+  // one set of block buffers, or two when the next mini-batch's block is
+  // computed while the current one iterates
+  BlockBufs bb[2];
+  const int nbuf = overlap ? 2 : 1;
+  for (int q = 0; q < nbuf; ++q)
+    KKM_TRY(alloc_block_bufs(ws, sp, Nmax, nLmax, ldk, kt_half, use_rtc, &bb[q], bm.fp32_half_block));
+  NvtxRange nv_fit("kkm_fit");
+  FitStreams fs;
+  KKM_TRY(fs.start(st, overlap));
+  const cudaStream_t ms = fs.main;
+  const bool first_fetched = pull_bad != nullptr;
+  if (first_fetched) {
+    const BatchGeom& g0 = geo[start];
+    const BlockBufs& b0 = bb[start % nbuf];
+    KKM_TRY(prep_rows(sp, X, g0.start, g0.step, g0.Ni, b0.Xi, b0.aux_i, overlap ? fs.side : ms, pull_bad));
   }
 
   // ---- random numbers (Section 3.1, 3.2): k-means++, bandwidth, landmarks
@@ -1386,19 +1448,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
 
 
   // ---- workspace
-  const int64_t ldk = round_up(Nmax, 32);
   const int trace_cap = B * iters;
-  // AUTO overlaps the next block with the inner loop when the loop is the
-  // tensor-core one, which holds one SM per 128 samples and leaves the rest
-  // to the block (measured 4 % faster on the MNIST-shaped fit)
-  const int first_nl = (int)(L_off[1] - L_off[0]);
-  const bool tc_loop = opt.iteration == KKM_ITER_AUTO || opt.iteration == KKM_ITER_TC
-                           ? tc_applies(sp, BlockMode(sp, nLmax), (int)geo[0].Ni, first_nl, C)
-                           : false;
-  const bool overlap = fit_overlaps(opt.pipeline, B, sp.kind, sp.precision) ||
-                       (opt.pipeline == KKM_PIPE_AUTO && B >= 2 && tc_loop);
-  // the block of the next mini-batch takes the SMs the tensor-core loop leaves
-  const int side_sms = overlap && tc_loop ? std::max(16, sm_count() - (int)ceil_div(Nmax, 128)) : 0;
   float *Kt, *Kmi, *MX, *auxM, *MIX, *auxMI, *rowbuf, *rowaux, *kcol, *MXn, *auxMn, *Kmn;
   int64_t *Mg, *W, *idMI, *Mg_prev;
   double* disp;
@@ -1406,18 +1456,6 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   unsigned long long* keys;
   double *ghat, *D2 = nullptr, *draws_d = nullptr;
   uint32_t* kpp_ticket = nullptr;
-  // The BF16 path keeps a Gaussian block in FP16 (values in [0, 1], 11-bit
-  // significand, finer than the BF16 inputs' rounding): the inner loop
-  // streams half the bytes.
-  const BlockMode bm(sp, nLmax);
-  const bool kt_half = bm.kt_half;
-  const bool use_rtc = bm.use_rtc;
-  // one set of block buffers, or two when the next mini-batch's block is
-  // computed while the current one iterates
-  BlockBufs bb[2];
-  const int nbuf = overlap ? 2 : 1;
-  for (int q = 0; q < nbuf; ++q)
-    KKM_TRY(alloc_block_bufs(ws, sp, Nmax, nLmax, ldk, kt_half, use_rtc, &bb[q], bm.fp32_half_block));
   KKM_TRY(ws.alloc(&Kt, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&Kmi, (int64_t)C * ldk));
   KKM_TRY(ws.alloc(&MX, (int64_t)C * sp.dp));
@@ -1501,7 +1539,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const int Ni = (int)g.Ni;
     const int nL = (int)(L_off[i + 1] - L_off[i]);
     const int32_t* Ld = Ld_all + L_off[i];
-    KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs));          // fetch X^i
+    if (!(first_fetched && i == start))
+      KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs, pull_bad));  // fetch X^i
     KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
     KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));
@@ -1519,10 +1558,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   };
 
   // ---- Algorithm 1
-  NvtxRange nv_fit("kkm_fit");
-  FitStreams fs;
-  KKM_TRY(fs.start(st, overlap));
-  const cudaStream_t ms = fs.main;
+  // both streams after the uploads and fills of the workspace on st
+  KKM_TRY(FitStreams::after(st, ms));
+  KKM_TRY(FitStreams::after(st, fs.side));
   // the first mini-batch's rows need no bandwidth: they are gathered while
   // the host waits for the finite check and the median rule.  With the
   // pipeline, k-means++ and the Eq. 8 labels of that mini-batch (which read
@@ -1563,15 +1601,9 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const BlockBufs& bk = bb[i % nbuf];
     if (overlap) {
       // the block of mini-batch i is ready (the first one: its rows; the
-      // block is waited for before the loop); the side stream then produces
-      // the next one into the other buffer set, whose last reader (mini-batch
-      // i - 1) is queued on the main stream before this point
+      // block is waited for before the loop)
       if (i == start) KKM_CK(cudaStreamWaitEvent(ms, rows_ready.e, 0));
       else KKM_TRY(FitStreams::after(fs.side, ms));
-      if (i + 1 < stop) {
-        KKM_TRY(FitStreams::after(ms, fs.side));
-        KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side, true));
-      }
     } else if (i == start) {
       KKM_TRY(block_gram(i, bk, ms, false));  // its rows are gathered above
     } else {
@@ -1585,6 +1617,15 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(kmeanspp_dev(sp, Xi, aux_i, Ni, C, kself, rowbuf, rowaux, kcol, ldk, D2, picks, draws_d, kpp_ticket,
                            ms));
       KKM_RUN("local_to_global", ms, launch_local_to_global(picks, C, g.start, g.step, Mg, ms));
+    }
+    // the side stream produces the next block into the other buffer set,
+    // whose last reader (mini-batch i - 1) is queued on the main stream
+    // before this point; in the first mini-batch only after k-means++, whose
+    // rounds re-read X^i from L2 (a fetch of the next rows beside them, from
+    // host memory in particular, would push X^i out)
+    if (overlap && i + 1 < stop) {
+      KKM_TRY(FitStreams::after(ms, fs.side));
+      KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side, true));
     }
     // Eq. 8: auxiliary block K~ = K(M, X^i) and nearest-medoid labels
     KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, ms));
@@ -1696,6 +1737,19 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   KKM_TRY(fs.join());
 
   // ---- results: every read-back through one pinned stage, one wait
+  if (pull_bad) {  // the rows' finite check, before any output is written
+    int h = 0;
+    KKM_CK(cudaMemcpyAsync(sig_h, pull_bad, 4, cudaMemcpyDeviceToHost, st));
+    KKM_CK(cudaStreamSynchronize(st));
+    memcpy(&h, sig_h, 4);
+    if (h) {
+      if (model_out && *model_out) {
+        delete *model_out;
+        *model_out = nullptr;
+      }
+      return invalid("X holds NaN or Inf");
+    }
+  }
   kkm_model* const mres = model_out ? *model_out : nullptr;
   const int32_t tcap = std::max(trace_cap, 1);
   int32_t tc = 0;

@@ -194,6 +194,55 @@ cudaError_t launch_copy_check(const float* src, float* dst, int64_t n, int* flag
   return cudaGetLastError();
 }
 
+// Rows start + l*step of pinned host memory, fetched by the copy engine (a
+// strided 2-D copy into rows of dp floats), then one pass over the fetched
+// rows: the padding columns zeroed, the squared norms (the arithmetic of
+// gather_rows4_kernel, so the rows are those of a device-memory gather bit
+// for bit) and *bad set when a value is NaN or Inf.  A fit whose X stays on
+// the host so checks every row as its mini-batch is fetched, and the fetch of
+// the next mini-batch crosses the link while the current one iterates; the
+// copy engine leaves the SMs (and their memory pipes) to the loop beside it.
+__global__ void rows_norm_check_kernel(float4* __restrict__ rows, int64_t d4, int dp4, int64_t n,
+                                       float* __restrict__ normsq, int* __restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  float4* r = rows + row * (int64_t)dp4;
+  float2 acc = make_float2(0.0f, 0.0f);
+  int nonfinite = 0;
+  for (int c0 = 0; c0 < dp4; c0 += 32 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = c0 + t * 32 + lane;
+      v[t] = c < d4 ? r[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = c0 + t * 32 + lane;
+      if (c < dp4) {
+        if (c >= d4) r[c] = v[t];
+        nonfinite |= !isfinite(v[t].x) | !isfinite(v[t].y) | !isfinite(v[t].z) | !isfinite(v[t].w);
+        acc = df_add_sq(df_add_sq(df_add_sq(df_add_sq(acc, v[t].x), v[t].y), v[t].z), v[t].w);
+      }
+    }
+  }
+  acc = warp_sum_df(acc);
+  if (normsq && lane == 0) normsq[row] = df_to_float(acc);
+  if (__any_sync(kFull, nonfinite) && lane == 0) atomicOr(bad, 1);
+}
+cudaError_t launch_gather_rows_pull(const float* X, int64_t d, int64_t start, int64_t step, int64_t n, float* out,
+                                    int dp, float* normsq, int* bad, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (d % 4 != 0 || dp % 4 != 0 || !aligned16(X) || !aligned16(out)) return cudaErrorInvalidValue;
+  const cudaError_t e = cudaMemcpy2DAsync(out, (size_t)dp * 4, X + start * d, (size_t)(step * d) * 4, (size_t)d * 4,
+                                          (size_t)n, cudaMemcpyDefault, st);
+  if (e != cudaSuccess) return e;
+  rows_norm_check_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(reinterpret_cast<float4*>(out), d / 4, dp / 4, n,
+                                                                   normsq, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const float* X, int64_t n, int* flag, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   int grid = (int)std::min<int64_t>(ceil_div(n, 256), 152 * 8);

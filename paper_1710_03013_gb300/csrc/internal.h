@@ -192,6 +192,11 @@ enum DevKind { DK_RBF = 0, DK_LINEAR = 1, DK_DIST = 2, DK_RMSD_EST = 3, DK_RAW =
 // with FP64-accumulated squared norms (normsq nullable).
 cudaError_t launch_gather_rows(const float* X, int64_t d, int64_t start, int64_t step,
                                int64_t n, float* out, int dp, float* normsq, cudaStream_t st);
+// The same rows from pinned host memory (X its device address; d and dp
+// multiples of 4, both 16-byte aligned), fetched by the copy engine, *bad set
+// when a value is NaN or Inf.
+cudaError_t launch_gather_rows_pull(const float* X, int64_t d, int64_t start, int64_t step, int64_t n, float* out,
+                                    int dp, float* normsq, int* bad, cudaStream_t st);
 // Rows X[idx[l]] (device indices, int64 or int32) copied like above.
 cudaError_t launch_gather_idx64(const float* X, int64_t d, const int64_t* idx, int64_t n,
                                 float* out, int dp, float* normsq, cudaStream_t st);

@@ -327,6 +327,38 @@ def test_fit_pinned_host_input(lib):
     assert "NaN" in str(e.value)
 
 
+@pytest.mark.parametrize("prec,pipeline", [("fp32", "auto"), ("fp32", "serial"), ("bf16", "auto"), ("bf16", "overlap")])
+def test_fit_pinned_host_input_in_place(lib, prec, pipeline):
+    """Pinned host input whose rows are a multiple of 4 floats stays on the
+    host in a whole fit: each mini-batch's rows are read over the link as they
+    are gathered (and checked there), the medoid and sample rows likewise.
+    Every result is the bits of the device-input fit; a NaN in the last row
+    (the last mini-batch to be fetched) is refused with no model."""
+    import torch
+    X, _ = blobs(3003, 16, 5, workload=63, problem=2)
+    sig = _median_sigma(X)
+    p = lib.KKM_BF16 if prec == "bf16" else lib.KKM_FP32
+    kw = dict(iters=8, seed=8, precision=p, pipeline=pipeline)
+    lab_d, m_d = lib.kkm_fit(_dev(X), 5, 3, 0.3, "rbf", 0.0, **kw)
+    Xp = torch.from_numpy(X).pin_memory()
+    assert Xp.data_ptr() % 16 == 0
+    lab_h, m_h = lib.kkm_fit(Xp, 5, 3, 0.3, "rbf", 0.0, **kw)
+    assert np.array_equal(_np(lab_d), _np(lab_h))
+    assert np.array_equal(m_d.trace()[0], m_h.trace()[0]) and np.array_equal(m_d.trace()[1], m_h.trace()[1])
+    for a, b in zip(m_d.medoids(), m_h.medoids()):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    for a, b in zip(m_d.supports(), m_h.supports()):
+        assert np.array_equal(np.asarray(a), np.asarray(b), equal_nan=True)
+    bad = Xp.clone().pin_memory()
+    bad[3002, 15] = float("nan")
+    with pytest.raises(lib.KKMError) as e:
+        lib.kkm_fit(bad, 5, 3, 0.3, "rbf", sig, **kw)
+    assert "NaN" in str(e.value)
+    bad[3002, 15] = float("inf")
+    with pytest.raises(lib.KKMError):
+        lib.kkm_fit(bad, 5, 3, 0.3, "rbf", sig, **kw)
+
+
 def test_fit_deterministic(lib):
     X, _ = blobs(5000, 32, 6, workload=64)
     sig = _median_sigma(X)

@@ -549,11 +549,19 @@ static kkm_status make_spec(const kkm_kernel* k, int64_t d, KernelSpec* sp) {
 }
 
 // Prepared rows start + l*step of X (device) -> out [n][dp], aux [n].
-// pull_bad: X is pinned host memory read in place, *pull_bad set for a NaN or
-// Inf among the rows.
+// pull_bad: X is pinned host memory fetched by the copy engine, *pull_bad set
+// for a NaN or Inf among the rows; MD frames go through `stage` ([n][d]
+// floats) and are prepared from there.
 static kkm_status prep_rows(const KernelSpec& sp, const float* X, int64_t start, int64_t step,
-                            int64_t n, float* out, float* aux, cudaStream_t st, int* pull_bad = nullptr) {
-  if (pull_bad)
+                            int64_t n, float* out, float* aux, cudaStream_t st, int* pull_bad = nullptr,
+                            float* stage = nullptr) {
+  if (pull_bad && sp.kind == KKM_RMSD) {
+    if (n <= 0) return KKM_OK;
+    KKM_CK(cudaMemcpy2DAsync(stage, (size_t)sp.d * 4, X + start * sp.d, (size_t)(step * sp.d) * 4, (size_t)sp.d * 4,
+                             (size_t)n, cudaMemcpyDefault, st));
+    KKM_RUN("check_finite", st, launch_check_finite(stage, n * sp.d, pull_bad, st));
+    KKM_RUN("rmsd_prep", st, launch_rmsd_prep_rows(stage, sp.n_atoms, 0, 1, n, out, sp.ap, aux, st));
+  } else if (pull_bad)
     KKM_RUN("gather_rows", st, launch_gather_rows_pull(X, sp.d, start, step, n, out, sp.dp, aux, pull_bad, st));
   else if (sp.kind == KKM_RMSD)
     KKM_RUN("rmsd_prep", st, launch_rmsd_prep_rows(X, sp.n_atoms, start, step, n, out, sp.ap, aux, st));
@@ -1353,11 +1361,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   // ---- inputs on the device; the finite check (then the median rule) runs
   // while the host draws the random numbers and sets up the workspace, and
   // a fit whose X holds NaN or Inf returns before any step of Alg. 1
-  // Pinned host X of the RBF and linear kernels with rows of a multiple of 4
-  // floats stays on the host in a whole fit: each mini-batch's rows cross the
-  // link when they are gathered (the next mini-batch's during the current
-  // loop) and are checked there; the fit reports NaN or Inf at its end,
-  // writing no output.
+  // Pinned host X (feature rows of a multiple of 4 floats, or MD frames)
+  // stays on the host in a whole fit: each mini-batch's rows cross the link
+  // when they are gathered (the next mini-batch's during the current loop)
+  // and are checked there; the fit reports NaN or Inf at its end, writing no
+  // output.
   const float* X = nullptr;
   PendingCheck chk;
   int* pull_bad = nullptr;
@@ -1365,7 +1373,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     bool bad = false;
     // (a call over part of the mini-batches reads rows it does not gather:
     // it checks all of X up front)
-    const bool may_pull = sp.kind != KKM_RMSD && d % 4 == 0 && start == 0 && stop == B;
+    const bool may_pull = (sp.kind == KKM_RMSD || d % 4 == 0) && start == 0 && stop == B;
     KKM_TRY(device_input_checked(ws, X_in, N * d, &X, &bad, &chk, may_pull ? &pull_bad : nullptr));
     if (bad) return invalid("X holds NaN or Inf");
   }
@@ -1401,11 +1409,16 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   FitStreams fs;
   KKM_TRY(fs.start(st, overlap));
   const cudaStream_t ms = fs.main;
+  // MD frames fetched from the host are staged, then prepared (one stream
+  // fetches at a time: the side stream, or the main one without the pipeline)
+  float* pull_stage = nullptr;
+  if (pull_bad && sp.kind == KKM_RMSD) KKM_TRY(ws.alloc(&pull_stage, Nmax * d));
   const bool first_fetched = pull_bad != nullptr;
   if (first_fetched) {
     const BatchGeom& g0 = geo[start];
     const BlockBufs& b0 = bb[start % nbuf];
-    KKM_TRY(prep_rows(sp, X, g0.start, g0.step, g0.Ni, b0.Xi, b0.aux_i, overlap ? fs.side : ms, pull_bad));
+    KKM_TRY(prep_rows(sp, X, g0.start, g0.step, g0.Ni, b0.Xi, b0.aux_i, overlap ? fs.side : ms, pull_bad,
+                      pull_stage));
   }
 
   // ---- random numbers (Section 3.1, 3.2): k-means++, bandwidth, landmarks
@@ -1540,7 +1553,7 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
     const int nL = (int)(L_off[i + 1] - L_off[i]);
     const int32_t* Ld = Ld_all + L_off[i];
     if (!(first_fetched && i == start))
-      KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs, pull_bad));  // fetch X^i
+      KKM_TRY(prep_rows(sp, X, g.start, g.step, Ni, b.Xi, b.aux_i, bs, pull_bad, pull_stage));  // fetch X^i
     KKM_RUN("iota", bs, (iota64_kernel<<<blocks_for(Ni), 256, 0, bs>>>(b.gid, g.start, g.step, Ni), cudaGetLastError()));
     KKM_TRY(copy_prepared(sp, b.Xi, Ld, nL, b.XL, b.auxL, bs));                 // landmarks
     KKM_RUN("gather_ids", bs, (gather_i64_kernel<<<blocks_for(nL), 256, 0, bs>>>(b.gid, Ld, nL, b.gidL), cudaGetLastError()));

@@ -359,6 +359,31 @@ def test_fit_pinned_host_input_in_place(lib, prec, pipeline):
         lib.kkm_fit(bad, 5, 3, 0.3, "rbf", sig, **kw)
 
 
+@pytest.mark.parametrize("n_atoms", [20, 21])
+def test_fit_pinned_host_md_frames_in_place(lib, n_atoms):
+    """Pinned host MD frames stay on the host in a whole fit: each
+    mini-batch's frames are staged by the copy engine, checked and prepared
+    from the staging buffer.  Every result is the bits of the device-input
+    fit (frames of 60 and 63 floats); a NaN in the last frame is refused."""
+    import torch
+    from synth import md_trajectory
+    F, _ = md_trajectory(2400, n_atoms, dwell=50.0, workload=63, problem=3)
+    X = np.ascontiguousarray(F.reshape(2400, -1).astype(np.float32))
+    kw = dict(iters=5, seed=4, pipeline="overlap")
+    lab_d, m_d = lib.kkm_fit(_dev(X), 4, 3, 0.2, "rmsd", 1.5, n_atoms, **kw)
+    Xp = torch.from_numpy(X).pin_memory()
+    lab_h, m_h = lib.kkm_fit(Xp, 4, 3, 0.2, "rmsd", 1.5, n_atoms, **kw)
+    assert np.array_equal(_np(lab_d), _np(lab_h))
+    assert np.array_equal(m_d.trace()[0], m_h.trace()[0])
+    for a, b in zip(m_d.medoids(), m_h.medoids()):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    bad = Xp.clone().pin_memory()
+    bad[2399, 0] = float("nan")
+    with pytest.raises(lib.KKMError) as e:
+        lib.kkm_fit(bad, 4, 3, 0.2, "rmsd", 1.5, n_atoms, **kw)
+    assert "NaN" in str(e.value)
+
+
 def test_fit_deterministic(lib):
     X, _ = blobs(5000, 32, 6, workload=64)
     sig = _median_sigma(X)

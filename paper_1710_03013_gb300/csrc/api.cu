@@ -1542,7 +1542,11 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       labels_dev = labels_out;
     }
   }
-  const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+  // Feature kernels carry the medoid rows from one mini-batch to the next
+  // (the rows after the merge are rows of the mini-batch just done); MD
+  // frames are prepared again from X.
+  const bool rows_carried = sp.kind != KKM_RMSD;
+  bool mx_ready = false;  // MX/auxM hold the rows of Mg
 
   // Alg. 1 line 3 for mini-batch i on stream `bs`, in two parts: its rows,
   // landmark rows, ids and reduced-precision copies (no bandwidth needed),
@@ -1641,7 +1645,8 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
       KKM_TRY(block_step(i + 1, bb[(i + 1) % nbuf], fs.side, true));
     }
     // Eq. 8: auxiliary block K~ = K(M, X^i) and nearest-medoid labels
-    KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, ms));
+    const float* kmm = sp.kind == KKM_LINEAR ? auxM : nullptr;
+    if (!mx_ready) KKM_TRY(prep_ids(sp, X, Mg, C, MX, auxM, ms));
     KKM_TRY(kernel_block(sp, MX, auxM, Mg, C, Xi, aux_i, gid, Ni, Kt, ldk, ms));
     KKM_RUN("nearest", ms, launch_nearest(Kt, ldk, Ni, C, kself, kmm, u, nullptr, ms));
 
@@ -1687,20 +1692,35 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
                       : launch_fhat_partial(bk.KT, ldk, Ni, S, Ifin, ms));
       KKM_RUN("medoid_keys", ms, launch_medoid_keys(ldk, Ni, S, Ifin, kself, u, keys, cnt, ghat, ms));
     }
-    KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms, /*reset_keys=*/true));
+    if (rows_carried) {
+      KKM_RUN("medoid_rows", ms,
+              launch_medoid_rows(keys, cnt, S.n_j, C, mi, mi_safe, Xi, aux_i, sp.dp, gid, MIX, auxMI, idMI, ms));
+    } else {
+      KKM_RUN("medoid_pick", ms, launch_medoid_pick(keys, cnt, S.n_j, C, mi, ms, /*reset_keys=*/true));
+      KKM_RUN("clamp_idx", ms, (clamp_idx_kernel<<<blocks_for(C), 256, 0, ms>>>(mi, C, mi_safe), cudaGetLastError()));
+      KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, ms));
+      KKM_RUN("gather_ids", ms, (gather_i64_kernel<<<blocks_for(C), 256, 0, ms>>>(gid, mi, C, idMI), cudaGetLastError()));
+    }
     // Eq. 12: K(X^i, m^i) and the convex merge
-    KKM_RUN("clamp_idx", ms, (clamp_idx_kernel<<<blocks_for(C), 256, 0, ms>>>(mi, C, mi_safe), cudaGetLastError()));
-    KKM_TRY(copy_prepared(sp, Xi, mi_safe, C, MIX, auxMI, ms));
-    KKM_RUN("gather_ids", ms, (gather_i64_kernel<<<blocks_for(C), 256, 0, ms>>>(gid, mi, C, idMI), cudaGetLastError()));
     KKM_TRY(kernel_block(sp, MIX, auxMI, idMI, C, Xi, aux_i, gid, Ni, Kmi, ldk, ms));
     KKM_RUN("merge_keys", ms, launch_merge_keys(Kt, Kmi, ldk, Ni, C, kself, mi, cnt, W, keys, ms));
     KKM_RUN("merge_apply", ms, launch_merge_apply(keys, mi, cnt, C, g.start, g.step, Mg, W, ms, Mg_prev));
     // how far the global medoids moved in this outer iteration (Fig. 4b):
-    // K(old medoid rows MX, new medoid rows) and its diagonal
-    KKM_TRY(prep_ids(sp, X, Mg, C, MXn, auxMn, ms));
-    KKM_TRY(kernel_block(sp, MX, auxM, Mg_prev, C, MXn, auxMn, Mg, C, Kmn, ldc, ms));
-    KKM_RUN("displacement", ms,
-            launch_displacement(Kmn, ldc, C, kmm, sp.kind == KKM_LINEAR ? auxMn : nullptr, Mg_prev, Mg, disp + i, ms));
+    // K(old medoid row, new medoid row) per cluster
+    if (rows_carried) {
+      KKM_RUN("displacement", ms,
+              launch_displacement_rows(MX, auxM, Xi, aux_i, sp.dp, C, keys, mi, Mg_prev, Mg, sp.kind == KKM_LINEAR,
+                                       sp.neg_scale(), disp + i, MXn, auxMn, ms));
+      std::swap(MX, MXn);  // the rows of the medoids after the merge
+      std::swap(auxM, auxMn);
+      mx_ready = true;
+    } else {
+      KKM_TRY(prep_ids(sp, X, Mg, C, MXn, auxMn, ms));
+      KKM_TRY(kernel_block(sp, MX, auxM, Mg_prev, C, MXn, auxMn, Mg, C, Kmn, ldc, ms));
+      KKM_RUN("displacement", ms,
+              launch_displacement(Kmn, ldc, C, kmm, sp.kind == KKM_LINEAR ? auxMn : nullptr, Mg_prev, Mg, disp + i,
+                                  ms));
+    }
     if (labels_dev)
       KKM_RUN("scatter_labels", ms, launch_scatter_labels(u, Ni, g.start, g.step, labels_dev, ms));
     if (i == B - 1 && model_out) {
@@ -1773,7 +1793,12 @@ static kkm_status fit_impl(const float* X_in, int64_t N, int64_t d, int32_t C, i
   Readback rb;
   if (mres) {
     kkm_model* m = mres;
-    KKM_TRY(prep_ids(sp, X, Mg, C, m->med, m->med_aux, st));
+    if (mx_ready) {
+      KKM_CK(cudaMemcpyAsync(m->med, MX, (size_t)C * sp.dp * 4, cudaMemcpyDeviceToDevice, st));
+      KKM_CK(cudaMemcpyAsync(m->med_aux, auxM, (size_t)C * 4, cudaMemcpyDeviceToDevice, st));
+    } else {
+      KKM_TRY(prep_ids(sp, X, Mg, C, m->med, m->med_aux, st));
+    }
     float* coords = nullptr;  // medoid rows in the caller's layout
     KKM_TRY(ws.alloc(&coords, (int64_t)C * d));
     KKM_RUN("gather_rows", st,

@@ -525,6 +525,19 @@ cudaError_t launch_merge_apply(const unsigned long long* keys, const int32_t* mi
                                cudaStream_t st, int64_t* prev = nullptr);
 // Average centre displacement across one mini-batch (Section 4.1, Fig. 4b)
 // from K[a][b] = K(old_a, cur_b) (C x C, row pitch ldk) into *out (device).
+// Eq. 10 medoids of the mini-batch with their rows (feature kernels): mi,
+// mi_safe, the keys reset, the medoid rows and norms copied from Xi/aux_i,
+// their global ids idMI (dp a multiple of 4).
+cudaError_t launch_medoid_rows(unsigned long long* keys, const int32_t* c, const int32_t* n_j, int C, int32_t* mi,
+                               int32_t* mi_safe, const float* Xi, const float* aux_i, int dp, const int64_t* gid,
+                               float* MIX, float* auxMI, int64_t* idMI, cudaStream_t st);
+// The displacement of a mini-batch from the medoid rows before (MX) and the
+// mini-batch rows (Gaussian or linear kernel); NX/nauxM get the medoid rows
+// after the merge (the next mini-batch's MX).
+cudaError_t launch_displacement_rows(const float* MX, const float* auxM, const float* Xi, const float* aux_i, int dp,
+                                     int C, const unsigned long long* keys, const int32_t* mi, const int64_t* old,
+                                     const int64_t* cur, bool linear, float neg_scale, double* out, float* NX,
+                                     float* nauxM, cudaStream_t st);
 cudaError_t launch_displacement(const float* K, int64_t ldk, int C, const float* selfA, const float* selfB,
                                 const int64_t* old, const int64_t* cur, double* out, cudaStream_t st);
 // labels_out[start + l*step] = u[l]

@@ -1847,6 +1847,109 @@ cudaError_t launch_displacement(const float* K, int64_t ldk, int C, const float*
   return cudaGetLastError();
 }
 
+// ------------------- Eq. 10 medoid rows, and the displacement from rows
+// Per cluster j (one warp each): mi[j] = the local index of the Eq. 10
+// medoid (-1 when empty), the Eq. 10 key reset to ~0 for the merge keys,
+// mi_safe[j] (0 for an empty cluster), idMI[j] its global id (-1 when empty),
+// and its prepared row and norm copied from the mini-batch's rows (the values
+// a gather of that row would give).
+__global__ void medoid_rows_kernel(unsigned long long* __restrict__ keys, const int32_t* __restrict__ c,
+                                   const int32_t* __restrict__ n_j, int C, int32_t* __restrict__ mi,
+                                   int32_t* __restrict__ mi_safe, const float4* __restrict__ Xi,
+                                   const float* __restrict__ aux_i, int dp4, const int64_t* __restrict__ gid,
+                                   float4* __restrict__ MIX, float* __restrict__ auxMI, int64_t* __restrict__ idMI) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (j >= C) return;
+  const unsigned long long key = keys[j];
+  const int m = (c[j] > 0 && n_j[j] > 0 && key != ~0ull) ? (int)(key & 0xffffffffull) : -1;
+  const int ms = m >= 0 ? m : 0;
+  for (int q = lane; q < dp4; q += 32) MIX[(int64_t)j * dp4 + q] = Xi[(int64_t)ms * dp4 + q];
+  __syncwarp();
+  if (lane == 0) {
+    mi[j] = m;
+    mi_safe[j] = ms;
+    keys[j] = ~0ull;
+    auxMI[j] = aux_i[ms];
+    idMI[j] = m >= 0 ? gid[m] : -1;
+  }
+}
+
+cudaError_t launch_medoid_rows(unsigned long long* keys, const int32_t* c, const int32_t* n_j, int C, int32_t* mi,
+                               int32_t* mi_safe, const float* Xi, const float* aux_i, int dp, const int64_t* gid,
+                               float* MIX, float* auxMI, int64_t* idMI, cudaStream_t st) {
+  if (dp % 4 != 0) return cudaErrorInvalidValue;
+  medoid_rows_kernel<<<(unsigned)ceil_div(C, 8), 256, 0, st>>>(keys, c, n_j, C, mi, mi_safe,
+                                                               reinterpret_cast<const float4*>(Xi), aux_i, dp / 4,
+                                                               gid, reinterpret_cast<float4*>(MIX), auxMI, idMI);
+  return cudaGetLastError();
+}
+
+// The displacement of a mini-batch (as displacement_kernel) from the rows:
+// the medoid before is MX[j] (global id old[j]); after the merge it is
+// cur[j], the mini-batch's local row (keys[j] & 0xffffffff) when mi[j] >= 0
+// and it moved.  K(a, b) = exp2(|a - b|^2 neg_scale) (Gaussian, self terms 1)
+// or a.b (linear, self terms the squared norms auxM, aux_i), |a - b|^2 and
+// a.b summed lane-strided over 16-byte vectors, then a fixed xor tree.  The
+// next mini-batch's medoid rows are written as well: NX[j] = the row after.
+__global__ void __launch_bounds__(256)
+displacement_rows_kernel(const float4* __restrict__ MX, const float* __restrict__ auxM,
+                         const float4* __restrict__ Xi, const float* __restrict__ aux_i, int dp4, int C,
+                         const unsigned long long* __restrict__ keys, const int32_t* __restrict__ mi,
+                         const int64_t* __restrict__ old, const int64_t* __restrict__ cur, int linear,
+                         float neg_scale, double* __restrict__ out, float4* __restrict__ NX, float* __restrict__ nauxM) {
+  __shared__ double val[kMaxC];
+  __shared__ double red[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = w; j < C; j += nw) {
+    const bool moved = mi[j] >= 0 && old[j] != cur[j];
+    const int l = moved ? (int)(keys[j] & 0xffffffffull) : 0;
+    const float4* a = MX + (int64_t)j * dp4;
+    const float4* b = Xi + (int64_t)l * dp4;
+    float acc = 0.0f;
+    for (int q = lane; q < dp4; q += 32) {
+      const float4 x = a[q], y = moved ? b[q] : x;
+      NX[(int64_t)j * dp4 + q] = y;
+      if (linear) {
+        acc = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc))));
+      } else {
+        const float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+        acc = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc))));
+      }
+    }
+    acc = warp_sum_f32(acc);
+    if (lane == 0) {
+      const float kb_f = moved ? aux_i[l] : auxM[j];
+      nauxM[j] = kb_f;
+      double v = 0.0;
+      if (moved) {
+        const double k = linear ? (double)acc : (double)exp2f(acc * neg_scale);
+        const double ka = linear ? (double)auxM[j] : 1.0, kb = linear ? (double)kb_f : 1.0;
+        const double d2 = ka - 2.0 * k + kb;
+        v = sqrt(d2 > 0.0 ? d2 : 0.0);
+      }
+      val[j] = v;
+    }
+  }
+  __syncthreads();
+  double s = 0.0;
+  for (int j = threadIdx.x; j < C; j += blockDim.x) s += val[j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s / (double)C;
+}
+
+cudaError_t launch_displacement_rows(const float* MX, const float* auxM, const float* Xi, const float* aux_i, int dp,
+                                     int C, const unsigned long long* keys, const int32_t* mi, const int64_t* old,
+                                     const int64_t* cur, bool linear, float neg_scale, double* out, float* NX,
+                                     float* nauxM, cudaStream_t st) {
+  if (dp % 4 != 0 || C > kMaxC) return cudaErrorInvalidValue;
+  displacement_rows_kernel<<<1, 256, 0, st>>>(reinterpret_cast<const float4*>(MX), auxM,
+                                              reinterpret_cast<const float4*>(Xi), aux_i, dp / 4, C, keys, mi, old,
+                                              cur, linear ? 1 : 0, neg_scale, out, reinterpret_cast<float4*>(NX),
+                                              nauxM);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- small utils
 __global__ void scatter_labels_kernel(const int32_t* __restrict__ u, int Ni, int64_t start,
                                       int64_t step, int32_t* __restrict__ out) {

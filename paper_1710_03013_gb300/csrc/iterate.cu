@@ -1775,13 +1775,42 @@ merge_keys_kernel(const float* __restrict__ Kt, const float* __restrict__ Kmi, i
     alpha[j] = mi[j] >= 0 ? (float)((double)c[j] / ((double)c[j] + (double)W[j])) : 0.0f;
   }
   __syncthreads();
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Ni; l += gridDim.x * blockDim.x) {
-    const float ks = kself ? kself[l] : 1.0f;
-    for (int j = 0; j < C; ++j) {
-      if (mi[j] < 0) continue;
-      const float a = alpha[j];
-      const float v = ks - 2.0f * (1.0f - a) * Kt[(int64_t)j * ldk + l] - 2.0f * a * Kmi[(int64_t)j * ldk + l];
-      atomicMin(&bkey[j], pack_key(v, (uint32_t)l));
+  // clusters in groups of 8: each thread's minimum over its samples (the
+  // group's 16 loads of a sample in flight together), then the warp's (a min
+  // is order-free: the same key whatever the split)
+  constexpr int G = 8;
+  for (int j0 = 0; j0 < C; j0 += G) {
+    unsigned long long kmin[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) kmin[q] = ~0ull;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < Ni; l += gridDim.x * blockDim.x) {
+      const float ks = kself ? kself[l] : 1.0f;
+      float kt[G], km[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int j = j0 + q;
+        kt[q] = j < C ? Kt[(int64_t)j * ldk + l] : 0.0f;
+        km[q] = j < C ? Kmi[(int64_t)j * ldk + l] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int j = j0 + q;
+        if (j < C && mi[j] >= 0) {
+          const float a = alpha[j];
+          const float v = ks - 2.0f * (1.0f - a) * kt[q] - 2.0f * a * km[q];
+          const unsigned long long k = pack_key(v, (uint32_t)l);
+          kmin[q] = k < kmin[q] ? k : kmin[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, kmin[q], o);
+        kmin[q] = y < kmin[q] ? y : kmin[q];
+      }
+      if ((threadIdx.x & 31) == 0 && j0 + q < C && kmin[q] != ~0ull) atomicMin(&bkey[j0 + q], kmin[q]);
     }
   }
   __syncthreads();
@@ -2128,6 +2157,159 @@ __device__ __forceinline__ double kpp_block_scan(double v, double* sh) {
   return off + v;
 }
 
+// One 32-sample group g of a round: the kernel column of the last pick m
+// (its row in kpp_row), the D^2 update (from D2in into D2out; the same array
+// for the one-launch-per-round kernel), the running sums P of the group and
+// its total bsum[g].
+__device__ __forceinline__ void kpp_group(const float* __restrict__ X, int dp, int N0, int linear, float neg_scale,
+                                          const float* __restrict__ kself, const double* D2in, double* D2out,
+                                          double* __restrict__ P, double* __restrict__ bsum, int m, int r, int g,
+                                          const float4* kpp_row, float* kv) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int d4 = dp >> 2;
+  const int l0 = g * kKppSamples;
+  {
+    const float4* xl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int l = l0 + 4 * w + q;
+      xl[q] = l < N0 ? reinterpret_cast<const float4*>(X + (int64_t)l * dp) : nullptr;
+    }
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int c0 = 0; c0 < d4; c0 += 64) {
+      float4 v[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = c0 + 32 * h + lane;
+          v[q][h] = (xl[q] && c < d4) ? __ldg(xl[q] + c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + 32 * h + lane;
+        const float4 b = c < d4 ? kpp_row[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 a = v[q][h];
+          if (linear) {
+            acc[q] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[q]))));
+          } else {
+            const float tx = a.x - b.x, ty = a.y - b.y, tz = a.z - b.z, tw = a.w - b.w;
+            acc[q] = fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, fmaf(tw, tw, acc[q]))));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float a = warp_sum_f32(acc[q]);
+      if (lane == 0) {
+        const int l = l0 + 4 * w + q;
+        kv[4 * w + q] = linear ? a : (l == m ? 1.0f : exp2f(a * neg_scale));
+      }
+    }
+  }
+  __syncthreads();
+  // D^2 update and running sums within the group (warp 0)
+  if (w == 0) {
+    const int l = l0 + lane;
+    const double km = kself ? (double)kself[m] : 1.0;
+    double dv = 0.0;
+    if (l < N0) {
+      const double ks = kself ? (double)kself[l] : 1.0;
+      double v = ks - 2.0 * (double)kv[lane] + km;
+      v = v > 0.0 ? v : 0.0;
+      dv = (r == 1) ? v : fmin(D2in[l], v);
+      D2out[l] = dv;
+    }
+    double x = dv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (l < N0) P[l] = x;
+    if (lane == 31) bsum[g] = x;
+  }
+}
+
+// The next pick from the groups' running sums (every thread of the CTA
+// calls it; the same value in every thread): the group totals' running sums
+// (a block scan per chunk of 256 groups, chunks in order), target = u * their
+// total, the first sample whose interval [running sum before, running sum
+// after) contains it; if rounding put the target at the very end, the last
+// sample with D^2 > 0; if every D^2 is 0, the lowest sample not picked yet
+// (picks[0..r) in global memory).
+__device__ int kpp_pick(int N0, int nb, const double* P, const double* bsum, const double* D2, const int32_t* picks,
+                        double u, int r, double* wsh, double* base_sh, double* total_sh, int* blk_sh, int* pick_sh) {
+  const int tid = threadIdx.x;
+  double run = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
+    const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
+    const double incl = kpp_block_scan(v, wsh);
+    if (tid == kKppThreads - 1) *total_sh = incl;
+    __syncthreads();
+    run += *total_sh;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *blk_sh = -1;
+    *pick_sh = -1;
+  }
+  __syncthreads();
+  const double total = run;
+  if (total > 0.0) {
+    const double target = u * total;
+    double before = 0.0;  // running sum of the earlier chunks
+    for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
+      const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
+      const double incl = before + kpp_block_scan(v, wsh);
+      const double excl = incl - v;
+      if (b0 + tid < nb && excl <= target && incl > target) {
+        *blk_sh = b0 + tid;
+        *base_sh = excl;
+      }
+      if (tid == kKppThreads - 1) *total_sh = incl;
+      __syncthreads();
+      before = *total_sh;
+      const bool found = *blk_sh >= 0;
+      __syncthreads();
+      if (found) break;
+    }
+    const int blk = *blk_sh;
+    if (blk >= 0 && tid < kKppSamples) {
+      // interval [base + P[l-1], base + P[l]) of sample l; neighbours share endpoints exactly
+      const double base = *base_sh;
+      const int l = blk * kKppSamples + tid;
+      if (l < N0) {
+        const double hi = base + __ldcg(P + l);
+        const double lo = base + (tid > 0 ? __ldcg(P + l - 1) : 0.0);
+        if (lo <= target && hi > target) *pick_sh = l;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *pick_sh < 0) {
+    if (total > 0.0) {  // rounding put the target at the very end
+      int l = N0 - 1;
+      while (l > 0 && !(__ldcg(D2 + l) > 0.0)) --l;
+      *pick_sh = l;
+    } else {
+      for (int l = 0; l < N0; ++l) {
+        bool taken = false;
+        for (int q = 0; q < r; ++q) taken |= (__ldcg(picks + q) == l);
+        if (!taken) {
+          *pick_sh = l;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return *pick_sh;
+}
+
 __global__ void __launch_bounds__(kKppThreads)
 kpp_fused_round_kernel(const float* __restrict__ X, int dp, int N0, int linear, float neg_scale,
                        const float* __restrict__ kself, double* __restrict__ D2, double* __restrict__ P,
@@ -2137,78 +2319,13 @@ kpp_fused_round_kernel(const float* __restrict__ X, int dp, int N0, int linear, 
   __shared__ float kv[kKppSamples];
   __shared__ double wsh[kKppThreads / 32];
   __shared__ double base_sh, total_sh;
-  __shared__ int blk_sh, last_sh;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  __shared__ int blk_sh, last_sh, pick_sh;
+  const int tid = threadIdx.x;
   const int m = picks[r - 1];
-  const int d4 = dp >> 2;
   const float4* xm_g = reinterpret_cast<const float4*>(X + (int64_t)m * dp);
-  for (int c = tid; c < d4; c += kKppThreads) kpp_row[c] = __ldg(xm_g + c);
+  for (int c = tid; c < (dp >> 2); c += kKppThreads) kpp_row[c] = __ldg(xm_g + c);
   __syncthreads();
-  const int l0 = blockIdx.x * kKppSamples;
-  {
-    const float4* xl[4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const int l = l0 + 4 * w + g;
-      xl[g] = l < N0 ? reinterpret_cast<const float4*>(X + (int64_t)l * dp) : nullptr;
-    }
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int c0 = 0; c0 < d4; c0 += 64) {
-      float4 v[4][2];
-#pragma unroll
-      for (int g = 0; g < 4; ++g)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = c0 + 32 * h + lane;
-          v[g][h] = (xl[g] && c < d4) ? __ldg(xl[g] + c) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = c0 + 32 * h + lane;
-        const float4 b = c < d4 ? kpp_row[c] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const float4 a = v[g][h];
-          if (linear) {
-            acc[g] = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc[g]))));
-          } else {
-            const float tx = a.x - b.x, ty = a.y - b.y, tz = a.z - b.z, tw = a.w - b.w;
-            acc[g] = fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, fmaf(tw, tw, acc[g]))));
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const float a = warp_sum_f32(acc[g]);
-      if (lane == 0) {
-        const int l = l0 + 4 * w + g;
-        kv[4 * w + g] = linear ? a : (l == m ? 1.0f : exp2f(a * neg_scale));
-      }
-    }
-  }
-  __syncthreads();
-  // D^2 update and running sums within the CTA (warp 0)
-  if (w == 0) {
-    const int l = l0 + lane;
-    const double km = kself ? (double)kself[m] : 1.0;
-    double dv = 0.0;
-    if (l < N0) {
-      const double ks = kself ? (double)kself[l] : 1.0;
-      double v = ks - 2.0 * (double)kv[lane] + km;
-      v = v > 0.0 ? v : 0.0;
-      dv = (r == 1) ? v : fmin(D2[l], v);
-      D2[l] = dv;
-    }
-    double x = dv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(kFull, x, o);
-      if (lane >= o) x += y;
-    }
-    if (l < N0) P[l] = x;
-    if (lane == 31) bsum[blockIdx.x] = x;
-  }
+  kpp_group(X, dp, N0, linear, neg_scale, kself, D2, D2, P, bsum, m, r, (int)blockIdx.x, kpp_row, kv);
   // the last CTA draws the next pick
   __threadfence();
   __syncthreads();
@@ -2216,71 +2333,10 @@ kpp_fused_round_kernel(const float* __restrict__ X, int dp, int N0, int linear, 
   __syncthreads();
   if (!last_sh) return;
   __threadfence();
-  const int nb = (int)gridDim.x;
-  // the CTA totals' running sums, chunk by chunk: first the total
-  double run = 0.0;
-  for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
-    const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
-    const double incl = kpp_block_scan(v, wsh);
-    if (tid == kKppThreads - 1) total_sh = incl;
-    __syncthreads();
-    run += total_sh;
-    __syncthreads();
-  }
+  const int pick = kpp_pick(N0, (int)gridDim.x, P, bsum, D2, picks, draws[r], r, wsh, &base_sh, &total_sh, &blk_sh,
+                            &pick_sh);
   if (tid == 0) {
-    blk_sh = -1;
-    picks[r] = -1;
-  }
-  __syncthreads();
-  const double total = run;
-  if (total > 0.0) {
-    const double target = draws[r] * total;
-    double before = 0.0;  // running sum of the earlier chunks
-    for (int b0 = 0; b0 < nb; b0 += kKppThreads) {
-      const double v = b0 + tid < nb ? __ldcg(bsum + b0 + tid) : 0.0;
-      const double incl = before + kpp_block_scan(v, wsh);
-      const double excl = incl - v;
-      if (b0 + tid < nb && excl <= target && incl > target) {
-        blk_sh = b0 + tid;
-        base_sh = excl;
-      }
-      if (tid == kKppThreads - 1) total_sh = incl;
-      __syncthreads();
-      before = total_sh;
-      const bool found = blk_sh >= 0;
-      __syncthreads();
-      if (found) break;
-    }
-    const int blk = blk_sh;
-    if (blk >= 0 && tid < kKppSamples) {
-      // interval [base + P[l-1], base + P[l]) of sample l; neighbours share endpoints exactly
-      const double base = base_sh;
-      const int l = blk * kKppSamples + tid;
-      if (l < N0) {
-        const double hi = base + __ldcg(P + l);
-        const double lo = base + (tid > 0 ? __ldcg(P + l - 1) : 0.0);
-        if (lo <= target && hi > target) picks[r] = l;
-      }
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (picks[r] < 0) {
-      if (total > 0.0) {  // rounding put the target at the very end
-        int l = N0 - 1;
-        while (l > 0 && !(__ldcg(D2 + l) > 0.0)) --l;
-        picks[r] = l;
-      } else {
-        for (int l = 0; l < N0; ++l) {
-          bool taken = false;
-          for (int q = 0; q < r; ++q) taken |= (picks[q] == l);
-          if (!taken) {
-            picks[r] = l;
-            break;
-          }
-        }
-      }
-    }
+    picks[r] = pick;
     *ticket = 0u;
   }
 }

@@ -40,9 +40,9 @@ namespace kkm {
 // rows per CTA spread a small round over the SMs, more rows amortise a CTA's
 // fixed work (cluster tables, barriers, its ticket) in a round of many loops.
 // Per key (the CTA width and the launch's row-block count rounded down to a
-// power of two) each candidate is timed on kTuneSamples live launches with
-// events, and the one with the least time per row block is kept for the
-// process.  KKM_TUNE_CACHE names a file the choices are read from when the
+// power of two; a fit's own assign launches and the work lists' are keyed
+// apart) each candidate is timed on kTuneSamples live launches with events,
+// and the one with the least time per row block is kept for the process.  KKM_TUNE_CACHE names a file the choices are read from when the
 // first executor starts and written back to when an executor stops (lines
 // "assign_rows <key> <rows>"); KKM_ASSIGN_ROWS forces one candidate.
 struct RowTuner {
@@ -127,6 +127,14 @@ struct RowTuner {
   }
 };
 static RowTuner g_row_tuner;
+int assign_rows_choose(long long key, bool* timed) {
+  g_row_tuner.load();
+  return g_row_tuner.choose(key, timed);
+}
+void assign_rows_sample(long long key, int rows, int blocks, float ms) { g_row_tuner.sample(key, rows, blocks, ms); }
+long long assign_rows_key(int nw, int blocks, bool solo) { return RowTuner::key(nw, blocks) + (solo ? (1LL << 20) : 0); }
+void assign_rows_load() { g_row_tuner.load(); }
+void assign_rows_save() { g_row_tuner.save(); }
 
 // ------------------------------------------------ inner loops as work lists
 // The fits of a batch hand their split-form inner loops to one executor

@@ -462,6 +462,14 @@ cudaError_t launch_sort_multi(const LoopItem* items, const RoundList& L, cudaStr
 // with the fit's stream ordered after it.
 struct LoopExecutor;
 LoopExecutor* current_loop_executor();
+// Rows per assign CTA (1, 2, 4 or 8 blocks of 32; no effect on results),
+// chosen by timing per key (batch.cu): the choice for a launch (*timed: time
+// it and report with assign_rows_sample), keys, the cache file.
+long long assign_rows_key(int nw, int blocks, bool solo);
+int assign_rows_choose(long long key, bool* timed);
+void assign_rows_sample(long long key, int rows, int blocks, float ms);
+void assign_rows_load();
+void assign_rows_save();
 kkm_status loop_executor_run(LoopExecutor* ex, const LoopItem& item, int iters, cudaStream_t st);
 
 // The whole inner loop of a mini-batch (up to `iters` iterations: f_hat,

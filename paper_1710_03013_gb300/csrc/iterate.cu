@@ -29,6 +29,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -878,9 +880,52 @@ __global__ void __launch_bounds__(kAssignWarps * 32, 4)
 assign_kernel(int64_t ldk, int Ni, Supports S, IterState I, const float* __restrict__ kself,
               int32_t* __restrict__ u, float* __restrict__ margin, float* __restrict__ dmin,
               float* __restrict__ fhat_out, double* __restrict__ ghat_out, int early_stop,
-              int trace, RescoreArgs R) {
+              int trace, RescoreArgs R, int RG) {
   assign_body(ldk, Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R, (int)blockIdx.x,
-              (int)gridDim.x);
+              (int)gridDim.x, false, RG);
+}
+
+// Timing samples of the row tuner from a fit's own assign launches: events
+// from a pool, read once they have completed (by a later launch).
+struct SoloSample {
+  long long key;
+  int rows, blocks;
+  cudaEvent_t a, b;
+};
+static std::mutex g_solo_mu;
+static std::vector<SoloSample> g_solo_samples;
+static std::vector<cudaEvent_t> g_solo_events;
+static cudaEvent_t solo_event() {
+  std::lock_guard<std::mutex> lk(g_solo_mu);
+  if (!g_solo_events.empty()) {
+    cudaEvent_t e = g_solo_events.back();
+    g_solo_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+static void solo_samples_collect() {
+  std::lock_guard<std::mutex> lk(g_solo_mu);
+  for (size_t q = 0; q < g_solo_samples.size();) {
+    SoloSample& m = g_solo_samples[q];
+    const cudaError_t e = cudaEventQuery(m.b);
+    if (e == cudaErrorNotReady) {
+      ++q;
+      continue;
+    }
+    float ms = 0.0f;
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess)
+      assign_rows_sample(m.key, m.rows, m.blocks, ms);
+    cudaGetLastError();
+    g_solo_events.push_back(m.a);
+    g_solo_events.push_back(m.b);
+    g_solo_samples.erase(g_solo_samples.begin() + (std::ptrdiff_t)q);
+  }
 }
 
 cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterState& I,
@@ -896,8 +941,31 @@ cudaError_t launch_assign(int64_t ldk, int Ni, const Supports& S, const IterStat
   static const cudaError_t attr =
       cudaFuncSetAttribute(assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAssignMaxDynSmem);
   if (attr != cudaSuccess) return attr;
-  return launch_pdl(assign_kernel, dim3((unsigned)ceil_div(Ni, kAssignRows)), dim3(threads), smem, st, ldk, Ni, S,
-                    I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R);
+  const int blocks = (int)ceil_div(Ni, kAssignRows);
+  // a fit's iteration launches: rows per CTA from the tuner (timing samples
+  // are events around a launch, read back by later calls)
+  int RG = 1;
+  bool timed = false;
+  long long key = 0;
+  if (trace == 1) {
+    solo_samples_collect();
+    key = assign_rows_key(threads / 32, blocks, /*solo=*/true);
+    RG = assign_rows_choose(key, &timed);
+  }
+  SoloSample smp{key, RG, blocks, nullptr, nullptr};
+  if (timed) {
+    smp.a = solo_event();
+    smp.b = solo_event();
+    if (smp.a && smp.b) cudaEventRecord(smp.a, st);
+  }
+  const cudaError_t e = launch_pdl(assign_kernel, dim3((unsigned)ceil_div(blocks, RG)), dim3(threads), smem, st, ldk,
+                                   Ni, S, I, kself, u, margin, dmin, fhat_out, ghat_out, early_stop, trace, R, RG);
+  if (timed && smp.a && smp.b) {
+    cudaEventRecord(smp.b, st);
+    std::lock_guard<std::mutex> lk(g_solo_mu);
+    g_solo_samples.push_back(smp);
+  }
+  return e;
 }
 
 // ------------------------------------------- inner loops as work lists

@@ -91,6 +91,24 @@ def test_assign_rows_per_cta_change_nothing(lib, monkeypatch, rows):
         _same_model((la, ma), (lb, mb))
 
 
+@pytest.mark.parametrize("rows", [2, 4, 8])
+def test_assign_rows_per_cta_solo_split_fit(lib, monkeypatch, rows):
+    """A fit's own assign launches (split loop, FP32 and the reduced-precision
+    re-score, a linear-kernel fit) take the same rows-per-CTA candidates:
+    bit-identical results."""
+    cases = [(blobs(5003, 16, 6, workload=3, problem=301)[0], "rbf", 0, 6, 3),
+             (blobs(3001, 32, 9, workload=3, problem=302)[0], "rbf", 1, 9, 2),
+             (blobs(2000, 8, 4, workload=3, problem=303)[0], "linear", 0, 4, 2)]
+    for X, kind, prec, C, B in cases:
+        Xd = _dev(X)
+        kw = dict(iters=6, seed=5, precision=prec, iteration="split", early_stop=False)
+        monkeypatch.setenv("KKM_ASSIGN_ROWS", "1")
+        ref = lib.kkm_fit(Xd, C, B, 0.3, kind, 0.0, **kw)
+        monkeypatch.setenv("KKM_ASSIGN_ROWS", str(rows))
+        got = lib.kkm_fit(Xd, C, B, 0.3, kind, 0.0, **kw)
+        _same_model(ref, got)
+
+
 def test_row_tuner_cache_file(lib, monkeypatch, tmp_path):
     """With KKM_TUNE_CACHE set, the choices the tuner settles on are written as
     'assign_rows <key> <rows>' lines, each a candidate."""

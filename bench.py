@@ -649,7 +649,7 @@ def run_ours(args, cfg, X):
                         "by events (short kernels include launch gaps); the roofline uses region 2",
         "final_omega": float(om[-1]) if len(om) else None,
     }
-    print(json.dumps(out), flush=True)
+    emit(out)
     if world > 1:
         dist.destroy_process_group()
 
@@ -902,7 +902,7 @@ def run_batched(args, cfg):
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 # ------------------------------------------------------------ serving loop
@@ -1103,7 +1103,35 @@ def run_serving(args, cfg):
     }
     ev, dt, desc = serving_oracle(cfg, 10.0)
     out["cpu_baseline"] = {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-    print(json.dumps(out), flush=True)
+    emit(out)
+
+
+# Where a workload's JSON line goes: printed, or collected when the default
+# run nests the other configurations' lines in its own.
+_SINK = None
+
+
+def emit(out):
+    if _SINK is not None:
+        _SINK.append(out)
+    else:
+        print(json.dumps(out), flush=True)
+
+
+def config_summary(out):
+    """The fields of another configuration's bench line that the default line
+    carries for it."""
+    keep = ("metric", "value", "unit", "ms_per_step", "iters_per_s", "dtype", "config", "e2e", "gpu_launches",
+            "matched_labels", "oracle_parity", "latency_ms", "cpu_baseline", "clocks", "fp32_path")
+    d = {k: out[k] for k in keep if k in out}
+    r = out.get("roofline")
+    if r:
+        d["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "peak_source",
+                                           "method_frac") if k in r}
+        if "screen" in r:
+            d["roofline"]["screen"] = {k: r["screen"][k] for k in ("kernel", "achieved", "peak", "frac",
+                                                                    "method_frac") if k in r["screen"]}
+    return d
 
 
 def ctypes_stream(stream):
@@ -1121,6 +1149,8 @@ def main():
     ap.add_argument("--streams", type=int, default=0, help="batched workload: concurrent streams (0: default)")
     ap.add_argument("--pipeline", default="auto", choices=["auto", "serial", "overlap"],
                     help="kernel-block scheduling of the fits (auto: next block overlapped when B >= 2)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: do not run and nest the MD, batched and serving configurations")
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     cfg["key"] = args.workload
@@ -1145,10 +1175,44 @@ def main():
         X, _ = mnist_like(cfg["N"], cfg["d"])
     if args.impl == "reference":
         run_reference(args, cfg, X)
-    else:
-        from paper_1710_03013_gb300 import build as _b
-        _b.build()
+        return
+    from paper_1710_03013_gb300 import build as _b
+    _b.build()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload != "mnist" or world > 1 or args.no_configs:
         run_ours(args, cfg, X)
+        return
+    # the default run: the headline line, with the other configurations'
+    # lines (short runs, each its own timed region) nested under "configs"
+    global _SINK
+    _SINK = []
+    run_ours(args, cfg, X)
+    head = _SINK[0]
+    del X
+    others = {}
+    for name, steps, warmup in (("md", 2, 3), ("batched", 2, 3), ("serving", 1, 1)):
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.workload = steps, warmup, name
+        c = dict(WORKLOADS[name])
+        c["key"] = name
+        _SINK = []
+        try:
+            if name == "serving":
+                run_serving(sub, c)
+            elif name == "batched":
+                run_batched(sub, c)
+            else:
+                from synth import md_trajectory
+                F, _ = md_trajectory(c["N"], c["n_atoms"])
+                run_ours(sub, c, F.reshape(c["N"], -1))
+                del F
+            others[name] = config_summary(_SINK[-1]) if _SINK else {"error": "no result"}
+            others[name]["steps"], others[name]["warmup"] = steps, warmup
+        except Exception as e:  # one configuration failing leaves the headline line intact
+            others[name] = {"error": f"{type(e).__name__}: {e}"}
+    head["configs"] = others
+    _SINK = None
+    emit(head)
 
 
 if __name__ == "__main__":

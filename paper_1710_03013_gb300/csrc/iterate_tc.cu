@@ -213,12 +213,15 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
       for (int pass = 0; pass < passes && go; ++pass) {
         for (int kt = r; kt < nKT; kt += kTcRings) {
           bool got = false;
+          // (the flags are read every few polls: a try_wait that finds the
+          // slot still busy may suspend the thread for a while, and at the
+          // end of the loop the slot is never released)
           for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
             if (mbar_try_wait(&sh.empty[r][s], ph ^ 1u)) {
               got = true;
               break;
             }
-            if ((it & 255u) == 255u && (*stop_flag || *abort_flag)) break;
+            if ((it & 7u) == 7u && (*stop_flag || *abort_flag)) break;
           }
           if (!got || *stop_flag || *abort_flag) {
             if (!got && !*stop_flag && !*abort_flag) {
@@ -347,33 +350,35 @@ iterate_tc_kernel(const __grid_constant__ CUtensorMap map, int Ni, Supports S, I
     const float tau = I.flag_tau;
     const bool rescore = R.Xi != nullptr && tau > 0.0f;
 
-    // Z and the cluster sizes from the landmark labels: one warp per tile of
-    // 64 landmarks, one ballot per cluster
-    for (int kt = warp - 2 * kTcRings; kt < nKT; kt += kTcEpiWarps) {
-      const int k0 = kt * 64 + lane, k1 = k0 + 32;
-      const int l0 = k0 < nL ? __ldcg(S.lab + k0) : -1;
-      const int l1 = k1 < nL ? __ldcg(S.lab + k1) : -1;
-      // 16 rows x 8 chunks of 16 bytes: lane writes chunks lane + 32 p, of
-      // cluster row n = 4 p + lane / 8
+    // Z and the cluster sizes from the landmark labels: Z zeroed, then a one
+    // (0x3C00) at (label, landmark) for every landmark, the labels of eight
+    // landmarks per thread loaded together; the sizes by one shared atomic per
+    // distinct label in a warp
+    {
+      uint4* const z4 = reinterpret_cast<uint4*>(Z);
+      for (int e = et; e < nKT * (kTcZTile / 16); e += kTcEpiWarps * 32) z4[e] = make_uint4(0u, 0u, 0u, 0u);
+      epi_sync();
+      // the trip count depends on the warp only (every lane takes part in
+      // each match; lanes past nL carry no label)
+      constexpr int kZPre = 8;
+      const int wbase = et & ~31;
+      for (int kb = wbase; kb < nL; kb += kZPre * kTcEpiWarps * 32) {
+        int lab[kZPre];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        unsigned long long mm = 0;
-#pragma unroll
-        for (int nn = 0; nn < 4; ++nn) {
-          const int n = p * 4 + nn;
-          const unsigned long long mn = (unsigned long long)__ballot_sync(kFull, l0 == n) |
-                                        ((unsigned long long)__ballot_sync(kFull, l1 == n) << 32);
-          if (lane == 0 && mn) atomicAdd(&sh.nj[n], __popcll(mn));
-          if ((lane >> 3) == nn) mm = mn;
+        for (int p = 0; p < kZPre; ++p) {
+          const int k = kb + p * kTcEpiWarps * 32 + lane;
+          lab[p] = k < nL ? __ldcg(S.lab + k) : -1;
         }
-        const int idx = lane + 32 * p, c = idx & 7, n = idx >> 3;
-        const unsigned bits = (unsigned)(mm >> (c * 8)) & 0xFFu;
-        uint32_t w[4];
 #pragma unroll
-        for (int h = 0; h < 4; ++h)
-          w[h] = ((bits >> (2 * h)) & 1u ? 0x3C00u : 0u) | ((bits >> (2 * h + 1)) & 1u ? 0x3C000000u : 0u);
-        *reinterpret_cast<uint4*>(Z + (size_t)kt * kTcZTile + (n >> 3) * 1024 + (n & 7) * 128 + ((c ^ (n & 7)) << 4)) =
-            make_uint4(w[0], w[1], w[2], w[3]);
+        for (int p = 0; p < kZPre; ++p) {
+          const int k = kb + p * kTcEpiWarps * 32 + lane;
+          const int l = lab[p];
+          const unsigned peers = __match_any_sync(kFull, l);
+          if (l >= 0 && l < kTcN) {
+            *reinterpret_cast<unsigned short*>(Z + z_offset(k, l)) = 0x3C00;
+            if (lane == __ffs(peers) - 1) atomicAdd(&sh.nj[l], __popc(peers));
+          }
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // Z is read by the tensor cores

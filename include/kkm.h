@@ -292,6 +292,9 @@ kkm_status kkm_elbow(const float* X, int64_t N, int64_t d, int32_t C_lo,
  *              timing per launch size and kept for the process; the
  *              environment variable KKM_TUNE_CACHE names a file that keeps
  *              the choices across processes, KKM_ASSIGN_ROWS forces one.
+ *              KKM_LOOP_CHAINS (1..8) sets how many such work-list streams
+ *              the call runs side by side (each fit's loops go to one of
+ *              them; no effect on results).
  *   models_out [n] host array of model pointers (nullable); a failed
  *              problem's entry is NULL.
  *   status_out [n] host array: each problem's status.

@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -437,6 +438,22 @@ kkm_status loop_executor_run(LoopExecutor* ex, const LoopItem& item, int iters, 
 constexpr int kBatchStreams = 32;
 constexpr int kBatchMaxStreams = 64;
 
+// Number of work-list chains (executors, each with its own thread and
+// stream); worker w hands its loops to chain w mod E.  The rounds of one
+// chain run in order, so while one chain's assign launch (bound by its CTAs'
+// fixed work, not by bytes) occupies part of the GPU, another chain's f_hat
+// stream can use the rest.  KKM_LOOP_CHAINS overrides the default.
+constexpr int kLoopChains = 1;
+constexpr int kLoopChainsMax = 8;
+static int loop_chains(int W) {
+  int e = kLoopChains;
+  if (const char* v = getenv("KKM_LOOP_CHAINS")) {
+    const int x = atoi(v);
+    if (x >= 1 && x <= kLoopChainsMax) e = x;
+  }
+  return std::max(1, std::min(e, W));
+}
+
 static double fit_work(const kkm_problem& p) {
   if (p.N < 1 || p.B < 1 || p.B > p.N) return 0.0;
   double w = (double)p.N * (double)p.d;
@@ -484,19 +501,23 @@ static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams,
   std::atomic<int32_t> next{0};
   std::vector<std::string> errors(n);
   std::vector<std::string> worker_err(W);
-  LoopExecutor exec;
   const bool use_exec = !no_work_lists;
+  std::vector<std::unique_ptr<LoopExecutor>> execs;
   if (use_exec) {
-    const kkm_status es = exec.start(dev);
-    if (es != KKM_OK) {
-      exec.stop();
-      cudaEventDestroy(ready);
-      return es;
+    const int E = loop_chains(W);
+    for (int c = 0; c < E; ++c) {
+      execs.emplace_back(new LoopExecutor());
+      const kkm_status es = execs.back()->start(dev);
+      if (es != KKM_OK) {
+        for (auto& x : execs) x->stop();
+        cudaEventDestroy(ready);
+        return es;
+      }
     }
   }
 
   auto worker = [&](int w) {
-    t_loop_exec = use_exec ? &exec : nullptr;
+    t_loop_exec = use_exec ? execs[w % execs.size()].get() : nullptr;
     cudaStream_t st = nullptr;
     if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamWaitEvent(st, ready, 0) != cudaSuccess) {
@@ -528,7 +549,7 @@ static kkm_status batch_impl(const kkm_problem* P, int32_t n, int32_t n_streams,
   threads.reserve(W);
   for (int w = 0; w < W; ++w) threads.emplace_back(worker, w);
   for (auto& t : threads) t.join();
-  exec.stop();
+  for (auto& x : execs) x->stop();
   cudaEventDestroy(ready);
 
   for (int w = 0; w < W; ++w)

@@ -91,6 +91,24 @@ def test_assign_rows_per_cta_change_nothing(lib, monkeypatch, rows):
         _same_model((la, ma), (lb, mb))
 
 
+
+@pytest.mark.parametrize("chains", [2, 3])
+def test_loop_chains_change_nothing(lib, monkeypatch, chains):
+    """KKM_LOOP_CHAINS runs the work lists as several chains side by side
+    (each fit's loops on one chain): every result is bit-identical to one
+    chain, with more chains than loops in flight at times and early stop on."""
+    probs = _small_problems(9, seed=13)
+    probs.append(dict(X=blobs(2500, 8, 20, workload=3, problem=304)[0], C=20, B=3, s=0.4, iters=5, seed=4,
+                      precision=1, early_stop=True))
+    dev = [dict(p, X=_dev(p["X"])) for p in probs]
+    monkeypatch.setenv("KKM_LOOP_CHAINS", "1")
+    ref = lib.kkm_fit_batch(dev, n_streams=5)
+    monkeypatch.setenv("KKM_LOOP_CHAINS", str(chains))
+    got = lib.kkm_fit_batch(dev, n_streams=5)
+    for (la, ma, sa), (lb, mb, sb) in zip(ref, got):
+        assert sa == 0 and sb == 0
+        _same_model((la, ma), (lb, mb))
+
 @pytest.mark.parametrize("rows", [2, 4, 8])
 def test_assign_rows_per_cta_solo_split_fit(lib, monkeypatch, rows):
     """A fit's own assign launches (split loop, FP32 and the reduced-precision

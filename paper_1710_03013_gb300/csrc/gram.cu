@@ -455,14 +455,41 @@ __host__ __device__ constexpr int scatter_shift() {
 }
 
 // K(A_a, B_b) for nA <= NA reference rows held in shared memory and many
-// sample rows: one warp takes kSkinnyRows sample rows at a time, each lane
-// keeping kSkinnyLoads 16-byte loads per row in flight (the sample rows are
-// the only HBM traffic), every shared-memory reference value serving all the
-// warp's rows.  The Gaussian and distance kinds sum the squared differences
-// directly: the kernel reads memory at its bandwidth limit, so the second
-// operation per component costs nothing, and the squared distance does not
-// cancel as |x|^2 + |y|^2 - 2 x.y does for rows far from the origin.
-constexpr int kSkinnyRows = 2, kSkinnyLoads = 4;
+// sample rows.  One warp takes skinny_rows<NA>() sample rows at a time; a
+// lane handles the 16-byte vectors q = lane, lane + 32, ... of a row, in that
+// order whatever the row count, so the sums do not depend on it.  The kernel
+// is bound by instruction issue, not memory (16 warps per SM, the FP32 work
+// of nA references per sample value), so:
+//  - the FP32 work runs on the paired (float2) instructions: two reference
+//    rows per instruction, each half the same IEEE operation on its own
+//    values as the scalar form (a - b as a + (-b), which rounds identically),
+//    so the sums are those of the scalar form bit for bit;
+//  - the reference rows sit in shared memory as pairs, interleaved by
+//    component ((a.x, b.x, a.y, b.y), (a.z, b.z, a.w, b.w) per vector;
+//    negated for the distance kinds), so one pair load feeds both halves;
+//  - the sample vectors reach shared memory by cp.async, two stages per warp,
+//    the next step's copies in flight while the current step computes.
+// The Gaussian and distance kinds sum the squared differences directly: the
+// squared distance does not cancel as |x|^2 + |y|^2 - 2 x.y does for rows far
+// from the origin.
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only) and its
+// group commit / wait (per thread: a thread's wait covers its own copies).
+__device__ __forceinline__ void skinny_cp16(float4* dst, const float4* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void skinny_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void skinny_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int NA>
+__host__ __device__ constexpr int skinny_rows() {
+  return NA <= 16 ? 4 : 2;
+}
+constexpr int kSkinnyLoadsInFlight = 8;  // 16-byte loads per lane, over the warp's rows
+constexpr size_t kSkinnyStageBytes = (size_t)8 * 2 * kSkinnyLoadsInFlight * 32 * 16;  // 8 warps, 2 stages
+// shared memory of the reference pairs (an odd count padded with a zero row)
+inline size_t skinny_ref_bytes(int64_t nA, int dp) { return (size_t)((nA + 1) / 2) * 2 * dp * sizeof(float); }
 
 template <int KIND, int NA>
 __global__ void __launch_bounds__(256)
@@ -470,66 +497,136 @@ gram_skinny_kernel(const float* __restrict__ A, int nA, const float* __restrict_
                    int dp, const float* __restrict__ normA, const float* __restrict__ normB,
                    const int64_t* __restrict__ idA, const int64_t* __restrict__ idB,
                    float neg_scale, float* __restrict__ out, int64_t ldo) {
-  constexpr int R = kSkinnyRows, QB = kSkinnyLoads;
-  extern __shared__ float4 As4[];  // [nA][dp/4]
+  constexpr int R = skinny_rows<NA>(), QB = kSkinnyLoadsInFlight / R;
+  constexpr int NP = NA >= 2 ? NA / 2 : 1;  // reference pairs per lane's accumulators
+  constexpr bool kDiff = KIND == DK_RBF || KIND == DK_DIST;
+  extern __shared__ float4 As4[];  // [(nA + 1) / 2][dp / 4][2] reference pairs, then the warps' stages
   const int dq = dp >> 2;
+  const int np = (nA + 1) / 2;
   const float4* A4 = reinterpret_cast<const float4*>(A);
-  for (int e = threadIdx.x; e < nA * dq; e += blockDim.x) As4[e] = A4[e];
+  {
+    // four vector pairs per thread in flight before any store
+    const int n2 = np * dq;
+    for (int e0 = threadIdx.x; e0 < n2; e0 += 4 * blockDim.x) {
+      float4 ra[4], rb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        ra[u] = rb[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (e < n2) {
+          const int pr = e / dq, q = e - pr * dq;
+          ra[u] = __ldg(A4 + (int64_t)(2 * pr) * dq + q);
+          if (2 * pr + 1 < nA) rb[u] = __ldg(A4 + (int64_t)(2 * pr + 1) * dq + q);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < n2) {
+          const float sg = kDiff ? -1.0f : 1.0f;  // exact
+          As4[2 * e] = make_float4(sg * ra[u].x, sg * rb[u].x, sg * ra[u].y, sg * rb[u].y);
+          As4[2 * e + 1] = make_float4(sg * ra[u].z, sg * rb[u].z, sg * ra[u].w, sg * rb[u].w);
+        }
+      }
+    }
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int nwarp = blockDim.x >> 5;
   const int a_mine = lane >> scatter_shift<NA>();
   const bool writer = (lane & ((1 << scatter_shift<NA>()) - 1)) == 0 && a_mine < nA;
-  for (int b0 = (blockIdx.x * nwarp + (threadIdx.x >> 5)) * R; b0 < nB; b0 += gridDim.x * nwarp * R) {
-    float acc[R][NA];
+  // The warp's work is a sequence of items (row group, step of 32 * QB
+  // vectors); the sample vectors of item k + 1 are copied to the warp's
+  // shared-memory stage (k + 1) & 1 while item k is computed from stage k & 1.
+  // Each lane copies and reads only its own 16-byte slots, so the lane's
+  // cp.async group wait is the only synchronisation.
+  const int warp = threadIdx.x >> 5;
+  float4* const stage = As4 + (size_t)np * dq * 2 + (size_t)warp * 2 * R * QB * 32;  // [2][R][QB][32]
+  const int first = (blockIdx.x * nwarp + warp) * R, stride = gridDim.x * nwarp * R;
+  const int steps = (dq + 32 * QB - 1) / (32 * QB);
+  const int groups = first < nB ? (nB - first + stride - 1) / stride : 0;
+  const int n_items = groups * steps;
+  auto issue = [&](int item) {
+    const int b0 = first + (item / steps) * stride, q0 = (item % steps) * 32 * QB;
+    float4* st = stage + (item & 1) * R * QB * 32;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int a = 0; a < NA; ++a) acc[r][a] = 0.0f;
-    const float4* pb[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) pb[r] = reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + r, nB - 1) * dp);
-    for (int q0 = 0; q0 < dq; q0 += 32 * QB) {
-      float4 x[R][QB];
+    for (int r = 0; r < R; ++r) {
+      const float4* pb = reinterpret_cast<const float4*>(Bm + (int64_t)min(b0 + r, nB - 1) * dp);
 #pragma unroll
       for (int t = 0; t < QB; ++t) {
         const int q = q0 + t * 32 + lane;
-#pragma unroll
-        for (int r = 0; r < R; ++r) x[r][t] = q < dq ? __ldg(pb[r] + q) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (q < dq) skinny_cp16(st + (r * QB + t) * 32 + lane, pb + q);
       }
+    }
+    skinny_commit();
+  };
+  // acc[r][p] = (sum for reference 2p, sum for reference 2p + 1) of row r
+  float2 acc[R][NP];
 #pragma unroll
-      for (int t = 0; t < QB; ++t) {
-        const int q = q0 + t * 32 + lane;
-        if (q >= dq) break;
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-          if (a < nA) {
-            const float4 y = As4[a * dq + q];
+    for (int p = 0; p < NP; ++p) acc[r][p] = make_float2(0.0f, 0.0f);
+  if (n_items > 0) issue(0);
+  for (int item = 0; item < n_items; ++item) {
+    if (item + 1 < n_items) {
+      issue(item + 1);
+      skinny_wait<1>();  // item's copies have landed
+    } else {
+      skinny_wait<0>();
+    }
+    const int b0 = first + (item / steps) * stride, q0 = (item % steps) * 32 * QB;
+    const float4* st = stage + (item & 1) * R * QB * 32;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-              if constexpr (KIND == DK_RBF || KIND == DK_DIST) {
-                const float e0 = x[r][t].x - y.x, e1 = x[r][t].y - y.y, e2 = x[r][t].z - y.z, e3 = x[r][t].w - y.w;
-                acc[r][a] = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc[r][a]))));
-              } else {
-                acc[r][a] =
-                    fmaf(x[r][t].x, y.x, fmaf(x[r][t].y, y.y, fmaf(x[r][t].z, y.z, fmaf(x[r][t].w, y.w, acc[r][a]))));
-              }
+    for (int t = 0; t < QB; ++t) {
+      const int q = q0 + t * 32 + lane;
+      if (q >= dq) break;
+      float4 x[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[r] = st[(r * QB + t) * 32 + lane];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        if (2 * p < nA) {
+          const float4 y0 = As4[2 * (p * dq + q)], y1 = As4[2 * (p * dq + q) + 1];
+          const float2 yx = make_float2(y0.x, y0.y), yy = make_float2(y0.z, y0.w);
+          const float2 yz = make_float2(y1.x, y1.y), yw = make_float2(y1.z, y1.w);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            // components w, z, y, x in that order, as the scalar form's fma nest
+            if constexpr (kDiff) {
+              const float2 ew = __fadd2_rn(make_float2(x[r].w, x[r].w), yw);
+              const float2 ez = __fadd2_rn(make_float2(x[r].z, x[r].z), yz);
+              const float2 ey = __fadd2_rn(make_float2(x[r].y, x[r].y), yy);
+              const float2 ex = __fadd2_rn(make_float2(x[r].x, x[r].x), yx);
+              acc[r][p] = __ffma2_rn(ew, ew, acc[r][p]);
+              acc[r][p] = __ffma2_rn(ez, ez, acc[r][p]);
+              acc[r][p] = __ffma2_rn(ey, ey, acc[r][p]);
+              acc[r][p] = __ffma2_rn(ex, ex, acc[r][p]);
+            } else {
+              acc[r][p] = __ffma2_rn(make_float2(x[r].w, x[r].w), yw, acc[r][p]);
+              acc[r][p] = __ffma2_rn(make_float2(x[r].z, x[r].z), yz, acc[r][p]);
+              acc[r][p] = __ffma2_rn(make_float2(x[r].y, x[r].y), yy, acc[r][p]);
+              acc[r][p] = __ffma2_rn(make_float2(x[r].x, x[r].x), yx, acc[r][p]);
             }
           }
         }
       }
     }
+    if (item % steps == steps - 1) {  // the group's last step: its rows are complete
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float sum = warp_reduce_scatter<NA>(acc[r], lane);  // x.y, or |x - y|^2
-      const int b = b0 + r;
-      if (writer && b < nB) {
-        const bool same = idA && idB && idA[a_mine] == idB[b];
-        float v;
-        if constexpr (KIND == DK_RBF) v = same ? 1.0f : exp2f(sum * neg_scale);
-        else if constexpr (KIND == DK_DIST) v = same ? 0.0f : sqrtf(sum);
-        else v = gram_epilogue<KIND>(sum, 0.0f, 0.0f, same, neg_scale);
-        out[(int64_t)a_mine * ldo + b] = v;
+      for (int r = 0; r < R; ++r) {
+        // x.y, or |x - y|^2, of reference a_mine
+        const float sum = warp_reduce_scatter<NA>(reinterpret_cast<float(&)[NA]>(acc[r][0]), lane);
+        const int b = b0 + r;
+        if (writer && b < nB) {
+          const bool same = idA && idB && idA[a_mine] == idB[b];
+          float v;
+          if constexpr (KIND == DK_RBF) v = same ? 1.0f : exp2f(sum * neg_scale);
+          else if constexpr (KIND == DK_DIST) v = same ? 0.0f : sqrtf(sum);
+          else v = gram_epilogue<KIND>(sum, 0.0f, 0.0f, same, neg_scale);
+          out[(int64_t)a_mine * ldo + b] = v;
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) acc[r][p] = make_float2(0.0f, 0.0f);
       }
     }
   }
@@ -540,17 +637,21 @@ static cudaError_t gram_dispatch(const float* A, int64_t nA, const float* Bm, in
                                  const float* normA, const float* normB, const int64_t* idA,
                                  const int64_t* idB, float neg_scale, float* out, int64_t ldo,
                                  cudaStream_t st) {
-  const size_t skinny_smem = (size_t)nA * dp * sizeof(float);
+  const size_t skinny_smem = skinny_ref_bytes(nA, dp);
   if (nA <= 32 && skinny_smem <= 96 * 1024) {
     // every CTA first copies the reference rows to shared memory: few CTAs,
-    // many sample rows each (two per SM)
-    const int grid = (int)std::min<int64_t>(ceil_div(nB, 8 * kSkinnyRows), 152 * 2);
+    // many sample rows each; behind the reference rows, each warp's two
+    // stages of sample vectors (8 warps x 2 x 8 x 32 x 16 B = 64 KB)
+    const size_t smem = skinny_smem + kSkinnyStageBytes;
+    const int per_sm = smem + 1024 <= 113 * 1024 ? 2 : 1;  // 228 KB of shared memory per SM
     cudaError_t e;
 #define KKM_SKINNY(NAV)                                                                 \
   e = cudaFuncSetAttribute(gram_skinny_kernel<KIND, NAV>,                               \
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);     \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,                 \
+                           96 * 1024 + (int)kSkinnyStageBytes);                         \
   if (e != cudaSuccess) return e;                                                       \
-  gram_skinny_kernel<KIND, NAV><<<grid, 256, skinny_smem, st>>>(                        \
+  gram_skinny_kernel<KIND, NAV><<<(int)std::min<int64_t>(ceil_div(nB, 8 * skinny_rows<NAV>()), 152 * per_sm), \
+                                  256, smem, st>>>(                                     \
       A, (int)nA, Bm, (int)nB, dp, normA, normB, idA, idB, neg_scale, out, ldo);
     if (nA <= 1) { KKM_SKINNY(1) }
     else if (nA <= 4) { KKM_SKINNY(4) }

@@ -1961,7 +1961,16 @@ __global__ void medoid_rows_kernel(unsigned long long* __restrict__ keys, const 
   const unsigned long long key = keys[j];
   const int m = (c[j] > 0 && n_j[j] > 0 && key != ~0ull) ? (int)(key & 0xffffffffull) : -1;
   const int ms = m >= 0 ? m : 0;
-  for (int q = lane; q < dp4; q += 32) MIX[(int64_t)j * dp4 + q] = Xi[(int64_t)ms * dp4 + q];
+  // four 16-byte loads in flight per lane before the stores
+  for (int q0 = lane; q0 < dp4; q0 += 128) {
+    float4 t[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if (q0 + 32 * v < dp4) t[v] = Xi[(int64_t)ms * dp4 + q0 + 32 * v];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if (q0 + 32 * v < dp4) MIX[(int64_t)j * dp4 + q0 + 32 * v] = t[v];
+  }
   __syncwarp();
   if (lane == 0) {
     mi[j] = m;
@@ -1989,14 +1998,18 @@ cudaError_t launch_medoid_rows(unsigned long long* keys, const int32_t* c, const
 // or a.b (linear, self terms the squared norms auxM, aux_i), |a - b|^2 and
 // a.b summed lane-strided over 16-byte vectors, then a fixed xor tree.  The
 // next mini-batch's medoid rows are written as well: NX[j] = the row after.
-__global__ void __launch_bounds__(256)
+// One warp per cluster (up to 32 warps; more clusters take turns), eight
+// 16-byte loads in flight per lane; the launch width changes no sum (thread
+// j holds cluster j's value for the block sum, the other slots are zero).
+constexpr int kDispMaxWarps = 32;
+__global__ void __launch_bounds__(kDispMaxWarps * 32)
 displacement_rows_kernel(const float4* __restrict__ MX, const float* __restrict__ auxM,
                          const float4* __restrict__ Xi, const float* __restrict__ aux_i, int dp4, int C,
                          const unsigned long long* __restrict__ keys, const int32_t* __restrict__ mi,
                          const int64_t* __restrict__ old, const int64_t* __restrict__ cur, int linear,
                          float neg_scale, double* __restrict__ out, float4* __restrict__ NX, float* __restrict__ nauxM) {
   __shared__ double val[kMaxC];
-  __shared__ double red[8];
+  __shared__ double red[kDispMaxWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = w; j < C; j += nw) {
     const bool moved = mi[j] >= 0 && old[j] != cur[j];
@@ -2004,14 +2017,29 @@ displacement_rows_kernel(const float4* __restrict__ MX, const float* __restrict_
     const float4* a = MX + (int64_t)j * dp4;
     const float4* b = Xi + (int64_t)l * dp4;
     float acc = 0.0f;
-    for (int q = lane; q < dp4; q += 32) {
-      const float4 x = a[q], y = moved ? b[q] : x;
-      NX[(int64_t)j * dp4 + q] = y;
-      if (linear) {
-        acc = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc))));
-      } else {
-        const float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
-        acc = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc))));
+    for (int q0 = lane; q0 < dp4; q0 += 128) {
+      float4 xs[4], ys[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int q = q0 + 32 * v;
+        if (q < dp4) {
+          xs[v] = a[q];
+          ys[v] = moved ? b[q] : xs[v];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int q = q0 + 32 * v;
+        if (q < dp4) {
+          const float4 x = xs[v], y = ys[v];
+          NX[(int64_t)j * dp4 + q] = y;
+          if (linear) {
+            acc = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, acc))));
+          } else {
+            const float e0 = x.x - y.x, e1 = x.y - y.y, e2 = x.z - y.z, e3 = x.w - y.w;
+            acc = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, acc))));
+          }
+        }
       }
     }
     acc = warp_sum_f32(acc);
@@ -2040,7 +2068,8 @@ cudaError_t launch_displacement_rows(const float* MX, const float* auxM, const f
                                      const int64_t* cur, bool linear, float neg_scale, double* out, float* NX,
                                      float* nauxM, cudaStream_t st) {
   if (dp % 4 != 0 || C > kMaxC) return cudaErrorInvalidValue;
-  displacement_rows_kernel<<<1, 256, 0, st>>>(reinterpret_cast<const float4*>(MX), auxM,
+  const int warps = std::min(std::max(C, 1), kDispMaxWarps);
+  displacement_rows_kernel<<<1, 32 * warps, 0, st>>>(reinterpret_cast<const float4*>(MX), auxM,
                                               reinterpret_cast<const float4*>(Xi), aux_i, dp / 4, C, keys, mi, old,
                                               cur, linear ? 1 : 0, neg_scale, out, reinterpret_cast<float4*>(NX),
                                               nauxM);

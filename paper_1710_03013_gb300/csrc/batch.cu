@@ -141,8 +141,9 @@ void assign_rows_save() { g_row_tuner.save(); }
 // The fits of a batch hand their split-form inner loops to one executor
 // thread, which runs them in rounds on its own stream: per round one f_hat
 // stream launch over every loop in flight (one per block type present), then
-// one assign launch per CTA width present, each item's CTAs doing what its
-// own launch would (same results as a fit alone).  A loop joins at the next
+// one assign launch for all of them (as wide as the widest, each CTA working
+// with its own loop's warp count, so its CTAs do what that loop's own launch
+// would: same results as a fit alone).  A loop joins at the next
 // round once the work before it on its fit's stream has finished (its event
 // is polled, so a fit still computing its block holds up no other loop) and
 // leaves after its iteration count; its fit's stream then waits for the
@@ -282,24 +283,27 @@ struct LoopExecutor {
       const cudaError_t e = launch_fhat_multi(slots, L, half != 0, st);
       if (e != cudaSuccess) return e;
     }
-    for (int nw = 1; nw <= 8; ++nw) {
-      int blocks = 0;
-      for (const Active& a : act)
-        if (a.r->item.nw == nw) blocks += a.r->item.assign_ctas;
-      if (blocks == 0) continue;
+    // one assign launch for every loop of the round, as wide as its widest
+    // loop: each CTA works with its own loop's warp count (the results of
+    // a launch of that width), so loops of small C no longer wait for
+    // launches of their own
+    {
+      int blocks = 0, nw = 1, smem = 0;
+      for (const Active& a : act) {
+        blocks += a.r->item.assign_ctas;
+        nw = std::max(nw, a.r->item.nw);
+        smem = std::max(smem, a.r->item.assign_smem);
+      }
       const long long key = RowTuner::key(nw, blocks);
       bool timed = false;
       const int RG = g_row_tuner.choose(key, &timed);
       RoundList L;
       L.cta_off[0] = 0;
-      int smem = 0;
-      for (const Active& a : act)
-        if (a.r->item.nw == nw) {
-          L.slot[L.n] = a.slot;
-          L.cta_off[L.n + 1] = L.cta_off[L.n] + (a.r->item.assign_ctas + RG - 1) / RG;
-          smem = std::max(smem, a.r->item.assign_smem);
-          ++L.n;
-        }
+      for (const Active& a : act) {
+        L.slot[L.n] = a.slot;
+        L.cta_off[L.n + 1] = L.cta_off[L.n] + (a.r->item.assign_ctas + RG - 1) / RG;
+        ++L.n;
+      }
       Sample smp{key, RG, blocks, nullptr, nullptr};
       if (timed) {
         smp.a = take_event();

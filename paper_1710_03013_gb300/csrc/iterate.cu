@@ -519,13 +519,17 @@ constexpr int kAssignMaxDynSmem = 160 * 1024;
 
 // The body takes its row block bx and the number of row blocks G of its
 // mini-batch explicitly, so that one launch can also cover the row blocks of
-// many mini-batches (assign_multi_kernel).
+// many mini-batches (assign_multi_kernel).  nw_item > 0 sets the warps that
+// work (the others only pass the barriers): a launch as wide as its widest
+// item then runs every item exactly as its own launch of nw_item warps would,
+// every split over warps and every thread-strided sum taken with nw_item.
 __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports& S, const IterState& I,
                                             const float* __restrict__ kself, int32_t* __restrict__ u,
                                             float* __restrict__ margin, float* __restrict__ dmin,
                                             float* __restrict__ fhat_out, double* __restrict__ ghat_out,
                                             int early_stop, int trace, const RescoreArgs& R, int bx, int G,
-                                            bool defer_sort = false, int RG = 1) {
+                                            bool defer_sort = false, int RG = 1, int nw_item = 0) {
+  const int nw = nw_item > 0 ? nw_item : (int)(blockDim.x >> 5);
   // dynamic shared memory (sized by the launch for this C): the distances of
   // the CTA's rows [C][kAssignRows], which the last CTA reuses as the support
   // sort's scratch, then the FP32 row of the slow re-score path [R.dp]
@@ -533,7 +537,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   __shared__ AssignShared sh;
   float* const dshp = dyn;
   auto dsh_at = [&](int j, int r) -> float& { return dshp[j * kAssignRows + r]; };
-  float* const xs = dyn + assign_dist_words(S.C, blockDim.x >> 5);
+  float* const xs = dyn + assign_dist_words(S.C, nw);
   __shared__ float rbest[kAssignRows], rsecond[kAssignRows];
   __shared__ int rlab[kAssignRows];
   __shared__ float wsum[32];
@@ -548,7 +552,8 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   // stream.
   if (I.done && *I.done) return;
   const int C = S.C;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool wact = w < nw;  // a working warp
   const float inf = __int_as_float(0x7f800000);
   for (int j = threadIdx.x; j < C; j += blockDim.x) {
     sh.nj[j] = S.n_j[j];
@@ -591,7 +596,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   // Warp w takes the contiguous clusters [jb, je), whose units are contiguous
   // too: one flat pass over them keeps 8 loads in flight across cluster
   // boundaries (j and its end are the same in every lane).
-  const int jb = (w * C) / nw, je = ((w + 1) * C) / nw;
+  const int jb = wact ? (w * C) / nw : 0, je = wact ? ((w + 1) * C) / nw : 0;
   if (jb < je) {
     int j = jb;
     int jend = sh.su[j + 1];
@@ -701,7 +706,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
     // every warp re-scores whole pairs, one landmark per lane (lane-strided
     // over the cluster's segment, then a fixed xor tree): FP32 kernel values
     // from the FP32 rows (16-byte loads; rows are padded to 8 floats)
-    for (int p = w; p < n_cand; p += nw) {
+    for (int p = w; wact && p < n_cand; p += nw) {
       const int r = cand[p] >> 9, j = cand[p] & 511;
       const int ir = rb * kAssignRows + r;
       const float4* xi = reinterpret_cast<const float4*>(R.Xi + (int64_t)ir * R.dp);
@@ -751,7 +756,7 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
         if (!(dj0 - b0 < I.flag_tau * fmaxf(fabsf(dj0), scale))) continue;
         const int k0 = S.seg_off[j], k1 = S.seg_off[j + 1];
         float acc = 0.0f;
-        for (int kk = k0 + w; kk < k1; kk += nw) {
+        for (int kk = k0 + w; wact && kk < k1; kk += nw) {
           const int k = S.perm[kk];
           float kv;
           if (R.K32) {  // the block's own FP32 values
@@ -833,7 +838,8 @@ __device__ __forceinline__ void assign_body(int64_t ldk, int Ni, const Supports&
   __threadfence();
   float2 o = make_float2(0.0f, 0.0f);
   int c = 0, lm = 0;
-  for (int b = threadIdx.x; b < G_rows; b += blockDim.x) {
+  const int nthr = 32 * nw;
+  for (int b = threadIdx.x; (int)threadIdx.x < nthr && b < G_rows; b += nthr) {
     o = df_add(o, __ldcg(I.omega_part + b));
     c += __ldcg(I.changed_part + b);
     lm += I.lm_part ? __ldcg(I.lm_part + b) : 0;
@@ -1014,7 +1020,7 @@ assign_multi_kernel(const LoopItem* __restrict__ items, RoundList L, int RG) {
   const LoopItem& it = load_item(items, L.slot[k], raw);
   const int bx = (int)blockIdx.x - L.cta_off[k], G = L.cta_off[k + 1] - L.cta_off[k];
   assign_body(it.ldk, it.Ni, it.S, it.I, it.kself, it.u, nullptr, nullptr, nullptr, nullptr, it.early_stop,
-              /*trace=*/1, it.R, bx, G, /*defer_sort=*/true, RG);
+              /*trace=*/1, it.R, bx, G, /*defer_sort=*/true, RG, it.nw);
 }
 
 // The support sort of every listed item (one CTA of kSortThreads each) whose

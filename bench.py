@@ -657,7 +657,7 @@ def run_ours(args, cfg, X):
 # ------------------------------------------------------------ batched form
 def batched_data(cfg):
     from synth import batched_problems, blobs
-    shapes = batched_problems(cfg["n_problems"])
+    shapes = batched_problems(cfg["n_problems"])[:cfg.get("take") or None]
     data = [blobs(p["N"], p["d"], p["C"], workload=3, problem=p["problem"])[0] for p in shapes]
     return shapes, data
 
@@ -1147,6 +1147,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mnist", choices=sorted(WORKLOADS))
     ap.add_argument("--streams", type=int, default=0, help="batched workload: concurrent streams (0: default)")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched workload: fit only its first N problems (a smaller case for profiling; 0: all)")
     ap.add_argument("--pipeline", default="auto", choices=["auto", "serial", "overlap"],
                     help="kernel-block scheduling of the fits (auto: next block overlapped when B >= 2)")
     ap.add_argument("--no-configs", action="store_true",
@@ -1154,6 +1156,9 @@ def main():
     args = ap.parse_args()
     cfg = dict(WORKLOADS[args.workload])
     cfg["key"] = args.workload
+    if args.workload == "batched" and args.problems > 0:
+        cfg["take"] = args.problems
+        cfg["name"] = f"first {args.problems} problems of the " + cfg["name"]
     if args.workload == "serving":
         if args.impl == "ours":
             from paper_1710_03013_gb300 import build as _b

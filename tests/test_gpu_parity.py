@@ -59,6 +59,29 @@ def test_kernel_matrix_linear(lib):
     assert np.max(np.abs(got - want) / scale) <= 1e-5
 
 
+
+@pytest.mark.parametrize("nA,nB,d,kind", [(3, 1000, 784, "rbf"), (17, 2051, 100, "rbf"), (32, 777, 8, "rbf"),
+                                          (2, 5000, 33, "rbf"), (5, 3001, 129, "linear"), (16, 1500, 256, "linear"),
+                                          (31, 300, 64, "linear")])
+def test_kernel_matrix_few_references(lib, nA, nB, d, kind):
+    """At most 32 reference rows (the medoid and k-means++ columns): the
+    reference rows held in shared memory as pairs (an odd count padded), two
+    or four sample rows per warp, row lengths that are not a multiple of the
+    128-value step; Gaussian and linear kinds against the oracle."""
+    X, _ = blobs(nA + nB, d, 5, workload=53, problem=nA * 1000 + d)
+    A, Bm = X[:nA], X[nA:]
+    if kind == "rbf":
+        sig = _median_sigma(X)
+        got = _np(lib.kkm_kernel_matrix(_dev(A), _dev(Bm), "rbf", sig))
+        want = O.Kernel(O.KIND_RBF, sig)(A, Bm)
+        assert np.max(np.abs(got - want)) <= KERNEL_ABS
+        assert np.mean(want > 0.05) > 0.05  # non-negligible values are covered
+    else:
+        got = _np(lib.kkm_kernel_matrix(_dev(A), _dev(Bm), "linear"))
+        want = A.astype(np.float64) @ Bm.astype(np.float64).T
+        scale = np.linalg.norm(A, axis=1)[:, None] * np.linalg.norm(Bm, axis=1)[None, :]
+        assert np.max(np.abs(got - want) / scale) <= 1e-5
+
 @pytest.mark.parametrize("atoms", [300, 57])
 def test_kernel_matrix_rmsd(lib, atoms):
     F, _ = md_trajectory(n_frames=260, n_atoms=atoms, n_states=3, dwell=40.0, workload=51,

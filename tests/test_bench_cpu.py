@@ -94,3 +94,14 @@ def test_committed_traffic_entries_name_existing_sources():
         for src in ent["sources"]:
             assert os.path.exists(os.path.join(bench.ROOT, "paper_1710_03013_gb300", "csrc", src)), (key, src)
         assert np.isfinite(ent["bytes_per_launch"])
+
+
+def test_batched_slice_is_a_prefix_of_the_workload():
+    """--problems N fits the first N problems of the batched workload: the
+    same shapes and data as those problems of the full batch."""
+    full = dict(bench.WORKLOADS["batched"], n_problems=12)
+    cut = dict(full, take=5)
+    shapes_f, data_f = bench.batched_data(full)
+    shapes_c, data_c = bench.batched_data(cut)
+    assert len(shapes_c) == 5 and shapes_c == shapes_f[:5]
+    assert all(np.array_equal(a, b) for a, b in zip(data_c, data_f[:5]))
